@@ -1,0 +1,131 @@
+"""Pins of the oracle's discretisation (Sec. 2): kernels of the blocks,
+optimal convergence on a manufactured solution (inf-sup stability of TH and
+SV, Sec. 2.1), pointwise divergence-free SV velocities, and the paper's
+printed nnz-per-DoF tables."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import geometry, lagrange, stokes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _mesh(n):
+    return W.unit_square_mesh(n)
+
+
+def test_block_kernels_and_integrals():
+    """A 1 = 0 (constants in the Laplacian's kernel before Dirichlet),
+    B u_const = 0, B^T 1_p = 0 on free velocity rows (the pressure null
+    space of the all-Dirichlet problem, Sec. 2), sum M = |Omega|,
+    sum int psi = |Omega|."""
+    v, c = _mesh(3)
+    for fam, k in [(stokes.TH, 2), (stokes.TH, 4), (stokes.SV, 2)]:
+        if fam == stokes.SV:
+            vv, cc, _ = geometry.refine_alfeld(v, c)
+        else:
+            vv, cc = v, c
+        D = stokes.discretize(vv, cc, fam, k)
+        d, nV, nQ = D.d, D.V.n, D.Q.n
+        Kf = D.Kfull
+        one_u = np.zeros(D.n_full); one_u[:nV] = 1.0
+        y = Kf @ one_u
+        assert np.abs(y).max() < 1e-12                 # A 1 = 0 and B (1,0) = 0
+        one_p = np.zeros(D.n_full); one_p[d * nV:] = 1.0
+        assert np.abs((D.K @ one_p[D.free])).max() < 1e-12
+        assert abs(D.Mv.sum() - 1.0) < 1e-13
+        assert abs(D.p_integrals.sum() - 1.0) < 1e-13
+        assert abs(Kf - Kf.T).max() < 1e-13
+
+
+def _mms_errors(fam, k, n, barycentric=False):
+    v, c = _mesh(n)
+    if barycentric:
+        v, c, _ = geometry.refine_alfeld(v, c)
+    D = stokes.discretize(v, c, fam, k)
+    f = W.mms_forcing(D.V.coords).T
+    g = W.mms_velocity(D.V.coords).T
+    b, xD = stokes.load_vector(D, f, g)
+    x = stokes.direct_solve(D, b)
+    full = stokes.zero_mean_pressure(D, stokes.expand(D, x, xD))
+    return stokes.l2_errors(D, full, W.mms_velocity, W.mms_pressure), D, full
+
+
+@pytest.mark.parametrize("fam,k,bary", [(stokes.TH, 2, False), (stokes.TH, 3, False), (stokes.SV, 2, True)])
+def test_optimal_convergence_rates(fam, k, bary):
+    """T1: inf-sup stable pairs give ||u-u_h|| = O(h^{k+1}), ||p-p_h|| = O(h^k)."""
+    errs = [_mms_errors(fam, k, n, bary)[0] for n in (4, 8, 16)]
+    eu = np.array([e[0] for e in errs]); ep = np.array([e[1] for e in errs])
+    ru = np.log2(eu[:-1] / eu[1:]); rp = np.log2(ep[:-1] / ep[1:])
+    assert ru[-1] > k + 1 - 0.25, ru
+    assert rp[-1] > k - 0.25, rp
+
+
+def _div_l2(D, full):
+    d, k = D.d, D.k
+    lam, w = lagrange.quadrature(d, 2 * k)
+    dphi = lagrange.basis_dlam(k, d, lam)
+    G, vol = lagrange.barycentric_gradients(D.verts, D.cells)
+    gphi = np.einsum("qbi,cid->cqbd", dphi, G)
+    U = full[:d * D.V.n].reshape(d, D.V.n)
+    div = sum(np.einsum("cqb,cb->cq", gphi[..., c], U[c][D.V.cell_nodes]) for c in range(d))
+    return np.sqrt((vol[:, None] * w[None] * div ** 2).sum())
+
+
+def test_scott_vogelius_is_pointwise_divergence_free():
+    """T2: div(P_k) is in P_{k-1}^disc, so the SV velocity is divergence-free
+    to round-off; the TH velocity is not (Sec. 2.1)."""
+    _, Dsv, xsv = _mms_errors(stokes.SV, 2, 4, True)
+    _, Dth, xth = _mms_errors(stokes.TH, 2, 4, False)
+    assert _div_l2(Dsv, xsv) < 1e-10
+    assert _div_l2(Dth, xth) > 1e-4
+
+
+def _nnz_full_blocks(fam, d, k, n):
+    """nnz/DoF of the full system as PETSc stores it: d x d velocity blocks
+    counted densely, B and B^T, the (structurally zero) pressure-pressure
+    block of the cell-coupling pattern allocated, Dirichlet rows kept."""
+    import scipy.sparse as sp
+    if d == 2:
+        v, c = W.unit_square_mesh(n)
+    else:
+        v, c = W.kuhn_cube_mesh(n)
+    if fam == stokes.SV:
+        v, c, _ = geometry.refine_alfeld(v, c)
+    D = stokes.discretize(v, c, fam, k)
+    nV, nQ = D.V.n, D.Q.n
+    cn, qn = D.V.cell_nodes, D.Q.cell_nodes
+
+    def pattern(rn, cnn, nr, nc):
+        r = np.repeat(rn[:, :, None], cnn.shape[1], 2).ravel()
+        col = np.repeat(cnn[:, None, :], rn.shape[1], 1).ravel()
+        m = sp.csr_matrix((np.ones(len(r)), (r, col)), shape=(nr, nc))
+        m.sum_duplicates()
+        return m.nnz
+    nnz = d * d * pattern(cn, cn, nV, nV) + 2 * d * pattern(qn, cn, nQ, nV) + pattern(qn, qn, nQ, nQ)
+    return nnz / (d * nV + nQ)
+
+
+def test_nnz_per_dof_matches_paper_tables():
+    """T3: the paper's printed nnz/DoF (Tables 2-5) is reproduced within 3%
+    by the oracle's spaces.  2D on 16x16 (TH) / Alfeld 8x8 (SV) structured
+    meshes; 3D extrapolated to an unbounded mesh from n = 4 and n = 6 (the
+    boundary share decays like 1/n; the paper's 3D meshes are large)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "nnz_per_dof.txt")) if l[0] != "#"]
+    checked = 0
+    for fam, d, k, want in rows:
+        d, k, want = int(d), int(k), float(want)
+        if k > 6 or (d == 3 and k > 3):
+            continue
+        F = stokes.TH if fam == "TH" else stokes.SV
+        if d == 2:
+            got = _nnz_full_blocks(F, 2, k, 16 if F == stokes.TH else 8)
+        else:
+            a, b = _nnz_full_blocks(F, 3, k, 4), _nnz_full_blocks(F, 3, k, 6)
+            got = (6 * b - 4 * a) / 2
+        assert abs(got - want) / want < 0.03, (fam, d, k, got, want)
+        checked += 1
+    assert checked == 9
