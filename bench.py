@@ -1,0 +1,327 @@
+"""Benchmark: FGMRES-phMG time to a 1e-8 relative residual plus setup time,
+mixed precision (FP32 V-cycle inside FP64 FGMRES) against FP64, on one GB300.
+
+One step = stokes_mg_setup (mesh refinement, assembly, patch gather, batched
+FP64 Gauss-Jordan, coarse LU, Arnoldi estimates, graph capture) + stokes_solve
+(load vector, FGMRES(30) preconditioned by the phMG V-cycle, zero-mean
+pressure) on the Taylor-Hood P4/P3 64x64 unit-square workload (169,347 DoFs
+with boundary, 167,299 free) with seeded U[-1,1] nodal forcing.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload NAME] [--no-cpu-baseline]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FGMRES-phMG time to 1e-8 residual + setup time, mixed vs FP64 on GB300"
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="th_p4_64x64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- oracle leg
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import multigrid as mg
+w = W.workload({name!r})
+t0 = time.perf_counter()
+h = mg.Hierarchy(w.verts, w.cells, w.n_refine, w.family, w.schedule, barycentric=w.barycentric)
+t1 = time.perf_counter()
+D = h.levels[0].disc
+f = W.nodal_forcing(D.V.n, D.d, w.seed)
+full, its, hist, b, x = mg.solve(h, f, None, tol={tol!r})
+t2 = time.perf_counter()
+print(json.dumps(dict(setup_s=t1 - t0, solve_s=t2 - t1, its=its, relres=hist[-1])))
+"""
+
+
+def run_oracle(name, timeout=900):
+    """The FP64 CPU oracle, as it stands, in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=timeout, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    runs = []
+    for _ in range(max(1, a.steps)):
+        runs.append(run_oracle(a.workload))
+    ms = [1e3 * (r["setup_s"] + r["solve_s"]) for r in runs]
+    value = sum(ms) / len(ms)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": value, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"full setup + FGMRES solve of {a.workload} per step, single-threaded numpy/scipy",
+                         "iterations": runs[0]["its"]},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows)
+        smax = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2407_07253_gb300 as P
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    P.lib()
+    w = W.workload(a.workload)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(precision):
+        return P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                          hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=precision,
+                          stream=stream.cuda_stream)
+
+    # forcing in the library's node order (seeded U[-1,1] nodal values)
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                       hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
+    info0 = probe.info()
+    probe.close()
+    nV, nQ, d = info0["n_vel_nodes"], info0["n_pres_nodes"], w.verts.shape[1]
+    f_host = torch.tensor(W.nodal_forcing(nV, d, w.seed).reshape(-1)).pin_memory()
+    f_dev = f_host.to(dev)
+    u_dev = torch.empty(d * nV, dtype=torch.float64, device=dev)
+    p_dev = torch.empty(nQ, dtype=torch.float64, device=dev)
+    u_host = torch.empty(d * nV, dtype=torch.float64).pin_memory()
+    p_host = torch.empty(nQ, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    def one_step(precision, e2e=False, prof=None):
+        flush.fill_(1.0)                      # L2 flush between steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = make(precision)
+        if prof is not None:
+            for k in prof:
+                h.prof_enable(k, True)
+        if e2e:
+            f = f_host.to(dev, non_blocking=True)
+        else:
+            f = f_dev
+        u, p, its, rel = h.solve(f, tol=TOL, u=u_dev, p=p_dev)
+        if e2e:
+            u_host.copy_(u, non_blocking=True)
+            p_host.copy_(p, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        st = h.info()
+        pr = {k: h.prof_read(k) for k in (prof or [])}
+        h.close()
+        return e0.elapsed_time(e1), its, rel, st, pr
+
+    # warm-up
+    for _ in range(a.warmup):
+        one_step(P.MIXED)
+    barrier()
+    # timed region: mixed precision, inputs resident in HBM
+    times, its_l, launches, gj_prof = [], [], 0, [0, 0.0]
+    stats = None
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            ms, its, rel, st, pr = one_step(P.MIXED, prof=[P._binding.PROF_GJ])
+            times.append(ms)
+            its_l.append(its)
+            launches += st["kernel_launches"]
+            gj_prof[0] += pr[P._binding.PROF_GJ][0]
+            gj_prof[1] += pr[P._binding.PROF_GJ][1]
+            stats = st
+        barrier()
+        wall = time.perf_counter() - t0
+    ms_local = sum(times) / len(times)
+    if pg is not None:
+        t = torch.tensor([ms_local], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms_local
+    # e2e through host buffers (pinned H2D of f, D2H of u and p inside the step)
+    e2e_times = [one_step(P.MIXED, e2e=True)[0] for _ in range(max(2, a.steps // 2))]
+    # FP64 V-cycle for the mixed-vs-FP64 comparison
+    f64 = [one_step(P.FP64) for _ in range(max(2, a.steps // 2))]
+    # solve-phase kernel timing of the patch apply (secondary roofline)
+    _, _, _, st_p, pr_p = one_step(P.MIXED, prof=[P._binding.PROF_PATCH, P._binding.PROF_SPMV])
+    barrier()
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # dominant kernel of a step: the batched FP64 Gauss-Jordan patch inversion
+    # (2 n_i^3 flop per patch; FP64 ALU bound on GB300)
+    sizes = []
+    flops_gj = 0.0
+    # algorithmic flops: sum over relaxed levels of sum_i 2 n_i^3, from the
+    # patch offsets of a host-only build (same hierarchy)
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                       hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
+    for li in range(stats["n_levels"] - 1):
+        off, _ = probe.patches(li)
+        n = np.diff(off).astype(np.float64)
+        sizes.append(n)
+        flops_gj += float((2.0 * n ** 3).sum())
+    probe.close()
+    gj_launches_per_step = gj_prof[0] / a.steps
+    gj_ms_per_step = gj_prof[1] / a.steps
+    fp64_peak_tflops = 1.25      # nominal GB300 FP64 (no measured FP64 peak)
+    # the coarse bordered GJ is many tiny launches; report the patch batches
+    # (launches over the relaxed levels) as the kernel
+    achieved_gj = flops_gj / (gj_ms_per_step * 1e-3) / 1e12 if gj_ms_per_step > 0 else None
+    # patch apply (FP32): bytes = sum n_i * ld32_i * 4 + 3 * sum n_i * 4 per launch, averaged over levels
+    n_patch_launch, ms_patch = pr_p[P._binding.PROF_PATCH]
+    line = {
+        "metric": METRIC, "value": ms_max, "unit": "ms", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": a.workload, "family": "TH" if w.family == 0 else "SV", "k": w.k,
+                   "schedule": w.schedule, "n_free": stats["n_free"], "nnz_level0": stats["nnz"][0],
+                   "tol": TOL, "precision": "mixed (FP32 V-cycle, FP64 FGMRES/LU/coarse)",
+                   "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) before every step",
+                   "inputs": "mesh on host, f resident in HBM"},
+        "iterations": its_l[-1],
+        "setup_ms": {k: stats[k] for k in ("t_mesh_ms", "t_assembly_ms", "t_upload_ms", "t_gather_lu_ms",
+                                           "t_coarse_ms", "t_eig_ms", "t_graph_ms", "t_total_ms")},
+        "e2e": {"value": sum(e2e_times) / len(e2e_times), "unit": "ms",
+                "h2d_bytes_per_step": int(f_host.numel() * 8),
+                "d2h_bytes_per_step": int((u_host.numel() + p_host.numel()) * 8)},
+        "fp64": {"value": sum(x[0] for x in f64) / len(f64), "unit": "ms", "iterations": f64[-1][1],
+                 "setup_ms": f64[-1][3]["t_total_ms"]},
+        "gpu_launches": int(launches / a.steps),
+        "roofline": {"kernel": "gj_inverse_smem (batched FP64 Gauss-Jordan, all relaxed levels)",
+                     "bound": "alu", "achieved": achieved_gj, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                     "frac": (achieved_gj / fp64_peak_tflops) if achieved_gj else None, "traffic": None,
+                     "peak_source": "nominal FP64 1.25 TFLOP/s (recipe), no measured FP64 peak",
+                     "launches_per_step": gj_launches_per_step, "ms_per_step": gj_ms_per_step,
+                     "flop_per_step": flops_gj},
+        "roofline_solve": {"kernel": "patch_apply_f32", "launches": n_patch_launch,
+                           "avg_us": 1e3 * ms_patch / max(1, n_patch_launch)},
+        "wall_s_timed": wall,
+    }
+    line["speedup_mixed_vs_fp64"] = line["fp64"]["value"] / ms_max
+    line["clocks"] = clk.summary()
+    if not a.no_cpu_baseline and world == 1:
+        try:
+            o = run_oracle(a.workload)
+            line["cpu_baseline"] = {"value": 1e3 * (o["setup_s"] + o["solve_s"]), "unit": "ms", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": f"one full setup + FGMRES solve of {a.workload} to {TOL}, "
+                                              "single-threaded numpy/scipy", "iterations": o["its"]}
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline"] = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {e}"[:200]}
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * stokes_mg.h -- C ABI of a GB300 (sm_103a) monolithic ph-multigrid
+ * preconditioner for high-order Taylor-Hood and Scott-Vogelius
+ * discretisations of stationary Stokes, used inside FGMRES.
+ *
+ * Method: Voronin, Harper, MacLachlan, Olson, Tuminaro, "Monolithic Multigrid
+ * Preconditioners for High-Order Discretizations of Stokes Equations"
+ * (arXiv 2407.07253).  Section / equation numbers below refer to it.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, a negative STOKES_E* code on failure; the
+ *     message of the last failure on the calling thread is available from
+ *     stokes_last_error().  No C++ exception crosses this boundary.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work of a call is ordered on that stream; calls that
+ *     return host results synchronise it.
+ *   - "device" pointers are CUDA global-memory pointers owned by the caller;
+ *     "host" pointers are ordinary CPU memory owned by the caller.  The
+ *     library never keeps a caller pointer beyond the call.
+ *   - The library owns every buffer it allocates; stokes_mg_destroy frees
+ *     them.  A handle is bound to the device that was current at setup.
+ *   - DoF order of a level's linear system ("free" vector, length n_free):
+ *     free velocity nodes of component 0, then of component 1 (then 2), then
+ *     every pressure node.  Dirichlet velocity DoFs are eliminated.  The
+ *     coordinates of every free DoF are exported by stokes_mg_level_dofs.
+ *   - DoF order of a full field (stokes_solve input/output): velocity of
+ *     component 0 at every velocity node (boundary included), component 1,
+ *     (component 2); pressure at every pressure node.  Node coordinates are
+ *     exported by stokes_mg_nodes.
+ */
+#ifndef STOKES_MG_H
+#define STOKES_MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define STOKES_OK               0
+#define STOKES_EINVAL          -1   /* invalid argument (sizes, family, k, mesh) */
+#define STOKES_EOOM            -2   /* device or host allocation failed */
+#define STOKES_ESINGULAR       -3   /* zero pivot in a patch or the coarse LU; stats.singular_patch names it */
+#define STOKES_ENOTCONVERGED   -4   /* FGMRES reached maxit above tol */
+#define STOKES_ENONFINITE      -5   /* NaN/Inf in a residual norm */
+#define STOKES_ECUDA           -6   /* a CUDA runtime call failed */
+#define STOKES_EUNSUPPORTED    -7   /* valid request outside what this build implements */
+
+/* element families (Sec. 2.1) */
+#define STOKES_TH 0   /* Taylor-Hood P_k / P_{k-1}, k >= 2 */
+#define STOKES_SV 1   /* Scott-Vogelius P_k / P_{k-1}^disc on an Alfeld-refined mesh, k >= d */
+
+/* p-hierarchy (Sec. 3.2, Fig. 7) */
+#define STOKES_HIER_DIRECT   0  /* P_k -> P_2, then h-coarsening */
+#define STOKES_HIER_GRADUAL  1  /* Fig. 7 schedule: k<=5 -> 2; k=6,7 -> 4 -> 2; k>=8 -> 5 -> 2 */
+#define STOKES_HIER_EXPLICIT 2  /* opts.schedule[0..n_schedule-1] velocity degrees, first = k */
+#define STOKES_HIER_HMG      3  /* no p-coarsening: P_k on every mesh (the paper's hMG) */
+
+/* precision of the V-cycle (FGMRES, Arnoldi, patch LU and coarse LU are FP64 in both) */
+#define STOKES_FP64  0
+#define STOKES_MIXED 1   /* FP32 SpMV, transfers and patch apply with FP32 accumulation */
+
+typedef struct {
+    int dim;               /* 2 (triangles) or 3 (tetrahedra) */
+    int n_verts;
+    int n_cells;
+    const double* verts;   /* host, [n_verts][dim] */
+    const int* cells;      /* host, [n_cells][dim+1] vertex indices */
+} stokes_mesh;
+
+typedef struct {
+    int hierarchy;          /* STOKES_HIER_* */
+    int n_schedule;         /* for STOKES_HIER_EXPLICIT */
+    int schedule[8];
+    int nu_p;               /* Chebyshev degree on the p-levels (Fig. 6b) */
+    int nu_h;               /* Chebyshev degree on the hMG levels (Fig. 6a) */
+    int n_V;                /* hMG cycles per phMG cycle (Sec. 4.1.1) */
+    int eig_steps;          /* Arnoldi steps of the lambda_max estimate */
+    unsigned long long eig_seed;  /* SplitMix64 seed of the Arnoldi start vectors */
+    double cheb_lo, cheb_hi;      /* Chebyshev interval = [lo, hi] * lambda_max */
+    double lmax_override[16];     /* > 0: use instead of the estimate on level i */
+    int precision;          /* STOKES_FP64 or STOKES_MIXED */
+    int restart;            /* FGMRES restart length (30 in Sec. 4) */
+    int maxit;              /* FGMRES iteration limit */
+    int use_graph;          /* capture the V-cycle in a CUDA graph (default 1) */
+    int host_only;          /* 1: build only the host-side hierarchy (meshes, spaces,
+                               CSR operators, transfers, patches) and make no CUDA
+                               call; only the info / dofs / nodes / get_csr /
+                               get_patches queries are valid on such a handle */
+} stokes_mg_opts;
+
+#define STOKES_MAX_LEVELS 16
+
+typedef struct {
+    int n_levels;
+    int dim, family, k;
+    int n_free[STOKES_MAX_LEVELS];
+    int degree[STOKES_MAX_LEVELS];        /* velocity degree of each level */
+    int level_family[STOKES_MAX_LEVELS];
+    int mesh_index[STOKES_MAX_LEVELS];    /* 0 = finest mesh */
+    int is_p_level[STOKES_MAX_LEVELS];
+    long long nnz[STOKES_MAX_LEVELS];     /* structural nonzeros of K_l (free rows) */
+    int n_patches[STOKES_MAX_LEVELS];
+    int max_patch[STOKES_MAX_LEVELS];
+    long long patch_entries[STOKES_MAX_LEVELS];  /* sum n_i^2 */
+    double lmax[STOKES_MAX_LEVELS];       /* lambda_max used by Chebyshev */
+    int n_vel_nodes, n_pres_nodes;        /* finest level, full fields */
+    int singular_patch;                   /* level*2^24 + patch of the first zero pivot, -1 if none */
+    /* setup phase times in ms (host clock for host phases, events for device) */
+    double t_mesh_ms, t_assembly_ms, t_upload_ms, t_gather_lu_ms, t_coarse_ms, t_eig_ms, t_graph_ms, t_total_ms;
+    long long kernel_launches;            /* launches made by this handle so far */
+} stokes_mg_stats;
+
+typedef struct stokes_mg* stokes_mg_t;
+
+/* Fill `o` with the defaults: GRADUAL, nu_p = nu_h = n_V = 1, 10 Arnoldi
+ * steps, seed 0, interval [0.1, 1.1], precision FP64, restart 30,
+ * maxit 1000, use_graph 1. */
+void stokes_mg_default_opts(stokes_mg_opts* o);
+
+/* Build the phMG hierarchy and everything a V-cycle needs (Sec. 3, Sec. 4).
+ *   coarse           host mesh M_L; the library refines it n_refine times
+ *                    (uniform R_u, Fig. 1) and, if barycentric_finest, splits
+ *                    the finest mesh by Alfeld (R_b; required for SV).
+ *   family, k        STOKES_TH / STOKES_SV and the velocity degree k.
+ *   opts             NULL = defaults.
+ *   nu_cell          host [cells of the finest mesh] viscosity per cell, or
+ *                    NULL for nu = 1 (coarse cells take their children's mean).
+ *   stream           device work of setup (gather, LU, eigen-estimate) runs here.
+ *   out              receives the handle.
+ * Errors: EINVAL (bad mesh/family/k), ESINGULAR (zero pivot; the stats
+ * name the patch), EOOM, ECUDA. */
+int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_finest,
+                    int family, int k, const stokes_mg_opts* opts,
+                    const double* nu_cell, void* stream, stokes_mg_t* out);
+
+/* z = B_MG r: one phMG V-cycle (Eq. 3.2 on the p-levels, Eq. 3.1 on the
+ * h-levels) from a zero initial guess, in the handle's precision.
+ * r_dev, z_dev: device, [nrhs][n_free(level 0)] FP64; nrhs >= 1 right-hand
+ * sides are processed one after another.  r_dev and z_dev may not alias. */
+int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, void* stream);
+
+/* Solve -nu Laplace(u) + grad p = f, div u = 0, u = g on the boundary with
+ * FGMRES(restart) right-preconditioned by the V-cycle (Sec. 4), stopped when
+ * ||b - K x||_2 <= tol ||b||_2.
+ *   f_nodal   device, [dim][n_vel_nodes]: nodal values of f; the load is
+ *             F = M f (exact mass-matrix product).
+ *   g_nodal   device, [dim][n_vel_nodes] or NULL (homogeneous); only
+ *             boundary nodes are read.
+ *   nu        constant viscosity > 0 (applied by scaling: the system with
+ *             nu = 1 is solved for (u, p/nu)); must be 1 if nu_cell was given.
+ *   u         device, [dim][n_vel_nodes] output (boundary values = g).
+ *   p         device, [n_pres_nodes] output, zero mean (int p = 0, Sec. 2).
+ *   iterations, final_relres   host outputs (may be NULL).
+ * Errors: ENOTCONVERGED (outputs hold the last iterate), ENONFINITE. */
+int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, double nu,
+                 double tol, double* u, double* p, int* iterations, double* final_relres,
+                 void* stream);
+
+/* Sizes and setup statistics (host struct). */
+int stokes_mg_info(stokes_mg_t h, stokes_mg_stats* st);
+
+/* Coordinates of the free DoFs of `level` (host outputs, caller-sized):
+ *   xyz   [n_free][dim] node coordinates,
+ *   comp  [n_free] 0..dim-1 velocity component, dim = pressure,
+ *   cell_center [n_free][dim] centroid of the owning cell for discontinuous
+ *         pressure DoFs (SV), zeros otherwise (may be NULL). */
+int stokes_mg_level_dofs(stokes_mg_t h, int level, double* xyz, int* comp, double* cell_center);
+
+/* Coordinates of the velocity nodes [n_vel_nodes][dim] and pressure nodes
+ * [n_pres_nodes][dim] of the finest level (full fields), plus the owning-cell
+ * centroid of each pressure node (SV; zeros for TH); host outputs. */
+int stokes_mg_nodes(stokes_mg_t h, double* vel_xyz, double* pres_xyz, double* pres_cell_center);
+
+/* ---- per-step entry points (each one step of the hot path) --------------- */
+
+/* which: 0 = K_l, 1 = P_l (coarse l+1 -> fine l), 2 = R_l = P_l^T.
+ * Query sizes with row_ptr = NULL: *n_rows, *n_cols, *nnz are returned.
+ * Otherwise copies the FP64 CSR into host arrays row_ptr[n_rows+1],
+ * col[nnz], val[nnz]. */
+int stokes_mg_get_csr(stokes_mg_t h, int level, int which, int* n_rows, int* n_cols,
+                      long long* nnz, int* row_ptr, int* col, double* val);
+
+/* Vanka-star patches of a level (Sec. 3.4, Fig. 5): with offsets = NULL
+ * returns *n_patches and *n_entries (= sum n_i); otherwise offsets[n+1] and
+ * free-DoF indices dofs[sum n_i] (sorted within each patch), host. */
+int stokes_mg_get_patches(stokes_mg_t h, int level, int* n_patches, long long* n_entries,
+                          int* offsets, int* dofs);
+
+/* a1: dense patch matrices K_i = I_i K I_i^T gathered on the device from the
+ * CSR of K_l (Eq. 3.4), written to host out[sum n_i^2], row-major per patch
+ * in patch order. */
+int stokes_mg_patch_matrices(stokes_mg_t h, int level, double* out, void* stream);
+
+/* a2: explicit inverses K_i^{-1} from the batched partial-pivot
+ * Gauss-Jordan kernel (FP64), host out[sum n_i^2], row-major per patch. */
+int stokes_mg_patch_inverses(stokes_mg_t h, int level, double* out, void* stream);
+
+/* a3: largest real Ritz value of `steps` Arnoldi steps on M_l^{-1} K_l from
+ * the device start vector v0_dev [n_free(level)] (FP64). */
+int stokes_mg_arnoldi_lmax(stokes_mg_t h, int level, const double* v0_dev, int steps,
+                           double* lmax, void* stream);
+
+/* a4: r = b - K_l x (device vectors, n_free(level)) in `precision`
+ * (STOKES_FP64 or STOKES_MIXED = FP32 values/accumulation; inputs and
+ * outputs are FP64 and rounded at the boundary). */
+int stokes_mg_residual(stokes_mg_t h, int level, const double* b, const double* x, double* r,
+                       int precision, void* stream);
+
+/* a5: z = M_l^{-1} r = sum_i I_i^T W_i K_i^{-1} I_i r (Eq. 3.4) with
+ * W_i = diag(1/multiplicity), in `precision` (device vectors). */
+int stokes_mg_asm(stokes_mg_t h, int level, const double* r, double* z, int precision, void* stream);
+
+/* a6: y = R_l x (restrict, x on level l, y on l+1) if dir = 0;
+ *     y += P_l x (prolong-and-add, x on l+1, y on l) if dir = 1. */
+int stokes_mg_transfer(stokes_mg_t h, int level, int dir, const double* x, double* y,
+                       int precision, void* stream);
+
+/* a7: coarsest-level solve of K_c x = r with the zero-mean pressure
+ * constraint (bordered FP64 LU inverse), device vectors. */
+int stokes_mg_coarse_solve(stokes_mg_t h, const double* r, double* x, void* stream);
+
+/* FGMRES on the free level-0 system K x = b (device b, x; x0 = 0). */
+int stokes_mg_fgmres(stokes_mg_t h, const double* b, double* x, double tol, int* iterations,
+                     double* final_relres, void* stream);
+
+/* Kernel timing for measurement: while enabled, the launches of kernel
+ * class `kind` (0 = patch apply, 1 = K SpMV, 2 = Gauss-Jordan, 3 = pull
+ * scatter, 4 = transfer SpMV) are bracketed with CUDA events on their stream
+ * and their total time accumulated (event pairs are read at the next
+ * stokes_prof_read).  enable = 0 stops. */
+int stokes_prof_enable(stokes_mg_t h, int kind, int enable);
+int stokes_prof_read(stokes_mg_t h, int kind, long long* launches, double* total_ms);
+
+/* Free everything the handle owns (NULL is accepted). */
+void stokes_mg_destroy(stokes_mg_t h);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* stokes_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOKES_MG_H */

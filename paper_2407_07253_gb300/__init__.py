@@ -1,0 +1,9 @@
+"""GB300-native monolithic ph-multigrid preconditioner for high-order
+Taylor-Hood / Scott-Vogelius Stokes (arXiv 2407.07253), used inside FGMRES.
+
+The computation lives in ``_lib/libstokes_mg.so`` (CUDA for sm_103a plus the
+host-side finite-element setup in C++), reached through the C ABI of
+``include/stokes_mg.h``; this package only marshals arguments.
+"""
+from ._binding import (FP64, HIER_DIRECT, HIER_EXPLICIT, HIER_GRADUAL, HIER_HMG, MIXED, SV, TH,  # noqa: F401
+                       StokesError, StokesMG, default_opts, lib, library_path)

@@ -1,0 +1,296 @@
+"""ctypes binding of libstokes_mg.so (include/stokes_mg.h): argument
+marshalling only.  Every numerical step runs inside the CUDA library; if the
+library is missing or fails to load this module raises instead of falling
+back to anything else."""
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_longlong, c_ulonglong, c_void_p
+
+import numpy as np
+
+TH, SV = 0, 1
+HIER_DIRECT, HIER_GRADUAL, HIER_EXPLICIT, HIER_HMG = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+ERRORS = {-1: "EINVAL", -2: "EOOM", -3: "ESINGULAR", -4: "ENOTCONVERGED", -5: "ENONFINITE",
+          -6: "ECUDA", -7: "EUNSUPPORTED"}
+PROF_PATCH, PROF_SPMV, PROF_GJ, PROF_PULL, PROF_TRANSFER = 0, 1, 2, 3, 4
+MAX_LEVELS = 16
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n_verts", c_int), ("n_cells", c_int),
+                ("verts", POINTER(c_double)), ("cells", POINTER(c_int))]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("hierarchy", c_int), ("n_schedule", c_int), ("schedule", c_int * 8),
+                ("nu_p", c_int), ("nu_h", c_int), ("n_V", c_int), ("eig_steps", c_int),
+                ("eig_seed", c_ulonglong), ("cheb_lo", c_double), ("cheb_hi", c_double),
+                ("lmax_override", c_double * 16), ("precision", c_int), ("restart", c_int),
+                ("maxit", c_int), ("use_graph", c_int), ("host_only", c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_levels", c_int), ("dim", c_int), ("family", c_int), ("k", c_int),
+                ("n_free", c_int * MAX_LEVELS), ("degree", c_int * MAX_LEVELS),
+                ("level_family", c_int * MAX_LEVELS), ("mesh_index", c_int * MAX_LEVELS),
+                ("is_p_level", c_int * MAX_LEVELS), ("nnz", c_longlong * MAX_LEVELS),
+                ("n_patches", c_int * MAX_LEVELS), ("max_patch", c_int * MAX_LEVELS),
+                ("patch_entries", c_longlong * MAX_LEVELS), ("lmax", c_double * MAX_LEVELS),
+                ("n_vel_nodes", c_int), ("n_pres_nodes", c_int), ("singular_patch", c_int),
+                ("t_mesh_ms", c_double), ("t_assembly_ms", c_double), ("t_upload_ms", c_double),
+                ("t_gather_lu_ms", c_double), ("t_coarse_ms", c_double), ("t_eig_ms", c_double),
+                ("t_graph_ms", c_double), ("t_total_ms", c_double), ("kernel_launches", c_longlong)]
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libstokes_mg.so")
+
+
+def lib():
+    """Load the CUDA library (building it first if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        from . import build
+        build.build()
+    L = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "stokes_mg_default_opts": (None, [POINTER(Opts)]),
+        "stokes_mg_setup": (c_int, [POINTER(Mesh), c_int, c_int, c_int, c_int, POINTER(Opts), P, P, POINTER(P)]),
+        "stokes_mg_vcycle": (c_int, [P, P, P, c_int, P]),
+        "stokes_solve": (c_int, [P, P, P, c_double, c_double, P, P, POINTER(c_int), POINTER(c_double), P]),
+        "stokes_mg_info": (c_int, [P, POINTER(Stats)]),
+        "stokes_mg_level_dofs": (c_int, [P, c_int, P, P, P]),
+        "stokes_mg_nodes": (c_int, [P, P, P, P]),
+        "stokes_mg_get_csr": (c_int, [P, c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_longlong), P, P, P]),
+        "stokes_mg_get_patches": (c_int, [P, c_int, POINTER(c_int), POINTER(c_longlong), P, P]),
+        "stokes_mg_patch_matrices": (c_int, [P, c_int, P, P]),
+        "stokes_mg_patch_inverses": (c_int, [P, c_int, P, P]),
+        "stokes_mg_arnoldi_lmax": (c_int, [P, c_int, P, c_int, POINTER(c_double), P]),
+        "stokes_mg_residual": (c_int, [P, c_int, P, P, P, c_int, P]),
+        "stokes_mg_asm": (c_int, [P, c_int, P, P, c_int, P]),
+        "stokes_mg_transfer": (c_int, [P, c_int, c_int, P, P, c_int, P]),
+        "stokes_mg_coarse_solve": (c_int, [P, P, P, P]),
+        "stokes_mg_fgmres": (c_int, [P, P, P, c_double, POINTER(c_int), POINTER(c_double), P]),
+        "stokes_prof_enable": (c_int, [P, c_int, c_int]),
+        "stokes_prof_read": (c_int, [P, c_int, POINTER(c_longlong), POINTER(c_double)]),
+        "stokes_mg_destroy": (None, [P]),
+        "stokes_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def check(rc):
+    if rc != 0:
+        raise StokesError(rc, lib().stokes_last_error().decode())
+    return rc
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib().stokes_mg_default_opts(byref(o))
+    for k, v in kw.items():
+        if k == "schedule":
+            o.n_schedule = len(v)
+            for i, x in enumerate(v):
+                o.schedule[i] = int(x)
+        elif k == "lmax_override":
+            for i, x in enumerate(v):
+                o.lmax_override[i] = float(x or 0.0)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class StokesMG:
+    """Handle on a phMG hierarchy built by stokes_mg_setup."""
+
+    def __init__(self, verts, cells, n_refine, family, k, barycentric=False, nu_cell=None,
+                 stream=None, **opts):
+        verts = np.ascontiguousarray(verts, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        self._mesh = Mesh(verts.shape[1], verts.shape[0], cells.shape[0],
+                          verts.ctypes.data_as(POINTER(c_double)), cells.ctypes.data_as(POINTER(c_int)))
+        self._keep = (verts, cells)
+        self.opts = default_opts(**opts)
+        nu = None
+        if nu_cell is not None:
+            nu = np.ascontiguousarray(nu_cell, dtype=np.float64)
+            self._keep = self._keep + (nu,)
+        self.h = c_void_p()
+        self.stream = stream
+        check(lib().stokes_mg_setup(byref(self._mesh), int(n_refine), int(bool(barycentric)), int(family), int(k),
+                                    byref(self.opts), None if nu is None else nu.ctypes.data_as(c_void_p),
+                                    _stream(stream), byref(self.h)))
+        self.dim = verts.shape[1]
+
+    # ---- queries
+    def info(self):
+        s = Stats()
+        check(lib().stokes_mg_info(self.h, byref(s)))
+        nl = s.n_levels
+        out = {}
+        for name, _ in Stats._fields_:
+            v = getattr(s, name)
+            out[name] = list(v)[:nl] if isinstance(v, ctypes.Array) else v
+        return out
+
+    def level_dofs(self, level):
+        n = self.info()["n_free"][level]
+        xyz = np.zeros((n, self.dim))
+        comp = np.zeros(n, dtype=np.int32)
+        cc = np.zeros((n, self.dim))
+        check(lib().stokes_mg_level_dofs(self.h, level, xyz.ctypes.data_as(c_void_p), comp.ctypes.data_as(c_void_p),
+                                         cc.ctypes.data_as(c_void_p)))
+        return xyz, comp, cc
+
+    def nodes(self):
+        i = self.info()
+        vx = np.zeros((i["n_vel_nodes"], self.dim))
+        px = np.zeros((i["n_pres_nodes"], self.dim))
+        pc = np.zeros((i["n_pres_nodes"], self.dim))
+        check(lib().stokes_mg_nodes(self.h, vx.ctypes.data_as(c_void_p), px.ctypes.data_as(c_void_p),
+                                    pc.ctypes.data_as(c_void_p)))
+        return vx, px, pc
+
+    def get_csr(self, level, which=0):
+        nr, nc, nnz = c_int(), c_int(), c_longlong()
+        check(lib().stokes_mg_get_csr(self.h, level, which, byref(nr), byref(nc), byref(nnz), None, None, None))
+        rp = np.zeros(nr.value + 1, dtype=np.int32)
+        ci = np.zeros(nnz.value, dtype=np.int32)
+        v = np.zeros(nnz.value)
+        check(lib().stokes_mg_get_csr(self.h, level, which, byref(nr), byref(nc), byref(nnz),
+                                      rp.ctypes.data_as(c_void_p), ci.ctypes.data_as(c_void_p), v.ctypes.data_as(c_void_p)))
+        import scipy.sparse as sp
+        return sp.csr_matrix((v, ci, rp), shape=(nr.value, nc.value))
+
+    def patches(self, level):
+        npch, nent = c_int(), c_longlong()
+        check(lib().stokes_mg_get_patches(self.h, level, byref(npch), byref(nent), None, None))
+        off = np.zeros(npch.value + 1, dtype=np.int32)
+        dofs = np.zeros(nent.value, dtype=np.int32)
+        check(lib().stokes_mg_get_patches(self.h, level, byref(npch), byref(nent), off.ctypes.data_as(c_void_p),
+                                          dofs.ctypes.data_as(c_void_p)))
+        return off, dofs
+
+    # ---- device work (torch CUDA tensors, float64)
+    def vcycle(self, r, out=None):
+        import torch
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        z = torch.empty_like(r) if out is None else out
+        check(lib().stokes_mg_vcycle(self.h, _ptr(r.contiguous()), _ptr(z), nrhs, _stream(self.stream)))
+        return z
+
+    def solve(self, f, g=None, nu=1.0, tol=1e-8, u=None, p=None, raise_on_nonconv=True):
+        import torch
+        i = self.info()
+        u = torch.empty(self.dim * i["n_vel_nodes"], dtype=torch.float64, device=f.device) if u is None else u
+        p = torch.empty(i["n_pres_nodes"], dtype=torch.float64, device=f.device) if p is None else p
+        its, rel = c_int(), c_double()
+        rc = lib().stokes_solve(self.h, _ptr(f.contiguous()), _ptr(g), float(nu), float(tol), _ptr(u), _ptr(p),
+                                byref(its), byref(rel), _stream(self.stream))
+        if rc != 0 and (raise_on_nonconv or rc != -4):
+            check(rc)
+        return u, p, its.value, rel.value
+
+    def fgmres(self, b, tol=1e-8):
+        import torch
+        x = torch.empty_like(b)
+        its, rel = c_int(), c_double()
+        check(lib().stokes_mg_fgmres(self.h, _ptr(b), _ptr(x), float(tol), byref(its), byref(rel), _stream(self.stream)))
+        return x, its.value, rel.value
+
+    def patch_matrices(self, level):
+        n = self.info()["patch_entries"][level]
+        out = np.zeros(n)
+        check(lib().stokes_mg_patch_matrices(self.h, level, out.ctypes.data_as(c_void_p), _stream(self.stream)))
+        return out
+
+    def patch_inverses(self, level):
+        n = self.info()["patch_entries"][level]
+        out = np.zeros(n)
+        check(lib().stokes_mg_patch_inverses(self.h, level, out.ctypes.data_as(c_void_p), _stream(self.stream)))
+        return out
+
+    def arnoldi_lmax(self, level, v0, steps=10):
+        out = c_double()
+        check(lib().stokes_mg_arnoldi_lmax(self.h, level, _ptr(v0), steps, byref(out), _stream(self.stream)))
+        return out.value
+
+    def residual(self, level, b, x, precision=FP64):
+        import torch
+        r = torch.empty_like(b)
+        check(lib().stokes_mg_residual(self.h, level, _ptr(b), _ptr(x), _ptr(r), precision, _stream(self.stream)))
+        return r
+
+    def asm(self, level, r, precision=FP64):
+        import torch
+        z = torch.empty_like(r)
+        check(lib().stokes_mg_asm(self.h, level, _ptr(r), _ptr(z), precision, _stream(self.stream)))
+        return z
+
+    def transfer(self, level, direction, x, y, precision=FP64):
+        check(lib().stokes_mg_transfer(self.h, level, direction, _ptr(x), _ptr(y), precision, _stream(self.stream)))
+        return y
+
+    def coarse_solve(self, r):
+        import torch
+        x = torch.empty_like(r)
+        check(lib().stokes_mg_coarse_solve(self.h, _ptr(r), _ptr(x), _stream(self.stream)))
+        return x
+
+    def prof_enable(self, kind, on=True):
+        check(lib().stokes_prof_enable(self.h, kind, int(on)))
+
+    def prof_read(self, kind):
+        n, ms = c_longlong(), c_double()
+        check(lib().stokes_prof_read(self.h, kind, byref(n), byref(ms)))
+        return n.value, ms.value
+
+    def close(self):
+        if self.h:
+            lib().stokes_mg_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1004 @@
+// Host-side finite-element setup; see fem.hpp.
+#include "fem.hpp"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <stdexcept>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+
+namespace sfem {
+
+int num_threads() {
+    static int n = [] {
+        const char* e = std::getenv("STOKES_HOST_THREADS");
+        int v = e ? std::atoi(e) : (int)std::thread::hardware_concurrency();
+        return std::max(1, std::min(v, 64));
+    }();
+    return n;
+}
+
+// Static-chunk parallel loop over [0, n).
+static void parallel_for(int n, const std::function<void(int, int, int)>& body) {
+    int T = std::min(num_threads(), std::max(1, n / 64));
+    if (T <= 1) { body(0, n, 0); return; }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) {
+        int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
+        th.emplace_back([=, &body] { body(lo, hi, t); });
+    }
+    for (auto& x : th) x.join();
+}
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- meshes --
+static inline uint64_t edge_key(int a, int b) {
+    if (a > b) std::swap(a, b);
+    return ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+}
+
+Mesh refine_uniform(const Mesh& m, std::vector<int>& parent) {
+    const int d = m.d, nvpc = d + 1;
+    Mesh r;
+    r.d = d;
+    std::unordered_map<uint64_t, int> mid;
+    mid.reserve((size_t)m.nc * 4);
+    r.X = m.X;
+    int nv = m.nv;
+    auto midpoint = [&](int a, int b) {
+        uint64_t key = edge_key(a, b);
+        auto it = mid.find(key);
+        if (it != mid.end()) return it->second;
+        for (int c = 0; c < d; ++c) r.X.push_back(0.5 * (m.X[(size_t)a * d + c] + m.X[(size_t)b * d + c]));
+        mid.emplace(key, nv);
+        return nv++;
+    };
+    const int nkids = d == 2 ? 4 : 8;
+    r.C.reserve((size_t)m.nc * nkids * nvpc);
+    parent.assign((size_t)m.nc * nkids, 0);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        if (d == 2) {
+            int m01 = midpoint(v[0], v[1]), m12 = midpoint(v[1], v[2]), m20 = midpoint(v[2], v[0]);
+            int kids[4][3] = {{v[0], m01, m20}, {m01, v[1], m12}, {m20, m12, v[2]}, {m12, m20, m01}};
+            for (auto& k : kids) r.C.insert(r.C.end(), k, k + 3);
+        } else {
+            int a = v[0], b = v[1], c = v[2], w = v[3];
+            int ab = midpoint(a, b), ac = midpoint(a, c), aw = midpoint(a, w);
+            int bc = midpoint(b, c), bw = midpoint(b, w), cw = midpoint(c, w);
+            // Bey's regular subdivision: four corner tetrahedra and the inner
+            // octahedron cut along the (ac, bw) diagonal.
+            int kids[8][4] = {{a, ab, ac, aw}, {ab, b, bc, bw}, {ac, bc, c, cw}, {aw, bw, cw, w},
+                              {ab, ac, aw, bw}, {ab, ac, bc, bw}, {ac, aw, bw, cw}, {ac, bc, bw, cw}};
+            for (auto& k : kids) r.C.insert(r.C.end(), k, k + 4);
+        }
+        for (int i = 0; i < nkids; ++i) parent[(size_t)e * nkids + i] = e;
+    }
+    r.nv = nv;
+    r.nc = m.nc * nkids;
+    return r;
+}
+
+Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent) {
+    const int d = m.d, nvpc = d + 1;
+    Mesh r;
+    r.d = d;
+    r.X = m.X;
+    r.X.reserve((size_t)(m.nv + m.nc) * d);
+    int nv = m.nv;
+    parent.assign((size_t)m.nc * nvpc, 0);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        for (int c = 0; c < d; ++c) {
+            double s = 0;
+            for (int i = 0; i < nvpc; ++i) s += m.X[(size_t)v[i] * d + c];
+            r.X.push_back(s / nvpc);
+        }
+        int g = nv++;
+        for (int i = 0; i < nvpc; ++i) {       // child i: vertex i replaced by the barycenter
+            for (int j = 0; j < nvpc; ++j) r.C.push_back(j == i ? g : v[j]);
+            parent[(size_t)e * nvpc + i] = e;
+        }
+    }
+    r.nv = nv;
+    r.nc = m.nc * nvpc;
+    return r;
+}
+
+// ------------------------------------------------------ reference element --
+static double factorial(int n) {
+    double f = 1;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+void RefElement::init(int d_, int k_) {
+    d = d_;
+    k = k_;
+    alpha.clear();
+    mono.clear();
+    if (d == 2) {
+        for (int j = 0; j <= k; ++j)
+            for (int i = 0; i <= k - j; ++i) alpha.push_back({k - i - j, i, j, 0});
+        for (int t = 0; t <= k; ++t)
+            for (int b = 0; b <= t; ++b) mono.push_back({t - b, b, 0});
+    } else {
+        for (int l = 0; l <= k; ++l)
+            for (int j = 0; j <= k - l; ++j)
+                for (int i = 0; i <= k - l - j; ++i) alpha.push_back({k - i - j - l, i, j, l});
+        for (int t = 0; t <= k; ++t)
+            for (int c = 0; c <= t; ++c)
+                for (int b = 0; b <= t - c; ++b) mono.push_back({t - b - c, b, c});
+    }
+    nb = (int)alpha.size();
+    nm = (int)mono.size();
+    if (nb != nm) throw std::runtime_error("reference element: node/monomial count mismatch");
+    // Vandermonde V[node][m] = xi^mono_m, inverted by Gauss-Jordan in long double
+    const int n = nb;
+    std::vector<long double> A((size_t)n * 2 * n, 0.0L);
+    for (int i = 0; i < n; ++i) {
+        long double xi[3] = {0, 0, 0};
+        for (int c = 0; c < d; ++c) xi[c] = (long double)alpha[i][c + 1] / (k > 0 ? k : 1);
+        for (int m = 0; m < n; ++m) {
+            long double v = 1;
+            for (int c = 0; c < d; ++c)
+                for (int p = 0; p < mono[m][c]; ++p) v *= xi[c];
+            A[(size_t)i * 2 * n + m] = v;
+        }
+        A[(size_t)i * 2 * n + n + i] = 1;
+    }
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabsl(A[(size_t)r * 2 * n + c]) > fabsl(A[(size_t)p * 2 * n + c])) p = r;
+        if (p != c)
+            for (int j = 0; j < 2 * n; ++j) std::swap(A[(size_t)p * 2 * n + j], A[(size_t)c * 2 * n + j]);
+        long double piv = A[(size_t)c * 2 * n + c];
+        if (piv == 0) throw std::runtime_error("singular Vandermonde");
+        for (int j = 0; j < 2 * n; ++j) A[(size_t)c * 2 * n + j] /= piv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            long double f = A[(size_t)r * 2 * n + c];
+            if (f == 0) continue;
+            for (int j = 0; j < 2 * n; ++j) A[(size_t)r * 2 * n + j] -= f * A[(size_t)c * 2 * n + j];
+        }
+    }
+    // Vinv[m][i] -> coef[i][m]
+    coef.assign((size_t)n * n, 0.0);
+    for (int m = 0; m < n; ++m)
+        for (int i = 0; i < n; ++i) coef[(size_t)i * n + m] = (double)A[(size_t)m * 2 * n + n + i];
+}
+
+void RefElement::eval(const double* xi, double* out) const {
+    double mv[320];   // up to P_10 in 3D (286 monomials)
+    for (int m = 0; m < nm; ++m) {
+        double v = 1;
+        for (int c = 0; c < d; ++c)
+            for (int p = 0; p < mono[m][c]; ++p) v *= xi[c];
+        mv[m] = v;
+    }
+    for (int i = 0; i < nb; ++i) {
+        double s = 0;
+        for (int m = 0; m < nm; ++m) s += coef[(size_t)i * nm + m] * mv[m];
+        out[i] = s;
+    }
+}
+
+// polynomial as (exponent, coefficient) list
+struct Poly {
+    std::vector<std::array<int, 3>> e;
+    std::vector<double> c;
+};
+
+static Poly basis_poly(const RefElement& re, int i) {
+    Poly p;
+    for (int m = 0; m < re.nm; ++m) {
+        p.e.push_back(re.mono[m]);
+        p.c.push_back(re.coef[(size_t)i * re.nm + m]);
+    }
+    return p;
+}
+
+static Poly deriv(const Poly& p, int a) {
+    Poly q;
+    for (size_t t = 0; t < p.e.size(); ++t) {
+        if (p.e[t][a] == 0) continue;
+        auto e = p.e[t];
+        double f = e[a];
+        e[a] -= 1;
+        q.e.push_back(e);
+        q.c.push_back(p.c[t] * f);
+    }
+    return q;
+}
+
+// exact integral of x^a y^b z^c over the reference d-simplex
+static double mono_integral(int d, int a, int b, int c) {
+    return factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + d);
+}
+
+static double integrate_product(int d, const Poly& p, const Poly& q) {
+    double s = 0;
+    for (size_t i = 0; i < p.e.size(); ++i) {
+        if (p.c[i] == 0) continue;
+        for (size_t j = 0; j < q.e.size(); ++j)
+            s += p.c[i] * q.c[j] *
+                 mono_integral(d, p.e[i][0] + q.e[j][0], p.e[i][1] + q.e[j][1], p.e[i][2] + q.e[j][2]);
+    }
+    return s;
+}
+
+void RefTensors::init(const RefElement& v, const RefElement& q) {
+    d = v.d;
+    nb = v.nb;
+    nq = q.nb;
+    std::vector<Poly> phi(nb), psi(nq);
+    std::vector<std::vector<Poly>> dphi(d, std::vector<Poly>(nb));
+    for (int i = 0; i < nb; ++i) {
+        phi[i] = basis_poly(v, i);
+        for (int a = 0; a < d; ++a) dphi[a][i] = deriv(phi[i], a);
+    }
+    for (int p = 0; p < nq; ++p) psi[p] = basis_poly(q, p);
+    S.assign((size_t)d * d * nb * nb, 0.0);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b)
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j)
+                    S[(((size_t)a * d + b) * nb + i) * nb + j] = integrate_product(d, dphi[a][i], dphi[b][j]);
+    Cq.assign((size_t)d * nq * nb, 0.0);
+    for (int a = 0; a < d; ++a)
+        for (int p = 0; p < nq; ++p)
+            for (int j = 0; j < nb; ++j)
+                Cq[((size_t)a * nq + p) * nb + j] = integrate_product(d, psi[p], dphi[a][j]);
+    M.assign((size_t)nb * nb, 0.0);
+    for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) M[(size_t)i * nb + j] = integrate_product(d, phi[i], phi[j]);
+    qint.assign(nq, 0.0);
+    Poly one;
+    one.e.push_back({0, 0, 0});
+    one.c.push_back(1.0);
+    for (int p = 0; p < nq; ++p) qint[p] = integrate_product(d, psi[p], one);
+}
+
+CSR transpose(const CSR& a) {
+    CSR t;
+    t.nr = a.ncol;
+    t.ncol = a.nr;
+    t.rp.assign(t.nr + 1, 0);
+    for (int c : a.ci) t.rp[c + 1]++;
+    for (int i = 0; i < t.nr; ++i) t.rp[i + 1] += t.rp[i];
+    t.ci.resize(a.ci.size());
+    t.v.resize(a.v.size());
+    std::vector<int> fill(t.rp.begin(), t.rp.end() - 1);
+    for (int r = 0; r < a.nr; ++r)
+        for (int p = a.rp[r]; p < a.rp[r + 1]; ++p) {
+            int q = fill[a.ci[p]]++;
+            t.ci[q] = r;
+            t.v[q] = a.v[p];
+        }
+    return t;
+}
+
+// ------------------------------------------------------------------ spaces --
+struct Topology {
+    int d = 0;
+    std::unordered_map<uint64_t, int> edge_id;
+    std::unordered_map<uint64_t, int> face_id;     // 3D only
+    std::vector<unsigned char> bvert;
+    std::unordered_set<uint64_t> bedge, bface;
+    std::vector<int> v2c_off, v2c;                  // vertex -> cells
+};
+
+static inline uint64_t face_key(int a, int b, int c, int nv) {
+    int t[3] = {a, b, c};
+    std::sort(t, t + 3);
+    return ((uint64_t)t[0] * (uint64_t)nv + (uint64_t)t[1]) * (uint64_t)nv + (uint64_t)t[2];
+}
+
+static void build_topology(const Mesh& m, Topology& T) {
+    const int d = m.d, nvpc = d + 1;
+    T.d = d;
+    T.edge_id.reserve((size_t)m.nc * 3);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        for (int i = 0; i < nvpc; ++i)
+            for (int j = i + 1; j < nvpc; ++j) {
+                uint64_t key = edge_key(v[i], v[j]);
+                if (!T.edge_id.count(key)) {
+                    int id = (int)T.edge_id.size();
+                    T.edge_id.emplace(key, id);
+                }
+            }
+        if (d == 3)
+            for (int i = 0; i < 4; ++i) {
+                int f[3], t = 0;
+                for (int j = 0; j < 4; ++j)
+                    if (j != i) f[t++] = v[j];
+                uint64_t key = face_key(f[0], f[1], f[2], m.nv);
+                if (!T.face_id.count(key)) {
+                    int id = (int)T.face_id.size();
+                    T.face_id.emplace(key, id);
+                }
+            }
+    }
+    // boundary facets: facets owned by one cell
+    std::unordered_map<uint64_t, int> cnt;
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        for (int i = 0; i < nvpc; ++i) {
+            int f[3], t = 0;
+            for (int j = 0; j < nvpc; ++j)
+                if (j != i) f[t++] = v[j];
+            uint64_t key = d == 2 ? edge_key(f[0], f[1]) : face_key(f[0], f[1], f[2], m.nv);
+            cnt[key]++;
+        }
+    }
+    T.bvert.assign(m.nv, 0);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        for (int i = 0; i < nvpc; ++i) {
+            int f[3], t = 0;
+            for (int j = 0; j < nvpc; ++j)
+                if (j != i) f[t++] = v[j];
+            uint64_t key = d == 2 ? edge_key(f[0], f[1]) : face_key(f[0], f[1], f[2], m.nv);
+            if (cnt[key] != 1) continue;
+            for (int j = 0; j < d; ++j) T.bvert[f[j]] = 1;
+            if (d == 2) {
+                T.bedge.insert(key);
+            } else {
+                T.bface.insert(key);
+                T.bedge.insert(edge_key(f[0], f[1]));
+                T.bedge.insert(edge_key(f[0], f[2]));
+                T.bedge.insert(edge_key(f[1], f[2]));
+            }
+        }
+    }
+    T.v2c_off.assign(m.nv + 1, 0);
+    for (int x : m.C) T.v2c_off[x + 1]++;
+    for (int i = 0; i < m.nv; ++i) T.v2c_off[i + 1] += T.v2c_off[i];
+    T.v2c.resize(m.C.size());
+    std::vector<int> fill(T.v2c_off.begin(), T.v2c_off.end() - 1);
+    for (int e = 0; e < m.nc; ++e)
+        for (int i = 0; i < nvpc; ++i) T.v2c[fill[m.C[(size_t)e * nvpc + i]]++] = e;
+}
+
+static int binom(int n, int r) {
+    if (r < 0 || r > n) return 0;
+    long long b = 1;
+    for (int i = 1; i <= r; ++i) b = b * (n - r + i) / i;
+    return (int)b;
+}
+
+// Continuous space: a node on cell e with multi-index alpha is owned by the
+// entity spanned by the vertices with alpha_i > 0; inside that entity it is
+// identified by the alpha values listed in increasing global vertex order
+// (a composition of k into |S| positive parts).  Nodes are finally
+// renumbered in order of first appearance over the cells (locality).
+static void build_space(const Mesh& m, const Topology& T, const RefElement& re, bool continuous, Space& S) {
+    const int d = m.d, nvpc = d + 1, nb = re.nb, k = re.k;
+    S.d = d;
+    S.k = k;
+    S.nb = nb;
+    S.continuous = continuous;
+    S.cell_nodes.assign((size_t)m.nc * nb, -1);
+    if (!continuous) {
+        S.n = m.nc * nb;
+        S.X.resize((size_t)S.n * d);
+        S.boundary.assign(S.n, 0);
+        S.support.resize(S.n);
+        S.owner_cell.resize(S.n);
+        parallel_for(m.nc, [&](int lo, int hi, int) {
+            for (int e = lo; e < hi; ++e) {
+                const int* v = &m.C[(size_t)e * nvpc];
+                std::array<int, 4> sup = {-1, -1, -1, -1};
+                for (int i = 0; i < nvpc; ++i) sup[i] = v[i];
+                std::sort(sup.begin(), sup.begin() + nvpc);
+                for (int l = 0; l < nb; ++l) {
+                    int id = e * nb + l;
+                    S.cell_nodes[(size_t)e * nb + l] = id;
+                    for (int c = 0; c < d; ++c) {
+                        double x = 0;
+                        for (int i = 0; i < nvpc; ++i) x += re.alpha[l][i] * m.X[(size_t)v[i] * d + c];
+                        S.X[(size_t)id * d + c] = x / (k > 0 ? k : 1);
+                    }
+                    S.support[id] = sup;
+                    S.owner_cell[id] = e;
+                }
+            }
+        });
+        return;
+    }
+    // rank tables for compositions of k into m positive parts
+    std::vector<std::map<long long, int>> rank(5);
+    std::vector<int> nint(5, 0);
+    for (int mm = 1; mm <= nvpc; ++mm) {
+        nint[mm] = binom(k - 1, mm - 1);
+        std::vector<int> part(mm, 1);
+        // enumerate all compositions by recursion over a simple odometer
+        std::function<void(int, int)> rec = [&](int pos, int left) {
+            if (pos == mm - 1) {
+                if (left >= 1) {
+                    part[pos] = left;
+                    long long code = 0;
+                    for (int t = 0; t < mm; ++t) code = code * (k + 1) + part[t];
+                    int r = (int)rank[mm].size();
+                    rank[mm][code] = r;
+                }
+                return;
+            }
+            for (int v = 1; v <= left - (mm - 1 - pos); ++v) {
+                part[pos] = v;
+                rec(pos + 1, left - v);
+            }
+        };
+        if (k >= mm) rec(0, k);
+    }
+    const long long ne = (long long)T.edge_id.size(), nf = (long long)T.face_id.size();
+    long long base[5] = {0, 0, 0, 0, 0};
+    base[1] = 0;
+    base[2] = base[1] + (long long)m.nv * nint[1];
+    base[3] = base[2] + ne * nint[2];
+    if (d == 2) {
+        base[4] = 0;
+    } else {
+        base[4] = base[3] + nf * nint[3];
+    }
+    long long ntmp = d == 2 ? base[3] + (long long)m.nc * nint[3] : base[4] + (long long)m.nc * nint[4];
+    std::vector<int> tmp((size_t)m.nc * nb);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        for (int l = 0; l < nb; ++l) {
+            int sv[4], sa[4], mm = 0;
+            for (int i = 0; i < nvpc; ++i)
+                if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sa[mm] = re.alpha[l][i]; ++mm; }
+            for (int a = 1; a < mm; ++a)          // sort by global vertex id
+                for (int b = a; b > 0 && sv[b - 1] > sv[b]; --b) { std::swap(sv[b - 1], sv[b]); std::swap(sa[b - 1], sa[b]); }
+            long long code = 0;
+            for (int t = 0; t < mm; ++t) code = code * (k + 1) + sa[t];
+            int r = rank[mm].at(code);
+            long long eid;
+            if (mm == 1) eid = sv[0];
+            else if (mm == 2) eid = T.edge_id.at(edge_key(sv[0], sv[1]));
+            else if (mm == 3 && d == 3) eid = T.face_id.at(face_key(sv[0], sv[1], sv[2], m.nv));
+            else eid = e;   // cell interior
+            tmp[(size_t)e * nb + l] = (int)(base[mm] + eid * nint[mm] + r);
+        }
+    }
+    // renumber by first appearance
+    std::vector<int> newid(ntmp, -1);
+    int n = 0;
+    for (size_t t = 0; t < tmp.size(); ++t) {
+        int& x = newid[tmp[t]];
+        if (x < 0) x = n++;
+        S.cell_nodes[t] = x;
+    }
+    S.n = n;
+    S.X.assign((size_t)n * d, 0.0);
+    S.boundary.assign(n, 0);
+    S.support.assign(n, {-1, -1, -1, -1});
+    S.owner_cell.assign(n, -1);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* v = &m.C[(size_t)e * nvpc];
+        for (int l = 0; l < nb; ++l) {
+            int id = S.cell_nodes[(size_t)e * nb + l];
+            if (S.owner_cell[id] >= 0) continue;
+            S.owner_cell[id] = e;
+            for (int c = 0; c < d; ++c) {
+                double x = 0;
+                for (int i = 0; i < nvpc; ++i) x += re.alpha[l][i] * m.X[(size_t)v[i] * d + c];
+                S.X[(size_t)id * d + c] = x / k;
+            }
+            int sv[4], mm = 0;
+            for (int i = 0; i < nvpc; ++i)
+                if (re.alpha[l][i] > 0) sv[mm++] = v[i];
+            std::sort(sv, sv + mm);
+            for (int t = 0; t < mm; ++t) S.support[id][t] = sv[t];
+            bool b;
+            if (mm == 1) b = T.bvert[sv[0]];
+            else if (mm == 2) b = T.bedge.count(edge_key(sv[0], sv[1])) > 0;
+            else if (mm == 3 && d == 3) b = T.bface.count(face_key(sv[0], sv[1], sv[2], m.nv)) > 0;
+            else b = false;
+            S.boundary[id] = b;
+        }
+    }
+}
+
+// --------------------------------------------------------------- assembly --
+struct CellGeom {
+    double detabs;
+    double Jinv[9];   // [a][c] = d xi_a / d x_c
+};
+
+static CellGeom cell_geom(const Mesh& m, int e) {
+    const int d = m.d;
+    const int* v = &m.C[(size_t)e * (d + 1)];
+    double J[9];
+    for (int c = 0; c < d; ++c)
+        for (int a = 0; a < d; ++a) J[c * d + a] = m.X[(size_t)v[a + 1] * d + c] - m.X[(size_t)v[0] * d + c];
+    CellGeom g;
+    if (d == 2) {
+        double det = J[0] * J[3] - J[1] * J[2];
+        g.detabs = std::fabs(det);
+        // Jinv[a][c]
+        g.Jinv[0] = J[3] / det;  g.Jinv[1] = -J[1] / det;
+        g.Jinv[2] = -J[2] / det; g.Jinv[3] = J[0] / det;
+    } else {
+        double a = J[0], b = J[1], c = J[2], dd = J[3], e2 = J[4], f = J[5], gg = J[6], h = J[7], i = J[8];
+        double A = e2 * i - f * h, B = -(dd * i - f * gg), Cc = dd * h - e2 * gg;
+        double det = a * A + b * B + c * Cc;
+        g.detabs = std::fabs(det);
+        double inv[9] = {A, -(b * i - c * h), b * f - c * e2,
+                         B, a * i - c * gg, -(a * f - c * dd),
+                         Cc, -(a * h - b * gg), a * e2 - b * dd};
+        for (int t = 0; t < 9; ++t) g.Jinv[t] = inv[t] / det;
+    }
+    return g;
+}
+
+// node -> (cell, local index) adjacency
+static void node_cells(const Space& S, int nc, std::vector<int>& off, std::vector<int>& adj) {
+    off.assign(S.n + 1, 0);
+    for (int x : S.cell_nodes) off[x + 1]++;
+    for (int i = 0; i < S.n; ++i) off[i + 1] += off[i];
+    adj.resize(S.cell_nodes.size());
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int e = 0; e < nc; ++e)
+        for (int l = 0; l < S.nb; ++l) adj[fill[S.cell_nodes[(size_t)e * S.nb + l]]++] = e * S.nb + l;
+}
+
+static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const std::vector<double>& nu) {
+    const int d = m.d, nb = L.V.nb, nq = L.Q.nb, nc = m.nc;
+    const Space &V = L.V, &Q = L.Q;
+    // element matrices: stiffness (scaled by nu_e) and divergence coupling
+    std::vector<double> Se((size_t)nc * nb * nb), Ce((size_t)nc * nq * nb * d), Me((size_t)nc * nb * nb);
+    std::vector<double> qe((size_t)nc * nq);
+    parallel_for(nc, [&](int lo, int hi, int) {
+        for (int e = lo; e < hi; ++e) {
+            CellGeom g = cell_geom(m, e);
+            double G[9];
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) {
+                    double s = 0;
+                    for (int c = 0; c < d; ++c) s += g.Jinv[a * d + c] * g.Jinv[b * d + c];
+                    G[a * d + b] = s;
+                }
+            double w = g.detabs * (nu.empty() ? 1.0 : nu[e]);
+            for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j) {
+                    double s = 0;
+                    for (int a = 0; a < d; ++a)
+                        for (int b = 0; b < d; ++b) s += G[a * d + b] * RT.S[(((size_t)a * d + b) * nb + i) * nb + j];
+                    Se[((size_t)e * nb + i) * nb + j] = w * s;
+                    Me[((size_t)e * nb + i) * nb + j] = g.detabs * RT.M[(size_t)i * nb + j];
+                }
+            // C[p][j][c] = -|det J| sum_a Jinv[a][c] Cq[a][p][j]
+            for (int p = 0; p < nq; ++p) {
+                qe[(size_t)e * nq + p] = g.detabs * RT.qint[p];
+                for (int j = 0; j < nb; ++j)
+                    for (int c = 0; c < d; ++c) {
+                        double s = 0;
+                        for (int a = 0; a < d; ++a) s += g.Jinv[a * d + c] * RT.Cq[((size_t)a * nq + p) * nb + j];
+                        Ce[(((size_t)e * nq + p) * nb + j) * d + c] = -g.detabs * s;
+                    }
+            }
+        }
+    });
+    // free numbering
+    L.vfree.assign(V.n, -1);
+    int nVf = 0;
+    for (int i = 0; i < V.n; ++i)
+        if (!V.boundary[i]) L.vfree[i] = nVf++;
+    L.nVf = nVf;
+    L.nQ = Q.n;
+    L.n_free = d * nVf + Q.n;
+    std::vector<int> voff, vadj, qoff, qadj;
+    node_cells(V, nc, voff, vadj);
+    node_cells(Q, nc, qoff, qadj);
+    // pressure integrals
+    L.pint.assign(Q.n, 0.0);
+    for (int e = 0; e < nc; ++e)
+        for (int p = 0; p < nq; ++p) L.pint[Q.cell_nodes[(size_t)e * nq + p]] += qe[(size_t)e * nq + p];
+    // --- row patterns, per velocity node and per pressure node
+    // velocity node i: free velocity neighbours (sorted by free index),
+    // Dirichlet velocity neighbours, pressure neighbours
+    const int T = num_threads();
+    std::vector<std::vector<int>> vnb(V.n), vdn(V.n), vqn(V.n), qvn(Q.n), qdn(Q.n);
+    std::vector<std::vector<int>> stampV(T, std::vector<int>(V.n, -1)), stampQ(T, std::vector<int>(Q.n, -1));
+    parallel_for(V.n, [&](int lo, int hi, int t) {
+        auto& sv = stampV[t];
+        auto& sq = stampQ[t];
+        for (int i = lo; i < hi; ++i) {
+            for (int a = voff[i]; a < voff[i + 1]; ++a) {
+                int e = vadj[a] / nb;
+                for (int l = 0; l < nb; ++l) {
+                    int j = V.cell_nodes[(size_t)e * nb + l];
+                    if (sv[j] == i) continue;
+                    sv[j] = i;
+                    if (L.vfree[j] >= 0) vnb[i].push_back(j);
+                    else vdn[i].push_back(j);
+                }
+                for (int l = 0; l < nq; ++l) {
+                    int q = Q.cell_nodes[(size_t)e * nq + l];
+                    if (sq[q] == i) continue;
+                    sq[q] = i;
+                    vqn[i].push_back(q);
+                }
+            }
+            std::sort(vnb[i].begin(), vnb[i].end(), [&](int a, int b) { return L.vfree[a] < L.vfree[b]; });
+            std::sort(vdn[i].begin(), vdn[i].end());
+            std::sort(vqn[i].begin(), vqn[i].end());
+        }
+    });
+    for (auto& s : stampV) std::fill(s.begin(), s.end(), -1);
+    parallel_for(Q.n, [&](int lo, int hi, int t) {
+        auto& sv = stampV[t];
+        for (int q = lo; q < hi; ++q) {
+            for (int a = qoff[q]; a < qoff[q + 1]; ++a) {
+                int e = qadj[a] / nq;
+                for (int l = 0; l < nb; ++l) {
+                    int j = V.cell_nodes[(size_t)e * nb + l];
+                    if (sv[j] == q) continue;
+                    sv[j] = q;
+                    if (L.vfree[j] >= 0) qvn[q].push_back(j);
+                    else qdn[q].push_back(j);
+                }
+            }
+            std::sort(qvn[q].begin(), qvn[q].end(), [&](int a, int b) { return L.vfree[a] < L.vfree[b]; });
+            std::sort(qdn[q].begin(), qdn[q].end());
+        }
+    });
+    // --- CSR offsets: rows [comp c free velocity nodes...], then pressure
+    const int n = L.n_free;
+    std::vector<int> vrow(nVf);   // free index -> node
+    for (int i = 0; i < V.n; ++i)
+        if (L.vfree[i] >= 0) vrow[L.vfree[i]] = i;
+    CSR& K = L.K;
+    K.nr = K.ncol = n;
+    K.rp.assign(n + 1, 0);
+    CSR& KD = L.KfD;
+    KD.nr = n;
+    KD.ncol = d * V.n;
+    KD.rp.assign(n + 1, 0);
+    for (int c = 0; c < d; ++c)
+        for (int f = 0; f < nVf; ++f) {
+            int i = vrow[f];
+            K.rp[c * nVf + f + 1] = (int)(vnb[i].size() + vqn[i].size());
+            KD.rp[c * nVf + f + 1] = (int)vdn[i].size();
+        }
+    for (int q = 0; q < Q.n; ++q) {
+        K.rp[d * nVf + q + 1] = d * (int)qvn[q].size();
+        KD.rp[d * nVf + q + 1] = d * (int)qdn[q].size();
+    }
+    for (int r = 0; r < n; ++r) { K.rp[r + 1] += K.rp[r]; KD.rp[r + 1] += KD.rp[r]; }
+    K.ci.assign(K.rp[n], 0);
+    K.v.assign(K.rp[n], 0.0);
+    KD.ci.assign(KD.rp[n], 0);
+    KD.v.assign(KD.rp[n], 0.0);
+    // --- values: velocity rows
+    std::vector<std::vector<int>> posV(T, std::vector<int>(V.n, -1)), posQ(T, std::vector<int>(Q.n, -1));
+    parallel_for(nVf, [&](int lo, int hi, int t) {
+        auto& pv = posV[t];
+        auto& pq = posQ[t];
+        for (int f = lo; f < hi; ++f) {
+            int i = vrow[f];
+            const auto &a = vnb[i], &b = vqn[i], &dn = vdn[i];
+            int nvv = (int)a.size();
+            for (int s = 0; s < nvv; ++s) pv[a[s]] = s;
+            for (int s = 0; s < (int)dn.size(); ++s) pv[dn[s]] = s;
+            for (int s = 0; s < (int)b.size(); ++s) pq[b[s]] = nvv + s;
+            for (int c = 0; c < d; ++c) {
+                int r = c * nVf + f;
+                int* ci = &K.ci[K.rp[r]];
+                double* vv = &K.v[K.rp[r]];
+                for (int s = 0; s < nvv; ++s) ci[s] = c * nVf + L.vfree[a[s]];
+                for (int s = 0; s < (int)b.size(); ++s) ci[nvv + s] = d * nVf + b[s];
+                int* dci = &KD.ci[KD.rp[r]];
+                double* dv = &KD.v[KD.rp[r]];
+                for (int s = 0; s < (int)dn.size(); ++s) dci[s] = c * V.n + dn[s];
+                for (int x = voff[i]; x < voff[i + 1]; ++x) {
+                    int e = vadj[x] / nb, la = vadj[x] % nb;
+                    const double* se = &Se[((size_t)e * nb + la) * nb];
+                    for (int l = 0; l < nb; ++l) {
+                        int j = V.cell_nodes[(size_t)e * nb + l];
+                        if (L.vfree[j] >= 0) vv[pv[j]] += se[l];
+                        else dv[pv[j]] += se[l];
+                    }
+                    for (int p = 0; p < nq; ++p) {
+                        int q = Q.cell_nodes[(size_t)e * nq + p];
+                        vv[pq[q]] += Ce[(((size_t)e * nq + p) * nb + la) * d + c];
+                    }
+                }
+            }
+        }
+    });
+    // --- values: pressure rows (columns: comp 0 free, comp 1 free, ...)
+    parallel_for(Q.n, [&](int lo, int hi, int t) {
+        auto& pv = posV[t];
+        for (int q = lo; q < hi; ++q) {
+            const auto &a = qvn[q], &dn = qdn[q];
+            int nvv = (int)a.size(), ndd = (int)dn.size();
+            for (int s = 0; s < nvv; ++s) pv[a[s]] = s;
+            for (int s = 0; s < ndd; ++s) pv[dn[s]] = s;
+            int r = d * nVf + q;
+            int* ci = &K.ci[K.rp[r]];
+            double* vv = &K.v[K.rp[r]];
+            int* dci = &KD.ci[KD.rp[r]];
+            double* dv = &KD.v[KD.rp[r]];
+            for (int c = 0; c < d; ++c) {
+                for (int s = 0; s < nvv; ++s) ci[c * nvv + s] = c * nVf + L.vfree[a[s]];
+                for (int s = 0; s < ndd; ++s) dci[c * ndd + s] = c * V.n + dn[s];
+            }
+            for (int x = qoff[q]; x < qoff[q + 1]; ++x) {
+                int e = qadj[x] / nq, lp = qadj[x] % nq;
+                for (int l = 0; l < nb; ++l) {
+                    int j = V.cell_nodes[(size_t)e * nb + l];
+                    const double* ce = &Ce[(((size_t)e * nq + lp) * nb + l) * d];
+                    if (L.vfree[j] >= 0)
+                        for (int c = 0; c < d; ++c) vv[c * nvv + pv[j]] += ce[c];
+                    else
+                        for (int c = 0; c < d; ++c) dv[c * ndd + pv[j]] += ce[c];
+                }
+            }
+        }
+    });
+    // --- scalar mass matrix on all velocity nodes (for F = M f)
+    CSR& Mv = L.Mv;
+    Mv.nr = Mv.ncol = V.n;
+    Mv.rp.assign(V.n + 1, 0);
+    for (int i = 0; i < V.n; ++i) Mv.rp[i + 1] = Mv.rp[i] + (int)(vnb[i].size() + vdn[i].size());
+    Mv.ci.assign(Mv.rp[V.n], 0);
+    Mv.v.assign(Mv.rp[V.n], 0.0);
+    parallel_for(V.n, [&](int lo, int hi, int t) {
+        auto& pv = posV[t];
+        std::vector<int> cols;
+        for (int i = lo; i < hi; ++i) {
+            cols.assign(vnb[i].begin(), vnb[i].end());
+            cols.insert(cols.end(), vdn[i].begin(), vdn[i].end());
+            std::sort(cols.begin(), cols.end());
+            for (int s = 0; s < (int)cols.size(); ++s) { pv[cols[s]] = s; Mv.ci[Mv.rp[i] + s] = cols[s]; }
+            for (int x = voff[i]; x < voff[i + 1]; ++x) {
+                int e = vadj[x] / nb, la = vadj[x] % nb;
+                for (int l = 0; l < nb; ++l)
+                    Mv.v[Mv.rp[i] + pv[V.cell_nodes[(size_t)e * nb + l]]] += Me[((size_t)e * nb + la) * nb + l];
+            }
+        }
+    });
+    L.cell_center.assign((size_t)nc * d, 0.0);
+    for (int e = 0; e < nc; ++e)
+        for (int c = 0; c < d; ++c) {
+            double s = 0;
+            for (int i = 0; i <= d; ++i) s += m.X[(size_t)m.C[(size_t)e * (d + 1) + i] * d + c];
+            L.cell_center[(size_t)e * d + c] = s / (d + 1);
+        }
+}
+
+// Vanka-star patches (Sec. 3.4, Fig. 5): per mesh vertex, the free velocity
+// DoFs on all cells around it and the pressure DoFs of its star (TH: nodes
+// whose owning entity contains the vertex; SV: all pressure nodes of the
+// cells around it).
+static void build_patches(const Mesh& m, const Topology& T, Level& L) {
+    const int d = m.d, nb = L.V.nb, nq = L.Q.nb;
+    std::vector<std::vector<int>> P(m.nv);
+    const int NT = num_threads();
+    std::vector<std::vector<int>> stV(NT, std::vector<int>(L.V.n, -1)), stQ(NT, std::vector<int>(L.Q.n, -1));
+    parallel_for(m.nv, [&](int lo, int hi, int t) {
+        auto& sv = stV[t];
+        auto& sq = stQ[t];
+        std::vector<int> vel, pre;
+        for (int v = lo; v < hi; ++v) {
+            vel.clear();
+            pre.clear();
+            for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
+                int e = T.v2c[a];
+                for (int l = 0; l < nb; ++l) {
+                    int j = L.V.cell_nodes[(size_t)e * nb + l];
+                    if (sv[j] == v || L.vfree[j] < 0) continue;
+                    sv[j] = v;
+                    vel.push_back(L.vfree[j]);
+                }
+                for (int l = 0; l < nq; ++l) {
+                    int q = L.Q.cell_nodes[(size_t)e * nq + l];
+                    if (sq[q] == v) continue;
+                    sq[q] = v;
+                    if (L.family == 0) {
+                        const auto& s = L.Q.support[q];
+                        bool in = false;
+                        for (int t2 = 0; t2 < 4; ++t2) in |= (s[t2] == v);
+                        if (!in) continue;
+                    }
+                    pre.push_back(q);
+                }
+            }
+            std::sort(vel.begin(), vel.end());
+            std::sort(pre.begin(), pre.end());
+            auto& out = P[v];
+            for (int c = 0; c < d; ++c)
+                for (int x : vel) out.push_back(c * L.nVf + x);
+            for (int q : pre) out.push_back(d * L.nVf + q);
+        }
+    });
+    L.patch_off.assign(1, 0);
+    L.patch_dofs.clear();
+    for (int v = 0; v < m.nv; ++v) {
+        if (P[v].empty()) continue;
+        L.patch_dofs.insert(L.patch_dofs.end(), P[v].begin(), P[v].end());
+        L.patch_off.push_back((int)L.patch_dofs.size());
+    }
+}
+
+// Finite-element interpolation (Sec. 3.1): the coarse basis evaluated at the
+// fine nodes, each fine node located in the coarse cell that contains the
+// fine cell owning it.  Entries with |v| <= 1e-14 (exact lattice zeros) are
+// dropped.
+static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const Space& Vc,
+                         const RefElement& rec, const std::vector<int>* parent) {
+    const int d = mf.d, nbc = Vc.nb;
+    CSR P;
+    P.nr = Vf.n;
+    P.ncol = Vc.n;
+    std::vector<std::vector<std::pair<int, double>>> rows(Vf.n);
+    parallel_for(Vf.n, [&](int lo, int hi, int) {
+        std::vector<double> val(nbc);
+        for (int i = lo; i < hi; ++i) {
+            int fc = Vf.owner_cell[i];
+            int cc = parent ? (*parent)[fc] : fc;
+            CellGeom g = cell_geom(mc, cc);
+            const int* cv = &mc.C[(size_t)cc * (d + 1)];
+            double xi[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) {
+                double s = 0;
+                for (int c = 0; c < d; ++c) s += g.Jinv[a * d + c] * (Vf.X[(size_t)i * d + c] - mc.X[(size_t)cv[0] * d + c]);
+                xi[a] = s;
+            }
+            rec.eval(xi, val.data());
+            for (int l = 0; l < nbc; ++l)
+                if (std::fabs(val[l]) > 1e-14) rows[i].push_back({Vc.cell_nodes[(size_t)cc * nbc + l], val[l]});
+            std::sort(rows[i].begin(), rows[i].end());
+        }
+    });
+    P.rp.assign(P.nr + 1, 0);
+    for (int i = 0; i < P.nr; ++i) P.rp[i + 1] = P.rp[i] + (int)rows[i].size();
+    for (int i = 0; i < P.nr; ++i)
+        for (auto& x : rows[i]) { P.ci.push_back(x.first); P.v.push_back(x.second); }
+    return P;
+}
+
+static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Level& C,
+                              const RefElement& recV, const RefElement& recQ, const std::vector<int>* parent) {
+    CSR PV = scalar_interp(mf, F.V, mc, C.V, recV, parent);
+    CSR PQ = scalar_interp(mf, F.Q, mc, C.Q, recQ, parent);
+    const int d = mf.d;
+    CSR& P = F.P;
+    P.nr = F.n_free;
+    P.ncol = C.n_free;
+    P.rp.assign(1, 0);
+    P.ci.clear();
+    P.v.clear();
+    std::vector<int> vrow(F.nVf);
+    for (int i = 0; i < F.V.n; ++i)
+        if (F.vfree[i] >= 0) vrow[F.vfree[i]] = i;
+    for (int c = 0; c < d; ++c)
+        for (int f = 0; f < F.nVf; ++f) {
+            int i = vrow[f];
+            for (int p = PV.rp[i]; p < PV.rp[i + 1]; ++p) {
+                int jc = C.vfree[PV.ci[p]];
+                if (jc < 0) continue;
+                P.ci.push_back(c * C.nVf + jc);
+                P.v.push_back(PV.v[p]);
+            }
+            P.rp.push_back((int)P.ci.size());
+        }
+    for (int q = 0; q < F.Q.n; ++q) {
+        for (int p = PQ.rp[q]; p < PQ.rp[q + 1]; ++p) {
+            P.ci.push_back(d * C.nVf + PQ.ci[p]);
+            P.v.push_back(PQ.v[p]);
+        }
+        P.rp.push_back((int)P.ci.size());
+    }
+    // keep column indices sorted within a row
+    for (int r = 0; r < P.nr; ++r) {
+        std::vector<std::pair<int, double>> t;
+        for (int p = P.rp[r]; p < P.rp[r + 1]; ++p) t.push_back({P.ci[p], P.v[p]});
+        std::sort(t.begin(), t.end());
+        for (int p = P.rp[r]; p < P.rp[r + 1]; ++p) { P.ci[p] = t[p - P.rp[r]].first; P.v[p] = t[p - P.rp[r]].second; }
+    }
+    F.R = transpose(P);
+}
+
+void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell, Hierarchy& H) {
+    double t0 = now_ms();
+    const int d = coarse.d;
+    if (d != 2 && d != 3) throw std::invalid_argument("dim must be 2 or 3");
+    if (spec.schedule.empty()) throw std::invalid_argument("empty p-schedule");
+    for (int x : coarse.C)
+        if (x < 0 || x >= coarse.nv) throw std::invalid_argument("cell vertex index out of range");
+    std::vector<Mesh> fine_to_coarse{coarse};
+    std::vector<std::vector<int>> par;
+    for (int r = 0; r < spec.n_refine; ++r) {
+        std::vector<int> p;
+        fine_to_coarse.push_back(refine_uniform(fine_to_coarse.back(), p));
+        par.push_back(std::move(p));
+    }
+    if (spec.barycentric) {
+        std::vector<int> p;
+        fine_to_coarse.push_back(refine_alfeld(fine_to_coarse.back(), p));
+        par.push_back(std::move(p));
+    }
+    H.meshes.assign(fine_to_coarse.rbegin(), fine_to_coarse.rend());
+    H.parents.assign(par.rbegin(), par.rend());
+    const int nm = (int)H.meshes.size();
+    for (int e = 0; e < H.meshes.back().nc; ++e) {
+        // reject degenerate coarse cells
+        CellGeom g = cell_geom(H.meshes.back(), e);
+        if (!(g.detabs > 0) || !std::isfinite(g.detabs)) throw std::invalid_argument("degenerate coarse cell");
+    }
+    // viscosity per cell on every mesh (coarse cell = mean of its children)
+    std::vector<std::vector<double>> nus(nm);
+    if (nu_cell) {
+        nus[0].assign(nu_cell, nu_cell + H.meshes[0].nc);
+        for (int i = 0; i + 1 < nm; ++i) {
+            std::vector<double> s(H.meshes[i + 1].nc, 0.0), c(H.meshes[i + 1].nc, 0.0);
+            for (int e = 0; e < H.meshes[i].nc; ++e) { s[H.parents[i][e]] += nus[i][e]; c[H.parents[i][e]] += 1; }
+            for (size_t e = 0; e < s.size(); ++e) s[e] /= c[e];
+            nus[i + 1] = s;
+        }
+    }
+    std::vector<Topology> topo(nm);
+    for (int i = 0; i < nm; ++i) build_topology(H.meshes[i], topo[i]);
+    double t1 = now_ms();
+    H.t_mesh_ms = t1 - t0;
+    // levels: p-levels on the finest mesh, then the hMG degree on every mesh
+    struct LS { int mesh, family, k; bool p; };
+    std::vector<LS> ls;
+    const int np = (int)spec.schedule.size() - 1;
+    for (int i = 0; i < np; ++i) ls.push_back({0, i == 0 ? spec.family : 0, spec.schedule[i], true});
+    const int q = spec.schedule.back();
+    for (int mi = 0; mi < nm; ++mi) ls.push_back({mi, (np == 0 && mi == 0) ? spec.family : 0, q, false});
+    if ((int)ls.size() > 16) throw std::invalid_argument("too many levels");
+    H.levels.assign(ls.size(), Level());
+    std::map<std::pair<int, int>, RefElement> refs;
+    auto ref = [&](int dd, int kk) -> RefElement& {
+        auto key = std::make_pair(dd, kk);
+        auto it = refs.find(key);
+        if (it == refs.end()) { refs[key].init(dd, kk); it = refs.find(key); }
+        return it->second;
+    };
+    for (size_t l = 0; l < ls.size(); ++l) {
+        Level& L = H.levels[l];
+        L.d = d;
+        L.family = ls[l].family;
+        L.k = ls[l].k;
+        L.mesh_index = ls[l].mesh;
+        L.p_level = ls[l].p;
+        if (L.k < 2 || L.k > 10) throw std::invalid_argument("velocity degree must be in [2, 10]");
+        if (L.family == 1 && L.k < d) throw std::invalid_argument("Scott-Vogelius needs k >= dim");
+        const Mesh& m = H.meshes[L.mesh_index];
+        const RefElement& rv = ref(d, L.k);
+        const RefElement& rq = ref(d, L.k - 1);
+        build_space(m, topo[L.mesh_index], rv, true, L.V);
+        build_space(m, topo[L.mesh_index], rq, L.family == 0, L.Q);
+        RefTensors RT;
+        RT.init(rv, rq);
+        assemble_level(m, L, RT, nus[L.mesh_index]);
+        if (l + 1 < ls.size()) build_patches(m, topo[L.mesh_index], L);
+    }
+    for (size_t l = 0; l + 1 < ls.size(); ++l) {
+        Level &F = H.levels[l], &C = H.levels[l + 1];
+        const std::vector<int>* par_map = (F.mesh_index == C.mesh_index) ? nullptr : &H.parents[F.mesh_index];
+        monolithic_interp(H.meshes[F.mesh_index], F, H.meshes[C.mesh_index], C, ref(d, C.k), ref(d, C.k - 1), par_map);
+    }
+    H.t_assembly_ms = now_ms() - t1;
+}
+
+}  // namespace sfem

@@ -1,0 +1,103 @@
+// Host-side finite-element setup of the phMG hierarchy: nested simplicial
+// meshes (uniform R_u and Alfeld R_b refinement, Fig. 1), equispaced
+// Lagrange P_k spaces (Sec. 2.1), assembly of K = [nu A, B^T; B, 0]
+// (Eq. 2.3) into CSR on the free DoFs, finite-element interpolation P and
+// R = P^T (Sec. 3.1), and the Vanka-star patch index sets (Sec. 3.4, Fig. 5).
+// Everything numeric that runs per V-cycle lives in the CUDA kernels; this
+// file only produces the index structures and matrix values that the device
+// setup consumes.
+#pragma once
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace sfem {
+
+struct Mesh {
+    int d = 0, nv = 0, nc = 0;
+    std::vector<double> X;   // [nv][d]
+    std::vector<int> C;      // [nc][d+1]
+};
+
+Mesh refine_uniform(const Mesh& m, std::vector<int>& parent);
+Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent);
+
+// Lagrange element of degree k on the reference d-simplex with the
+// equispaced lattice nodes xi = (alpha_1, ..., alpha_d) / k.  Basis
+// functions are expanded in monomials; the coefficients come from inverting
+// the Vandermonde matrix of the nodes.
+struct RefElement {
+    int d = 0, k = 0, nb = 0, nm = 0;
+    std::vector<std::array<int, 4>> alpha;   // [nb] barycentric multi-index, alpha[0] = k - sum
+    std::vector<std::array<int, 3>> mono;    // [nm] exponents
+    std::vector<double> coef;                // [nb][nm]
+    void init(int d, int k);
+    void eval(const double* xi, double* out) const;   // out[nb]
+};
+
+// Reference tensors of one (velocity degree k, pressure degree kq) pair,
+// integrated exactly on the reference simplex.
+struct RefTensors {
+    int d = 0, nb = 0, nq = 0;
+    std::vector<double> S;     // [d][d][nb][nb]   int dphi_i/dxi_a dphi_j/dxi_b
+    std::vector<double> Cq;    // [d][nq][nb]      int psi_p dphi_j/dxi_a
+    std::vector<double> M;     // [nb][nb]         int phi_i phi_j
+    std::vector<double> qint;  // [nq]             int psi_p
+    void init(const RefElement& v, const RefElement& q);
+};
+
+struct CSR {
+    int nr = 0, ncol = 0;
+    std::vector<int> rp, ci;
+    std::vector<double> v;
+    long long nnz() const { return (long long)ci.size(); }
+};
+CSR transpose(const CSR& a);
+
+struct Space {
+    int d = 0, k = 0, nb = 0, n = 0;
+    bool continuous = true;
+    std::vector<int> cell_nodes;               // [nc][nb]
+    std::vector<double> X;                     // [n][d]
+    std::vector<unsigned char> boundary;       // [n]
+    std::vector<std::array<int, 4>> support;   // [n] vertices of the owning entity (-1 padded)
+    std::vector<int> owner_cell;               // [n] a cell containing the node
+};
+
+struct Level {
+    int d = 0, family = 0, k = 0, mesh_index = 0;
+    bool p_level = false;
+    Space V, Q;
+    std::vector<int> vfree;    // velocity node -> free node index or -1
+    int nVf = 0, nQ = 0, n_free = 0;
+    CSR K;                     // free x free
+    CSR KfD;                   // free rows x full velocity DoFs (Dirichlet columns only)
+    CSR Mv;                    // scalar velocity mass matrix on all nodes
+    std::vector<double> pint;  // int psi_j for every pressure node
+    CSR P, R;                  // interpolation from level+1 (free x free) and its transpose
+    std::vector<int> patch_off, patch_dofs;   // Vanka-star patches (free DoF indices)
+    std::vector<double> cell_center;          // [nc][d]
+};
+
+struct HierarchySpec {
+    int family = 0, k = 2;
+    std::vector<int> schedule;   // velocity degrees of the p-levels + the hMG degree
+    int n_refine = 0;
+    bool barycentric = false;
+};
+
+struct Hierarchy {
+    std::vector<Mesh> meshes;                 // [0] = finest
+    std::vector<std::vector<int>> parents;    // parents[i]: cells of meshes[i] -> meshes[i+1]
+    std::vector<Level> levels;
+    double t_mesh_ms = 0, t_assembly_ms = 0;
+};
+
+// Build the whole host hierarchy; throws std::runtime_error on invalid input.
+void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell,
+                     Hierarchy& H);
+
+int num_threads();
+
+}  // namespace sfem

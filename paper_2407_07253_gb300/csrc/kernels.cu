@@ -1,0 +1,512 @@
+// sm_103a kernels of the phMG hot path; declarations and roles in kernels.cuh.
+#include "kernels.cuh"
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace skern {
+
+__global__ void scale_by_inv(int n, const double* __restrict__ x, const double* __restrict__ s, double* __restrict__ y) {
+    const double inv = 1.0 / s[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = x[i] * inv;
+}
+
+__global__ void sub_scalar(int n, double* __restrict__ x, const double* __restrict__ num, double den) {
+    const double m = num[0] / den;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] -= m;
+}
+
+// ------------------------------------------------------------ reductions ---
+constexpr int MDOT_MAX = 32;
+
+__global__ void __launch_bounds__(256) mdot_partial(int n, int m, const double* __restrict__ V, long long ldv,
+                                                    const double* __restrict__ w, double* __restrict__ partial) {
+    double acc[MDOT_MAX];
+#pragma unroll
+    for (int i = 0; i < MDOT_MAX; ++i) acc[i] = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double wk = w[k];
+#pragma unroll
+        for (int i = 0; i < MDOT_MAX; ++i)
+            if (i < m) acc[i] += V[(long long)i * ldv + k] * wk;
+    }
+    __shared__ double red[8][MDOT_MAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < MDOT_MAX; ++i) {
+        if (i >= m) break;
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double s = 0;
+        for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += red[wv][threadIdx.x];
+        partial[(long long)blockIdx.x * m + threadIdx.x] = s;
+    }
+}
+
+__global__ void mdot_final(int nblocks, int m, const double* __restrict__ partial, double* __restrict__ out,
+                           double* __restrict__ acc, int sqrt_out) {
+    const int i = threadIdx.x;
+    if (i >= m) return;
+    double s = 0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * m + i];
+    if (acc) acc[i] += s;
+    out[i] = (sqrt_out && i == 0) ? sqrt(s) : s;
+}
+
+__global__ void __launch_bounds__(256) maxpy(int n, int m, const double* __restrict__ V, long long ldv,
+                                             const double* __restrict__ h, double sign, double* __restrict__ w) {
+    __shared__ double hs[MDOT_MAX];
+    if (threadIdx.x < m) hs[threadIdx.x] = sign * h[threadIdx.x];
+    __syncthreads();
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double s = w[k];
+        for (int i = 0; i < m; ++i) s += hs[i] * V[(long long)i * ldv + k];
+        w[k] = s;
+    }
+}
+
+// -------------------------------------------------------------- patches ---
+__global__ void __launch_bounds__(256) patch_gather(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                    const long long* __restrict__ moff, const int* __restrict__ rp,
+                                                    const int* __restrict__ ci, const double* __restrict__ av,
+                                                    double* __restrict__ out) {
+    extern __shared__ int sdofs[];
+    const int p = blockIdx.x;
+    const int s = poff[p], n = poff[p + 1] - s;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) sdofs[a] = pdofs[s + a];
+    __syncthreads();
+    double* M = out + moff[p];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int a = warp; a < n; a += nw) {
+        const int g = sdofs[a];
+        const int e = rp[g + 1];
+        for (int q = rp[g] + lane; q < e; q += 32) {
+            const int c = ci[q];
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {              // first position with sdofs[pos] >= c
+                const int mid = (lo + hi) >> 1;
+                if (sdofs[mid] < c) lo = mid + 1; else hi = mid;
+            }
+            if (sdofs[lo] == c) M[(long long)a * n + lo] = av[q];
+        }
+    }
+}
+
+// In-place Gauss-Jordan with partial pivoting on a row-major n x n matrix A
+// (shared or global memory).  The first maximum |A[i][k]|, i >= k, is the
+// pivot; rows are swapped, the pivot row scaled, column k eliminated from all
+// other rows; at the end columns are swapped back in reverse order.  Returns
+// (in *status) 0, or 1 + the step of the first zero pivot.
+__device__ void gj_core(double* A, int n, double* colk, int* ipiv, int* status) {
+    __shared__ double s_val[32];
+    __shared__ int s_idx[32];
+    __shared__ int s_p;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+        // pivot search: each warp scans a strided subset, then warp 0 reduces
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += nt) {
+            const double v = fabs(A[(long long)i * n + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = nt >> 5;
+            best = lane < nw ? s_val[lane] : -1.0;
+            bi = lane < nw ? s_idx[lane] : n;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) {
+                if (!(best > 0.0) || bi >= n) { bi = k; if (!bad) bad = k + 1; }
+                s_p = bi;
+                ipiv[k] = bi;
+                if (bad && *status == 0) *status = bad;
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < n; j += nt) {
+                const double t = A[(long long)k * n + j];
+                A[(long long)k * n + j] = A[(long long)p * n + j];
+                A[(long long)p * n + j] = t;
+            }
+        __syncthreads();
+        const double piv = A[(long long)k * n + k];
+        const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+        for (int i = tid; i < n; i += nt) colk[i] = A[(long long)i * n + k];
+        __syncthreads();
+        for (int j = tid; j < n; j += nt) A[(long long)k * n + j] = (j == k) ? inv : A[(long long)k * n + j] * inv;
+        __syncthreads();
+        // rank-1 elimination of column k from every other row
+        int i = tid / n, j = tid - (tid / n) * n;
+        const int step_i = nt / n, step_j = nt - step_i * n;
+        for (; i < n;) {
+            if (i != k) {
+                const double f = colk[i];
+                if (j == k) A[(long long)i * n + k] = -f * inv;
+                else A[(long long)i * n + j] -= f * A[(long long)k * n + j];
+            }
+            i += step_i;
+            j += step_j;
+            if (j >= n) { j -= n; ++i; }
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges by column interchanges in reverse order
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = ipiv[k];
+        if (p != k)
+            for (int i = tid; i < n; i += nt) {
+                const double t = A[(long long)i * n + k];
+                A[(long long)i * n + k] = A[(long long)i * n + p];
+                A[(long long)i * n + p] = t;
+            }
+        __syncthreads();
+    }
+}
+
+__device__ void gj_store(const double* A, int n, double* inv64, long long o64, float* inv32, long long o32) {
+    const int ld64 = (n + 1) & ~1, ld32 = (n + 3) & ~3;
+    if (inv64)
+        for (int t = threadIdx.x; t < ld64 * n; t += blockDim.x) {
+            const int j = t / ld64, i = t - j * ld64;
+            inv64[o64 + t] = i < n ? A[(long long)i * n + j] : 0.0;
+        }
+    if (inv32)
+        for (int t = threadIdx.x; t < ld32 * n; t += blockDim.x) {
+            const int j = t / ld32, i = t - j * ld32;
+            inv32[o32 + t] = i < n ? (float)A[(long long)i * n + j] : 0.0f;
+        }
+}
+
+__global__ void __launch_bounds__(256) gj_inverse_smem(int npatch, const int* __restrict__ poff, const long long* __restrict__ moff,
+                                                       double* __restrict__ work, const long long* __restrict__ off64,
+                                                       double* __restrict__ inv64, const long long* __restrict__ off32,
+                                                       float* __restrict__ inv32, int* __restrict__ status, int) {
+    extern __shared__ double smem[];
+    const int p = blockIdx.x;
+    const int n = poff[p + 1] - poff[p];
+    if (n > GJ_SMEM_MAX_N || n == 0) return;
+    double* A = smem;
+    double* colk = smem + (long long)n * n;
+    int* ipiv = (int*)(colk + n);
+    __shared__ int st;
+    if (threadIdx.x == 0) st = 0;
+    const double* W = work + moff[p];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = W[t];
+    __syncthreads();
+    gj_core(A, n, colk, ipiv, &st);
+    __syncthreads();
+    gj_store(A, n, inv64, off64 ? off64[p] : 0, inv32, off32 ? off32[p] : 0);
+    // keep the row-major inverse in the workspace for export
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) work[moff[p] + t] = A[t];
+    if (threadIdx.x == 0) status[p] = st;
+}
+
+__global__ void __launch_bounds__(512) gj_inverse_global(int npatch, const int* __restrict__ poff, const long long* __restrict__ moff,
+                                                         double* __restrict__ work, const long long* __restrict__ off64,
+                                                         double* __restrict__ inv64, const long long* __restrict__ off32,
+                                                         float* __restrict__ inv32, int* __restrict__ status,
+                                                         int* __restrict__ ipiv_ws, double* __restrict__ col_ws) {
+    const int p = blockIdx.x;
+    const int n = poff[p + 1] - poff[p];
+    if (n <= GJ_SMEM_MAX_N) return;
+    __shared__ int st;
+    if (threadIdx.x == 0) st = 0;
+    __syncthreads();
+    double* A = work + moff[p];
+    gj_core(A, n, col_ws + poff[p], ipiv_ws + poff[p], &st);
+    __syncthreads();
+    gj_store(A, n, inv64, off64 ? off64[p] : 0, inv32, off32 ? off32[p] : 0);
+    if (threadIdx.x == 0) status[p] = st;
+}
+
+// One ASM sweep.  Each thread owns VEC consecutive rows of the column-major
+// padded inverse and streams its columns; the gathered residual sits in
+// shared memory.
+__global__ void __launch_bounds__(256) patch_apply_f32(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                          const long long* __restrict__ ioff, const float* __restrict__ inv,
+                                                          const float* __restrict__ r, const float* __restrict__ wt,
+                                                          float* __restrict__ Y) {
+    extern __shared__ float xs32[];
+    const int p = blockIdx.x;
+    const int s = poff[p], n = poff[p + 1] - s;
+    const int ld4 = (n + 3) >> 2;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) xs32[a] = r[pdofs[s + a]];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t >= ld4) return;
+    const float4* col = reinterpret_cast<const float4*>(inv + ioff[p]) + t;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+        const float4 v0 = __ldcs(col + (long long)(j + 0) * ld4);
+        const float4 v1 = __ldcs(col + (long long)(j + 1) * ld4);
+        const float4 v2 = __ldcs(col + (long long)(j + 2) * ld4);
+        const float4 v3 = __ldcs(col + (long long)(j + 3) * ld4);
+        const float x0 = xs32[j], x1 = xs32[j + 1], x2 = xs32[j + 2], x3 = xs32[j + 3];
+        acc.x += v0.x * x0; acc.y += v0.y * x0; acc.z += v0.z * x0; acc.w += v0.w * x0;
+        acc.x += v1.x * x1; acc.y += v1.y * x1; acc.z += v1.z * x1; acc.w += v1.w * x1;
+        acc.x += v2.x * x2; acc.y += v2.y * x2; acc.z += v2.z * x2; acc.w += v2.w * x2;
+        acc.x += v3.x * x3; acc.y += v3.y * x3; acc.z += v3.z * x3; acc.w += v3.w * x3;
+    }
+    for (; j < n; ++j) {
+        const float4 v = __ldcs(col + (long long)j * ld4);
+        const float x = xs32[j];
+        acc.x += v.x * x; acc.y += v.y * x; acc.z += v.z * x; acc.w += v.w * x;
+    }
+    const int a0 = 4 * t;
+    const float o[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (a0 + q < n) Y[s + a0 + q] = wt[pdofs[s + a0 + q]] * o[q];
+}
+
+__global__ void __launch_bounds__(256) patch_apply_f64(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                           const long long* __restrict__ ioff, const double* __restrict__ inv,
+                                                           const double* __restrict__ r, const double* __restrict__ wt,
+                                                           double* __restrict__ Y) {
+    extern __shared__ double xs64[];
+    const int p = blockIdx.x;
+    const int s = poff[p], n = poff[p + 1] - s;
+    const int ld2 = (n + 1) >> 1;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) xs64[a] = r[pdofs[s + a]];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t >= ld2) return;
+    const double2* col = reinterpret_cast<const double2*>(inv + ioff[p]) + t;
+    double2 acc = make_double2(0.0, 0.0);
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+        const double2 v0 = __ldcs(col + (long long)(j + 0) * ld2);
+        const double2 v1 = __ldcs(col + (long long)(j + 1) * ld2);
+        const double2 v2 = __ldcs(col + (long long)(j + 2) * ld2);
+        const double2 v3 = __ldcs(col + (long long)(j + 3) * ld2);
+        acc.x += v0.x * xs64[j]; acc.y += v0.y * xs64[j];
+        acc.x += v1.x * xs64[j + 1]; acc.y += v1.y * xs64[j + 1];
+        acc.x += v2.x * xs64[j + 2]; acc.y += v2.y * xs64[j + 2];
+        acc.x += v3.x * xs64[j + 3]; acc.y += v3.y * xs64[j + 3];
+    }
+    for (; j < n; ++j) {
+        const double2 v = __ldcs(col + (long long)j * ld2);
+        acc.x += v.x * xs64[j]; acc.y += v.y * xs64[j];
+    }
+    const int a0 = 2 * t;
+    if (a0 < n) Y[s + a0] = wt[pdofs[s + a0]] * acc.x;
+    if (a0 + 1 < n) Y[s + a0 + 1] = wt[pdofs[s + a0 + 1]] * acc.y;
+}
+
+// ---------------------------------------------------------- coarse GJ ---
+__global__ void __launch_bounds__(256) gj_step_pivot(int n, int k, double* __restrict__ A, int* __restrict__ ipiv,
+                                                     double* __restrict__ colk, int* __restrict__ status) {
+    __shared__ double s_val[8];
+    __shared__ int s_idx[8];
+    __shared__ int s_p;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += blockDim.x) {
+        const double v = fabs(A[(long long)i * n + k]);
+        if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (s_val[w] > best || (s_val[w] == best && s_idx[w] < bi)) { best = s_val[w]; bi = s_idx[w]; }
+        if (!(best > 0.0) || bi >= n) { bi = k; if (*status == 0) *status = k + 1; }
+        s_p = bi;
+        ipiv[k] = bi;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != k)
+        for (int j = tid; j < n; j += blockDim.x) {
+            const double t = A[(long long)k * n + j];
+            A[(long long)k * n + j] = A[(long long)p * n + j];
+            A[(long long)p * n + j] = t;
+        }
+    __syncthreads();
+    const double piv = A[(long long)k * n + k];
+    const double inv = piv != 0.0 ? 1.0 / piv : 0.0;
+    for (int i = tid; i < n; i += blockDim.x) colk[i] = A[(long long)i * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += blockDim.x) A[(long long)k * n + j] = (j == k) ? inv : A[(long long)k * n + j] * inv;
+}
+
+__global__ void __launch_bounds__(256) gj_step_eliminate(int n, int k, double* __restrict__ A, const double* __restrict__ colk) {
+    const long long total = (long long)n * n;
+    const double inv = A[(long long)k * n + k];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t - (long long)i * n);
+        if (i == k) continue;
+        const double f = colk[i];
+        if (j == k) A[t] = -f * inv;
+        else A[t] -= f * A[(long long)k * n + j];
+    }
+}
+
+__global__ void gj_unpivot_rows(int n, double* __restrict__ A, const int* __restrict__ ipiv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = n - 1; k >= 0; --k) {
+            const int p = ipiv[k];
+            if (p != k) {
+                const double t = A[(long long)i * n + k];
+                A[(long long)i * n + k] = A[(long long)i * n + p];
+                A[(long long)i * n + p] = t;
+            }
+        }
+}
+
+__global__ void __launch_bounds__(256) dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A,
+                                                  const double* __restrict__ x, double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= nout) return;
+    double s = 0;
+    for (int j = lane; j < ncol; j += 32) s += A[(long long)row * lda + j] * x[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s;
+}
+
+// ------------------------------------------------------ small Hessenberg ---
+__global__ void fgmres_givens(int j, int ldh, double* __restrict__ H, const double* __restrict__ hcol,
+                              const double* __restrict__ hnorm, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, double* __restrict__ resid) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i <= j; ++i) H[i * ldh + j] = hcol[i];
+    H[(j + 1) * ldh + j] = hnorm[0];
+    for (int i = 0; i < j; ++i) {
+        const double a = H[i * ldh + j], b = H[(i + 1) * ldh + j];
+        H[i * ldh + j] = cs[i] * a + sn[i] * b;
+        H[(i + 1) * ldh + j] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = H[j * ldh + j], b = H[(j + 1) * ldh + j];
+    const double den = hypot(a, b);
+    double c = 1.0, s = 0.0;
+    if (den > 0.0) { c = a / den; s = b / den; }
+    cs[j] = c;
+    sn[j] = s;
+    H[j * ldh + j] = den > 0.0 ? den : a;
+    H[(j + 1) * ldh + j] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    resid[0] = fabs(g[j + 1]);
+}
+
+__global__ void fgmres_backsolve(int m, int ldh, const double* __restrict__ H, const double* __restrict__ g,
+                                 double* __restrict__ y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = m - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int l = i + 1; l < m; ++l) s -= H[i * ldh + l] * y[l];
+        y[i] = s / H[i * ldh + i];
+    }
+}
+
+__global__ void arnoldi_store(int j, int m, double* __restrict__ Hs, const double* __restrict__ h,
+                              const double* __restrict__ hnorm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i <= j; ++i) Hs[i * m + j] = h[i];
+    Hs[(j + 1) * m + j] = hnorm[0];
+}
+
+struct cplx { double re, im; };
+__device__ inline cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ inline cplx cconj(cplx a) { return {a.re, -a.im}; }
+__device__ inline double cabs2(cplx a) { return hypot(a.re, a.im); }
+__device__ inline cplx csqrt2(cplx z) {
+    const double r = cabs2(z);
+    double re = sqrt(fmax(0.0, 0.5 * (r + z.re)));
+    double im = sqrt(fmax(0.0, 0.5 * (r - z.re)));
+    if (z.im < 0) im = -im;
+    return {re, im};
+}
+__device__ inline cplx cscale(cplx a, double s) { return {a.re * s, a.im * s}; }
+
+// Eigenvalues of a small upper Hessenberg matrix by the shifted QR
+// iteration in complex arithmetic (Wilkinson shift from the trailing 2 x 2
+// block, Givens rotations, deflation on negligible subdiagonals).
+__global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict__ Hs, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    constexpr int MX = 16;
+    __shared__ cplx A[MX][MX];
+    __shared__ cplx cr[MX], sr[MX];
+    const int m = mm < MX ? mm : MX;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) A[i][j] = {(j >= i - 1) ? Hs[i * ld + j] : 0.0, 0.0};
+    double best = -1e300;
+    int hi = m - 1, it = 0, total = 0, failed = 0;
+    while (hi >= 0) {
+        if (hi == 0) { best = fmax(best, A[0][0].re); break; }
+        int l = hi;
+        while (l > 0) {
+            const double sub = cabs2(A[l][l - 1]);
+            const double diag = cabs2(A[l][l]) + cabs2(A[l - 1][l - 1]);
+            if (sub <= 1e-15 * (diag > 0 ? diag : 1.0)) break;
+            --l;
+        }
+        if (l == hi) { best = fmax(best, A[hi][hi].re); --hi; it = 0; continue; }
+        if (++total > 200 * m) { failed = 1; for (int i = 0; i <= hi; ++i) best = fmax(best, A[i][i].re); break; }
+        // Wilkinson shift: eigenvalue of the trailing 2x2 closest to A[hi][hi]
+        const cplx a = A[hi - 1][hi - 1], b = A[hi - 1][hi], c = A[hi][hi - 1], d = A[hi][hi];
+        const cplx half = cscale(csub(a, d), 0.5);
+        const cplx disc = csqrt2(cadd(cmul(half, half), cmul(b, c)));
+        const cplx mid = cscale(cadd(a, d), 0.5);
+        const cplx m1 = cadd(mid, disc), m2 = csub(mid, disc);
+        cplx mu = cabs2(csub(m1, d)) < cabs2(csub(m2, d)) ? m1 : m2;
+        if (++it % 11 == 10) mu = cadd(d, cplx{cabs2(c), 0.0});   // exceptional shift
+        for (int i = l; i <= hi; ++i) A[i][i] = csub(A[i][i], mu);
+        for (int i = l; i < hi; ++i) {
+            const cplx x = A[i][i], y = A[i + 1][i];
+            const double r = hypot(cabs2(x), cabs2(y));
+            cplx cc = {1.0, 0.0}, ss = {0.0, 0.0};
+            if (r > 0) { cc = cscale(x, 1.0 / r); ss = cscale(y, 1.0 / r); }
+            cr[i] = cc;
+            sr[i] = ss;
+            for (int j = i; j <= hi; ++j) {
+                const cplx u = A[i][j], v = A[i + 1][j];
+                A[i][j] = cadd(cmul(cconj(cc), u), cmul(cconj(ss), v));
+                A[i + 1][j] = csub(cmul(cc, v), cmul(ss, u));
+            }
+        }
+        for (int i = l; i < hi; ++i) {
+            const cplx cc = cr[i], ss = sr[i];
+            const int rmax = (i + 2 < hi) ? i + 2 : hi;
+            for (int rr = l; rr <= rmax; ++rr) {
+                const cplx u = A[rr][i], v = A[rr][i + 1];
+                A[rr][i] = cadd(cmul(u, cc), cmul(v, ss));
+                A[rr][i + 1] = csub(cmul(v, cconj(cc)), cmul(u, cconj(ss)));
+            }
+        }
+        for (int i = l; i <= hi; ++i) A[i][i] = cadd(A[i][i], mu);
+    }
+    out[0] = best;
+    out[1] = failed;
+}
+
+}  // namespace skern

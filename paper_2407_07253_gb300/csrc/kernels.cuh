@@ -1,0 +1,175 @@
+// sm_103a kernels of the phMG hot path.
+//
+//   spmv_*            CSR SpMV / fused residual r = b - K x (Eq. 3.1, 3.2
+//                     residuals), prolongation y += P x and restriction y = R x
+//                     (Sec. 3.1 transfers).
+//   patch_gather      K_i = I_i K I_i^T from the CSR operator (Eq. 3.4,
+//                     Sec. 3.4 assembled-matrix patch extraction).
+//   gj_inverse_*      batched partial-pivot Gauss-Jordan inversion of the
+//                     patch matrices in FP64 (exact patch solves, Sec. 3.4).
+//   patch_apply       y_i = W_i K_i^{-1} (I_i r) for every patch (one ASM
+//                     sweep, Eq. 3.4), streamed from HBM.
+//   pull_scatter      z = sum_i I_i^T y_i as a deterministic gather over the
+//                     DoF -> (patch slot) transpose map, fused with the
+//                     Chebyshev / damped update.
+//   mdot / maxpy ...  FGMRES and Arnoldi vector kernels (FP64).
+//   hess_*            small Hessenberg / Givens kernels run by one thread.
+//
+// All kernels take plain device pointers; grids are sized by the host.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace skern {
+
+constexpr int GJ_SMEM_MAX_N = 160;   // FP64 patch held in shared memory up to this size
+
+// ----------------------------------------------------------------- SpMV ---
+enum SpmvMode { SPMV_SET = 0, SPMV_ADD = 1, SPMV_RESID = 2 };
+
+// One LANES-wide group of threads per row; values of type T accumulate in T.
+// mode SET:   y = A x        ADD: y += A x        RESID: y = b - A x
+template <typename T, int LANES, int MODE>
+__global__ void __launch_bounds__(256) spmv_csr(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                const T* __restrict__ av, const T* __restrict__ x,
+                                                T* __restrict__ y, const T* __restrict__ b) {
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = gtid / LANES;
+    const int lane = threadIdx.x % LANES;
+    if (row >= nrows) return;   // whole LANES-group exits together (LANES divides 32)
+    const int s = __ldg(rp + row), e = __ldg(rp + row + 1);
+    T acc = 0;
+    for (int p = s + lane; p < e; p += LANES) acc += __ldg(av + p) * __ldg(x + __ldg(ci + p));
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LANES);
+    if (lane == 0) {
+        if (MODE == SPMV_SET) y[row] = acc;
+        else if (MODE == SPMV_ADD) y[row] += acc;
+        else y[row] = b[row] - acc;
+    }
+}
+
+// ------------------------------------------------------- vector kernels ---
+template <typename TO, typename TI>
+__global__ void convert_vec(int n, const TI* __restrict__ x, TO* __restrict__ y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = (TO)x[i];
+}
+
+template <typename T>
+__global__ void fill_vec(long long n, T v, T* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) y[i] = v;
+}
+
+// y = a x + b y
+template <typename T>
+__global__ void axpby(int n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = a * x[i] + b * y[i];
+}
+
+// y = x * (1 / *s)   (device scalar divisor, FGMRES / Arnoldi normalisation)
+__global__ void scale_by_inv(int n, const double* __restrict__ x, const double* __restrict__ s, double* __restrict__ y);
+
+// y = x - K x is not needed; the FGMRES/Arnoldi reductions:
+// partial[b*m + i] = sum over this block's rows of V[i][k] * w[k]
+__global__ void mdot_partial(int n, int m, const double* __restrict__ V, long long ldv,
+                             const double* __restrict__ w, double* __restrict__ partial);
+// out[i] = sum_b partial[b*m + i] (fixed order), optionally accumulated
+// into acc[i] as well; if sqrt_out, out[0] = sqrt(sum).
+__global__ void mdot_final(int nblocks, int m, const double* __restrict__ partial, double* __restrict__ out,
+                           double* __restrict__ acc, int sqrt_out);
+// w[k] += sign * sum_i h[i] V[i][k]
+__global__ void maxpy(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ h,
+                      double sign, double* __restrict__ w);
+
+// ------------------------------------------------------------- patches ---
+// Dense K_i (row-major n_i x n_i, FP64) gathered from the CSR of K: one CTA
+// per patch; column positions found by binary search in the sorted patch DoF
+// list.  out must be zeroed by the caller.
+__global__ void patch_gather(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                             const long long* __restrict__ moff, const int* __restrict__ rp,
+                             const int* __restrict__ ci, const double* __restrict__ av, double* __restrict__ out);
+
+// In-place Gauss-Jordan inversion with partial pivoting of every patch
+// matrix (row-major, FP64), shared-memory variant (n_i <= GJ_SMEM_MAX_N).
+// Writes K_i^{-1} column-major with leading dimension ld64 (FP64) and, if
+// inv32 != nullptr, ld32 (FP32); the row-major inverse is also written back
+// to `work` when keep_rowmajor.  status[patch] = 0, or 1 + pivot step of the
+// first zero pivot.
+__global__ void gj_inverse_smem(int npatch, const int* __restrict__ poff, const long long* __restrict__ moff,
+                                double* __restrict__ work, const long long* __restrict__ off64, double* __restrict__ inv64,
+                                const long long* __restrict__ off32, float* __restrict__ inv32,
+                                int* __restrict__ status, int only_large);
+// Same algorithm operating on the matrix in global memory (large patches).
+__global__ void gj_inverse_global(int npatch, const int* __restrict__ poff, const long long* __restrict__ moff,
+                                  double* __restrict__ work, const long long* __restrict__ off64, double* __restrict__ inv64,
+                                  const long long* __restrict__ off32, float* __restrict__ inv32,
+                                  int* __restrict__ status, int* __restrict__ ipiv_ws, double* __restrict__ col_ws);
+
+// One ASM sweep (Eq. 3.4): Y[poff[i] + a] = w[dof_a] * sum_b Kinv_i[a][b] r[dof_b].
+// FP32: float4 loads of 4 consecutive rows per thread; FP64: double2 loads
+// of 2 rows.  One CTA per patch; blockDim = round_up(ld / VEC, 32).
+__global__ void patch_apply_f32(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                const long long* __restrict__ ioff, const float* __restrict__ inv,
+                                const float* __restrict__ r, const float* __restrict__ wt, float* __restrict__ Y);
+__global__ void patch_apply_f64(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                const long long* __restrict__ ioff, const double* __restrict__ inv,
+                                const double* __restrict__ r, const double* __restrict__ wt, double* __restrict__ Y);
+
+// out[j] = alpha * sum_{s in slots(j)} Y[s] + beta * out[j]  (slots in a
+// fixed order, so the sum is bitwise reproducible)
+template <typename T>
+__global__ void __launch_bounds__(256) pull_scatter(int n, const int* __restrict__ soff, const int* __restrict__ sidx,
+                                                    const T* __restrict__ Y, T alpha, T beta, T* __restrict__ out) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        T s = 0;
+        const int e = soff[j + 1];
+        for (int q = soff[j]; q < e; ++q) s += Y[sidx[q]];
+        out[j] = beta == T(0) ? alpha * s : alpha * s + beta * out[j];
+    }
+}
+
+// ------------------------------------------------------ coarse solve ---
+// One Gauss-Jordan step k on a dense row-major n x n FP64 matrix in global
+// memory: pivot search, row swap, pivot-row scaling and copy of column k
+// (single CTA), then the rank-1 elimination over all rows (whole grid).
+__global__ void gj_step_pivot(int n, int k, double* __restrict__ A, int* __restrict__ ipiv,
+                              double* __restrict__ colk, int* __restrict__ status);
+__global__ void gj_step_eliminate(int n, int k, double* __restrict__ A, const double* __restrict__ colk);
+__global__ void gj_unpivot_rows(int n, double* __restrict__ A, const int* __restrict__ ipiv);
+// y[i] = sum_j A[i][j] x[j] for i < nout (row-major, leading dimension lda)
+__global__ void dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A, const double* __restrict__ x,
+                           double* __restrict__ y);
+
+// --------------------------------------------------- small Hessenberg ---
+// FGMRES: apply the previous Givens rotations to column j of H (stored
+// [restart+1][restart] row-major), build rotation j, update g; resid[0] = |g[j+1]|.
+// hcol holds h[0..j]; hnorm[0] = h[j+1].
+__global__ void fgmres_givens(int j, int ldh, double* __restrict__ H, const double* __restrict__ hcol,
+                              const double* __restrict__ hnorm, double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, double* __restrict__ resid);
+// y = H[0:m,0:m]^{-1} g (upper triangular back substitution)
+__global__ void fgmres_backsolve(int m, int ldh, const double* __restrict__ H, const double* __restrict__ g,
+                                 double* __restrict__ y);
+// Arnoldi: store column j of H (h[0..j], hnorm) into Hs [(m+1) x m].
+__global__ void arnoldi_store(int j, int m, double* __restrict__ Hs, const double* __restrict__ h,
+                              const double* __restrict__ hnorm);
+// largest real part of the eigenvalues of the leading mm x mm block of the
+// upper Hessenberg Hs (complex shifted QR iteration), out[0]; out[1] = 0 if
+// converged, 1 otherwise.
+__global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict__ Hs, double* __restrict__ out);
+
+// ------------------------------------------------------ solve plumbing ---
+// b_free[r] = (F restricted) computed by the host-built maps:
+// x_free gathers: out[i] = in[idx[i]]; scatter: out[idx[i]] = in[i]
+template <typename T>
+__global__ void gather_idx(int n, const int* __restrict__ idx, const T* __restrict__ in, T* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[idx[i]];
+}
+template <typename T>
+__global__ void scatter_idx(int n, const int* __restrict__ idx, const T* __restrict__ in, T* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[idx[i]] = in[i];
+}
+// x[i] -= mean; mean = (sum_i w[i] x[i]) / wsum from a device scalar
+__global__ void sub_scalar(int n, double* __restrict__ x, const double* __restrict__ num, double den);
+
+}  // namespace skern

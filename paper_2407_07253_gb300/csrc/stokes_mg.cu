@@ -1,0 +1,1315 @@
+// C ABI of the GB300 phMG library (include/stokes_mg.h): device data of the
+// hierarchy, setup (patch gather, batched Gauss-Jordan, coarse bordered
+// inverse, Arnoldi lambda_max), the V-cycle (Eq. 3.1 / 3.2 with Chebyshev-
+// wrapped additive Schwarz, Eq. 3.4), FGMRES (Sec. 4) and the per-step
+// entry points used by the parity tests.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/stokes_mg.h"
+#include "fem.hpp"
+#include "kernels.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct StokesError : std::runtime_error {
+    int code;
+    StokesError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            throw StokesError(e_ == cudaErrorMemoryAllocation ? STOKES_EOOM : STOKES_ECUDA,        \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+double host_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename T>
+T* dalloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    return (T*)p;
+}
+
+template <typename T>
+T* dupload(const std::vector<T>& h, cudaStream_t s) {
+    T* p = dalloc<T>(h.size());
+    if (!h.empty()) CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return p;
+}
+
+inline int grid_for(long long n, int block = 256) {
+    long long g = (n + block - 1) / block;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
+}
+
+struct DevCSR {
+    int nr = 0, nc = 0;
+    long long nnz = 0;
+    int lanes = 16;
+    int *rp = nullptr, *ci = nullptr;
+    double* v64 = nullptr;
+    float* v32 = nullptr;
+};
+
+struct DevLevel {
+    int n = 0;
+    bool p_level = false;
+    DevCSR K, P, R;
+    // patches
+    int npatch = 0, maxn = 0;
+    long long nent = 0, nsq = 0;
+    int *poff = nullptr, *pdofs = nullptr;
+    long long *moff = nullptr, *ioff64 = nullptr, *ioff32 = nullptr;
+    long long ninv64 = 0, ninv32 = 0;
+    double* inv64 = nullptr;
+    float* inv32 = nullptr;
+    double* wt64 = nullptr;
+    float* wt32 = nullptr;
+    int *soff = nullptr, *sidx = nullptr;
+    double* Y64 = nullptr;
+    float* Y32 = nullptr;
+    // V-cycle work vectors (both precisions)
+    double *b64 = nullptr, *e64 = nullptr, *r64 = nullptr, *d64 = nullptr, *t64 = nullptr, *u64 = nullptr;
+    float *b32 = nullptr, *e32 = nullptr, *r32 = nullptr, *d32 = nullptr, *t32 = nullptr, *u32 = nullptr;
+    double lmax = 0;
+};
+
+struct Prof {
+    bool on = false;
+    long long launches = 0;
+    double total_ms = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+}  // namespace
+
+struct stokes_mg {
+    int device = 0;
+    stokes_mg_opts opts;
+    sfem::Hierarchy H;
+    std::vector<DevLevel> L;
+    int dim = 2, family = 0, k = 2;
+    // coarse bordered inverse
+    int nc = 0;
+    double* Cinv = nullptr;
+    double *cb64 = nullptr, *ce64 = nullptr;
+    // FGMRES
+    int restart = 30;
+    double *V = nullptr, *Z = nullptr, *Hh = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double *h = nullptr, *hn = nullptr, *resid = nullptr, *partial = nullptr, *scal = nullptr;
+    double* pinned = nullptr;
+    int partial_blocks = 0;
+    // V-cycle graph I/O
+    double *vin = nullptr, *vout = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches[2] = {0, 0};
+    // solve plumbing (finest level)
+    DevCSR Mv, KfD;
+    int *vel_rows = nullptr;    // free velocity row -> full velocity index
+    double *F = nullptr, *bvec = nullptr, *xvec = nullptr, *ones = nullptr, *pint = nullptr, *gzero = nullptr;
+    double pint_sum = 0;
+    // stats / profiling
+    stokes_mg_stats st;
+    long long launches = 0;
+    Prof prof[5];
+    bool capturing = false;
+    bool host_only = false;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+enum ProfKind { PK_PATCH = 0, PK_SPMV = 1, PK_GJ = 2, PK_PULL = 3, PK_TRANSFER = 4 };
+
+template <typename F>
+void launch(stokes_mg* h, int kind, cudaStream_t s, F&& f) {
+    Prof* p = (kind >= 0 && kind < 5) ? &h->prof[kind] : nullptr;
+    bool ev = p && p->on && !h->capturing;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ev) {
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        CK(cudaEventRecord(a, s));
+    }
+    f();
+    CK(cudaGetLastError());
+    h->launches++;
+    if (ev) {
+        CK(cudaEventRecord(b, s));
+        p->pending.push_back({a, b});
+        p->launches++;
+    }
+}
+
+template <typename T>
+T* track(stokes_mg* h, T* p) {
+    h->allocs.push_back((void*)p);
+    return p;
+}
+
+int choose_lanes(const DevCSR& A) {
+    double avg = A.nr ? (double)A.nnz / A.nr : 1;
+    if (avg <= 6) return 4;
+    if (avg <= 12) return 8;
+    if (avg <= 48) return 16;
+    return 32;
+}
+
+DevCSR upload_csr(stokes_mg* h, const sfem::CSR& A, bool want32, cudaStream_t s) {
+    DevCSR d;
+    d.nr = A.nr;
+    d.nc = A.ncol;
+    d.nnz = A.nnz();
+    d.rp = track(h, dupload(A.rp, s));
+    d.ci = track(h, dupload(A.ci, s));
+    d.v64 = track(h, dupload(A.v, s));
+    if (want32) {
+        d.v32 = track(h, dalloc<float>(d.nnz));
+        skern::convert_vec<float, double><<<grid_for(d.nnz), 256, 0, s>>>((int)d.nnz, d.v64, d.v32);
+        CK(cudaGetLastError());
+    }
+    d.lanes = choose_lanes(d);
+    return d;
+}
+
+template <typename T>
+const T* vals(const DevCSR& A);
+template <>
+const double* vals<double>(const DevCSR& A) { return A.v64; }
+template <>
+const float* vals<float>(const DevCSR& A) { return A.v32; }
+
+template <typename T, int MODE>
+void spmv_lanes(const DevCSR& A, const T* x, T* y, const T* b, cudaStream_t s) {
+    const long long threads = (long long)A.nr * A.lanes;
+    const int grid = (int)((threads + 255) / 256);
+    if (A.nr == 0) return;
+    switch (A.lanes) {
+        case 4: skern::spmv_csr<T, 4, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
+        case 8: skern::spmv_csr<T, 8, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
+        case 16: skern::spmv_csr<T, 16, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
+        default: skern::spmv_csr<T, 32, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
+    }
+}
+
+template <typename T>
+void spmv(stokes_mg* h, int kind, const DevCSR& A, int mode, const T* x, T* y, const T* b, cudaStream_t s) {
+    launch(h, kind, s, [&] {
+        if (mode == skern::SPMV_SET) spmv_lanes<T, skern::SPMV_SET>(A, x, y, b, s);
+        else if (mode == skern::SPMV_ADD) spmv_lanes<T, skern::SPMV_ADD>(A, x, y, b, s);
+        else spmv_lanes<T, skern::SPMV_RESID>(A, x, y, b, s);
+    });
+}
+
+// ---- per-precision accessors of a level
+template <typename T> struct LV;
+template <> struct LV<double> {
+    static double* b(DevLevel& l) { return l.b64; }
+    static double* e(DevLevel& l) { return l.e64; }
+    static double* r(DevLevel& l) { return l.r64; }
+    static double* d(DevLevel& l) { return l.d64; }
+    static double* t(DevLevel& l) { return l.t64; }
+    static double* u(DevLevel& l) { return l.u64; }
+};
+template <> struct LV<float> {
+    static float* b(DevLevel& l) { return l.b32; }
+    static float* e(DevLevel& l) { return l.e32; }
+    static float* r(DevLevel& l) { return l.r32; }
+    static float* d(DevLevel& l) { return l.d32; }
+    static float* t(DevLevel& l) { return l.t32; }
+    static float* u(DevLevel& l) { return l.u32; }
+};
+
+// one ASM sweep: Y = W_i K_i^{-1} I_i r for every patch, then
+// out = alpha * sum_i I_i^T Y_i + beta * out
+template <typename T>
+void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, double beta, cudaStream_t s);
+
+template <>
+void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
+    const int ld4max = (l.maxn + 3) / 4;
+    const int block = std::min(256, std::max(32, (ld4max + 31) / 32 * 32));
+    launch(h, PK_PATCH, s, [&] {
+        skern::patch_apply_f32<<<l.npatch, block, l.maxn * sizeof(float), s>>>(l.npatch, l.poff, l.pdofs, l.ioff32, l.inv32,
+                                                                              r, l.wt32, l.Y32);
+    });
+    launch(h, PK_PULL, s, [&] {
+        skern::pull_scatter<float><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y32, (float)alpha, (float)beta, out);
+    });
+}
+
+template <>
+void asm_apply<double>(stokes_mg* h, DevLevel& l, const double* r, double* out, double alpha, double beta, cudaStream_t s) {
+    const int ld2max = (l.maxn + 1) / 2;
+    const int block = std::min(256, std::max(32, (ld2max + 31) / 32 * 32));
+    launch(h, PK_PATCH, s, [&] {
+        skern::patch_apply_f64<<<l.npatch, block, l.maxn * sizeof(double), s>>>(l.npatch, l.poff, l.pdofs, l.ioff64, l.inv64,
+                                                                                r, l.wt64, l.Y64);
+    });
+    launch(h, PK_PULL, s, [&] {
+        skern::pull_scatter<double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y64, alpha, beta, out);
+    });
+}
+
+template <typename T>
+void axpby_l(stokes_mg* h, int n, double a, const T* x, double b, T* y, cudaStream_t s) {
+    launch(h, -1, s, [&] { skern::axpby<T><<<grid_for(n), 256, 0, s>>>(n, (T)a, x, (T)b, y); });
+}
+
+// Chebyshev(nu) preconditioned by one ASM sweep per step, on [lo, hi]*lmax
+// (three-term recurrence); x_zero: x starts at 0.
+template <typename T>
+void smooth(stokes_mg* h, int li, const T* b, T* x, bool x_zero, int nu, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    const double a = h->opts.cheb_lo * l.lmax, bb = h->opts.cheb_hi * l.lmax;
+    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    T* r = LV<T>::r(l);
+    const T* rin;
+    if (x_zero) {
+        rin = b;
+    } else {
+        spmv<T>(h, PK_SPMV, l.K, skern::SPMV_RESID, x, r, b, s);
+        rin = r;
+    }
+    if (nu == 1) {
+        asm_apply<T>(h, l, rin, x, 1.0 / theta, x_zero ? 0.0 : 1.0, s);
+        return;
+    }
+    T* d = LV<T>::d(l);
+    asm_apply<T>(h, l, rin, d, 1.0 / theta, 0.0, s);
+    if (x_zero) {
+        CK(cudaMemcpyAsync(x, d, sizeof(T) * l.n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(r, b, sizeof(T) * l.n, cudaMemcpyDeviceToDevice, s));
+    } else {
+        axpby_l<T>(h, l.n, 1.0, d, 1.0, x, s);
+    }
+    for (int i = 1; i < nu; ++i) {
+        spmv<T>(h, PK_SPMV, l.K, skern::SPMV_RESID, d, r, r, s);    // r -= K d
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        asm_apply<T>(h, l, r, d, 2.0 * rho_new / delta, rho_new * rho, s);
+        axpby_l<T>(h, l.n, 1.0, d, 1.0, x, s);
+        rho = rho_new;
+    }
+}
+
+template <typename T>
+void coarse_apply(stokes_mg* h, const T* b, T* e, cudaStream_t s);
+
+template <>
+void coarse_apply<double>(stokes_mg* h, const double* b, double* e, cudaStream_t s) {
+    const int n = h->nc;
+    launch(h, -1, s, [&] { skern::dense_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, n, n + 1, h->Cinv, b, e); });
+}
+template <>
+void coarse_apply<float>(stokes_mg* h, const float* b, float* e, cudaStream_t s) {
+    const int n = h->nc;
+    launch(h, -1, s, [&] { skern::convert_vec<double, float><<<grid_for(n), 256, 0, s>>>(n, b, h->cb64); });
+    launch(h, -1, s, [&] { skern::dense_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, n, n + 1, h->Cinv, h->cb64, h->ce64); });
+    launch(h, -1, s, [&] { skern::convert_vec<float, double><<<grid_for(n), 256, 0, s>>>(n, h->ce64, e); });
+}
+
+// hMG V-cycle (Eq. 3.1, Fig. 2) on level li from e = 0
+template <typename T>
+void hcycle(stokes_mg* h, int li, const T* b, T* e, cudaStream_t s) {
+    const int last = (int)h->L.size() - 1;
+    if (li == last) { coarse_apply<T>(h, b, e, s); return; }
+    DevLevel& l = h->L[li];
+    DevLevel& c = h->L[li + 1];
+    const int nu = h->opts.nu_h;
+    smooth<T>(h, li, b, e, true, nu, s);
+    spmv<T>(h, PK_SPMV, l.K, skern::SPMV_RESID, e, LV<T>::r(l), b, s);
+    spmv<T>(h, PK_TRANSFER, l.R, skern::SPMV_SET, LV<T>::r(l), LV<T>::b(c), (const T*)nullptr, s);
+    hcycle<T>(h, li + 1, LV<T>::b(c), LV<T>::e(c), s);
+    spmv<T>(h, PK_TRANSFER, l.P, skern::SPMV_ADD, LV<T>::e(c), e, (const T*)nullptr, s);
+    smooth<T>(h, li, b, e, false, nu, s);
+}
+
+// phMG cycle: defect correction (Eq. 3.2) on the p-levels; the first hMG
+// level runs n_V hMG cycles, each on the current defect.
+template <typename T>
+void pcycle(stokes_mg* h, int li, const T* b, T* e, cudaStream_t s) {
+    const int last = (int)h->L.size() - 1;
+    if (li == last) { coarse_apply<T>(h, b, e, s); return; }
+    DevLevel& l = h->L[li];
+    if (!l.p_level) {
+        hcycle<T>(h, li, b, e, s);
+        for (int t = 1; t < h->opts.n_V; ++t) {
+            spmv<T>(h, PK_SPMV, l.K, skern::SPMV_RESID, e, LV<T>::t(l), b, s);
+            hcycle<T>(h, li, LV<T>::t(l), LV<T>::u(l), s);
+            axpby_l<T>(h, l.n, 1.0, LV<T>::u(l), 1.0, e, s);
+        }
+        return;
+    }
+    DevLevel& c = h->L[li + 1];
+    const int nu = h->opts.nu_p;
+    smooth<T>(h, li, b, e, true, nu, s);
+    spmv<T>(h, PK_SPMV, l.K, skern::SPMV_RESID, e, LV<T>::r(l), b, s);
+    spmv<T>(h, PK_TRANSFER, l.R, skern::SPMV_SET, LV<T>::r(l), LV<T>::b(c), (const T*)nullptr, s);
+    pcycle<T>(h, li + 1, LV<T>::b(c), LV<T>::e(c), s);
+    spmv<T>(h, PK_TRANSFER, l.P, skern::SPMV_ADD, LV<T>::e(c), e, (const T*)nullptr, s);
+    smooth<T>(h, li, b, e, false, nu, s);
+}
+
+// vout = B_MG vin in the requested precision (vin/vout are the FP64 graph I/O buffers)
+void vcycle_body(stokes_mg* h, int prec, cudaStream_t s) {
+    DevLevel& l0 = h->L[0];
+    const int n = l0.n;
+    if (prec == STOKES_FP64) {
+        pcycle<double>(h, 0, h->vin, h->vout, s);
+    } else {
+        launch(h, -1, s, [&] { skern::convert_vec<float, double><<<grid_for(n), 256, 0, s>>>(n, h->vin, l0.b32); });
+        pcycle<float>(h, 0, l0.b32, l0.e32, s);
+        launch(h, -1, s, [&] { skern::convert_vec<double, float><<<grid_for(n), 256, 0, s>>>(n, l0.e32, h->vout); });
+    }
+}
+
+void vcycle_run(stokes_mg* h, int prec, cudaStream_t s) {
+    // per-launch events cannot sit inside a replayed graph: profiling any
+    // V-cycle kernel class runs the V-cycle as plain launches
+    const bool any_prof = h->prof[PK_PATCH].on || h->prof[PK_SPMV].on || h->prof[PK_PULL].on || h->prof[PK_TRANSFER].on;
+    if (h->graph[prec] && !any_prof) {
+        CK(cudaGraphLaunch(h->graph[prec], s));
+        h->launches += h->graph_launches[prec];
+    } else {
+        vcycle_body(h, prec, s);
+    }
+}
+
+void capture_graph(stokes_mg* h, int prec, cudaStream_t s) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    long long before = h->launches;
+    h->capturing = true;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        vcycle_body(h, prec, cs);
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cs, &dummy);
+        h->capturing = false;
+        cudaStreamDestroy(cs);
+        throw;
+    }
+    CK(cudaStreamEndCapture(cs, &g));
+    h->capturing = false;
+    h->graph_launches[prec] = h->launches - before;
+    h->launches = before;
+    CK(cudaGraphInstantiate(&h->graph[prec], g, 0));
+    CK(cudaGraphDestroy(g));
+    CK(cudaStreamDestroy(cs));
+    (void)s;
+}
+
+// ---- reductions for FGMRES / Arnoldi (FP64, deterministic two-stage)
+void mdot(stokes_mg* h, int n, int m, const double* V, long long ldv, const double* w, double* out, double* acc,
+          bool sqrt_out, cudaStream_t s) {
+    launch(h, -1, s, [&] { skern::mdot_partial<<<h->partial_blocks, 256, 0, s>>>(n, m, V, ldv, w, h->partial); });
+    launch(h, -1, s, [&] { skern::mdot_final<<<1, 32, 0, s>>>(h->partial_blocks, m, h->partial, out, acc, sqrt_out ? 1 : 0); });
+}
+
+void maxpy_l(stokes_mg* h, int n, int m, const double* V, long long ldv, const double* hh, double sign, double* w,
+             cudaStream_t s) {
+    launch(h, -1, s, [&] { skern::maxpy<<<grid_for(n), 256, 0, s>>>(n, m, V, ldv, hh, sign, w); });
+}
+
+// orthogonalise w (length n) against V[0..m-1] by classical Gram-Schmidt
+// applied twice; h[0..m-1] receives the coefficients, hn[0] = ||w|| after.
+void cgs2(stokes_mg* h, int n, int m, const double* V, double* w, double* hcoef, double* h2, double* hn, cudaStream_t s) {
+    mdot(h, n, m, V, n, w, hcoef, nullptr, false, s);
+    maxpy_l(h, n, m, V, n, hcoef, -1.0, w, s);
+    mdot(h, n, m, V, n, w, h2, hcoef, false, s);
+    maxpy_l(h, n, m, V, n, h2, -1.0, w, s);
+    mdot(h, n, 1, w, n, w, hn, nullptr, true, s);
+}
+
+double d2h_scalar(stokes_mg* h, const double* d, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h->pinned, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return h->pinned[0];
+}
+
+// Arnoldi lambda_max on level li from v0 (device, FP64): returns the largest
+// real part of the Ritz values.
+double arnoldi_lmax(stokes_mg* h, int li, const double* v0, int steps, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    const int n = l.n;
+    const int m = std::min(steps, std::min(n, 16));
+    double* V = h->V;     // reuse the FGMRES basis (>= m+1 vectors of length >= n)
+    double* Hs = h->Hh;   // (m+1) x m
+    launch(h, -1, s, [&] { skern::fill_vec<double><<<1, 256, 0, s>>>((long long)(m + 1) * m, 0.0, Hs); });
+    mdot(h, n, 1, v0, n, v0, h->hn, nullptr, true, s);
+    launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, v0, h->hn, V); });
+    int used = m;
+    for (int j = 0; j < m; ++j) {
+        double* w = V + (long long)(j + 1) * n;
+        spmv<double>(h, PK_SPMV, l.K, skern::SPMV_SET, V + (long long)j * n, l.t64, nullptr, s);
+        asm_apply<double>(h, l, l.t64, w, 1.0, 0.0, s);
+        cgs2(h, n, j + 1, V, w, h->h, h->y, h->hn, s);
+        launch(h, -1, s, [&] { skern::arnoldi_store<<<1, 1, 0, s>>>(j, m, Hs, h->h, h->hn); });
+        // breakdown test on the host (setup only): H[j+1][j] <= 1e-14 |H[j][j]|
+        double hnorm = d2h_scalar(h, h->hn, s);
+        double hjj = std::fabs(d2h_scalar(h, h->h + j, s));
+        if (!std::isfinite(hnorm)) throw StokesError(STOKES_ENONFINITE, "non-finite Arnoldi norm");
+        if (hnorm <= 1e-14 * hjj + 1e-300) { used = j + 1; break; }
+        launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, h->hn, w); });
+    }
+    launch(h, -1, s, [&] { skern::hessenberg_max_real_eig<<<1, 1, 0, s>>>(used, m, Hs, h->scal); });
+    CK(cudaMemcpyAsync(h->pinned, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return h->pinned[0];
+}
+
+// SplitMix64 start vector (the same counter-based definition as the tests'
+// generator): value i of stream `st` in [-1, 1).
+__global__ void splitmix_uniform(int n, unsigned long long seed, unsigned long long st, double* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (st * (1ULL << 32) + (unsigned long long)i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z = z ^ (z >> 31);
+        out[i] = (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+    }
+}
+
+// FGMRES(restart) right-preconditioned by the V-cycle (Sec. 4), x0 = 0.
+int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, double* rel_out, cudaStream_t s) {
+    DevLevel& l0 = h->L[0];
+    const int n = l0.n, m = h->restart;
+    const int prec = h->opts.precision;
+    launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(n), 256, 0, s>>>(n, 0.0, x); });
+    mdot(h, n, 1, b, n, b, h->hn, nullptr, true, s);
+    const double beta0 = d2h_scalar(h, h->hn, s);
+    if (!std::isfinite(beta0)) throw StokesError(STOKES_ENONFINITE, "non-finite right-hand side");
+    int its = 0;
+    double rel = 0.0;
+    if (beta0 == 0.0) {
+        if (its_out) *its_out = 0;
+        if (rel_out) *rel_out = 0.0;
+        return STOKES_OK;
+    }
+    double* r = l0.t64;
+    const double* rcur = b;
+    double beta = beta0;
+    bool converged = false;
+    std::vector<double> g0(m + 1, 0.0);
+    while (its < h->opts.maxit) {
+        // V[0] = r / beta, g = (beta, 0, ...)
+        g0.assign(m + 1, 0.0);
+        g0[0] = beta;
+        CK(cudaMemcpyAsync(h->g, g0.data(), sizeof(double) * (m + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->scal, &g0[0], sizeof(double), cudaMemcpyHostToDevice, s));
+        launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, rcur, h->scal, h->V); });
+        CK(cudaStreamSynchronize(s));   // g0 is a host temporary
+        int jend = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = h->V + (long long)j * n;
+            double* zj = h->Z + (long long)j * n;
+            double* w = h->V + (long long)(j + 1) * n;
+            CK(cudaMemcpyAsync(h->vin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            vcycle_run(h, prec, s);
+            CK(cudaMemcpyAsync(zj, h->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            spmv<double>(h, PK_SPMV, l0.K, skern::SPMV_SET, zj, w, nullptr, s);
+            cgs2(h, n, j + 1, h->V, w, h->h, h->y, h->hn, s);
+            launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, h->hn, w); });
+            launch(h, -1, s, [&] {
+                skern::fgmres_givens<<<1, 1, 0, s>>>(j, m, h->Hh, h->h, h->hn, h->cs, h->sn, h->g, h->resid);
+            });
+            const double res = d2h_scalar(h, h->resid, s);
+            ++its;
+            jend = j + 1;
+            if (!std::isfinite(res)) throw StokesError(STOKES_ENONFINITE, "non-finite FGMRES residual");
+            rel = res / beta0;
+            if (res <= tol * beta0) { converged = true; break; }
+            if (its >= h->opts.maxit) break;
+        }
+        launch(h, -1, s, [&] { skern::fgmres_backsolve<<<1, 1, 0, s>>>(jend, m, h->Hh, h->g, h->y); });
+        maxpy_l(h, n, jend, h->Z, n, h->y, 1.0, x, s);
+        if (converged) break;
+        spmv<double>(h, PK_SPMV, l0.K, skern::SPMV_RESID, x, r, b, s);
+        mdot(h, n, 1, r, n, r, h->hn, nullptr, true, s);
+        beta = d2h_scalar(h, h->hn, s);
+        rel = beta / beta0;
+        if (beta <= tol * beta0) { converged = true; break; }
+        rcur = r;
+    }
+    if (its_out) *its_out = its;
+    if (rel_out) *rel_out = rel;
+    return converged ? STOKES_OK : STOKES_ENOTCONVERGED;
+}
+
+// ---------------------------------------------------------------- setup --
+void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
+    const sfem::Level& HL = h->H.levels[li];
+    DevLevel& l = h->L[li];
+    l.n = HL.n_free;
+    l.p_level = HL.p_level;
+    l.K = upload_csr(h, HL.K, want32, s);
+    const bool last = li + 1 == (int)h->H.levels.size();
+    if (!last) {
+        l.P = upload_csr(h, HL.P, want32, s);
+        l.R = upload_csr(h, HL.R, want32, s);
+        l.npatch = (int)HL.patch_off.size() - 1;
+        l.nent = HL.patch_dofs.size();
+        std::vector<long long> moff(l.npatch + 1, 0), o64(l.npatch + 1, 0), o32(l.npatch + 1, 0);
+        l.maxn = 0;
+        for (int p = 0; p < l.npatch; ++p) {
+            const long long n = HL.patch_off[p + 1] - HL.patch_off[p];
+            l.maxn = std::max<int>(l.maxn, (int)n);
+            moff[p + 1] = moff[p] + n * n;
+            o64[p + 1] = o64[p] + ((n + 1) & ~1LL) * n;
+            o32[p + 1] = o32[p] + ((n + 3) & ~3LL) * n;
+        }
+        l.nsq = moff[l.npatch];
+        l.ninv64 = o64[l.npatch];
+        l.ninv32 = o32[l.npatch];
+        l.poff = track(h, dupload(HL.patch_off, s));
+        l.pdofs = track(h, dupload(HL.patch_dofs, s));
+        l.moff = track(h, dupload(moff, s));
+        l.ioff64 = track(h, dupload(o64, s));
+        l.ioff32 = track(h, dupload(o32, s));
+        // partition of unity W_i = diag(1/m_j) and the DoF -> slot map
+        std::vector<int> mult(l.n, 0);
+        for (int x : HL.patch_dofs) mult[x]++;
+        std::vector<double> wt(l.n);
+        for (int j = 0; j < l.n; ++j) wt[j] = mult[j] ? 1.0 / mult[j] : 0.0;
+        std::vector<int> soff(l.n + 1, 0), sidx(l.nent);
+        for (int j = 0; j < l.n; ++j) soff[j + 1] = soff[j] + mult[j];
+        std::vector<int> fill(soff.begin(), soff.end() - 1);
+        for (long long q = 0; q < l.nent; ++q) sidx[fill[HL.patch_dofs[q]]++] = (int)q;
+        l.wt64 = track(h, dupload(wt, s));
+        l.soff = track(h, dupload(soff, s));
+        l.sidx = track(h, dupload(sidx, s));
+        l.Y64 = track(h, dalloc<double>(l.nent));
+        l.inv64 = track(h, dalloc<double>(l.ninv64));
+        if (want32) {
+            l.wt32 = track(h, dalloc<float>(l.n));
+            skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.wt64, l.wt32);
+            CK(cudaGetLastError());
+            l.Y32 = track(h, dalloc<float>(l.nent));
+            l.inv32 = track(h, dalloc<float>(l.ninv32));
+        }
+    }
+    l.b64 = track(h, dalloc<double>(l.n)); l.e64 = track(h, dalloc<double>(l.n)); l.r64 = track(h, dalloc<double>(l.n));
+    l.d64 = track(h, dalloc<double>(l.n)); l.t64 = track(h, dalloc<double>(l.n)); l.u64 = track(h, dalloc<double>(l.n));
+    if (want32) {
+        l.b32 = track(h, dalloc<float>(l.n)); l.e32 = track(h, dalloc<float>(l.n)); l.r32 = track(h, dalloc<float>(l.n));
+        l.d32 = track(h, dalloc<float>(l.n)); l.t32 = track(h, dalloc<float>(l.n)); l.u32 = track(h, dalloc<float>(l.n));
+    }
+}
+
+// gather K_i and invert every patch of level li; work receives the
+// row-major inverses (sum n_i^2 doubles) when keep != nullptr.
+void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* status, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    if (l.npatch == 0) return;
+    launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(l.nsq), 256, 0, s>>>(l.nsq, 0.0, work); });
+    launch(h, -1, s, [&] {
+        skern::patch_gather<<<l.npatch, 256, l.maxn * sizeof(int), s>>>(l.npatch, l.poff, l.pdofs, l.moff, l.K.rp, l.K.ci,
+                                                                       l.K.v64, work);
+    });
+    const int nsm = std::min(l.maxn, skern::GJ_SMEM_MAX_N);
+    const size_t smem = (size_t)nsm * nsm * sizeof(double) + nsm * sizeof(double) + nsm * sizeof(int) + 64;
+    CK(cudaFuncSetAttribute(skern::gj_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch(h, PK_GJ, s, [&] {
+        skern::gj_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, l.poff, l.moff, work, store ? l.ioff64 : nullptr,
+                                                           store ? l.inv64 : nullptr, store ? l.ioff32 : nullptr,
+                                                           store ? l.inv32 : nullptr, status, 0);
+    });
+    if (l.maxn > skern::GJ_SMEM_MAX_N) {
+        int* ipiv = dalloc<int>(l.nent);
+        double* col = dalloc<double>(l.nent);
+        launch(h, PK_GJ, s, [&] {
+            skern::gj_inverse_global<<<l.npatch, 512, 0, s>>>(l.npatch, l.poff, l.moff, work, store ? l.ioff64 : nullptr,
+                                                              store ? l.inv64 : nullptr, store ? l.ioff32 : nullptr,
+                                                              store ? l.inv32 : nullptr, status, ipiv, col);
+        });
+        CK(cudaStreamSynchronize(s));
+        cudaFree(ipiv);
+        cudaFree(col);
+    }
+}
+
+void setup_patches(stokes_mg* h, cudaStream_t s) {
+    for (int li = 0; li + 1 < (int)h->L.size(); ++li) {
+        DevLevel& l = h->L[li];
+        if (l.npatch == 0) continue;
+        double* work = dalloc<double>(l.nsq);
+        int* status = dalloc<int>(l.npatch);
+        CK(cudaMemsetAsync(status, 0, sizeof(int) * l.npatch, s));
+        try {
+            gather_and_invert(h, li, work, true, status, s);
+            std::vector<int> hs(l.npatch);
+            CK(cudaMemcpyAsync(hs.data(), status, sizeof(int) * l.npatch, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int p = 0; p < l.npatch; ++p)
+                if (hs[p] != 0) {
+                    h->st.singular_patch = li * (1 << 24) + p;
+                    throw StokesError(STOKES_ESINGULAR, "zero pivot in patch " + std::to_string(p) + " of level " +
+                                                            std::to_string(li));
+                }
+        } catch (...) {
+            cudaFree(work);
+            cudaFree(status);
+            throw;
+        }
+        cudaFree(work);
+        cudaFree(status);
+    }
+}
+
+void setup_coarse(stokes_mg* h, cudaStream_t s) {
+    const sfem::Level& C = h->H.levels.back();
+    const int n = C.n_free, nb = n + 1;
+    h->nc = n;
+    std::vector<double> A((size_t)nb * nb, 0.0);
+    for (int r = 0; r < n; ++r)
+        for (int p = C.K.rp[r]; p < C.K.rp[r + 1]; ++p) A[(size_t)r * nb + C.K.ci[p]] = C.K.v[p];
+    // border with c_j = int psi_j on the pressure DoFs (zero-mean pressure, Sec. 2)
+    for (int q = 0; q < C.nQ; ++q) {
+        const int r = C.d * C.nVf + q;
+        A[(size_t)r * nb + n] = C.pint[q];
+        A[(size_t)n * nb + r] = C.pint[q];
+    }
+    h->Cinv = track(h, dupload(A, s));
+    int* ipiv = dalloc<int>(nb);
+    double* colk = dalloc<double>(nb);
+    int* status = dalloc<int>(1);
+    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    const long long tot = (long long)nb * nb;
+    const int egrid = (int)std::min<long long>((tot + 255) / 256, 152LL * 8);
+    for (int k = 0; k < nb; ++k) {
+        launch(h, PK_GJ, s, [&] { skern::gj_step_pivot<<<1, 256, 0, s>>>(nb, k, h->Cinv, ipiv, colk, status); });
+        launch(h, PK_GJ, s, [&] { skern::gj_step_eliminate<<<egrid, 256, 0, s>>>(nb, k, h->Cinv, colk); });
+    }
+    launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, ipiv); });
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(ipiv);
+    cudaFree(colk);
+    cudaFree(status);
+    if (hs != 0) {
+        h->st.singular_patch = -2;
+        throw StokesError(STOKES_ESINGULAR, "zero pivot in the coarse bordered LU");
+    }
+    h->cb64 = track(h, dalloc<double>(n));
+    h->ce64 = track(h, dalloc<double>(n));
+}
+
+void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
+    const sfem::Level& F = h->H.levels[0];
+    const int d = F.d;
+    h->Mv = upload_csr(h, F.Mv, false, s);
+    h->KfD = upload_csr(h, F.KfD, false, s);
+    std::vector<int> rows(d * F.nVf);
+    std::vector<int> vrow(F.nVf);
+    for (int i = 0; i < F.V.n; ++i)
+        if (F.vfree[i] >= 0) vrow[F.vfree[i]] = i;
+    for (int c = 0; c < d; ++c)
+        for (int f = 0; f < F.nVf; ++f) rows[c * F.nVf + f] = c * F.V.n + vrow[f];
+    h->vel_rows = track(h, dupload(rows, s));
+    h->F = track(h, dalloc<double>((size_t)d * F.V.n));
+    h->gzero = track(h, dalloc<double>((size_t)d * F.V.n));
+    CK(cudaMemsetAsync(h->gzero, 0, sizeof(double) * d * F.V.n, s));
+    h->bvec = track(h, dalloc<double>(F.n_free));
+    h->xvec = track(h, dalloc<double>(F.n_free));
+    std::vector<double> ones(F.nQ, 1.0);
+    h->ones = track(h, dupload(ones, s));
+    h->pint = track(h, dupload(F.pint, s));
+    h->pint_sum = 0;
+    for (double v : F.pint) h->pint_sum += v;
+}
+
+void fill_stats(stokes_mg* h) {
+    stokes_mg_stats& st = h->st;
+    st.n_levels = (int)h->H.levels.size();
+    st.dim = h->dim;
+    st.family = h->family;
+    st.k = h->k;
+    for (int i = 0; i < st.n_levels; ++i) {
+        const sfem::Level& HL = h->H.levels[i];
+        st.n_free[i] = HL.n_free;
+        st.degree[i] = HL.k;
+        st.level_family[i] = HL.family;
+        st.mesh_index[i] = HL.mesh_index;
+        st.is_p_level[i] = HL.p_level ? 1 : 0;
+        st.nnz[i] = HL.K.nnz();
+        const int np = HL.patch_off.empty() ? 0 : (int)HL.patch_off.size() - 1;
+        long long sq = 0;
+        int mx = 0;
+        for (int p = 0; p < np; ++p) {
+            const long long n = HL.patch_off[p + 1] - HL.patch_off[p];
+            sq += n * n;
+            mx = std::max<int>(mx, (int)n);
+        }
+        st.n_patches[i] = np;
+        st.max_patch[i] = mx;
+        st.patch_entries[i] = sq;
+        st.lmax[i] = i < (int)h->L.size() ? h->L[i].lmax : 0.0;
+    }
+    st.n_vel_nodes = h->H.levels[0].V.n;
+    st.n_pres_nodes = h->H.levels[0].nQ;
+}
+
+int fail(const StokesError& e) {
+    g_last_error = e.what();
+    return e.code;
+}
+
+template <typename F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const StokesError& e) {
+        return fail(e);
+    } catch (const std::invalid_argument& e) {
+        g_last_error = e.what();
+        return STOKES_EINVAL;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return STOKES_EOOM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return STOKES_EINVAL;
+    }
+}
+
+void require(bool c, const char* msg) {
+    if (!c) throw StokesError(STOKES_EINVAL, msg);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(const stokes_mg* h) {
+        require(!h->host_only, "the handle was built with host_only: no device data");
+        const int dev = h->device;
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// temporary FP32/FP64 conversions for the per-step entry points
+struct Tmp32 {
+    float* p = nullptr;
+    explicit Tmp32(size_t n) { p = dalloc<float>(n); }
+    ~Tmp32() { cudaFree(p); }
+};
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* stokes_last_error(void) { return g_last_error.c_str(); }
+
+void stokes_mg_default_opts(stokes_mg_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->hierarchy = STOKES_HIER_GRADUAL;
+    o->nu_p = o->nu_h = o->n_V = 1;
+    o->eig_steps = 10;
+    o->eig_seed = 0;
+    o->cheb_lo = 0.1;
+    o->cheb_hi = 1.1;
+    o->precision = STOKES_FP64;
+    o->restart = 30;
+    o->maxit = 1000;
+    o->use_graph = 1;
+}
+
+int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_finest, int family, int k,
+                    const stokes_mg_opts* opts, const double* nu_cell, void* stream, stokes_mg_t* out) {
+    g_last_error.clear();
+    if (!out) { g_last_error = "out is NULL"; return STOKES_EINVAL; }
+    *out = nullptr;
+    auto h = std::make_unique<stokes_mg>();
+    std::memset(&h->st, 0, sizeof(h->st));
+    h->st.singular_patch = -1;
+    int rc = guarded([&] {
+        const double t0 = host_ms();
+        require(coarse && coarse->verts && coarse->cells, "mesh is NULL");
+        require(coarse->dim == 2 || coarse->dim == 3, "dim must be 2 or 3");
+        require(coarse->n_verts > 0 && coarse->n_cells > 0, "empty mesh");
+        require(n_refine >= 0 && n_refine <= 8, "n_refine out of range");
+        require(family == STOKES_TH || family == STOKES_SV, "unknown family");
+        require(family == STOKES_TH || barycentric_finest, "Scott-Vogelius needs the barycentric finest mesh");
+        require(k >= 2 && k <= 10, "k must be in [2, 10]");
+        if (opts) h->opts = *opts; else stokes_mg_default_opts(&h->opts);
+        stokes_mg_opts& o = h->opts;
+        require(o.nu_p >= 1 && o.nu_h >= 1 && o.n_V >= 1 && o.nu_p <= 16 && o.nu_h <= 16 && o.n_V <= 16, "bad sweep counts");
+        require(o.restart >= 1 && o.restart <= 31, "restart must be in [1, 31]");
+        require(o.eig_steps >= 1 && o.eig_steps <= 15, "eig_steps must be in [1, 15]");
+        require(o.precision == STOKES_FP64 || o.precision == STOKES_MIXED, "bad precision");
+        require(o.cheb_hi > o.cheb_lo && o.cheb_lo > 0, "bad Chebyshev interval");
+        if (!o.host_only) CK(cudaGetDevice(&h->device));
+        cudaStream_t s = (cudaStream_t)stream;
+        h->dim = coarse->dim;
+        h->family = family;
+        h->k = k;
+        h->restart = o.restart;
+        sfem::Mesh cm;
+        cm.d = coarse->dim;
+        cm.nv = coarse->n_verts;
+        cm.nc = coarse->n_cells;
+        cm.X.assign(coarse->verts, coarse->verts + (size_t)cm.nv * cm.d);
+        cm.C.assign(coarse->cells, coarse->cells + (size_t)cm.nc * (cm.d + 1));
+        sfem::HierarchySpec spec;
+        spec.family = family;
+        spec.k = k;
+        spec.n_refine = n_refine;
+        spec.barycentric = barycentric_finest != 0;
+        if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
+        else if (o.hierarchy == STOKES_HIER_GRADUAL) {
+            if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
+            else if (k <= 7) spec.schedule = {k, 4, 2};
+            else spec.schedule = {k, 5, 2};
+        } else if (o.hierarchy == STOKES_HIER_EXPLICIT) {
+            require(o.n_schedule >= 1 && o.n_schedule <= 8 && o.schedule[0] == k, "explicit schedule must start at k");
+            spec.schedule.assign(o.schedule, o.schedule + o.n_schedule);
+            for (size_t i = 1; i < spec.schedule.size(); ++i)
+                require(spec.schedule[i] >= 2 && spec.schedule[i] < spec.schedule[i - 1], "schedule must decrease");
+        } else if (o.hierarchy == STOKES_HIER_HMG) {
+            spec.schedule = {k};
+        } else {
+            require(false, "unknown hierarchy");
+        }
+        require(!(family == STOKES_SV && spec.schedule.size() < 2), "Scott-Vogelius needs at least one p-coarsening");
+        sfem::build_hierarchy(cm, spec, nu_cell, h->H);
+        h->st.t_mesh_ms = h->H.t_mesh_ms;
+        h->st.t_assembly_ms = h->H.t_assembly_ms;
+        const int nl = (int)h->H.levels.size();
+        require(nl >= 2, "the hierarchy needs at least two levels (n_refine >= 1 or a p-coarsening)");
+        if (o.host_only) {
+            h->host_only = true;
+            h->st.t_total_ms = host_ms() - t0;
+            fill_stats(h.get());
+            return STOKES_OK;
+        }
+        const bool want32 = o.precision == STOKES_MIXED;
+        double t1 = host_ms();
+        h->L.assign(nl, DevLevel());
+        for (int li = 0; li < nl; ++li) upload_level(h.get(), li, want32, s);
+        // FGMRES / Arnoldi buffers
+        const int n0 = h->L[0].n;
+        const int m = h->restart;
+        const int basis = std::max(m + 1, 17);
+        h->V = track(h.get(), dalloc<double>((size_t)basis * n0));
+        h->Z = track(h.get(), dalloc<double>((size_t)m * n0));
+        h->Hh = track(h.get(), dalloc<double>((size_t)(basis + 1) * basis));
+        h->cs = track(h.get(), dalloc<double>(basis));
+        h->sn = track(h.get(), dalloc<double>(basis));
+        h->g = track(h.get(), dalloc<double>(basis + 1));
+        h->y = track(h.get(), dalloc<double>(basis + 1));
+        h->h = track(h.get(), dalloc<double>(basis + 1));
+        h->hn = track(h.get(), dalloc<double>(2));
+        h->resid = track(h.get(), dalloc<double>(2));
+        h->scal = track(h.get(), dalloc<double>(4));
+        h->partial_blocks = 152 * 2;
+        h->partial = track(h.get(), dalloc<double>((size_t)h->partial_blocks * 32));
+        h->vin = track(h.get(), dalloc<double>(n0));
+        h->vout = track(h.get(), dalloc<double>(n0));
+        CK(cudaMallocHost((void**)&h->pinned, 64));
+        setup_solve_buffers(h.get(), s);
+        CK(cudaStreamSynchronize(s));
+        h->st.t_upload_ms = host_ms() - t1;
+        t1 = host_ms();
+        setup_patches(h.get(), s);
+        CK(cudaStreamSynchronize(s));
+        h->st.t_gather_lu_ms = host_ms() - t1;
+        t1 = host_ms();
+        setup_coarse(h.get(), s);
+        h->st.t_coarse_ms = host_ms() - t1;
+        t1 = host_ms();
+        double* v0 = dalloc<double>(n0);
+        try {
+            for (int li = 0; li + 1 < nl; ++li) {
+                if (li < 16 && o.lmax_override[li] > 0) { h->L[li].lmax = o.lmax_override[li]; continue; }
+                const int n = h->L[li].n;
+                splitmix_uniform<<<grid_for(n), 256, 0, s>>>(n, o.eig_seed, (unsigned long long)li, v0);
+                CK(cudaGetLastError());
+                h->L[li].lmax = arnoldi_lmax(h.get(), li, v0, o.eig_steps, s);
+                if (!(h->L[li].lmax > 0) || !std::isfinite(h->L[li].lmax))
+                    throw StokesError(STOKES_ENONFINITE, "lambda_max estimate is not positive on level " + std::to_string(li));
+            }
+        } catch (...) {
+            cudaFree(v0);
+            throw;
+        }
+        cudaFree(v0);
+        h->st.t_eig_ms = host_ms() - t1;
+        t1 = host_ms();
+        if (o.use_graph) capture_graph(h.get(), o.precision, s);
+        CK(cudaStreamSynchronize(s));
+        h->st.t_graph_ms = host_ms() - t1;
+        h->st.t_total_ms = host_ms() - t0;
+        fill_stats(h.get());
+        return STOKES_OK;
+    });
+    if (rc != STOKES_OK) {
+        stokes_mg_destroy(h.release());
+        return rc;
+    }
+    *out = h.release();
+    return STOKES_OK;
+}
+
+int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && r_dev && z_dev && nrhs >= 1, "invalid argument");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        const int n = h->L[0].n;
+        for (int q = 0; q < nrhs; ++q) {
+            CK(cudaMemcpyAsync(h->vin, r_dev + (size_t)q * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            vcycle_run(h, h->opts.precision, s);
+            CK(cudaMemcpyAsync(z_dev + (size_t)q * n, h->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        }
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_fgmres(stokes_mg_t h, const double* b, double* x, double tol, int* iterations, double* final_relres,
+                     void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && b && x && tol > 0, "invalid argument");
+        DeviceGuard dg(h);
+        int rc = fgmres(h, b, x, tol, iterations, final_relres, (cudaStream_t)stream);
+        if (rc != STOKES_OK) g_last_error = "FGMRES did not reach the tolerance within maxit";
+        return rc;
+    });
+}
+
+int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, double nu, double tol, double* u,
+                 double* p, int* iterations, double* final_relres, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && f_nodal && u && p, "invalid argument");
+        require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        const sfem::Level& F = h->H.levels[0];
+        const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ, n = F.n_free;
+        // F_c = M f_c
+        for (int c = 0; c < d; ++c)
+            spmv<double>(h, -1, h->Mv, skern::SPMV_SET, f_nodal + (size_t)c * nV, h->F + (size_t)c * nV, nullptr, s);
+        // b_vel = F / nu on the free rows, b_p = 0; then b -= K_{free,D} g
+        launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->F, h->bvec); });
+        if (nu != 1.0) axpby_l<double>(h, d * nVf, 0.0, h->bvec, 1.0 / nu, h->bvec, s);
+        CK(cudaMemsetAsync(h->bvec + (size_t)d * nVf, 0, sizeof(double) * nQ, s));
+        const double* gfull = g_nodal ? g_nodal : h->gzero;
+        spmv<double>(h, -1, h->KfD, skern::SPMV_RESID, gfull, h->bvec, h->bvec, s);
+        // remove the component along the pressure null vector (consistency)
+        mdot(h, nQ, 1, h->bvec + (size_t)d * nVf, nQ, h->ones, h->scal, nullptr, false, s);
+        launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, h->bvec + (size_t)d * nVf, h->scal, (double)nQ); });
+        int rc = fgmres(h, h->bvec, h->xvec, tol, iterations, final_relres, s);
+        // u = g on the boundary, x on the free nodes; p = nu * p' with zero mean
+        CK(cudaMemcpyAsync(u, gfull, sizeof(double) * d * nV, cudaMemcpyDeviceToDevice, s));
+        launch(h, -1, s, [&] { skern::scatter_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->xvec, u); });
+        CK(cudaMemcpyAsync(p, h->xvec + (size_t)d * nVf, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
+        if (nu != 1.0) axpby_l<double>(h, nQ, 0.0, p, nu, p, s);
+        mdot(h, nQ, 1, p, nQ, h->pint, h->scal, nullptr, false, s);
+        launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, p, h->scal, h->pint_sum); });
+        (void)n;
+        if (rc != STOKES_OK) g_last_error = "FGMRES did not reach the tolerance within maxit";
+        return rc;
+    });
+}
+
+int stokes_mg_info(stokes_mg_t h, stokes_mg_stats* st) {
+    if (!h || !st) { g_last_error = "invalid argument"; return STOKES_EINVAL; }
+    fill_stats(h);
+    h->st.kernel_launches = h->launches;
+    *st = h->st;
+    return STOKES_OK;
+}
+
+int stokes_mg_level_dofs(stokes_mg_t h, int level, double* xyz, int* comp, double* cell_center) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && level >= 0 && level < (int)h->H.levels.size() && xyz && comp, "invalid argument");
+        const sfem::Level& L = h->H.levels[level];
+        const int d = L.d;
+        std::vector<int> vrow(L.nVf);
+        for (int i = 0; i < L.V.n; ++i)
+            if (L.vfree[i] >= 0) vrow[L.vfree[i]] = i;
+        for (int r = 0; r < L.n_free; ++r) {
+            const double* x;
+            if (r < d * L.nVf) {
+                comp[r] = r / L.nVf;
+                x = &L.V.X[(size_t)vrow[r % L.nVf] * d];
+            } else {
+                comp[r] = d;
+                x = &L.Q.X[(size_t)(r - d * L.nVf) * d];
+            }
+            for (int c = 0; c < d; ++c) xyz[(size_t)r * d + c] = x[c];
+            if (cell_center) {
+                for (int c = 0; c < d; ++c) cell_center[(size_t)r * d + c] = 0.0;
+                if (r >= d * L.nVf && !L.Q.continuous) {
+                    const int e = L.Q.owner_cell[r - d * L.nVf];
+                    for (int c = 0; c < d; ++c) cell_center[(size_t)r * d + c] = L.cell_center[(size_t)e * d + c];
+                }
+            }
+        }
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_nodes(stokes_mg_t h, double* vel_xyz, double* pres_xyz, double* pres_cell_center) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h, "invalid argument");
+        const sfem::Level& L = h->H.levels[0];
+        const int d = L.d;
+        if (vel_xyz) std::memcpy(vel_xyz, L.V.X.data(), sizeof(double) * L.V.X.size());
+        if (pres_xyz) std::memcpy(pres_xyz, L.Q.X.data(), sizeof(double) * L.Q.X.size());
+        if (pres_cell_center)
+            for (int q = 0; q < L.nQ; ++q)
+                for (int c = 0; c < d; ++c)
+                    pres_cell_center[(size_t)q * d + c] = L.Q.continuous ? 0.0 : L.cell_center[(size_t)L.Q.owner_cell[q] * d + c];
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_get_csr(stokes_mg_t h, int level, int which, int* n_rows, int* n_cols, long long* nnz, int* row_ptr,
+                      int* col, double* val) {
+    g_last_error.clear();
+    return guarded([&] {
+        const int nl = h ? (int)h->H.levels.size() : 0;
+        require(h && level >= 0 && level < nl && which >= 0 && which <= 2, "invalid argument");
+        const sfem::Level& L = h->H.levels[level];
+        require(which == 0 || level + 1 < nl, "no transfer on the coarsest level");
+        const sfem::CSR& A = which == 0 ? L.K : (which == 1 ? L.P : L.R);
+        if (n_rows) *n_rows = A.nr;
+        if (n_cols) *n_cols = A.ncol;
+        if (nnz) *nnz = A.nnz();
+        if (row_ptr) {
+            std::memcpy(row_ptr, A.rp.data(), sizeof(int) * (A.nr + 1));
+            if (col) std::memcpy(col, A.ci.data(), sizeof(int) * A.nnz());
+            if (val) std::memcpy(val, A.v.data(), sizeof(double) * A.nnz());
+        }
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_get_patches(stokes_mg_t h, int level, int* n_patches, long long* n_entries, int* offsets, int* dofs) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && level >= 0 && level + 1 < (int)h->H.levels.size(), "invalid argument");
+        const sfem::Level& HL = h->H.levels[level];
+        if (n_patches) *n_patches = (int)HL.patch_off.size() - 1;
+        if (n_entries) *n_entries = (long long)HL.patch_dofs.size();
+        if (offsets) std::memcpy(offsets, HL.patch_off.data(), sizeof(int) * HL.patch_off.size());
+        if (dofs) std::memcpy(dofs, HL.patch_dofs.data(), sizeof(int) * HL.patch_dofs.size());
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_patch_matrices(stokes_mg_t h, int level, double* out, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && out && level >= 0 && level + 1 < (int)h->L.size(), "invalid argument");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel& l = h->L[level];
+        double* work = dalloc<double>(l.nsq);
+        launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(l.nsq), 256, 0, s>>>(l.nsq, 0.0, work); });
+        launch(h, -1, s, [&] {
+            skern::patch_gather<<<l.npatch, 256, l.maxn * sizeof(int), s>>>(l.npatch, l.poff, l.pdofs, l.moff, l.K.rp,
+                                                                           l.K.ci, l.K.v64, work);
+        });
+        cudaError_t e = cudaMemcpyAsync(out, work, sizeof(double) * l.nsq, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(work);
+        CK(e);
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_patch_inverses(stokes_mg_t h, int level, double* out, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && out && level >= 0 && level + 1 < (int)h->L.size(), "invalid argument");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel& l = h->L[level];
+        double* work = dalloc<double>(l.nsq);
+        int* status = dalloc<int>(l.npatch);
+        cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int) * l.npatch, s);
+        try {
+            gather_and_invert(h, level, work, false, status, s);
+        } catch (...) {
+            cudaFree(work);
+            cudaFree(status);
+            throw;
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, work, sizeof(double) * l.nsq, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(work);
+        cudaFree(status);
+        CK(e);
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_arnoldi_lmax(stokes_mg_t h, int level, const double* v0_dev, int steps, double* lmax, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && v0_dev && lmax && level >= 0 && level + 1 < (int)h->L.size() && steps >= 1 && steps <= 15,
+                "invalid argument");
+        DeviceGuard dg(h);
+        *lmax = arnoldi_lmax(h, level, v0_dev, steps, (cudaStream_t)stream);
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_residual(stokes_mg_t h, int level, const double* b, const double* x, double* r, int precision,
+                       void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && b && x && r && level >= 0 && level < (int)h->L.size(), "invalid argument");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel& l = h->L[level];
+        if (precision == STOKES_FP64) {
+            spmv<double>(h, PK_SPMV, l.K, skern::SPMV_RESID, x, r, b, s);
+        } else {
+            require(l.K.v32, "mixed precision needs a MIXED handle");
+            Tmp32 tb(l.n), tx(l.n), tr(l.n);
+            skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, b, tb.p);
+            skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, x, tx.p);
+            spmv<float>(h, PK_SPMV, l.K, skern::SPMV_RESID, tx.p, tr.p, tb.p, s);
+            skern::convert_vec<double, float><<<grid_for(l.n), 256, 0, s>>>(l.n, tr.p, r);
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaGetLastError());
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_asm(stokes_mg_t h, int level, const double* r, double* z, int precision, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && r && z && level >= 0 && level + 1 < (int)h->L.size(), "invalid argument");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel& l = h->L[level];
+        if (precision == STOKES_FP64) {
+            asm_apply<double>(h, l, r, z, 1.0, 0.0, s);
+        } else {
+            require(l.inv32, "mixed precision needs a MIXED handle");
+            Tmp32 tr(l.n), tz(l.n);
+            skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, r, tr.p);
+            asm_apply<float>(h, l, tr.p, tz.p, 1.0, 0.0, s);
+            skern::convert_vec<double, float><<<grid_for(l.n), 256, 0, s>>>(l.n, tz.p, z);
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaGetLastError());
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_transfer(stokes_mg_t h, int level, int dir, const double* x, double* y, int precision, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && x && y && level >= 0 && level + 1 < (int)h->L.size() && (dir == 0 || dir == 1), "invalid argument");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel& l = h->L[level];
+        const DevCSR& A = dir == 0 ? l.R : l.P;
+        const int mode = dir == 0 ? skern::SPMV_SET : skern::SPMV_ADD;
+        if (precision == STOKES_FP64) {
+            spmv<double>(h, PK_TRANSFER, A, mode, x, y, nullptr, s);
+        } else {
+            require(A.v32, "mixed precision needs a MIXED handle");
+            Tmp32 tx(A.nc), ty(A.nr);
+            skern::convert_vec<float, double><<<grid_for(A.nc), 256, 0, s>>>(A.nc, x, tx.p);
+            skern::convert_vec<float, double><<<grid_for(A.nr), 256, 0, s>>>(A.nr, y, ty.p);
+            spmv<float>(h, PK_TRANSFER, A, mode, tx.p, ty.p, nullptr, s);
+            skern::convert_vec<double, float><<<grid_for(A.nr), 256, 0, s>>>(A.nr, ty.p, y);
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaGetLastError());
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_coarse_solve(stokes_mg_t h, const double* r, double* x, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && r && x, "invalid argument");
+        DeviceGuard dg(h);
+        coarse_apply<double>(h, r, x, (cudaStream_t)stream);
+        return STOKES_OK;
+    });
+}
+
+int stokes_prof_enable(stokes_mg_t h, int kind, int enable) {
+    if (!h || kind < 0 || kind >= 5) { g_last_error = "invalid argument"; return STOKES_EINVAL; }
+    h->prof[kind].on = enable != 0;
+    return STOKES_OK;
+}
+
+int stokes_prof_read(stokes_mg_t h, int kind, long long* launches, double* total_ms) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && kind >= 0 && kind < 5, "invalid argument");
+        Prof& p = h->prof[kind];
+        for (auto& ab : p.pending) {
+            CK(cudaEventSynchronize(ab.second));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ab.first, ab.second));
+            p.total_ms += ms;
+            cudaEventDestroy(ab.first);
+            cudaEventDestroy(ab.second);
+        }
+        p.pending.clear();
+        if (launches) *launches = p.launches;
+        if (total_ms) *total_ms = p.total_ms;
+        return STOKES_OK;
+    });
+}
+
+void stokes_mg_destroy(stokes_mg_t h) {
+    if (!h) return;
+    if (h->host_only || (h->allocs.empty() && !h->pinned)) { delete h; return; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != h->device) cudaSetDevice(h->device);
+    for (auto& p : h->prof)
+        for (auto& ab : p.pending) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+"""CPU parity of the library's host-side setup (meshes, spaces, assembly of
+K, transfers P / R, Vanka-star patches) against the oracle, through the
+C ABI with host_only = 1 (no GPU needed).  Matrices agree entry by entry
+after mapping DoFs by position; patches agree as DoF sets."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multigrid as mg, stokes
+from tests.dofmap import level_perm
+
+P = pytest.importorskip("paper_2407_07253_gb300")
+
+CASES = [
+    # name, coarse mesh, n_refine, family, k, schedule, barycentric
+    ("th_p2_8x8", W.unit_square_mesh(2), 2, 0, 2, [2], False),
+    ("th_p4_8x8", W.unit_square_mesh(2), 2, 0, 4, [4, 2], False),
+    ("th_p4_gradual3", W.unit_square_mesh(2), 1, 0, 4, [4, 3, 2], False),
+    ("sv_p3_alfeld", W.unit_square_mesh(2), 1, 1, 3, [3, 2], True),
+    ("sv_p4_disk", W.delaunay_disk_mesh(0, h=0.5), 1, 1, 4, [4, 2], True),
+    ("th3d_p3", W.kuhn_cube_mesh(1), 1, 0, 3, [3, 2], False),
+]
+
+
+def _build(case):
+    name, (v, c), nref, fam, k, sched, bary = case
+    h = P.StokesMG(v, c, nref, fam, k, barycentric=bary, host_only=1,
+                   hierarchy=P.HIER_EXPLICIT, schedule=sched)
+    ora = mg.Hierarchy(v, c, nref, fam, sched, barycentric=bary, lmax=[1.0] * 16)
+    return h, ora
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_host_hierarchy_matches_oracle(case):
+    h, ora = _build(case)
+    info = h.info()
+    assert info["n_levels"] == len(ora.levels)
+    perms = []
+    for li, L in enumerate(ora.levels):
+        assert info["n_free"][li] == L.disc.n_free
+        perm = level_perm(h, li, L.disc)
+        perms.append(perm)
+        K = h.get_csr(li, 0)
+        Kp = K[perm][:, perm]
+        Ko = L.disc.K
+        scale = abs(Ko).max()
+        assert abs(Kp - Ko).max() <= 1e-12 * scale, (li, abs(Kp - Ko).max())
+    for li, L in enumerate(ora.levels[:-1]):
+        pf, pc = perms[li], perms[li + 1]
+        Pm = h.get_csr(li, 1)[pf][:, pc]
+        assert abs(Pm - L.P).max() <= 1e-13
+        Rm = h.get_csr(li, 2)[pc][:, pf]
+        assert abs(Rm - L.R).max() <= 1e-13
+        off, dofs = h.patches(li)
+        inv = np.argsort(pf)          # library index -> oracle index
+        lib_sets = sorted(tuple(sorted(inv[dofs[off[i]:off[i + 1]]].tolist())) for i in range(len(off) - 1))
+        ora_sets = sorted(tuple(p.tolist()) for p in L.asm.patches)
+        assert lib_sets == ora_sets
+
+
+def test_host_invalid_inputs_are_rejected():
+    v, c = W.unit_square_mesh(2)
+    with pytest.raises(P.StokesError) as e:
+        P.StokesMG(v, c, 1, 0, 1, host_only=1)                 # k < 2
+    assert e.value.code == -1
+    with pytest.raises(P.StokesError):
+        P.StokesMG(v, c, 1, 1, 3, host_only=1)                 # SV without Alfeld
+    bad = c.copy(); bad[0, 0] = 10 ** 6
+    with pytest.raises(P.StokesError):
+        P.StokesMG(v, bad, 1, 0, 2, host_only=1)               # vertex index out of range
+    deg = c.copy(); deg[0] = [0, 0, 1]
+    with pytest.raises(P.StokesError):
+        P.StokesMG(v, deg, 1, 0, 2, host_only=1)               # degenerate cell
+    with pytest.raises(P.StokesError):
+        P.StokesMG(v, c, 0, 0, 2, host_only=1)                 # single level
+
+
+def test_library_exports_every_declared_symbol():
+    """Every function declared in include/stokes_mg.h is exported by the .so."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "stokes_mg.h")).read()
+    names = set(re.findall(r"\b(stokes_[a-z_0-9]+)\s*\(", hdr))
+    lib = P.lib()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing and len(names) >= 20, missing
