@@ -32,6 +32,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="th_p4_64x64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", action="store_true",
+                    help="one mixed-precision setup + solve and exit (profiling driver)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
 
@@ -164,10 +167,10 @@ def main():
     w = W.workload(a.workload)
     stream = torch.cuda.current_stream(dev)
 
-    def make(precision):
+    def make(precision, prof_mask=0):
         return P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
                           hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=precision,
-                          stream=stream.cuda_stream)
+                          stream=stream.cuda_stream, prof_mask=prof_mask)
 
     # forcing in the library's node order (seeded U[-1,1] nodal values)
     probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
@@ -193,10 +196,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = make(precision)
-        if prof is not None:
-            for k in prof:
-                h.prof_enable(k, True)
+        h = make(precision, sum(1 << k for k in (prof or [])))
         if e2e:
             f = f_host.to(dev, non_blocking=True)
         else:
@@ -212,6 +212,12 @@ def main():
         h.close()
         return e0.elapsed_time(e1), its, rel, st, pr
 
+    if a.single:
+        ms, its, rel, st, _ = one_step(P.MIXED if a.precision == "mixed" else P.FP64)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"single_step_ms": ms, "iterations": its, "relres": rel,
+                          "setup_ms": st["t_total_ms"], "launches": st["kernel_launches"]}))
+        return
     # warm-up
     for _ in range(a.warmup):
         one_step(P.MIXED)

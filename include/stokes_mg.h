@@ -86,6 +86,8 @@ typedef struct {
                                CSR operators, transfers, patches) and make no CUDA
                                call; only the info / dofs / nodes / get_csr /
                                get_patches queries are valid on such a handle */
+    int prof_mask;          /* bit k set: time kernel class k (see stokes_prof_enable)
+                               from the start of setup */
 } stokes_mg_opts;
 
 #define STOKES_MAX_LEVELS 16

@@ -251,32 +251,32 @@ __global__ void __launch_bounds__(256) patch_apply_f32(int npatch, const int* __
     const int ld4 = (n + 3) >> 2;
     for (int a = threadIdx.x; a < n; a += blockDim.x) xs32[a] = r[pdofs[s + a]];
     __syncthreads();
-    const int t = threadIdx.x;
-    if (t >= ld4) return;
-    const float4* col = reinterpret_cast<const float4*>(inv + ioff[p]) + t;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int j = 0;
-    for (; j + 4 <= n; j += 4) {
-        const float4 v0 = __ldcs(col + (long long)(j + 0) * ld4);
-        const float4 v1 = __ldcs(col + (long long)(j + 1) * ld4);
-        const float4 v2 = __ldcs(col + (long long)(j + 2) * ld4);
-        const float4 v3 = __ldcs(col + (long long)(j + 3) * ld4);
-        const float x0 = xs32[j], x1 = xs32[j + 1], x2 = xs32[j + 2], x3 = xs32[j + 3];
-        acc.x += v0.x * x0; acc.y += v0.y * x0; acc.z += v0.z * x0; acc.w += v0.w * x0;
-        acc.x += v1.x * x1; acc.y += v1.y * x1; acc.z += v1.z * x1; acc.w += v1.w * x1;
-        acc.x += v2.x * x2; acc.y += v2.y * x2; acc.z += v2.z * x2; acc.w += v2.w * x2;
-        acc.x += v3.x * x3; acc.y += v3.y * x3; acc.z += v3.z * x3; acc.w += v3.w * x3;
-    }
-    for (; j < n; ++j) {
-        const float4 v = __ldcs(col + (long long)j * ld4);
-        const float x = xs32[j];
-        acc.x += v.x * x; acc.y += v.y * x; acc.z += v.z * x; acc.w += v.w * x;
-    }
-    const int a0 = 4 * t;
-    const float o[4] = {acc.x, acc.y, acc.z, acc.w};
+    for (int t = threadIdx.x; t < ld4; t += blockDim.x) {
+        const float4* col = reinterpret_cast<const float4*>(inv + ioff[p]) + t;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        int j = 0;
+        for (; j + 4 <= n; j += 4) {
+            const float4 v0 = __ldcs(col + (long long)(j + 0) * ld4);
+            const float4 v1 = __ldcs(col + (long long)(j + 1) * ld4);
+            const float4 v2 = __ldcs(col + (long long)(j + 2) * ld4);
+            const float4 v3 = __ldcs(col + (long long)(j + 3) * ld4);
+            const float x0 = xs32[j], x1 = xs32[j + 1], x2 = xs32[j + 2], x3 = xs32[j + 3];
+            acc.x += v0.x * x0; acc.y += v0.y * x0; acc.z += v0.z * x0; acc.w += v0.w * x0;
+            acc.x += v1.x * x1; acc.y += v1.y * x1; acc.z += v1.z * x1; acc.w += v1.w * x1;
+            acc.x += v2.x * x2; acc.y += v2.y * x2; acc.z += v2.z * x2; acc.w += v2.w * x2;
+            acc.x += v3.x * x3; acc.y += v3.y * x3; acc.z += v3.z * x3; acc.w += v3.w * x3;
+        }
+        for (; j < n; ++j) {
+            const float4 v = __ldcs(col + (long long)j * ld4);
+            const float x = xs32[j];
+            acc.x += v.x * x; acc.y += v.y * x; acc.z += v.z * x; acc.w += v.w * x;
+        }
+        const int a0 = 4 * t;
+        const float o[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (a0 + q < n) Y[s + a0 + q] = wt[pdofs[s + a0 + q]] * o[q];
+        for (int q = 0; q < 4; ++q)
+            if (a0 + q < n) Y[s + a0 + q] = wt[pdofs[s + a0 + q]] * o[q];
+    }
 }
 
 __global__ void __launch_bounds__(256) patch_apply_f64(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
@@ -289,28 +289,28 @@ __global__ void __launch_bounds__(256) patch_apply_f64(int npatch, const int* __
     const int ld2 = (n + 1) >> 1;
     for (int a = threadIdx.x; a < n; a += blockDim.x) xs64[a] = r[pdofs[s + a]];
     __syncthreads();
-    const int t = threadIdx.x;
-    if (t >= ld2) return;
-    const double2* col = reinterpret_cast<const double2*>(inv + ioff[p]) + t;
-    double2 acc = make_double2(0.0, 0.0);
-    int j = 0;
-    for (; j + 4 <= n; j += 4) {
-        const double2 v0 = __ldcs(col + (long long)(j + 0) * ld2);
-        const double2 v1 = __ldcs(col + (long long)(j + 1) * ld2);
-        const double2 v2 = __ldcs(col + (long long)(j + 2) * ld2);
-        const double2 v3 = __ldcs(col + (long long)(j + 3) * ld2);
-        acc.x += v0.x * xs64[j]; acc.y += v0.y * xs64[j];
-        acc.x += v1.x * xs64[j + 1]; acc.y += v1.y * xs64[j + 1];
-        acc.x += v2.x * xs64[j + 2]; acc.y += v2.y * xs64[j + 2];
-        acc.x += v3.x * xs64[j + 3]; acc.y += v3.y * xs64[j + 3];
+    for (int t = threadIdx.x; t < ld2; t += blockDim.x) {
+        const double2* col = reinterpret_cast<const double2*>(inv + ioff[p]) + t;
+        double2 acc = make_double2(0.0, 0.0);
+        int j = 0;
+        for (; j + 4 <= n; j += 4) {
+            const double2 v0 = __ldcs(col + (long long)(j + 0) * ld2);
+            const double2 v1 = __ldcs(col + (long long)(j + 1) * ld2);
+            const double2 v2 = __ldcs(col + (long long)(j + 2) * ld2);
+            const double2 v3 = __ldcs(col + (long long)(j + 3) * ld2);
+            acc.x += v0.x * xs64[j]; acc.y += v0.y * xs64[j];
+            acc.x += v1.x * xs64[j + 1]; acc.y += v1.y * xs64[j + 1];
+            acc.x += v2.x * xs64[j + 2]; acc.y += v2.y * xs64[j + 2];
+            acc.x += v3.x * xs64[j + 3]; acc.y += v3.y * xs64[j + 3];
+        }
+        for (; j < n; ++j) {
+            const double2 v = __ldcs(col + (long long)j * ld2);
+            acc.x += v.x * xs64[j]; acc.y += v.y * xs64[j];
+        }
+        const int a0 = 2 * t;
+        if (a0 < n) Y[s + a0] = wt[pdofs[s + a0]] * acc.x;
+        if (a0 + 1 < n) Y[s + a0 + 1] = wt[pdofs[s + a0 + 1]] * acc.y;
     }
-    for (; j < n; ++j) {
-        const double2 v = __ldcs(col + (long long)j * ld2);
-        acc.x += v.x * xs64[j]; acc.y += v.y * xs64[j];
-    }
-    const int a0 = 2 * t;
-    if (a0 < n) Y[s + a0] = wt[pdofs[s + a0]] * acc.x;
-    if (a0 + 1 < n) Y[s + a0 + 1] = wt[pdofs[s + a0 + 1]] * acc.y;
 }
 
 // ---------------------------------------------------------- coarse GJ ---
@@ -433,30 +433,27 @@ __global__ void arnoldi_store(int j, int m, double* __restrict__ Hs, const doubl
     Hs[(j + 1) * m + j] = hnorm[0];
 }
 
-struct cplx { double re, im; };
-__device__ inline cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
-__device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ inline cplx cconj(cplx a) { return {a.re, -a.im}; }
-__device__ inline double cabs2(cplx a) { return hypot(a.re, a.im); }
-__device__ inline cplx csqrt2(cplx z) {
+
+__host__ __device__ inline cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ inline cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__host__ __device__ inline cplx cconj(cplx a) { return {a.re, -a.im}; }
+__host__ __device__ inline double cabs2(cplx a) { return hypot(a.re, a.im); }
+__host__ __device__ inline cplx csqrt2(cplx z) {
     const double r = cabs2(z);
     double re = sqrt(fmax(0.0, 0.5 * (r + z.re)));
     double im = sqrt(fmax(0.0, 0.5 * (r - z.re)));
     if (z.im < 0) im = -im;
     return {re, im};
 }
-__device__ inline cplx cscale(cplx a, double s) { return {a.re * s, a.im * s}; }
+__host__ __device__ inline cplx cscale(cplx a, double s) { return {a.re * s, a.im * s}; }
 
 // Eigenvalues of a small upper Hessenberg matrix by the shifted QR
 // iteration in complex arithmetic (Wilkinson shift from the trailing 2 x 2
-// block, Givens rotations, deflation on negligible subdiagonals).
-__global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict__ Hs, double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    constexpr int MX = 16;
-    __shared__ cplx A[MX][MX];
-    __shared__ cplx cr[MX], sr[MX];
-    const int m = mm < MX ? mm : MX;
+// block, Givens rotations, deflation on negligible subdiagonals).  Writes
+// out[0] = largest real part, out[1] = 0 if converged, 1 otherwise.
+__host__ __device__ void hessenberg_eig_core(int m, int ld, const double* Hs, double* out, cplx (*A)[HESS_MAX],
+                                             cplx* cr, cplx* sr) {
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) A[i][j] = {(j >= i - 1) ? Hs[i * ld + j] : 0.0, 0.0};
     double best = -1e300;
@@ -472,7 +469,6 @@ __global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict
         }
         if (l == hi) { best = fmax(best, A[hi][hi].re); --hi; it = 0; continue; }
         if (++total > 200 * m) { failed = 1; for (int i = 0; i <= hi; ++i) best = fmax(best, A[i][i].re); break; }
-        // Wilkinson shift: eigenvalue of the trailing 2x2 closest to A[hi][hi]
         const cplx a = A[hi - 1][hi - 1], b = A[hi - 1][hi], c = A[hi][hi - 1], d = A[hi][hi];
         const cplx half = cscale(csub(a, d), 0.5);
         const cplx disc = csqrt2(cadd(cmul(half, half), cmul(b, c)));
@@ -507,6 +503,13 @@ __global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict
     }
     out[0] = best;
     out[1] = failed;
+}
+
+__global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict__ Hs, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ cplx A[HESS_MAX][HESS_MAX];
+    __shared__ cplx cr[HESS_MAX], sr[HESS_MAX];
+    hessenberg_eig_core(mm < HESS_MAX ? mm : HESS_MAX, ld, Hs, out, A, cr, sr);
 }
 
 }  // namespace skern

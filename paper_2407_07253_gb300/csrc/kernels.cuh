@@ -153,6 +153,10 @@ __global__ void fgmres_backsolve(int m, int ldh, const double* __restrict__ H, c
 // Arnoldi: store column j of H (h[0..j], hnorm) into Hs [(m+1) x m].
 __global__ void arnoldi_store(int j, int m, double* __restrict__ Hs, const double* __restrict__ h,
                               const double* __restrict__ hnorm);
+constexpr int HESS_MAX = 16;
+struct cplx { double re, im; };
+__host__ __device__ void hessenberg_eig_core(int m, int ld, const double* Hs, double* out, cplx (*A)[HESS_MAX],
+                                             cplx* cr, cplx* sr);
 // largest real part of the eigenvalues of the leading mm x mm block of the
 // upper Hessenberg Hs (complex shifted QR iteration), out[0]; out[1] = 0 if
 // converged, 1 otherwise.

@@ -698,8 +698,8 @@ void setup_coarse(stokes_mg* h, cudaStream_t s) {
     const long long tot = (long long)nb * nb;
     const int egrid = (int)std::min<long long>((tot + 255) / 256, 152LL * 8);
     for (int k = 0; k < nb; ++k) {
-        launch(h, PK_GJ, s, [&] { skern::gj_step_pivot<<<1, 256, 0, s>>>(nb, k, h->Cinv, ipiv, colk, status); });
-        launch(h, PK_GJ, s, [&] { skern::gj_step_eliminate<<<egrid, 256, 0, s>>>(nb, k, h->Cinv, colk); });
+        launch(h, -1, s, [&] { skern::gj_step_pivot<<<1, 256, 0, s>>>(nb, k, h->Cinv, ipiv, colk, status); });
+        launch(h, -1, s, [&] { skern::gj_step_eliminate<<<egrid, 256, 0, s>>>(nb, k, h->Cinv, colk); });
     }
     launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, ipiv); });
     int hs = 0;
@@ -867,6 +867,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         require(o.precision == STOKES_FP64 || o.precision == STOKES_MIXED, "bad precision");
         require(o.cheb_hi > o.cheb_lo && o.cheb_lo > 0, "bad Chebyshev interval");
         if (!o.host_only) CK(cudaGetDevice(&h->device));
+        for (int kk = 0; kk < 5; ++kk) h->prof[kk].on = (o.prof_mask >> kk) & 1;
         cudaStream_t s = (cudaStream_t)stream;
         h->dim = coarse->dim;
         h->family = family;
