@@ -110,6 +110,9 @@ typedef struct {
     /* setup phase times in ms (host clock for host phases, events for device) */
     double t_mesh_ms, t_assembly_ms, t_upload_ms, t_gather_lu_ms, t_coarse_ms, t_eig_ms, t_graph_ms, t_total_ms;
     long long kernel_launches;            /* launches made by this handle so far */
+    /* split of t_assembly_ms (host): spaces + reference tensors, CSR
+       matrices, Vanka patches, transfers */
+    double t_spaces_ms, t_matrices_ms, t_patches_ms, t_transfers_ms;
 } stokes_mg_stats;
 
 typedef struct stokes_mg* stokes_mg_t;

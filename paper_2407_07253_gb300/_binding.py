@@ -40,7 +40,9 @@ class Stats(ctypes.Structure):
                 ("n_vel_nodes", c_int), ("n_pres_nodes", c_int), ("singular_patch", c_int),
                 ("t_mesh_ms", c_double), ("t_assembly_ms", c_double), ("t_upload_ms", c_double),
                 ("t_gather_lu_ms", c_double), ("t_coarse_ms", c_double), ("t_eig_ms", c_double),
-                ("t_graph_ms", c_double), ("t_total_ms", c_double), ("kernel_launches", c_longlong)]
+                ("t_graph_ms", c_double), ("t_total_ms", c_double), ("kernel_launches", c_longlong),
+                ("t_spaces_ms", c_double), ("t_matrices_ms", c_double), ("t_patches_ms", c_double),
+                ("t_transfers_ms", c_double)]
 
 
 class StokesError(RuntimeError):

@@ -3,9 +3,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <functional>
 #include <map>
 #include <numeric>
@@ -25,16 +28,126 @@ int num_threads() {
     return n;
 }
 
-// Static-chunk parallel loop over [0, n).
-static void parallel_for(int n, const std::function<void(int, int, int)>& body) {
-    int T = std::min(num_threads(), std::max(1, n / 64));
-    if (T <= 1) { body(0, n, 0); return; }
-    std::vector<std::thread> th;
-    for (int t = 0; t < T; ++t) {
-        int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
-        th.emplace_back([=, &body] { body(lo, hi, t); });
+// Persistent worker pool: parallel_for splits [0, n) into one contiguous,
+// ordered chunk per worker (the caller runs chunk 0).
+class Pool {
+  public:
+    static Pool& get() {
+        static Pool p(num_threads());
+        return p;
     }
-    for (auto& x : th) x.join();
+    int size() const { return (int)workers_.size() + 1; }
+    void run(int chunks, const std::function<void(int)>& job) {
+        if (chunks <= 1 || workers_.empty()) {
+            for (int c = 0; c < chunks; ++c) job(c);
+            return;
+        }
+        std::unique_lock<std::mutex> lk(m_);
+        job_ = &job;
+        chunks_ = chunks;
+        next_ = 1;
+        pending_ = chunks - 1;
+        ++gen_;
+        cv_.notify_all();
+        lk.unlock();
+        job(0);
+        lk.lock();
+        // help with remaining chunks, then wait for the workers
+        while (next_ < chunks_) {
+            int c = next_++;
+            lk.unlock();
+            job(c);
+            lk.lock();
+            --pending_;
+        }
+        done_.wait(lk, [&] { return pending_ == 0; });
+        job_ = nullptr;
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            stop_ = true;
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (auto& t : workers_) t.join();
+    }
+
+  private:
+    explicit Pool(int n) {
+        for (int i = 1; i < n; ++i) workers_.emplace_back([this] { loop(); });
+    }
+    void loop() {
+        unsigned seen = 0;
+        std::unique_lock<std::mutex> lk(m_);
+        for (;;) {
+            cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+            if (stop_) return;
+            seen = gen_;
+            while (job_ && next_ < chunks_) {
+                int c = next_++;
+                const std::function<void(int)>* j = job_;
+                lk.unlock();
+                (*j)(c);
+                lk.lock();
+                if (--pending_ == 0) done_.notify_all();
+            }
+        }
+    }
+    std::vector<std::thread> workers_;
+    std::mutex m_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)>* job_ = nullptr;
+    int chunks_ = 0, next_ = 0, pending_ = 0;
+    unsigned gen_ = 0;
+    bool stop_ = false;
+};
+
+static int chunk_count(int n) { return std::max(1, std::min(Pool::get().size(), n / 64)); }
+
+// Static-chunk parallel loop over [0, n): body(lo, hi, chunk).
+static void parallel_for(int n, const std::function<void(int, int, int)>& body) {
+    const int T = chunk_count(n);
+    Pool::get().run(T, [&](int t) {
+        int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
+        body(lo, hi, t);
+    });
+}
+
+// Variable-length lists built in parallel without per-item allocations:
+// the static chunks of parallel_for are contiguous and ordered, so the
+// per-thread buffers concatenate in item order.
+struct FlatLists {
+    std::vector<int> off;
+    fvec<int> data;
+    const int* begin(int i) const { return data.data() + off[i]; }
+    int size(int i) const { return off[i + 1] - off[i]; }
+};
+
+template <class F>
+static FlatLists build_lists(int n, F&& fill) {
+    const int T = chunk_count(n);
+    std::vector<std::vector<int>> buf(T);
+    FlatLists L;
+    L.off.assign(n + 1, 0);
+    std::vector<int> lo(T + 1);
+    for (int t = 0; t <= T; ++t) lo[t] = (int)((long long)n * t / T);
+    Pool::get().run(T, [&](int t) {
+        std::vector<int>& b = buf[t];
+        b.reserve((size_t)(lo[t + 1] - lo[t]) * 32);
+        for (int i = lo[t]; i < lo[t + 1]; ++i) {
+            size_t before = b.size();
+            fill(i, b, t);
+            L.off[i + 1] = (int)(b.size() - before);
+        }
+    });
+    for (int i = 0; i < n; ++i) L.off[i + 1] += L.off[i];
+    L.data.resize(L.off[n]);
+    parallel_for(T, [&](int a, int b2, int) {
+        for (int t = a; t < b2; ++t)
+            if (!buf[t].empty()) std::memcpy(L.data.data() + L.off[lo[t]], buf[t].data(), buf[t].size() * sizeof(int));
+    });
+    return L;
 }
 
 static double now_ms() {
@@ -557,12 +670,13 @@ static void node_cells(const Space& S, int nc, std::vector<int>& off, std::vecto
         for (int l = 0; l < S.nb; ++l) adj[fill[S.cell_nodes[(size_t)e * S.nb + l]]++] = e * S.nb + l;
 }
 
-static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const std::vector<double>& nu) {
+static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const std::vector<double>& nu,
+                           bool with_load) {
     const int d = m.d, nb = L.V.nb, nq = L.Q.nb, nc = m.nc;
     const Space &V = L.V, &Q = L.Q;
     // element matrices: stiffness (scaled by nu_e) and divergence coupling
-    std::vector<double> Se((size_t)nc * nb * nb), Ce((size_t)nc * nq * nb * d), Me((size_t)nc * nb * nb);
-    std::vector<double> qe((size_t)nc * nq);
+    fvec<double> Se((size_t)nc * nb * nb), Ce((size_t)nc * nq * nb * d), Me((size_t)nc * nb * nb);
+    fvec<double> qe((size_t)nc * nq);
     parallel_for(nc, [&](int lo, int hi, int) {
         for (int e = lo; e < hi; ++e) {
             CellGeom g = cell_geom(m, e);
@@ -612,51 +726,81 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
     // --- row patterns, per velocity node and per pressure node
     // velocity node i: free velocity neighbours (sorted by free index),
     // Dirichlet velocity neighbours, pressure neighbours
-    const int T = num_threads();
-    std::vector<std::vector<int>> vnb(V.n), vdn(V.n), vqn(V.n), qvn(Q.n), qdn(Q.n);
+    const int T = Pool::get().size();
     std::vector<std::vector<int>> stampV(T, std::vector<int>(V.n, -1)), stampQ(T, std::vector<int>(Q.n, -1));
-    parallel_for(V.n, [&](int lo, int hi, int t) {
+    auto by_free = [&](int a, int b) { return L.vfree[a] < L.vfree[b]; };
+    FlatLists vnb = build_lists(V.n, [&](int i, std::vector<int>& out, int t) {
         auto& sv = stampV[t];
-        auto& sq = stampQ[t];
-        for (int i = lo; i < hi; ++i) {
-            for (int a = voff[i]; a < voff[i + 1]; ++a) {
-                int e = vadj[a] / nb;
-                for (int l = 0; l < nb; ++l) {
-                    int j = V.cell_nodes[(size_t)e * nb + l];
-                    if (sv[j] == i) continue;
-                    sv[j] = i;
-                    if (L.vfree[j] >= 0) vnb[i].push_back(j);
-                    else vdn[i].push_back(j);
-                }
-                for (int l = 0; l < nq; ++l) {
-                    int q = Q.cell_nodes[(size_t)e * nq + l];
-                    if (sq[q] == i) continue;
-                    sq[q] = i;
-                    vqn[i].push_back(q);
-                }
+        size_t s0 = out.size();
+        for (int a = voff[i]; a < voff[i + 1]; ++a) {
+            int e = vadj[a] / nb;
+            for (int l = 0; l < nb; ++l) {
+                int j = V.cell_nodes[(size_t)e * nb + l];
+                if (sv[j] == i || L.vfree[j] < 0) continue;
+                sv[j] = i;
+                out.push_back(j);
             }
-            std::sort(vnb[i].begin(), vnb[i].end(), [&](int a, int b) { return L.vfree[a] < L.vfree[b]; });
-            std::sort(vdn[i].begin(), vdn[i].end());
-            std::sort(vqn[i].begin(), vqn[i].end());
         }
+        std::sort(out.begin() + s0, out.end(), by_free);
     });
     for (auto& s : stampV) std::fill(s.begin(), s.end(), -1);
-    parallel_for(Q.n, [&](int lo, int hi, int t) {
+    FlatLists vdn = build_lists(V.n, [&](int i, std::vector<int>& out, int t) {
         auto& sv = stampV[t];
-        for (int q = lo; q < hi; ++q) {
-            for (int a = qoff[q]; a < qoff[q + 1]; ++a) {
-                int e = qadj[a] / nq;
-                for (int l = 0; l < nb; ++l) {
-                    int j = V.cell_nodes[(size_t)e * nb + l];
-                    if (sv[j] == q) continue;
-                    sv[j] = q;
-                    if (L.vfree[j] >= 0) qvn[q].push_back(j);
-                    else qdn[q].push_back(j);
-                }
+        size_t s0 = out.size();
+        for (int a = voff[i]; a < voff[i + 1]; ++a) {
+            int e = vadj[a] / nb;
+            for (int l = 0; l < nb; ++l) {
+                int j = V.cell_nodes[(size_t)e * nb + l];
+                if (sv[j] == i || L.vfree[j] >= 0) continue;
+                sv[j] = i;
+                out.push_back(j);
             }
-            std::sort(qvn[q].begin(), qvn[q].end(), [&](int a, int b) { return L.vfree[a] < L.vfree[b]; });
-            std::sort(qdn[q].begin(), qdn[q].end());
         }
+        std::sort(out.begin() + s0, out.end());
+    });
+    FlatLists vqn = build_lists(V.n, [&](int i, std::vector<int>& out, int t) {
+        auto& sq = stampQ[t];
+        size_t s0 = out.size();
+        for (int a = voff[i]; a < voff[i + 1]; ++a) {
+            int e = vadj[a] / nb;
+            for (int l = 0; l < nq; ++l) {
+                int q = Q.cell_nodes[(size_t)e * nq + l];
+                if (sq[q] == i) continue;
+                sq[q] = i;
+                out.push_back(q);
+            }
+        }
+        std::sort(out.begin() + s0, out.end());
+    });
+    for (auto& s : stampV) std::fill(s.begin(), s.end(), -1);
+    FlatLists qvn = build_lists(Q.n, [&](int q, std::vector<int>& out, int t) {
+        auto& sv = stampV[t];
+        size_t s0 = out.size();
+        for (int a = qoff[q]; a < qoff[q + 1]; ++a) {
+            int e = qadj[a] / nq;
+            for (int l = 0; l < nb; ++l) {
+                int j = V.cell_nodes[(size_t)e * nb + l];
+                if (sv[j] == q || L.vfree[j] < 0) continue;
+                sv[j] = q;
+                out.push_back(j);
+            }
+        }
+        std::sort(out.begin() + s0, out.end(), by_free);
+    });
+    for (auto& s : stampV) std::fill(s.begin(), s.end(), -1);
+    FlatLists qdn = build_lists(Q.n, [&](int q, std::vector<int>& out, int t) {
+        auto& sv = stampV[t];
+        size_t s0 = out.size();
+        for (int a = qoff[q]; a < qoff[q + 1]; ++a) {
+            int e = qadj[a] / nq;
+            for (int l = 0; l < nb; ++l) {
+                int j = V.cell_nodes[(size_t)e * nb + l];
+                if (sv[j] == q || L.vfree[j] >= 0) continue;
+                sv[j] = q;
+                out.push_back(j);
+            }
+        }
+        std::sort(out.begin() + s0, out.end());
     });
     // --- CSR offsets: rows [comp c free velocity nodes...], then pressure
     const int n = L.n_free;
@@ -673,18 +817,18 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
     for (int c = 0; c < d; ++c)
         for (int f = 0; f < nVf; ++f) {
             int i = vrow[f];
-            K.rp[c * nVf + f + 1] = (int)(vnb[i].size() + vqn[i].size());
-            KD.rp[c * nVf + f + 1] = (int)vdn[i].size();
+            K.rp[c * nVf + f + 1] = vnb.size(i) + vqn.size(i);
+            KD.rp[c * nVf + f + 1] = vdn.size(i);
         }
     for (int q = 0; q < Q.n; ++q) {
-        K.rp[d * nVf + q + 1] = d * (int)qvn[q].size();
-        KD.rp[d * nVf + q + 1] = d * (int)qdn[q].size();
+        K.rp[d * nVf + q + 1] = d * qvn.size(q);
+        KD.rp[d * nVf + q + 1] = d * qdn.size(q);
     }
     for (int r = 0; r < n; ++r) { K.rp[r + 1] += K.rp[r]; KD.rp[r + 1] += KD.rp[r]; }
-    K.ci.assign(K.rp[n], 0);
-    K.v.assign(K.rp[n], 0.0);
-    KD.ci.assign(KD.rp[n], 0);
-    KD.v.assign(KD.rp[n], 0.0);
+    K.ci.resize(K.rp[n]);
+    K.v.resize(K.rp[n]);
+    KD.ci.resize(KD.rp[n]);
+    KD.v.resize(KD.rp[n]);
     // --- values: velocity rows
     std::vector<std::vector<int>> posV(T, std::vector<int>(V.n, -1)), posQ(T, std::vector<int>(Q.n, -1));
     parallel_for(nVf, [&](int lo, int hi, int t) {
@@ -692,20 +836,24 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
         auto& pq = posQ[t];
         for (int f = lo; f < hi; ++f) {
             int i = vrow[f];
-            const auto &a = vnb[i], &b = vqn[i], &dn = vdn[i];
-            int nvv = (int)a.size();
+            const int* a = vnb.begin(i);
+            const int* b = vqn.begin(i);
+            const int* dn = vdn.begin(i);
+            const int nvv = vnb.size(i), nbq = vqn.size(i), ndd = vdn.size(i);
             for (int s = 0; s < nvv; ++s) pv[a[s]] = s;
-            for (int s = 0; s < (int)dn.size(); ++s) pv[dn[s]] = s;
-            for (int s = 0; s < (int)b.size(); ++s) pq[b[s]] = nvv + s;
+            for (int s = 0; s < ndd; ++s) pv[dn[s]] = s;
+            for (int s = 0; s < nbq; ++s) pq[b[s]] = nvv + s;
             for (int c = 0; c < d; ++c) {
                 int r = c * nVf + f;
                 int* ci = &K.ci[K.rp[r]];
                 double* vv = &K.v[K.rp[r]];
                 for (int s = 0; s < nvv; ++s) ci[s] = c * nVf + L.vfree[a[s]];
-                for (int s = 0; s < (int)b.size(); ++s) ci[nvv + s] = d * nVf + b[s];
+                for (int s = 0; s < nbq; ++s) ci[nvv + s] = d * nVf + b[s];
+                for (int s = 0; s < nvv + nbq; ++s) vv[s] = 0.0;
                 int* dci = &KD.ci[KD.rp[r]];
                 double* dv = &KD.v[KD.rp[r]];
-                for (int s = 0; s < (int)dn.size(); ++s) dci[s] = c * V.n + dn[s];
+                for (int s = 0; s < ndd; ++s) dci[s] = c * V.n + dn[s];
+                for (int s = 0; s < ndd; ++s) dv[s] = 0.0;
                 for (int x = voff[i]; x < voff[i + 1]; ++x) {
                     int e = vadj[x] / nb, la = vadj[x] % nb;
                     const double* se = &Se[((size_t)e * nb + la) * nb];
@@ -726,8 +874,9 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
     parallel_for(Q.n, [&](int lo, int hi, int t) {
         auto& pv = posV[t];
         for (int q = lo; q < hi; ++q) {
-            const auto &a = qvn[q], &dn = qdn[q];
-            int nvv = (int)a.size(), ndd = (int)dn.size();
+            const int* a = qvn.begin(q);
+            const int* dn = qdn.begin(q);
+            const int nvv = qvn.size(q), ndd = qdn.size(q);
             for (int s = 0; s < nvv; ++s) pv[a[s]] = s;
             for (int s = 0; s < ndd; ++s) pv[dn[s]] = s;
             int r = d * nVf + q;
@@ -739,6 +888,8 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
                 for (int s = 0; s < nvv; ++s) ci[c * nvv + s] = c * nVf + L.vfree[a[s]];
                 for (int s = 0; s < ndd; ++s) dci[c * ndd + s] = c * V.n + dn[s];
             }
+            for (int s = 0; s < d * nvv; ++s) vv[s] = 0.0;
+            for (int s = 0; s < d * ndd; ++s) dv[s] = 0.0;
             for (int x = qoff[q]; x < qoff[q + 1]; ++x) {
                 int e = qadj[x] / nq, lp = qadj[x] % nq;
                 for (int l = 0; l < nb; ++l) {
@@ -752,21 +903,24 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
             }
         }
     });
-    // --- scalar mass matrix on all velocity nodes (for F = M f)
+    // --- scalar mass matrix on all velocity nodes (for F = M f); only the
+    // finest level's load vector is ever formed
+    if (!with_load) { L.KfD = CSR(); goto centers; }
+    {
     CSR& Mv = L.Mv;
     Mv.nr = Mv.ncol = V.n;
     Mv.rp.assign(V.n + 1, 0);
-    for (int i = 0; i < V.n; ++i) Mv.rp[i + 1] = Mv.rp[i] + (int)(vnb[i].size() + vdn[i].size());
-    Mv.ci.assign(Mv.rp[V.n], 0);
-    Mv.v.assign(Mv.rp[V.n], 0.0);
+    for (int i = 0; i < V.n; ++i) Mv.rp[i + 1] = Mv.rp[i] + vnb.size(i) + vdn.size(i);
+    Mv.ci.resize(Mv.rp[V.n]);
+    Mv.v.resize(Mv.rp[V.n]);
     parallel_for(V.n, [&](int lo, int hi, int t) {
         auto& pv = posV[t];
         std::vector<int> cols;
         for (int i = lo; i < hi; ++i) {
-            cols.assign(vnb[i].begin(), vnb[i].end());
-            cols.insert(cols.end(), vdn[i].begin(), vdn[i].end());
+            cols.assign(vnb.begin(i), vnb.begin(i) + vnb.size(i));
+            cols.insert(cols.end(), vdn.begin(i), vdn.begin(i) + vdn.size(i));
             std::sort(cols.begin(), cols.end());
-            for (int s = 0; s < (int)cols.size(); ++s) { pv[cols[s]] = s; Mv.ci[Mv.rp[i] + s] = cols[s]; }
+            for (int s = 0; s < (int)cols.size(); ++s) { pv[cols[s]] = s; Mv.ci[Mv.rp[i] + s] = cols[s]; Mv.v[Mv.rp[i] + s] = 0.0; }
             for (int x = voff[i]; x < voff[i + 1]; ++x) {
                 int e = vadj[x] / nb, la = vadj[x] % nb;
                 for (int l = 0; l < nb; ++l)
@@ -774,6 +928,8 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
             }
         }
     });
+    }
+centers:
     L.cell_center.assign((size_t)nc * d, 0.0);
     for (int e = 0; e < nc; ++e)
         for (int c = 0; c < d; ++c) {
@@ -790,7 +946,7 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
 static void build_patches(const Mesh& m, const Topology& T, Level& L) {
     const int d = m.d, nb = L.V.nb, nq = L.Q.nb;
     std::vector<std::vector<int>> P(m.nv);
-    const int NT = num_threads();
+    const int NT = Pool::get().size();
     std::vector<std::vector<int>> stV(NT, std::vector<int>(L.V.n, -1)), stQ(NT, std::vector<int>(L.Q.n, -1));
     parallel_for(m.nv, [&](int lo, int hi, int t) {
         auto& sv = stV[t];
@@ -869,8 +1025,15 @@ static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const 
     });
     P.rp.assign(P.nr + 1, 0);
     for (int i = 0; i < P.nr; ++i) P.rp[i + 1] = P.rp[i] + (int)rows[i].size();
-    for (int i = 0; i < P.nr; ++i)
-        for (auto& x : rows[i]) { P.ci.push_back(x.first); P.v.push_back(x.second); }
+    P.ci.resize(P.rp[P.nr]);
+    P.v.resize(P.rp[P.nr]);
+    parallel_for(P.nr, [&](int lo, int hi, int) {
+        for (int i = lo; i < hi; ++i)
+            for (size_t t = 0; t < rows[i].size(); ++t) {
+                P.ci[P.rp[i] + t] = rows[i][t].first;
+                P.v[P.rp[i] + t] = rows[i][t].second;
+            }
+    });
     return P;
 }
 
@@ -882,37 +1045,49 @@ static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Le
     CSR& P = F.P;
     P.nr = F.n_free;
     P.ncol = C.n_free;
-    P.rp.assign(1, 0);
-    P.ci.clear();
-    P.v.clear();
     std::vector<int> vrow(F.nVf);
     for (int i = 0; i < F.V.n; ++i)
         if (F.vfree[i] >= 0) vrow[F.vfree[i]] = i;
+    // free coarse columns only; the coarse free numbering follows node order,
+    // so rows of PV (sorted by coarse node) stay sorted
+    std::vector<int> vcount(F.nVf);
+    parallel_for(F.nVf, [&](int lo, int hi, int) {
+        for (int f = lo; f < hi; ++f) {
+            int i = vrow[f], c = 0;
+            for (int p = PV.rp[i]; p < PV.rp[i + 1]; ++p) c += C.vfree[PV.ci[p]] >= 0;
+            vcount[f] = c;
+        }
+    });
+    P.rp.assign(P.nr + 1, 0);
     for (int c = 0; c < d; ++c)
-        for (int f = 0; f < F.nVf; ++f) {
+        for (int f = 0; f < F.nVf; ++f) P.rp[c * F.nVf + f + 1] = vcount[f];
+    for (int q = 0; q < F.Q.n; ++q) P.rp[d * F.nVf + q + 1] = PQ.rp[q + 1] - PQ.rp[q];
+    for (int r = 0; r < P.nr; ++r) P.rp[r + 1] += P.rp[r];
+    P.ci.resize(P.rp[P.nr]);
+    P.v.resize(P.rp[P.nr]);
+    parallel_for(F.nVf, [&](int lo, int hi, int) {
+        for (int f = lo; f < hi; ++f) {
             int i = vrow[f];
-            for (int p = PV.rp[i]; p < PV.rp[i + 1]; ++p) {
-                int jc = C.vfree[PV.ci[p]];
-                if (jc < 0) continue;
-                P.ci.push_back(c * C.nVf + jc);
-                P.v.push_back(PV.v[p]);
+            for (int c = 0; c < d; ++c) {
+                int o = P.rp[c * F.nVf + f];
+                for (int p = PV.rp[i]; p < PV.rp[i + 1]; ++p) {
+                    int jc = C.vfree[PV.ci[p]];
+                    if (jc < 0) continue;
+                    P.ci[o] = c * C.nVf + jc;
+                    P.v[o++] = PV.v[p];
+                }
             }
-            P.rp.push_back((int)P.ci.size());
         }
-    for (int q = 0; q < F.Q.n; ++q) {
-        for (int p = PQ.rp[q]; p < PQ.rp[q + 1]; ++p) {
-            P.ci.push_back(d * C.nVf + PQ.ci[p]);
-            P.v.push_back(PQ.v[p]);
+    });
+    parallel_for(F.Q.n, [&](int lo, int hi, int) {
+        for (int q = lo; q < hi; ++q) {
+            int o = P.rp[d * F.nVf + q];
+            for (int p = PQ.rp[q]; p < PQ.rp[q + 1]; ++p) {
+                P.ci[o] = d * C.nVf + PQ.ci[p];
+                P.v[o++] = PQ.v[p];
+            }
         }
-        P.rp.push_back((int)P.ci.size());
-    }
-    // keep column indices sorted within a row
-    for (int r = 0; r < P.nr; ++r) {
-        std::vector<std::pair<int, double>> t;
-        for (int p = P.rp[r]; p < P.rp[r + 1]; ++p) t.push_back({P.ci[p], P.v[p]});
-        std::sort(t.begin(), t.end());
-        for (int p = P.rp[r]; p < P.rp[r + 1]; ++p) { P.ci[p] = t[p - P.rp[r]].first; P.v[p] = t[p - P.rp[r]].second; }
-    }
+    });
     F.R = transpose(P);
 }
 
@@ -984,20 +1159,28 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         if (L.k < 2 || L.k > 10) throw std::invalid_argument("velocity degree must be in [2, 10]");
         if (L.family == 1 && L.k < d) throw std::invalid_argument("Scott-Vogelius needs k >= dim");
         const Mesh& m = H.meshes[L.mesh_index];
+        double ta = now_ms();
         const RefElement& rv = ref(d, L.k);
         const RefElement& rq = ref(d, L.k - 1);
         build_space(m, topo[L.mesh_index], rv, true, L.V);
         build_space(m, topo[L.mesh_index], rq, L.family == 0, L.Q);
         RefTensors RT;
         RT.init(rv, rq);
-        assemble_level(m, L, RT, nus[L.mesh_index]);
+        double tb = now_ms();
+        assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
+        double tc = now_ms();
         if (l + 1 < ls.size()) build_patches(m, topo[L.mesh_index], L);
+        H.t_spaces_ms += tb - ta;
+        H.t_matrices_ms += tc - tb;
+        H.t_patches_ms += now_ms() - tc;
     }
+    double tt = now_ms();
     for (size_t l = 0; l + 1 < ls.size(); ++l) {
         Level &F = H.levels[l], &C = H.levels[l + 1];
         const std::vector<int>* par_map = (F.mesh_index == C.mesh_index) ? nullptr : &H.parents[F.mesh_index];
         monolithic_interp(H.meshes[F.mesh_index], F, H.meshes[C.mesh_index], C, ref(d, C.k), ref(d, C.k - 1), par_map);
     }
+    H.t_transfers_ms = now_ms() - tt;
     H.t_assembly_ms = now_ms() - t1;
 }
 

@@ -10,9 +10,29 @@
 #include <array>
 #include <cstdint>
 #include <string>
+#include <memory>
+#include <utility>
 #include <vector>
 
 namespace sfem {
+
+// std::vector storage whose resize() leaves trivially constructible
+// elements uninitialised, so that large arrays are first touched (and their
+// pages faulted in) by the parallel loops that fill them.
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind { using other = DefaultInitAlloc<U>; };
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept { ::new ((void*)p) U; }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
+};
+template <class T>
+using fvec = std::vector<T, DefaultInitAlloc<T>>;
 
 struct Mesh {
     int d = 0, nv = 0, nc = 0;
@@ -49,8 +69,8 @@ struct RefTensors {
 
 struct CSR {
     int nr = 0, ncol = 0;
-    std::vector<int> rp, ci;
-    std::vector<double> v;
+    fvec<int> rp, ci;
+    fvec<double> v;
     long long nnz() const { return (long long)ci.size(); }
 };
 CSR transpose(const CSR& a);
@@ -92,6 +112,7 @@ struct Hierarchy {
     std::vector<std::vector<int>> parents;    // parents[i]: cells of meshes[i] -> meshes[i+1]
     std::vector<Level> levels;
     double t_mesh_ms = 0, t_assembly_ms = 0;
+    double t_spaces_ms = 0, t_matrices_ms = 0, t_patches_ms = 0, t_transfers_ms = 0;
 };
 
 // Build the whole host hierarchy; throws std::runtime_error on invalid input.

@@ -48,8 +48,9 @@ T* dalloc(size_t n) {
     return (T*)p;
 }
 
-template <typename T>
-T* dupload(const std::vector<T>& h, cudaStream_t s) {
+template <typename Vec>
+typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
+    using T = typename Vec::value_type;
     T* p = dalloc<T>(h.size());
     if (!h.empty()) CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     return p;
@@ -903,6 +904,10 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         sfem::build_hierarchy(cm, spec, nu_cell, h->H);
         h->st.t_mesh_ms = h->H.t_mesh_ms;
         h->st.t_assembly_ms = h->H.t_assembly_ms;
+        h->st.t_spaces_ms = h->H.t_spaces_ms;
+        h->st.t_matrices_ms = h->H.t_matrices_ms;
+        h->st.t_patches_ms = h->H.t_patches_ms;
+        h->st.t_transfers_ms = h->H.t_transfers_ms;
         const int nl = (int)h->H.levels.size();
         require(nl >= 2, "the hierarchy needs at least two levels (n_refine >= 1 or a p-coarsening)");
         if (o.host_only) {
