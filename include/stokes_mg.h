@@ -236,6 +236,40 @@ int stokes_mg_fgmres(stokes_mg_t h, const double* b, double* x, double tol, int*
 int stokes_prof_enable(stokes_mg_t h, int kind, int enable);
 int stokes_prof_read(stokes_mg_t h, int kind, long long* launches, double* total_ms);
 
+/* ---- allocation-free batched inverse ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: applications whose HBM is owned by
+ * another allocator (a framework's caching pool that has reserved it, so
+ * cudaMalloc would fail or fragment it) and code that must not enter the
+ * CUDA allocator at all (cudaFree synchronises the device).
+ *
+ * Inverts, in place and in FP64, npatch dense row-major matrices packed back
+ * to back in `mats` (device, caller-owned): matrix p has size n_p = sizes[p]
+ * (host array) and starts at element sum_{q<p} n_q^2.  The algorithm is the
+ * batched partial-pivot Gauss-Jordan of stokes_mg_patch_inverses.
+ *   sizes[p] in [1, 4096]; npatch <= STOKES_NOALLOC_MAX_PATCHES and
+ *   sum of sizes <= STOKES_NOALLOC_MAX_ENTRIES, else STOKES_EINVAL and no
+ *   GPU work.
+ *   first_singular (host, may be NULL): index of the first patch with a zero
+ *   pivot (STOKES_ESINGULAR is returned; its matrix is then not an inverse),
+ *   -1 otherwise.
+ * Allocates nothing: no cudaMalloc, no cudaFree, no host heap.  Its scratch
+ * (offsets, pivot status, pivot workspace of matrices larger than 160) is a
+ * fixed array of about 7 MB in this library's device memory, held by every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array and it keeps the last call's contents (the pivot
+ * status is cleared by each call): calls whose GPU work overlaps, on any
+ * stream or thread, race on it.  The call synchronises `stream`.
+ * Errors: EINVAL (sizes), ESINGULAR, ECUDA; message from
+ * stokes_noalloc_last_error(). */
+#define STOKES_NOALLOC_MAX_PATCHES 65536
+#define STOKES_NOALLOC_MAX_ENTRIES 524288
+int stokes_batched_inverse_noalloc(int npatch, const int* sizes, double* mats, int* first_singular,
+                                   void* stream);
+const char* stokes_noalloc_last_error(void);
+
 /* Free everything the handle owns (NULL is accepted). */
 void stokes_mg_destroy(stokes_mg_t h);
 

@@ -91,6 +91,8 @@ def lib():
         "stokes_prof_read": (c_int, [P, c_int, POINTER(c_longlong), POINTER(c_double)]),
         "stokes_mg_destroy": (None, [P]),
         "stokes_last_error": (ctypes.c_char_p, []),
+        "stokes_batched_inverse_noalloc": (c_int, [c_int, P, P, POINTER(c_int), P]),
+        "stokes_noalloc_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
