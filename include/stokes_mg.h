@@ -88,6 +88,12 @@ typedef struct {
                                get_patches queries are valid on such a handle */
     int prof_mask;          /* bit k set: time kernel class k (see stokes_prof_enable)
                                from the start of setup */
+    int patch_solver;       /* exact patch solves (Sec. 3.4), both FP64:
+                               0 (default) block inverse of the saddle structure
+                                 [L 0 B0^T; 0 L B1^T; B0 B1 0]: SPD L and Schur
+                                 complement S = sum B_c L^-1 B_c^T inverted by
+                                 Gauss-Jordan without pivoting;
+                               1 partial-pivot Gauss-Jordan on the whole patch */
 } stokes_mg_opts;
 
 #define STOKES_MAX_LEVELS 16
@@ -117,7 +123,7 @@ typedef struct {
 
 typedef struct stokes_mg* stokes_mg_t;
 
-/* Fill `o` with the defaults: GRADUAL, nu_p = nu_h = n_V = 1, 10 Arnoldi
+/* Fill `o` with the defaults: GRADUAL, nu_p = nu_h = n_V = 1, 15 Arnoldi
  * steps, seed 0, interval [0.1, 1.1], precision FP64, restart 30,
  * maxit 1000, use_graph 1. */
 void stokes_mg_default_opts(stokes_mg_opts* o);

@@ -27,7 +27,8 @@ class Opts(ctypes.Structure):
                 ("nu_p", c_int), ("nu_h", c_int), ("n_V", c_int), ("eig_steps", c_int),
                 ("eig_seed", c_ulonglong), ("cheb_lo", c_double), ("cheb_hi", c_double),
                 ("lmax_override", c_double * 16), ("precision", c_int), ("restart", c_int),
-                ("maxit", c_int), ("use_graph", c_int), ("host_only", c_int), ("prof_mask", c_int)]
+                ("maxit", c_int), ("use_graph", c_int), ("host_only", c_int), ("prof_mask", c_int),
+                ("patch_solver", c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -946,6 +946,7 @@ centers:
 static void build_patches(const Mesh& m, const Topology& T, Level& L) {
     const int d = m.d, nb = L.V.nb, nq = L.Q.nb;
     std::vector<std::vector<int>> P(m.nv);
+    std::vector<int> NV(m.nv, 0);
     const int NT = Pool::get().size();
     std::vector<std::vector<int>> stV(NT, std::vector<int>(L.V.n, -1)), stQ(NT, std::vector<int>(L.Q.n, -1));
     parallel_for(m.nv, [&](int lo, int hi, int t) {
@@ -979,6 +980,7 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
             std::sort(vel.begin(), vel.end());
             std::sort(pre.begin(), pre.end());
             auto& out = P[v];
+            NV[v] = (int)vel.size();
             for (int c = 0; c < d; ++c)
                 for (int x : vel) out.push_back(c * L.nVf + x);
             for (int q : pre) out.push_back(d * L.nVf + q);
@@ -986,10 +988,12 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
     });
     L.patch_off.assign(1, 0);
     L.patch_dofs.clear();
+    L.patch_nv.clear();
     for (int v = 0; v < m.nv; ++v) {
         if (P[v].empty()) continue;
         L.patch_dofs.insert(L.patch_dofs.end(), P[v].begin(), P[v].end());
         L.patch_off.push_back((int)L.patch_dofs.size());
+        L.patch_nv.push_back(NV[v]);
     }
 }
 

@@ -97,6 +97,9 @@ struct Level {
     std::vector<double> pint;  // int psi_j for every pressure node
     CSR P, R;                  // interpolation from level+1 (free x free) and its transpose
     std::vector<int> patch_off, patch_dofs;   // Vanka-star patches (free DoF indices)
+    std::vector<int> patch_nv;                // velocity nodes per component of each patch:
+                                              // a patch lists d blocks of n_v velocity DoFs
+                                              // (same nodes per component), then n_p pressures
     std::vector<double> cell_center;          // [nc][d]
 };
 

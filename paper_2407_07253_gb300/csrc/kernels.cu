@@ -57,6 +57,57 @@ __global__ void mdot_final(int nblocks, int m, const double* __restrict__ partia
     out[i] = (sqrt_out && i == 0) ? sqrt(s) : s;
 }
 
+// Single-launch multi-dot: every block writes its partial sums, the last
+// block to finish (atomic ticket) adds them in a fixed order, so the result
+// is bitwise reproducible.  Launched with MDOT_BLOCKS blocks of 512 threads.
+__global__ void __launch_bounds__(512) mdot_fused(int n, int m, const double* __restrict__ V, long long ldv,
+                                                  const double* __restrict__ w, double* __restrict__ partial,
+                                                  unsigned int* __restrict__ ticket, double* __restrict__ out,
+                                                  double* __restrict__ acc, int sqrt_out) {
+    double a[MDOT_MAX];
+#pragma unroll
+    for (int i = 0; i < MDOT_MAX; ++i) a[i] = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double wk = w[k];
+#pragma unroll
+        for (int i = 0; i < MDOT_MAX; ++i)
+            if (i < m) a[i] += V[(long long)i * ldv + k] * wk;
+    }
+    __shared__ double red[16][MDOT_MAX];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < MDOT_MAX; ++i) {
+        if (i >= m) break;
+        double v = a[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double s = 0;
+        for (int wv = 0; wv < nw; ++wv) s += red[wv][threadIdx.x];
+        partial[(long long)blockIdx.x * m + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // 16 threads per output, fixed strided assignment, fixed shuffle tree
+    const int i = threadIdx.x >> 4, sub = threadIdx.x & 15;
+    double s = 0;
+    if (i < m)
+        for (int b = sub; b < (int)gridDim.x; b += 16) s += ((volatile double*)partial)[(long long)b * m + i];
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 16);
+    if (i < m && sub == 0) {
+        if (acc) acc[i] += s;
+        out[i] = (sqrt_out && i == 0) ? sqrt(s) : s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 __global__ void __launch_bounds__(256) maxpy(int n, int m, const double* __restrict__ V, long long ldv,
                                              const double* __restrict__ h, double sign, double* __restrict__ w) {
     __shared__ double hs[MDOT_MAX];
@@ -235,6 +286,158 @@ __global__ void __launch_bounds__(512) gj_inverse_global(int npatch, const int* 
     gj_core(A, n, col_ws + poff[p], ipiv_ws + poff[p], &st);
     __syncthreads();
     gj_store(A, n, inv64, off64 ? off64[p] : 0, inv32, off32 ? off32[p] : 0);
+    if (threadIdx.x == 0) status[p] = st;
+}
+
+// In-place inverse of an SPD matrix (row-major, leading dimension lda) by
+// Gauss-Jordan without pivoting: an SPD matrix needs no row interchanges.
+// status <- 1 + step of the first non-positive pivot.
+__device__ void gj_spd(double* A, int n, int lda, double* colk, int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 0; k < n; ++k) {
+        const double piv = A[(long long)k * lda + k];
+        if (tid == 0 && !(piv > 0.0) && *status == 0) *status = k + 1;
+        const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
+        for (int i = tid; i < n; i += nt) colk[i] = A[(long long)i * lda + k];
+        __syncthreads();
+        for (int j = tid; j < n; j += nt) A[(long long)k * lda + j] = (j == k) ? inv : A[(long long)k * lda + j] * inv;
+        __syncthreads();
+        for (int t = tid; t < n * n; t += nt) {
+            const int i = t / n, j = t - (t / n) * n;
+            if (i == k) continue;
+            const double f = colk[i];
+            if (j == k) A[(long long)i * lda + k] = -f * inv;
+            else A[(long long)i * lda + j] -= f * A[(long long)k * lda + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Block inverse of one Vanka patch with the saddle structure
+//   K_i = [L 0 .. B_0^T; 0 L .. B_1^T; ..; B_0 B_1 .. 0]
+// (the d velocity components share the SPD block L on the same nodes):
+//   Li = L^{-1}, W_c = Li B_c^T, S = sum_c B_c W_c, Si = S^{-1}, X_c = W_c Si,
+//   K_i^{-1} = [blockdiag(Li) - X W^T, X; X^T, -Si].
+// K (row-major n x n) is read from the workspace; the inverse is written
+// column-major (padded) in FP64 / FP32 and, if back != 0, row-major back to K.
+__device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, double* inv64, float* inv32,
+                            int back, int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int np = n - d * nv, npp = np | 1, dnv = d * nv;
+    double* Ls = scratch;
+    double* Bt = Ls + (long long)nv * nv;          // [c][a][q], becomes X
+    double* Wm = Bt + (long long)d * nv * npp;     // [c][a][q]
+    double* Ss = Wm + (long long)d * nv * npp;     // [q][r]
+    double* colk = Ss + (long long)np * np;
+    for (int t = tid; t < nv * nv; t += nt) {
+        const int a = t / nv, b = t - (t / nv) * nv;
+        Ls[t] = K[(long long)a * n + b];
+    }
+    for (int t = tid; t < dnv * np; t += nt) {
+        const int r = t / np, q = t - (t / np) * np;       // r = c*nv + a
+        Bt[(long long)r * npp + q] = K[(long long)r * n + dnv + q];
+    }
+    __syncthreads();
+    gj_spd(Ls, nv, nv, colk, status);
+    // W_c = Li B_c^T
+    for (int t = tid; t < dnv * np; t += nt) {
+        const int r = t / np, q = t - (t / np) * np;
+        const int c = r / nv, a = r - c * nv;
+        const double* li = Ls + (long long)a * nv;
+        const double* bt = Bt + (long long)c * nv * npp + q;
+        double s = 0.0;
+        for (int b = 0; b < nv; ++b) s += li[b] * bt[(long long)b * npp];
+        Wm[(long long)r * npp + q] = s;
+    }
+    __syncthreads();
+    // S = sum_c B_c W_c
+    for (int t = tid; t < np * np; t += nt) {
+        const int q = t / np, r = t - (t / np) * np;
+        double s = 0.0;
+        for (int a = 0; a < dnv; ++a) s += Bt[(long long)a * npp + q] * Wm[(long long)a * npp + r];
+        Ss[t] = s;
+    }
+    __syncthreads();
+    gj_spd(Ss, np, np, colk, status);
+    // X_c = W_c Si (overwrites Bt)
+    for (int t = tid; t < dnv * np; t += nt) {
+        const int r = t / np, q = t - (t / np) * np;
+        const double* w = Wm + (long long)r * npp;
+        double s = 0.0;
+        for (int x = 0; x < np; ++x) s += w[x] * Ss[(long long)x * np + q];
+        Bt[(long long)r * npp + q] = s;
+    }
+    __syncthreads();
+    const int ld64 = (n + 1) & ~1, ld32 = (n + 3) & ~3;
+    const int ldw = inv64 ? ld64 : (inv32 ? ld32 : n);
+    for (long long t = tid; t < (long long)ldw * n; t += nt) {
+        const int j = (int)(t / ldw), i = (int)(t - (long long)j * ldw);
+        double v = 0.0;
+        if (i < n) {
+            if (i < dnv && j < dnv) {
+                const int c = i / nv, a = i - c * nv, c2 = j / nv, b = j - c2 * nv;
+                const double* x = Bt + (long long)i * npp;
+                const double* w = Wm + (long long)j * npp;
+                double s = 0.0;
+                for (int q = 0; q < np; ++q) s += x[q] * w[q];
+                v = (c == c2 ? Ls[(long long)a * nv + b] : 0.0) - s;
+            } else if (i < dnv) {
+                v = Bt[(long long)i * npp + (j - dnv)];
+            } else if (j < dnv) {
+                v = Bt[(long long)j * npp + (i - dnv)];
+            } else {
+                v = -Ss[(long long)(i - dnv) * np + (j - dnv)];
+            }
+        }
+        if (inv64 && ldw == ld64) inv64[t] = v;
+        if (inv32 && ldw == ld32) inv32[t] = (float)v;
+        if (back && i < n) K[(long long)i * n + j] = v;
+    }
+    // FP32 copy when its padding differs from the FP64 one
+    if (inv64 && inv32 && ld32 != ld64) {
+        __syncthreads();
+        for (long long t = tid; t < (long long)ld32 * n; t += nt) {
+            const int j = (int)(t / ld32), i = (int)(t - (long long)j * ld32);
+            inv32[t] = i < n ? (float)inv64[(long long)j * ld64 + i] : 0.0f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff,
+                                                           const int* __restrict__ pnv, const long long* __restrict__ moff,
+                                                           double* __restrict__ work, const long long* __restrict__ off64,
+                                                           double* __restrict__ inv64, const long long* __restrict__ off32,
+                                                           float* __restrict__ inv32, int back, long long max_scratch,
+                                                           int* __restrict__ status) {
+    extern __shared__ double sscr[];
+    const int p = blockIdx.x;
+    const int n = poff[p + 1] - poff[p], nv = pnv[p];
+    if (n == 0 || saddle_scratch(d, n, nv) > max_scratch) return;
+    __shared__ int st;
+    if (threadIdx.x == 0) st = 0;
+    __syncthreads();
+    saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr, inv32 ? inv32 + off32[p] : nullptr,
+                back, &st);
+    __syncthreads();
+    if (threadIdx.x == 0) status[p] = st;
+}
+
+__global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, const int* __restrict__ poff,
+                                                             const int* __restrict__ pnv, const long long* __restrict__ moff,
+                                                             double* __restrict__ work, const long long* __restrict__ off64,
+                                                             double* __restrict__ inv64, const long long* __restrict__ off32,
+                                                             float* __restrict__ inv32, int back, long long max_scratch,
+                                                             const long long* __restrict__ soff, double* __restrict__ scratch,
+                                                             int* __restrict__ status) {
+    const int p = blockIdx.x;
+    const int n = poff[p + 1] - poff[p], nv = pnv[p];
+    if (n == 0 || saddle_scratch(d, n, nv) <= max_scratch) return;
+    __shared__ int st;
+    if (threadIdx.x == 0) st = 0;
+    __syncthreads();
+    saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,
+                inv32 ? inv32 + off32[p] : nullptr, back, &st);
+    __syncthreads();
     if (threadIdx.x == 0) status[p] = st;
 }
 
@@ -503,13 +706,6 @@ __host__ __device__ void hessenberg_eig_core(int m, int ld, const double* Hs, do
     }
     out[0] = best;
     out[1] = failed;
-}
-
-__global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict__ Hs, double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    __shared__ cplx A[HESS_MAX][HESS_MAX];
-    __shared__ cplx cr[HESS_MAX], sr[HESS_MAX];
-    hessenberg_eig_core(mm < HESS_MAX ? mm : HESS_MAX, ld, Hs, out, A, cr, sr);
 }
 
 }  // namespace skern

@@ -77,6 +77,12 @@ __global__ void mdot_partial(int n, int m, const double* __restrict__ V, long lo
 // into acc[i] as well; if sqrt_out, out[0] = sqrt(sum).
 __global__ void mdot_final(int nblocks, int m, const double* __restrict__ partial, double* __restrict__ out,
                            double* __restrict__ acc, int sqrt_out);
+// Same reduction in one launch (last block finishes in a fixed order);
+// MDOT_BLOCKS blocks of 512 threads; ticket must start at 0 and is reset.
+constexpr int MDOT_BLOCKS = 152;
+__global__ void mdot_fused(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ w,
+                           double* __restrict__ partial, unsigned int* __restrict__ ticket, double* __restrict__ out,
+                           double* __restrict__ acc, int sqrt_out);
 // w[k] += sign * sum_i h[i] V[i][k]
 __global__ void maxpy(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ h,
                       double sign, double* __restrict__ w);
@@ -104,6 +110,31 @@ __global__ void gj_inverse_global(int npatch, const int* __restrict__ poff, cons
                                   double* __restrict__ work, const long long* __restrict__ off64, double* __restrict__ inv64,
                                   const long long* __restrict__ off32, float* __restrict__ inv32,
                                   int* __restrict__ status, int* __restrict__ ipiv_ws, double* __restrict__ col_ws);
+
+// Block (Schur-complement) inverse of saddle-structured Vanka patches:
+// K_i = [L 0 B_0^T; 0 L B_1^T; B_0 B_1 0] with one SPD velocity block L per
+// component (vector Laplacian), pnv[p] velocity nodes per component.  FP64;
+// SPD blocks inverted by Gauss-Jordan without pivoting; status as above.
+// Patches whose scratch (saddle_scratch doubles) is <= max_scratch run in
+// shared memory (saddle_inverse_smem), the others in the global scratch at
+// soff[p] (saddle_inverse_global).
+__host__ __device__ inline long long saddle_scratch(int d, int n, int nv) {
+    const int np = n - d * nv, npp = np | 1;
+    const int mx = nv > np ? nv : np;
+    return (long long)nv * nv + 2LL * d * nv * npp + (long long)np * np + mx;
+}
+constexpr long long SADDLE_SMEM_MAX_DOUBLES = 25600;   // 200 KB of shared memory
+__global__ void saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
+                                    const long long* __restrict__ moff, double* __restrict__ work,
+                                    const long long* __restrict__ off64, double* __restrict__ inv64,
+                                    const long long* __restrict__ off32, float* __restrict__ inv32, int back,
+                                    long long max_scratch, int* __restrict__ status);
+__global__ void saddle_inverse_global(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
+                                      const long long* __restrict__ moff, double* __restrict__ work,
+                                      const long long* __restrict__ off64, double* __restrict__ inv64,
+                                      const long long* __restrict__ off32, float* __restrict__ inv32, int back,
+                                      long long max_scratch, const long long* __restrict__ soff,
+                                      double* __restrict__ scratch, int* __restrict__ status);
 
 // One ASM sweep (Eq. 3.4): Y[poff[i] + a] = w[dof_a] * sum_b Kinv_i[a][b] r[dof_b].
 // FP32: float4 loads of 4 consecutive rows per thread; FP64: double2 loads
@@ -157,11 +188,10 @@ constexpr int HESS_MAX = 16;
 struct cplx { double re, im; };
 __host__ __device__ void hessenberg_eig_core(int m, int ld, const double* Hs, double* out, cplx (*A)[HESS_MAX],
                                              cplx* cr, cplx* sr);
-// largest real part of the eigenvalues of the leading mm x mm block of the
-// upper Hessenberg Hs (complex shifted QR iteration), out[0]; out[1] = 0 if
-// converged, 1 otherwise.
-__global__ void hessenberg_max_real_eig(int mm, int ld, const double* __restrict__ Hs, double* __restrict__ out);
-
+// Eigenvalues of the leading m x m block of an upper Hessenberg matrix
+// (row-major, leading dimension ld) by the shifted QR iteration in complex
+// arithmetic; out[0] = largest real part, out[1] = 1 if not converged.
+// Host and device callable; the library runs it on the host.
 // ------------------------------------------------------ solve plumbing ---
 // b_free[r] = (F restricted) computed by the host-built maps:
 // x_free gathers: out[i] = in[idx[i]]; scatter: out[idx[i]] = in[i]

@@ -77,8 +77,11 @@ struct DevLevel {
     // patches
     int npatch = 0, maxn = 0;
     long long nent = 0, nsq = 0;
-    int *poff = nullptr, *pdofs = nullptr;
+    int *poff = nullptr, *pdofs = nullptr, *pnv = nullptr;
     long long *moff = nullptr, *ioff64 = nullptr, *ioff32 = nullptr;
+    long long saddle_smem = 0;      // max scratch (doubles) of the patches inverted in shared memory
+    long long saddle_global = 0;    // total scratch (doubles) of the others
+    long long* scoff = nullptr;     // their offsets into the global scratch
     long long ninv64 = 0, ninv32 = 0;
     double* inv64 = nullptr;
     float* inv32 = nullptr;
@@ -118,6 +121,7 @@ struct stokes_mg {
     double *h = nullptr, *hn = nullptr, *resid = nullptr, *partial = nullptr, *scal = nullptr;
     double* pinned = nullptr;
     int partial_blocks = 0;
+    unsigned int* ticket = nullptr;
     // V-cycle graph I/O
     double *vin = nullptr, *vout = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -424,8 +428,10 @@ void capture_graph(stokes_mg* h, int prec, cudaStream_t s) {
 // ---- reductions for FGMRES / Arnoldi (FP64, deterministic two-stage)
 void mdot(stokes_mg* h, int n, int m, const double* V, long long ldv, const double* w, double* out, double* acc,
           bool sqrt_out, cudaStream_t s) {
-    launch(h, -1, s, [&] { skern::mdot_partial<<<h->partial_blocks, 256, 0, s>>>(n, m, V, ldv, w, h->partial); });
-    launch(h, -1, s, [&] { skern::mdot_final<<<1, 32, 0, s>>>(h->partial_blocks, m, h->partial, out, acc, sqrt_out ? 1 : 0); });
+    launch(h, -1, s, [&] {
+        skern::mdot_fused<<<skern::MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, h->partial, h->ticket, out, acc,
+                                                            sqrt_out ? 1 : 0);
+    });
 }
 
 void maxpy_l(stokes_mg* h, int n, int m, const double* V, long long ldv, const double* hh, double sign, double* w,
@@ -449,35 +455,40 @@ double d2h_scalar(stokes_mg* h, const double* d, cudaStream_t s) {
     return h->pinned[0];
 }
 
-// Arnoldi lambda_max on level li from v0 (device, FP64): returns the largest
-// real part of the Ritz values.
+// Arnoldi lambda_max on level li from v0 (device, FP64): all steps run on
+// the device without host round trips; the (m+1) x m Hessenberg matrix is
+// then read once, truncated at the first breakdown H[j+1][j] <= 1e-14
+// |H[j][j]|, and its eigenvalues found on the host (a 15 x 15 problem).
 double arnoldi_lmax(stokes_mg* h, int li, const double* v0, int steps, cudaStream_t s) {
     DevLevel& l = h->L[li];
     const int n = l.n;
-    const int m = std::min(steps, std::min(n, 16));
+    const int m = std::min(steps, std::min(n, skern::HESS_MAX - 1));
     double* V = h->V;     // reuse the FGMRES basis (>= m+1 vectors of length >= n)
     double* Hs = h->Hh;   // (m+1) x m
     launch(h, -1, s, [&] { skern::fill_vec<double><<<1, 256, 0, s>>>((long long)(m + 1) * m, 0.0, Hs); });
     mdot(h, n, 1, v0, n, v0, h->hn, nullptr, true, s);
     launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, v0, h->hn, V); });
-    int used = m;
     for (int j = 0; j < m; ++j) {
         double* w = V + (long long)(j + 1) * n;
         spmv<double>(h, PK_SPMV, l.K, skern::SPMV_SET, V + (long long)j * n, l.t64, nullptr, s);
         asm_apply<double>(h, l, l.t64, w, 1.0, 0.0, s);
         cgs2(h, n, j + 1, V, w, h->h, h->y, h->hn, s);
         launch(h, -1, s, [&] { skern::arnoldi_store<<<1, 1, 0, s>>>(j, m, Hs, h->h, h->hn); });
-        // breakdown test on the host (setup only): H[j+1][j] <= 1e-14 |H[j][j]|
-        double hnorm = d2h_scalar(h, h->hn, s);
-        double hjj = std::fabs(d2h_scalar(h, h->h + j, s));
-        if (!std::isfinite(hnorm)) throw StokesError(STOKES_ENONFINITE, "non-finite Arnoldi norm");
-        if (hnorm <= 1e-14 * hjj + 1e-300) { used = j + 1; break; }
         launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, h->hn, w); });
     }
-    launch(h, -1, s, [&] { skern::hessenberg_max_real_eig<<<1, 1, 0, s>>>(used, m, Hs, h->scal); });
-    CK(cudaMemcpyAsync(h->pinned, h->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    std::vector<double> H((size_t)(m + 1) * m);
+    CK(cudaMemcpyAsync(H.data(), Hs, sizeof(double) * H.size(), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return h->pinned[0];
+    int used = m;
+    for (int j = 0; j < m; ++j) {
+        const double sub = H[(size_t)(j + 1) * m + j], dj = H[(size_t)j * m + j];
+        if (!std::isfinite(sub) || !std::isfinite(dj)) throw StokesError(STOKES_ENONFINITE, "non-finite Arnoldi entry");
+        if (std::fabs(sub) <= 1e-14 * std::fabs(dj) + 1e-300) { used = j + 1; break; }
+    }
+    skern::cplx A[skern::HESS_MAX][skern::HESS_MAX], cr[skern::HESS_MAX], sr[skern::HESS_MAX];
+    double out[2];
+    skern::hessenberg_eig_core(used, m, H.data(), out, A, cr, sr);
+    return out[0];
 }
 
 // SplitMix64 start vector (the same counter-based definition as the tests'
@@ -585,6 +596,15 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         l.ninv32 = o32[l.npatch];
         l.poff = track(h, dupload(HL.patch_off, s));
         l.pdofs = track(h, dupload(HL.patch_dofs, s));
+        l.pnv = track(h, dupload(HL.patch_nv, s));
+        std::vector<long long> scoff(l.npatch + 1, 0);
+        for (int p = 0; p < l.npatch; ++p) {
+            const long long sc = skern::saddle_scratch(HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p]);
+            if (sc <= skern::SADDLE_SMEM_MAX_DOUBLES) { l.saddle_smem = std::max(l.saddle_smem, sc); scoff[p + 1] = scoff[p]; }
+            else scoff[p + 1] = scoff[p] + sc;
+        }
+        l.saddle_global = scoff[l.npatch];
+        l.scoff = track(h, dupload(scoff, s));
         l.moff = track(h, dupload(moff, s));
         l.ioff64 = track(h, dupload(o64, s));
         l.ioff32 = track(h, dupload(o32, s));
@@ -628,6 +648,32 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
         skern::patch_gather<<<l.npatch, 256, l.maxn * sizeof(int), s>>>(l.npatch, l.poff, l.pdofs, l.moff, l.K.rp, l.K.ci,
                                                                        l.K.v64, work);
     });
+    if (h->opts.patch_solver == 0) {
+        // saddle block inverse (default)
+        const int d = h->dim;
+        double* i64 = store ? l.inv64 : nullptr;
+        float* i32 = store ? l.inv32 : nullptr;
+        if (l.saddle_smem > 0) {
+            const size_t smem = (size_t)l.saddle_smem * sizeof(double);
+            CK(cudaFuncSetAttribute(skern::saddle_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            launch(h, PK_GJ, s, [&] {
+                skern::saddle_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
+                                                                       l.ioff32, i32, store ? 0 : 1,
+                                                                       skern::SADDLE_SMEM_MAX_DOUBLES, status);
+            });
+        }
+        if (l.saddle_global > 0) {
+            double* scr = dalloc<double>(l.saddle_global);
+            launch(h, PK_GJ, s, [&] {
+                skern::saddle_inverse_global<<<l.npatch, 256, 0, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
+                                                                      l.ioff32, i32, store ? 0 : 1,
+                                                                      skern::SADDLE_SMEM_MAX_DOUBLES, l.scoff, scr, status);
+            });
+            CK(cudaStreamSynchronize(s));
+            cudaFree(scr);
+        }
+        return;
+    }
     const int nsm = std::min(l.maxn, skern::GJ_SMEM_MAX_N);
     const size_t smem = (size_t)nsm * nsm * sizeof(double) + nsm * sizeof(double) + nsm * sizeof(int) + 64;
     CK(cudaFuncSetAttribute(skern::gj_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -833,7 +879,7 @@ void stokes_mg_default_opts(stokes_mg_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->hierarchy = STOKES_HIER_GRADUAL;
     o->nu_p = o->nu_h = o->n_V = 1;
-    o->eig_steps = 10;
+    o->eig_steps = 15;
     o->eig_seed = 0;
     o->cheb_lo = 0.1;
     o->cheb_hi = 1.1;
@@ -867,6 +913,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         require(o.eig_steps >= 1 && o.eig_steps <= 15, "eig_steps must be in [1, 15]");
         require(o.precision == STOKES_FP64 || o.precision == STOKES_MIXED, "bad precision");
         require(o.cheb_hi > o.cheb_lo && o.cheb_lo > 0, "bad Chebyshev interval");
+        require(o.patch_solver == 0 || o.patch_solver == 1, "patch_solver must be 0 (saddle block) or 1 (Gauss-Jordan)");
         if (!o.host_only) CK(cudaGetDevice(&h->device));
         for (int kk = 0; kk < 5; ++kk) h->prof[kk].on = (o.prof_mask >> kk) & 1;
         cudaStream_t s = (cudaStream_t)stream;
@@ -935,8 +982,10 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         h->hn = track(h.get(), dalloc<double>(2));
         h->resid = track(h.get(), dalloc<double>(2));
         h->scal = track(h.get(), dalloc<double>(4));
-        h->partial_blocks = 152 * 2;
+        h->partial_blocks = skern::MDOT_BLOCKS;
         h->partial = track(h.get(), dalloc<double>((size_t)h->partial_blocks * 32));
+        h->ticket = track(h.get(), dalloc<unsigned int>(1));
+        CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s));
         h->vin = track(h.get(), dalloc<double>(n0));
         h->vout = track(h.get(), dalloc<double>(n0));
         CK(cudaMallocHost((void**)&h->pinned, 64));

@@ -45,6 +45,7 @@ def pair(name, precision=P.FP64, **o):
         return _cache[key]
     (v, c), nref, fam, k, sched, bary = CASES[name]
     opts = mg.Options(nu_p=o.get("nu_p", 1), nu_h=o.get("nu_h", 1), n_V=o.get("n_V", 1))
+    # the oracle has one exact patch solve; patch_solver only selects the library's kernel
     ora = mg.Hierarchy(v, c, nref, fam, sched, barycentric=bary, opts=opts)
     lm = [L.lmax for L in ora.levels[:-1]]
     h = P.StokesMG(v, c, nref, fam, k, barycentric=bary, hierarchy=P.HIER_EXPLICIT, schedule=sched,
@@ -96,10 +97,12 @@ def test_a1_patch_gather_is_exact(name):
 
 
 @pytest.mark.parametrize("name", NAMES)
-def test_a2_patch_inverses(name):
-    """a2: batched partial-pivot Gauss-Jordan inverses equal the inverse of
-    the oracle's patch block (LAPACK LU) to cond * eps."""
-    h, ora, perms = pair(name)
+@pytest.mark.parametrize("solver", [0, 1])
+def test_a2_patch_inverses(name, solver):
+    """a2: the batched FP64 patch inverses (0: saddle block inverse, 1:
+    partial-pivot Gauss-Jordan) equal the inverse of the oracle's patch block
+    (LAPACK LU) to cond * eps."""
+    h, ora, perms = pair(name, patch_solver=solver)
     for li, L in enumerate(ora.levels[:-1]):
         got = h.patch_inverses(li)
         off, dofs = h.patches(li)
@@ -134,7 +137,7 @@ def test_a3_arnoldi_lambda_max(name):
     lm = hd.info()["lmax"]
     for li, L in enumerate(ora.levels[:-1]):
         v0 = rng.uniform_pm1(0, li, perms[li])
-        want = mg.arnoldi_lmax(L.disc.K, L.asm.apply, v0, 10)
+        want = mg.arnoldi_lmax(L.disc.K, L.asm.apply, v0, mg.Options().eig_steps)
         assert abs(lm[li] - want) <= 1e-9 * abs(want)
     hd.close()
 
