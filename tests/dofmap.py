@@ -50,3 +50,26 @@ def oracle_free_keys(disc):
 def level_perm(h, level, disc):
     xyz, comp, cc = h.level_dofs(level)
     return permutation(keys(xyz, comp, cc), oracle_free_keys(disc))
+
+
+def oracle_pressure_keys(disc):
+    """Keys of the oracle's pressure nodes (full field order), matching
+    stokes_mg_nodes' (pres_xyz, pres_cell_center)."""
+    center = np.zeros_like(disc.Q.coords)
+    if not disc.Q.continuous:
+        cells = np.asarray(disc.cells)
+        cent = disc.verts[cells].mean(axis=1)
+        owner = np.zeros(disc.Q.n, dtype=np.int64)
+        for ci in range(len(cells)):
+            owner[disc.Q.cell_nodes[ci]] = ci
+        center = cent[owner]
+    return keys(disc.Q.coords, np.zeros(disc.Q.n), center)
+
+
+def full_field_perms(h, disc):
+    """(velocity-node perm, pressure-node perm): library node perm[i] is
+    oracle node i, for the full fields of stokes_solve."""
+    vx, px, pc = h.nodes()
+    pv = permutation(keys(vx, np.zeros(len(vx))), keys(disc.V.coords, np.zeros(disc.V.n)))
+    pq = permutation(keys(px, np.zeros(len(px)), pc), oracle_pressure_keys(disc))
+    return pv, pq
