@@ -336,9 +336,15 @@ static Poly deriv(const Poly& p, int a) {
     return q;
 }
 
-// exact integral of x^a y^b z^c over the reference d-simplex
+// exact integral of x^a y^b z^c over the reference d-simplex:
+// a! b! c! / (a + b + c + d)!
 static double mono_integral(int d, int a, int b, int c) {
-    return factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + d);
+    static const std::vector<double> f = [] {
+        std::vector<double> t(80, 1.0);
+        for (int i = 1; i < 80; ++i) t[i] = t[i - 1] * i;
+        return t;
+    }();
+    return f[a] * f[b] * f[c] / f[a + b + c + d];
 }
 
 static double integrate_product(int d, const Poly& p, const Poly& q) {
@@ -388,30 +394,60 @@ CSR transpose(const CSR& a) {
     CSR t;
     t.nr = a.ncol;
     t.ncol = a.nr;
+    const int T = chunk_count(a.nr);
+    std::vector<std::vector<int>> hist(T, std::vector<int>(a.ncol + 1, 0));
+    Pool::get().run(T, [&](int th) {
+        const int lo = (int)((long long)a.nr * th / T), hi = (int)((long long)a.nr * (th + 1) / T);
+        auto& hh = hist[th];
+        for (int p = a.rp[lo]; p < a.rp[hi]; ++p) hh[a.ci[p]]++;
+    });
+    // column c of thread th starts after all of column c's entries from
+    // threads < th: rows stay in increasing order within every column
     t.rp.assign(t.nr + 1, 0);
-    for (int c : a.ci) t.rp[c + 1]++;
-    for (int i = 0; i < t.nr; ++i) t.rp[i + 1] += t.rp[i];
-    t.ci.resize(a.ci.size());
-    t.v.resize(a.v.size());
-    std::vector<int> fill(t.rp.begin(), t.rp.end() - 1);
-    for (int r = 0; r < a.nr; ++r)
-        for (int p = a.rp[r]; p < a.rp[r + 1]; ++p) {
-            int q = fill[a.ci[p]]++;
-            t.ci[q] = r;
-            t.v[q] = a.v[p];
+    std::vector<std::vector<int>> start(T, std::vector<int>(a.ncol));
+    long long run = 0;
+    for (int col = 0; col < a.ncol; ++col) {
+        t.rp[col] = (int)run;
+        for (int th = 0; th < T; ++th) {
+            start[th][col] = (int)run;
+            run += hist[th][col];
         }
+    }
+    t.rp[t.nr] = (int)run;
+    t.ci.resize(run);
+    t.v.resize(run);
+    Pool::get().run(T, [&](int th) {
+        const int lo = (int)((long long)a.nr * th / T), hi = (int)((long long)a.nr * (th + 1) / T);
+        auto& st = start[th];
+        for (int r = lo; r < hi; ++r)
+            for (int p = a.rp[r]; p < a.rp[r + 1]; ++p) {
+                const int q = st[a.ci[p]]++;
+                t.ci[q] = r;
+                t.v[q] = a.v[p];
+            }
+    });
     return t;
 }
 
 // ------------------------------------------------------------------ spaces --
 struct Topology {
-    int d = 0;
-    std::unordered_map<uint64_t, int> edge_id;
-    std::unordered_map<uint64_t, int> face_id;     // 3D only
-    std::vector<unsigned char> bvert;
-    std::unordered_set<uint64_t> bedge, bface;
-    std::vector<int> v2c_off, v2c;                  // vertex -> cells
+    int d = 0, ne = 0, nf = 0;
+    std::vector<int> cell_edge;             // [nc][d==2 ? 3 : 6], local edge order of kEdges
+    std::vector<int> cell_face;             // [nc][4] (3D): face opposite local vertex i
+    std::vector<unsigned char> bvert, bedge, bface;   // on the boundary, by vertex / edge / face id
+    std::vector<int> v2c_off, v2c;          // vertex -> cells
 };
+
+// local vertex pairs of the edges of a simplex (2D uses the first three
+// entries of the triangle table)
+static const int kEdges2[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+static const int kEdges3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+static inline int local_edge(int d, int i, int j) {
+    if (i > j) std::swap(i, j);
+    if (d == 2) return i == 0 ? j - 1 : 2;
+    return i == 0 ? j - 1 : (i == 1 ? j + 1 : 5);
+}
 
 static inline uint64_t face_key(int a, int b, int c, int nv) {
     int t[3] = {a, b, c};
@@ -420,60 +456,61 @@ static inline uint64_t face_key(int a, int b, int c, int nv) {
 }
 
 static void build_topology(const Mesh& m, Topology& T) {
-    const int d = m.d, nvpc = d + 1;
+    const int d = m.d, nvpc = d + 1, nle = d == 2 ? 3 : 6;
     T.d = d;
-    T.edge_id.reserve((size_t)m.nc * 3);
+    T.cell_edge.resize((size_t)m.nc * nle);
+    std::unordered_map<uint64_t, int> eid;
+    eid.reserve((size_t)m.nc * (d == 2 ? 2 : 2));
     for (int e = 0; e < m.nc; ++e) {
         const int* v = &m.C[(size_t)e * nvpc];
-        for (int i = 0; i < nvpc; ++i)
-            for (int j = i + 1; j < nvpc; ++j) {
-                uint64_t key = edge_key(v[i], v[j]);
-                if (!T.edge_id.count(key)) {
-                    int id = (int)T.edge_id.size();
-                    T.edge_id.emplace(key, id);
-                }
-            }
-        if (d == 3)
+        for (int t = 0; t < nle; ++t) {
+            const int i = d == 2 ? kEdges2[t][0] : kEdges3[t][0], j = d == 2 ? kEdges2[t][1] : kEdges3[t][1];
+            auto ins = eid.emplace(edge_key(v[i], v[j]), (int)eid.size());
+            T.cell_edge[(size_t)e * nle + t] = ins.first->second;
+        }
+    }
+    T.ne = (int)eid.size();
+    std::vector<int> facet_count;
+    if (d == 3) {
+        T.cell_face.resize((size_t)m.nc * 4);
+        std::unordered_map<uint64_t, int> fid;
+        fid.reserve((size_t)m.nc * 2);
+        for (int e = 0; e < m.nc; ++e) {
+            const int* v = &m.C[(size_t)e * 4];
             for (int i = 0; i < 4; ++i) {
                 int f[3], t = 0;
                 for (int j = 0; j < 4; ++j)
                     if (j != i) f[t++] = v[j];
-                uint64_t key = face_key(f[0], f[1], f[2], m.nv);
-                if (!T.face_id.count(key)) {
-                    int id = (int)T.face_id.size();
-                    T.face_id.emplace(key, id);
-                }
+                auto ins = fid.emplace(face_key(f[0], f[1], f[2], m.nv), (int)fid.size());
+                T.cell_face[(size_t)e * 4 + i] = ins.first->second;
             }
-    }
-    // boundary facets: facets owned by one cell
-    std::unordered_map<uint64_t, int> cnt;
-    for (int e = 0; e < m.nc; ++e) {
-        const int* v = &m.C[(size_t)e * nvpc];
-        for (int i = 0; i < nvpc; ++i) {
-            int f[3], t = 0;
-            for (int j = 0; j < nvpc; ++j)
-                if (j != i) f[t++] = v[j];
-            uint64_t key = d == 2 ? edge_key(f[0], f[1]) : face_key(f[0], f[1], f[2], m.nv);
-            cnt[key]++;
         }
+        T.nf = (int)fid.size();
+        facet_count.assign(T.nf, 0);
+        for (int x : T.cell_face) facet_count[x]++;
+    } else {
+        facet_count.assign(T.ne, 0);
+        for (int x : T.cell_edge) facet_count[x]++;
     }
+    // boundary facets: owned by one cell; mark their vertices, edges, faces
     T.bvert.assign(m.nv, 0);
+    T.bedge.assign(T.ne, 0);
+    T.bface.assign(T.nf, 0);
     for (int e = 0; e < m.nc; ++e) {
         const int* v = &m.C[(size_t)e * nvpc];
-        for (int i = 0; i < nvpc; ++i) {
-            int f[3], t = 0;
+        for (int i = 0; i < nvpc; ++i) {          // facet opposite local vertex i
+            const int fidx = d == 3 ? T.cell_face[(size_t)e * 4 + i]
+                                    : T.cell_edge[(size_t)e * 3 + local_edge(2, (i + 1) % 3, (i + 2) % 3)];
+            if (facet_count[fidx] != 1) continue;
             for (int j = 0; j < nvpc; ++j)
-                if (j != i) f[t++] = v[j];
-            uint64_t key = d == 2 ? edge_key(f[0], f[1]) : face_key(f[0], f[1], f[2], m.nv);
-            if (cnt[key] != 1) continue;
-            for (int j = 0; j < d; ++j) T.bvert[f[j]] = 1;
+                if (j != i) T.bvert[v[j]] = 1;
             if (d == 2) {
-                T.bedge.insert(key);
+                T.bedge[fidx] = 1;
             } else {
-                T.bface.insert(key);
-                T.bedge.insert(edge_key(f[0], f[1]));
-                T.bedge.insert(edge_key(f[0], f[2]));
-                T.bedge.insert(edge_key(f[1], f[2]));
+                T.bface[fidx] = 1;
+                for (int a = 0; a < 4; ++a)
+                    for (int b2 = a + 1; b2 < 4; ++b2)
+                        if (a != i && b2 != i) T.bedge[T.cell_edge[(size_t)e * 6 + local_edge(3, a, b2)]] = 1;
             }
         }
     }
@@ -533,10 +570,14 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         return;
     }
     // rank tables for compositions of k into m positive parts
-    std::vector<std::map<long long, int>> rank(5);
+    std::vector<std::vector<int>> rank(5);
     std::vector<int> nint(5, 0);
     for (int mm = 1; mm <= nvpc; ++mm) {
         nint[mm] = binom(k - 1, mm - 1);
+        long long ncode = 1;
+        for (int t = 0; t < mm; ++t) ncode *= (k + 1);
+        rank[mm].assign(ncode, -1);
+        int nr = 0;
         std::vector<int> part(mm, 1);
         // enumerate all compositions by recursion over a simple odometer
         std::function<void(int, int)> rec = [&](int pos, int left) {
@@ -545,8 +586,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
                     part[pos] = left;
                     long long code = 0;
                     for (int t = 0; t < mm; ++t) code = code * (k + 1) + part[t];
-                    int r = (int)rank[mm].size();
-                    rank[mm][code] = r;
+                    rank[mm][code] = nr++;
                 }
                 return;
             }
@@ -557,7 +597,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         };
         if (k >= mm) rec(0, k);
     }
-    const long long ne = (long long)T.edge_id.size(), nf = (long long)T.face_id.size();
+    const long long ne = T.ne, nf = T.nf;
     long long base[5] = {0, 0, 0, 0, 0};
     base[1] = 0;
     base[2] = base[1] + (long long)m.nv * nint[1];
@@ -572,18 +612,20 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
     for (int e = 0; e < m.nc; ++e) {
         const int* v = &m.C[(size_t)e * nvpc];
         for (int l = 0; l < nb; ++l) {
-            int sv[4], sa[4], mm = 0;
+            int sv[4], sa[4], sl[4], mm = 0;
             for (int i = 0; i < nvpc; ++i)
-                if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sa[mm] = re.alpha[l][i]; ++mm; }
+                if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sa[mm] = re.alpha[l][i]; sl[mm] = i; ++mm; }
             for (int a = 1; a < mm; ++a)          // sort by global vertex id
-                for (int b = a; b > 0 && sv[b - 1] > sv[b]; --b) { std::swap(sv[b - 1], sv[b]); std::swap(sa[b - 1], sa[b]); }
+                for (int b = a; b > 0 && sv[b - 1] > sv[b]; --b) {
+                    std::swap(sv[b - 1], sv[b]); std::swap(sa[b - 1], sa[b]); std::swap(sl[b - 1], sl[b]);
+                }
             long long code = 0;
             for (int t = 0; t < mm; ++t) code = code * (k + 1) + sa[t];
-            int r = rank[mm].at(code);
+            int r = rank[mm][code];
             long long eid;
             if (mm == 1) eid = sv[0];
-            else if (mm == 2) eid = T.edge_id.at(edge_key(sv[0], sv[1]));
-            else if (mm == 3 && d == 3) eid = T.face_id.at(face_key(sv[0], sv[1], sv[2], m.nv));
+            else if (mm == 2) eid = T.cell_edge[(size_t)e * (d == 2 ? 3 : 6) + local_edge(d, sl[0], sl[1])];
+            else if (mm == 3 && d == 3) eid = T.cell_face[(size_t)e * 4 + (6 - sl[0] - sl[1] - sl[2])];
             else eid = e;   // cell interior
             tmp[(size_t)e * nb + l] = (int)(base[mm] + eid * nint[mm] + r);
         }
@@ -612,15 +654,19 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
                 for (int i = 0; i < nvpc; ++i) x += re.alpha[l][i] * m.X[(size_t)v[i] * d + c];
                 S.X[(size_t)id * d + c] = x / k;
             }
-            int sv[4], mm = 0;
+            int sv[4], sl[4], mm = 0;
             for (int i = 0; i < nvpc; ++i)
-                if (re.alpha[l][i] > 0) sv[mm++] = v[i];
-            std::sort(sv, sv + mm);
-            for (int t = 0; t < mm; ++t) S.support[id][t] = sv[t];
+                if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sl[mm] = i; ++mm; }
+            {
+                int tmpv[4];
+                for (int t = 0; t < mm; ++t) tmpv[t] = sv[t];
+                std::sort(tmpv, tmpv + mm);
+                for (int t = 0; t < mm; ++t) S.support[id][t] = tmpv[t];
+            }
             bool b;
             if (mm == 1) b = T.bvert[sv[0]];
-            else if (mm == 2) b = T.bedge.count(edge_key(sv[0], sv[1])) > 0;
-            else if (mm == 3 && d == 3) b = T.bface.count(face_key(sv[0], sv[1], sv[2], m.nv)) > 0;
+            else if (mm == 2) b = T.bedge[T.cell_edge[(size_t)e * (d == 2 ? 3 : 6) + local_edge(d, sl[0], sl[1])]];
+            else if (mm == 3 && d == 3) b = T.bface[T.cell_face[(size_t)e * 4 + (6 - sl[0] - sl[1] - sl[2])]];
             else b = false;
             S.boundary[id] = b;
         }
@@ -1007,9 +1053,13 @@ static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const 
     CSR P;
     P.nr = Vf.n;
     P.ncol = Vc.n;
-    std::vector<std::vector<std::pair<int, double>>> rows(Vf.n);
+    // a row has at most nbc entries: fill fixed slots in parallel, then compact
+    std::vector<int> cnt(Vf.n);
+    fvec<int> scol((size_t)Vf.n * nbc);
+    fvec<double> sval((size_t)Vf.n * nbc);
     parallel_for(Vf.n, [&](int lo, int hi, int) {
-        std::vector<double> val(nbc);
+        double val[320];
+        std::pair<int, double> row[320];
         for (int i = lo; i < hi; ++i) {
             int fc = Vf.owner_cell[i];
             int cc = parent ? (*parent)[fc] : fc;
@@ -1021,21 +1071,27 @@ static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const 
                 for (int c = 0; c < d; ++c) s += g.Jinv[a * d + c] * (Vf.X[(size_t)i * d + c] - mc.X[(size_t)cv[0] * d + c]);
                 xi[a] = s;
             }
-            rec.eval(xi, val.data());
+            rec.eval(xi, val);
+            int m = 0;
             for (int l = 0; l < nbc; ++l)
-                if (std::fabs(val[l]) > 1e-14) rows[i].push_back({Vc.cell_nodes[(size_t)cc * nbc + l], val[l]});
-            std::sort(rows[i].begin(), rows[i].end());
+                if (std::fabs(val[l]) > 1e-14) row[m++] = {Vc.cell_nodes[(size_t)cc * nbc + l], val[l]};
+            std::sort(row, row + m);
+            cnt[i] = m;
+            for (int t = 0; t < m; ++t) {
+                scol[(size_t)i * nbc + t] = row[t].first;
+                sval[(size_t)i * nbc + t] = row[t].second;
+            }
         }
     });
     P.rp.assign(P.nr + 1, 0);
-    for (int i = 0; i < P.nr; ++i) P.rp[i + 1] = P.rp[i] + (int)rows[i].size();
+    for (int i = 0; i < P.nr; ++i) P.rp[i + 1] = P.rp[i] + cnt[i];
     P.ci.resize(P.rp[P.nr]);
     P.v.resize(P.rp[P.nr]);
     parallel_for(P.nr, [&](int lo, int hi, int) {
         for (int i = lo; i < hi; ++i)
-            for (size_t t = 0; t < rows[i].size(); ++t) {
-                P.ci[P.rp[i] + t] = rows[i][t].first;
-                P.v[P.rp[i] + t] = rows[i][t].second;
+            for (int t = 0; t < cnt[i]; ++t) {
+                P.ci[P.rp[i] + t] = scol[(size_t)i * nbc + t];
+                P.v[P.rp[i] + t] = sval[(size_t)i * nbc + t];
             }
     });
     return P;
@@ -1147,6 +1203,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     if ((int)ls.size() > 16) throw std::invalid_argument("too many levels");
     H.levels.assign(ls.size(), Level());
     std::map<std::pair<int, int>, RefElement> refs;
+    std::map<std::pair<int, int>, RefTensors> tensors;
     auto ref = [&](int dd, int kk) -> RefElement& {
         auto key = std::make_pair(dd, kk);
         auto it = refs.find(key);
@@ -1168,8 +1225,10 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         const RefElement& rq = ref(d, L.k - 1);
         build_space(m, topo[L.mesh_index], rv, true, L.V);
         build_space(m, topo[L.mesh_index], rq, L.family == 0, L.Q);
-        RefTensors RT;
-        RT.init(rv, rq);
+        auto rkey = std::make_pair(d * 100 + L.k, 0);
+        auto rit = tensors.find(rkey);
+        if (rit == tensors.end()) { tensors[rkey].init(rv, rq); rit = tensors.find(rkey); }
+        const RefTensors& RT = rit->second;
         double tb = now_ms();
         assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
         double tc = now_ms();
