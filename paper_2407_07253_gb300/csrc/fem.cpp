@@ -1151,7 +1151,8 @@ static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Le
     F.R = transpose(P);
 }
 
-void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell, Hierarchy& H) {
+void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell, Hierarchy& H,
+                     const std::function<void(int)>& on_level) {
     double t0 = now_ms();
     const int d = coarse.d;
     if (d != 2 && d != 3) throw std::invalid_argument("dim must be 2 or 3");
@@ -1236,6 +1237,11 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         H.t_spaces_ms += tb - ta;
         H.t_matrices_ms += tc - tb;
         H.t_patches_ms += now_ms() - tc;
+        if (on_level) {
+            const double tcb = now_ms();
+            on_level((int)l);
+            H.t_callbacks_ms += now_ms() - tcb;
+        }
     }
     double tt = now_ms();
     for (size_t l = 0; l + 1 < ls.size(); ++l) {
@@ -1244,7 +1250,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         monolithic_interp(H.meshes[F.mesh_index], F, H.meshes[C.mesh_index], C, ref(d, C.k), ref(d, C.k - 1), par_map);
     }
     H.t_transfers_ms = now_ms() - tt;
-    H.t_assembly_ms = now_ms() - t1;
+    H.t_assembly_ms = now_ms() - t1 - H.t_callbacks_ms;
 }
 
 }  // namespace sfem

@@ -9,6 +9,7 @@
 #pragma once
 #include <array>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <memory>
 #include <utility>
@@ -115,12 +116,15 @@ struct Hierarchy {
     std::vector<std::vector<int>> parents;    // parents[i]: cells of meshes[i] -> meshes[i+1]
     std::vector<Level> levels;
     double t_mesh_ms = 0, t_assembly_ms = 0;
-    double t_spaces_ms = 0, t_matrices_ms = 0, t_patches_ms = 0, t_transfers_ms = 0;
+    double t_spaces_ms = 0, t_matrices_ms = 0, t_patches_ms = 0, t_transfers_ms = 0, t_callbacks_ms = 0;
 };
 
 // Build the whole host hierarchy; throws std::runtime_error on invalid input.
+// on_level(l), if given, runs as soon as level l's spaces, operator and
+// patches exist (before coarser levels and the transfers are built), so the
+// caller can start device work on it while the host continues.
 void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell,
-                     Hierarchy& H);
+                     Hierarchy& H, const std::function<void(int)>& on_level = {});
 
 int num_threads();
 

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -96,6 +97,12 @@ struct DevLevel {
     double lmax = 0;
 };
 
+struct PendingPatches {
+    int level = 0;
+    double* work = nullptr;
+    int* status = nullptr;
+};
+
 struct Prof {
     bool on = false;
     long long launches = 0;
@@ -137,6 +144,12 @@ struct stokes_mg {
     Prof prof[5];
     bool capturing = false;
     bool host_only = false;
+    // setup in flight
+    std::vector<PendingPatches> pending;
+    int* c_ipiv = nullptr;
+    double* c_colk = nullptr;
+    int* c_status = nullptr;
+    cudaStream_t s_up = nullptr, s_coarse = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -578,8 +591,6 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     l.K = upload_csr(h, HL.K, want32, s);
     const bool last = li + 1 == (int)h->H.levels.size();
     if (!last) {
-        l.P = upload_csr(h, HL.P, want32, s);
-        l.R = upload_csr(h, HL.R, want32, s);
         l.npatch = (int)HL.patch_off.size() - 1;
         l.nent = HL.patch_dofs.size();
         std::vector<long long> moff(l.npatch + 1, 0), o64(l.npatch + 1, 0), o32(l.npatch + 1, 0);
@@ -636,6 +647,13 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         l.b32 = track(h, dalloc<float>(l.n)); l.e32 = track(h, dalloc<float>(l.n)); l.r32 = track(h, dalloc<float>(l.n));
         l.d32 = track(h, dalloc<float>(l.n)); l.t32 = track(h, dalloc<float>(l.n)); l.u32 = track(h, dalloc<float>(l.n));
     }
+}
+
+void upload_transfers(stokes_mg* h, int li, bool want32, cudaStream_t s) {
+    const sfem::Level& HL = h->H.levels[li];
+    DevLevel& l = h->L[li];
+    l.P = upload_csr(h, HL.P, want32, s);
+    l.R = upload_csr(h, HL.R, want32, s);
 }
 
 // gather K_i and invert every patch of level li; work receives the
@@ -696,35 +714,48 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
     }
 }
 
-void setup_patches(stokes_mg* h, cudaStream_t s) {
-    for (int li = 0; li + 1 < (int)h->L.size(); ++li) {
-        DevLevel& l = h->L[li];
-        if (l.npatch == 0) continue;
-        double* work = dalloc<double>(l.nsq);
-        int* status = dalloc<int>(l.npatch);
-        CK(cudaMemsetAsync(status, 0, sizeof(int) * l.npatch, s));
-        try {
-            gather_and_invert(h, li, work, true, status, s);
-            std::vector<int> hs(l.npatch);
-            CK(cudaMemcpyAsync(hs.data(), status, sizeof(int) * l.npatch, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int p = 0; p < l.npatch; ++p)
-                if (hs[p] != 0) {
-                    h->st.singular_patch = li * (1 << 24) + p;
-                    throw StokesError(STOKES_ESINGULAR, "zero pivot in patch " + std::to_string(p) + " of level " +
-                                                            std::to_string(li));
-                }
-        } catch (...) {
-            cudaFree(work);
-            cudaFree(status);
-            throw;
-        }
-        cudaFree(work);
-        cudaFree(status);
-    }
+// Launch the gather + inversion of level li on stream s without waiting;
+// the workspace and status array stay in h->pending until finish_patches.
+void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    if (l.npatch == 0) return;
+    PendingPatches pp;
+    pp.level = li;
+    pp.work = dalloc<double>(l.nsq);
+    pp.status = dalloc<int>(l.npatch);
+    h->pending.push_back(pp);
+    CK(cudaMemsetAsync(pp.status, 0, sizeof(int) * l.npatch, s));
+    gather_and_invert(h, li, pp.work, true, pp.status, s);
 }
 
-void setup_coarse(stokes_mg* h, cudaStream_t s) {
+void free_pending(stokes_mg* h) {
+    for (auto& pp : h->pending) {
+        cudaFree(pp.work);
+        cudaFree(pp.status);
+    }
+    h->pending.clear();
+}
+
+// Wait for every launched patch inversion and report the first zero pivot.
+void finish_patches(stokes_mg* h, cudaStream_t s) {
+    CK(cudaStreamSynchronize(s));
+    for (auto& pp : h->pending) {
+        DevLevel& l = h->L[pp.level];
+        std::vector<int> hs(l.npatch);
+        CK(cudaMemcpy(hs.data(), pp.status, sizeof(int) * l.npatch, cudaMemcpyDeviceToHost));
+        for (int p = 0; p < l.npatch; ++p)
+            if (hs[p] != 0) {
+                h->st.singular_patch = pp.level * (1 << 24) + p;
+                throw StokesError(STOKES_ESINGULAR, "zero pivot in patch " + std::to_string(p) + " of level " +
+                                                        std::to_string(pp.level));
+            }
+    }
+    free_pending(h);
+}
+
+// Bordered coarse matrix (zero-mean pressure constraint, Sec. 2) inverted in
+// place by one Gauss-Jordan step per pivot on stream s (no wait).
+void launch_coarse(stokes_mg* h, cudaStream_t su, cudaStream_t s) {
     const sfem::Level& C = h->H.levels.back();
     const int n = C.n_free, nb = n + 1;
     h->nc = n;
@@ -737,30 +768,45 @@ void setup_coarse(stokes_mg* h, cudaStream_t s) {
         A[(size_t)r * nb + n] = C.pint[q];
         A[(size_t)n * nb + r] = C.pint[q];
     }
-    h->Cinv = track(h, dupload(A, s));
-    int* ipiv = dalloc<int>(nb);
-    double* colk = dalloc<double>(nb);
-    int* status = dalloc<int>(1);
-    CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+    h->Cinv = track(h, dupload(A, su));
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, su));
+    CK(cudaStreamWaitEvent(s, ev, 0));
+    CK(cudaEventDestroy(ev));
+    h->c_ipiv = dalloc<int>(nb);
+    h->c_colk = dalloc<double>(nb);
+    h->c_status = dalloc<int>(1);
+    CK(cudaMemsetAsync(h->c_status, 0, sizeof(int), s));
     const long long tot = (long long)nb * nb;
     const int egrid = (int)std::min<long long>((tot + 255) / 256, 152LL * 8);
     for (int k = 0; k < nb; ++k) {
-        launch(h, -1, s, [&] { skern::gj_step_pivot<<<1, 256, 0, s>>>(nb, k, h->Cinv, ipiv, colk, status); });
-        launch(h, -1, s, [&] { skern::gj_step_eliminate<<<egrid, 256, 0, s>>>(nb, k, h->Cinv, colk); });
+        launch(h, -1, s, [&] { skern::gj_step_pivot<<<1, 256, 0, s>>>(nb, k, h->Cinv, h->c_ipiv, h->c_colk, h->c_status); });
+        launch(h, -1, s, [&] { skern::gj_step_eliminate<<<egrid, 256, 0, s>>>(nb, k, h->Cinv, h->c_colk); });
     }
-    launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, ipiv); });
+    launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
+    h->cb64 = track(h, dalloc<double>(n));
+    h->ce64 = track(h, dalloc<double>(n));
+}
+
+void free_coarse_ws(stokes_mg* h) {
+    if (h->c_ipiv) cudaFree(h->c_ipiv);
+    if (h->c_colk) cudaFree(h->c_colk);
+    if (h->c_status) cudaFree(h->c_status);
+    h->c_ipiv = nullptr;
+    h->c_colk = nullptr;
+    h->c_status = nullptr;
+}
+
+void finish_coarse(stokes_mg* h, cudaStream_t s) {
     int hs = 0;
-    CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hs, h->c_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    cudaFree(ipiv);
-    cudaFree(colk);
-    cudaFree(status);
+    free_coarse_ws(h);
     if (hs != 0) {
         h->st.singular_patch = -2;
         throw StokesError(STOKES_ESINGULAR, "zero pivot in the coarse bordered LU");
     }
-    h->cb64 = track(h, dalloc<double>(n));
-    h->ce64 = track(h, dalloc<double>(n));
 }
 
 void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
@@ -948,7 +994,34 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             require(false, "unknown hierarchy");
         }
         require(!(family == STOKES_SV && spec.schedule.size() < 2), "Scott-Vogelius needs at least one p-coarsening");
-        sfem::build_hierarchy(cm, spec, nu_cell, h->H);
+        const bool want32 = o.precision == STOKES_MIXED;
+        double t_cb_upload = 0;
+        std::function<void(int)> on_level;
+        if (!o.host_only) {
+            // level-by-level pipeline: upload on s_up, then the patch
+            // inversion (or the coarse factorisation) starts on the device
+            // while the host assembles the next, coarser levels
+            CK(cudaStreamCreateWithFlags(&h->s_up, cudaStreamNonBlocking));
+            CK(cudaStreamCreateWithFlags(&h->s_coarse, cudaStreamNonBlocking));
+            on_level = [&](int li) {
+                const double tu = host_ms();
+                const int nlv = (int)h->H.levels.size();
+                if ((int)h->L.size() != nlv) h->L.assign(nlv, DevLevel());
+                upload_level(h.get(), li, want32, h->s_up);
+                if (li + 1 < nlv) {
+                    cudaEvent_t ev;
+                    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                    CK(cudaEventRecord(ev, h->s_up));
+                    CK(cudaStreamWaitEvent(s, ev, 0));
+                    CK(cudaEventDestroy(ev));
+                    launch_patches(h.get(), li, s);
+                } else {
+                    launch_coarse(h.get(), h->s_up, h->s_coarse);
+                }
+                t_cb_upload += host_ms() - tu;
+            };
+        }
+        sfem::build_hierarchy(cm, spec, nu_cell, h->H, on_level);
         h->st.t_mesh_ms = h->H.t_mesh_ms;
         h->st.t_assembly_ms = h->H.t_assembly_ms;
         h->st.t_spaces_ms = h->H.t_spaces_ms;
@@ -963,10 +1036,8 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             fill_stats(h.get());
             return STOKES_OK;
         }
-        const bool want32 = o.precision == STOKES_MIXED;
         double t1 = host_ms();
-        h->L.assign(nl, DevLevel());
-        for (int li = 0; li < nl; ++li) upload_level(h.get(), li, want32, s);
+        for (int li = 0; li + 1 < nl; ++li) upload_transfers(h.get(), li, want32, h->s_up);
         // FGMRES / Arnoldi buffers
         const int n0 = h->L[0].n;
         const int m = h->restart;
@@ -985,19 +1056,20 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         h->partial_blocks = skern::MDOT_BLOCKS;
         h->partial = track(h.get(), dalloc<double>((size_t)h->partial_blocks * 32));
         h->ticket = track(h.get(), dalloc<unsigned int>(1));
-        CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s));
+        CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->s_up));
         h->vin = track(h.get(), dalloc<double>(n0));
         h->vout = track(h.get(), dalloc<double>(n0));
         CK(cudaMallocHost((void**)&h->pinned, 64));
-        setup_solve_buffers(h.get(), s);
-        CK(cudaStreamSynchronize(s));
-        h->st.t_upload_ms = host_ms() - t1;
+        setup_solve_buffers(h.get(), h->s_up);
+        CK(cudaStreamSynchronize(h->s_up));
+        h->st.t_upload_ms = t_cb_upload + host_ms() - t1;
+        // what remains of the patch inversions and of the coarse
+        // factorisation once the host is done
         t1 = host_ms();
-        setup_patches(h.get(), s);
-        CK(cudaStreamSynchronize(s));
+        finish_patches(h.get(), s);
         h->st.t_gather_lu_ms = host_ms() - t1;
         t1 = host_ms();
-        setup_coarse(h.get(), s);
+        finish_coarse(h.get(), h->s_coarse);
         h->st.t_coarse_ms = host_ms() - t1;
         t1 = host_ms();
         double* v0 = dalloc<double>(n0);
@@ -1361,6 +1433,11 @@ void stokes_mg_destroy(stokes_mg_t h) {
         for (auto& ab : p.pending) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
     for (int i = 0; i < 2; ++i)
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    if (h->s_up || h->s_coarse) cudaDeviceSynchronize();   // setup work may still be in flight after an error
+    free_pending(h);
+    free_coarse_ws(h);
+    if (h->s_up) cudaStreamDestroy(h->s_up);
+    if (h->s_coarse) cudaStreamDestroy(h->s_coarse);
     for (void* p : h->allocs) cudaFree(p);
     if (h->pinned) cudaFreeHost(h->pinned);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
