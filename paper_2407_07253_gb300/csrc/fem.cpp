@@ -114,6 +114,16 @@ static void parallel_for(int n, const std::function<void(int, int, int)>& body) 
     });
 }
 
+void parallel_copy(void* dst, const void* src, size_t bytes) {
+    const size_t chunk = 1 << 20;
+    const int n = (int)((bytes + chunk - 1) / chunk);
+    const int T = std::max(1, std::min(Pool::get().size(), n));
+    Pool::get().run(T, [&](int t) {
+        const size_t lo = bytes * t / T, hi = bytes * (t + 1) / T;
+        std::memcpy((char*)dst + lo, (const char*)src + lo, hi - lo);
+    });
+}
+
 // Variable-length lists built in parallel without per-item allocations:
 // the static chunks of parallel_for are contiguous and ordered, so the
 // per-thread buffers concatenate in item order.

@@ -128,4 +128,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
 
 int num_threads();
 
+// memcpy split over the host worker pool
+void parallel_copy(void* dst, const void* src, size_t bytes);
+
 }  // namespace sfem

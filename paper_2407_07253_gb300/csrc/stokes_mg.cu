@@ -12,6 +12,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -49,13 +50,64 @@ T* dalloc(size_t n) {
     return (T*)p;
 }
 
+// Process-wide pinned staging arena for large host-to-device uploads: the
+// host copies into pinned memory in parallel, the DMA engine then runs at
+// pinned speed.  Grow-only chunks, bump-allocated while a setup holds the
+// lock, reused by the next setup.
+struct PinnedArena {
+    std::mutex mu;
+    std::vector<std::pair<char*, size_t>> chunks;
+    size_t cur = 0, used = 0;
+    void* take(size_t bytes) {
+        bytes = (bytes + 255) & ~size_t(255);
+        while (cur < chunks.size() && chunks[cur].second - used < bytes) { ++cur; used = 0; }
+        if (cur == chunks.size()) {
+            size_t sz = std::max<size_t>(bytes, size_t(64) << 20);
+            char* p = nullptr;
+            if (cudaHostAlloc((void**)&p, sz, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+            chunks.push_back({p, sz});
+            used = 0;
+        }
+        void* r = chunks[cur].first + used;
+        used += bytes;
+        return r;
+    }
+    void reset() { cur = 0; used = 0; }
+};
+PinnedArena& arena() {
+    static PinnedArena a;
+    return a;
+}
+thread_local bool t_arena_locked = false;
+
 template <typename Vec>
 typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
     using T = typename Vec::value_type;
     T* p = dalloc<T>(h.size());
-    if (!h.empty()) CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    const size_t bytes = h.size() * sizeof(T);
+    if (bytes == 0) return p;
+    void* st = (t_arena_locked && bytes >= (size_t(1) << 20)) ? arena().take(bytes) : nullptr;
+    if (st) {
+        sfem::parallel_copy(st, h.data(), bytes);
+        CK(cudaMemcpyAsync(p, st, bytes, cudaMemcpyHostToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(p, h.data(), bytes, cudaMemcpyHostToDevice, s));
+    }
     return p;
 }
+
+// Holds the staging arena for one setup; the arena is reset once the upload
+// stream has drained.
+struct ArenaLock {
+    std::unique_lock<std::mutex> lk;
+    cudaStream_t s;
+    explicit ArenaLock(cudaStream_t st) : lk(arena().mu), s(st) { t_arena_locked = true; arena().reset(); }
+    ~ArenaLock() {
+        if (s) cudaStreamSynchronize(s);
+        arena().reset();
+        t_arena_locked = false;
+    }
+};
 
 inline int grid_for(long long n, int block = 256) {
     long long g = (n + block - 1) / block;
@@ -127,6 +179,10 @@ struct stokes_mg {
     double *V = nullptr, *Z = nullptr, *Hh = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *h = nullptr, *hn = nullptr, *resid = nullptr, *partial = nullptr, *scal = nullptr;
     double* pinned = nullptr;
+    double* pinned_H = nullptr;          // [STOKES_MAX_LEVELS + 1][HESS_MAX * HESS_MAX]
+    double* Hlev = nullptr;              // device Hessenberg matrices, one per level
+    double* v0buf = nullptr;             // Arnoldi start vector
+    int arn_m[STOKES_MAX_LEVELS] = {0};
     int partial_blocks = 0;
     unsigned int* ticket = nullptr;
     // V-cycle graph I/O
@@ -472,12 +528,15 @@ double d2h_scalar(stokes_mg* h, const double* d, cudaStream_t s) {
 // the device without host round trips; the (m+1) x m Hessenberg matrix is
 // then read once, truncated at the first breakdown H[j+1][j] <= 1e-14
 // |H[j][j]|, and its eigenvalues found on the host (a 15 x 15 problem).
-double arnoldi_lmax(stokes_mg* h, int li, const double* v0, int steps, cudaStream_t s) {
+// Launch `steps` Arnoldi steps on M_l^{-1} K_l from v0 on stream s (no host
+// round trip) and queue the copy of the (m+1) x m Hessenberg matrix into
+// H_host (pinned); returns m.  Uses the FGMRES basis V as workspace, so
+// launches on one stream run one level after another.
+int arnoldi_launch(stokes_mg* h, int li, const double* v0, int steps, double* Hs, double* H_host, cudaStream_t s) {
     DevLevel& l = h->L[li];
     const int n = l.n;
     const int m = std::min(steps, std::min(n, skern::HESS_MAX - 1));
-    double* V = h->V;     // reuse the FGMRES basis (>= m+1 vectors of length >= n)
-    double* Hs = h->Hh;   // (m+1) x m
+    double* V = h->V;
     launch(h, -1, s, [&] { skern::fill_vec<double><<<1, 256, 0, s>>>((long long)(m + 1) * m, 0.0, Hs); });
     mdot(h, n, 1, v0, n, v0, h->hn, nullptr, true, s);
     launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, v0, h->hn, V); });
@@ -489,9 +548,14 @@ double arnoldi_lmax(stokes_mg* h, int li, const double* v0, int steps, cudaStrea
         launch(h, -1, s, [&] { skern::arnoldi_store<<<1, 1, 0, s>>>(j, m, Hs, h->h, h->hn); });
         launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, h->hn, w); });
     }
-    std::vector<double> H((size_t)(m + 1) * m);
-    CK(cudaMemcpyAsync(H.data(), Hs, sizeof(double) * H.size(), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpyAsync(H_host, Hs, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToHost, s));
+    return m;
+}
+
+// Largest real Ritz value from a Hessenberg matrix read back by
+// arnoldi_launch, truncated at the first breakdown H[j+1][j] <= 1e-14 |H[j][j]|
+// (a 15 x 15 eigenproblem, solved on the host).
+double arnoldi_finish(const double* H, int m) {
     int used = m;
     for (int j = 0; j < m; ++j) {
         const double sub = H[(size_t)(j + 1) * m + j], dj = H[(size_t)j * m + j];
@@ -500,8 +564,16 @@ double arnoldi_lmax(stokes_mg* h, int li, const double* v0, int steps, cudaStrea
     }
     skern::cplx A[skern::HESS_MAX][skern::HESS_MAX], cr[skern::HESS_MAX], sr[skern::HESS_MAX];
     double out[2];
-    skern::hessenberg_eig_core(used, m, H.data(), out, A, cr, sr);
+    skern::hessenberg_eig_core(used, m, H, out, A, cr, sr);
     return out[0];
+}
+
+double arnoldi_lmax(stokes_mg* h, int li, const double* v0, int steps, cudaStream_t s) {
+    double* Hs = h->Hh;
+    double* Hh = h->pinned_H;
+    const int m = arnoldi_launch(h, li, v0, steps, Hs, Hh, s);
+    CK(cudaStreamSynchronize(s));
+    return arnoldi_finish(Hh, m);
 }
 
 // SplitMix64 start vector (the same counter-based definition as the tests'
@@ -833,6 +905,34 @@ void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
     for (double v : F.pint) h->pint_sum += v;
 }
 
+// FGMRES / Arnoldi buffers sized by the finest level
+void alloc_krylov(stokes_mg* h, cudaStream_t s) {
+    const int n0 = h->L[0].n;
+    const int m = h->restart;
+    const int basis = std::max(m + 1, skern::HESS_MAX + 1);
+    h->V = track(h, dalloc<double>((size_t)basis * n0));
+    h->Z = track(h, dalloc<double>((size_t)m * n0));
+    h->Hh = track(h, dalloc<double>((size_t)(basis + 1) * basis));
+    h->cs = track(h, dalloc<double>(basis));
+    h->sn = track(h, dalloc<double>(basis));
+    h->g = track(h, dalloc<double>(basis + 1));
+    h->y = track(h, dalloc<double>(basis + 1));
+    h->h = track(h, dalloc<double>(basis + 1));
+    h->hn = track(h, dalloc<double>(2));
+    h->resid = track(h, dalloc<double>(2));
+    h->scal = track(h, dalloc<double>(4));
+    h->partial_blocks = skern::MDOT_BLOCKS;
+    h->partial = track(h, dalloc<double>((size_t)h->partial_blocks * 32));
+    h->ticket = track(h, dalloc<unsigned int>(1));
+    CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s));
+    h->vin = track(h, dalloc<double>(n0));
+    h->vout = track(h, dalloc<double>(n0));
+    h->v0buf = track(h, dalloc<double>(n0));
+    h->Hlev = track(h, dalloc<double>((size_t)STOKES_MAX_LEVELS * skern::HESS_MAX * skern::HESS_MAX));
+    CK(cudaMallocHost((void**)&h->pinned, 64));
+    CK(cudaMallocHost((void**)&h->pinned_H, sizeof(double) * (STOKES_MAX_LEVELS + 1) * skern::HESS_MAX * skern::HESS_MAX));
+}
+
 void fill_stats(stokes_mg* h) {
     stokes_mg_stats& st = h->st;
     st.n_levels = (int)h->H.levels.size();
@@ -996,6 +1096,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         require(!(family == STOKES_SV && spec.schedule.size() < 2), "Scott-Vogelius needs at least one p-coarsening");
         const bool want32 = o.precision == STOKES_MIXED;
         double t_cb_upload = 0;
+        std::unique_ptr<ArenaLock> arena_lock;
         std::function<void(int)> on_level;
         if (!o.host_only) {
             // level-by-level pipeline: upload on s_up, then the patch
@@ -1003,11 +1104,13 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             // while the host assembles the next, coarser levels
             CK(cudaStreamCreateWithFlags(&h->s_up, cudaStreamNonBlocking));
             CK(cudaStreamCreateWithFlags(&h->s_coarse, cudaStreamNonBlocking));
+            arena_lock.reset(new ArenaLock(h->s_up));
             on_level = [&](int li) {
                 const double tu = host_ms();
                 const int nlv = (int)h->H.levels.size();
                 if ((int)h->L.size() != nlv) h->L.assign(nlv, DevLevel());
                 upload_level(h.get(), li, want32, h->s_up);
+                if (li == 0) alloc_krylov(h.get(), h->s_up);
                 if (li + 1 < nlv) {
                     cudaEvent_t ev;
                     CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1015,6 +1118,15 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                     CK(cudaStreamWaitEvent(s, ev, 0));
                     CK(cudaEventDestroy(ev));
                     launch_patches(h.get(), li, s);
+                    // lambda_max estimate right behind the inversion (same stream)
+                    if (!(li < 16 && o.lmax_override[li] > 0)) {
+                        const int n = h->L[li].n;
+                        splitmix_uniform<<<grid_for(n), 256, 0, s>>>(n, o.eig_seed, (unsigned long long)li, h->v0buf);
+                        CK(cudaGetLastError());
+                        const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
+                        h->arn_m[li] = arnoldi_launch(h.get(), li, h->v0buf, o.eig_steps, h->Hlev + li * hsz,
+                                                      h->pinned_H + (li + 1) * hsz, s);
+                    }
                 } else {
                     launch_coarse(h.get(), h->s_up, h->s_coarse);
                 }
@@ -1038,30 +1150,10 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         }
         double t1 = host_ms();
         for (int li = 0; li + 1 < nl; ++li) upload_transfers(h.get(), li, want32, h->s_up);
-        // FGMRES / Arnoldi buffers
         const int n0 = h->L[0].n;
-        const int m = h->restart;
-        const int basis = std::max(m + 1, 17);
-        h->V = track(h.get(), dalloc<double>((size_t)basis * n0));
-        h->Z = track(h.get(), dalloc<double>((size_t)m * n0));
-        h->Hh = track(h.get(), dalloc<double>((size_t)(basis + 1) * basis));
-        h->cs = track(h.get(), dalloc<double>(basis));
-        h->sn = track(h.get(), dalloc<double>(basis));
-        h->g = track(h.get(), dalloc<double>(basis + 1));
-        h->y = track(h.get(), dalloc<double>(basis + 1));
-        h->h = track(h.get(), dalloc<double>(basis + 1));
-        h->hn = track(h.get(), dalloc<double>(2));
-        h->resid = track(h.get(), dalloc<double>(2));
-        h->scal = track(h.get(), dalloc<double>(4));
-        h->partial_blocks = skern::MDOT_BLOCKS;
-        h->partial = track(h.get(), dalloc<double>((size_t)h->partial_blocks * 32));
-        h->ticket = track(h.get(), dalloc<unsigned int>(1));
-        CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->s_up));
-        h->vin = track(h.get(), dalloc<double>(n0));
-        h->vout = track(h.get(), dalloc<double>(n0));
-        CK(cudaMallocHost((void**)&h->pinned, 64));
         setup_solve_buffers(h.get(), h->s_up);
         CK(cudaStreamSynchronize(h->s_up));
+        arena_lock.reset();
         h->st.t_upload_ms = t_cb_upload + host_ms() - t1;
         // what remains of the patch inversions and of the coarse
         // factorisation once the host is done
@@ -1072,22 +1164,15 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         finish_coarse(h.get(), h->s_coarse);
         h->st.t_coarse_ms = host_ms() - t1;
         t1 = host_ms();
-        double* v0 = dalloc<double>(n0);
-        try {
+        {
+            const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
             for (int li = 0; li + 1 < nl; ++li) {
                 if (li < 16 && o.lmax_override[li] > 0) { h->L[li].lmax = o.lmax_override[li]; continue; }
-                const int n = h->L[li].n;
-                splitmix_uniform<<<grid_for(n), 256, 0, s>>>(n, o.eig_seed, (unsigned long long)li, v0);
-                CK(cudaGetLastError());
-                h->L[li].lmax = arnoldi_lmax(h.get(), li, v0, o.eig_steps, s);
+                h->L[li].lmax = arnoldi_finish(h->pinned_H + (li + 1) * hsz, h->arn_m[li]);
                 if (!(h->L[li].lmax > 0) || !std::isfinite(h->L[li].lmax))
                     throw StokesError(STOKES_ENONFINITE, "lambda_max estimate is not positive on level " + std::to_string(li));
             }
-        } catch (...) {
-            cudaFree(v0);
-            throw;
         }
-        cudaFree(v0);
         h->st.t_eig_ms = host_ms() - t1;
         t1 = host_ms();
         if (o.use_graph) capture_graph(h.get(), o.precision, s);
@@ -1440,6 +1525,7 @@ void stokes_mg_destroy(stokes_mg_t h) {
     if (h->s_coarse) cudaStreamDestroy(h->s_coarse);
     for (void* p : h->allocs) cudaFree(p);
     if (h->pinned) cudaFreeHost(h->pinned);
+    if (h->pinned_H) cudaFreeHost(h->pinned_H);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     delete h;
 }
