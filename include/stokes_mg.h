@@ -119,6 +119,10 @@ typedef struct {
     /* split of t_assembly_ms (host): spaces + reference tensors, CSR
        matrices, Vanka patches, transfers */
     double t_spaces_ms, t_matrices_ms, t_patches_ms, t_transfers_ms;
+    /* busy time of the thread that issues the per-level uploads and launches
+       while the calling thread assembles (overlapped); t_upload_ms is what
+       is left on the critical path after assembly */
+    double t_launch_thread_ms;
 } stokes_mg_stats;
 
 typedef struct stokes_mg* stokes_mg_t;

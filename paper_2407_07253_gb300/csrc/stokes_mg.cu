@@ -12,7 +12,11 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <atomic>
+#include <condition_variable>
+#include <exception>
 #include <mutex>
+#include <thread>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -79,6 +83,16 @@ PinnedArena& arena() {
     return a;
 }
 thread_local bool t_arena_locked = false;
+std::mutex& arena_take_mu() {
+    static std::mutex m;
+    return m;
+}
+// set while a setup holds the arena, so its launcher thread may stage too
+std::atomic<int>& arena_owner_flag() {
+    static std::atomic<int> f{0};
+    return f;
+}
+bool arena_owner_active() { return arena_owner_flag().load() != 0; }
 
 template <typename Vec>
 typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
@@ -86,9 +100,13 @@ typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
     T* p = dalloc<T>(h.size());
     const size_t bytes = h.size() * sizeof(T);
     if (bytes == 0) return p;
-    void* st = (t_arena_locked && bytes >= (size_t(1) << 20)) ? arena().take(bytes) : nullptr;
+    void* st = nullptr;
+    if (bytes >= (size_t(1) << 20)) {
+        std::lock_guard<std::mutex> g(arena_take_mu());
+        if (t_arena_locked || arena_owner_active()) st = arena().take(bytes);
+    }
     if (st) {
-        sfem::parallel_copy(st, h.data(), bytes);
+        std::memcpy(st, h.data(), bytes);
         CK(cudaMemcpyAsync(p, st, bytes, cudaMemcpyHostToDevice, s));
     } else {
         CK(cudaMemcpyAsync(p, h.data(), bytes, cudaMemcpyHostToDevice, s));
@@ -96,15 +114,81 @@ typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
     return p;
 }
 
+// One host thread that issues the device side of setup (uploads, kernel
+// launches) in submission order, so that it overlaps with the assembly of
+// the next level on the calling thread.  The first exception is kept and
+// rethrown by finish(); later tasks are skipped.
+class Launcher {
+  public:
+    Launcher() : th_([this] { loop(); }) {}
+    ~Launcher() {
+        if (th_.joinable()) {
+            {
+                std::lock_guard<std::mutex> g(mu_);
+                stop_ = true;
+            }
+            cv_.notify_all();
+            th_.join();
+        }
+    }
+    void submit(std::function<void()> f) {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            q_.push_back(std::move(f));
+        }
+        cv_.notify_all();
+    }
+    void finish() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        th_.join();
+        if (err_) std::rethrow_exception(err_);
+    }
+
+  private:
+    void loop() {
+        for (;;) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || !q_.empty(); });
+                if (q_.empty()) return;
+                f = std::move(q_.front());
+                q_.erase(q_.begin());
+            }
+            if (err_) continue;
+            try {
+                f();
+            } catch (...) {
+                err_ = std::current_exception();
+            }
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::vector<std::function<void()>> q_;
+    bool stop_ = false;
+    std::exception_ptr err_;
+    std::thread th_;
+};
+
 // Holds the staging arena for one setup; the arena is reset once the upload
 // stream has drained.
 struct ArenaLock {
     std::unique_lock<std::mutex> lk;
     cudaStream_t s;
-    explicit ArenaLock(cudaStream_t st) : lk(arena().mu), s(st) { t_arena_locked = true; arena().reset(); }
+    explicit ArenaLock(cudaStream_t st) : lk(arena().mu), s(st) {
+        t_arena_locked = true;
+        arena().reset();
+        arena_owner_flag().store(1);
+    }
     ~ArenaLock() {
         if (s) cudaStreamSynchronize(s);
         arena().reset();
+        arena_owner_flag().store(0);
         t_arena_locked = false;
     }
 };
@@ -1097,6 +1181,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         const bool want32 = o.precision == STOKES_MIXED;
         double t_cb_upload = 0;
         std::unique_ptr<ArenaLock> arena_lock;
+        std::unique_ptr<Launcher> launcher;
         std::function<void(int)> on_level;
         if (!o.host_only) {
             // level-by-level pipeline: upload on s_up, then the patch
@@ -1105,32 +1190,37 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             CK(cudaStreamCreateWithFlags(&h->s_up, cudaStreamNonBlocking));
             CK(cudaStreamCreateWithFlags(&h->s_coarse, cudaStreamNonBlocking));
             arena_lock.reset(new ArenaLock(h->s_up));
+            launcher.reset(new Launcher());
             on_level = [&](int li) {
-                const double tu = host_ms();
-                const int nlv = (int)h->H.levels.size();
-                if ((int)h->L.size() != nlv) h->L.assign(nlv, DevLevel());
-                upload_level(h.get(), li, want32, h->s_up);
-                if (li == 0) alloc_krylov(h.get(), h->s_up);
-                if (li + 1 < nlv) {
-                    cudaEvent_t ev;
-                    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-                    CK(cudaEventRecord(ev, h->s_up));
-                    CK(cudaStreamWaitEvent(s, ev, 0));
-                    CK(cudaEventDestroy(ev));
-                    launch_patches(h.get(), li, s);
-                    // lambda_max estimate right behind the inversion (same stream)
-                    if (!(li < 16 && o.lmax_override[li] > 0)) {
-                        const int n = h->L[li].n;
-                        splitmix_uniform<<<grid_for(n), 256, 0, s>>>(n, o.eig_seed, (unsigned long long)li, h->v0buf);
-                        CK(cudaGetLastError());
-                        const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
-                        h->arn_m[li] = arnoldi_launch(h.get(), li, h->v0buf, o.eig_steps, h->Hlev + li * hsz,
-                                                      h->pinned_H + (li + 1) * hsz, s);
+                stokes_mg* hp = h.get();
+                const int nlv = (int)hp->H.levels.size();
+                if ((int)hp->L.size() != nlv) hp->L.assign(nlv, DevLevel());
+                launcher->submit([hp, li, nlv, want32, s, &o, &t_cb_upload] {
+                    const double tu = host_ms();
+                    CK(cudaSetDevice(hp->device));
+                    upload_level(hp, li, want32, hp->s_up);
+                    if (li == 0) alloc_krylov(hp, hp->s_up);
+                    if (li + 1 < nlv) {
+                        cudaEvent_t ev;
+                        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                        CK(cudaEventRecord(ev, hp->s_up));
+                        CK(cudaStreamWaitEvent(s, ev, 0));
+                        CK(cudaEventDestroy(ev));
+                        launch_patches(hp, li, s);
+                        // lambda_max estimate right behind the inversion (same stream)
+                        if (!(li < 16 && o.lmax_override[li] > 0)) {
+                            const int n = hp->L[li].n;
+                            splitmix_uniform<<<grid_for(n), 256, 0, s>>>(n, o.eig_seed, (unsigned long long)li, hp->v0buf);
+                            CK(cudaGetLastError());
+                            const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
+                            hp->arn_m[li] = arnoldi_launch(hp, li, hp->v0buf, o.eig_steps, hp->Hlev + li * hsz,
+                                                           hp->pinned_H + (li + 1) * hsz, s);
+                        }
+                    } else {
+                        launch_coarse(hp, hp->s_up, hp->s_coarse);
                     }
-                } else {
-                    launch_coarse(h.get(), h->s_up, h->s_coarse);
-                }
-                t_cb_upload += host_ms() - tu;
+                    t_cb_upload += host_ms() - tu;
+                });
             };
         }
         sfem::build_hierarchy(cm, spec, nu_cell, h->H, on_level);
@@ -1149,12 +1239,16 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             return STOKES_OK;
         }
         double t1 = host_ms();
+        launcher->finish();   // all per-level uploads and launches issued
+        const double t_wait_launch = host_ms() - t1;
+        t1 = host_ms();
         for (int li = 0; li + 1 < nl; ++li) upload_transfers(h.get(), li, want32, h->s_up);
         const int n0 = h->L[0].n;
         setup_solve_buffers(h.get(), h->s_up);
         CK(cudaStreamSynchronize(h->s_up));
         arena_lock.reset();
-        h->st.t_upload_ms = t_cb_upload + host_ms() - t1;
+        h->st.t_upload_ms = host_ms() - t1 + t_wait_launch;
+        h->st.t_launch_thread_ms = t_cb_upload;
         // what remains of the patch inversions and of the coarse
         // factorisation once the host is done
         t1 = host_ms();
