@@ -119,10 +119,10 @@ typedef struct {
     /* split of t_assembly_ms (host): spaces + reference tensors, CSR
        matrices, Vanka patches, transfers */
     double t_spaces_ms, t_matrices_ms, t_patches_ms, t_transfers_ms;
-    /* busy time of the thread that issues the per-level uploads and launches
-       while the calling thread assembles (overlapped); t_upload_ms is what
-       is left on the critical path after assembly */
-    double t_launch_thread_ms;
+    /* busy time of the thread that issues the per-level kernel launches
+       while the calling thread assembles (overlapped), and the time the
+       calling thread then waited for it */
+    double t_launch_thread_ms, t_launch_wait_ms;
 } stokes_mg_stats;
 
 typedef struct stokes_mg* stokes_mg_t;

@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
                 ("t_gather_lu_ms", c_double), ("t_coarse_ms", c_double), ("t_eig_ms", c_double),
                 ("t_graph_ms", c_double), ("t_total_ms", c_double), ("kernel_launches", c_longlong),
                 ("t_spaces_ms", c_double), ("t_matrices_ms", c_double), ("t_patches_ms", c_double),
-                ("t_transfers_ms", c_double), ("t_launch_thread_ms", c_double)]
+                ("t_transfers_ms", c_double), ("t_launch_thread_ms", c_double),
+                ("t_launch_wait_ms", c_double)]
 
 
 class StokesError(RuntimeError):

@@ -106,7 +106,8 @@ typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
         if (t_arena_locked || arena_owner_active()) st = arena().take(bytes);
     }
     if (st) {
-        std::memcpy(st, h.data(), bytes);
+        if (t_arena_locked) sfem::parallel_copy(st, h.data(), bytes);
+        else std::memcpy(st, h.data(), bytes);
         CK(cudaMemcpyAsync(p, st, bytes, cudaMemcpyHostToDevice, s));
     } else {
         CK(cudaMemcpyAsync(p, h.data(), bytes, cudaMemcpyHostToDevice, s));
@@ -911,7 +912,7 @@ void finish_patches(stokes_mg* h, cudaStream_t s) {
 
 // Bordered coarse matrix (zero-mean pressure constraint, Sec. 2) inverted in
 // place by one Gauss-Jordan step per pivot on stream s (no wait).
-void launch_coarse(stokes_mg* h, cudaStream_t su, cudaStream_t s) {
+void upload_coarse(stokes_mg* h, cudaStream_t su) {
     const sfem::Level& C = h->H.levels.back();
     const int n = C.n_free, nb = n + 1;
     h->nc = n;
@@ -925,15 +926,17 @@ void launch_coarse(stokes_mg* h, cudaStream_t su, cudaStream_t s) {
         A[(size_t)n * nb + r] = C.pint[q];
     }
     h->Cinv = track(h, dupload(A, su));
-    cudaEvent_t ev;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    CK(cudaEventRecord(ev, su));
-    CK(cudaStreamWaitEvent(s, ev, 0));
-    CK(cudaEventDestroy(ev));
     h->c_ipiv = dalloc<int>(nb);
     h->c_colk = dalloc<double>(nb);
     h->c_status = dalloc<int>(1);
-    CK(cudaMemsetAsync(h->c_status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(h->c_status, 0, sizeof(int), su));
+    h->cb64 = track(h, dalloc<double>(n));
+    h->ce64 = track(h, dalloc<double>(n));
+}
+
+// coarse factorisation steps on stream s (the upload must be ordered before)
+void launch_coarse(stokes_mg* h, cudaStream_t s) {
+    const int nb = h->nc + 1;
     const long long tot = (long long)nb * nb;
     const int egrid = (int)std::min<long long>((tot + 255) / 256, 152LL * 8);
     for (int k = 0; k < nb; ++k) {
@@ -941,8 +944,6 @@ void launch_coarse(stokes_mg* h, cudaStream_t su, cudaStream_t s) {
         launch(h, -1, s, [&] { skern::gj_step_eliminate<<<egrid, 256, 0, s>>>(nb, k, h->Cinv, h->c_colk); });
     }
     launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
-    h->cb64 = track(h, dalloc<double>(n));
-    h->ce64 = track(h, dalloc<double>(n));
 }
 
 void free_coarse_ws(stokes_mg* h) {
@@ -1182,6 +1183,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         double t_cb_upload = 0;
         std::unique_ptr<ArenaLock> arena_lock;
         std::unique_ptr<Launcher> launcher;
+        double t_launch = 0;
         std::function<void(int)> on_level;
         if (!o.host_only) {
             // level-by-level pipeline: upload on s_up, then the patch
@@ -1192,20 +1194,30 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             arena_lock.reset(new ArenaLock(h->s_up));
             launcher.reset(new Launcher());
             on_level = [&](int li) {
+                const double tu = host_ms();
                 stokes_mg* hp = h.get();
                 const int nlv = (int)hp->H.levels.size();
                 if ((int)hp->L.size() != nlv) hp->L.assign(nlv, DevLevel());
-                launcher->submit([hp, li, nlv, want32, s, &o, &t_cb_upload] {
-                    const double tu = host_ms();
-                    CK(cudaSetDevice(hp->device));
+                // uploads on this thread (parallel copy into pinned staging)
+                cudaStream_t target = li + 1 < nlv ? s : hp->s_coarse;
+                if (li + 1 < nlv) {
                     upload_level(hp, li, want32, hp->s_up);
                     if (li == 0) alloc_krylov(hp, hp->s_up);
+                } else {
+                    upload_level(hp, li, want32, hp->s_up);
+                    upload_coarse(hp, hp->s_up);
+                }
+                cudaEvent_t ev;
+                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                CK(cudaEventRecord(ev, hp->s_up));
+                CK(cudaStreamWaitEvent(target, ev, 0));
+                CK(cudaEventDestroy(ev));
+                t_cb_upload += host_ms() - tu;
+                // kernel launches on the launcher thread
+                launcher->submit([hp, li, nlv, s, &o, &t_launch] {
+                    const double tl = host_ms();
+                    CK(cudaSetDevice(hp->device));
                     if (li + 1 < nlv) {
-                        cudaEvent_t ev;
-                        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-                        CK(cudaEventRecord(ev, hp->s_up));
-                        CK(cudaStreamWaitEvent(s, ev, 0));
-                        CK(cudaEventDestroy(ev));
                         launch_patches(hp, li, s);
                         // lambda_max estimate right behind the inversion (same stream)
                         if (!(li < 16 && o.lmax_override[li] > 0)) {
@@ -1217,9 +1229,9 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                                                            hp->pinned_H + (li + 1) * hsz, s);
                         }
                     } else {
-                        launch_coarse(hp, hp->s_up, hp->s_coarse);
+                        launch_coarse(hp, hp->s_coarse);
                     }
-                    t_cb_upload += host_ms() - tu;
+                    t_launch += host_ms() - tl;
                 });
             };
         }
@@ -1247,8 +1259,9 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         setup_solve_buffers(h.get(), h->s_up);
         CK(cudaStreamSynchronize(h->s_up));
         arena_lock.reset();
-        h->st.t_upload_ms = host_ms() - t1 + t_wait_launch;
-        h->st.t_launch_thread_ms = t_cb_upload;
+        h->st.t_upload_ms = t_cb_upload + host_ms() - t1;
+        h->st.t_launch_wait_ms = t_wait_launch;
+        h->st.t_launch_thread_ms = t_launch;
         // what remains of the patch inversions and of the coarse
         // factorisation once the host is done
         t1 = host_ms();
