@@ -308,7 +308,7 @@ def main():
                    "inputs": "mesh on host, f resident in HBM"},
         "iterations": its_l[-1],
         "setup_ms": {k: round(stats[k], 3) for k in ("t_mesh_ms", "t_assembly_ms", "t_spaces_ms", "t_matrices_ms",
-                                                     "t_patches_ms", "t_transfers_ms", "t_upload_ms", "t_launch_thread_ms", "t_launch_wait_ms", "t_gather_lu_ms",
+                                                     "t_patches_ms", "t_transfers_ms", "t_upload_ms", "t_launch_thread_ms", "t_launch_wait_ms", "t_upload_post_ms", "t_gather_lu_ms",
                                                      "t_coarse_ms", "t_eig_ms", "t_graph_ms", "t_total_ms")},
         "e2e": {"value": sum(e2e_times) / len(e2e_times), "unit": "ms",
                 "h2d_bytes_per_step": int(f_host.numel() * 8),

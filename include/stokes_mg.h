@@ -123,6 +123,9 @@ typedef struct {
        while the calling thread assembles (overlapped), and the time the
        calling thread then waited for it */
     double t_launch_thread_ms, t_launch_wait_ms;
+    /* uploads issued between levels (t_upload_ms) and after assembly
+       (transfers, load operators, t_upload_post_ms) */
+    double t_upload_post_ms;
 } stokes_mg_stats;
 
 typedef struct stokes_mg* stokes_mg_t;

@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
                 ("t_graph_ms", c_double), ("t_total_ms", c_double), ("kernel_launches", c_longlong),
                 ("t_spaces_ms", c_double), ("t_matrices_ms", c_double), ("t_patches_ms", c_double),
                 ("t_transfers_ms", c_double), ("t_launch_thread_ms", c_double),
-                ("t_launch_wait_ms", c_double)]
+                ("t_launch_wait_ms", c_double), ("t_upload_post_ms", c_double)]
 
 
 class StokesError(RuntimeError):
