@@ -221,6 +221,10 @@ struct stokes_mg {
     Prof prof[5];
     bool capturing = false;
     bool host_only = false;
+    // bump allocator for the handle's long-lived device buffers: a few large
+    // cudaMalloc chunks instead of one call per array
+    char* slab_cur = nullptr;
+    size_t slab_left = 0;
     // setup in flight
     std::vector<PendingPatches> pending;
     int* c_ipiv = nullptr;
@@ -260,6 +264,33 @@ T* track(stokes_mg* h, T* p) {
     return p;
 }
 
+constexpr size_t kSlabChunk = size_t(256) << 20;
+
+// Device buffer owned by the handle (freed by stokes_mg_destroy), 256-byte
+// aligned, carved from 256 MB chunks; large requests get their own chunk.
+template <typename T>
+T* halloc(stokes_mg* h, size_t n) {
+    size_t bytes = ((std::max<size_t>(n, 1) * sizeof(T)) + 255) & ~size_t(255);
+    if (bytes > kSlabChunk / 4) return track(h, dalloc<T>(n));
+    if (h->slab_left < bytes) {
+        h->slab_cur = (char*)track(h, dalloc<char>(kSlabChunk));
+        h->slab_left = kSlabChunk;
+    }
+    T* p = (T*)h->slab_cur;
+    h->slab_cur += bytes;
+    h->slab_left -= bytes;
+    return p;
+}
+
+template <typename Vec>
+typename Vec::value_type* hupload(stokes_mg* h, const Vec& v, cudaStream_t s) {
+    using T = typename Vec::value_type;
+    T* p = halloc<T>(h, v.size());
+    const size_t bytes = v.size() * sizeof(T);
+    if (bytes) CK(cudaMemcpyAsync(p, v.data(), bytes, cudaMemcpyHostToDevice, s));
+    return p;
+}
+
 int choose_lanes(const DevCSR& A) {
     double avg = A.nr ? (double)A.nnz / A.nr : 1;
     if (avg <= 6) return 4;
@@ -273,11 +304,11 @@ DevCSR upload_csr(stokes_mg* h, const sfem::CSR& A, bool want32, cudaStream_t s)
     d.nr = A.nr;
     d.nc = A.ncol;
     d.nnz = A.nnz();
-    d.rp = track(h, dupload(A.rp, s));
-    d.ci = track(h, dupload(A.ci, s));
-    d.v64 = track(h, dupload(A.v, s));
+    d.rp = hupload(h, A.rp, s);
+    d.ci = hupload(h, A.ci, s);
+    d.v64 = hupload(h, A.v, s);
     if (want32) {
-        d.v32 = track(h, dalloc<float>(d.nnz));
+        d.v32 = halloc<float>(h, d.nnz);
         skern::convert_vec<float, double><<<grid_for(d.nnz), 256, 0, s>>>((int)d.nnz, d.v64, d.v32);
         CK(cudaGetLastError());
     }
@@ -698,9 +729,9 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         l.nsq = moff[l.npatch];
         l.ninv64 = o64[l.npatch];
         l.ninv32 = o32[l.npatch];
-        l.poff = track(h, dupload(HL.patch_off, s));
-        l.pdofs = track(h, dupload(HL.patch_dofs, s));
-        l.pnv = track(h, dupload(HL.patch_nv, s));
+        l.poff = hupload(h, HL.patch_off, s);
+        l.pdofs = hupload(h, HL.patch_dofs, s);
+        l.pnv = hupload(h, HL.patch_nv, s);
         std::vector<long long> scoff(l.npatch + 1, 0);
         for (int p = 0; p < l.npatch; ++p) {
             const long long sc = skern::saddle_scratch(HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p]);
@@ -708,10 +739,10 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
             else scoff[p + 1] = scoff[p] + sc;
         }
         l.saddle_global = scoff[l.npatch];
-        l.scoff = track(h, dupload(scoff, s));
-        l.moff = track(h, dupload(moff, s));
-        l.ioff64 = track(h, dupload(o64, s));
-        l.ioff32 = track(h, dupload(o32, s));
+        l.scoff = hupload(h, scoff, s);
+        l.moff = hupload(h, moff, s);
+        l.ioff64 = hupload(h, o64, s);
+        l.ioff32 = hupload(h, o32, s);
         // partition of unity W_i = diag(1/m_j) and the DoF -> slot map
         std::vector<int> mult(l.n, 0);
         for (int x : HL.patch_dofs) mult[x]++;
@@ -721,24 +752,24 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         for (int j = 0; j < l.n; ++j) soff[j + 1] = soff[j] + mult[j];
         std::vector<int> fill(soff.begin(), soff.end() - 1);
         for (long long q = 0; q < l.nent; ++q) sidx[fill[HL.patch_dofs[q]]++] = (int)q;
-        l.wt64 = track(h, dupload(wt, s));
-        l.soff = track(h, dupload(soff, s));
-        l.sidx = track(h, dupload(sidx, s));
-        l.Y64 = track(h, dalloc<double>(l.nent));
-        l.inv64 = track(h, dalloc<double>(l.ninv64));
+        l.wt64 = hupload(h, wt, s);
+        l.soff = hupload(h, soff, s);
+        l.sidx = hupload(h, sidx, s);
+        l.Y64 = halloc<double>(h, l.nent);
+        l.inv64 = halloc<double>(h, l.ninv64);
         if (want32) {
-            l.wt32 = track(h, dalloc<float>(l.n));
+            l.wt32 = halloc<float>(h, l.n);
             skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.wt64, l.wt32);
             CK(cudaGetLastError());
-            l.Y32 = track(h, dalloc<float>(l.nent));
-            l.inv32 = track(h, dalloc<float>(l.ninv32));
+            l.Y32 = halloc<float>(h, l.nent);
+            l.inv32 = halloc<float>(h, l.ninv32);
         }
     }
-    l.b64 = track(h, dalloc<double>(l.n)); l.e64 = track(h, dalloc<double>(l.n)); l.r64 = track(h, dalloc<double>(l.n));
-    l.d64 = track(h, dalloc<double>(l.n)); l.t64 = track(h, dalloc<double>(l.n)); l.u64 = track(h, dalloc<double>(l.n));
+    l.b64 = halloc<double>(h, l.n); l.e64 = halloc<double>(h, l.n); l.r64 = halloc<double>(h, l.n);
+    l.d64 = halloc<double>(h, l.n); l.t64 = halloc<double>(h, l.n); l.u64 = halloc<double>(h, l.n);
     if (want32) {
-        l.b32 = track(h, dalloc<float>(l.n)); l.e32 = track(h, dalloc<float>(l.n)); l.r32 = track(h, dalloc<float>(l.n));
-        l.d32 = track(h, dalloc<float>(l.n)); l.t32 = track(h, dalloc<float>(l.n)); l.u32 = track(h, dalloc<float>(l.n));
+        l.b32 = halloc<float>(h, l.n); l.e32 = halloc<float>(h, l.n); l.r32 = halloc<float>(h, l.n);
+        l.d32 = halloc<float>(h, l.n); l.t32 = halloc<float>(h, l.n); l.u32 = halloc<float>(h, l.n);
     }
 }
 
@@ -861,13 +892,13 @@ void upload_coarse(stokes_mg* h, cudaStream_t su) {
         A[(size_t)r * nb + n] = C.pint[q];
         A[(size_t)n * nb + r] = C.pint[q];
     }
-    h->Cinv = track(h, dupload(A, su));
+    h->Cinv = hupload(h, A, su);
     h->c_ipiv = dalloc<int>(nb);
     h->c_colk = dalloc<double>(nb);
     h->c_status = dalloc<int>(1);
     CK(cudaMemsetAsync(h->c_status, 0, sizeof(int), su));
-    h->cb64 = track(h, dalloc<double>(n));
-    h->ce64 = track(h, dalloc<double>(n));
+    h->cb64 = halloc<double>(h, n);
+    h->ce64 = halloc<double>(h, n);
 }
 
 // coarse factorisation steps on stream s (the upload must be ordered before)
@@ -913,15 +944,15 @@ void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
         if (F.vfree[i] >= 0) vrow[F.vfree[i]] = i;
     for (int c = 0; c < d; ++c)
         for (int f = 0; f < F.nVf; ++f) rows[c * F.nVf + f] = c * F.V.n + vrow[f];
-    h->vel_rows = track(h, dupload(rows, s));
-    h->F = track(h, dalloc<double>((size_t)d * F.V.n));
-    h->gzero = track(h, dalloc<double>((size_t)d * F.V.n));
+    h->vel_rows = hupload(h, rows, s);
+    h->F = halloc<double>(h, (size_t)d * F.V.n);
+    h->gzero = halloc<double>(h, (size_t)d * F.V.n);
     CK(cudaMemsetAsync(h->gzero, 0, sizeof(double) * d * F.V.n, s));
-    h->bvec = track(h, dalloc<double>(F.n_free));
-    h->xvec = track(h, dalloc<double>(F.n_free));
+    h->bvec = halloc<double>(h, F.n_free);
+    h->xvec = halloc<double>(h, F.n_free);
     std::vector<double> ones(F.nQ, 1.0);
-    h->ones = track(h, dupload(ones, s));
-    h->pint = track(h, dupload(F.pint, s));
+    h->ones = hupload(h, ones, s);
+    h->pint = hupload(h, F.pint, s);
     h->pint_sum = 0;
     for (double v : F.pint) h->pint_sum += v;
 }
@@ -931,25 +962,25 @@ void alloc_krylov(stokes_mg* h, cudaStream_t s) {
     const int n0 = h->L[0].n;
     const int m = h->restart;
     const int basis = std::max(m + 1, skern::HESS_MAX + 1);
-    h->V = track(h, dalloc<double>((size_t)basis * n0));
-    h->Z = track(h, dalloc<double>((size_t)m * n0));
-    h->Hh = track(h, dalloc<double>((size_t)(basis + 1) * basis));
-    h->cs = track(h, dalloc<double>(basis));
-    h->sn = track(h, dalloc<double>(basis));
-    h->g = track(h, dalloc<double>(basis + 1));
-    h->y = track(h, dalloc<double>(basis + 1));
-    h->h = track(h, dalloc<double>(basis + 1));
-    h->hn = track(h, dalloc<double>(2));
-    h->resid = track(h, dalloc<double>(2));
-    h->scal = track(h, dalloc<double>(4));
+    h->V = halloc<double>(h, (size_t)basis * n0);
+    h->Z = halloc<double>(h, (size_t)m * n0);
+    h->Hh = halloc<double>(h, (size_t)(basis + 1) * basis);
+    h->cs = halloc<double>(h, basis);
+    h->sn = halloc<double>(h, basis);
+    h->g = halloc<double>(h, basis + 1);
+    h->y = halloc<double>(h, basis + 1);
+    h->h = halloc<double>(h, basis + 1);
+    h->hn = halloc<double>(h, 2);
+    h->resid = halloc<double>(h, 2);
+    h->scal = halloc<double>(h, 4);
     h->partial_blocks = skern::MDOT_BLOCKS;
-    h->partial = track(h, dalloc<double>((size_t)h->partial_blocks * 32));
-    h->ticket = track(h, dalloc<unsigned int>(1));
+    h->partial = halloc<double>(h, (size_t)h->partial_blocks * 32);
+    h->ticket = halloc<unsigned int>(h, 1);
     CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), s));
-    h->vin = track(h, dalloc<double>(n0));
-    h->vout = track(h, dalloc<double>(n0));
-    h->v0buf = track(h, dalloc<double>(n0));
-    h->Hlev = track(h, dalloc<double>((size_t)STOKES_MAX_LEVELS * skern::HESS_MAX * skern::HESS_MAX));
+    h->vin = halloc<double>(h, n0);
+    h->vout = halloc<double>(h, n0);
+    h->v0buf = halloc<double>(h, n0);
+    h->Hlev = halloc<double>(h, (size_t)STOKES_MAX_LEVELS * skern::HESS_MAX * skern::HESS_MAX);
     CK(cudaMallocHost((void**)&h->pinned, 64));
     CK(cudaMallocHost((void**)&h->pinned_H, sizeof(double) * (STOKES_MAX_LEVELS + 1) * skern::HESS_MAX * skern::HESS_MAX));
 }
