@@ -441,79 +441,97 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
     if (threadIdx.x == 0) status[p] = st;
 }
 
-// One ASM sweep.  Each thread owns VEC consecutive rows of the column-major
-// padded inverse and streams its columns; the gathered residual sits in
+// One ASM sweep.  The patch inverse is column-major with its leading
+// dimension padded to VEC rows; a thread owns VEC consecutive rows (one
+// 16-byte vector per column) and the columns are split among G groups of
+// row-owners (G = blockDim / row groups), each thread keeping 8 independent
+// 16-byte loads in flight.  The groups' partial sums are added in shared
+// memory in a fixed order.  The gathered residual of the patch sits in
 // shared memory.
-__global__ void __launch_bounds__(256) patch_apply_f32(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
-                                                          const long long* __restrict__ ioff, const float* __restrict__ inv,
-                                                          const float* __restrict__ r, const float* __restrict__ wt,
-                                                          float* __restrict__ Y) {
-    extern __shared__ float xs32[];
-    const int p = blockIdx.x;
+template <typename T, typename V, int VEC>
+__device__ __forceinline__ void patch_apply_body(int p, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                 const long long* __restrict__ ioff, const T* __restrict__ inv,
+                                                 const T* __restrict__ r, const T* __restrict__ wt, T* __restrict__ Y,
+                                                 T* xs, V* red) {
     const int s = poff[p], n = poff[p + 1] - s;
-    const int ld4 = (n + 3) >> 2;
-    for (int a = threadIdx.x; a < n; a += blockDim.x) xs32[a] = r[pdofs[s + a]];
+    const int ldv = (n + VEC - 1) / VEC;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) xs[a] = r[pdofs[s + a]];
     __syncthreads();
-    for (int t = threadIdx.x; t < ld4; t += blockDim.x) {
-        const float4* col = reinterpret_cast<const float4*>(inv + ioff[p]) + t;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        int j = 0;
-        for (; j + 4 <= n; j += 4) {
-            const float4 v0 = __ldcs(col + (long long)(j + 0) * ld4);
-            const float4 v1 = __ldcs(col + (long long)(j + 1) * ld4);
-            const float4 v2 = __ldcs(col + (long long)(j + 2) * ld4);
-            const float4 v3 = __ldcs(col + (long long)(j + 3) * ld4);
-            const float x0 = xs32[j], x1 = xs32[j + 1], x2 = xs32[j + 2], x3 = xs32[j + 3];
-            acc.x += v0.x * x0; acc.y += v0.y * x0; acc.z += v0.z * x0; acc.w += v0.w * x0;
-            acc.x += v1.x * x1; acc.y += v1.y * x1; acc.z += v1.z * x1; acc.w += v1.w * x1;
-            acc.x += v2.x * x2; acc.y += v2.y * x2; acc.z += v2.z * x2; acc.w += v2.w * x2;
-            acc.x += v3.x * x3; acc.y += v3.y * x3; acc.z += v3.z * x3; acc.w += v3.w * x3;
-        }
-        for (; j < n; ++j) {
-            const float4 v = __ldcs(col + (long long)j * ld4);
-            const float x = xs32[j];
-            acc.x += v.x * x; acc.y += v.y * x; acc.z += v.z * x; acc.w += v.w * x;
-        }
-        const int a0 = 4 * t;
-        const float o[4] = {acc.x, acc.y, acc.z, acc.w};
+    const int G = ldv >= (int)blockDim.x ? 1 : (int)blockDim.x / ldv;
+    const V* base = reinterpret_cast<const V*>(inv + ioff[p]);
+    for (int t0 = 0; t0 < ldv; t0 += blockDim.x) {          // more row groups than threads: loop
+        const int t = threadIdx.x;
+        const int rg = t0 + (G == 1 ? t : t % ldv), g = G == 1 ? 0 : t / ldv;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        if (g < G && rg < ldv) {
+            const V* col = base + rg;
+            int j = g;
+            for (; j + 7 * G < n; j += 8 * G) {
+                V v[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (a0 + q < n) Y[s + a0 + q] = wt[pdofs[s + a0 + q]] * o[q];
+                for (int u = 0; u < 8; ++u) v[u] = __ldcs(col + (long long)(j + u * G) * ldv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const T x = xs[j + u * G];
+                    if constexpr (VEC == 4) { a0 += v[u].x * x; a1 += v[u].y * x; a2 += v[u].z * x; a3 += v[u].w * x; }
+                    else { a0 += v[u].x * x; a1 += v[u].y * x; }
+                }
+            }
+            for (; j < n; j += G) {
+                const V v = __ldcs(col + (long long)j * ldv);
+                const T x = xs[j];
+                if constexpr (VEC == 4) { a0 += v.x * x; a1 += v.y * x; a2 += v.z * x; a3 += v.w * x; }
+                else { a0 += v.x * x; a1 += v.y * x; }
+            }
+        }
+        if (G > 1) {
+            if (g < G && rg < ldv) {
+                V o;
+                if constexpr (VEC == 4) o = V{a0, a1, a2, a3};
+                else o = V{a0, a1};
+                red[g * ldv + (rg - t0)] = o;
+            }
+            __syncthreads();
+            if (t < ldv) {
+                V o = red[t];
+                for (int gg = 1; gg < G; ++gg) {
+                    const V q = red[gg * ldv + t];
+                    if constexpr (VEC == 4) { o.x += q.x; o.y += q.y; o.z += q.z; o.w += q.w; }
+                    else { o.x += q.x; o.y += q.y; }
+                }
+                if constexpr (VEC == 4) { a0 = o.x; a1 = o.y; a2 = o.z; a3 = o.w; }
+                else { a0 = o.x; a1 = o.y; }
+            }
+        }
+        if (g == 0 && rg < ldv) {
+            const int row0 = VEC * rg;
+            const T out[4] = {a0, a1, a2, a3};
+#pragma unroll
+            for (int q = 0; q < VEC; ++q)
+                if (row0 + q < n) Y[s + row0 + q] = wt[pdofs[s + row0 + q]] * out[q];
+        }
+        if (G > 1) __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(256) patch_apply_f64(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
-                                                           const long long* __restrict__ ioff, const double* __restrict__ inv,
-                                                           const double* __restrict__ r, const double* __restrict__ wt,
-                                                           double* __restrict__ Y) {
-    extern __shared__ double xs64[];
-    const int p = blockIdx.x;
-    const int s = poff[p], n = poff[p + 1] - s;
-    const int ld2 = (n + 1) >> 1;
-    for (int a = threadIdx.x; a < n; a += blockDim.x) xs64[a] = r[pdofs[s + a]];
-    __syncthreads();
-    for (int t = threadIdx.x; t < ld2; t += blockDim.x) {
-        const double2* col = reinterpret_cast<const double2*>(inv + ioff[p]) + t;
-        double2 acc = make_double2(0.0, 0.0);
-        int j = 0;
-        for (; j + 4 <= n; j += 4) {
-            const double2 v0 = __ldcs(col + (long long)(j + 0) * ld2);
-            const double2 v1 = __ldcs(col + (long long)(j + 1) * ld2);
-            const double2 v2 = __ldcs(col + (long long)(j + 2) * ld2);
-            const double2 v3 = __ldcs(col + (long long)(j + 3) * ld2);
-            acc.x += v0.x * xs64[j]; acc.y += v0.y * xs64[j];
-            acc.x += v1.x * xs64[j + 1]; acc.y += v1.y * xs64[j + 1];
-            acc.x += v2.x * xs64[j + 2]; acc.y += v2.y * xs64[j + 2];
-            acc.x += v3.x * xs64[j + 3]; acc.y += v3.y * xs64[j + 3];
-        }
-        for (; j < n; ++j) {
-            const double2 v = __ldcs(col + (long long)j * ld2);
-            acc.x += v.x * xs64[j]; acc.y += v.y * xs64[j];
-        }
-        const int a0 = 2 * t;
-        if (a0 < n) Y[s + a0] = wt[pdofs[s + a0]] * acc.x;
-        if (a0 + 1 < n) Y[s + a0 + 1] = wt[pdofs[s + a0 + 1]] * acc.y;
-    }
+__global__ void __launch_bounds__(128) patch_apply_f32(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                       const long long* __restrict__ ioff, const float* __restrict__ inv,
+                                                       const float* __restrict__ r, const float* __restrict__ wt,
+                                                       float* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char smem_pa[];
+    float4* red = reinterpret_cast<float4*>(smem_pa);
+    float* xs = reinterpret_cast<float*>(smem_pa + sizeof(float4) * (blockDim.x + 4));
+    patch_apply_body<float, float4, 4>(blockIdx.x, poff, pdofs, ioff, inv, r, wt, Y, xs, red);
+}
+
+__global__ void __launch_bounds__(128) patch_apply_f64(int npatch, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                       const long long* __restrict__ ioff, const double* __restrict__ inv,
+                                                       const double* __restrict__ r, const double* __restrict__ wt,
+                                                       double* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char smem_pa[];
+    double2* red = reinterpret_cast<double2*>(smem_pa);
+    double* xs = reinterpret_cast<double*>(smem_pa + sizeof(double2) * (blockDim.x + 4));
+    patch_apply_body<double, double2, 2>(blockIdx.x, poff, pdofs, ioff, inv, r, wt, Y, xs, red);
 }
 
 // ---------------------------------------------------------- coarse GJ ---

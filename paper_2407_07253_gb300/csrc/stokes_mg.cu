@@ -371,11 +371,9 @@ void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, doub
 
 template <>
 void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
-    const int ld4max = (l.maxn + 3) / 4;
-    const int block = std::min(256, std::max(32, (ld4max + 31) / 32 * 32));
+    const size_t smem = sizeof(float4) * (128 + 4) + sizeof(float) * l.maxn;
     launch(h, PK_PATCH, s, [&] {
-        skern::patch_apply_f32<<<l.npatch, block, l.maxn * sizeof(float), s>>>(l.npatch, l.poff, l.pdofs, l.ioff32, l.inv32,
-                                                                              r, l.wt32, l.Y32);
+        skern::patch_apply_f32<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff32, l.inv32, r, l.wt32, l.Y32);
     });
     launch(h, PK_PULL, s, [&] {
         skern::pull_scatter<float><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y32, (float)alpha, (float)beta, out);
@@ -384,11 +382,9 @@ void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, dou
 
 template <>
 void asm_apply<double>(stokes_mg* h, DevLevel& l, const double* r, double* out, double alpha, double beta, cudaStream_t s) {
-    const int ld2max = (l.maxn + 1) / 2;
-    const int block = std::min(256, std::max(32, (ld2max + 31) / 32 * 32));
+    const size_t smem = sizeof(double2) * (128 + 4) + sizeof(double) * l.maxn;
     launch(h, PK_PATCH, s, [&] {
-        skern::patch_apply_f64<<<l.npatch, block, l.maxn * sizeof(double), s>>>(l.npatch, l.poff, l.pdofs, l.ioff64, l.inv64,
-                                                                                r, l.wt64, l.Y64);
+        skern::patch_apply_f64<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff64, l.inv64, r, l.wt64, l.Y64);
     });
     launch(h, PK_PULL, s, [&] {
         skern::pull_scatter<double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y64, alpha, beta, out);
