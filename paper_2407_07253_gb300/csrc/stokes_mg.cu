@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -44,6 +45,18 @@ struct StokesError : std::runtime_error {
 
 double host_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// STOKES_TRACE=1 prints the host timeline of setup to stderr.
+bool trace_on() {
+    static const bool on = [] {
+        const char* e = std::getenv("STOKES_TRACE");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+void trace(const char* what, int level, double t0) {
+    if (trace_on()) std::fprintf(stderr, "[stokes] %-28s level %d  %8.3f ms\n", what, level, host_ms() - t0);
 }
 
 template <typename T>
@@ -174,6 +187,7 @@ struct PendingPatches {
     int level = 0;
     double* work = nullptr;
     int* status = nullptr;
+    cudaStream_t stream = nullptr;
 };
 
 struct Prof {
@@ -225,6 +239,7 @@ struct stokes_mg {
     // cudaMalloc chunks instead of one call per array
     char* slab_cur = nullptr;
     size_t slab_left = 0;
+    std::vector<void*> pool_allocs;      // freed to the device pool at destroy
     // setup in flight
     std::vector<PendingPatches> pending;
     int* c_ipiv = nullptr;
@@ -264,6 +279,36 @@ T* track(stokes_mg* h, T* p) {
     return p;
 }
 
+// Process-wide stream-ordered memory pool per device.  Its release
+// threshold is unlimited, so memory freed by one handle stays reserved and
+// the next setup allocates without touching the driver's allocator (a plain
+// cudaMalloc issued while the patch inversion runs was observed to wait for it).
+cudaMemPool_t device_pool(int dev) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {nullptr};
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64) throw StokesError(STOKES_EUNSUPPORTED, "device index beyond 64");
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CK(cudaMemPoolCreate(&pools[dev], &props));
+        unsigned long long thr = ~0ULL;
+        CK(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+    }
+    return pools[dev];
+}
+
+template <typename T>
+T* palloc(int dev, size_t n, cudaStream_t s) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    CK(cudaMallocFromPoolAsync(&p, n * sizeof(T), device_pool(dev), s));
+    return (T*)p;
+}
+
 constexpr size_t kSlabChunk = size_t(256) << 20;
 
 // Device buffer owned by the handle (freed by stokes_mg_destroy), 256-byte
@@ -271,9 +316,14 @@ constexpr size_t kSlabChunk = size_t(256) << 20;
 template <typename T>
 T* halloc(stokes_mg* h, size_t n) {
     size_t bytes = ((std::max<size_t>(n, 1) * sizeof(T)) + 255) & ~size_t(255);
-    if (bytes > kSlabChunk / 4) return track(h, dalloc<T>(n));
+    if (bytes > kSlabChunk / 4) {
+        T* p = palloc<T>(h->device, n, h->s_up);
+        h->pool_allocs.push_back((void*)p);
+        return p;
+    }
     if (h->slab_left < bytes) {
-        h->slab_cur = (char*)track(h, dalloc<char>(kSlabChunk));
+        h->slab_cur = palloc<char>(h->device, kSlabChunk, h->s_up);
+        h->pool_allocs.push_back((void*)h->slab_cur);
         h->slab_left = kSlabChunk;
     }
     T* p = (T*)h->slab_cur;
@@ -708,7 +758,10 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     DevLevel& l = h->L[li];
     l.n = HL.n_free;
     l.p_level = HL.p_level;
+    double tt = host_ms();
     l.K = upload_csr(h, HL.K, want32, s);
+    trace("upload K", li, tt);
+    tt = host_ms();
     const bool last = li + 1 == (int)h->H.levels.size();
     if (!last) {
         l.npatch = (int)HL.patch_off.size() - 1;
@@ -748,6 +801,8 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         for (int j = 0; j < l.n; ++j) soff[j + 1] = soff[j] + mult[j];
         std::vector<int> fill(soff.begin(), soff.end() - 1);
         for (long long q = 0; q < l.nent; ++q) sidx[fill[HL.patch_dofs[q]]++] = (int)q;
+        trace("patch maps (host)", li, tt);
+        tt = host_ms();
         l.wt64 = hupload(h, wt, s);
         l.soff = hupload(h, soff, s);
         l.sidx = hupload(h, sidx, s);
@@ -761,6 +816,8 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
             l.inv32 = halloc<float>(h, l.ninv32);
         }
     }
+    trace("patch uploads + allocs", li, tt);
+    tt = host_ms();
     l.b64 = halloc<double>(h, l.n); l.e64 = halloc<double>(h, l.n); l.r64 = halloc<double>(h, l.n);
     l.d64 = halloc<double>(h, l.n); l.t64 = halloc<double>(h, l.n); l.u64 = halloc<double>(h, l.n);
     if (want32) {
@@ -841,8 +898,9 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
     if (l.npatch == 0) return;
     PendingPatches pp;
     pp.level = li;
-    pp.work = dalloc<double>(l.nsq);
-    pp.status = dalloc<int>(l.npatch);
+    pp.work = palloc<double>(h->device, l.nsq, s);
+    pp.status = palloc<int>(h->device, l.npatch, s);
+    pp.stream = s;
     h->pending.push_back(pp);
     CK(cudaMemsetAsync(pp.status, 0, sizeof(int) * l.npatch, s));
     gather_and_invert(h, li, pp.work, true, pp.status, s);
@@ -850,8 +908,8 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
 
 void free_pending(stokes_mg* h) {
     for (auto& pp : h->pending) {
-        cudaFree(pp.work);
-        cudaFree(pp.status);
+        cudaFreeAsync(pp.work, pp.stream);
+        cudaFreeAsync(pp.status, pp.stream);
     }
     h->pending.clear();
 }
@@ -1151,7 +1209,12 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             // level-by-level pipeline: upload on s_up, then the patch
             // inversion (or the coarse factorisation) starts on the device
             // while the host assembles the next, coarser levels
-            CK(cudaStreamCreateWithFlags(&h->s_up, cudaStreamNonBlocking));
+            // uploads get the highest stream priority: pageable copies on this
+            // node run through the SMs, and must not queue behind the patch
+            // inversion that occupies every SM
+            int prio_lo = 0, prio_hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+            CK(cudaStreamCreateWithPriority(&h->s_up, cudaStreamNonBlocking, prio_hi));
             CK(cudaStreamCreateWithFlags(&h->s_coarse, cudaStreamNonBlocking));
             launcher.reset(new Launcher());
             on_level = [&](int li) {
@@ -1163,7 +1226,9 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                 cudaStream_t target = li + 1 < nlv ? s : hp->s_coarse;
                 if (li + 1 < nlv) {
                     upload_level(hp, li, want32, hp->s_up);
+                    const double tk = host_ms();
                     if (li == 0) alloc_krylov(hp, hp->s_up);
+                    trace("krylov buffers", li, tk);
                 } else {
                     upload_level(hp, li, want32, hp->s_up);
                     upload_coarse(hp, hp->s_up);
@@ -1174,6 +1239,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                 CK(cudaStreamWaitEvent(target, ev, 0));
                 CK(cudaEventDestroy(ev));
                 t_cb_upload += host_ms() - tu;
+                trace("level callback total", li, tu);
                 // kernel launches on the launcher thread
                 launcher->submit([hp, li, nlv, s, &o, &t_launch] {
                     const double tl = host_ms();
@@ -1592,6 +1658,10 @@ void stokes_mg_destroy(stokes_mg_t h) {
     if (h->s_up) cudaStreamDestroy(h->s_up);
     if (h->s_coarse) cudaStreamDestroy(h->s_coarse);
     for (void* p : h->allocs) cudaFree(p);
+    if (!h->pool_allocs.empty()) {
+        for (void* p : h->pool_allocs) cudaFreeAsync(p, 0);
+        cudaStreamSynchronize(0);
+    }
     if (h->pinned) cudaFreeHost(h->pinned);
     if (h->pinned_H) cudaFreeHost(h->pinned_H);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
