@@ -1,0 +1,351 @@
+// Device assembly of the Stokes operator and matrix-free load vector; see
+// assembly.cuh.
+#include "assembly.cuh"
+
+#include <climits>
+
+namespace sasm {
+
+namespace {
+
+constexpr int WARPS = 4;               // warps per block, one node per warp
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Geo {
+    double det;                        // |det J|
+    double Ji[9];                      // Jinv[a][c] = d xi_a / d x_c
+};
+
+__device__ Geo geometry(const AsmMesh& m, int e) {
+    const int d = m.d;
+    const int* v = m.C + (long long)e * (d + 1);
+    double J[9];
+    for (int c = 0; c < d; ++c)
+        for (int a = 0; a < d; ++a) J[c * d + a] = m.X[(long long)v[a + 1] * d + c] - m.X[(long long)v[0] * d + c];
+    Geo g;
+    if (d == 2) {
+        const double det = J[0] * J[3] - J[1] * J[2];
+        g.det = fabs(det);
+        g.Ji[0] = J[3] / det;  g.Ji[1] = -J[1] / det;
+        g.Ji[2] = -J[2] / det; g.Ji[3] = J[0] / det;
+    } else {
+        const double a = J[0], b = J[1], c = J[2], dd = J[3], e2 = J[4], f = J[5], gg = J[6], h = J[7], i = J[8];
+        const double A = e2 * i - f * h, B = -(dd * i - f * gg), Cc = dd * h - e2 * gg;
+        const double det = a * A + b * B + c * Cc;
+        g.det = fabs(det);
+        const double inv[9] = {A, -(b * i - c * h), b * f - c * e2, B, a * i - c * gg, -(a * f - c * dd),
+                               Cc, -(a * h - b * gg), a * e2 - b * dd};
+        for (int t = 0; t < 9; ++t) g.Ji[t] = inv[t] / det;
+    }
+    return g;
+}
+
+// Warp-cooperative insertion of this lane's candidate into the list of
+// distinct values (first-appearance order).  Returns false on overflow.
+__device__ bool warp_insert(int* list, int* cnt, int cand, bool valid) {
+    const int lane = threadIdx.x & 31;
+    const int n0 = *cnt;
+    bool keep = valid;
+    if (keep)
+        for (int t = 0; t < n0; ++t)
+            if (list[t] == cand) { keep = false; break; }
+    const unsigned same = __match_any_sync(FULL, keep ? cand : INT_MIN + lane);
+    keep = keep && (lane == __ffs(same) - 1);
+    const unsigned km = __ballot_sync(FULL, keep);
+    const int pos = n0 + __popc(km & ((1u << lane) - 1u));
+    const bool ok = n0 + __popc(km) <= MAX_ROW;
+    if (keep && ok) list[pos] = cand;
+    __syncwarp();
+    if (lane == 0) *cnt = ok ? n0 + __popc(km) : MAX_ROW + 1;
+    __syncwarp();
+    return ok;
+}
+
+// neighbours of node `node` whose incident cells are adj[off[node] .. ):
+// free velocity nodes into lv, pressure nodes into lq (if lq != nullptr)
+__device__ bool neighbours(const AsmMesh& m, const int* off, const int* adj, int per_cell, int node, int* lv,
+                           int* cv, int* lq, int* cq) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = off[node], ncell = off[node + 1] - c0;
+    if (lane == 0) { *cv = 0; if (lq) *cq = 0; }
+    __syncwarp();
+    const int tv = ncell * m.nb;
+    for (int base = 0; base < tv; base += 32) {
+        const int t = base + lane;
+        int cand = 0;
+        bool valid = false;
+        if (t < tv) {
+            const int e = adj[c0 + t / m.nb] / per_cell;
+            cand = m.vcell[(long long)e * m.nb + t % m.nb];
+            valid = m.vfree[cand] >= 0;
+        }
+        if (!warp_insert(lv, cv, cand, valid)) return false;
+    }
+    if (lq) {
+        const int tq = ncell * m.nq;
+        for (int base = 0; base < tq; base += 32) {
+            const int t = base + lane;
+            int cand = 0;
+            bool valid = false;
+            if (t < tq) {
+                const int e = adj[c0 + t / m.nq] / per_cell;
+                cand = m.qcell[(long long)e * m.nq + t % m.nq];
+                valid = true;
+            }
+            if (!warp_insert(lq, cq, cand, valid)) return false;
+        }
+    }
+    return true;
+}
+
+__device__ int find(const int* list, int n, int x) {
+    for (int t = 0; t < n; ++t)
+        if (list[t] == x) return t;
+    return -1;
+}
+
+struct WarpLists {
+    int lv[MAX_ROW];
+    int lq[MAX_ROW];
+    int cv, cq;
+};
+
+__global__ void __launch_bounds__(WARPS * 32) k_row_lengths(AsmMesh m, int* len, int* status) {
+    __shared__ WarpLists W[WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WARPS + w;
+    WarpLists& L = W[w];
+    if (item < m.nVf) {
+        const int node = m.vrow[item];
+        if (!neighbours(m, m.voff, m.vadj, m.nb, node, L.lv, &L.cv, L.lq, &L.cq)) {
+            if (lane == 0) atomicExch(status, 1);
+            return;
+        }
+        if (lane == 0)
+            for (int c = 0; c < m.d; ++c) len[c * m.nVf + item] = L.cv + L.cq;
+    } else if (item < m.nVf + m.nQ) {
+        const int q = item - m.nVf;
+        if (!neighbours(m, m.qoff, m.qadj, m.nq, q, L.lv, &L.cv, nullptr, nullptr)) {
+            if (lane == 0) atomicExch(status, 1);
+            return;
+        }
+        if (lane == 0) len[m.d * m.nVf + q] = m.d * L.cv;
+    }
+}
+
+// Values accumulate directly in the output row segments: a warp owns its
+// rows, lanes of one cell touch distinct positions, and __syncwarp orders the
+// cells, so the sums are deterministic without atomics.
+__global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, int* ci, double* val, int* status) {
+    __shared__ WarpLists W[WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WARPS + w;
+    WarpLists& L = W[w];
+    const int d = m.d, nb = m.nb, nq = m.nq;
+    if (item < m.nVf) {
+        const int node = m.vrow[item];
+        if (!neighbours(m, m.voff, m.vadj, nb, node, L.lv, &L.cv, L.lq, &L.cq)) {
+            if (lane == 0) atomicExch(status, 1);
+            return;
+        }
+        const int len = L.cv + L.cq;
+        for (int c = 0; c < d; ++c) {
+            const long long r0 = rp[c * m.nVf + item];
+            for (int t = lane; t < len; t += 32) {
+                val[r0 + t] = 0.0;
+                ci[r0 + t] = t < L.cv ? c * m.nVf + m.vfree[L.lv[t]] : d * m.nVf + L.lq[t - L.cv];
+            }
+        }
+        __syncwarp();
+        const long long r00 = rp[item];
+        for (int x = m.voff[node]; x < m.voff[node + 1]; ++x) {
+            const int e = m.vadj[x] / nb, la = m.vadj[x] % nb;
+            const Geo g = geometry(m, e);
+            const double wgt = g.det * (m.nu ? m.nu[e] : 1.0);
+            double G[9];
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) {
+                    double s = 0;
+                    for (int c = 0; c < d; ++c) s += g.Ji[a * d + c] * g.Ji[b * d + c];
+                    G[a * d + b] = s;
+                }
+            for (int b = lane; b < nb; b += 32) {
+                const int j = m.vcell[(long long)e * nb + b];
+                if (m.vfree[j] < 0) continue;
+                double s = 0;
+                for (int a = 0; a < d; ++a)
+                    for (int bb = 0; bb < d; ++bb) s += G[a * d + bb] * m.S[(((long long)a * d + bb) * nb + la) * nb + b];
+                val[r00 + find(L.lv, L.cv, j)] += wgt * s;
+            }
+            for (int p = lane; p < nq; p += 32) {
+                const int q = m.qcell[(long long)e * nq + p];
+                const int pos = L.cv + find(L.lq, L.cq, q);
+                for (int c = 0; c < d; ++c) {
+                    double s = 0;
+                    for (int a = 0; a < d; ++a) s += g.Ji[a * d + c] * m.Cq[((long long)a * nq + p) * nb + la];
+                    val[rp[c * m.nVf + item] + pos] += -g.det * s;
+                }
+            }
+            __syncwarp();
+        }
+        // the velocity block is the same for every component
+        for (int c = 1; c < d; ++c) {
+            const long long r0 = rp[c * m.nVf + item];
+            for (int t = lane; t < L.cv; t += 32) val[r0 + t] = val[r00 + t];
+        }
+    } else if (item < m.nVf + m.nQ) {
+        const int q = item - m.nVf;
+        if (!neighbours(m, m.qoff, m.qadj, nq, q, L.lv, &L.cv, nullptr, nullptr)) {
+            if (lane == 0) atomicExch(status, 1);
+            return;
+        }
+        const long long r0 = rp[d * m.nVf + q];
+        for (int c = 0; c < d; ++c)
+            for (int t = lane; t < L.cv; t += 32) {
+                ci[r0 + (long long)c * L.cv + t] = c * m.nVf + m.vfree[L.lv[t]];
+                val[r0 + (long long)c * L.cv + t] = 0.0;
+            }
+        __syncwarp();
+        for (int x = m.qoff[q]; x < m.qoff[q + 1]; ++x) {
+            const int e = m.qadj[x] / nq, lp = m.qadj[x] % nq;
+            const Geo g = geometry(m, e);
+            for (int b = lane; b < nb; b += 32) {
+                const int j = m.vcell[(long long)e * nb + b];
+                if (m.vfree[j] < 0) continue;
+                const int pos = find(L.lv, L.cv, j);
+                for (int c = 0; c < d; ++c) {
+                    double s = 0;
+                    for (int a = 0; a < d; ++a) s += g.Ji[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + b];
+                    val[r0 + (long long)c * L.cv + pos] += -g.det * s;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// exclusive scan, 1024 elements per block
+__global__ void __launch_bounds__(1024) k_scan_block(const int* in, int n, int* out, int* bsum) {
+    __shared__ int ws[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = i < n ? in[i] : 0;
+    int v = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) ws[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int s = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    const int incl = v + (w > 0 ? ws[w - 1] : 0);
+    if (i < n) out[i] = incl - x;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_sums(int* bsum, int nb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int t = bsum[b];
+        bsum[b] = run;
+        run += t;
+    }
+    bsum[nb] = run;
+}
+
+__global__ void k_scan_add(int* out, int n, const int* bsum, int nblk) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[i / 1024];
+    if (i == 0) out[n] = bsum[nblk];
+}
+
+// one thread per row: b = (M f)/nu on velocity rows minus K[r, D] g
+__global__ void k_load(AsmMesh m, const double* f, const double* gD, double inv_nu, double* b) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = m.d, nb = m.nb, nq = m.nq;
+    if (r < d * m.nVf) {
+        const int c = r / m.nVf, fi = r - c * m.nVf;
+        const int node = m.vrow[fi];
+        double F = 0, lift = 0;
+        for (int x = m.voff[node]; x < m.voff[node + 1]; ++x) {
+            const int e = m.vadj[x] / nb, la = m.vadj[x] % nb;
+            const Geo g = geometry(m, e);
+            for (int bb = 0; bb < nb; ++bb) {
+                const int j = m.vcell[(long long)e * nb + bb];
+                F += g.det * m.M[(long long)la * nb + bb] * f[(long long)c * m.nV + j];
+            }
+            if (gD) {
+                const double wgt = g.det * (m.nu ? m.nu[e] : 1.0);
+                double G[9];
+                for (int a = 0; a < d; ++a)
+                    for (int a2 = 0; a2 < d; ++a2) {
+                        double s = 0;
+                        for (int k = 0; k < d; ++k) s += g.Ji[a * d + k] * g.Ji[a2 * d + k];
+                        G[a * d + a2] = s;
+                    }
+                for (int bb = 0; bb < nb; ++bb) {
+                    const int j = m.vcell[(long long)e * nb + bb];
+                    if (m.vfree[j] >= 0) continue;
+                    double s = 0;
+                    for (int a = 0; a < d; ++a)
+                        for (int a2 = 0; a2 < d; ++a2) s += G[a * d + a2] * m.S[(((long long)a * d + a2) * nb + la) * nb + bb];
+                    lift += wgt * s * gD[(long long)c * m.nV + j];
+                }
+            }
+        }
+        b[r] = F * inv_nu - lift;
+    } else if (r < d * m.nVf + m.nQ) {
+        const int q = r - d * m.nVf;
+        double lift = 0;
+        if (gD)
+            for (int x = m.qoff[q]; x < m.qoff[q + 1]; ++x) {
+                const int e = m.qadj[x] / nq, lp = m.qadj[x] % nq;
+                const Geo g = geometry(m, e);
+                for (int bb = 0; bb < nb; ++bb) {
+                    const int j = m.vcell[(long long)e * nb + bb];
+                    if (m.vfree[j] >= 0) continue;
+                    for (int c = 0; c < d; ++c) {
+                        double s = 0;
+                        for (int a = 0; a < d; ++a) s += g.Ji[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + bb];
+                        lift += -g.det * s * gD[(long long)c * m.nV + j];
+                    }
+                }
+            }
+        b[r] = -lift;
+    }
+}
+
+}  // namespace
+
+void row_lengths(const AsmMesh& m, int* len, int* status, cudaStream_t s) {
+    const int items = m.nVf + m.nQ;
+    k_row_lengths<<<(items + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(m, len, status);
+}
+
+void scan_rows(const int* len, int n, int* rp, int* tmp, cudaStream_t s) {
+    const int nblk = (n + 1023) / 1024;
+    k_scan_block<<<nblk, 1024, 0, s>>>(len, n, rp, tmp);
+    k_scan_sums<<<1, 1, 0, s>>>(tmp, nblk);
+    k_scan_add<<<(n + 255) / 256, 256, 0, s>>>(rp, n, tmp, nblk);
+}
+
+void fill_rows(const AsmMesh& m, const int* rp, int* ci, double* v, int* status, cudaStream_t s) {
+    const int items = m.nVf + m.nQ;
+    k_fill<<<(items + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(m, rp, ci, v, status);
+}
+
+void load_vector(const AsmMesh& m, const double* f, const double* g, double inv_nu, double* b, cudaStream_t s) {
+    const int rows = m.d * m.nVf + m.nQ;
+    k_load<<<(rows + 127) / 128, 128, 0, s>>>(m, f, g, inv_nu, b);
+}
+
+}  // namespace sasm

@@ -717,6 +717,7 @@ static CellGeom cell_geom(const Mesh& m, int e) {
 
 // node -> (cell, local index) adjacency
 static void node_cells(const Space& S, int nc, std::vector<int>& off, std::vector<int>& adj) {
+    // (cells in increasing index for every node)
     off.assign(S.n + 1, 0);
     for (int x : S.cell_nodes) off[x + 1]++;
     for (int i = 0; i < S.n; ++i) off[i + 1] += off[i];
@@ -724,6 +725,33 @@ static void node_cells(const Space& S, int nc, std::vector<int>& off, std::vecto
     std::vector<int> fill(off.begin(), off.end() - 1);
     for (int e = 0; e < nc; ++e)
         for (int l = 0; l < S.nb; ++l) adj[fill[S.cell_nodes[(size_t)e * S.nb + l]]++] = e * S.nb + l;
+}
+
+// DoF maps and adjacency a device assembly needs (no matrices).
+static void prepare_level(const Mesh& m, Level& L, const RefTensors& RT) {
+    const int d = m.d, nq = L.Q.nb, nc = m.nc;
+    const Space &V = L.V, &Q = L.Q;
+    L.vfree.assign(V.n, -1);
+    int nVf = 0;
+    for (int i = 0; i < V.n; ++i)
+        if (!V.boundary[i]) L.vfree[i] = nVf++;
+    L.nVf = nVf;
+    L.nQ = Q.n;
+    L.n_free = d * nVf + Q.n;
+    node_cells(V, nc, L.voff, L.vadj);
+    node_cells(Q, nc, L.qoff, L.qadj);
+    L.pint.assign(Q.n, 0.0);
+    for (int e = 0; e < nc; ++e) {
+        const double det = cell_geom(m, e).detabs;
+        for (int p = 0; p < nq; ++p) L.pint[Q.cell_nodes[(size_t)e * nq + p]] += det * RT.qint[p];
+    }
+    L.cell_center.assign((size_t)nc * d, 0.0);
+    for (int e = 0; e < nc; ++e)
+        for (int cc = 0; cc < d; ++cc) {
+            double s = 0;
+            for (int i = 0; i <= d; ++i) s += m.X[(size_t)m.C[(size_t)e * (d + 1) + i] * d + cc];
+            L.cell_center[(size_t)e * d + cc] = s / (d + 1);
+        }
 }
 
 static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const std::vector<double>& nu,
@@ -772,9 +800,9 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
     L.nVf = nVf;
     L.nQ = Q.n;
     L.n_free = d * nVf + Q.n;
-    std::vector<int> voff, vadj, qoff, qadj;
-    node_cells(V, nc, voff, vadj);
-    node_cells(Q, nc, qoff, qadj);
+    node_cells(V, nc, L.voff, L.vadj);
+    node_cells(Q, nc, L.qoff, L.qadj);
+    const std::vector<int>&voff = L.voff, &vadj = L.vadj, &qoff = L.qoff, &qadj = L.qadj;
     // pressure integrals
     L.pint.assign(Q.n, 0.0);
     for (int e = 0; e < nc; ++e)
@@ -1241,7 +1269,11 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         if (rit == tensors.end()) { tensors[rkey].init(rv, rq); rit = tensors.find(rkey); }
         const RefTensors& RT = rit->second;
         double tb = now_ms();
-        assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
+        L.RT = RT;
+        L.nu_cells = nus[L.mesh_index];
+        L.host_matrices = !spec.device_assembly || l + 1 == ls.size();
+        if (L.host_matrices) assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
+        else prepare_level(m, L, RT);
         double tc = now_ms();
         if (l + 1 < ls.size()) build_patches(m, topo[L.mesh_index], L);
         H.t_spaces_ms += tb - ta;

@@ -102,6 +102,12 @@ struct Level {
                                               // a patch lists d blocks of n_v velocity DoFs
                                               // (same nodes per component), then n_p pressures
     std::vector<double> cell_center;          // [nc][d]
+    // what a device assembly needs: node -> (cell * nb + local) adjacency,
+    // the reference tensors and the cell viscosities
+    std::vector<int> voff, vadj, qoff, qadj;
+    RefTensors RT;
+    std::vector<double> nu_cells;
+    bool host_matrices = true;                // K (and on level 0 Mv, KfD) assembled here
 };
 
 struct HierarchySpec {
@@ -109,6 +115,7 @@ struct HierarchySpec {
     std::vector<int> schedule;   // velocity degrees of the p-levels + the hMG degree
     int n_refine = 0;
     bool barycentric = false;
+    bool device_assembly = false;             // leave K of all but the coarsest level to the device
 };
 
 struct Hierarchy {

@@ -24,6 +24,7 @@
 
 #include "../../include/stokes_mg.h"
 #include "fem.hpp"
+#include "assembly.cuh"
 #include "kernels.cuh"
 
 namespace {
@@ -181,6 +182,12 @@ struct DevLevel {
     double *b64 = nullptr, *e64 = nullptr, *r64 = nullptr, *d64 = nullptr, *t64 = nullptr, *u64 = nullptr;
     float *b32 = nullptr, *e32 = nullptr, *r32 = nullptr, *d32 = nullptr, *t32 = nullptr, *u32 = nullptr;
     double lmax = 0;
+    // device assembly of K (all levels but the coarsest)
+    bool dev_asm = false;
+    sasm::AsmMesh am;
+    int* asm_len = nullptr;
+    int* asm_tmp = nullptr;
+    int* asm_status = nullptr;
 };
 
 struct PendingPatches {
@@ -246,6 +253,8 @@ struct stokes_mg {
     double* c_colk = nullptr;
     int* c_status = nullptr;
     cudaStream_t s_up = nullptr, s_coarse = nullptr;
+    std::vector<double*> mesh_X;         // device vertex coordinates per mesh
+    std::vector<int*> mesh_C;            // device cells per mesh
     std::vector<void*> allocs;
 };
 
@@ -753,13 +762,19 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
 }
 
 // ---------------------------------------------------------------- setup --
+void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s);
+
 void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     const sfem::Level& HL = h->H.levels[li];
     DevLevel& l = h->L[li];
     l.n = HL.n_free;
     l.p_level = HL.p_level;
     double tt = host_ms();
-    l.K = upload_csr(h, HL.K, want32, s);
+    if (HL.host_matrices) {
+        l.K = upload_csr(h, HL.K, want32, s);
+    } else {
+        upload_assembly_inputs(h, li, want32, s);
+    }
     trace("upload K", li, tt);
     tt = host_ms();
     const bool last = li + 1 == (int)h->H.levels.size();
@@ -823,6 +838,94 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     if (want32) {
         l.b32 = halloc<float>(h, l.n); l.e32 = halloc<float>(h, l.n); l.r32 = halloc<float>(h, l.n);
         l.d32 = halloc<float>(h, l.n); l.t32 = halloc<float>(h, l.n); l.u32 = halloc<float>(h, l.n);
+    }
+}
+
+// Mesh, DoF maps, adjacency and reference tensors of a level whose K is
+// assembled on the device; K's arrays are sized by an upper bound on the
+// row lengths (incident cells times nodes per cell).
+void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s) {
+    const sfem::Level& HL = h->H.levels[li];
+    DevLevel& l = h->L[li];
+    const sfem::Mesh& mesh = h->H.meshes[HL.mesh_index];
+    const int nm = (int)h->H.meshes.size();
+    if ((int)h->mesh_X.size() != nm) { h->mesh_X.assign(nm, nullptr); h->mesh_C.assign(nm, nullptr); }
+    if (!h->mesh_X[HL.mesh_index]) {
+        h->mesh_X[HL.mesh_index] = hupload(h, mesh.X, s);
+        h->mesh_C[HL.mesh_index] = hupload(h, mesh.C, s);
+    }
+    sasm::AsmMesh& a = l.am;
+    a.d = HL.d;
+    a.nc = mesh.nc;
+    a.nb = HL.V.nb;
+    a.nq = HL.Q.nb;
+    a.nV = HL.V.n;
+    a.nQ = HL.nQ;
+    a.nVf = HL.nVf;
+    a.X = h->mesh_X[HL.mesh_index];
+    a.C = h->mesh_C[HL.mesh_index];
+    a.vcell = hupload(h, HL.V.cell_nodes, s);
+    a.qcell = hupload(h, HL.Q.cell_nodes, s);
+    a.vfree = hupload(h, HL.vfree, s);
+    std::vector<int> vrow(HL.nVf);
+    for (int i = 0; i < HL.V.n; ++i)
+        if (HL.vfree[i] >= 0) vrow[HL.vfree[i]] = i;
+    a.vrow = hupload(h, vrow, s);
+    a.voff = hupload(h, HL.voff, s);
+    a.vadj = hupload(h, HL.vadj, s);
+    a.qoff = hupload(h, HL.qoff, s);
+    a.qadj = hupload(h, HL.qadj, s);
+    a.nu = HL.nu_cells.empty() ? nullptr : hupload(h, HL.nu_cells, s);
+    a.S = hupload(h, HL.RT.S, s);
+    a.Cq = hupload(h, HL.RT.Cq, s);
+    a.M = hupload(h, HL.RT.M, s);
+    long long bound = 0;
+    for (int f = 0; f < HL.nVf; ++f) {
+        const int i = vrow[f];
+        bound += (long long)HL.d * (HL.voff[i + 1] - HL.voff[i]) * (a.nb + a.nq);
+    }
+    for (int q = 0; q < HL.nQ; ++q) bound += (long long)HL.d * (HL.qoff[q + 1] - HL.qoff[q]) * a.nb;
+    const int n = HL.n_free;
+    DevCSR& K = l.K;
+    K.nr = K.nc = n;
+    K.nnz = bound;                       // exact count read back once setup has synchronised
+    K.rp = halloc<int>(h, n + 1);
+    K.ci = halloc<int>(h, bound);
+    K.v64 = halloc<double>(h, bound);
+    K.v32 = want32 ? halloc<float>(h, bound) : nullptr;
+    K.lanes = 16;
+    l.asm_len = halloc<int>(h, n);
+    l.asm_tmp = halloc<int>(h, (n + 1023) / 1024 + 2);
+    l.asm_status = halloc<int>(h, 1);
+    CK(cudaMemsetAsync(l.asm_status, 0, sizeof(int), s));
+    l.dev_asm = true;
+}
+
+// K of a device-assembled level: row lengths, scan, values (stream s)
+void assemble_on_device(stokes_mg* h, int li, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    if (!l.dev_asm) return;
+    const int n = l.K.nr;
+    launch(h, -1, s, [&] { sasm::row_lengths(l.am, l.asm_len, l.asm_status, s); });
+    launch(h, -1, s, [&] { sasm::scan_rows(l.asm_len, n, l.K.rp, l.asm_tmp, s); });
+    launch(h, -1, s, [&] { sasm::fill_rows(l.am, l.K.rp, l.K.ci, l.K.v64, l.asm_status, s); });
+    if (l.K.v32)
+        launch(h, -1, s, [&] {
+            skern::convert_vec<float, double><<<grid_for(l.K.nnz), 256, 0, s>>>((int)l.K.nnz, l.K.v64, l.K.v32);
+        });
+}
+
+// exact nnz of the device-assembled operators (after the setup stream synchronised)
+void finish_assembly(stokes_mg* h) {
+    for (size_t li = 0; li < h->L.size(); ++li) {
+        DevLevel& l = h->L[li];
+        if (!l.dev_asm) continue;
+        int st = 0, nnz = 0;
+        CK(cudaMemcpy(&st, l.asm_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st != 0) throw StokesError(STOKES_EUNSUPPORTED, "a node has more than 1024 neighbours (level " + std::to_string(li) + ")");
+        CK(cudaMemcpy(&nnz, l.K.rp + l.K.nr, sizeof(int), cudaMemcpyDeviceToHost));
+        l.K.nnz = nnz;
+        l.K.lanes = choose_lanes(l.K);
     }
 }
 
@@ -990,8 +1093,10 @@ void finish_coarse(stokes_mg* h, cudaStream_t s) {
 void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
     const sfem::Level& F = h->H.levels[0];
     const int d = F.d;
-    h->Mv = upload_csr(h, F.Mv, false, s);
-    h->KfD = upload_csr(h, F.KfD, false, s);
+    if (F.host_matrices) {
+        h->Mv = upload_csr(h, F.Mv, false, s);
+        h->KfD = upload_csr(h, F.KfD, false, s);
+    }
     std::vector<int> rows(d * F.nVf);
     std::vector<int> vrow(F.nVf);
     for (int i = 0; i < F.V.n; ++i)
@@ -1052,7 +1157,7 @@ void fill_stats(stokes_mg* h) {
         st.level_family[i] = HL.family;
         st.mesh_index[i] = HL.mesh_index;
         st.is_p_level[i] = HL.p_level ? 1 : 0;
-        st.nnz[i] = HL.K.nnz();
+        st.nnz[i] = (!HL.host_matrices && i < (int)h->L.size()) ? h->L[i].K.nnz : HL.K.nnz();
         const int np = HL.patch_off.empty() ? 0 : (int)HL.patch_off.size() - 1;
         long long sq = 0;
         int mx = 0;
@@ -1184,6 +1289,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         spec.k = k;
         spec.n_refine = n_refine;
         spec.barycentric = barycentric_finest != 0;
+        spec.device_assembly = !o.host_only;
         if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
         else if (o.hierarchy == STOKES_HIER_GRADUAL) {
             if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
@@ -1245,6 +1351,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                     const double tl = host_ms();
                     CK(cudaSetDevice(hp->device));
                     if (li + 1 < nlv) {
+                        assemble_on_device(hp, li, s);
                         launch_patches(hp, li, s);
                         // lambda_max estimate right behind the inversion (same stream)
                         if (!(li < 16 && o.lmax_override[li] > 0)) {
@@ -1293,6 +1400,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         // factorisation once the host is done
         t1 = host_ms();
         finish_patches(h.get(), s);
+        finish_assembly(h.get());
         h->st.t_gather_lu_ms = host_ms() - t1;
         t1 = host_ms();
         finish_coarse(h.get(), h->s_coarse);
@@ -1362,15 +1470,21 @@ int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, do
         cudaStream_t s = (cudaStream_t)stream;
         const sfem::Level& F = h->H.levels[0];
         const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ, n = F.n_free;
-        // F_c = M f_c
-        for (int c = 0; c < d; ++c)
-            spmv<double>(h, -1, h->Mv, skern::SPMV_SET, f_nodal + (size_t)c * nV, h->F + (size_t)c * nV, nullptr, s);
-        // b_vel = F / nu on the free rows, b_p = 0; then b -= K_{free,D} g
-        launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->F, h->bvec); });
-        if (nu != 1.0) axpby_l<double>(h, d * nVf, 0.0, h->bvec, 1.0 / nu, h->bvec, s);
-        CK(cudaMemsetAsync(h->bvec + (size_t)d * nVf, 0, sizeof(double) * nQ, s));
         const double* gfull = g_nodal ? g_nodal : h->gzero;
-        spmv<double>(h, -1, h->KfD, skern::SPMV_RESID, gfull, h->bvec, h->bvec, s);
+        if (h->L[0].dev_asm) {
+            // matrix-free: b = (M f)/nu - K[free, D] g, assembled per row from
+            // the incident cells (same element integrals as the operator)
+            launch(h, -1, s, [&] { sasm::load_vector(h->L[0].am, f_nodal, g_nodal, 1.0 / nu, h->bvec, s); });
+        } else {
+            // F_c = M f_c
+            for (int c = 0; c < d; ++c)
+                spmv<double>(h, -1, h->Mv, skern::SPMV_SET, f_nodal + (size_t)c * nV, h->F + (size_t)c * nV, nullptr, s);
+            // b_vel = F / nu on the free rows, b_p = 0; then b -= K_{free,D} g
+            launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->F, h->bvec); });
+            if (nu != 1.0) axpby_l<double>(h, d * nVf, 0.0, h->bvec, 1.0 / nu, h->bvec, s);
+            CK(cudaMemsetAsync(h->bvec + (size_t)d * nVf, 0, sizeof(double) * nQ, s));
+            spmv<double>(h, -1, h->KfD, skern::SPMV_RESID, gfull, h->bvec, h->bvec, s);
+        }
         // remove the component along the pressure null vector (consistency)
         mdot(h, nQ, 1, h->bvec + (size_t)d * nVf, nQ, h->ones, h->scal, nullptr, false, s);
         launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, h->bvec + (size_t)d * nVf, h->scal, (double)nQ); });
@@ -1451,6 +1565,19 @@ int stokes_mg_get_csr(stokes_mg_t h, int level, int which, int* n_rows, int* n_c
         require(h && level >= 0 && level < nl && which >= 0 && which <= 2, "invalid argument");
         const sfem::Level& L = h->H.levels[level];
         require(which == 0 || level + 1 < nl, "no transfer on the coarsest level");
+        if (which == 0 && !L.host_matrices) {
+            // assembled on the device
+            const DevCSR& D = h->L[level].K;
+            if (n_rows) *n_rows = D.nr;
+            if (n_cols) *n_cols = D.nc;
+            if (nnz) *nnz = D.nnz;
+            if (row_ptr) {
+                CK(cudaMemcpy(row_ptr, D.rp, sizeof(int) * (D.nr + 1), cudaMemcpyDeviceToHost));
+                if (col) CK(cudaMemcpy(col, D.ci, sizeof(int) * D.nnz, cudaMemcpyDeviceToHost));
+                if (val) CK(cudaMemcpy(val, D.v64, sizeof(double) * D.nnz, cudaMemcpyDeviceToHost));
+            }
+            return STOKES_OK;
+        }
         const sfem::CSR& A = which == 0 ? L.K : (which == 1 ? L.P : L.R);
         if (n_rows) *n_rows = A.nr;
         if (n_cols) *n_cols = A.ncol;
