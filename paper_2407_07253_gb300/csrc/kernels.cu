@@ -289,28 +289,36 @@ __global__ void __launch_bounds__(512) gj_inverse_global(int npatch, const int* 
     if (threadIdx.x == 0) status[p] = st;
 }
 
-// In-place inverse of an SPD matrix (row-major, leading dimension lda) by
-// Gauss-Jordan without pivoting: an SPD matrix needs no row interchanges.
-// status <- 1 + step of the first non-positive pivot.
-__device__ void gj_spd(double* A, int n, int lda, double* colk, int* status) {
+// Goodnight's symmetric sweep of an SPD matrix (row-major, leading
+// dimension lda), working on the upper triangle only: sweeping pivot k maps
+//   a_kk -> -1/a_kk,  a_ik -> a_ik/a_kk,  a_ij -> a_ij - a_ik a_kj / a_kk,
+// and sweeping every pivot in order leaves -A^{-1} (upper triangle).  An SPD
+// matrix needs no pivoting.  status <- 1 + step of the first non-positive pivot.
+__device__ void sweep_spd(double* A, int n, int lda, double* colk, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int k = 0; k < n; ++k) {
         const double piv = A[(long long)k * lda + k];
         if (tid == 0 && !(piv > 0.0) && *status == 0) *status = k + 1;
         const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
-        for (int i = tid; i < n; i += nt) colk[i] = A[(long long)i * lda + k];
-        __syncthreads();
-        for (int j = tid; j < n; j += nt) A[(long long)k * lda + j] = (j == k) ? inv : A[(long long)k * lda + j] * inv;
+        for (int i = tid; i < n; i += nt) colk[i] = i <= k ? A[(long long)i * lda + k] : A[(long long)k * lda + i];
         __syncthreads();
         for (int t = tid; t < n * n; t += nt) {
             const int i = t / n, j = t - (t / n) * n;
-            if (i == k) continue;
-            const double f = colk[i];
-            if (j == k) A[(long long)i * lda + k] = -f * inv;
-            else A[(long long)i * lda + j] -= f * A[(long long)k * lda + j];
+            if (j < i) continue;
+            double v;
+            if (i == k && j == k) v = -inv;
+            else if (i == k) v = colk[j] * inv;
+            else if (j == k) v = colk[i] * inv;
+            else v = A[(long long)i * lda + j] - colk[i] * colk[j] * inv;
+            A[(long long)i * lda + j] = v;
         }
         __syncthreads();
     }
+}
+
+// symmetric access to the upper triangle of a swept matrix: A^{-1}[i][j]
+__device__ __forceinline__ double neg_upper(const double* A, int lda, int i, int j) {
+    return -(i <= j ? A[(long long)i * lda + j] : A[(long long)j * lda + i]);
 }
 
 // Block inverse of one Vanka patch with the saddle structure
@@ -318,8 +326,10 @@ __device__ void gj_spd(double* A, int n, int lda, double* colk, int* status) {
 // (the d velocity components share the SPD block L on the same nodes):
 //   Li = L^{-1}, W_c = Li B_c^T, S = sum_c B_c W_c, Si = S^{-1}, X_c = W_c Si,
 //   K_i^{-1} = [blockdiag(Li) - X W^T, X; X^T, -Si].
-// K (row-major n x n) is read from the workspace; the inverse is written
-// column-major (padded) in FP64 / FP32 and, if back != 0, row-major back to K.
+// Li and Si come from the symmetric sweep; the symmetric velocity block is
+// computed on its upper triangle and mirrored.  K (row-major n x n) is read
+// from the workspace and overwritten by the (exactly symmetric) inverse,
+// which is then written column-major (padded) in FP64 / FP32.
 __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, double* inv64, float* inv32,
                             int back, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -338,69 +348,78 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
         Bt[(long long)r * npp + q] = K[(long long)r * n + dnv + q];
     }
     __syncthreads();
-    gj_spd(Ls, nv, nv, colk, status);
+    sweep_spd(Ls, nv, nv, colk, status);
     // W_c = Li B_c^T
     for (int t = tid; t < dnv * np; t += nt) {
         const int r = t / np, q = t - (t / np) * np;
         const int c = r / nv, a = r - c * nv;
-        const double* li = Ls + (long long)a * nv;
         const double* bt = Bt + (long long)c * nv * npp + q;
         double s = 0.0;
-        for (int b = 0; b < nv; ++b) s += li[b] * bt[(long long)b * npp];
+        for (int b = 0; b < nv; ++b) s += neg_upper(Ls, nv, a, b) * bt[(long long)b * npp];
         Wm[(long long)r * npp + q] = s;
     }
     __syncthreads();
-    // S = sum_c B_c W_c
+    // S = sum_c B_c W_c (symmetric: upper triangle)
     for (int t = tid; t < np * np; t += nt) {
         const int q = t / np, r = t - (t / np) * np;
+        if (r < q) continue;
         double s = 0.0;
         for (int a = 0; a < dnv; ++a) s += Bt[(long long)a * npp + q] * Wm[(long long)a * npp + r];
         Ss[t] = s;
     }
     __syncthreads();
-    gj_spd(Ss, np, np, colk, status);
+    sweep_spd(Ss, np, np, colk, status);
     // X_c = W_c Si (overwrites Bt)
     for (int t = tid; t < dnv * np; t += nt) {
         const int r = t / np, q = t - (t / np) * np;
         const double* w = Wm + (long long)r * npp;
         double s = 0.0;
-        for (int x = 0; x < np; ++x) s += w[x] * Ss[(long long)x * np + q];
+        for (int x = 0; x < np; ++x) s += w[x] * neg_upper(Ss, np, x, q);
         Bt[(long long)r * npp + q] = s;
     }
     __syncthreads();
-    const int ld64 = (n + 1) & ~1, ld32 = (n + 3) & ~3;
-    const int ldw = inv64 ? ld64 : (inv32 ? ld32 : n);
-    for (long long t = tid; t < (long long)ldw * n; t += nt) {
-        const int j = (int)(t / ldw), i = (int)(t - (long long)j * ldw);
-        double v = 0.0;
-        if (i < n) {
-            if (i < dnv && j < dnv) {
-                const int c = i / nv, a = i - c * nv, c2 = j / nv, b = j - c2 * nv;
-                const double* x = Bt + (long long)i * npp;
-                const double* w = Wm + (long long)j * npp;
-                double s = 0.0;
-                for (int q = 0; q < np; ++q) s += x[q] * w[q];
-                v = (c == c2 ? Ls[(long long)a * nv + b] : 0.0) - s;
-            } else if (i < dnv) {
-                v = Bt[(long long)i * npp + (j - dnv)];
-            } else if (j < dnv) {
-                v = Bt[(long long)j * npp + (i - dnv)];
-            } else {
-                v = -Ss[(long long)(i - dnv) * np + (j - dnv)];
-            }
+    // the inverse, row-major into K; velocity block on its upper triangle
+    for (long long t = tid; t < (long long)n * n; t += nt) {
+        const int i = (int)(t / n), j = (int)(t - (long long)i * n);
+        double v;
+        if (i < dnv && j < dnv) {
+            if (j < i) continue;
+            const int c = i / nv, a = i - c * nv, c2 = j / nv, b = j - c2 * nv;
+            const double* x = Bt + (long long)i * npp;
+            const double* w = Wm + (long long)j * npp;
+            double s = 0.0;
+            for (int q = 0; q < np; ++q) s += x[q] * w[q];
+            v = (c == c2 ? neg_upper(Ls, nv, a, b) : 0.0) - s;
+        } else if (i < dnv) {
+            v = Bt[(long long)i * npp + (j - dnv)];
+        } else if (j < dnv) {
+            v = Bt[(long long)j * npp + (i - dnv)];
+        } else {
+            // the pressure block of K^-1 is -Si, which the sweep left in Ss
+            const int ii = i - dnv, jj = j - dnv;
+            v = ii <= jj ? Ss[(long long)ii * np + jj] : Ss[(long long)jj * np + ii];
         }
-        if (inv64 && ldw == ld64) inv64[t] = v;
-        if (inv32 && ldw == ld32) inv32[t] = (float)v;
-        if (back && i < n) K[(long long)i * n + j] = v;
+        K[t] = v;
     }
-    // FP32 copy when its padding differs from the FP64 one
-    if (inv64 && inv32 && ld32 != ld64) {
-        __syncthreads();
+    __syncthreads();
+    for (long long t = tid; t < (long long)dnv * dnv; t += nt) {   // mirror the velocity block
+        const int i = (int)(t / dnv), j = (int)(t - (long long)i * dnv);
+        if (j < i) K[(long long)i * n + j] = K[(long long)j * n + i];
+    }
+    __syncthreads();
+    // column-major padded copies; the inverse is symmetric, so column j is row j
+    const int ld64 = (n + 1) & ~1, ld32 = (n + 3) & ~3;
+    if (inv64)
+        for (long long t = tid; t < (long long)ld64 * n; t += nt) {
+            const int j = (int)(t / ld64), i = (int)(t - (long long)j * ld64);
+            inv64[t] = i < n ? K[(long long)j * n + i] : 0.0;
+        }
+    if (inv32)
         for (long long t = tid; t < (long long)ld32 * n; t += nt) {
             const int j = (int)(t / ld32), i = (int)(t - (long long)j * ld32);
-            inv32[t] = i < n ? (float)inv64[(long long)j * ld64 + i] : 0.0f;
+            inv32[t] = i < n ? (float)K[(long long)j * n + i] : 0.0f;
         }
-    }
+    (void)back;
 }
 
 __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff,

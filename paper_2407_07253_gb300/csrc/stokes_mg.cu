@@ -190,6 +190,13 @@ struct DevLevel {
     int* asm_status = nullptr;
 };
 
+// Scratch of one Arnoldi run (one per relaxed level, so that levels can
+// run concurrently on their own streams)
+struct KrylovWS {
+    double *V = nullptr, *h = nullptr, *y = nullptr, *hn = nullptr, *partial = nullptr, *v0 = nullptr;
+    unsigned int* ticket = nullptr;
+};
+
 struct PendingPatches {
     int level = 0;
     double* work = nullptr;
@@ -253,6 +260,8 @@ struct stokes_mg {
     double* c_colk = nullptr;
     int* c_status = nullptr;
     cudaStream_t s_up = nullptr, s_coarse = nullptr;
+    std::vector<KrylovWS> kws;           // per relaxed level (level 0 aliases the FGMRES buffers)
+    std::vector<cudaStream_t> s_lvl;     // per level (level 0 runs on the caller's stream)
     std::vector<double*> mesh_X;         // device vertex coordinates per mesh
     std::vector<int*> mesh_C;            // device cells per mesh
     std::vector<void*> allocs;
@@ -603,9 +612,11 @@ void capture_graph(stokes_mg* h, int prec, cudaStream_t s) {
 
 // ---- reductions for FGMRES / Arnoldi (FP64, deterministic two-stage)
 void mdot(stokes_mg* h, int n, int m, const double* V, long long ldv, const double* w, double* out, double* acc,
-          bool sqrt_out, cudaStream_t s) {
+          bool sqrt_out, cudaStream_t s, const KrylovWS* ws = nullptr) {
+    double* partial = ws ? ws->partial : h->partial;
+    unsigned int* ticket = ws ? ws->ticket : h->ticket;
     launch(h, -1, s, [&] {
-        skern::mdot_fused<<<skern::MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, h->partial, h->ticket, out, acc,
+        skern::mdot_fused<<<skern::MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc,
                                                             sqrt_out ? 1 : 0);
     });
 }
@@ -617,12 +628,13 @@ void maxpy_l(stokes_mg* h, int n, int m, const double* V, long long ldv, const d
 
 // orthogonalise w (length n) against V[0..m-1] by classical Gram-Schmidt
 // applied twice; h[0..m-1] receives the coefficients, hn[0] = ||w|| after.
-void cgs2(stokes_mg* h, int n, int m, const double* V, double* w, double* hcoef, double* h2, double* hn, cudaStream_t s) {
-    mdot(h, n, m, V, n, w, hcoef, nullptr, false, s);
+void cgs2(stokes_mg* h, int n, int m, const double* V, double* w, double* hcoef, double* h2, double* hn, cudaStream_t s,
+          const KrylovWS* ws = nullptr) {
+    mdot(h, n, m, V, n, w, hcoef, nullptr, false, s, ws);
     maxpy_l(h, n, m, V, n, hcoef, -1.0, w, s);
-    mdot(h, n, m, V, n, w, h2, hcoef, false, s);
+    mdot(h, n, m, V, n, w, h2, hcoef, false, s, ws);
     maxpy_l(h, n, m, V, n, h2, -1.0, w, s);
-    mdot(h, n, 1, w, n, w, hn, nullptr, true, s);
+    mdot(h, n, 1, w, n, w, hn, nullptr, true, s, ws);
 }
 
 double d2h_scalar(stokes_mg* h, const double* d, cudaStream_t s) {
@@ -639,21 +651,25 @@ double d2h_scalar(stokes_mg* h, const double* d, cudaStream_t s) {
 // round trip) and queue the copy of the (m+1) x m Hessenberg matrix into
 // H_host (pinned); returns m.  Uses the FGMRES basis V as workspace, so
 // launches on one stream run one level after another.
-int arnoldi_launch(stokes_mg* h, int li, const double* v0, int steps, double* Hs, double* H_host, cudaStream_t s) {
+int arnoldi_launch(stokes_mg* h, int li, const double* v0, int steps, double* Hs, double* H_host, cudaStream_t s,
+                   const KrylovWS* ws = nullptr) {
     DevLevel& l = h->L[li];
     const int n = l.n;
     const int m = std::min(steps, std::min(n, skern::HESS_MAX - 1));
-    double* V = h->V;
+    double* V = ws ? ws->V : h->V;
+    double* hh = ws ? ws->h : h->h;
+    double* yy = ws ? ws->y : h->y;
+    double* hn = ws ? ws->hn : h->hn;
     launch(h, -1, s, [&] { skern::fill_vec<double><<<1, 256, 0, s>>>((long long)(m + 1) * m, 0.0, Hs); });
-    mdot(h, n, 1, v0, n, v0, h->hn, nullptr, true, s);
-    launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, v0, h->hn, V); });
+    mdot(h, n, 1, v0, n, v0, hn, nullptr, true, s, ws);
+    launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, v0, hn, V); });
     for (int j = 0; j < m; ++j) {
         double* w = V + (long long)(j + 1) * n;
         spmv<double>(h, PK_SPMV, l.K, skern::SPMV_SET, V + (long long)j * n, l.t64, nullptr, s);
         asm_apply<double>(h, l, l.t64, w, 1.0, 0.0, s);
-        cgs2(h, n, j + 1, V, w, h->h, h->y, h->hn, s);
-        launch(h, -1, s, [&] { skern::arnoldi_store<<<1, 1, 0, s>>>(j, m, Hs, h->h, h->hn); });
-        launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, h->hn, w); });
+        cgs2(h, n, j + 1, V, w, hh, yy, hn, s, ws);
+        launch(h, -1, s, [&] { skern::arnoldi_store<<<1, 1, 0, s>>>(j, m, Hs, hh, hn); });
+        launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, hn, w); });
     }
     CK(cudaMemcpyAsync(H_host, Hs, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToHost, s));
     return m;
@@ -1003,7 +1019,7 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
     pp.level = li;
     pp.work = palloc<double>(h->device, l.nsq, s);
     pp.status = palloc<int>(h->device, l.npatch, s);
-    pp.stream = s;
+    pp.stream = s;   // freed on the same stream after finish_patches synchronised it
     h->pending.push_back(pp);
     CK(cudaMemsetAsync(pp.status, 0, sizeof(int) * l.npatch, s));
     gather_and_invert(h, li, pp.work, true, pp.status, s);
@@ -1020,6 +1036,8 @@ void free_pending(stokes_mg* h) {
 // Wait for every launched patch inversion and report the first zero pivot.
 void finish_patches(stokes_mg* h, cudaStream_t s) {
     CK(cudaStreamSynchronize(s));
+    for (cudaStream_t x : h->s_lvl)
+        if (x) CK(cudaStreamSynchronize(x));
     for (auto& pp : h->pending) {
         DevLevel& l = h->L[pp.level];
         std::vector<int> hs(l.npatch);
@@ -1114,6 +1132,21 @@ void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
     h->pint = hupload(h, F.pint, s);
     h->pint_sum = 0;
     for (double v : F.pint) h->pint_sum += v;
+}
+
+// Arnoldi scratch of relaxed level li >= 1 (its own stream and buffers)
+void alloc_level_krylov(stokes_mg* h, int li, cudaStream_t s) {
+    const int n = h->L[li].n;
+    if ((int)h->kws.size() < (int)h->L.size()) h->kws.resize(h->L.size());
+    KrylovWS& w = h->kws[li];
+    w.V = halloc<double>(h, (size_t)skern::HESS_MAX * n);
+    w.v0 = halloc<double>(h, n);
+    w.h = halloc<double>(h, skern::HESS_MAX + 1);
+    w.y = halloc<double>(h, skern::HESS_MAX + 1);
+    w.hn = halloc<double>(h, 2);
+    w.partial = halloc<double>(h, (size_t)skern::MDOT_BLOCKS * 32);
+    w.ticket = halloc<unsigned int>(h, 1);
+    CK(cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s));
 }
 
 // FGMRES / Arnoldi buffers sized by the finest level
@@ -1328,12 +1361,20 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                 stokes_mg* hp = h.get();
                 const int nlv = (int)hp->H.levels.size();
                 if ((int)hp->L.size() != nlv) hp->L.assign(nlv, DevLevel());
-                // uploads on this thread (parallel copy into pinned staging)
-                cudaStream_t target = li + 1 < nlv ? s : hp->s_coarse;
+                // uploads on this thread; each relaxed level then computes on
+                // its own stream (level 0 on the caller's), the coarse level on s_coarse
+                if ((int)hp->s_lvl.size() != nlv) hp->s_lvl.assign(nlv, nullptr);
+                if (li > 0 && li + 1 < nlv) {
+                    int plo = 0, phi = 0;
+                    CK(cudaDeviceGetStreamPriorityRange(&plo, &phi));
+                    CK(cudaStreamCreateWithPriority(&hp->s_lvl[li], cudaStreamNonBlocking, plo));
+                }
+                cudaStream_t target = li + 1 < nlv ? (li == 0 ? s : hp->s_lvl[li]) : hp->s_coarse;
                 if (li + 1 < nlv) {
                     upload_level(hp, li, want32, hp->s_up);
                     const double tk = host_ms();
                     if (li == 0) alloc_krylov(hp, hp->s_up);
+                    else alloc_level_krylov(hp, li, hp->s_up);
                     trace("krylov buffers", li, tk);
                 } else {
                     upload_level(hp, li, want32, hp->s_up);
@@ -1347,20 +1388,23 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                 t_cb_upload += host_ms() - tu;
                 trace("level callback total", li, tu);
                 // kernel launches on the launcher thread
-                launcher->submit([hp, li, nlv, s, &o, &t_launch] {
+                launcher->submit([hp, li, nlv, s, target, &o, &t_launch] {
                     const double tl = host_ms();
                     CK(cudaSetDevice(hp->device));
                     if (li + 1 < nlv) {
-                        assemble_on_device(hp, li, s);
-                        launch_patches(hp, li, s);
+                        const cudaStream_t sl = target;
+                        assemble_on_device(hp, li, sl);
+                        launch_patches(hp, li, sl);
                         // lambda_max estimate right behind the inversion (same stream)
                         if (!(li < 16 && o.lmax_override[li] > 0)) {
                             const int n = hp->L[li].n;
-                            splitmix_uniform<<<grid_for(n), 256, 0, s>>>(n, o.eig_seed, (unsigned long long)li, hp->v0buf);
+                            const KrylovWS* ws = li == 0 ? nullptr : &hp->kws[li];
+                            double* v0 = li == 0 ? hp->v0buf : ws->v0;
+                            splitmix_uniform<<<grid_for(n), 256, 0, sl>>>(n, o.eig_seed, (unsigned long long)li, v0);
                             CK(cudaGetLastError());
                             const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
-                            hp->arn_m[li] = arnoldi_launch(hp, li, hp->v0buf, o.eig_steps, hp->Hlev + li * hsz,
-                                                           hp->pinned_H + (li + 1) * hsz, s);
+                            hp->arn_m[li] = arnoldi_launch(hp, li, v0, o.eig_steps, hp->Hlev + li * hsz,
+                                                           hp->pinned_H + (li + 1) * hsz, sl, ws);
                         }
                     } else {
                         launch_coarse(hp, hp->s_coarse);
@@ -1783,6 +1827,8 @@ void stokes_mg_destroy(stokes_mg_t h) {
     free_pending(h);
     free_coarse_ws(h);
     if (h->s_up) cudaStreamDestroy(h->s_up);
+    for (cudaStream_t x : h->s_lvl)
+        if (x) cudaStreamDestroy(x);
     if (h->s_coarse) cudaStreamDestroy(h->s_coarse);
     for (void* p : h->allocs) cudaFree(p);
     if (!h->pool_allocs.empty()) {
