@@ -269,9 +269,10 @@ def main():
     sizes = []
     flops_gj = 0.0
     # algorithmic flops of the saddle block inverse per patch (n_v velocity
-    # nodes per component, n_p pressures, d components):
-    #   2 (n_v^3 + d n_v^2 n_p + 2 d n_v n_p^2 + n_p^3 + d^2 n_v^2 n_p)
-    # (L^-1, W = L^-1 B^T, S = B W and X = W S^-1, S^-1, velocity block)
+    # nodes per component, n_p pressures, d components), symmetric version:
+    #   n_v^3 (sweep of L, upper triangle) + 2 d n_v^2 n_p (W = L^-1 B^T)
+    #   + d n_v n_p^2 (S = B W, upper) + n_p^3 (sweep of S) + 2 d n_v n_p^2
+    #   (X = W S^-1) + d^2 n_v^2 n_p (velocity block, upper triangle)
     probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
                        hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
     flops_levels = []
@@ -284,7 +285,8 @@ def main():
             c = cd[off[pi]:off[pi + 1]]
             nv = float((c == 0).sum())
             npr = float((c == d).sum())
-            f += 2.0 * (nv ** 3 + d * nv * nv * npr + 2 * d * nv * npr * npr + npr ** 3 + d * d * nv * nv * npr)
+            f += (nv ** 3 + 2 * d * nv * nv * npr + d * nv * npr * npr + npr ** 3 + 2 * d * nv * npr * npr
+                  + d * d * nv * nv * npr)
         flops_levels.append(f)
         sizes.append(np.diff(off))
     flops_gj = sum(flops_levels)

@@ -1361,15 +1361,11 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                 stokes_mg* hp = h.get();
                 const int nlv = (int)hp->H.levels.size();
                 if ((int)hp->L.size() != nlv) hp->L.assign(nlv, DevLevel());
-                // uploads on this thread; each relaxed level then computes on
-                // its own stream (level 0 on the caller's), the coarse level on s_coarse
-                if ((int)hp->s_lvl.size() != nlv) hp->s_lvl.assign(nlv, nullptr);
-                if (li > 0 && li + 1 < nlv) {
-                    int plo = 0, phi = 0;
-                    CK(cudaDeviceGetStreamPriorityRange(&plo, &phi));
-                    CK(cudaStreamCreateWithPriority(&hp->s_lvl[li], cudaStreamNonBlocking, plo));
-                }
-                cudaStream_t target = li + 1 < nlv ? (li == 0 ? s : hp->s_lvl[li]) : hp->s_coarse;
+                // uploads on this thread; the relaxed levels then compute on the
+                // caller's stream, the coarse level on s_coarse
+                // (all relaxed levels share one stream: separate streams let the
+                // small levels' launches crowd the latency-bound coarse steps)
+                cudaStream_t target = li + 1 < nlv ? s : hp->s_coarse;
                 if (li + 1 < nlv) {
                     upload_level(hp, li, want32, hp->s_up);
                     const double tk = host_ms();
