@@ -293,24 +293,27 @@ __global__ void __launch_bounds__(512) gj_inverse_global(int npatch, const int* 
 // dimension lda), working on the upper triangle only: sweeping pivot k maps
 //   a_kk -> -1/a_kk,  a_ik -> a_ik/a_kk,  a_ij -> a_ij - a_ik a_kj / a_kk,
 // and sweeping every pivot in order leaves -A^{-1} (upper triangle).  An SPD
-// matrix needs no pivoting.  status <- 1 + step of the first non-positive pivot.
+// matrix needs no pivoting.  Rows go to warps, columns to lanes.
+// status <- 1 + step of the first non-positive pivot.
 __device__ void sweep_spd(double* A, int n, int lda, double* colk, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     for (int k = 0; k < n; ++k) {
         const double piv = A[(long long)k * lda + k];
         if (tid == 0 && !(piv > 0.0) && *status == 0) *status = k + 1;
         const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
         for (int i = tid; i < n; i += nt) colk[i] = i <= k ? A[(long long)i * lda + k] : A[(long long)k * lda + i];
         __syncthreads();
-        for (int t = tid; t < n * n; t += nt) {
-            const int i = t / n, j = t - (t / n) * n;
-            if (j < i) continue;
-            double v;
-            if (i == k && j == k) v = -inv;
-            else if (i == k) v = colk[j] * inv;
-            else if (j == k) v = colk[i] * inv;
-            else v = A[(long long)i * lda + j] - colk[i] * colk[j] * inv;
-            A[(long long)i * lda + j] = v;
+        for (int i = warp; i < n; i += nw) {
+            const double ci = colk[i] * inv;
+            double* row = A + (long long)i * lda;
+            for (int j = i + lane; j < n; j += 32) {
+                double v;
+                if (i == k) v = (j == k) ? -inv : colk[j] * inv;
+                else if (j == k) v = ci;
+                else v = row[j] - ci * colk[j];
+                row[j] = v;
+            }
         }
         __syncthreads();
     }
@@ -326,100 +329,90 @@ __device__ __forceinline__ double neg_upper(const double* A, int lda, int i, int
 // (the d velocity components share the SPD block L on the same nodes):
 //   Li = L^{-1}, W_c = Li B_c^T, S = sum_c B_c W_c, Si = S^{-1}, X_c = W_c Si,
 //   K_i^{-1} = [blockdiag(Li) - X W^T, X; X^T, -Si].
-// Li and Si come from the symmetric sweep; the symmetric velocity block is
-// computed on its upper triangle and mirrored.  K (row-major n x n) is read
-// from the workspace and overwritten by the (exactly symmetric) inverse,
-// which is then written column-major (padded) in FP64 / FP32.
+// Li and Si come from the symmetric sweep; the (symmetric) inverse is
+// computed on its upper triangle and every value written to both of its
+// positions: column-major padded FP64 / FP32 and, if back, row-major into K.
 __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, double* inv64, float* inv32,
                             int back, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int np = n - d * nv, npp = np | 1, dnv = d * nv;
     double* Ls = scratch;
     double* Bt = Ls + (long long)nv * nv;          // [c][a][q], becomes X
     double* Wm = Bt + (long long)d * nv * npp;     // [c][a][q]
     double* Ss = Wm + (long long)d * nv * npp;     // [q][r]
     double* colk = Ss + (long long)np * np;
-    for (int t = tid; t < nv * nv; t += nt) {
-        const int a = t / nv, b = t - (t / nv) * nv;
-        Ls[t] = K[(long long)a * n + b];
-    }
-    for (int t = tid; t < dnv * np; t += nt) {
-        const int r = t / np, q = t - (t / np) * np;       // r = c*nv + a
-        Bt[(long long)r * npp + q] = K[(long long)r * n + dnv + q];
-    }
+    for (int i = warp; i < nv; i += nw)
+        for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
+    for (int r = warp; r < dnv; r += nw)
+        for (int q = lane; q < np; q += 32) Bt[(long long)r * npp + q] = K[(long long)r * n + dnv + q];
     __syncthreads();
     sweep_spd(Ls, nv, nv, colk, status);
     // W_c = Li B_c^T
-    for (int t = tid; t < dnv * np; t += nt) {
-        const int r = t / np, q = t - (t / np) * np;
+    for (int r = warp; r < dnv; r += nw) {
         const int c = r / nv, a = r - c * nv;
-        const double* bt = Bt + (long long)c * nv * npp + q;
-        double s = 0.0;
-        for (int b = 0; b < nv; ++b) s += neg_upper(Ls, nv, a, b) * bt[(long long)b * npp];
-        Wm[(long long)r * npp + q] = s;
+        for (int q = lane; q < np; q += 32) {
+            const double* bt = Bt + (long long)c * nv * npp + q;
+            double s = 0.0;
+            for (int b = 0; b < nv; ++b) s += neg_upper(Ls, nv, a, b) * bt[(long long)b * npp];
+            Wm[(long long)r * npp + q] = s;
+        }
     }
     __syncthreads();
     // S = sum_c B_c W_c (symmetric: upper triangle)
-    for (int t = tid; t < np * np; t += nt) {
-        const int q = t / np, r = t - (t / np) * np;
-        if (r < q) continue;
-        double s = 0.0;
-        for (int a = 0; a < dnv; ++a) s += Bt[(long long)a * npp + q] * Wm[(long long)a * npp + r];
-        Ss[t] = s;
-    }
+    for (int q = warp; q < np; q += nw)
+        for (int r = q + lane; r < np; r += 32) {
+            double s = 0.0;
+            for (int a = 0; a < dnv; ++a) s += Bt[(long long)a * npp + q] * Wm[(long long)a * npp + r];
+            Ss[q * np + r] = s;
+        }
     __syncthreads();
     sweep_spd(Ss, np, np, colk, status);
     // X_c = W_c Si (overwrites Bt)
-    for (int t = tid; t < dnv * np; t += nt) {
-        const int r = t / np, q = t - (t / np) * np;
-        const double* w = Wm + (long long)r * npp;
-        double s = 0.0;
-        for (int x = 0; x < np; ++x) s += w[x] * neg_upper(Ss, np, x, q);
-        Bt[(long long)r * npp + q] = s;
-    }
-    __syncthreads();
-    // the inverse, row-major into K; velocity block on its upper triangle
-    for (long long t = tid; t < (long long)n * n; t += nt) {
-        const int i = (int)(t / n), j = (int)(t - (long long)i * n);
-        double v;
-        if (i < dnv && j < dnv) {
-            if (j < i) continue;
-            const int c = i / nv, a = i - c * nv, c2 = j / nv, b = j - c2 * nv;
-            const double* x = Bt + (long long)i * npp;
-            const double* w = Wm + (long long)j * npp;
+    for (int r = warp; r < dnv; r += nw)
+        for (int q = lane; q < np; q += 32) {
+            const double* w = Wm + (long long)r * npp;
             double s = 0.0;
-            for (int q = 0; q < np; ++q) s += x[q] * w[q];
-            v = (c == c2 ? neg_upper(Ls, nv, a, b) : 0.0) - s;
-        } else if (i < dnv) {
-            v = Bt[(long long)i * npp + (j - dnv)];
-        } else if (j < dnv) {
-            v = Bt[(long long)j * npp + (i - dnv)];
-        } else {
-            // the pressure block of K^-1 is -Si, which the sweep left in Ss
-            const int ii = i - dnv, jj = j - dnv;
-            v = ii <= jj ? Ss[(long long)ii * np + jj] : Ss[(long long)jj * np + ii];
+            for (int x = 0; x < np; ++x) s += w[x] * neg_upper(Ss, np, x, q);
+            Bt[(long long)r * npp + q] = s;
         }
-        K[t] = v;
-    }
     __syncthreads();
-    for (long long t = tid; t < (long long)dnv * dnv; t += nt) {   // mirror the velocity block
-        const int i = (int)(t / dnv), j = (int)(t - (long long)i * dnv);
-        if (j < i) K[(long long)i * n + j] = K[(long long)j * n + i];
-    }
-    __syncthreads();
-    // column-major padded copies; the inverse is symmetric, so column j is row j
     const int ld64 = (n + 1) & ~1, ld32 = (n + 3) & ~3;
-    if (inv64)
-        for (long long t = tid; t < (long long)ld64 * n; t += nt) {
-            const int j = (int)(t / ld64), i = (int)(t - (long long)j * ld64);
-            inv64[t] = i < n ? K[(long long)j * n + i] : 0.0;
+    auto put = [&](int i, int j, double v) {
+        if (inv64) { inv64[(long long)j * ld64 + i] = v; inv64[(long long)i * ld64 + j] = v; }
+        if (inv32) { inv32[(long long)j * ld32 + i] = (float)v; inv32[(long long)i * ld32 + j] = (float)v; }
+        if (back) { K[(long long)i * n + j] = v; K[(long long)j * n + i] = v; }
+    };
+    for (int i = warp; i < n; i += nw) {
+        if (i < dnv) {
+            const int c = i / nv, a = i - c * nv;
+            const double* x = Bt + (long long)i * npp;
+            for (int j = i + lane; j < n; j += 32) {
+                double v;
+                if (j < dnv) {
+                    const int c2 = j / nv, b = j - c2 * nv;
+                    const double* w = Wm + (long long)j * npp;
+                    double s = 0.0;
+                    for (int q = 0; q < np; ++q) s += x[q] * w[q];
+                    v = (c == c2 ? neg_upper(Ls, nv, a, b) : 0.0) - s;
+                } else {
+                    v = x[j - dnv];
+                }
+                put(i, j, v);
+            }
+        } else {
+            const int ii = i - dnv;
+            for (int j = i + lane; j < n; j += 32)
+                put(i, j, Ss[(long long)ii * np + (j - dnv)]);   // -Si, left in Ss by the sweep
         }
-    if (inv32)
-        for (long long t = tid; t < (long long)ld32 * n; t += nt) {
-            const int j = (int)(t / ld32), i = (int)(t - (long long)j * ld32);
-            inv32[t] = i < n ? (float)K[(long long)j * n + i] : 0.0f;
-        }
-    (void)back;
+    }
+    // zero the padding rows of the column-major copies
+    for (int j = tid; j < n; j += nt) {
+        if (inv64)
+            for (int i = n; i < ld64; ++i) inv64[(long long)j * ld64 + i] = 0.0;
+        if (inv32)
+            for (int i = n; i < ld32; ++i) inv32[(long long)j * ld32 + i] = 0.0f;
+    }
 }
 
 __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff,
