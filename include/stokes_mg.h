@@ -55,7 +55,8 @@ extern "C" {
 #define STOKES_HIER_EXPLICIT 2  /* opts.schedule[0..n_schedule-1] velocity degrees, first = k */
 #define STOKES_HIER_HMG      3  /* no p-coarsening: P_k on every mesh (the paper's hMG) */
 
-/* precision of the V-cycle (FGMRES, Arnoldi, patch LU and coarse LU are FP64 in both) */
+/* precision of the V-cycle and of the operator inside the lambda_max Arnoldi
+ * (FGMRES, the Arnoldi basis, patch LU and coarse LU are FP64 in both) */
 #define STOKES_FP64  0
 #define STOKES_MIXED 1   /* FP32 SpMV, transfers and patch apply with FP32 accumulation */
 
@@ -214,7 +215,10 @@ int stokes_mg_patch_matrices(stokes_mg_t h, int level, double* out, void* stream
 int stokes_mg_patch_inverses(stokes_mg_t h, int level, double* out, void* stream);
 
 /* a3: largest real Ritz value of `steps` Arnoldi steps on M_l^{-1} K_l from
- * the device start vector v0_dev [n_free(level)] (FP64). */
+ * the device start vector v0_dev [n_free(level)] (FP64).  The operator is
+ * applied in the handle's V-cycle precision (FP32 CSR values and stored
+ * inverses for STOKES_MIXED, the smoother the estimate serves); the Krylov
+ * basis, its CGS2 orthogonalisation and the Hessenberg matrix are FP64. */
 int stokes_mg_arnoldi_lmax(stokes_mg_t h, int level, const double* v0_dev, int steps,
                            double* lmax, void* stream);
 

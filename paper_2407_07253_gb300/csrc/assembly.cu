@@ -11,33 +11,42 @@ namespace {
 constexpr int WARPS = 4;               // warps per block, one node per warp
 constexpr unsigned FULL = 0xffffffffu;
 
-struct Geo {
-    double det;                        // |det J|
-    double Ji[9];                      // Jinv[a][c] = d xi_a / d x_c
-};
-
-__device__ Geo geometry(const AsmMesh& m, int e) {
+// one thread per cell: the factors described with CG_STRIDE
+__global__ void k_cell_geometry(AsmMesh m, double* cg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.nc) return;
     const int d = m.d;
     const int* v = m.C + (long long)e * (d + 1);
     double J[9];
     for (int c = 0; c < d; ++c)
         for (int a = 0; a < d; ++a) J[c * d + a] = m.X[(long long)v[a + 1] * d + c] - m.X[(long long)v[0] * d + c];
-    Geo g;
+    double adj[9], det;
     if (d == 2) {
-        const double det = J[0] * J[3] - J[1] * J[2];
-        g.det = fabs(det);
-        g.Ji[0] = J[3] / det;  g.Ji[1] = -J[1] / det;
-        g.Ji[2] = -J[2] / det; g.Ji[3] = J[0] / det;
+        det = J[0] * J[3] - J[1] * J[2];
+        adj[0] = J[3];  adj[1] = -J[1];
+        adj[2] = -J[2]; adj[3] = J[0];
     } else {
         const double a = J[0], b = J[1], c = J[2], dd = J[3], e2 = J[4], f = J[5], gg = J[6], h = J[7], i = J[8];
         const double A = e2 * i - f * h, B = -(dd * i - f * gg), Cc = dd * h - e2 * gg;
-        const double det = a * A + b * B + c * Cc;
-        g.det = fabs(det);
-        const double inv[9] = {A, -(b * i - c * h), b * f - c * e2, B, a * i - c * gg, -(a * f - c * dd),
-                               Cc, -(a * h - b * gg), a * e2 - b * dd};
-        for (int t = 0; t < 9; ++t) g.Ji[t] = inv[t] / det;
+        det = a * A + b * B + c * Cc;
+        const double t[9] = {A, -(b * i - c * h), b * f - c * e2, B, a * i - c * gg, -(a * f - c * dd),
+                             Cc, -(a * h - b * gg), a * e2 - b * dd};
+        for (int k = 0; k < 9; ++k) adj[k] = t[k];
     }
-    return g;
+    const double rdet = 1.0 / det, adet = fabs(det);
+    double Ji[9];
+    for (int k = 0; k < d * d; ++k) Ji[k] = adj[k] * rdet;   // Jinv[a][c] = d xi_a / d x_c
+    double* o = cg + (long long)e * CG_STRIDE;
+    const double wgt = adet * (m.nu ? m.nu[e] : 1.0);
+    o[0] = adet;
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double s = 0;
+            for (int c = 0; c < d; ++c) s += Ji[a * d + c] * Ji[b * d + c];
+            o[1 + a * d + b] = wgt * s;
+        }
+    for (int a = 0; a < d; ++a)
+        for (int c = 0; c < d; ++c) o[1 + d * d + a * d + c] = -adet * Ji[a * d + c];
 }
 
 // Warp-cooperative insertion of this lane's candidate into the list of
@@ -160,30 +169,23 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
         const long long r00 = rp[item];
         for (int x = m.voff[node]; x < m.voff[node + 1]; ++x) {
             const int e = m.vadj[x] / nb, la = m.vadj[x] % nb;
-            const Geo g = geometry(m, e);
-            const double wgt = g.det * (m.nu ? m.nu[e] : 1.0);
-            double G[9];
-            for (int a = 0; a < d; ++a)
-                for (int b = 0; b < d; ++b) {
-                    double s = 0;
-                    for (int c = 0; c < d; ++c) s += g.Ji[a * d + c] * g.Ji[b * d + c];
-                    G[a * d + b] = s;
-                }
+            const double* G = m.cg + (long long)e * CG_STRIDE + 1;      // weighted stiffness factors
+            const double* D = G + d * d;                                // divergence factors
             for (int b = lane; b < nb; b += 32) {
                 const int j = m.vcell[(long long)e * nb + b];
                 if (m.vfree[j] < 0) continue;
                 double s = 0;
                 for (int a = 0; a < d; ++a)
                     for (int bb = 0; bb < d; ++bb) s += G[a * d + bb] * m.S[(((long long)a * d + bb) * nb + la) * nb + b];
-                val[r00 + find(L.lv, L.cv, j)] += wgt * s;
+                val[r00 + find(L.lv, L.cv, j)] += s;
             }
             for (int p = lane; p < nq; p += 32) {
                 const int q = m.qcell[(long long)e * nq + p];
                 const int pos = L.cv + find(L.lq, L.cq, q);
                 for (int c = 0; c < d; ++c) {
                     double s = 0;
-                    for (int a = 0; a < d; ++a) s += g.Ji[a * d + c] * m.Cq[((long long)a * nq + p) * nb + la];
-                    val[rp[c * m.nVf + item] + pos] += -g.det * s;
+                    for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + p) * nb + la];
+                    val[rp[c * m.nVf + item] + pos] += s;
                 }
             }
             __syncwarp();
@@ -208,15 +210,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
         __syncwarp();
         for (int x = m.qoff[q]; x < m.qoff[q + 1]; ++x) {
             const int e = m.qadj[x] / nq, lp = m.qadj[x] % nq;
-            const Geo g = geometry(m, e);
+            const double* D = m.cg + (long long)e * CG_STRIDE + 1 + d * d;
             for (int b = lane; b < nb; b += 32) {
                 const int j = m.vcell[(long long)e * nb + b];
                 if (m.vfree[j] < 0) continue;
                 const int pos = find(L.lv, L.cv, j);
                 for (int c = 0; c < d; ++c) {
                     double s = 0;
-                    for (int a = 0; a < d; ++a) s += g.Ji[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + b];
-                    val[r0 + (long long)c * L.cv + pos] += -g.det * s;
+                    for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + b];
+                    val[r0 + (long long)c * L.cv + pos] += s;
                 }
             }
             __syncwarp();
@@ -278,27 +280,22 @@ __global__ void k_load(AsmMesh m, const double* f, const double* gD, double inv_
         double F = 0, lift = 0;
         for (int x = m.voff[node]; x < m.voff[node + 1]; ++x) {
             const int e = m.vadj[x] / nb, la = m.vadj[x] % nb;
-            const Geo g = geometry(m, e);
+            const double* cge = m.cg + (long long)e * CG_STRIDE;
+            double Fe = 0;
             for (int bb = 0; bb < nb; ++bb) {
                 const int j = m.vcell[(long long)e * nb + bb];
-                F += g.det * m.M[(long long)la * nb + bb] * f[(long long)c * m.nV + j];
+                Fe += m.M[(long long)la * nb + bb] * f[(long long)c * m.nV + j];
             }
+            F += cge[0] * Fe;
             if (gD) {
-                const double wgt = g.det * (m.nu ? m.nu[e] : 1.0);
-                double G[9];
-                for (int a = 0; a < d; ++a)
-                    for (int a2 = 0; a2 < d; ++a2) {
-                        double s = 0;
-                        for (int k = 0; k < d; ++k) s += g.Ji[a * d + k] * g.Ji[a2 * d + k];
-                        G[a * d + a2] = s;
-                    }
+                const double* G = cge + 1;
                 for (int bb = 0; bb < nb; ++bb) {
                     const int j = m.vcell[(long long)e * nb + bb];
                     if (m.vfree[j] >= 0) continue;
                     double s = 0;
                     for (int a = 0; a < d; ++a)
                         for (int a2 = 0; a2 < d; ++a2) s += G[a * d + a2] * m.S[(((long long)a * d + a2) * nb + la) * nb + bb];
-                    lift += wgt * s * gD[(long long)c * m.nV + j];
+                    lift += s * gD[(long long)c * m.nV + j];
                 }
             }
         }
@@ -309,14 +306,14 @@ __global__ void k_load(AsmMesh m, const double* f, const double* gD, double inv_
         if (gD)
             for (int x = m.qoff[q]; x < m.qoff[q + 1]; ++x) {
                 const int e = m.qadj[x] / nq, lp = m.qadj[x] % nq;
-                const Geo g = geometry(m, e);
+                const double* D = m.cg + (long long)e * CG_STRIDE + 1 + d * d;
                 for (int bb = 0; bb < nb; ++bb) {
                     const int j = m.vcell[(long long)e * nb + bb];
                     if (m.vfree[j] >= 0) continue;
                     for (int c = 0; c < d; ++c) {
                         double s = 0;
-                        for (int a = 0; a < d; ++a) s += g.Ji[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + bb];
-                        lift += -g.det * s * gD[(long long)c * m.nV + j];
+                        for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + bb];
+                        lift += s * gD[(long long)c * m.nV + j];
                     }
                 }
             }
@@ -325,6 +322,10 @@ __global__ void k_load(AsmMesh m, const double* f, const double* gD, double inv_
 }
 
 }  // namespace
+
+void cell_geometry(const AsmMesh& m, double* cg, cudaStream_t s) {
+    k_cell_geometry<<<(m.nc + 127) / 128, 128, 0, s>>>(m, cg);
+}
 
 void row_lengths(const AsmMesh& m, int* len, int* status, cudaStream_t s) {
     const int items = m.nVf + m.nQ;

@@ -29,7 +29,15 @@ struct AsmMesh {
     const double* S;                   // [d][d][nb][nb] reference stiffness tensors
     const double* Cq;                  // [d][nq][nb] int psi_p d(phi_j)/dxi_a
     const double* M;                   // [nb][nb] reference mass matrix
+    const double* cg;                  // [nc][CG_STRIDE] per-cell factors (cell_geometry)
 };
+
+// Per-cell factors of the affine map x = x_0 + J xi, computed once per level:
+//   cg[0]                 |det J|
+//   cg[1 + a d + b]       nu_e |det J| sum_c Jinv[a][c] Jinv[b][c]   (stiffness)
+//   cg[1 + d d + a d + c] -|det J| Jinv[a][c]                        (divergence)
+constexpr int CG_STRIDE = 20;
+void cell_geometry(const AsmMesh& m, double* cg, cudaStream_t s);
 
 constexpr int MAX_ROW = 1024;          // neighbours of one node (per kind)
 

@@ -1249,7 +1249,11 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         if (it == refs.end()) { refs[key].init(dd, kk); it = refs.find(key); }
         return it->second;
     };
-    for (size_t l = 0; l < ls.size(); ++l) {
+    std::vector<size_t> order;
+    if (spec.coarsest_first) order.push_back(ls.size() - 1);
+    for (size_t l = 0; l < ls.size(); ++l)
+        if (!(spec.coarsest_first && l + 1 == ls.size())) order.push_back(l);
+    for (size_t l : order) {
         Level& L = H.levels[l];
         L.d = d;
         L.family = ls[l].family;

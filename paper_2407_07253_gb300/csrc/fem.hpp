@@ -116,6 +116,11 @@ struct HierarchySpec {
     int n_refine = 0;
     bool barycentric = false;
     bool device_assembly = false;             // leave K of all but the coarsest level to the device
+    // order of construction (and of the per-level callbacks): false = finest
+    // to coarsest; true = the coarsest level first (its device factorisation
+    // is a long chain of small steps that then runs while the host builds the
+    // other levels), then finest to coarsest
+    bool coarsest_first = false;
 };
 
 struct Hierarchy {
@@ -128,8 +133,9 @@ struct Hierarchy {
 
 // Build the whole host hierarchy; throws std::runtime_error on invalid input.
 // on_level(l), if given, runs as soon as level l's spaces, operator and
-// patches exist (before coarser levels and the transfers are built), so the
-// caller can start device work on it while the host continues.
+// patches exist (levels in the order that spec.coarsest_first selects;
+// the transfers are built after every level), so the caller can start device
+// work on it while the host continues.
 void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell,
                      Hierarchy& H, const std::function<void(int)>& on_level = {});
 

@@ -57,55 +57,181 @@ __global__ void mdot_final(int nblocks, int m, const double* __restrict__ partia
     out[i] = (sqrt_out && i == 0) ? sqrt(s) : s;
 }
 
-// Single-launch multi-dot: every block writes its partial sums, the last
-// block to finish (atomic ticket) adds them in a fixed order, so the result
-// is bitwise reproducible.  Launched with MDOT_BLOCKS blocks of 512 threads.
-__global__ void __launch_bounds__(512) mdot_fused(int n, int m, const double* __restrict__ V, long long ldv,
-                                                  const double* __restrict__ w, double* __restrict__ partial,
-                                                  unsigned int* __restrict__ ticket, double* __restrict__ out,
-                                                  double* __restrict__ acc, int sqrt_out) {
-    double a[MDOT_MAX];
-#pragma unroll
-    for (int i = 0; i < MDOT_MAX; ++i) a[i] = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const double wk = w[k];
-#pragma unroll
-        for (int i = 0; i < MDOT_MAX; ++i)
-            if (i < m) a[i] += V[(long long)i * ldv + k] * wk;
-    }
+// Fused multi-dots: every block writes its partial sums, the last block to
+// finish (atomic ticket) adds them in a fixed order, so results are bitwise
+// reproducible.  Launched with MDOT_BLOCKS blocks of 512 threads.
+
+// block partial sums of a[0..m) (and, if with_extra, of `extra` as column
+// m) into partial[blockIdx.x][0..m + with_extra)
+template <int MM>
+__device__ __forceinline__ void mdot_block_partials(int m, const double (&a)[MM], double extra, bool with_extra,
+                                                    double* partial) {
     __shared__ double red[16][MDOT_MAX];
-    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int i = 0; i < MDOT_MAX; ++i) {
+    for (int i = 0; i < MM; ++i) {
         if (i >= m) break;
         double v = a[i];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][i] = v;
     }
+    if (with_extra) {
+        double v = extra;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][m] = v;
+    }
     __syncthreads();
-    if (threadIdx.x < m) {
+    const int mc = m + (with_extra ? 1 : 0);
+    if (threadIdx.x < mc) {
         double s = 0;
         for (int wv = 0; wv < nw; ++wv) s += red[wv][threadIdx.x];
-        partial[(long long)blockIdx.x * m + threadIdx.x] = s;
+        partial[(long long)blockIdx.x * mc + threadIdx.x] = s;
     }
+}
+
+// true in the last block to arrive (which then resets the ticket)
+__device__ __forceinline__ bool mdot_last_block(unsigned int* ticket) {
+    __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // 16 threads per output, fixed strided assignment, fixed shuffle tree
+    if (last) __threadfence();
+    return last;
+}
+
+// last block: out[i] = sum_b partial[b][i] (i < mcols, row stride mcols)
+// over the grid's blocks in a fixed order (16 threads per output, strided,
+// then a fixed shuffle tree), with acc[i] += out[i] for i < macc; the
+// partials are read from L2 (ld.global.cg) with all loads issued together
+__device__ __forceinline__ void mdot_reduce_partials(int mcols, int macc, const double* partial, double* out,
+                                                     double* acc, int sqrt_out, unsigned int* ticket) {
     const int i = threadIdx.x >> 4, sub = threadIdx.x & 15;
     double s = 0;
-    if (i < m)
-        for (int b = sub; b < (int)gridDim.x; b += 16) s += ((volatile double*)partial)[(long long)b * m + i];
+    if (i < mcols) {
+        double t[(MDOT_BLOCKS + 15) / 16];
+#pragma unroll
+        for (int q = 0; q < (MDOT_BLOCKS + 15) / 16; ++q) {
+            const int b = sub + 16 * q;
+            t[q] = b < (int)gridDim.x ? __ldcg(partial + (long long)b * mcols + i) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < (MDOT_BLOCKS + 15) / 16; ++q) s += t[q];
+    }
     for (int o = 8; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 16);
-    if (i < m && sub == 0) {
-        if (acc) acc[i] += s;
+    if (i < mcols && sub == 0) {
+        if (acc && i < macc) acc[i] += s;
         out[i] = (sqrt_out && i == 0) ? sqrt(s) : s;
     }
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// The accumulators are unrolled to MM (>= m): FP64 FMAs are scarce on this
+// GPU, so the host picks the smallest MM in {4, 8, 16, 32} that holds m.
+template <int MM>
+__global__ void __launch_bounds__(512) mdot_fused_t(int n, int m, const double* __restrict__ V, long long ldv,
+                                                    const double* __restrict__ w, double* __restrict__ partial,
+                                                    unsigned int* __restrict__ ticket, double* __restrict__ out,
+                                                    double* __restrict__ acc, int sqrt_out) {
+    double a[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) a[i] = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double wk = w[k];
+#pragma unroll
+        for (int i = 0; i < MM; ++i)
+            if (i < m) a[i] = fma(V[(long long)i * ldv + k], wk, a[i]);
+    }
+    mdot_block_partials(m, a, 0.0, false, partial);
+    if (!mdot_last_block(ticket)) return;
+    mdot_reduce_partials(m, acc ? m : 0, partial, out, acc, sqrt_out, ticket);
+}
+
+void mdot_fused(int n, int m, const double* V, long long ldv, const double* w, double* partial, unsigned int* ticket,
+                double* out, double* acc, int sqrt_out, cudaStream_t s) {
+    if (m <= 4) mdot_fused_t<4><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    else if (m <= 8) mdot_fused_t<8><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    else if (m <= 16) mdot_fused_t<16><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    else mdot_fused_t<32><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+}
+
+// Second classical Gram-Schmidt pass fused with the first pass's update:
+//   w <- w - V h  (h = the first pass's coefficients),
+//   out[0..m) = V^T w,  out[m] = w^T w  (of the updated w),  acc[i] += out[i].
+// m <= MDOT_MAX - 1.
+template <int MM>
+__global__ void __launch_bounds__(512) maxpy_mdot_t(int n, int m, const double* __restrict__ V, long long ldv,
+                                                    const double* __restrict__ h, double* __restrict__ w,
+                                                    double* __restrict__ partial, unsigned int* __restrict__ ticket,
+                                                    double* __restrict__ out, double* __restrict__ acc) {
+    __shared__ double hs[MDOT_MAX];
+    if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    double a[MM], nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < MM; ++i) a[i] = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double wk = w[k];
+        if constexpr (MM <= 8) {
+            // few vectors: keep V[.][k] in registers between the two uses
+            double vk[MM];
+#pragma unroll
+            for (int i = 0; i < MM; ++i)
+                if (i < m) { vk[i] = V[(long long)i * ldv + k]; wk = fma(-hs[i], vk[i], wk); }
+            w[k] = wk;
+#pragma unroll
+            for (int i = 0; i < MM; ++i)
+                if (i < m) a[i] = fma(vk[i], wk, a[i]);
+        } else {
+            // many vectors: the second read hits L1
+#pragma unroll
+            for (int i = 0; i < MM; ++i)
+                if (i < m) wk = fma(-hs[i], V[(long long)i * ldv + k], wk);
+            w[k] = wk;
+#pragma unroll
+            for (int i = 0; i < MM; ++i)
+                if (i < m) a[i] = fma(V[(long long)i * ldv + k], wk, a[i]);
+        }
+        nrm = fma(wk, wk, nrm);
+    }
+    mdot_block_partials(m, a, nrm, true, partial);
+    if (!mdot_last_block(ticket)) return;
+    mdot_reduce_partials(m + 1, m, partial, out, acc, 0, ticket);
+}
+
+void maxpy_mdot(int n, int m, const double* V, long long ldv, const double* h, double* w, double* partial,
+                unsigned int* ticket, double* out, double* acc, cudaStream_t s) {
+    if (m <= 4) maxpy_mdot_t<4><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    else if (m <= 8) maxpy_mdot_t<8><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    else if (m <= 16) maxpy_mdot_t<16><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    else maxpy_mdot_t<31><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+}
+
+// Last update of classical Gram-Schmidt, normalised:
+//   w <- (w - V h) / nu,  nu = sqrt(max(nrm2 - sum_i h_i^2, 0)),  *hn = nu,
+// where nrm2 = ||w||^2 before the update (Pythagoras: the second pass's h is
+// O(eps) relative to w, so the difference loses no accuracy).
+__global__ void __launch_bounds__(256) maxpy_normalise(int n, int m, const double* __restrict__ V, long long ldv,
+                                                       const double* __restrict__ h, const double* __restrict__ nrm2,
+                                                       double* __restrict__ w, double* __restrict__ hn) {
+    __shared__ double hs[MDOT_MAX];
+    __shared__ double sinv;
+    if (threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double q = *nrm2;
+        for (int i = 0; i < m; ++i) q -= hs[i] * hs[i];
+        const double nu = sqrt(q > 0.0 ? q : 0.0);
+        sinv = 1.0 / nu;
+        if (blockIdx.x == 0) *hn = nu;
+    }
+    __syncthreads();
+    const double inv = sinv;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double s = w[k];
+        for (int i = 0; i < m; ++i) s -= hs[i] * V[(long long)i * ldv + k];
+        w[k] = s * inv;
+    }
 }
 
 __global__ void __launch_bounds__(256) maxpy(int n, int m, const double* __restrict__ V, long long ldv,
@@ -289,39 +415,81 @@ __global__ void __launch_bounds__(512) gj_inverse_global(int npatch, const int* 
     if (threadIdx.x == 0) status[p] = st;
 }
 
-// Goodnight's symmetric sweep of an SPD matrix (row-major, leading
-// dimension lda), working on the upper triangle only: sweeping pivot k maps
-//   a_kk -> -1/a_kk,  a_ik -> a_ik/a_kk,  a_ij -> a_ij - a_ik a_kj / a_kk,
-// and sweeping every pivot in order leaves -A^{-1} (upper triangle).  An SPD
-// matrix needs no pivoting.  Rows go to warps, columns to lanes.
-// status <- 1 + step of the first non-positive pivot.
-__device__ void sweep_spd(double* A, int n, int lda, double* colk, int* status) {
+// Sign flip of a double through its bit pattern: no floating-point
+// instruction (the FP64 pipe is the bottleneck of the patch inversion).
+__device__ __forceinline__ double flip(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
+// Row-pair mapping of an upper triangle: warp w takes rows w and n-1-w, whose
+// (n - w) + (w + 1) = n + 1 entries fill its lanes evenly; entry l of the pair
+// is (i, j).  Returns the entry count of the pair.
+__device__ __forceinline__ int pair_len(int n, int pr) { return (pr == n - 1 - pr) ? n - pr : n + 1; }
+__device__ __forceinline__ void pair_entry(int n, int pr, int l, int& i, int& j) {
+    const int len0 = n - pr;
+    if (l < len0) { i = pr; j = pr + l; }
+    else { i = n - 1 - pr; j = i + (l - len0); }
+}
+
+// Goodnight's symmetric sweep of an SPD matrix in full row-major storage
+// (leading dimension lda), updating the upper triangle.  Sweeping pivot k maps
+//   a_kk -> -1/a_kk,  a_ik -> a_ik/a_kk (i != k),  a_ij -> a_ij - a_ik a_kj / a_kk,
+// and sweeping every pivot in order leaves -A^{-1}.  An SPD matrix needs no
+// pivoting.  On return the full matrix holds +A^{-1} (upper triangle negated
+// and mirrored by sign-bit flips).  Every updated entry costs exactly one FMA:
+// the pivot column is published scaled (cs) and unscaled (ck), and the lane
+// that updates the next diagonal entry forms the next reciprocal, so a pivot
+// needs two barriers.  Scratch: ck[2n] (double-buffered column), cs[n],
+// rinv[2].  status <- 1 + step of the first non-positive pivot.
+__device__ void sweep_spd(double* A, int n, int lda, double* ck, double* cs, double* rinv, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int npair = (n + 1) >> 1;
+    if (tid == 0) {
+        const double piv = A[0];
+        if (!(piv > 0.0) && *status == 0) *status = 1;
+        rinv[0] = piv > 0.0 ? 1.0 / piv : 0.0;
+    }
+    for (int i = tid; i < n; i += nt) ck[i] = A[i];
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        const double piv = A[(long long)k * lda + k];
-        if (tid == 0 && !(piv > 0.0) && *status == 0) *status = k + 1;
-        const double inv = piv > 0.0 ? 1.0 / piv : 0.0;
-        for (int i = tid; i < n; i += nt) colk[i] = i <= k ? A[(long long)i * lda + k] : A[(long long)k * lda + i];
+        const double* ckc = ck + (k & 1) * n;
+        double* ckn = ck + ((k + 1) & 1) * n;
+        const double inv = rinv[k & 1];
+        for (int i = tid; i < n; i += nt) cs[i] = ckc[i] * inv;
         __syncthreads();
-        for (int i = warp; i < n; i += nw) {
-            const double ci = colk[i] * inv;
-            double* row = A + (long long)i * lda;
-            for (int j = i + lane; j < n; j += 32) {
-                double v;
-                if (i == k) v = (j == k) ? -inv : colk[j] * inv;
-                else if (j == k) v = ci;
-                else v = row[j] - ci * colk[j];
-                row[j] = v;
+        for (int pr = warp; pr < npair; pr += nw) {
+            const int tot = pair_len(n, pr);
+            for (int l = lane; l < tot; l += 32) {
+                int i, j;
+                pair_entry(n, pr, l, i, j);
+                double* a = A + (long long)i * lda + j;
+                double v = fma(-cs[i], ckc[j], *a);
+                if (i == k || j == k) v = (i == j) ? flip(inv) : cs[i == k ? j : i];
+                *a = v;
+                // publish column k+1 of the updated matrix for the next pivot
+                if (j == k + 1) ckn[i] = v;
+                else if (i == k + 1) ckn[j] = v;
+                if (i == k + 1 && j == k + 1) {
+                    if (!(v > 0.0) && *status == 0) *status = k + 2;
+                    rinv[(k + 1) & 1] = v > 0.0 ? 1.0 / v : 0.0;
+                }
             }
         }
         __syncthreads();
     }
-}
-
-// symmetric access to the upper triangle of a swept matrix: A^{-1}[i][j]
-__device__ __forceinline__ double neg_upper(const double* A, int lda, int i, int j) {
-    return -(i <= j ? A[(long long)i * lda + j] : A[(long long)j * lda + i]);
+    // -A^{-1} (upper) -> +A^{-1} (full)
+    for (int pr = warp; pr < npair; pr += nw) {
+        const int tot = pair_len(n, pr);
+        for (int l = lane; l < tot; l += 32) {
+            int i, j;
+            pair_entry(n, pr, l, i, j);
+            const double v = flip(A[(long long)i * lda + j]);
+            A[(long long)i * lda + j] = v;
+            A[(long long)j * lda + i] = v;
+        }
+    }
+    __syncthreads();
 }
 
 // Block inverse of one Vanka patch with the saddle structure
@@ -329,53 +497,63 @@ __device__ __forceinline__ double neg_upper(const double* A, int lda, int i, int
 // (the d velocity components share the SPD block L on the same nodes):
 //   Li = L^{-1}, W_c = Li B_c^T, S = sum_c B_c W_c, Si = S^{-1}, X_c = W_c Si,
 //   K_i^{-1} = [blockdiag(Li) - X W^T, X; X^T, -Si].
-// Li and Si come from the symmetric sweep; the (symmetric) inverse is
-// computed on its upper triangle and every value written to both of its
-// positions: column-major padded FP64 / FP32 and, if back, row-major into K.
+// Li and Si come from the symmetric sweep.  Products map one output entry
+// to one thread (a warp's lanes share few rows), the symmetric velocity block
+// uses the row-pair mapping, so FP64 instructions run with full warps.  The
+// (symmetric) inverse is formed on its upper triangle and every value written
+// to both of its positions: column-major padded FP64 / FP32 and, if back,
+// row-major into K.
 __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, double* inv64, float* inv32,
                             int back, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int np = n - d * nv, npp = np | 1, dnv = d * nv;
-    double* Ls = scratch;
+    const int mx = nv > np ? nv : np;
+    double* Ls = scratch;                          // [nv][nv]
     double* Bt = Ls + (long long)nv * nv;          // [c][a][q], becomes X
     double* Wm = Bt + (long long)d * nv * npp;     // [c][a][q]
     double* Ss = Wm + (long long)d * nv * npp;     // [q][r]
-    double* colk = Ss + (long long)np * np;
+    double* ck = Ss + (long long)np * np;          // [2][mx]
+    double* cs = ck + 2 * mx;                      // [mx]
+    double* rinv = cs + mx;                        // [2]
     for (int i = warp; i < nv; i += nw)
         for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
     for (int r = warp; r < dnv; r += nw)
         for (int q = lane; q < np; q += 32) Bt[(long long)r * npp + q] = K[(long long)r * n + dnv + q];
     __syncthreads();
-    sweep_spd(Ls, nv, nv, colk, status);
-    // W_c = Li B_c^T
-    for (int r = warp; r < dnv; r += nw) {
+    sweep_spd(Ls, nv, nv, ck, cs, rinv, status);
+    // W_c = Li B_c^T: entry t = (r, q), r = c nv + a
+    const int nw_out = dnv * np;
+    for (int t = tid; t < nw_out; t += nt) {
+        const int r = t / np, q = t - r * np;
         const int c = r / nv, a = r - c * nv;
-        for (int q = lane; q < np; q += 32) {
-            const double* bt = Bt + (long long)c * nv * npp + q;
-            double s = 0.0;
-            for (int b = 0; b < nv; ++b) s += neg_upper(Ls, nv, a, b) * bt[(long long)b * npp];
-            Wm[(long long)r * npp + q] = s;
-        }
+        const double* li = Ls + a * nv;
+        const double* bt = Bt + (long long)c * nv * npp + q;
+        double s = 0.0;
+        for (int b = 0; b < nv; ++b) s = fma(li[b], bt[(long long)b * npp], s);
+        Wm[(long long)r * npp + q] = s;
     }
     __syncthreads();
-    // S = sum_c B_c W_c (symmetric: upper triangle)
-    for (int q = warp; q < np; q += nw)
-        for (int r = q + lane; r < np; r += 32) {
-            double s = 0.0;
-            for (int a = 0; a < dnv; ++a) s += Bt[(long long)a * npp + q] * Wm[(long long)a * npp + r];
-            Ss[q * np + r] = s;
-        }
+    // S = sum_c B_c W_c, upper triangle q <= r
+    const int ns = np * (np + 1) / 2;
+    for (int t = tid; t < ns; t += nt) {
+        int q = 0, rem = t;
+        while (rem >= np - q) { rem -= np - q; ++q; }
+        const int r = q + rem;
+        double s = 0.0;
+        for (int a = 0; a < dnv; ++a) s = fma(Bt[(long long)a * npp + q], Wm[(long long)a * npp + r], s);
+        Ss[q * np + r] = s;
+    }
     __syncthreads();
-    sweep_spd(Ss, np, np, colk, status);
+    sweep_spd(Ss, np, np, ck, cs, rinv, status);
     // X_c = W_c Si (overwrites Bt)
-    for (int r = warp; r < dnv; r += nw)
-        for (int q = lane; q < np; q += 32) {
-            const double* w = Wm + (long long)r * npp;
-            double s = 0.0;
-            for (int x = 0; x < np; ++x) s += w[x] * neg_upper(Ss, np, x, q);
-            Bt[(long long)r * npp + q] = s;
-        }
+    for (int t = tid; t < nw_out; t += nt) {
+        const int r = t / np, q = t - r * np;
+        const double* w = Wm + (long long)r * npp;
+        double s = 0.0;
+        for (int x = 0; x < np; ++x) s = fma(w[x], Ss[x * np + q], s);
+        Bt[(long long)r * npp + q] = s;
+    }
     __syncthreads();
     const int ld64 = (n + 1) & ~1, ld32 = (n + 3) & ~3;
     auto put = [&](int i, int j, double v) {
@@ -383,28 +561,30 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
         if (inv32) { inv32[(long long)j * ld32 + i] = (float)v; inv32[(long long)i * ld32 + j] = (float)v; }
         if (back) { K[(long long)i * n + j] = v; K[(long long)j * n + i] = v; }
     };
-    for (int i = warp; i < n; i += nw) {
-        if (i < dnv) {
-            const int c = i / nv, a = i - c * nv;
+    // velocity block: blockdiag(Li) - X W^T, upper triangle by row pairs
+    const int vpairs = (dnv + 1) >> 1;
+    for (int pr = warp; pr < vpairs; pr += nw) {
+        const int tot = pair_len(dnv, pr);
+        for (int l = lane; l < tot; l += 32) {
+            int i, j;
+            pair_entry(dnv, pr, l, i, j);
+            const int c = i / nv, a = i - c * nv, c2 = j / nv, b = j - c2 * nv;
             const double* x = Bt + (long long)i * npp;
-            for (int j = i + lane; j < n; j += 32) {
-                double v;
-                if (j < dnv) {
-                    const int c2 = j / nv, b = j - c2 * nv;
-                    const double* w = Wm + (long long)j * npp;
-                    double s = 0.0;
-                    for (int q = 0; q < np; ++q) s += x[q] * w[q];
-                    v = (c == c2 ? neg_upper(Ls, nv, a, b) : 0.0) - s;
-                } else {
-                    v = x[j - dnv];
-                }
-                put(i, j, v);
-            }
-        } else {
-            const int ii = i - dnv;
-            for (int j = i + lane; j < n; j += 32)
-                put(i, j, Ss[(long long)ii * np + (j - dnv)]);   // -Si, left in Ss by the sweep
+            const double* w = Wm + (long long)j * npp;
+            double v = c == c2 ? Ls[a * nv + b] : 0.0;
+            for (int q = 0; q < np; ++q) v = fma(-x[q], w[q], v);
+            put(i, j, v);
         }
+    }
+    // velocity-pressure block X and pressure block -Si (copies)
+    for (int t = tid; t < nw_out; t += nt) {
+        const int r = t / np, q = t - r * np;
+        put(r, dnv + q, Bt[(long long)r * npp + q]);
+    }
+    for (int t = tid; t < ns; t += nt) {
+        int q = 0, rem = t;
+        while (rem >= np - q) { rem -= np - q; ++q; }
+        put(dnv + q, dnv + q + rem, flip(Ss[q * np + q + rem]));
     }
     // zero the padding rows of the column-major copies
     for (int j = tid; j < n; j += nt) {

@@ -80,9 +80,15 @@ __global__ void mdot_final(int nblocks, int m, const double* __restrict__ partia
 // Same reduction in one launch (last block finishes in a fixed order);
 // MDOT_BLOCKS blocks of 512 threads; ticket must start at 0 and is reset.
 constexpr int MDOT_BLOCKS = 152;
-__global__ void mdot_fused(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ w,
-                           double* __restrict__ partial, unsigned int* __restrict__ ticket, double* __restrict__ out,
-                           double* __restrict__ acc, int sqrt_out);
+void mdot_fused(int n, int m, const double* V, long long ldv, const double* w, double* partial, unsigned int* ticket,
+                double* out, double* acc, int sqrt_out, cudaStream_t s);
+// w <- w - V h; out[0..m) = V^T w, out[m] = w^T w of the updated w,
+// acc[i] += out[i] (i < m); MDOT_BLOCKS blocks of 512 threads, m <= 31.
+void maxpy_mdot(int n, int m, const double* V, long long ldv, const double* h, double* w, double* partial,
+                unsigned int* ticket, double* out, double* acc, cudaStream_t s);
+// w <- (w - V h) / nu, nu = sqrt(max(*nrm2 - |h|^2, 0)), *hn = nu
+__global__ void maxpy_normalise(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ h,
+                                const double* __restrict__ nrm2, double* __restrict__ w, double* __restrict__ hn);
 // w[k] += sign * sum_i h[i] V[i][k]
 __global__ void maxpy(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ h,
                       double sign, double* __restrict__ w);
@@ -121,7 +127,7 @@ __global__ void gj_inverse_global(int npatch, const int* __restrict__ poff, cons
 __host__ __device__ inline long long saddle_scratch(int d, int n, int nv) {
     const int np = n - d * nv, npp = np | 1;
     const int mx = nv > np ? nv : np;
-    return (long long)nv * nv + 2LL * d * nv * npp + (long long)np * np + mx;
+    return (long long)nv * nv + 2LL * d * nv * npp + (long long)np * np + 3LL * mx + 2;
 }
 constexpr long long SADDLE_SMEM_MAX_DOUBLES = 25600;   // 200 KB of shared memory
 __global__ void saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,

@@ -185,6 +185,7 @@ struct DevLevel {
     // device assembly of K (all levels but the coarsest)
     bool dev_asm = false;
     sasm::AsmMesh am;
+    double* cellgeo = nullptr;          // am.cg, filled on the device
     int* asm_len = nullptr;
     int* asm_tmp = nullptr;
     int* asm_status = nullptr;
@@ -265,6 +266,10 @@ struct stokes_mg {
     std::vector<double*> mesh_X;         // device vertex coordinates per mesh
     std::vector<int*> mesh_C;            // device cells per mesh
     std::vector<void*> allocs;
+    // STOKES_TRACE=1: device timeline of setup (event, label, host time)
+    struct Mark { std::string what; double host, dev; };
+    std::vector<Mark*> marks;
+    std::mutex marks_mu;
 };
 
 namespace {
@@ -289,6 +294,31 @@ void launch(stokes_mg* h, int kind, cudaStream_t s, F&& f) {
         p->pending.push_back({a, b});
         p->launches++;
     }
+}
+
+// Device timeline of setup under STOKES_TRACE=1: a host function enqueued
+// on `s` stamps the time at which the stream reaches this point; print_marks
+// lists the stamps against the first one.
+void mark_cb(void* p) { static_cast<stokes_mg::Mark*>(p)->dev = host_ms(); }
+void mark(stokes_mg* h, const std::string& what, cudaStream_t s) {
+    if (!trace_on()) return;
+    stokes_mg::Mark* m = new stokes_mg::Mark{what, host_ms(), 0.0};
+    {
+        std::lock_guard<std::mutex> g(h->marks_mu);
+        h->marks.push_back(m);
+    }
+    CK(cudaLaunchHostFunc(s, mark_cb, m));
+}
+void print_marks(stokes_mg* h) {
+    if (h->marks.empty()) return;
+    CK(cudaDeviceSynchronize());
+    const double t0 = h->marks[0]->host;
+    for (auto* m : h->marks) {
+        std::fprintf(stderr, "[stokes] %-34s device %8.3f ms  issued %8.3f ms\n", m->what.c_str(), m->dev - t0,
+                     m->host - t0);
+        delete m;
+    }
+    h->marks.clear();
 }
 
 template <typename T>
@@ -616,8 +646,7 @@ void mdot(stokes_mg* h, int n, int m, const double* V, long long ldv, const doub
     double* partial = ws ? ws->partial : h->partial;
     unsigned int* ticket = ws ? ws->ticket : h->ticket;
     launch(h, -1, s, [&] {
-        skern::mdot_fused<<<skern::MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc,
-                                                            sqrt_out ? 1 : 0);
+        skern::mdot_fused(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out ? 1 : 0, s);
     });
 }
 
@@ -626,15 +655,21 @@ void maxpy_l(stokes_mg* h, int n, int m, const double* V, long long ldv, const d
     launch(h, -1, s, [&] { skern::maxpy<<<grid_for(n), 256, 0, s>>>(n, m, V, ldv, hh, sign, w); });
 }
 
-// orthogonalise w (length n) against V[0..m-1] by classical Gram-Schmidt
-// applied twice; h[0..m-1] receives the coefficients, hn[0] = ||w|| after.
+// Orthogonalise w (length n) against V[0..m-1] by classical Gram-Schmidt
+// applied twice, then normalise it: hcoef[0..m-1] receives the summed
+// coefficients, hn[0] = ||w|| before the normalisation (the new Hessenberg
+// entry).  Three launches: the first pass's dots; its update fused with the
+// second pass's dots and ||w||^2; the second update with the scaling.
+// h2 holds m + 1 values.
 void cgs2(stokes_mg* h, int n, int m, const double* V, double* w, double* hcoef, double* h2, double* hn, cudaStream_t s,
           const KrylovWS* ws = nullptr) {
+    double* partial = ws ? ws->partial : h->partial;
+    unsigned int* ticket = ws ? ws->ticket : h->ticket;
     mdot(h, n, m, V, n, w, hcoef, nullptr, false, s, ws);
-    maxpy_l(h, n, m, V, n, hcoef, -1.0, w, s);
-    mdot(h, n, m, V, n, w, h2, hcoef, false, s, ws);
-    maxpy_l(h, n, m, V, n, h2, -1.0, w, s);
-    mdot(h, n, 1, w, n, w, hn, nullptr, true, s, ws);
+    launch(h, -1, s, [&] {
+        skern::maxpy_mdot(n, m, V, n, hcoef, w, partial, ticket, h2, hcoef, s);
+    });
+    launch(h, -1, s, [&] { skern::maxpy_normalise<<<grid_for(n), 256, 0, s>>>(n, m, V, n, h2, h2 + m, w, hn); });
 }
 
 double d2h_scalar(stokes_mg* h, const double* d, cudaStream_t s) {
@@ -663,13 +698,23 @@ int arnoldi_launch(stokes_mg* h, int li, const double* v0, int steps, double* Hs
     launch(h, -1, s, [&] { skern::fill_vec<double><<<1, 256, 0, s>>>((long long)(m + 1) * m, 0.0, Hs); });
     mdot(h, n, 1, v0, n, v0, hn, nullptr, true, s, ws);
     launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, v0, hn, V); });
+    // the operator M^{-1} K is applied in the precision of the smoother that
+    // the estimate serves (FP32 K and inverses in mixed mode); the basis and
+    // its orthogonalisation stay FP64
+    const bool f32 = h->opts.precision == STOKES_MIXED && l.inv32 && l.K.v32 && l.t32 && l.u32;
     for (int j = 0; j < m; ++j) {
         double* w = V + (long long)(j + 1) * n;
-        spmv<double>(h, PK_SPMV, l.K, skern::SPMV_SET, V + (long long)j * n, l.t64, nullptr, s);
-        asm_apply<double>(h, l, l.t64, w, 1.0, 0.0, s);
+        if (f32) {
+            launch(h, -1, s, [&] { skern::convert_vec<float, double><<<grid_for(n), 256, 0, s>>>(n, V + (long long)j * n, l.t32); });
+            spmv<float>(h, PK_SPMV, l.K, skern::SPMV_SET, l.t32, l.u32, nullptr, s);
+            asm_apply<float>(h, l, l.u32, l.t32, 1.0, 0.0, s);
+            launch(h, -1, s, [&] { skern::convert_vec<double, float><<<grid_for(n), 256, 0, s>>>(n, l.t32, w); });
+        } else {
+            spmv<double>(h, PK_SPMV, l.K, skern::SPMV_SET, V + (long long)j * n, l.t64, nullptr, s);
+            asm_apply<double>(h, l, l.t64, w, 1.0, 0.0, s);
+        }
         cgs2(h, n, j + 1, V, w, hh, yy, hn, s, ws);
         launch(h, -1, s, [&] { skern::arnoldi_store<<<1, 1, 0, s>>>(j, m, Hs, hh, hn); });
-        launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, hn, w); });
     }
     CK(cudaMemcpyAsync(H_host, Hs, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToHost, s));
     return m;
@@ -750,7 +795,6 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
             CK(cudaMemcpyAsync(zj, h->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             spmv<double>(h, PK_SPMV, l0.K, skern::SPMV_SET, zj, w, nullptr, s);
             cgs2(h, n, j + 1, h->V, w, h->h, h->y, h->hn, s);
-            launch(h, -1, s, [&] { skern::scale_by_inv<<<grid_for(n), 256, 0, s>>>(n, w, h->hn, w); });
             launch(h, -1, s, [&] {
                 skern::fgmres_givens<<<1, 1, 0, s>>>(j, m, h->Hh, h->h, h->hn, h->cs, h->sn, h->g, h->resid);
             });
@@ -895,6 +939,8 @@ void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     a.S = hupload(h, HL.RT.S, s);
     a.Cq = hupload(h, HL.RT.Cq, s);
     a.M = hupload(h, HL.RT.M, s);
+    l.cellgeo = halloc<double>(h, (size_t)mesh.nc * sasm::CG_STRIDE);
+    a.cg = l.cellgeo;
     long long bound = 0;
     for (int f = 0; f < HL.nVf; ++f) {
         const int i = vrow[f];
@@ -922,6 +968,7 @@ void assemble_on_device(stokes_mg* h, int li, cudaStream_t s) {
     DevLevel& l = h->L[li];
     if (!l.dev_asm) return;
     const int n = l.K.nr;
+    launch(h, -1, s, [&] { sasm::cell_geometry(l.am, l.cellgeo, s); });
     launch(h, -1, s, [&] { sasm::row_lengths(l.am, l.asm_len, l.asm_status, s); });
     launch(h, -1, s, [&] { sasm::scan_rows(l.asm_len, n, l.K.rp, l.asm_tmp, s); });
     launch(h, -1, s, [&] { sasm::fill_rows(l.am, l.K.rp, l.K.ci, l.K.v64, l.asm_status, s); });
@@ -969,7 +1016,10 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
         float* i32 = store ? l.inv32 : nullptr;
         if (l.saddle_smem > 0) {
             const size_t smem = (size_t)l.saddle_smem * sizeof(double);
-            CK(cudaFuncSetAttribute(skern::saddle_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            // one upper bound for every level (levels launch from one thread
+            // onto different streams)
+            CK(cudaFuncSetAttribute(skern::saddle_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(skern::SADDLE_SMEM_MAX_DOUBLES * sizeof(double))));
             launch(h, PK_GJ, s, [&] {
                 skern::saddle_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
                                                                        l.ioff32, i32, store ? 0 : 1,
@@ -990,7 +1040,11 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
     }
     const int nsm = std::min(l.maxn, skern::GJ_SMEM_MAX_N);
     const size_t smem = (size_t)nsm * nsm * sizeof(double) + nsm * sizeof(double) + nsm * sizeof(int) + 64;
-    CK(cudaFuncSetAttribute(skern::gj_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        const int gmax = skern::GJ_SMEM_MAX_N;
+        CK(cudaFuncSetAttribute(skern::gj_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((size_t)gmax * gmax * sizeof(double) + gmax * sizeof(double) + gmax * sizeof(int) + 64)));
+    }
     launch(h, PK_GJ, s, [&] {
         skern::gj_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, l.poff, l.moff, work, store ? l.ioff64 : nullptr,
                                                            store ? l.inv64 : nullptr, store ? l.ioff32 : nullptr,
@@ -1172,8 +1226,13 @@ void alloc_krylov(stokes_mg* h, cudaStream_t s) {
     h->vin = halloc<double>(h, n0);
     h->vout = halloc<double>(h, n0);
     h->v0buf = halloc<double>(h, n0);
-    h->Hlev = halloc<double>(h, (size_t)STOKES_MAX_LEVELS * skern::HESS_MAX * skern::HESS_MAX);
     CK(cudaMallocHost((void**)&h->pinned, 64));
+}
+
+// Hessenberg matrices of the lambda_max estimates: one device and one pinned
+// host slot per level (allocated with the first level that reaches setup)
+void alloc_hess(stokes_mg* h, cudaStream_t s) {
+    h->Hlev = halloc<double>(h, (size_t)STOKES_MAX_LEVELS * skern::HESS_MAX * skern::HESS_MAX);
     CK(cudaMallocHost((void**)&h->pinned_H, sizeof(double) * (STOKES_MAX_LEVELS + 1) * skern::HESS_MAX * skern::HESS_MAX));
 }
 
@@ -1305,6 +1364,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         require(o.cheb_hi > o.cheb_lo && o.cheb_lo > 0, "bad Chebyshev interval");
         require(o.patch_solver == 0 || o.patch_solver == 1, "patch_solver must be 0 (saddle block) or 1 (Gauss-Jordan)");
         if (!o.host_only) CK(cudaGetDevice(&h->device));
+        if (!o.host_only) mark(h.get(), "setup start", (cudaStream_t)stream);
         for (int kk = 0; kk < 5; ++kk) h->prof[kk].on = (o.prof_mask >> kk) & 1;
         cudaStream_t s = (cudaStream_t)stream;
         h->dim = coarse->dim;
@@ -1323,6 +1383,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         spec.n_refine = n_refine;
         spec.barycentric = barycentric_finest != 0;
         spec.device_assembly = !o.host_only;
+        spec.coarsest_first = !o.host_only;
         if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
         else if (o.hierarchy == STOKES_HIER_GRADUAL) {
             if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
@@ -1354,18 +1415,31 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             int prio_lo = 0, prio_hi = 0;
             CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
             CK(cudaStreamCreateWithPriority(&h->s_up, cudaStreamNonBlocking, prio_hi));
-            CK(cudaStreamCreateWithFlags(&h->s_coarse, cudaStreamNonBlocking));
+            // the coarse Gauss-Jordan is a chain of small latency-bound
+            // launches: highest priority, so that its blocks are scheduled
+            // ahead of the waiting blocks of the patch kernels
+            CK(cudaStreamCreateWithPriority(&h->s_coarse, cudaStreamNonBlocking, prio_hi));
+            // relaxed levels below the finest share a second compute stream,
+            // so their inversion and lambda_max estimate overlap level 0's
+            // (one step above the default priority: their blocks are placed
+            // between level 0's patch-inversion blocks instead of after them)
+            cudaStream_t s_small = nullptr;
+            CK(cudaStreamCreateWithPriority(&s_small, cudaStreamNonBlocking, std::max(prio_hi, prio_lo - 1)));
+            h->s_lvl.push_back(s_small);
             launcher.reset(new Launcher());
             on_level = [&](int li) {
                 const double tu = host_ms();
                 stokes_mg* hp = h.get();
                 const int nlv = (int)hp->H.levels.size();
-                if ((int)hp->L.size() != nlv) hp->L.assign(nlv, DevLevel());
-                // uploads on this thread; the relaxed levels then compute on the
-                // caller's stream, the coarse level on s_coarse
-                // (all relaxed levels share one stream: separate streams let the
-                // small levels' launches crowd the latency-bound coarse steps)
-                cudaStream_t target = li + 1 < nlv ? s : hp->s_coarse;
+                if ((int)hp->L.size() != nlv) {
+                    hp->L.assign(nlv, DevLevel());
+                    hp->kws.resize(nlv);      // sized once: launches keep pointers into it
+                    alloc_hess(hp, hp->s_up);
+                }
+                // uploads on this thread; level 0 then computes on the caller's
+                // stream, the other relaxed levels on s_lvl[0], the coarse
+                // level on s_coarse
+                cudaStream_t target = li == 0 ? s : (li + 1 < nlv ? hp->s_lvl[0] : hp->s_coarse);
                 if (li + 1 < nlv) {
                     upload_level(hp, li, want32, hp->s_up);
                     const double tk = host_ms();
@@ -1376,6 +1450,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                     upload_level(hp, li, want32, hp->s_up);
                     upload_coarse(hp, hp->s_up);
                 }
+                mark(hp, "L" + std::to_string(li) + " uploaded", hp->s_up);
                 cudaEvent_t ev;
                 CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
                 CK(cudaEventRecord(ev, hp->s_up));
@@ -1389,8 +1464,11 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                     CK(cudaSetDevice(hp->device));
                     if (li + 1 < nlv) {
                         const cudaStream_t sl = target;
+                        mark(hp, "L" + std::to_string(li) + " device start", sl);
                         assemble_on_device(hp, li, sl);
+                        mark(hp, "L" + std::to_string(li) + " assembled", sl);
                         launch_patches(hp, li, sl);
+                        mark(hp, "L" + std::to_string(li) + " inverted", sl);
                         // lambda_max estimate right behind the inversion (same stream)
                         if (!(li < 16 && o.lmax_override[li] > 0)) {
                             const int n = hp->L[li].n;
@@ -1401,15 +1479,19 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                             const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
                             hp->arn_m[li] = arnoldi_launch(hp, li, v0, o.eig_steps, hp->Hlev + li * hsz,
                                                            hp->pinned_H + (li + 1) * hsz, sl, ws);
+                            mark(hp, "L" + std::to_string(li) + " arnoldi", sl);
                         }
                     } else {
+                        mark(hp, "coarse start", hp->s_coarse);
                         launch_coarse(hp, hp->s_coarse);
+                        mark(hp, "coarse factorised", hp->s_coarse);
                     }
                     t_launch += host_ms() - tl;
                 });
             };
         }
         sfem::build_hierarchy(cm, spec, nu_cell, h->H, on_level);
+        if (!o.host_only) mark(h.get(), "host hierarchy built", h->s_up);
         h->st.t_mesh_ms = h->H.t_mesh_ms;
         h->st.t_assembly_ms = h->H.t_assembly_ms;
         h->st.t_spaces_ms = h->H.t_spaces_ms;
@@ -1431,6 +1513,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         for (int li = 0; li + 1 < nl; ++li) upload_transfers(h.get(), li, want32, h->s_up);
         const int n0 = h->L[0].n;
         setup_solve_buffers(h.get(), h->s_up);
+        mark(h.get(), "transfers uploaded", h->s_up);
         CK(cudaStreamSynchronize(h->s_up));
         h->st.t_upload_ms = t_cb_upload;
         h->st.t_upload_post_ms = host_ms() - t1;
@@ -1461,6 +1544,8 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         CK(cudaStreamSynchronize(s));
         h->st.t_graph_ms = host_ms() - t1;
         h->st.t_total_ms = host_ms() - t0;
+        mark(h.get(), "setup end", s);
+        print_marks(h.get());
         fill_stats(h.get());
         return STOKES_OK;
     });
@@ -1817,6 +1902,8 @@ void stokes_mg_destroy(stokes_mg_t h) {
     if (prev != h->device) cudaSetDevice(h->device);
     for (auto& p : h->prof)
         for (auto& ab : p.pending) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
+    if (h->s_up || h->s_coarse) cudaDeviceSynchronize();
+    for (auto* m : h->marks) delete m;
     for (int i = 0; i < 2; ++i)
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
     if (h->s_up || h->s_coarse) cudaDeviceSynchronize();   // setup work may still be in flight after an error

@@ -2,7 +2,8 @@
 bench.py times (HIER_EXPLICIT schedule, defaults otherwise).
 
 * TH P4/P3 on the 64x64 square (167,299 free DoFs, the benchmark workload):
-  lambda_max of every level from the library's SplitMix64 start vector, one
+  lambda_max of every level from the library's SplitMix64 start vector (FP64
+  handle 1e-9; the mixed handle's FP32 operator within 1e-4), one
   V-cycle in FP64 (1e-10) and in mixed precision (2e-4) against the oracle's
   V-cycle with the same lambda_max, FGMRES iteration counts (+-1).
 * SV P4/P3disc on the Alfeld-refined Delaunay disk and TH P3/P2 on the 16^3
@@ -47,7 +48,9 @@ def test_benchmark_workload_th_p4_64x64():
     hmx = _lib(w, P.MIXED)
     perms = [level_perm(h64, li, L.disc) for li, L in enumerate(ora.levels)]
     lm = h64.info()["lmax"]
-    assert hmx.info()["lmax"][:len(lm) - 1] == lm[:len(lm) - 1]     # both precisions estimate in FP64
+    # mixed mode applies M^{-1} K in FP32 inside the FP64-orthogonalised Arnoldi
+    for a, b in zip(hmx.info()["lmax"][:len(lm) - 1], lm[:len(lm) - 1]):
+        assert abs(a - b) <= 1e-4 * b, (a, b)
     for li, L in enumerate(ora.levels[:-1]):
         v0 = rng.uniform_pm1(0, li, perms[li])
         want = mg.arnoldi_lmax(L.disc.K, L.asm.apply, v0, mg.Options().eig_steps)

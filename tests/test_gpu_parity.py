@@ -140,6 +140,16 @@ def test_a3_arnoldi_lambda_max(name):
         want = mg.arnoldi_lmax(L.disc.K, L.asm.apply, v0, mg.Options().eig_steps)
         assert abs(lm[li] - want) <= 1e-9 * abs(want)
     hd.close()
+    # mixed precision: the same Arnoldi with M^{-1} K applied in FP32 (FP32 CSR
+    # values and stored inverses); the basis stays FP64
+    hm = P.StokesMG(v, c, nref, fam, k, barycentric=bary, hierarchy=P.HIER_EXPLICIT, schedule=sched,
+                    precision=P.MIXED)
+    lmm = hm.info()["lmax"]
+    for li, L in enumerate(ora.levels[:-1]):
+        v0 = rng.uniform_pm1(0, li, perms[li])
+        want = mg.arnoldi_lmax(L.disc.K, L.asm.apply, v0, mg.Options().eig_steps)
+        assert abs(lmm[li] - want) <= 1e-4 * abs(want), (li, lmm[li], want)
+    hm.close()
 
 
 @pytest.mark.parametrize("name", NAMES)
