@@ -1,6 +1,9 @@
 // Host-side finite-element setup; see fem.hpp.
 #include "fem.hpp"
 
+#include <cstdio>
+#include <cstdlib>
+
 #include <algorithm>
 #include <atomic>
 #include <condition_variable>
@@ -103,11 +106,13 @@ class Pool {
     bool stop_ = false;
 };
 
-static int chunk_count(int n) { return std::max(1, std::min(Pool::get().size(), n / 64)); }
+// chunks for n items of at least `grain` items each (1 = run inline: waking
+// the workers costs more than a light loop over a few thousand items)
+static int chunk_count(int n, int grain = 64) { return std::max(1, std::min(Pool::get().size(), n / grain)); }
 
 // Static-chunk parallel loop over [0, n): body(lo, hi, chunk).
-static void parallel_for(int n, const std::function<void(int, int, int)>& body) {
-    const int T = chunk_count(n);
+static void parallel_for(int n, const std::function<void(int, int, int)>& body, int grain = 64) {
+    const int T = chunk_count(n, grain);
     Pool::get().run(T, [&](int t) {
         int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
         body(lo, hi, t);
@@ -158,6 +163,51 @@ static FlatLists build_lists(int n, F&& fill) {
             if (!buf[t].empty()) std::memcpy(L.data.data() + L.off[lo[t]], buf[t].data(), buf[t].size() * sizeof(int));
     });
     return L;
+}
+
+// Parallel exclusive scan of cnt[0..n) into out[0..n] (out[n] = total).
+static void parallel_scan(const int* cnt, int n, int* out) {
+    const int T = chunk_count(n, 16384);
+    std::vector<long long> part(T + 1, 0);
+    Pool::get().run(T, [&](int t) {
+        const int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
+        long long s = 0;
+        for (int i = lo; i < hi; ++i) s += cnt[i];
+        part[t + 1] = s;
+    });
+    for (int t = 0; t < T; ++t) part[t + 1] += part[t];
+    Pool::get().run(T, [&](int t) {
+        const int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
+        long long s = part[t];
+        for (int i = lo; i < hi; ++i) { out[i] = (int)s; s += cnt[i]; }
+    });
+    out[n] = (int)part[T];
+}
+
+void invert_index(const int* idx, long long m, int n, std::vector<int>& off, std::vector<int>& pos) {
+    off.assign(n + 1, 0);
+    std::vector<int> cnt(n, 0);
+    const int T = (int)std::max<long long>(1, std::min<long long>(Pool::get().size(), m / 8192));
+    Pool::get().run(T, [&](int t) {
+        const long long lo = m * t / T, hi = m * (t + 1) / T;
+        for (long long q = lo; q < hi; ++q) __atomic_fetch_add(&cnt[idx[q]], 1, __ATOMIC_RELAXED);
+    });
+    parallel_scan(cnt.data(), n, off.data());
+    pos.resize(m);
+    std::vector<int> cur(off.begin(), off.end() - 1);
+    Pool::get().run(T, [&](int t) {
+        const long long lo = m * t / T, hi = m * (t + 1) / T;
+        for (long long q = lo; q < hi; ++q) pos[__atomic_fetch_add(&cur[idx[q]], 1, __ATOMIC_RELAXED)] = (int)q;
+    });
+    // restore increasing positions within every list (lists are short)
+    parallel_for(n, [&](int lo, int hi, int) {
+        for (int i = lo; i < hi; ++i) {
+            int* a = pos.data() + off[i];
+            const int len = off[i + 1] - off[i];
+            for (int x = 1; x < len; ++x)
+                for (int y = x; y > 0 && a[y - 1] > a[y]; --y) std::swap(a[y - 1], a[y]);
+        }
+    }, 4096);
 }
 
 static double now_ms() {
@@ -618,46 +668,62 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         base[4] = base[3] + nf * nint[3];
     }
     long long ntmp = d == 2 ? base[3] + (long long)m.nc * nint[3] : base[4] + (long long)m.nc * nint[4];
+    // entity-based id of every (cell, local node)
     std::vector<int> tmp((size_t)m.nc * nb);
-    for (int e = 0; e < m.nc; ++e) {
-        const int* v = &m.C[(size_t)e * nvpc];
-        for (int l = 0; l < nb; ++l) {
-            int sv[4], sa[4], sl[4], mm = 0;
-            for (int i = 0; i < nvpc; ++i)
-                if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sa[mm] = re.alpha[l][i]; sl[mm] = i; ++mm; }
-            for (int a = 1; a < mm; ++a)          // sort by global vertex id
-                for (int b = a; b > 0 && sv[b - 1] > sv[b]; --b) {
-                    std::swap(sv[b - 1], sv[b]); std::swap(sa[b - 1], sa[b]); std::swap(sl[b - 1], sl[b]);
-                }
-            long long code = 0;
-            for (int t = 0; t < mm; ++t) code = code * (k + 1) + sa[t];
-            int r = rank[mm][code];
-            long long eid;
-            if (mm == 1) eid = sv[0];
-            else if (mm == 2) eid = T.cell_edge[(size_t)e * (d == 2 ? 3 : 6) + local_edge(d, sl[0], sl[1])];
-            else if (mm == 3 && d == 3) eid = T.cell_face[(size_t)e * 4 + (6 - sl[0] - sl[1] - sl[2])];
-            else eid = e;   // cell interior
-            tmp[(size_t)e * nb + l] = (int)(base[mm] + eid * nint[mm] + r);
+    parallel_for(m.nc, [&](int lo, int hi, int) {
+        for (int e = lo; e < hi; ++e) {
+            const int* v = &m.C[(size_t)e * nvpc];
+            for (int l = 0; l < nb; ++l) {
+                int sv[4], sa[4], sl[4], mm = 0;
+                for (int i = 0; i < nvpc; ++i)
+                    if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sa[mm] = re.alpha[l][i]; sl[mm] = i; ++mm; }
+                for (int a = 1; a < mm; ++a)          // sort by global vertex id
+                    for (int b = a; b > 0 && sv[b - 1] > sv[b]; --b) {
+                        std::swap(sv[b - 1], sv[b]); std::swap(sa[b - 1], sa[b]); std::swap(sl[b - 1], sl[b]);
+                    }
+                long long code = 0;
+                for (int t = 0; t < mm; ++t) code = code * (k + 1) + sa[t];
+                int r = rank[mm][code];
+                long long eid;
+                if (mm == 1) eid = sv[0];
+                else if (mm == 2) eid = T.cell_edge[(size_t)e * (d == 2 ? 3 : 6) + local_edge(d, sl[0], sl[1])];
+                else if (mm == 3 && d == 3) eid = T.cell_face[(size_t)e * 4 + (6 - sl[0] - sl[1] - sl[2])];
+                else eid = e;   // cell interior
+                tmp[(size_t)e * nb + l] = (int)(base[mm] + eid * nint[mm] + r);
+            }
         }
-    }
-    // renumber by first appearance
-    std::vector<int> newid(ntmp, -1);
-    int n = 0;
-    for (size_t t = 0; t < tmp.size(); ++t) {
-        int& x = newid[tmp[t]];
-        if (x < 0) x = n++;
-        S.cell_nodes[t] = x;
-    }
+    }, 512);
+    // renumber by first appearance: first[x] = least position of id x, the
+    // first positions in increasing order get 0, 1, 2, ...
+    const long long ntot = (long long)tmp.size();
+    std::vector<int> first(ntmp, INT32_MAX);
+    parallel_for((int)ntot, [&](int lo, int hi, int) {
+        for (int t = lo; t < hi; ++t) {
+            int* f = &first[tmp[t]];
+            int cur = __atomic_load_n(f, __ATOMIC_RELAXED);
+            while (t < cur && !__atomic_compare_exchange_n(f, &cur, t, true, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {}
+        }
+    }, 16384);
+    std::vector<int> isfirst(ntot), rankpos(ntot + 1);
+    parallel_for((int)ntot, [&](int lo, int hi, int) {
+        for (int t = lo; t < hi; ++t) isfirst[t] = first[tmp[t]] == t;
+    }, 16384);
+    parallel_scan(isfirst.data(), (int)ntot, rankpos.data());
+    const int n = rankpos[ntot];
+    parallel_for((int)ntot, [&](int lo, int hi, int) {
+        for (int t = lo; t < hi; ++t) S.cell_nodes[t] = rankpos[first[tmp[t]]];
+    }, 16384);
     S.n = n;
     S.X.assign((size_t)n * d, 0.0);
     S.boundary.assign(n, 0);
     S.support.assign(n, {-1, -1, -1, -1});
     S.owner_cell.assign(n, -1);
-    for (int e = 0; e < m.nc; ++e) {
-        const int* v = &m.C[(size_t)e * nvpc];
-        for (int l = 0; l < nb; ++l) {
-            int id = S.cell_nodes[(size_t)e * nb + l];
-            if (S.owner_cell[id] >= 0) continue;
+    // node data from its first (cell, local node)
+    parallel_for((int)ntot, [&](int lo, int hi, int) {
+        for (int t = lo; t < hi; ++t) {
+            if (!isfirst[t]) continue;
+            const int e = t / nb, l = t % nb, id = rankpos[t];
+            const int* v = &m.C[(size_t)e * nvpc];
             S.owner_cell[id] = e;
             for (int c = 0; c < d; ++c) {
                 double x = 0;
@@ -669,9 +735,9 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
                 if (re.alpha[l][i] > 0) { sv[mm] = v[i]; sl[mm] = i; ++mm; }
             {
                 int tmpv[4];
-                for (int t = 0; t < mm; ++t) tmpv[t] = sv[t];
+                for (int q = 0; q < mm; ++q) tmpv[q] = sv[q];
                 std::sort(tmpv, tmpv + mm);
-                for (int t = 0; t < mm; ++t) S.support[id][t] = tmpv[t];
+                for (int q = 0; q < mm; ++q) S.support[id][q] = tmpv[q];
             }
             bool b;
             if (mm == 1) b = T.bvert[sv[0]];
@@ -680,7 +746,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
             else b = false;
             S.boundary[id] = b;
         }
-    }
+    }, 4096);
 }
 
 // --------------------------------------------------------------- assembly --
@@ -718,13 +784,7 @@ static CellGeom cell_geom(const Mesh& m, int e) {
 // node -> (cell, local index) adjacency
 static void node_cells(const Space& S, int nc, std::vector<int>& off, std::vector<int>& adj) {
     // (cells in increasing index for every node)
-    off.assign(S.n + 1, 0);
-    for (int x : S.cell_nodes) off[x + 1]++;
-    for (int i = 0; i < S.n; ++i) off[i + 1] += off[i];
-    adj.resize(S.cell_nodes.size());
-    std::vector<int> fill(off.begin(), off.end() - 1);
-    for (int e = 0; e < nc; ++e)
-        for (int l = 0; l < S.nb; ++l) adj[fill[S.cell_nodes[(size_t)e * S.nb + l]]++] = e * S.nb + l;
+    invert_index(S.cell_nodes.data(), (long long)nc * S.nb, S.n, off, adj);
 }
 
 // DoF maps and adjacency a device assembly needs (no matrices).
@@ -740,18 +800,27 @@ static void prepare_level(const Mesh& m, Level& L, const RefTensors& RT) {
     L.n_free = d * nVf + Q.n;
     node_cells(V, nc, L.voff, L.vadj);
     node_cells(Q, nc, L.qoff, L.qadj);
-    L.pint.assign(Q.n, 0.0);
-    for (int e = 0; e < nc; ++e) {
-        const double det = cell_geom(m, e).detabs;
-        for (int p = 0; p < nq; ++p) L.pint[Q.cell_nodes[(size_t)e * nq + p]] += det * RT.qint[p];
-    }
-    L.cell_center.assign((size_t)nc * d, 0.0);
-    for (int e = 0; e < nc; ++e)
-        for (int cc = 0; cc < d; ++cc) {
-            double s = 0;
-            for (int i = 0; i <= d; ++i) s += m.X[(size_t)m.C[(size_t)e * (d + 1) + i] * d + cc];
-            L.cell_center[(size_t)e * d + cc] = s / (d + 1);
+    std::vector<double> det(nc);
+    L.cell_center.resize((size_t)nc * d);
+    parallel_for(nc, [&](int lo, int hi, int) {
+        for (int e = lo; e < hi; ++e) {
+            det[e] = cell_geom(m, e).detabs;
+            for (int cc = 0; cc < d; ++cc) {
+                double s = 0;
+                for (int i = 0; i <= d; ++i) s += m.X[(size_t)m.C[(size_t)e * (d + 1) + i] * d + cc];
+                L.cell_center[(size_t)e * d + cc] = s / (d + 1);
+            }
         }
+    }, 1024);
+    // int psi_q: contributions of the incident cells in increasing order
+    L.pint.assign(Q.n, 0.0);
+    parallel_for(Q.n, [&](int lo, int hi, int) {
+        for (int q = lo; q < hi; ++q) {
+            double s = 0.0;
+            for (int x = L.qoff[q]; x < L.qoff[q + 1]; ++x) s += det[L.qadj[x] / nq] * RT.qint[L.qadj[x] % nq];
+            L.pint[q] = s;
+        }
+    }, 4096);
 }
 
 static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const std::vector<double>& nu,
@@ -1029,56 +1098,65 @@ centers:
 // cells around it).
 static void build_patches(const Mesh& m, const Topology& T, Level& L) {
     const int d = m.d, nb = L.V.nb, nq = L.Q.nb;
-    std::vector<std::vector<int>> P(m.nv);
-    std::vector<int> NV(m.nv, 0);
-    const int NT = Pool::get().size();
-    std::vector<std::vector<int>> stV(NT, std::vector<int>(L.V.n, -1)), stQ(NT, std::vector<int>(L.Q.n, -1));
-    parallel_for(m.nv, [&](int lo, int hi, int t) {
-        auto& sv = stV[t];
-        auto& sq = stQ[t];
-        std::vector<int> vel, pre;
-        for (int v = lo; v < hi; ++v) {
-            vel.clear();
-            pre.clear();
-            for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
-                int e = T.v2c[a];
-                for (int l = 0; l < nb; ++l) {
-                    int j = L.V.cell_nodes[(size_t)e * nb + l];
-                    if (sv[j] == v || L.vfree[j] < 0) continue;
-                    sv[j] = v;
-                    vel.push_back(L.vfree[j]);
-                }
-                for (int l = 0; l < nq; ++l) {
-                    int q = L.Q.cell_nodes[(size_t)e * nq + l];
-                    if (sq[q] == v) continue;
-                    sq[q] = v;
-                    if (L.family == 0) {
-                        const auto& s = L.Q.support[q];
-                        bool in = false;
-                        for (int t2 = 0; t2 < 4; ++t2) in |= (s[t2] == v);
-                        if (!in) continue;
-                    }
-                    pre.push_back(q);
-                }
+    // per vertex: the free velocity nodes of the cells around it, then the
+    // pressure nodes of its star (TH: nodes whose entity has the vertex in
+    // its closure) or of those cells (SV), each group sorted and unique
+    std::vector<int> NV(m.nv, 0), NP(m.nv, 0);
+    FlatLists lists = build_lists(m.nv, [&](int v, std::vector<int>& out, int) {
+        const size_t s0 = out.size();
+        for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
+            const int e = T.v2c[a];
+            for (int l = 0; l < nb; ++l) {
+                const int j = L.V.cell_nodes[(size_t)e * nb + l];
+                if (L.vfree[j] >= 0) out.push_back(L.vfree[j]);
             }
-            std::sort(vel.begin(), vel.end());
-            std::sort(pre.begin(), pre.end());
-            auto& out = P[v];
-            NV[v] = (int)vel.size();
-            for (int c = 0; c < d; ++c)
-                for (int x : vel) out.push_back(c * L.nVf + x);
-            for (int q : pre) out.push_back(d * L.nVf + q);
         }
+        std::sort(out.begin() + s0, out.end());
+        out.erase(std::unique(out.begin() + s0, out.end()), out.end());
+        const size_t s1 = out.size();
+        for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
+            const int e = T.v2c[a];
+            for (int l = 0; l < nq; ++l) {
+                const int q = L.Q.cell_nodes[(size_t)e * nq + l];
+                if (L.family == 0) {
+                    const auto& sp = L.Q.support[q];
+                    bool in = false;
+                    for (int t2 = 0; t2 < 4; ++t2) in |= (sp[t2] == v);
+                    if (!in) continue;
+                }
+                out.push_back(q);
+            }
+        }
+        std::sort(out.begin() + s1, out.end());
+        out.erase(std::unique(out.begin() + s1, out.end()), out.end());
+        NV[v] = (int)(s1 - s0);
+        NP[v] = (int)(out.size() - s1);
     });
-    L.patch_off.assign(1, 0);
-    L.patch_dofs.clear();
-    L.patch_nv.clear();
-    for (int v = 0; v < m.nv; ++v) {
-        if (P[v].empty()) continue;
-        L.patch_dofs.insert(L.patch_dofs.end(), P[v].begin(), P[v].end());
-        L.patch_off.push_back((int)L.patch_dofs.size());
-        L.patch_nv.push_back(NV[v]);
-    }
+    // vertices with a non-empty patch, in order; patch p lists d blocks of its
+    // velocity nodes (one per component), then its pressures
+    std::vector<int> vid;
+    vid.reserve(m.nv);
+    for (int v = 0; v < m.nv; ++v)
+        if (NV[v] + NP[v] > 0) vid.push_back(v);
+    const int np = (int)vid.size();
+    std::vector<int> sz(np);
+    for (int p = 0; p < np; ++p) sz[p] = d * NV[vid[p]] + NP[vid[p]];
+    L.patch_off.resize(np + 1);
+    parallel_scan(sz.data(), np, L.patch_off.data());
+    L.patch_dofs.resize(L.patch_off[np]);
+    L.patch_nv.resize(np);
+    parallel_for(np, [&](int lo, int hi, int) {
+        for (int p = lo; p < hi; ++p) {
+            const int v = vid[p];
+            const int* src = lists.begin(v);
+            int* dst = L.patch_dofs.data() + L.patch_off[p];
+            const int nvv = NV[v];
+            for (int c = 0; c < d; ++c)
+                for (int x = 0; x < nvv; ++x) *dst++ = c * L.nVf + src[x];
+            for (int x = 0; x < NP[v]; ++x) *dst++ = d * L.nVf + src[nvv + x];
+            L.patch_nv[p] = nvv;
+        }
+    }, 512);
 }
 
 // Finite-element interpolation (Sec. 3.1): the coarse basis evaluated at the
@@ -1190,7 +1268,7 @@ static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Le
 }
 
 void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell, Hierarchy& H,
-                     const std::function<void(int)>& on_level) {
+                     const std::function<void(int, int)>& on_level) {
     double t0 = now_ms();
     const int d = coarse.d;
     if (d != 2 && d != 3) throw std::invalid_argument("dim must be 2 or 3");
@@ -1228,8 +1306,14 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
             nus[i + 1] = s;
         }
     }
+    // topologies on demand: the coarsest mesh's now, the others when their
+    // first level is built (so that a coarsest-first build starts at once)
     std::vector<Topology> topo(nm);
-    for (int i = 0; i < nm; ++i) build_topology(H.meshes[i], topo[i]);
+    std::vector<char> have_topo(nm, 0);
+    auto need_topo = [&](int i) {
+        if (!have_topo[i]) { build_topology(H.meshes[i], topo[i]); have_topo[i] = 1; }
+    };
+    need_topo(nm - 1);
     double t1 = now_ms();
     H.t_mesh_ms = t1 - t0;
     // levels: p-levels on the finest mesh, then the hMG degree on every mesh
@@ -1264,6 +1348,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         if (L.family == 1 && L.k < d) throw std::invalid_argument("Scott-Vogelius needs k >= dim");
         const Mesh& m = H.meshes[L.mesh_index];
         double ta = now_ms();
+        need_topo(L.mesh_index);
         const RefElement& rv = ref(d, L.k);
         const RefElement& rq = ref(d, L.k - 1);
         build_space(m, topo[L.mesh_index], rv, true, L.V);
@@ -1279,13 +1364,22 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         if (L.host_matrices) assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
         else prepare_level(m, L, RT);
         double tc = now_ms();
+        if (on_level) {
+            on_level((int)l, 0);
+            const double tcb = now_ms();
+            H.t_callbacks_ms += tcb - tc;
+            tc = tcb;
+        }
         if (l + 1 < ls.size()) build_patches(m, topo[L.mesh_index], L);
         H.t_spaces_ms += tb - ta;
         H.t_matrices_ms += tc - tb;
         H.t_patches_ms += now_ms() - tc;
+        if (const char* tr = std::getenv("STOKES_TRACE"); tr && tr[0] == '1')
+            std::fprintf(stderr, "[sfem] level %zu: spaces %.3f  operator data %.3f  patches %.3f ms\n", l, tb - ta,
+                         tc - tb, now_ms() - tc);
         if (on_level) {
             const double tcb = now_ms();
-            on_level((int)l);
+            on_level((int)l, 1);
             H.t_callbacks_ms += now_ms() - tcb;
         }
     }

@@ -132,14 +132,20 @@ struct Hierarchy {
 };
 
 // Build the whole host hierarchy; throws std::runtime_error on invalid input.
-// on_level(l), if given, runs as soon as level l's spaces, operator and
-// patches exist (levels in the order that spec.coarsest_first selects;
-// the transfers are built after every level), so the caller can start device
-// work on it while the host continues.
+// on_level(l, stage), if given, runs twice per level: stage 0 once its
+// spaces and operator data exist, stage 1 once its patches exist too (levels
+// in the order that spec.coarsest_first selects; the transfers are built
+// after every level), so the caller can start device work on each part
+// while the host continues.
 void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell,
-                     Hierarchy& H, const std::function<void(int)>& on_level = {});
+                     Hierarchy& H, const std::function<void(int, int)>& on_level = {});
 
 int num_threads();
+
+// For idx[0..m) with values in [0, n): off[0..n] and pos[0..m) list, for
+// every value, the positions q where it occurs, in increasing order
+// (parallel counting sort).
+void invert_index(const int* idx, long long m, int n, std::vector<int>& off, std::vector<int>& pos);
 
 // memcpy split over the host worker pool
 void parallel_copy(void* dst, const void* src, size_t bytes);

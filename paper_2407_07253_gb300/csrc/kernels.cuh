@@ -39,7 +39,22 @@ __global__ void __launch_bounds__(256) spmv_csr(int nrows, const int* __restrict
     if (row >= nrows) return;   // whole LANES-group exits together (LANES divides 32)
     const int s = __ldg(rp + row), e = __ldg(rp + row + 1);
     T acc = 0;
-    for (int p = s + lane; p < e; p += LANES) acc += __ldg(av + p) * __ldg(x + __ldg(ci + p));
+    // four entries per lane per round: their column and value loads, then
+    // their x loads, are issued together (a row of ~40 entries takes one
+    // round at 16 lanes instead of a chain of three dependent load pairs)
+    for (int base = s + lane; base < e; base += 4 * LANES) {
+        int c[4];
+        T a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = base + u * LANES;
+            const bool ok = p < e;
+            c[u] = ok ? __ldg(ci + p) : 0;
+            a[u] = ok ? __ldg(av + p) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += a[u] * __ldg(x + c[u]);
+    }
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LANES);
     if (lane == 0) {
@@ -92,6 +107,15 @@ __global__ void maxpy_normalise(int n, int m, const double* __restrict__ V, long
 // w[k] += sign * sum_i h[i] V[i][k]
 __global__ void maxpy(int n, int m, const double* __restrict__ V, long long ldv, const double* __restrict__ h,
                       double sign, double* __restrict__ w);
+
+// ------------------------------------------------------ DoF -> slot map ---
+// slot_count (cnt zeroed) -> exclusive scan of cnt into soff[0..n] ->
+// slot_fill (cur zeroed) -> slot_sort: sidx lists every DoF's slots in
+// increasing order, wt[j] = 1 / multiplicity.
+__global__ void slot_count(long long nent, const int* __restrict__ pdofs, int* __restrict__ cnt);
+__global__ void slot_fill(long long nent, const int* __restrict__ pdofs, const int* __restrict__ soff, int* __restrict__ cur,
+                          int* __restrict__ sidx);
+__global__ void slot_sort(int n, const int* __restrict__ soff, int* __restrict__ sidx, double* __restrict__ wt);
 
 // ------------------------------------------------------------- patches ---
 // Dense K_i (row-major n_i x n_i, FP64) gathered from the CSR of K: one CTA
@@ -173,6 +197,16 @@ __global__ void gj_step_pivot(int n, int k, double* __restrict__ A, int* __restr
                               double* __restrict__ colk, int* __restrict__ status);
 __global__ void gj_step_eliminate(int n, int k, double* __restrict__ A, const double* __restrict__ colk);
 __global__ void gj_unpivot_rows(int n, double* __restrict__ A, const int* __restrict__ ipiv);
+// Whole in-place Gauss-Jordan inverse (partial pivoting, row swaps in ipiv)
+// of one n x n matrix by one cluster of GJC_CTAS CTAs holding its rows in
+// shared memory: (ceil(n / GJC_CTAS) + 2) n + 2 ceil(n / GJC_CTAS) doubles
+// of dynamic shared memory per CTA; follow with gj_unpivot_rows.
+constexpr int GJC_CTAS = 16, GJC_THREADS = 512;
+__host__ __device__ inline long long gj_cluster_smem_doubles(int n) {
+    const long long R = (n + GJC_CTAS - 1) / GJC_CTAS;
+    return (R + 2) * n + 2 * R;
+}
+__global__ void gj_cluster_inverse(int n, double* __restrict__ A, int* __restrict__ ipiv, int* __restrict__ status);
 // y[i] = sum_j A[i][j] x[j] for i < nout (row-major, leading dimension lda)
 __global__ void dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A, const double* __restrict__ x,
                            double* __restrict__ y);

@@ -262,7 +262,7 @@ struct stokes_mg {
     int* c_status = nullptr;
     cudaStream_t s_up = nullptr, s_coarse = nullptr;
     std::vector<KrylovWS> kws;           // per relaxed level (level 0 aliases the FGMRES buffers)
-    std::vector<cudaStream_t> s_lvl;     // per level (level 0 runs on the caller's stream)
+    std::vector<cudaStream_t> s_lvl;     // setup compute stream of each relaxed level
     std::vector<double*> mesh_X;         // device vertex coordinates per mesh
     std::vector<int*> mesh_C;            // device cells per mesh
     std::vector<void*> allocs;
@@ -824,7 +824,9 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
 // ---------------------------------------------------------------- setup --
 void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s);
 
-void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
+// Operator part of a level (its CSR, or the inputs of the device assembly)
+// and the level's work vectors.
+void upload_level_operator(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     const sfem::Level& HL = h->H.levels[li];
     DevLevel& l = h->L[li];
     l.n = HL.n_free;
@@ -836,7 +838,20 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         upload_assembly_inputs(h, li, want32, s);
     }
     trace("upload K", li, tt);
-    tt = host_ms();
+    l.b64 = halloc<double>(h, l.n); l.e64 = halloc<double>(h, l.n); l.r64 = halloc<double>(h, l.n);
+    l.d64 = halloc<double>(h, l.n); l.t64 = halloc<double>(h, l.n); l.u64 = halloc<double>(h, l.n);
+    if (want32) {
+        l.b32 = halloc<float>(h, l.n); l.e32 = halloc<float>(h, l.n); l.r32 = halloc<float>(h, l.n);
+        l.d32 = halloc<float>(h, l.n); l.t32 = halloc<float>(h, l.n); l.u32 = halloc<float>(h, l.n);
+    }
+}
+
+// Patch part of a relaxed level: index sets, offsets of the dense blocks and
+// inverses, partition-of-unity weights and the DoF -> slot map.
+void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
+    const sfem::Level& HL = h->H.levels[li];
+    DevLevel& l = h->L[li];
+    double tt = host_ms();
     const bool last = li + 1 == (int)h->H.levels.size();
     if (!last) {
         l.npatch = (int)HL.patch_off.size() - 1;
@@ -853,9 +868,11 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         l.nsq = moff[l.npatch];
         l.ninv64 = o64[l.npatch];
         l.ninv32 = o32[l.npatch];
+        trace("patch offsets (host)", li, tt);
         l.poff = hupload(h, HL.patch_off, s);
         l.pdofs = hupload(h, HL.patch_dofs, s);
         l.pnv = hupload(h, HL.patch_nv, s);
+        trace("patch lists uploaded", li, tt);
         std::vector<long long> scoff(l.npatch + 1, 0);
         for (int p = 0; p < l.npatch; ++p) {
             const long long sc = skern::saddle_scratch(HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p]);
@@ -868,19 +885,25 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         l.ioff64 = hupload(h, o64, s);
         l.ioff32 = hupload(h, o32, s);
         // partition of unity W_i = diag(1/m_j) and the DoF -> slot map
-        std::vector<int> mult(l.n, 0);
-        for (int x : HL.patch_dofs) mult[x]++;
-        std::vector<double> wt(l.n);
-        for (int j = 0; j < l.n; ++j) wt[j] = mult[j] ? 1.0 / mult[j] : 0.0;
-        std::vector<int> soff(l.n + 1, 0), sidx(l.nent);
-        for (int j = 0; j < l.n; ++j) soff[j + 1] = soff[j] + mult[j];
-        std::vector<int> fill(soff.begin(), soff.end() - 1);
-        for (long long q = 0; q < l.nent; ++q) sidx[fill[HL.patch_dofs[q]]++] = (int)q;
-        trace("patch maps (host)", li, tt);
+        trace("block offsets uploaded", li, tt);
+        // slots of every DoF in increasing order (the pull scatter's order)
+        // and the weights W_i = 1 / multiplicity, built on the device
+        l.wt64 = halloc<double>(h, l.n);
+        l.soff = halloc<int>(h, (size_t)l.n + 1);
+        l.sidx = halloc<int>(h, l.nent);
+        {
+            const int n = l.n;
+            int* scr = palloc<int>(h->device, 2 * (size_t)n + (n + 1023) / 1024 + 2, s);
+            int *cnt = scr, *cur = scr + n, *stmp = scr + 2 * n;
+            CK(cudaMemsetAsync(scr, 0, sizeof(int) * 2 * (size_t)n, s));
+            launch(h, -1, s, [&] { skern::slot_count<<<grid_for(l.nent), 256, 0, s>>>(l.nent, l.pdofs, cnt); });
+            launch(h, -1, s, [&] { sasm::scan_rows(cnt, n, l.soff, stmp, s); });
+            launch(h, -1, s, [&] { skern::slot_fill<<<grid_for(l.nent), 256, 0, s>>>(l.nent, l.pdofs, l.soff, cur, l.sidx); });
+            launch(h, -1, s, [&] { skern::slot_sort<<<grid_for(n), 256, 0, s>>>(n, l.soff, l.sidx, l.wt64); });
+            CK(cudaFreeAsync(scr, s));
+        }
+        trace("patch maps", li, tt);
         tt = host_ms();
-        l.wt64 = hupload(h, wt, s);
-        l.soff = hupload(h, soff, s);
-        l.sidx = hupload(h, sidx, s);
         l.Y64 = halloc<double>(h, l.nent);
         l.inv64 = halloc<double>(h, l.ninv64);
         if (want32) {
@@ -892,13 +915,6 @@ void upload_level(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         }
     }
     trace("patch uploads + allocs", li, tt);
-    tt = host_ms();
-    l.b64 = halloc<double>(h, l.n); l.e64 = halloc<double>(h, l.n); l.r64 = halloc<double>(h, l.n);
-    l.d64 = halloc<double>(h, l.n); l.t64 = halloc<double>(h, l.n); l.u64 = halloc<double>(h, l.n);
-    if (want32) {
-        l.b32 = halloc<float>(h, l.n); l.e32 = halloc<float>(h, l.n); l.r32 = halloc<float>(h, l.n);
-        l.d32 = halloc<float>(h, l.n); l.t32 = halloc<float>(h, l.n); l.u32 = halloc<float>(h, l.n);
-    }
 }
 
 // Mesh, DoF maps, adjacency and reference tensors of a level whose K is
@@ -1107,7 +1123,8 @@ void finish_patches(stokes_mg* h, cudaStream_t s) {
 }
 
 // Bordered coarse matrix (zero-mean pressure constraint, Sec. 2) inverted in
-// place by one Gauss-Jordan step per pivot on stream s (no wait).
+// place on stream s (no wait): by one thread-block cluster when its rows fit
+// in the cluster's shared memory, else by one Gauss-Jordan step per pivot.
 void upload_coarse(stokes_mg* h, cudaStream_t su) {
     const sfem::Level& C = h->H.levels.back();
     const int n = C.n_free, nb = n + 1;
@@ -1131,8 +1148,61 @@ void upload_coarse(stokes_mg* h, cudaStream_t su) {
 }
 
 // coarse factorisation steps on stream s (the upload must be ordered before)
+// One cluster of skern::GJC_CTAS CTAs can hold the bordered coarse matrix in
+// shared memory (and the device runs clusters of that size)?
+bool coarse_cluster_ok(stokes_mg* h, int nb, size_t* smem_out) {
+    const size_t smem = (size_t)skern::gj_cluster_smem_doubles(nb) * sizeof(double);
+    int dev_max = 0;
+    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (smem + 1024 > (size_t)dev_max) return false;
+    if (cudaFuncSetAttribute(skern::gj_cluster_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(skern::gj_cluster_inverse, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = skern::GJC_CTAS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(skern::GJC_CTAS);
+    cfg.blockDim = dim3(skern::GJC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, skern::gj_cluster_inverse, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *smem_out = smem;
+    return nclusters > 0;
+}
+
 void launch_coarse(stokes_mg* h, cudaStream_t s) {
     const int nb = h->nc + 1;
+    size_t smem = 0;
+    if (coarse_cluster_ok(h, nb, &smem)) {
+        // the whole factorisation in one cluster launch
+        launch(h, -1, s, [&] {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = skern::GJC_CTAS;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(skern::GJC_CTAS);
+            cfg.blockDim = dim3(skern::GJC_THREADS);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CK(cudaLaunchKernelEx(&cfg, skern::gj_cluster_inverse, nb, h->Cinv, h->c_ipiv, h->c_status));
+        });
+        launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
+        return;
+    }
     const long long tot = (long long)nb * nb;
     const int egrid = (int)std::min<long long>((tot + 255) / 256, 152LL * 8);
     for (int k = 0; k < nb; ++k) {
@@ -1404,7 +1474,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         double t_cb_upload = 0;
         std::unique_ptr<Launcher> launcher;
         double t_launch = 0;
-        std::function<void(int)> on_level;
+        std::function<void(int, int)> on_level;
         if (!o.host_only) {
             // level-by-level pipeline: upload on s_up, then the patch
             // inversion (or the coarse factorisation) starts on the device
@@ -1414,20 +1484,38 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
             // inversion that occupies every SM
             int prio_lo = 0, prio_hi = 0;
             CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-            CK(cudaStreamCreateWithPriority(&h->s_up, cudaStreamNonBlocking, prio_hi));
-            // the coarse Gauss-Jordan is a chain of small latency-bound
-            // launches: highest priority, so that its blocks are scheduled
-            // ahead of the waiting blocks of the patch kernels
-            CK(cudaStreamCreateWithPriority(&h->s_coarse, cudaStreamNonBlocking, prio_hi));
-            // relaxed levels below the finest share a second compute stream,
-            // so their inversion and lambda_max estimate overlap level 0's
-            // (one step above the default priority: their blocks are placed
-            // between level 0's patch-inversion blocks instead of after them)
-            cudaStream_t s_small = nullptr;
-            CK(cudaStreamCreateWithPriority(&s_small, cudaStreamNonBlocking, std::max(prio_hi, prio_lo - 1)));
-            h->s_lvl.push_back(s_small);
+            // (a greater priority is a numerically smaller value)
+            auto prio = [&](int steps_below_top) { return std::min(prio_lo, prio_hi + steps_below_top); };
+            CK(cudaStreamCreateWithPriority(&h->s_up, cudaStreamNonBlocking, prio(0)));
+            // level 0 (the critical path: largest inversion, then its
+            // lambda_max estimate) runs on its own stream one step below the
+            // uploads; the coarse Gauss-Jordan, a chain of small latency-bound
+            // launches, at the same priority so that its blocks are placed
+            // between the patch-inversion blocks; the other relaxed levels
+            // one step lower, each on its own stream so that their inversions
+            // and lambda_max estimates overlap each other and level 0's
+            CK(cudaStreamCreateWithPriority(&h->s_coarse, cudaStreamNonBlocking, prio(1)));
+            const int prio_l0 = prio(1), prio_small = prio(2);
+            {
+                // level 0's stream starts after whatever the caller queued on s
+                h->s_lvl.assign(1, nullptr);
+                CK(cudaStreamCreateWithPriority(&h->s_lvl[0], cudaStreamNonBlocking, prio_l0));
+                cudaEvent_t ev;
+                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                CK(cudaEventRecord(ev, s));
+                CK(cudaStreamWaitEvent(h->s_lvl[0], ev, 0));
+                CK(cudaEventDestroy(ev));
+            }
             launcher.reset(new Launcher());
-            on_level = [&](int li) {
+            // order the launcher's work on `target` after everything queued on s_up so far
+            auto after_uploads = [](stokes_mg* hp, cudaStream_t target) {
+                cudaEvent_t ev;
+                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                CK(cudaEventRecord(ev, hp->s_up));
+                CK(cudaStreamWaitEvent(target, ev, 0));
+                CK(cudaEventDestroy(ev));
+            };
+            on_level = [&](int li, int stage) {
                 const double tu = host_ms();
                 stokes_mg* hp = h.get();
                 const int nlv = (int)hp->H.levels.size();
@@ -1435,38 +1523,50 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                     hp->L.assign(nlv, DevLevel());
                     hp->kws.resize(nlv);      // sized once: launches keep pointers into it
                     alloc_hess(hp, hp->s_up);
+                    hp->s_lvl.resize(nlv, nullptr);
+                    for (int x = 1; x + 1 < nlv; ++x)
+                        CK(cudaStreamCreateWithPriority(&hp->s_lvl[x], cudaStreamNonBlocking, prio_small));
                 }
-                // uploads on this thread; level 0 then computes on the caller's
-                // stream, the other relaxed levels on s_lvl[0], the coarse
-                // level on s_coarse
-                cudaStream_t target = li == 0 ? s : (li + 1 < nlv ? hp->s_lvl[0] : hp->s_coarse);
-                if (li + 1 < nlv) {
-                    upload_level(hp, li, want32, hp->s_up);
+                // uploads on this thread; relaxed level l then computes on
+                // s_lvl[l], the coarse level on s_coarse
+                const bool relaxed = li + 1 < nlv;
+                cudaStream_t target = relaxed ? hp->s_lvl[li] : hp->s_coarse;
+                if (stage == 0) {
+                    // operator: the device assembly starts while the host
+                    // builds the patches
+                    if (!relaxed) return;
+                    upload_level_operator(hp, li, want32, hp->s_up);
+                    mark(hp, "L" + std::to_string(li) + " operator uploaded", hp->s_up);
+                    after_uploads(hp, target);
+                    t_cb_upload += host_ms() - tu;
+                    launcher->submit([hp, li, target] {
+                        CK(cudaSetDevice(hp->device));
+                        mark(hp, "L" + std::to_string(li) + " device start", target);
+                        assemble_on_device(hp, li, target);
+                        mark(hp, "L" + std::to_string(li) + " assembled", target);
+                    });
+                    return;
+                }
+                if (relaxed) {
+                    upload_level_patches(hp, li, want32, hp->s_up);
                     const double tk = host_ms();
                     if (li == 0) alloc_krylov(hp, hp->s_up);
                     else alloc_level_krylov(hp, li, hp->s_up);
                     trace("krylov buffers", li, tk);
                 } else {
-                    upload_level(hp, li, want32, hp->s_up);
+                    upload_level_operator(hp, li, want32, hp->s_up);
                     upload_coarse(hp, hp->s_up);
                 }
                 mark(hp, "L" + std::to_string(li) + " uploaded", hp->s_up);
-                cudaEvent_t ev;
-                CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-                CK(cudaEventRecord(ev, hp->s_up));
-                CK(cudaStreamWaitEvent(target, ev, 0));
-                CK(cudaEventDestroy(ev));
+                after_uploads(hp, target);
                 t_cb_upload += host_ms() - tu;
                 trace("level callback total", li, tu);
                 // kernel launches on the launcher thread
-                launcher->submit([hp, li, nlv, s, target, &o, &t_launch] {
+                launcher->submit([hp, li, nlv, target, &o, &t_launch] {
                     const double tl = host_ms();
                     CK(cudaSetDevice(hp->device));
                     if (li + 1 < nlv) {
                         const cudaStream_t sl = target;
-                        mark(hp, "L" + std::to_string(li) + " device start", sl);
-                        assemble_on_device(hp, li, sl);
-                        mark(hp, "L" + std::to_string(li) + " assembled", sl);
                         launch_patches(hp, li, sl);
                         mark(hp, "L" + std::to_string(li) + " inverted", sl);
                         // lambda_max estimate right behind the inversion (same stream)
