@@ -60,33 +60,39 @@ __global__ void mdot_final(int nblocks, int m, const double* __restrict__ partia
 
 // Fused multi-dots: every block writes its partial sums, the last block to
 // finish (atomic ticket) adds them in a fixed order, so results are bitwise
-// reproducible.  Launched with MDOT_BLOCKS blocks of 512 threads.
+// reproducible.  Launched with MDOT_BLOCKS blocks of MDOT_THREADS threads.
 
-// block partial sums of a[0..m) (and, if with_extra, of `extra` as column
-// m) into partial[blockIdx.x][0..m + with_extra)
+// Block partial sums of a[0..m) (and, if with_extra, of `extra` as column
+// m) into partial[blockIdx.x][0..m + with_extra).  The threads' values go to
+// shared memory 16 columns at a time and one warp sums a column (8 adds per
+// lane, then 5 shuffle steps): FP64 adds are scarce on this GPU, and this
+// takes ~13 warp instructions per column instead of 5 per warp and column
+// for a shuffle tree in every warp.
 template <int MM>
 __device__ __forceinline__ void mdot_block_partials(int m, const double (&a)[MM], double extra, bool with_extra,
                                                     double* partial) {
-    __shared__ double red[16][MDOT_MAX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int i = 0; i < MM; ++i) {
-        if (i >= m) break;
-        double v = a[i];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][i] = v;
-    }
-    if (with_extra) {
-        double v = extra;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][m] = v;
-    }
-    __syncthreads();
+    constexpr int NT = MDOT_THREADS, CH = 16;
+    __shared__ double red[CH][NT];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = NT >> 5;
     const int mc = m + (with_extra ? 1 : 0);
-    if (threadIdx.x < mc) {
-        double s = 0;
-        for (int wv = 0; wv < nw; ++wv) s += red[wv][threadIdx.x];
-        partial[(long long)blockIdx.x * mc + threadIdx.x] = s;
+#pragma unroll
+    for (int c0 = 0; c0 < MM + 1; c0 += CH) {
+        if (c0 >= mc) break;
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int c = c0 + q;
+            if (c < MM && c < m) red[q][t] = a[c < MM ? c : 0];
+            else if (with_extra && c == m) red[q][t] = extra;
+        }
+        __syncthreads();
+        for (int q = warp; q < CH && c0 + q < mc; q += nw) {
+            double sum = 0.0;
+#pragma unroll
+            for (int j = 0; j < NT / 32; ++j) sum += red[q][lane + 32 * j];
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            if (lane == 0) partial[(long long)blockIdx.x * mc + c0 + q] = sum;
+        }
+        __syncthreads();
     }
 }
 
@@ -101,25 +107,27 @@ __device__ __forceinline__ bool mdot_last_block(unsigned int* ticket) {
     return last;
 }
 
-// last block: out[i] = sum_b partial[b][i] (i < mcols, row stride mcols)
-// over the grid's blocks in a fixed order (16 threads per output, strided,
-// then a fixed shuffle tree), with acc[i] += out[i] for i < macc; the
-// partials are read from L2 (ld.global.cg) with all loads issued together
+// last block: out[i] = sum_b partial[b][i] (i < mcols <= 32, row stride
+// mcols) over the grid's blocks in a fixed order (MDOT_THREADS / 32 threads
+// per output, strided, then a fixed shuffle tree), with acc[i] += out[i] for
+// i < macc; the partials are read from L2 (ld.global.cg), all loads issued
+// together
 __device__ __forceinline__ void mdot_reduce_partials(int mcols, int macc, const double* partial, double* out,
                                                      double* acc, int sqrt_out, unsigned int* ticket) {
-    const int i = threadIdx.x >> 4, sub = threadIdx.x & 15;
+    constexpr int G = MDOT_THREADS / 32;
+    const int i = threadIdx.x / G, sub = threadIdx.x % G;
     double s = 0;
     if (i < mcols) {
-        double t[(MDOT_BLOCKS + 15) / 16];
+        double t[(MDOT_BLOCKS + G - 1) / G];
 #pragma unroll
-        for (int q = 0; q < (MDOT_BLOCKS + 15) / 16; ++q) {
-            const int b = sub + 16 * q;
+        for (int q = 0; q < (MDOT_BLOCKS + G - 1) / G; ++q) {
+            const int b = sub + G * q;
             t[q] = b < (int)gridDim.x ? __ldcg(partial + (long long)b * mcols + i) : 0.0;
         }
 #pragma unroll
-        for (int q = 0; q < (MDOT_BLOCKS + 15) / 16; ++q) s += t[q];
+        for (int q = 0; q < (MDOT_BLOCKS + G - 1) / G; ++q) s += t[q];
     }
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, 16);
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
     if (i < mcols && sub == 0) {
         if (acc && i < macc) acc[i] += s;
         out[i] = (sqrt_out && i == 0) ? sqrt(s) : s;
@@ -130,7 +138,7 @@ __device__ __forceinline__ void mdot_reduce_partials(int mcols, int macc, const 
 // The accumulators are unrolled to MM (>= m): FP64 FMAs are scarce on this
 // GPU, so the host picks the smallest MM in {4, 8, 16, 32} that holds m.
 template <int MM>
-__global__ void __launch_bounds__(512) mdot_fused_t(int n, int m, const double* __restrict__ V, long long ldv,
+__global__ void __launch_bounds__(MDOT_THREADS) mdot_fused_t(int n, int m, const double* __restrict__ V, long long ldv,
                                                     const double* __restrict__ w, double* __restrict__ partial,
                                                     unsigned int* __restrict__ ticket, double* __restrict__ out,
                                                     double* __restrict__ acc, int sqrt_out) {
@@ -150,10 +158,10 @@ __global__ void __launch_bounds__(512) mdot_fused_t(int n, int m, const double* 
 
 void mdot_fused(int n, int m, const double* V, long long ldv, const double* w, double* partial, unsigned int* ticket,
                 double* out, double* acc, int sqrt_out, cudaStream_t s) {
-    if (m <= 4) mdot_fused_t<4><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
-    else if (m <= 8) mdot_fused_t<8><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
-    else if (m <= 16) mdot_fused_t<16><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
-    else mdot_fused_t<32><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    if (m <= 4) mdot_fused_t<4><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    else if (m <= 8) mdot_fused_t<8><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    else if (m <= 16) mdot_fused_t<16><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
+    else mdot_fused_t<32><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, w, partial, ticket, out, acc, sqrt_out);
 }
 
 // Second classical Gram-Schmidt pass fused with the first pass's update:
@@ -161,7 +169,7 @@ void mdot_fused(int n, int m, const double* V, long long ldv, const double* w, d
 //   out[0..m) = V^T w,  out[m] = w^T w  (of the updated w),  acc[i] += out[i].
 // m <= MDOT_MAX - 1.
 template <int MM>
-__global__ void __launch_bounds__(512) maxpy_mdot_t(int n, int m, const double* __restrict__ V, long long ldv,
+__global__ void __launch_bounds__(MDOT_THREADS) maxpy_mdot_t(int n, int m, const double* __restrict__ V, long long ldv,
                                                     const double* __restrict__ h, double* __restrict__ w,
                                                     double* __restrict__ partial, unsigned int* __restrict__ ticket,
                                                     double* __restrict__ out, double* __restrict__ acc) {
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(512) maxpy_mdot_t(int n, int m, const double* 
     for (int i = 0; i < MM; ++i) a[i] = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         double wk = w[k];
-        if constexpr (MM <= 8) {
+        if constexpr (MM <= 16) {
             // few vectors: keep V[.][k] in registers between the two uses
             double vk[MM];
 #pragma unroll
@@ -202,10 +210,10 @@ __global__ void __launch_bounds__(512) maxpy_mdot_t(int n, int m, const double* 
 
 void maxpy_mdot(int n, int m, const double* V, long long ldv, const double* h, double* w, double* partial,
                 unsigned int* ticket, double* out, double* acc, cudaStream_t s) {
-    if (m <= 4) maxpy_mdot_t<4><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
-    else if (m <= 8) maxpy_mdot_t<8><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
-    else if (m <= 16) maxpy_mdot_t<16><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
-    else maxpy_mdot_t<31><<<MDOT_BLOCKS, 512, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    if (m <= 4) maxpy_mdot_t<4><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    else if (m <= 8) maxpy_mdot_t<8><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    else if (m <= 16) maxpy_mdot_t<16><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
+    else maxpy_mdot_t<31><<<MDOT_BLOCKS, MDOT_THREADS, 0, s>>>(n, m, V, ldv, h, w, partial, ticket, out, acc);
 }
 
 // Last update of classical Gram-Schmidt, normalised:

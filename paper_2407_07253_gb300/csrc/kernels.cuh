@@ -93,12 +93,12 @@ __global__ void mdot_partial(int n, int m, const double* __restrict__ V, long lo
 __global__ void mdot_final(int nblocks, int m, const double* __restrict__ partial, double* __restrict__ out,
                            double* __restrict__ acc, int sqrt_out);
 // Same reduction in one launch (last block finishes in a fixed order);
-// MDOT_BLOCKS blocks of 512 threads; ticket must start at 0 and is reset.
-constexpr int MDOT_BLOCKS = 152;
+// MDOT_BLOCKS blocks of MDOT_THREADS threads; ticket must start at 0 and is reset.
+constexpr int MDOT_BLOCKS = 152, MDOT_THREADS = 256;
 void mdot_fused(int n, int m, const double* V, long long ldv, const double* w, double* partial, unsigned int* ticket,
                 double* out, double* acc, int sqrt_out, cudaStream_t s);
 // w <- w - V h; out[0..m) = V^T w, out[m] = w^T w of the updated w,
-// acc[i] += out[i] (i < m); MDOT_BLOCKS blocks of 512 threads, m <= 31.
+// acc[i] += out[i] (i < m); MDOT_BLOCKS blocks of MDOT_THREADS threads, m <= 31.
 void maxpy_mdot(int n, int m, const double* V, long long ldv, const double* h, double* w, double* partial,
                 unsigned int* ticket, double* out, double* acc, cudaStream_t s);
 // w <- (w - V h) / nu, nu = sqrt(max(*nrm2 - |h|^2, 0)), *hn = nu
