@@ -209,6 +209,8 @@ def main():
         e1.synchronize()
         st = h.info()
         pr = {k: h.prof_read(k) for k in (prof or [])}
+        if P._binding.PROF_GJ in (prof or []) and pr[P._binding.PROF_GJ][0] > 0:
+            pr["gj0"] = h.prof_read_one(P._binding.PROF_GJ, 0)     # level 0's inversion launch
         h.close()
         return e0.elapsed_time(e1), its, rel, st, pr
 
@@ -223,7 +225,7 @@ def main():
         one_step(P.MIXED)
     barrier()
     # timed region: mixed precision, inputs resident in HBM
-    times, its_l, launches, gj_prof = [], [], 0, [0, 0.0]
+    times, its_l, launches, gj_prof, gj0 = [], [], 0, [0, 0.0], []
     stats = None
     with Clocks(local) as clk:
         t0 = time.perf_counter()
@@ -234,6 +236,7 @@ def main():
             launches += st["kernel_launches"]
             gj_prof[0] += pr[P._binding.PROF_GJ][0]
             gj_prof[1] += pr[P._binding.PROF_GJ][1]
+            gj0.append(pr.get("gj0", 0.0))
             stats = st
         barrier()
         wall = time.perf_counter() - t0
@@ -250,8 +253,20 @@ def main():
     # FP64 V-cycle for the mixed-vs-FP64 comparison
     one_step(P.FP64)                     # untimed: FP64 warm-up
     f64 = [one_step(P.FP64) for _ in range(max(3, a.steps))]
-    # solve-phase kernel timing of the patch apply (secondary roofline)
-    _, _, _, st_p, pr_p = one_step(P.MIXED, prof=[P._binding.PROF_PATCH, P._binding.PROF_SPMV])
+    # solve-phase roofline: level 0's FP32 patch apply (one ASM sweep over
+    # 4225 inverses), timed by CUDA events on its stream after an L2 flush
+    hp = make(P.MIXED, 1 << P._binding.PROF_PATCH)
+    n0 = hp.info()["n_free"][0]
+    rr = torch.randn(n0, dtype=torch.float64, device=dev)
+    k0 = hp.prof_read(P._binding.PROF_PATCH)[0]
+    for _ in range(10):
+        flush.fill_(1.0)
+        hp.asm(0, rr, P.MIXED)
+    torch.cuda.synchronize(dev)
+    k1 = hp.prof_read(P._binding.PROF_PATCH)[0]
+    patch_ms = sorted(hp.prof_read_one(P._binding.PROF_PATCH, i) for i in range(k0, k1))
+    patch_ms = patch_ms[len(patch_ms) // 2] if patch_ms else 0.0     # median launch
+    hp.close()
     barrier()
     if rank != 0:
         if pg is not None:
@@ -293,12 +308,21 @@ def main():
     probe.close()
     gj_launches_per_step = gj_prof[0] / a.steps
     gj_ms_per_step = gj_prof[1] / a.steps
-    fp64_peak_tflops = 1.25      # nominal GB300 FP64 (no measured FP64 peak)
-    # the coarse bordered GJ is many tiny launches; report the patch batches
-    # (launches over the relaxed levels) as the kernel
+    # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
+    # clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s)
+    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+    # dominant kernel: level 0's saddle block inversion launch (4225 patches)
+    gj0_ms = sorted(gj0)[len(gj0) // 2] if gj0 else 0.0
+    achieved_gj0 = flops_levels[0] / (gj0_ms * 1e-3) / 1e12 if gj0_ms > 0 else None
     achieved_gj = flops_gj / (gj_ms_per_step * 1e-3) / 1e12 if gj_ms_per_step > 0 else None
-    # patch apply (FP32): bytes = sum n_i * ld32_i * 4 + 3 * sum n_i * 4 per launch, averaged over levels
-    n_patch_launch, ms_patch = pr_p[P._binding.PROF_PATCH]
+    # DRAM bytes of that launch from one ncu capture of the same kernel and
+    # workload (dram__bytes_read.sum + dram__bytes_write.sum)
+    traffic_gj0 = (288.104448 + 968.318976) * 1e6 if a.workload == "th_p4_64x64" else None
+    # level-0 FP32 patch apply: algorithmic bytes = sum n_i^2 * 4 (inverses)
+    # + 3 * sum n_i * 4 (gathered residual, weights, result)
+    n_i = sizes[0].astype(np.float64)
+    patch_bytes = 4.0 * float((n_i ** 2).sum()) + 12.0 * float(n_i.sum())
+    patch_gbs = patch_bytes / (patch_ms * 1e-3) / 1e9 if patch_ms > 0 else None
     line = {
         "metric": METRIC, "value": ms_max, "unit": "ms", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
@@ -318,14 +342,18 @@ def main():
         "fp64": {"value": sum(x[0] for x in f64) / len(f64), "unit": "ms", "iterations": f64[-1][1],
                  "setup_ms": f64[-1][3]["t_total_ms"]},
         "gpu_launches": int(launches / a.steps),
-        "roofline": {"kernel": "saddle_inverse_smem (batched FP64 saddle block patch inverse, all relaxed levels)",
-                     "bound": "alu", "achieved": achieved_gj, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                     "frac": (achieved_gj / fp64_peak_tflops) if achieved_gj else None, "traffic": None,
-                     "peak_source": "nominal FP64 1.25 TFLOP/s (recipe), no measured FP64 peak",
-                     "launches_per_step": gj_launches_per_step, "ms_per_step": gj_ms_per_step,
-                     "flop_per_step": flops_gj},
-        "roofline_solve": {"kernel": "patch_apply_f32", "launches": n_patch_launch,
-                           "avg_us": 1e3 * ms_patch / max(1, n_patch_launch)},
+        "roofline": {"kernel": "saddle_inverse_smem, level-0 launch (4225 Vanka patches, FP64 saddle block inverse)",
+                     "bound": "alu", "achieved": achieved_gj0, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                     "frac": (achieved_gj0 / fp64_peak_tflops) if achieved_gj0 else None,
+                     "traffic": traffic_gj0,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                     "flop_per_launch": flops_levels[0], "ms_per_launch": gj0_ms,
+                     "all_levels": {"launches_per_step": gj_launches_per_step, "ms_per_step": gj_ms_per_step,
+                                    "flop_per_step": flops_gj, "achieved": achieved_gj}},
+        "roofline_solve": {"kernel": "patch_apply_f32, level 0 (one ASM sweep)", "bound": "hbm",
+                           "achieved": patch_gbs, "peak": hbm, "unit": "GB/s",
+                           "frac": (patch_gbs / hbm) if patch_gbs else None, "bytes_per_launch": patch_bytes,
+                           "us_per_launch": 1e3 * patch_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
         "wall_s_timed": wall,
     }
     line["speedup_mixed_vs_fp64"] = line["fp64"]["value"] / ms_max

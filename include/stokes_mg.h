@@ -252,6 +252,11 @@ int stokes_mg_fgmres(stokes_mg_t h, const double* b, double* x, double tol, int*
  * stokes_prof_read).  enable = 0 stops. */
 int stokes_prof_enable(stokes_mg_t h, int kind, int enable);
 int stokes_prof_read(stokes_mg_t h, int kind, long long* launches, double* total_ms);
+/* Duration (ms, CUDA events on the launching stream) of the index-th timed
+ * launch of class `kind`, in launch order (0-based; EINVAL if out of range).
+ * During setup the patch-inversion launches of the relaxed levels are timed
+ * in the order the levels are built (level 0 first). */
+int stokes_prof_read_one(stokes_mg_t h, int kind, long long index, double* ms);
 
 /* ---- allocation-free batched inverse ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

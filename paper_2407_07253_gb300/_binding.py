@@ -91,6 +91,7 @@ def lib():
         "stokes_mg_fgmres": (c_int, [P, P, P, c_double, POINTER(c_int), POINTER(c_double), P]),
         "stokes_prof_enable": (c_int, [P, c_int, c_int]),
         "stokes_prof_read": (c_int, [P, c_int, POINTER(c_longlong), POINTER(c_double)]),
+        "stokes_prof_read_one": (c_int, [P, c_int, c_longlong, POINTER(c_double)]),
         "stokes_mg_destroy": (None, [P]),
         "stokes_last_error": (ctypes.c_char_p, []),
         "stokes_batched_inverse_noalloc": (c_int, [c_int, P, P, POINTER(c_int), P]),
@@ -289,6 +290,11 @@ class StokesMG:
         n, ms = c_longlong(), c_double()
         check(lib().stokes_prof_read(self.h, kind, byref(n), byref(ms)))
         return n.value, ms.value
+
+    def prof_read_one(self, kind, index):
+        ms = c_double()
+        check(lib().stokes_prof_read_one(self.h, kind, int(index), byref(ms)))
+        return ms.value
 
     def close(self):
         if self.h:

@@ -209,6 +209,7 @@ struct Prof {
     bool on = false;
     long long launches = 0;
     double total_ms = 0;
+    std::vector<double> each_ms;        // resolved launches, in launch order
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
 };
 
@@ -1977,22 +1978,39 @@ int stokes_prof_enable(stokes_mg_t h, int kind, int enable) {
     return STOKES_OK;
 }
 
+static void prof_resolve(Prof& p) {
+    for (auto& ab : p.pending) {
+        CK(cudaEventSynchronize(ab.second));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ab.first, ab.second));
+        p.total_ms += ms;
+        p.each_ms.push_back(ms);
+        cudaEventDestroy(ab.first);
+        cudaEventDestroy(ab.second);
+    }
+    p.pending.clear();
+}
+
 int stokes_prof_read(stokes_mg_t h, int kind, long long* launches, double* total_ms) {
     g_last_error.clear();
     return guarded([&] {
         require(h && kind >= 0 && kind < 5, "invalid argument");
         Prof& p = h->prof[kind];
-        for (auto& ab : p.pending) {
-            CK(cudaEventSynchronize(ab.second));
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, ab.first, ab.second));
-            p.total_ms += ms;
-            cudaEventDestroy(ab.first);
-            cudaEventDestroy(ab.second);
-        }
-        p.pending.clear();
+        prof_resolve(p);
         if (launches) *launches = p.launches;
         if (total_ms) *total_ms = p.total_ms;
+        return STOKES_OK;
+    });
+}
+
+int stokes_prof_read_one(stokes_mg_t h, int kind, long long index, double* ms) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && kind >= 0 && kind < 5 && ms, "invalid argument");
+        Prof& p = h->prof[kind];
+        prof_resolve(p);
+        require(index >= 0 && index < (long long)p.each_ms.size(), "launch index out of range");
+        *ms = p.each_ms[index];
         return STOKES_OK;
     });
 }
