@@ -38,6 +38,17 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, pg, device):
+    """The largest per-replica value over all ranks (a step is as slow as the
+    slowest replica); pg is torch.distributed or None for one process."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -113,7 +124,7 @@ class Clocks:
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
         return self
@@ -241,12 +252,7 @@ def main():
         barrier()
         wall = time.perf_counter() - t0
     ms_local = sum(times) / len(times)
-    if pg is not None:
-        t = torch.tensor([ms_local], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms_local
+    ms_max = max_over_ranks(ms_local, pg, dev)
     # e2e through host buffers (pinned H2D of f, D2H of u and p inside the step)
     one_step(P.MIXED, e2e=True)          # untimed: first pinned-copy path
     e2e_times = [one_step(P.MIXED, e2e=True)[0] for _ in range(max(3, a.steps))]

@@ -975,7 +975,7 @@ void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     K.ci = halloc<int>(h, bound);
     K.v64 = halloc<double>(h, bound);
     K.v32 = want32 ? halloc<float>(h, bound) : nullptr;
-    K.lanes = 16;
+    K.lanes = 4;                         // rows of ~25-120 entries (choose_lanes after assembly)
     l.asm_len = halloc<int>(h, n);
     l.asm_tmp = halloc<int>(h, (n + 1023) / 1024 + 2);
     l.asm_status = halloc<int>(h, 1);
