@@ -158,6 +158,31 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
  * sides are processed one after another.  r_dev and z_dev may not alias. */
 int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, void* stream);
 
+/* Z = B_MG R for a batch of right-hand sides in one pass: the same V-cycle
+ * as stokes_mg_vcycle (Eq. 3.2 / 3.1, Chebyshev-accelerated ASM relaxation,
+ * Sec. 3.3), with the batch interleaved DoF-major on the device so that
+ * every sparse matrix is read once per batch and each patch apply
+ * W_i K_i^{-1} R_i is a dense (n_i x n_i) x (n_i x m) product on the tensor
+ * cores.  The paper applies the preconditioner to one vector at a time; the
+ * batch is this library's extension for many independent right-hand sides
+ * (block Krylov methods, several load cases).
+ *   r_dev, z_dev   device, [nrhs][n_free(level 0)] FP64, as stokes_mg_vcycle;
+ *                  may not alias.
+ *   nrhs           1 .. STOKES_BATCH_MAX; the batch is padded with zero
+ *                  columns to the next width of 8, 16, 32 or 64.
+ *   mode           STOKES_BATCH_TF32: TF32 products (about 1e-3 relative);
+ *                  STOKES_BATCH_3XTF32: split-TF32 products with FP32
+ *                  accuracy (the single-vector MIXED V-cycle to ~1e-5).
+ * Needs a MIXED handle (FP32 operators and inverses).  Work buffers of the
+ * width are allocated on first use and kept; one CUDA graph per mode and
+ * width is captured on first use unless opts.use_graph is 0.
+ * Errors: EINVAL (nrhs, mode, an FP64 handle), EUNSUPPORTED (a patch too
+ * large for the per-block shared memory at this width), ECUDA. */
+#define STOKES_BATCH_MAX    64
+#define STOKES_BATCH_TF32   0
+#define STOKES_BATCH_3XTF32 1
+int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, int mode, void* stream);
+
 /* Solve -nu Laplace(u) + grad p = f, div u = 0, u = g on the boundary with
  * FGMRES(restart) right-preconditioned by the V-cycle (Sec. 4), stopped when
  * ||b - K x||_2 <= tol ||b||_2.

@@ -15,6 +15,8 @@ ERRORS = {-1: "EINVAL", -2: "EOOM", -3: "ESINGULAR", -4: "ENOTCONVERGED", -5: "E
           -6: "ECUDA", -7: "EUNSUPPORTED"}
 PROF_PATCH, PROF_SPMV, PROF_GJ, PROF_PULL, PROF_TRANSFER = 0, 1, 2, 3, 4
 MAX_LEVELS = 16
+BATCH_TF32, BATCH_3XTF32 = 0, 1
+BATCH_MAX = 64
 
 
 class Mesh(ctypes.Structure):
@@ -75,6 +77,7 @@ def lib():
         "stokes_mg_default_opts": (None, [POINTER(Opts)]),
         "stokes_mg_setup": (c_int, [POINTER(Mesh), c_int, c_int, c_int, c_int, POINTER(Opts), P, P, POINTER(P)]),
         "stokes_mg_vcycle": (c_int, [P, P, P, c_int, P]),
+        "stokes_mg_vcycle_batched": (c_int, [P, P, P, c_int, c_int, P]),
         "stokes_solve": (c_int, [P, P, P, c_double, c_double, P, P, POINTER(c_int), POINTER(c_double), P]),
         "stokes_mg_info": (c_int, [P, POINTER(Stats)]),
         "stokes_mg_level_dofs": (c_int, [P, c_int, P, P, P]),
@@ -224,6 +227,16 @@ class StokesMG:
         z = torch.empty_like(r) if out is None else out
         check(lib().stokes_mg_vcycle(self.h, _ptr(r.contiguous()), _ptr(z), nrhs, _stream(self.stream)))
         return z
+
+    def vcycle_batched(self, R, mode=BATCH_3XTF32, out=None):
+        """Z = B_MG R for R of shape [nrhs, n_free] (float64, device), all
+        right-hand sides in one interleaved pass (stokes_mg_vcycle_batched)."""
+        import torch
+        R = R.contiguous()
+        nrhs = 1 if R.dim() == 1 else R.shape[0]
+        Z = torch.empty_like(R) if out is None else out
+        check(lib().stokes_mg_vcycle_batched(self.h, _ptr(R), _ptr(Z), nrhs, int(mode), _stream(self.stream)))
+        return Z
 
     def solve(self, f, g=None, nu=1.0, tol=1e-8, u=None, p=None, raise_on_nonconv=True):
         import torch

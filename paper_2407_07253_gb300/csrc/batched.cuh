@@ -1,0 +1,45 @@
+// Kernels of the batched (multi-right-hand-side) V-cycle.
+//
+// The m right-hand sides of one batch are interleaved DoF-major: vector v of
+// a level is stored as X[j * m + c] (DoF j, right-hand side c), m a multiple
+// of 8.  A sparse matrix is then read once per batch, every gathered row is
+// m contiguous floats, and the patch apply becomes one dense GEMM per patch,
+//   Y_i (n_i x m) = W_i K_i^{-1} (n_i x n_i) R_i (n_i x m),
+// which runs on the tensor cores (warp-level m16n8k8 TF32 MMA; the 3xTF32
+// split a = a_hi + a_lo keeps FP32 accuracy).  At m = 64 the GEMM does
+// 2 m = 128 flop per 4-byte inverse entry, so it is bound by streaming the
+// FP32 inverses from HBM, not by the MMA rate.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sbat {
+
+enum GemmMode { GEMM_TF32 = 0, GEMM_3XTF32 = 1 };
+
+// X[j * m + c] = (float) r[c * n + j] for c < nrhs, 0 for nrhs <= c < m
+void to_interleaved(int n, int nrhs, int m, const double* r, float* X, cudaStream_t s);
+// z[c * n + j] = X[j * m + c] for c < nrhs
+void from_interleaved(int n, int nrhs, int m, const float* X, double* z, cudaStream_t s);
+
+// Y = A X (mode 0), Y += A X (mode 1), Y = B - A X (mode 2); A in CSR (FP32
+// values), X, Y, B interleaved with width m.
+void spmm(int mode, int nr, int m, const int* rp, const int* ci, const float* av, const float* X, float* Y,
+          const float* B, cudaStream_t s);
+
+// Yb[(poff[p] + a) * m + c] = wt[dof] * (K_p^{-1} R_p)[a][c], R_p[a][c] =
+// X[pdofs[poff[p] + a] * m + c]; inverses column-major with leading
+// dimension (n + 3) & ~3 at ioff[p] (the FP32 ASM layout).  maxn bounds the
+// patch size (shared memory).
+void patch_gemm(int mode, int npatch, int maxn, int m, const int* poff, const int* pdofs, const long long* ioff,
+                const float* inv, const float* X, const float* wt, float* Yb, cudaStream_t s);
+
+// out[j * m + c] = alpha * sum_{q in slots(j)} Yb[sidx[q] * m + c] + beta * out[j * m + c]
+// (slots in increasing order: a fixed summation order)
+void pull_scatter(int n, int m, const int* soff, const int* sidx, const float* Yb, float alpha, float beta,
+                  float* out, cudaStream_t s);
+
+// E[i * m + c] = sum_j C[i * ldc + j] B[j * m + c] for i, j < nc: the dense
+// FP64 coarse inverse applied to a batch (FP64 accumulation).
+void coarse_gemm(int nc, int ldc, int m, const double* C, const float* B, float* E, cudaStream_t s);
+
+}  // namespace sbat

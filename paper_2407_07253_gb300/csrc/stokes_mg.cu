@@ -26,6 +26,7 @@
 #include "fem.hpp"
 #include "assembly.cuh"
 #include "kernels.cuh"
+#include "batched.cuh"
 
 namespace {
 
@@ -240,6 +241,14 @@ struct stokes_mg {
     double *vin = nullptr, *vout = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};
+    // batched V-cycle: interleaved work vectors of width bm per level, and
+    // one captured graph per patch-GEMM mode for that width
+    struct BatchLevel { float *b = nullptr, *e = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *u = nullptr,
+                              *Yb = nullptr; };
+    int bm = 0;
+    std::vector<BatchLevel> bl;
+    cudaGraphExec_t bgraph[2] = {nullptr, nullptr};
+    long long bgraph_launches[2] = {0, 0};
     // solve plumbing (finest level)
     DevCSR Mv, KfD;
     int *vel_rows = nullptr;    // free velocity row -> full velocity index
@@ -642,6 +651,148 @@ void capture_graph(stokes_mg* h, int prec, cudaStream_t s) {
     CK(cudaGraphDestroy(g));
     CK(cudaStreamDestroy(cs));
     (void)s;
+}
+
+// ---- batched V-cycle (m interleaved right-hand sides, FP32 operators) -----
+// The same cycle as pcycle / hcycle / smooth (Eq. 3.2 / 3.1, Chebyshev around
+// one ASM sweep), with SpMM for the SpMVs and transfers, the patch apply as a
+// per-patch GEMM on the tensor cores (sbat::patch_gemm, mode gm) and the
+// dense FP64 coarse inverse applied to the whole batch.
+using BatchLevel = stokes_mg::BatchLevel;
+
+void b_spmm(stokes_mg* h, int kind, const DevCSR& A, int mode, int m, const float* X, float* Y, const float* B,
+            cudaStream_t s) {
+    launch(h, kind, s, [&] { sbat::spmm(mode, A.nr, m, A.rp, A.ci, A.v32, X, Y, B, s); });
+}
+
+void b_asm(stokes_mg* h, int li, int gm, int m, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    BatchLevel& B = h->bl[li];
+    launch(h, PK_PATCH, s, [&] {
+        sbat::patch_gemm(gm, l.npatch, l.maxn, m, l.poff, l.pdofs, l.ioff32, l.inv32, r, l.wt32, B.Yb, s);
+    });
+    launch(h, PK_PULL, s, [&] { sbat::pull_scatter(l.n, m, l.soff, l.sidx, B.Yb, (float)alpha, (float)beta, out, s); });
+}
+
+void b_smooth(stokes_mg* h, int li, int gm, int m, const float* b, float* x, bool x_zero, int nu, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    BatchLevel& B = h->bl[li];
+    const double a = h->opts.cheb_lo * l.lmax, bb = h->opts.cheb_hi * l.lmax;
+    const double theta = 0.5 * (bb + a), delta = 0.5 * (bb - a), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    const int N = l.n * m;
+    const float* rin = b;
+    if (!x_zero) {
+        b_spmm(h, PK_SPMV, l.K, skern::SPMV_RESID, m, x, B.r, b, s);
+        rin = B.r;
+    }
+    if (nu == 1) {
+        b_asm(h, li, gm, m, rin, x, 1.0 / theta, x_zero ? 0.0 : 1.0, s);
+        return;
+    }
+    b_asm(h, li, gm, m, rin, B.d, 1.0 / theta, 0.0, s);
+    if (x_zero) {
+        CK(cudaMemcpyAsync(x, B.d, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(B.r, b, sizeof(float) * N, cudaMemcpyDeviceToDevice, s));
+    } else {
+        axpby_l<float>(h, N, 1.0, B.d, 1.0, x, s);
+    }
+    for (int i = 1; i < nu; ++i) {
+        b_spmm(h, PK_SPMV, l.K, skern::SPMV_RESID, m, B.d, B.r, B.r, s);    // r -= K d
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        b_asm(h, li, gm, m, B.r, B.d, 2.0 * rho_new / delta, rho_new * rho, s);
+        axpby_l<float>(h, N, 1.0, B.d, 1.0, x, s);
+        rho = rho_new;
+    }
+}
+
+void b_coarse(stokes_mg* h, int m, const float* b, float* e, cudaStream_t s) {
+    const int n = h->nc;
+    launch(h, -1, s, [&] { sbat::coarse_gemm(n, n + 1, m, h->Cinv, b, e, s); });
+}
+
+void b_hcycle(stokes_mg* h, int li, int gm, int m, const float* b, float* e, cudaStream_t s) {
+    const int last = (int)h->L.size() - 1;
+    if (li == last) { b_coarse(h, m, b, e, s); return; }
+    DevLevel& l = h->L[li];
+    BatchLevel& B = h->bl[li];
+    BatchLevel& C = h->bl[li + 1];
+    const int nu = h->opts.nu_h;
+    b_smooth(h, li, gm, m, b, e, true, nu, s);
+    b_spmm(h, PK_SPMV, l.K, skern::SPMV_RESID, m, e, B.r, b, s);
+    b_spmm(h, PK_TRANSFER, l.R, skern::SPMV_SET, m, B.r, C.b, nullptr, s);
+    b_hcycle(h, li + 1, gm, m, C.b, C.e, s);
+    b_spmm(h, PK_TRANSFER, l.P, skern::SPMV_ADD, m, C.e, e, nullptr, s);
+    b_smooth(h, li, gm, m, b, e, false, nu, s);
+}
+
+void b_pcycle(stokes_mg* h, int li, int gm, int m, const float* b, float* e, cudaStream_t s) {
+    const int last = (int)h->L.size() - 1;
+    if (li == last) { b_coarse(h, m, b, e, s); return; }
+    DevLevel& l = h->L[li];
+    BatchLevel& B = h->bl[li];
+    if (!l.p_level) {
+        b_hcycle(h, li, gm, m, b, e, s);
+        for (int t = 1; t < h->opts.n_V; ++t) {
+            b_spmm(h, PK_SPMV, l.K, skern::SPMV_RESID, m, e, B.t, b, s);
+            b_hcycle(h, li, gm, m, B.t, B.u, s);
+            axpby_l<float>(h, l.n * m, 1.0, B.u, 1.0, e, s);
+        }
+        return;
+    }
+    BatchLevel& C = h->bl[li + 1];
+    const int nu = h->opts.nu_p;
+    b_smooth(h, li, gm, m, b, e, true, nu, s);
+    b_spmm(h, PK_SPMV, l.K, skern::SPMV_RESID, m, e, B.r, b, s);
+    b_spmm(h, PK_TRANSFER, l.R, skern::SPMV_SET, m, B.r, C.b, nullptr, s);
+    b_pcycle(h, li + 1, gm, m, C.b, C.e, s);
+    b_spmm(h, PK_TRANSFER, l.P, skern::SPMV_ADD, m, C.e, e, nullptr, s);
+    b_smooth(h, li, gm, m, b, e, false, nu, s);
+}
+
+// interleaved work vectors of width m on every level (kept for later calls)
+void ensure_batch(stokes_mg* h, int m) {
+    if (h->bm == m) return;
+    const int nl = (int)h->L.size();
+    h->bl.assign(nl, BatchLevel());
+    for (int li = 0; li < nl; ++li) {
+        const size_t N = (size_t)h->L[li].n * m;
+        BatchLevel& B = h->bl[li];
+        B.b = halloc<float>(h, N); B.e = halloc<float>(h, N); B.r = halloc<float>(h, N);
+        B.d = halloc<float>(h, N); B.t = halloc<float>(h, N); B.u = halloc<float>(h, N);
+        if (li + 1 < nl) B.Yb = halloc<float>(h, (size_t)h->L[li].nent * m);
+    }
+    CK(cudaStreamSynchronize(h->s_up));      // new chunks are pool-ordered on s_up
+    for (int i = 0; i < 2; ++i) {
+        if (h->bgraph[i]) CK(cudaGraphExecDestroy(h->bgraph[i]));
+        h->bgraph[i] = nullptr;
+    }
+    h->bm = m;
+}
+
+void capture_batched(stokes_mg* h, int gm, int m) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    long long before = h->launches;
+    h->capturing = true;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        b_pcycle(h, 0, gm, m, h->bl[0].b, h->bl[0].e, cs);
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(cs, &dummy);
+        h->capturing = false;
+        cudaStreamDestroy(cs);
+        throw;
+    }
+    CK(cudaStreamEndCapture(cs, &g));
+    h->capturing = false;
+    h->bgraph_launches[gm] = h->launches - before;
+    h->launches = before;
+    CK(cudaGraphInstantiate(&h->bgraph[gm], g, 0));
+    CK(cudaGraphDestroy(g));
+    CK(cudaStreamDestroy(cs));
 }
 
 // ---- reductions for FGMRES / Arnoldi (FP64, deterministic two-stage)
@@ -1677,6 +1828,40 @@ int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs
     });
 }
 
+int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, int mode, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && r_dev && z_dev && nrhs >= 1 && nrhs <= STOKES_BATCH_MAX, "invalid argument");
+        require(mode == STOKES_BATCH_TF32 || mode == STOKES_BATCH_3XTF32, "unknown batch mode");
+        require(!h->host_only && h->opts.precision == STOKES_MIXED,
+                "the batched V-cycle needs a MIXED handle (FP32 operators and inverses)");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
+        int dev_max = 0;
+        CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+        for (size_t li = 0; li + 1 < h->L.size(); ++li) {
+            const size_t smem = sizeof(float) * (size_t)((h->L[li].maxn + 7) & ~7) * (m + 4);
+            if (smem > (size_t)dev_max)
+                throw StokesError(STOKES_EUNSUPPORTED, "patch too large for the batched patch GEMM at this width");
+        }
+        ensure_batch(h, m);
+        const int n = h->L[0].n;
+        launch(h, -1, s, [&] { sbat::to_interleaved(n, nrhs, m, r_dev, h->bl[0].b, s); });
+        const bool any_prof = h->prof[PK_PATCH].on || h->prof[PK_SPMV].on || h->prof[PK_PULL].on ||
+                              h->prof[PK_TRANSFER].on;
+        if (h->opts.use_graph && !any_prof) {
+            if (!h->bgraph[mode]) capture_batched(h, mode, m);
+            CK(cudaGraphLaunch(h->bgraph[mode], s));
+            h->launches += h->bgraph_launches[mode];
+        } else {
+            b_pcycle(h, 0, mode, m, h->bl[0].b, h->bl[0].e, s);
+        }
+        launch(h, -1, s, [&] { sbat::from_interleaved(n, nrhs, m, h->bl[0].e, z_dev, s); });
+        return STOKES_OK;
+    });
+}
+
 int stokes_mg_fgmres(stokes_mg_t h, const double* b, double* x, double tol, int* iterations, double* final_relres,
                      void* stream) {
     g_last_error.clear();
@@ -2025,8 +2210,10 @@ void stokes_mg_destroy(stokes_mg_t h) {
         for (auto& ab : p.pending) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
     if (h->s_up || h->s_coarse) cudaDeviceSynchronize();
     for (auto* m : h->marks) delete m;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        if (h->bgraph[i]) cudaGraphExecDestroy(h->bgraph[i]);
+    }
     if (h->s_up || h->s_coarse) cudaDeviceSynchronize();   // setup work may still be in flight after an error
     free_pending(h);
     free_coarse_ws(h);

@@ -1,0 +1,94 @@
+"""The batched V-cycle (stokes_mg_vcycle_batched) against the FP64 oracle.
+
+The batch runs the same cycle as the single-vector mixed-precision V-cycle
+(Eq. 3.2 / 3.1 with Chebyshev-accelerated ASM relaxation, Sec. 3.3), with the
+right-hand sides interleaved DoF-major, SpMM for the SpMVs and transfers and
+the patch apply W_i K_i^{-1} R_i as a tensor-core GEMM per patch.
+
+Tolerances:
+  * 3xTF32 splits every FP32 operand into a TF32 head and tail and keeps the
+    three cross products, which is FP32 accuracy up to the dropped lo*lo term
+    (2^-22 relative), so the batch agrees with the oracle to the same 2e-4 as
+    the single-vector mixed V-cycle (FP32 accumulation over a V-cycle), and
+    with that V-cycle itself to 1e-4;
+  * TF32 rounds the inverses and residuals to 10 mantissa bits (2^-11
+    relative per product), so one V-cycle lands within 2e-2 of the oracle.
+Each column of a batch is computed with the same arithmetic in the same
+order whatever the width, so the first columns of a wide batch equal a
+narrow batch bit for bit, and repeated runs are bitwise equal.
+"""
+import numpy as np
+import pytest
+
+from tests.test_gpu_parity import CASES, from_lib, pair, relerr, to_lib
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2407_07253_gb300")
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["th_p2_8x8", "th_p4_8x8", "th_p4_gradual", "sv_p3_alfeld", "th3d_p3"]
+assert all(n in CASES for n in NAMES)
+
+
+def _batch(ora, perm, nrhs, seed):
+    n = ora.levels[0].disc.n_free
+    R_o = np.random.default_rng(seed).standard_normal((nrhs, n))
+    R = torch.stack([to_lib(R_o[q], perm) for q in range(nrhs)])
+    return R_o, R
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_batched_3xtf32_matches_oracle_and_single_vcycle(name):
+    h, ora, perms = pair(name, P.MIXED)
+    R_o, R = _batch(ora, perms[0], 5, 3)
+    Z = h.vcycle_batched(R, P.BATCH_3XTF32)
+    Z1 = h.vcycle(R)
+    for q in range(R.shape[0]):
+        z = from_lib(Z[q], perms[0])
+        assert relerr(z, ora.vcycle(R_o[q])) < 2e-4, q
+        assert relerr(z, from_lib(Z1[q], perms[0])) < 1e-4, q
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_batched_tf32_matches_oracle(name):
+    h, ora, perms = pair(name, P.MIXED)
+    R_o, R = _batch(ora, perms[0], 3, 4)
+    Z = h.vcycle_batched(R, P.BATCH_TF32)
+    for q in range(R.shape[0]):
+        assert relerr(from_lib(Z[q], perms[0]), ora.vcycle(R_o[q])) < 2e-2, q
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batched_columns_independent_of_width_and_deterministic(mode):
+    h, ora, perms = pair("th_p4_8x8", P.MIXED)
+    _, R = _batch(ora, perms[0], P.BATCH_MAX, 9)
+    Zw = h.vcycle_batched(R, mode)                   # width 64
+    assert torch.equal(Zw, h.vcycle_batched(R, mode))
+    for nrhs in (1, 8, 13, 32):                      # widths 8, 8, 16, 32
+        Zn = h.vcycle_batched(R[:nrhs], mode)
+        assert torch.equal(Zn, Zw[:nrhs]), nrhs
+
+
+def test_batched_graph_and_eager_paths_agree():
+    h, ora, perms = pair("th_p4_gradual", P.MIXED)
+    he, _, _ = pair("th_p4_gradual", P.MIXED, use_graph=0)
+    _, R = _batch(ora, perms[0], 20, 6)
+    for mode in (P.BATCH_TF32, P.BATCH_3XTF32):
+        assert torch.equal(h.vcycle_batched(R, mode), he.vcycle_batched(R, mode))
+
+
+def test_batched_bad_arguments():
+    h, ora, perms = pair("th_p2_8x8", P.MIXED)
+    n = ora.levels[0].disc.n_free
+    R = torch.zeros(P.BATCH_MAX + 1, n, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.StokesError) as e:
+        h.vcycle_batched(R)
+    assert e.value.code == -1
+    with pytest.raises(P.StokesError) as e:
+        h.vcycle_batched(R[:2], mode=7)
+    assert e.value.code == -1
+    h64, _, _ = pair("th_p2_8x8", P.FP64)
+    with pytest.raises(P.StokesError) as e:
+        h64.vcycle_batched(R[:2])
+    assert e.value.code == -1
