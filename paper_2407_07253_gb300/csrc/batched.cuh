@@ -12,6 +12,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 namespace sbat {
 
 enum GemmMode { GEMM_TF32 = 0, GEMM_3XTF32 = 1 };
@@ -25,6 +27,9 @@ void from_interleaved(int n, int nrhs, int m, const float* X, double* z, cudaStr
 // values), X, Y, B interleaved with width m.
 void spmm(int mode, int nr, int m, const int* rp, const int* ci, const float* av, const float* X, float* Y,
           const float* B, cudaStream_t s);
+
+// dynamic shared memory of one patch_gemm CTA for patches of <= maxn DoFs
+size_t patch_gemm_smem(int maxn, int m);
 
 // Yb[(poff[p] + a) * m + c] = wt[dof] * (K_p^{-1} R_p)[a][c], R_p[a][c] =
 // X[pdofs[poff[p] + a] * m + c]; inverses column-major with leading

@@ -1841,8 +1841,7 @@ int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, 
         int dev_max = 0;
         CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
         for (size_t li = 0; li + 1 < h->L.size(); ++li) {
-            const size_t smem = sizeof(float) * (size_t)((h->L[li].maxn + 7) & ~7) * (m + 4);
-            if (smem > (size_t)dev_max)
+            if (sbat::patch_gemm_smem(h->L[li].maxn, m) > (size_t)dev_max)
                 throw StokesError(STOKES_EUNSUPPORTED, "patch too large for the batched patch GEMM at this width");
         }
         ensure_batch(h, m);
