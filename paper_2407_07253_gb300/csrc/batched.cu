@@ -1,7 +1,14 @@
 // Kernels of the batched V-cycle; see batched.cuh.
 #include "batched.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
 
 namespace sbat {
 
@@ -264,6 +271,322 @@ __global__ void __launch_bounds__(512, 1) k_patch_gemm(int npatch, const int* __
     cp_async_wait<0>();
 }
 
+// ---- TF32 mode on the 5th-generation tensor cores (tcgen05) -------------
+//
+// A persistent kernel (one CTA per SM) walks its share of the patches with a
+// warp-specialised pipeline over stages of KS = 16 inverse columns:
+//   warp 0, lane 0   TMA: the stage's rows of K_p^{-1} (one 128-row box per
+//                    row tile, 64-byte swizzle, zero fill outside the patch)
+//                    through the per-patch tensor map.  K_p^{-1} is
+//                    symmetric, so row r of the product's left factor is the
+//                    stored column r: each box row is 64 contiguous bytes.
+//   warps 2-9        the stage's 16 rows of R_p, gathered from X, rounded to
+//                    TF32 and written as the K-major B operand (8 x 16-byte
+//                    core matrices, no swizzle), then fenced to the async
+//                    proxy; each warp takes every G-th stage, so up to
+//                    G = min(8, stages) gathers are in flight.
+//   warp 1, lane 0   waits for both, issues the stage's M = 128, N = np,
+//                    K = 8 MMAs (one per row tile and k-step) into the
+//                    patch's tensor-memory accumulator and commits them to
+//                    the stage's empty barrier; after the patch's last stage
+//                    it commits the accumulator to the epilogue.
+//   warps 10-13      epilogue: tensor memory -> registers (the 32 lanes of
+//                    warp w % 4), times the partition-of-unity weight, -> Yb.
+// Two accumulators alternate between patches when they fit in the 512
+// tensor-memory columns, so the epilogue of one patch overlaps the MMAs of
+// the next.  All mbarrier waits are bounded; on a timeout the CTA records it
+// in *status, stops every role and returns.
+namespace tc {
+
+constexpr int KS = 16;                    // inverse columns per stage: two K = 8 steps
+constexpr int A_TILE = 128 * KS * 4;      // bytes of one 128-row tile of a stage (8 KB)
+constexpr int B_GROUP = (KS / 4) * 128;   // bytes between 8-row groups of the B operand
+constexpr int HDR = 1024;                 // barriers, tensor-memory address, abort flag
+constexpr int GATHER_WARPS = 8;           // stages gathered concurrently
+constexpr int THREADS = 32 * (2 + GATHER_WARPS + 4);
+constexpr long long WAIT_LIMIT = 1ll << 22;
+
+__host__ __device__ constexpr int np_of(int m) { return m < 16 ? 16 : m; }
+__host__ __device__ inline int tiles_of(int n) { return (n + 127) >> 7; }
+__host__ __device__ inline int stage_bytes(int maxn, int np) {
+    return (tiles_of(maxn) * A_TILE + np * KS * 4 + 1023) & ~1023;
+}
+__host__ __device__ inline int acc_cols(int maxn, int np) { return tiles_of(maxn) * np; }
+__host__ __device__ inline int acc_bufs(int maxn, int np) { return 2 * acc_cols(maxn, np) <= 512 ? 2 : 1; }
+__host__ __device__ inline int tmem_cols(int maxn, int np) {
+    int need = acc_bufs(maxn, np) * acc_cols(maxn, np), c = 32;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+// shared-memory matrix descriptors (K-major): without swizzle (8-row x
+// 16-byte core matrices, lbo along K, sbo along M / N) and with the 64-byte
+// swizzle of the TMA boxes (8-row atoms of 64-byte rows, sbo = 512)
+__device__ __forceinline__ uint64_t desc_plain(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
+           (4ull << 61);
+}
+
+// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = np
+__host__ __device__ constexpr uint32_t idesc(int np) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(np >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false (and the CTA's abort flag set) after WAIT_LIMIT polls,
+// or at once if another role has already given up
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try(a, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint32_t mbar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(tmap), "r"(mbar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+template <int M, int ST>
+__global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int maxn, const int* __restrict__ poff,
+                                                              const int* __restrict__ pdofs,
+                                                              const CUtensorMap* __restrict__ tmaps,
+                                                              const float* __restrict__ X,
+                                                              const float* __restrict__ wt, float* __restrict__ Yb,
+                                                              int* status) {
+    constexpr int NP = np_of(M);
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = smem_u32(smem_tc);
+    const uint32_t full0 = base, empty0 = base + 8 * ST, accf0 = base + 16 * ST, acce0 = accf0 + 16;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_tc + 16 * ST + 32);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem_tc + 16 * ST + 36);
+    const int sbytes = stage_bytes(maxn, NP);
+    const uint32_t stage0 = (base + HDR + 1023) & ~1023u;     // swizzle atoms need 1024-byte alignment
+    const uint32_t b_off = (uint32_t)(tiles_of(maxn) * A_TILE);      // B operand inside a stage
+    const int nbuf = acc_bufs(maxn, NP), ccols = acc_cols(maxn, NP), ncols = tmem_cols(maxn, NP);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(full0 + 8 * s, 1 + 32);      // TMA arrival with the byte count + one gather warp
+            mbar_init(empty0 + 8 * s, 1);          // MMA commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);           // MMA commit of a patch's last stage
+            mbar_init(acce0 + 8 * b, 128);         // epilogue threads
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA ---
+        if (lane == 0) {
+            int it = 0;
+            for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+                const int n = poff[p + 1] - poff[p], tiles = tiles_of(n), nst = (n + KS - 1) / KS;
+                const CUtensorMap* tm = tmaps + p;
+                for (int j = 0; j < nst; ++j, ++it) {
+                    const int s = it % ST;
+                    if (it >= ST && !mbar_wait(empty0 + 8 * s, ((it / ST) - 1) & 1, abort_flag)) goto done;
+                    const uint32_t st = stage0 + (uint32_t)(s * sbytes);
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(tiles * A_TILE));
+                    for (int mt = 0; mt < tiles; ++mt) tma_load_2d(st + mt * A_TILE, tm, full0 + 8 * s, j * KS, mt * 128);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA ---
+        if (lane == 0) {
+            constexpr uint32_t ID = idesc(NP);
+            int it = 0, pc = 0;
+            for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++pc) {
+                const int n = poff[p + 1] - poff[p], tiles = tiles_of(n), nst = (n + KS - 1) / KS;
+                const int b = pc % nbuf;
+                if (pc >= nbuf && !mbar_wait(acce0 + 8 * b, ((pc / nbuf) - 1) & 1, abort_flag)) goto done;
+                fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * ccols);
+                for (int j = 0; j < nst; ++j, ++it) {
+                    const int s = it % ST;
+                    if (!mbar_wait(full0 + 8 * s, (it / ST) & 1, abort_flag)) goto done;
+                    fence_after();
+                    const uint32_t st = stage0 + (uint32_t)(s * sbytes);
+#pragma unroll
+                    for (int u = 0; u < KS / 8; ++u) {
+                        const uint64_t bd = desc_plain(st + b_off + (uint32_t)(u * 2 * 128), 128, B_GROUP);
+                        for (int mt = 0; mt < tiles; ++mt)
+                            mma(acc + (uint32_t)(mt * NP), desc_sw64(st + (uint32_t)(mt * A_TILE + u * 32)), bd, ID,
+                                (j | u) != 0);
+                    }
+                    commit(empty0 + 8 * s);
+                }
+                commit(accf0 + 8 * b);
+            }
+        }
+    } else if (warp < 2 + GATHER_WARPS) {
+        // ------------------------------------------------------- gather ---
+        // gather warp g fills the B operand of every G-th stage: element
+        // (c, k) at (c / 8) B_GROUP + (k / 4) 128 + (c % 8) 16 + (k % 4) 4 for
+        // the stage's k = 0 .. KS - 1; lane (k % 4, c / 4 % 8).  G <= ST: a
+        // warp waits on a stage's empty barrier only after its own previous
+        // wait (G stages back) has seen the MMAs of ST - G <= 0 stages
+        // earlier, so the barrier is never a full phase behind the parity
+        // it polls for.
+        constexpr int G = GATHER_WARPS < ST ? GATHER_WARPS : ST;
+        const int g = warp - 2, kk = lane & 3, c4l = lane >> 2;
+        constexpr int NE = (NP / 4 + 7) / 8;
+        if (g >= G) goto done;
+        int it = 0;
+        for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+            const int s0 = poff[p], n = poff[p + 1] - s0, nst = (n + KS - 1) / KS;
+            for (int j = 0; j < nst; ++j, ++it) {
+                if (it % G != g) continue;
+                const int s = it % ST;
+                int dof[KS / 4];
+#pragma unroll
+                for (int k4 = 0; k4 < KS / 4; ++k4) {
+                    const int k = j * KS + 4 * k4 + kk;
+                    dof[k4] = k < n ? __ldg(pdofs + s0 + k) : -1;
+                }
+                float4 v[KS / 4][NE];
+#pragma unroll
+                for (int k4 = 0; k4 < KS / 4; ++k4)
+#pragma unroll
+                    for (int e = 0; e < NE; ++e) {
+                        const int c = 4 * (c4l + 8 * e);
+                        v[k4][e] = (dof[k4] >= 0 && c < M)
+                                       ? __ldg(reinterpret_cast<const float4*>(X + (long long)dof[k4] * M + c))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                if (it >= ST && !mbar_wait(empty0 + 8 * s, ((it / ST) - 1) & 1, abort_flag)) goto done;
+                unsigned char* bp = smem_tc + (stage0 - base) + (size_t)s * sbytes + b_off;
+#pragma unroll
+                for (int k4 = 0; k4 < KS / 4; ++k4) {
+#pragma unroll
+                    for (int e = 0; e < NE; ++e) {
+                        const int c = 4 * (c4l + 8 * e);
+                        if (c < NP) {
+                            const float f[4] = {v[k4][e].x, v[k4][e].y, v[k4][e].z, v[k4][e].w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int cc = c + u;
+                                *reinterpret_cast<uint32_t*>(bp + (cc >> 3) * B_GROUP + k4 * 128 + (cc & 7) * 16 + kk * 4) =
+                                    to_tf32(f[u]);
+                            }
+                        }
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(full0 + 8 * s);
+            }
+        }
+    } else {
+        // ----------------------------------------------------- epilogue ---
+        const int q = warp & 3;            // tensor-memory lanes 32 q .. 32 q + 31
+        int pc = 0;
+        for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++pc) {
+            const int s0 = poff[p], n = poff[p + 1] - s0, tiles = tiles_of(n);
+            const int b = pc % nbuf;
+            float w[8];
+#pragma unroll
+            for (int mt = 0; mt < 8; ++mt) {
+                const int row = mt * 128 + 32 * q + lane;
+                w[mt] = (mt < tiles && row < n) ? __ldg(wt + __ldg(pdofs + s0 + row)) : 0.f;
+            }
+            if (!mbar_wait(accf0 + 8 * b, (pc / nbuf) & 1, abort_flag)) goto done;
+            fence_after();
+#pragma unroll
+            for (int mt = 0; mt < 8; ++mt) {
+                if (mt >= tiles) break;
+                const int row = mt * 128 + 32 * q + lane;
+#pragma unroll
+                for (int cb = 0; cb < NP; cb += 16) {
+                    uint32_t v[16];
+                    ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * ccols + mt * NP + cb), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (row < n && cb < M) {
+                        float4* dst = reinterpret_cast<float4*>(Yb + (long long)(s0 + row) * M + cb);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (cb + 4 * e < M)
+                                dst[e] = make_float4(w[mt] * __uint_as_float(v[4 * e]), w[mt] * __uint_as_float(v[4 * e + 1]),
+                                                     w[mt] * __uint_as_float(v[4 * e + 2]),
+                                                     w[mt] * __uint_as_float(v[4 * e + 3]));
+                    }
+                }
+            }
+            fence_before();
+            mbar_arrive(acce0 + 8 * b);
+        }
+    }
+done:
+    if (tid == 0 && *abort_flag) atomicExch(status, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+}  // namespace tc
+
 __global__ void __launch_bounds__(256) k_pull_scatter(int n, int m, const int* __restrict__ soff,
                                                       const int* __restrict__ sidx, const float2* __restrict__ Yb,
                                                       float alpha, float beta, float2* __restrict__ out) {
@@ -330,7 +653,6 @@ static size_t gemm_smem(int maxn, int m, int stages) {
     return sizeof(float) * ((size_t)m * rt_ld(maxn) + (size_t)patch_gemm_warps(maxn) * stages * SLOT);
 }
 
-size_t patch_gemm_smem(int maxn, int m) { return gemm_smem(maxn, m, MIN_STAGES); }
 
 template <int M, int MODE, int ST>
 static void launch_gemm(int threads, size_t smem, int npatch, const int* poff, const int* pdofs,
@@ -360,20 +682,119 @@ static void launch_gemm_st(int maxn, int npatch, const int* poff, const int* pdo
                                          wt, Yb, s);
 }
 
+static int device_attr(cudaDeviceAttr attr) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, attr, dev);
+    return v;
+}
+
+// tensor-core TF32 path: a persistent grid of one CTA per SM (the dynamic
+// shared memory is at least half an SM's, so no two CTAs share an SM and its
+// 512 tensor-memory columns), with as many pipeline stages as fit, at most 12
+struct TcPlan { int stages = 0; size_t smem = 0; int grid = 0; };
+
+static TcPlan tc_plan(int maxn, int m, int npatch) {
+    TcPlan pl;
+    const int np = tc::np_of(m);
+    if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, np) > 512) return pl;
+    const long long optin = device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin);
+    const long long per_sm = device_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor);
+    const long long fixed = tc::HDR + 1024, sb = tc::stage_bytes(maxn, np);
+    const long long st = std::min<long long>(12, (optin - fixed) / sb);
+    if (st < 2) return pl;
+    pl.stages = (int)st;
+    pl.smem = (size_t)std::max<long long>(fixed + st * sb, per_sm / 2 + 1024);
+    if ((long long)pl.smem > optin) pl.smem = (size_t)optin;
+    pl.grid = std::max(1, std::min(npatch, device_attr(cudaDevAttrMultiProcessorCount)));
+    return pl;
+}
+
+template <int M, int ST>
+static void launch_tc(const TcPlan& pl, int npatch, int maxn, const int* poff, const int* pdofs, const void* tmaps,
+                      const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
+    cudaFuncSetAttribute(tc::k_patch_gemm_tc<M, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    tc::k_patch_gemm_tc<M, ST><<<pl.grid, tc::THREADS, pl.smem, s>>>(
+        npatch, maxn, poff, pdofs, reinterpret_cast<const CUtensorMap*>(tmaps), X, wt, Yb, status);
+}
+
+template <int M>
+static void launch_tc_st(int npatch, int maxn, const int* poff, const int* pdofs, const void* tmaps, const float* X,
+                         const float* wt, float* Yb, int* status, cudaStream_t s) {
+    const TcPlan pl = tc_plan(maxn, M, npatch);
+    switch (pl.stages) {
+#define SBAT_TC_CASE(S) \
+    case S: launch_tc<M, S>(pl, npatch, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s); break;
+        SBAT_TC_CASE(2) SBAT_TC_CASE(3) SBAT_TC_CASE(4) SBAT_TC_CASE(5) SBAT_TC_CASE(6) SBAT_TC_CASE(7)
+        SBAT_TC_CASE(8) SBAT_TC_CASE(9) SBAT_TC_CASE(10) SBAT_TC_CASE(11) SBAT_TC_CASE(12)
+#undef SBAT_TC_CASE
+        default: break;
+    }
+}
+
 template <int M>
 static void patch_gemm_m(int mode, int npatch, int maxn, const int* poff, const int* pdofs, const long long* ioff,
-                         const float* inv, const float* X, const float* wt, float* Yb, cudaStream_t s) {
+                         const float* inv, const void* tmaps, const float* X, const float* wt, float* Yb, int* status,
+                         cudaStream_t s) {
     if (mode == GEMM_3XTF32) launch_gemm_st<M, GEMM_3XTF32>(maxn, npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
-    else launch_gemm_st<M, GEMM_TF32>(maxn, npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
+    else launch_tc_st<M>(npatch, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s);
+}
+
+const char* patch_gemm_check(int mode, int maxn, int m) {
+    if (mode == GEMM_3XTF32)
+        return gemm_smem(maxn, m, MIN_STAGES) <= (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin)
+                   ? nullptr
+                   : "patch too large for the shared memory of the 3xTF32 patch GEMM at this width";
+    if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, tc::np_of(m)) > 512)
+        return "patch too large for the tensor memory at this width";
+    return tc_plan(maxn, m, 1).stages ? nullptr : "patch too large for the shared memory of the TF32 patch GEMM";
+}
+
+size_t tmap_bytes(int npatch) { return sizeof(CUtensorMap) * (size_t)std::max(npatch, 1); }
+
+// One 2-D tensor map per patch over its FP32 inverse (inner extent ld =
+// (n + 3) & ~3 floats, n rows of stride ld), box 16 x 128 with the 64-byte
+// swizzle the MMA descriptors expect; zero fill outside.
+void build_tmaps(int npatch, const int* poff_d, const long long* ioff_d, const float* inv_d, void* out_d) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            throw std::runtime_error("cuTensorMapEncodeTiled is not available");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    std::vector<int> poff(npatch + 1);
+    std::vector<long long> ioff(npatch);
+    if (cudaMemcpy(poff.data(), poff_d, sizeof(int) * (npatch + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(ioff.data(), ioff_d, sizeof(long long) * npatch, cudaMemcpyDeviceToHost) != cudaSuccess)
+        throw std::runtime_error("patch offsets could not be read");
+    std::vector<CUtensorMap> maps(npatch);
+    for (int p = 0; p < npatch; ++p) {
+        const int n = poff[p + 1] - poff[p], ld = (n + 3) & ~3;
+        const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
+        const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)tc::KS, 128u};
+        const cuuint32_t estr[2] = {1u, 1u};
+        const CUresult r = encode(&maps[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)(inv_d + ioff[p]), dims, strides,
+                                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed for patch " + std::to_string(p));
+    }
+    if (cudaMemcpy(out_d, maps.data(), sizeof(CUtensorMap) * npatch, cudaMemcpyHostToDevice) != cudaSuccess)
+        throw std::runtime_error("tensor maps could not be uploaded");
 }
 
 void patch_gemm(int mode, int npatch, int maxn, int m, const int* poff, const int* pdofs, const long long* ioff,
-                const float* inv, const float* X, const float* wt, float* Yb, cudaStream_t s) {
+                const float* inv, const void* tmaps, const float* X, const float* wt, float* Yb, int* status,
+                cudaStream_t s) {
     switch (m) {
-        case 8: patch_gemm_m<8>(mode, npatch, maxn, poff, pdofs, ioff, inv, X, wt, Yb, s); break;
-        case 16: patch_gemm_m<16>(mode, npatch, maxn, poff, pdofs, ioff, inv, X, wt, Yb, s); break;
-        case 32: patch_gemm_m<32>(mode, npatch, maxn, poff, pdofs, ioff, inv, X, wt, Yb, s); break;
-        default: patch_gemm_m<64>(mode, npatch, maxn, poff, pdofs, ioff, inv, X, wt, Yb, s); break;
+        case 8: patch_gemm_m<8>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
+        case 16: patch_gemm_m<16>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
+        case 32: patch_gemm_m<32>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
+        default: patch_gemm_m<64>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
     }
 }
 

@@ -28,15 +28,25 @@ void from_interleaved(int n, int nrhs, int m, const float* X, double* z, cudaStr
 void spmm(int mode, int nr, int m, const int* rp, const int* ci, const float* av, const float* X, float* Y,
           const float* B, cudaStream_t s);
 
-// dynamic shared memory of one patch_gemm CTA for patches of <= maxn DoFs
-size_t patch_gemm_smem(int maxn, int m);
+// nullptr if patch_gemm of this mode and width handles patches of <= maxn
+// DoFs on the current device, else the reason (shared or tensor memory)
+const char* patch_gemm_check(int mode, int maxn, int m);
+
+// bytes of the per-patch tensor maps of a level, and their construction
+// (host encoding from the device offsets; synchronous)
+size_t tmap_bytes(int npatch);
+void build_tmaps(int npatch, const int* poff, const long long* ioff, const float* inv, void* tmaps);
 
 // Yb[(poff[p] + a) * m + c] = wt[dof] * (K_p^{-1} R_p)[a][c], R_p[a][c] =
 // X[pdofs[poff[p] + a] * m + c]; inverses column-major with leading
-// dimension (n + 3) & ~3 at ioff[p] (the FP32 ASM layout).  maxn bounds the
-// patch size (shared memory).
+// dimension (n + 3) & ~3 at ioff[p] (the FP32 ASM layout), symmetric.
+// GEMM_TF32 runs on the tcgen05 tensor cores and reads the inverses through
+// tmaps (build_tmaps); GEMM_3XTF32 runs on the warp-level MMA.  maxn bounds
+// the patch size; *status (host-mapped) is set to 1 if a tensor-core CTA
+// gave up waiting on one of its mbarriers.
 void patch_gemm(int mode, int npatch, int maxn, int m, const int* poff, const int* pdofs, const long long* ioff,
-                const float* inv, const float* X, const float* wt, float* Yb, cudaStream_t s);
+                const float* inv, const void* tmaps, const float* X, const float* wt, float* Yb, int* status,
+                cudaStream_t s);
 
 // out[j * m + c] = alpha * sum_{q in slots(j)} Yb[sidx[q] * m + c] + beta * out[j * m + c]
 // (slots in increasing order: a fixed summation order)

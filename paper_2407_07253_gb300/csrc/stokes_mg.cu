@@ -247,6 +247,8 @@ struct stokes_mg {
                               *Yb = nullptr; };
     int bm = 0;
     std::vector<BatchLevel> bl;
+    int *bstat_h = nullptr, *bstat_d = nullptr;   // host-mapped timeout flag of the tensor-core patch GEMM
+    std::vector<void*> tmaps;                      // per relaxed level: tensor maps over the FP32 inverses
     cudaGraphExec_t bgraph[2] = {nullptr, nullptr};
     long long bgraph_launches[2] = {0, 0};
     // solve plumbing (finest level)
@@ -669,7 +671,8 @@ void b_asm(stokes_mg* h, int li, int gm, int m, const float* r, float* out, doub
     DevLevel& l = h->L[li];
     BatchLevel& B = h->bl[li];
     launch(h, PK_PATCH, s, [&] {
-        sbat::patch_gemm(gm, l.npatch, l.maxn, m, l.poff, l.pdofs, l.ioff32, l.inv32, r, l.wt32, B.Yb, s);
+        sbat::patch_gemm(gm, l.npatch, l.maxn, m, l.poff, l.pdofs, l.ioff32, l.inv32, h->tmaps[li], r, l.wt32, B.Yb,
+                         h->bstat_d, s);
     });
     launch(h, PK_PULL, s, [&] { sbat::pull_scatter(l.n, m, l.soff, l.sidx, B.Yb, (float)alpha, (float)beta, out, s); });
 }
@@ -752,6 +755,11 @@ void b_pcycle(stokes_mg* h, int li, int gm, int m, const float* b, float* e, cud
 
 // interleaved work vectors of width m on every level (kept for later calls)
 void ensure_batch(stokes_mg* h, int m) {
+    if (!h->bstat_h) {
+        CK(cudaHostAlloc((void**)&h->bstat_h, sizeof(int), cudaHostAllocMapped));
+        *h->bstat_h = 0;
+        CK(cudaHostGetDevicePointer((void**)&h->bstat_d, h->bstat_h, 0));
+    }
     if (h->bm == m) return;
     const int nl = (int)h->L.size();
     h->bl.assign(nl, BatchLevel());
@@ -761,6 +769,17 @@ void ensure_batch(stokes_mg* h, int m) {
         B.b = halloc<float>(h, N); B.e = halloc<float>(h, N); B.r = halloc<float>(h, N);
         B.d = halloc<float>(h, N); B.t = halloc<float>(h, N); B.u = halloc<float>(h, N);
         if (li + 1 < nl) B.Yb = halloc<float>(h, (size_t)h->L[li].nent * m);
+    }
+    // per-patch tensor maps over the FP32 inverses (the tensor-core TF32
+    // path), built once per handle
+    if (h->tmaps.empty()) {
+        h->tmaps.assign(nl, nullptr);
+        for (int li = 0; li + 1 < nl; ++li) h->tmaps[li] = halloc<unsigned char>(h, sbat::tmap_bytes(h->L[li].npatch));
+        CK(cudaStreamSynchronize(h->s_up));
+        for (int li = 0; li + 1 < nl; ++li) {
+            DevLevel& l = h->L[li];
+            sbat::build_tmaps(l.npatch, l.poff, l.ioff32, l.inv32, h->tmaps[li]);
+        }
     }
     CK(cudaStreamSynchronize(h->s_up));      // new chunks are pool-ordered on s_up
     for (int i = 0; i < 2; ++i) {
@@ -1838,11 +1857,13 @@ int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, 
         DeviceGuard dg(h);
         cudaStream_t s = (cudaStream_t)stream;
         const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
-        int dev_max = 0;
-        CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-        for (size_t li = 0; li + 1 < h->L.size(); ++li) {
-            if (sbat::patch_gemm_smem(h->L[li].maxn, m) > (size_t)dev_max)
-                throw StokesError(STOKES_EUNSUPPORTED, "patch too large for the batched patch GEMM at this width");
+        for (size_t li = 0; li + 1 < h->L.size(); ++li)
+            if (const char* why = sbat::patch_gemm_check(mode, h->L[li].maxn, m))
+                throw StokesError(STOKES_EUNSUPPORTED, why);
+        if (h->bstat_h && *(volatile int*)h->bstat_h) {
+            *(volatile int*)h->bstat_h = 0;
+            throw StokesError(STOKES_ECUDA, "a tensor-core patch GEMM of an earlier batched V-cycle timed out on "
+                                            "its mbarrier; its output was not written");
         }
         ensure_batch(h, m);
         const int n = h->L[0].n;
@@ -2227,6 +2248,7 @@ void stokes_mg_destroy(stokes_mg_t h) {
     }
     if (h->pinned) cudaFreeHost(h->pinned);
     if (h->pinned_H) cudaFreeHost(h->pinned_H);
+    if (h->bstat_h) cudaFreeHost(h->bstat_h);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     delete h;
 }
