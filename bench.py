@@ -35,6 +35,12 @@ def parse():
     ap.add_argument("--single", action="store_true",
                     help="one mixed-precision setup + solve and exit (profiling driver)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--batched-workload", default="th_p3_cube16",
+                    help="workload of the batched multi-RHS V-cycle measurement")
+    ap.add_argument("--nrhs", type=int, default=64)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched V-cycle measurement (profiling driver)")
     return ap.parse_args()
 
 
@@ -153,6 +159,113 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
+def batched_section(a, P, W, dev, stream, flush, hbm):
+    """Batched V-cycle (m right-hand sides interleaved, patch apply as a
+    per-patch GEMM on the tensor cores) on its own workload: time per
+    V-cycle for the whole batch in both modes against m single-RHS mixed
+    V-cycles, the end-to-end call with host buffers, and the roofline of
+    level 0's TF32 patch GEMM (one launch, CUDA events on its stream)."""
+    import numpy as np
+    import torch
+
+    w = W.workload(a.batched_workload)
+    m = a.nrhs
+
+    def make(prof_mask=0):
+        return P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                          hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=P.MIXED,
+                          stream=stream.cuda_stream, prof_mask=prof_mask)
+
+    h = make()
+    n = h.info()["n_free"][0]
+    R_host = torch.tensor(np.random.default_rng(w.seed + 1).standard_normal((m, n))).pin_memory()
+    Z_host = torch.empty_like(R_host).pin_memory()
+    R = R_host.to(dev)
+    Z = torch.empty_like(R)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        out = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return sorted(out)[len(out) // 2]
+
+    reps = max(5, a.steps)
+    l0 = h.info()["kernel_launches"]
+    h.vcycle_batched(R, P.BATCH_TF32, out=Z)
+    torch.cuda.synchronize(dev)
+    launches = h.info()["kernel_launches"] - l0
+    tf32_ms = timed(lambda: h.vcycle_batched(R, P.BATCH_TF32, out=Z), reps)
+    x3_ms = timed(lambda: h.vcycle_batched(R, P.BATCH_3XTF32, out=Z), reps)
+    k1 = min(8, m)
+    single_ms = timed(lambda: h.vcycle(R[:k1], out=Z[:k1]), reps) / k1
+
+    def e2e():
+        Rd = R_host.to(dev, non_blocking=True)
+        Zd = h.vcycle_batched(Rd, P.BATCH_TF32)
+        Z_host.copy_(Zd, non_blocking=True)
+    e2e_ms = timed(e2e, reps)
+    h.close()
+
+    # level-0 TF32 patch GEMM launches, CUDA events recorded by the library
+    # on the launching stream (eager path)
+    hp = make(1 << P._binding.PROF_PATCH)
+    npatch_levels = hp.info()["n_levels"] - 1
+    off, _ = hp.patches(0)
+    n_i = np.diff(off).astype(np.float64)
+    ld_i = np.floor((n_i + 3) / 4) * 4
+    for _ in range(3):
+        hp.vcycle_batched(R, P.BATCH_TF32, out=Z)
+    torch.cuda.synchronize(dev)
+    per = []
+    for _ in range(reps):
+        k0 = hp.prof_read(P._binding.PROF_PATCH)[0]
+        flush.fill_(1.0)
+        hp.vcycle_batched(R, P.BATCH_TF32, out=Z)
+        torch.cuda.synchronize(dev)
+        k1_ = hp.prof_read(P._binding.PROF_PATCH)[0]
+        ms = [hp.prof_read_one(P._binding.PROF_PATCH, i) for i in range(k0, k1_)]
+        per.append(ms[0])                 # the cycle's first patch launch: level 0, pre-smoothing
+    hp.close()
+    gemm_ms = sorted(per)[len(per) // 2]
+    # algorithmic bytes: FP32 inverses once + Yb written (n_i x m) + X read once
+    gemm_bytes = 4.0 * float((n_i * ld_i).sum()) + 4.0 * m * float(n_i.sum()) + 4.0 * m * n
+    gemm_flop = 2.0 * m * float((n_i * n_i).sum())
+    gemm_gbs = gemm_bytes / (gemm_ms * 1e-3) / 1e9
+    # DRAM traffic per launch: one ncu capture of the same kernel on
+    # th_p3_cube8 at 64 right-hand sides (dram__bytes_read.sum +
+    # dram__bytes_write.sum = 439.09 + 47.52 MB against 472.14 MB of
+    # algorithmic bytes), scaled to this launch by the algorithmic bytes
+    traffic, traffic_src = None, None
+    if m == 64 and w.name in ("th_p3_cube16", "th_p3_cube8"):
+        traffic = gemm_bytes * (439.092480 + 47.523840) / 472.143392
+        traffic_src = "ncu on th_p3_cube8 (486.6 MB for 472.1 MB algorithmic), scaled by algorithmic bytes"
+    return {
+        "workload": a.batched_workload, "nrhs": m, "n_free": n, "relaxed_levels": npatch_levels,
+        "vcycle_ms": {"tf32": tf32_ms, "3xtf32": x3_ms, "single_rhs_mixed_per_rhs": single_ms},
+        "rhs_per_s": {"tf32": 1e3 * m / tf32_ms, "3xtf32": 1e3 * m / x3_ms, "single_rhs": 1e3 / single_ms},
+        "speedup_vs_single_rhs": {"tf32": single_ms * m / tf32_ms, "3xtf32": single_ms * m / x3_ms},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(R_host.numel() * 8),
+                "d2h_bytes_per_step": int(Z_host.numel() * 8)},
+        "gpu_launches_per_vcycle": launches,
+        "roofline": {"kernel": "k_patch_gemm_tc (tcgen05 TF32), level 0, one launch", "bound": "hbm",
+                     "achieved": gemm_gbs, "peak": hbm, "unit": "GB/s", "frac": gemm_gbs / hbm,
+                     "bytes_per_launch": gemm_bytes, "us_per_launch": 1e3 * gemm_ms,
+                     "tf32_tflops": gemm_flop / (gemm_ms * 1e-3) / 1e12,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "l2": "flushed (256 MB write) before every timed V-cycle",
+    }
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -225,6 +338,11 @@ def main():
         h.close()
         return e0.elapsed_time(e1), its, rel, st, pr
 
+    if a.batched_only:
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm_only = json.load(open(peaks_path)).get("hbm_gbs", 6800.0) if os.path.exists(peaks_path) else 6800.0
+        print(json.dumps(batched_section(a, P, W, dev, stream, flush, hbm_only)))
+        return
     if a.single:
         ms, its, rel, st, _ = one_step(P.MIXED if a.precision == "mixed" else P.FP64)
         torch.cuda.synchronize(dev)
@@ -273,6 +391,14 @@ def main():
     patch_ms = sorted(hp.prof_read_one(P._binding.PROF_PATCH, i) for i in range(k0, k1))
     patch_ms = patch_ms[len(patch_ms) // 2] if patch_ms else 0.0     # median launch
     hp.close()
+    batched = None
+    if not a.no_batched:
+        try:
+            batched = batched_section(a, P, W, dev, stream, flush,
+                                      json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+                                      if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0)
+        except Exception as e:  # noqa: BLE001
+            batched = {"error": str(e)[:300]}
     barrier()
     if rank != 0:
         if pg is not None:
@@ -363,6 +489,8 @@ def main():
         "wall_s_timed": wall,
     }
     line["speedup_mixed_vs_fp64"] = line["fp64"]["value"] / ms_max
+    if batched is not None:
+        line["batched"] = batched
     line["clocks"] = clk.summary()
     if not a.no_cpu_baseline and world == 1:
         try:

@@ -689,6 +689,10 @@ static int device_attr(cudaDeviceAttr attr) {
     return v;
 }
 
+// Levels whose patches all have <= TC_MIN_N DoFs fill under half of a
+// 128-row MMA tile; the warp-level kernel is faster there.
+constexpr int TC_MIN_N = 64;
+
 // tensor-core TF32 path: a persistent grid of one CTA per SM (the dynamic
 // shared memory is at least half an SM's, so no two CTAs share an SM and its
 // 512 tensor-memory columns), with as many pipeline stages as fit, at most 12
@@ -737,14 +741,15 @@ static void patch_gemm_m(int mode, int npatch, int maxn, const int* poff, const 
                          const float* inv, const void* tmaps, const float* X, const float* wt, float* Yb, int* status,
                          cudaStream_t s) {
     if (mode == GEMM_3XTF32) launch_gemm_st<M, GEMM_3XTF32>(maxn, npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
+    else if (maxn <= TC_MIN_N) launch_gemm_st<M, GEMM_TF32>(maxn, npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
     else launch_tc_st<M>(npatch, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s);
 }
 
 const char* patch_gemm_check(int mode, int maxn, int m) {
-    if (mode == GEMM_3XTF32)
+    if (mode == GEMM_3XTF32 || maxn <= TC_MIN_N)
         return gemm_smem(maxn, m, MIN_STAGES) <= (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin)
                    ? nullptr
-                   : "patch too large for the shared memory of the 3xTF32 patch GEMM at this width";
+                   : "patch too large for the shared memory of the warp-MMA patch GEMM at this width";
     if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, tc::np_of(m)) > 512)
         return "patch too large for the tensor memory at this width";
     return tc_plan(maxn, m, 1).stages ? nullptr : "patch too large for the shared memory of the TF32 patch GEMM";

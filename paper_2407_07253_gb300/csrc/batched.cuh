@@ -41,7 +41,8 @@ void build_tmaps(int npatch, const int* poff, const long long* ioff, const float
 // X[pdofs[poff[p] + a] * m + c]; inverses column-major with leading
 // dimension (n + 3) & ~3 at ioff[p] (the FP32 ASM layout), symmetric.
 // GEMM_TF32 runs on the tcgen05 tensor cores and reads the inverses through
-// tmaps (build_tmaps); GEMM_3XTF32 runs on the warp-level MMA.  maxn bounds
+// tmaps (build_tmaps) when maxn > 64, else on the warp-level MMA, like
+// GEMM_3XTF32.  maxn bounds
 // the patch size; *status (host-mapped) is set to 1 if a tensor-core CTA
 // gave up waiting on one of its mbarriers.
 void patch_gemm(int mode, int npatch, int maxn, int m, const int* poff, const int* pdofs, const long long* ioff,

@@ -153,7 +153,8 @@ class Workload:
 
 
 def workload(name: str) -> Workload:
-    """The five synthetic problems used by the tests and the benchmark."""
+    """The synthetic problems used by the tests and the benchmark (the five
+    configurations plus th_p3_cube8, a small 3D case for profiling)."""
     if name == "th_p2_8x8":
         v, c = unit_square_mesh(2)
         return Workload(name, v, c, 2, TH, 2, [2], forcing="mms")
@@ -166,6 +167,11 @@ def workload(name: str) -> Workload:
     if name == "th_p3_cube16":
         v, c = kuhn_cube_mesh(4)
         return Workload(name, v, c, 2, TH, 3, [3, 2])
+    if name == "th_p3_cube8":
+        # the 16^3 problem one refinement down: same patch structure, 1/8 of
+        # the patches (a small case for profiling the batched kernels)
+        v, c = kuhn_cube_mesh(4)
+        return Workload(name, v, c, 1, TH, 3, [3, 2])
     if name == "th_p3_128x128_nu":
         v, c = unit_square_mesh(8)
         return Workload(name, v, c, 4, TH, 3, [3, 2], nu_cells=True)
