@@ -158,6 +158,45 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
  * sides are processed one after another.  r_dev and z_dev may not alias. */
 int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, void* stream);
 
+/* Discrete adjoint of stokes_solve (differentiation of the solution with
+ * respect to the forcing and the cell viscosities).  The paper does not
+ * differentiate its solver; this is the standard adjoint of the linear solve
+ * of Sec. 2 / Eq. 2.3 with the phMG-preconditioned FGMRES of Sec. 4.
+ * For a loss L(u, p) of the outputs of stokes_solve on this handle, with
+ *   gu = dL/du   device [dim][n_vel_nodes] (boundary entries are ignored:
+ *                the boundary velocity is the Dirichlet data),
+ *   gp = dL/dp   device [n_pres_nodes],
+ * stokes_adjoint_solve solves K lambda = r (K is symmetric) with the same
+ * FGMRES(restart)-phMG to ||r - K lambda|| <= tol ||r||, where r holds gu on
+ * the free velocity DoFs and nu * (gp - w (sum gp) / (sum w)) on the
+ * pressures (w_j = int psi_j: the transpose of the zero-mean normalisation
+ * of p; nu the constant viscosity given to stokes_solve).
+ *   lam_u    device [dim][n_vel_nodes] out: lambda's velocity, 0 on the boundary.
+ *   lam_p    device [n_pres_nodes] out or NULL: lambda's pressure, zero plain
+ *            mean (it is fixed only up to a constant).
+ *   grad_f   device [dim][n_vel_nodes] out or NULL: dL/df_nodal = M lam_u / nu,
+ *            M the velocity mass matrix (stokes_solve's load is F = M f).
+ * Errors: EINVAL, ENOTCONVERGED (outputs hold the last iterate), ENONFINITE. */
+int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, double nu, double tol, double* lam_u,
+                         double* lam_p, double* grad_f, int* iterations, double* final_relres, void* stream);
+
+/* dL/dnu_e = -sum_c lam_u,c[e]^T A_e u_c[e] for every cell e of the finest
+ * mesh (in the order of stokes_mg_cell_centroids, which is the order of
+ * setup's nu_cell), A_e the cell's unit-viscosity stiffness (Eq. 2.2 with
+ * nu = 1 on e), u the velocity returned by stokes_solve (boundary values
+ * included) and lam_u from stokes_adjoint_solve; the Dirichlet lifting's
+ * dependence on nu is folded in by using the full u.  Valid for a handle
+ * whose viscosity is nu_cell (stokes_solve's nu = 1).
+ *   u, lam_u  device [dim][n_vel_nodes];  grad  device [n_cells] out.
+ * Errors: EINVAL; EUNSUPPORTED for a single-level hierarchy (the finest
+ * level is then assembled on the host). */
+int stokes_grad_viscosity(stokes_mg_t h, const double* u, const double* lam_u, double* grad, void* stream);
+
+/* Cells of the finest mesh: *n_cells, and if xyz != NULL their centroids
+ * [n_cells][dim] (host) in the library's order, the order of nu_cell and of
+ * stokes_grad_viscosity's output. */
+int stokes_mg_cell_centroids(stokes_mg_t h, int* n_cells, double* xyz);
+
 /* Z = B_MG R for a batch of right-hand sides in one pass: the same V-cycle
  * as stokes_mg_vcycle (Eq. 3.2 / 3.1, Chebyshev-accelerated ASM relaxation,
  * Sec. 3.3), with the batch interleaved DoF-major on the device so that

@@ -78,6 +78,9 @@ def lib():
         "stokes_mg_setup": (c_int, [POINTER(Mesh), c_int, c_int, c_int, c_int, POINTER(Opts), P, P, POINTER(P)]),
         "stokes_mg_vcycle": (c_int, [P, P, P, c_int, P]),
         "stokes_mg_vcycle_batched": (c_int, [P, P, P, c_int, c_int, P]),
+        "stokes_adjoint_solve": (c_int, [P, P, P, c_double, c_double, P, P, P, P, P, P]),
+        "stokes_grad_viscosity": (c_int, [P, P, P, P, P]),
+        "stokes_mg_cell_centroids": (c_int, [P, P, P]),
         "stokes_solve": (c_int, [P, P, P, c_double, c_double, P, P, POINTER(c_int), POINTER(c_double), P]),
         "stokes_mg_info": (c_int, [P, POINTER(Stats)]),
         "stokes_mg_level_dofs": (c_int, [P, c_int, P, P, P]),
@@ -237,6 +240,44 @@ class StokesMG:
         Z = torch.empty_like(R) if out is None else out
         check(lib().stokes_mg_vcycle_batched(self.h, _ptr(R), _ptr(Z), nrhs, int(mode), _stream(self.stream)))
         return Z
+
+    def adjoint(self, gu, gp, nu=1.0, tol=1e-8, grad_f=True, raise_on_nonconv=True):
+        """Discrete adjoint of solve (stokes_adjoint_solve): returns (lam_u,
+        lam_p, dL/df or None, iterations, relres) for gu = dL/du [dim, nV]
+        and gp = dL/dp [nQ] (device float64)."""
+        import torch
+        gu = gu.contiguous()
+        gp = gp.contiguous()
+        lam_u = torch.empty_like(gu)
+        lam_p = torch.empty_like(gp)
+        gf = torch.empty_like(gu) if grad_f else None
+        its, rel = c_int(), c_double()
+        rc = lib().stokes_adjoint_solve(self.h, _ptr(gu), _ptr(gp), float(nu), float(tol), _ptr(lam_u), _ptr(lam_p),
+                                        _ptr(gf), byref(its), byref(rel), _stream(self.stream))
+        if rc != -4 or raise_on_nonconv:
+            check(rc)
+        return lam_u, lam_p, gf, its.value, rel.value
+
+    def grad_viscosity(self, u, lam_u):
+        """dL/dnu per finest cell (stokes_grad_viscosity)."""
+        import torch
+        n = self.n_cells()
+        g = torch.empty(n, dtype=torch.float64, device=u.device)
+        check(lib().stokes_grad_viscosity(self.h, _ptr(u.contiguous()), _ptr(lam_u.contiguous()), _ptr(g),
+                                          _stream(self.stream)))
+        return g
+
+    def n_cells(self):
+        nc = c_int()
+        check(lib().stokes_mg_cell_centroids(self.h, byref(nc), None))
+        return nc.value
+
+    def cell_centroids(self):
+        """[n_cells, dim] centroids of the finest cells, in nu_cell order."""
+        nc = self.n_cells()
+        x = np.zeros((nc, self.dim), dtype=np.float64)
+        check(lib().stokes_mg_cell_centroids(self.h, byref(c_int()), x.ctypes.data_as(c_void_p)))
+        return x
 
     def solve(self, f, g=None, nu=1.0, tol=1e-8, u=None, p=None, raise_on_nonconv=True):
         import torch

@@ -2,6 +2,8 @@
 // assembly.cuh.
 #include "assembly.cuh"
 
+#include <algorithm>
+
 #include <climits>
 
 namespace sasm {
@@ -321,7 +323,74 @@ __global__ void k_load(AsmMesh m, const double* f, const double* gD, double inv_
     }
 }
 
+// dL/dnu_e = -lambda_e^T A_e u_e summed over the velocity components, A_e
+// the cell's unit-viscosity scalar stiffness (the operator's A_e(nu_e) =
+// nu_e A_e, so the stored factors are divided by nu_e).  One warp per cell:
+// the cell's velocities are staged in shared memory, lane i takes element
+// row i, forms A_e[i][j] = sum_ab G_ab S_ab[i][j] on the fly (the same for
+// every component) and pairs it with lambda_c[i] u_c[j]; a warp sum ends it.
+__global__ void __launch_bounds__(256) k_grad_nu(AsmMesh m, const double* __restrict__ u,
+                                                 const double* __restrict__ lam, double* __restrict__ grad) {
+    extern __shared__ double us_all[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, d = m.d, nb = m.nb;
+    double* us = us_all + (size_t)w * d * nb;
+    for (int e = blockIdx.x * 8 + w; e < m.nc; e += gridDim.x * 8) {
+        const int* vc = m.vcell + (long long)e * nb;
+        for (int t = lane; t < d * nb; t += 32) {
+            const int c = t / nb, j = t - c * nb;
+            us[t] = u[(long long)c * m.nV + vc[j]];
+        }
+        __syncwarp();
+        const double* G = m.cg + (long long)e * CG_STRIDE + 1;
+        double acc = 0;
+        for (int i = lane; i < nb; i += 32) {
+            const int node = vc[i];
+            double li[3] = {0, 0, 0};
+            for (int c = 0; c < d; ++c) li[c] = lam[(long long)c * m.nV + node];
+            for (int j = 0; j < nb; ++j) {
+                double aij = 0;
+                for (int a = 0; a < d; ++a)
+                    for (int a2 = 0; a2 < d; ++a2) aij += G[a * d + a2] * m.S[(((long long)a * d + a2) * nb + i) * nb + j];
+                double sj = 0;
+                for (int c = 0; c < d; ++c) sj += li[c] * us[c * nb + j];
+                acc += aij * sj;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) grad[e] = -acc / (m.nu ? m.nu[e] : 1.0);
+        __syncwarp();
+    }
+}
+
+// out[c][i] = scale (M lambda_c)[i] on every velocity node, pulled over the
+// node's cells in adjacency order (deterministic)
+__global__ void k_mass_all(AsmMesh m, const double* __restrict__ lam, double scale, double* __restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)m.d * m.nV) return;
+    const int c = (int)(t / m.nV), node = (int)(t - (long long)c * m.nV), nb = m.nb;
+    double F = 0;
+    for (int x = m.voff[node]; x < m.voff[node + 1]; ++x) {
+        const int e = m.vadj[x] / nb, la = m.vadj[x] % nb;
+        double Fe = 0;
+        for (int bb = 0; bb < nb; ++bb)
+            Fe += m.M[(long long)la * nb + bb] * lam[(long long)c * m.nV + m.vcell[(long long)e * nb + bb]];
+        F += m.cg[(long long)e * CG_STRIDE] * Fe;
+    }
+    out[t] = scale * F;
+}
+
 }  // namespace
+
+void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, double* grad, cudaStream_t s) {
+    const size_t smem = sizeof(double) * 8 * m.d * m.nb;
+    const int grid = (int)std::min<long long>((m.nc + 7) / 8, 152LL * 16);
+    k_grad_nu<<<grid, 256, smem, s>>>(m, u, lam, grad);
+}
+
+void mass_apply_all(const AsmMesh& m, const double* lam, double scale, double* out, cudaStream_t s) {
+    const long long n = (long long)m.d * m.nV;
+    k_mass_all<<<(int)((n + 255) / 256), 256, 0, s>>>(m, lam, scale, out);
+}
 
 void cell_geometry(const AsmMesh& m, double* cg, cudaStream_t s) {
     k_cell_geometry<<<(m.nc + 127) / 128, 128, 0, s>>>(m, cg);

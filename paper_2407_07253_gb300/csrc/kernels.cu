@@ -17,6 +17,12 @@ __global__ void sub_scalar(int n, double* __restrict__ x, const double* __restri
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] -= m;
 }
 
+__global__ void sub_weighted(int n, double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ num,
+                             double den) {
+    const double m = num[0] / den;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] -= w[i] * m;
+}
+
 // ------------------------------------------------------------ reductions ---
 constexpr int MDOT_MAX = 32;
 

@@ -245,5 +245,8 @@ __global__ void scatter_idx(int n, const int* __restrict__ idx, const T* __restr
 }
 // x[i] -= mean; mean = (sum_i w[i] x[i]) / wsum from a device scalar
 __global__ void sub_scalar(int n, double* __restrict__ x, const double* __restrict__ num, double den);
+// x[i] -= w[i] * num[0] / den
+__global__ void sub_weighted(int n, double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ num,
+                             double den);
 
 }  // namespace skern

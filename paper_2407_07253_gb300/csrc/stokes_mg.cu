@@ -1936,6 +1936,79 @@ int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, do
     });
 }
 
+int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, double nu, double tol, double* lam_u,
+                         double* lam_p, double* grad_f, int* iterations, double* final_relres, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && gu && gp && lam_u, "invalid argument");
+        require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        const sfem::Level& F = h->H.levels[0];
+        const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ;
+        double* rp = h->bvec + (size_t)d * nVf;
+        // r = (gu on the free velocity DoFs, nu Pi^T gp), Pi^T gp = gp - w (1^T gp) / (w^T 1):
+        // the transpose of the zero-mean normalisation of the solve's pressure output
+        launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, gu, h->bvec); });
+        CK(cudaMemcpyAsync(rp, gp, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
+        mdot(h, nQ, 1, rp, nQ, h->ones, h->scal, nullptr, false, s);
+        launch(h, -1, s, [&] { skern::sub_weighted<<<grid_for(nQ), 256, 0, s>>>(nQ, rp, h->pint, h->scal, h->pint_sum); });
+        if (nu != 1.0) axpby_l<double>(h, nQ, 0.0, rp, nu, rp, s);
+        // K is symmetric: the adjoint system is the forward one (same FGMRES-phMG)
+        int rc = fgmres(h, h->bvec, h->xvec, tol, iterations, final_relres, s);
+        CK(cudaMemsetAsync(lam_u, 0, sizeof(double) * d * nV, s));
+        launch(h, -1, s, [&] { skern::scatter_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->xvec, lam_u); });
+        if (lam_p) {
+            CK(cudaMemcpyAsync(lam_p, h->xvec + (size_t)d * nVf, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
+            mdot(h, nQ, 1, lam_p, nQ, h->ones, h->scal, nullptr, false, s);
+            launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, lam_p, h->scal, (double)nQ); });
+        }
+        if (grad_f) {
+            // dL/df_c = M lambda_u,c / nu on every velocity node
+            if (h->L[0].dev_asm) {
+                launch(h, -1, s, [&] { sasm::mass_apply_all(h->L[0].am, lam_u, 1.0 / nu, grad_f, s); });
+            } else {
+                for (int c = 0; c < d; ++c)
+                    spmv<double>(h, -1, h->Mv, skern::SPMV_SET, lam_u + (size_t)c * nV, grad_f + (size_t)c * nV, nullptr, s);
+                if (nu != 1.0) axpby_l<double>(h, d * nV, 0.0, grad_f, 1.0 / nu, grad_f, s);
+            }
+        }
+        if (rc != STOKES_OK) g_last_error = "FGMRES did not reach the tolerance within maxit";
+        return rc;
+    });
+}
+
+int stokes_grad_viscosity(stokes_mg_t h, const double* u, const double* lam_u, double* grad, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && u && lam_u && grad, "invalid argument");
+        DeviceGuard dg(h);
+        if (!h->L[0].dev_asm)
+            throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs a device-assembled finest level "
+                                                   "(a hierarchy of more than one level)");
+        cudaStream_t s = (cudaStream_t)stream;
+        launch(h, -1, s, [&] { sasm::grad_viscosity(h->L[0].am, u, lam_u, grad, s); });
+        return STOKES_OK;
+    });
+}
+
+int stokes_mg_cell_centroids(stokes_mg_t h, int* n_cells, double* xyz) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && n_cells, "invalid argument");
+        const sfem::Mesh& m = h->H.meshes[0];
+        *n_cells = m.nc;
+        if (xyz)
+            for (int e = 0; e < m.nc; ++e)
+                for (int c = 0; c < m.d; ++c) {
+                    double x = 0;
+                    for (int v = 0; v <= m.d; ++v) x += m.X[(size_t)m.C[(size_t)e * (m.d + 1) + v] * m.d + c];
+                    xyz[(size_t)e * m.d + c] = x / (m.d + 1);
+                }
+        return STOKES_OK;
+    });
+}
+
 int stokes_mg_info(stokes_mg_t h, stokes_mg_stats* st) {
     if (!h || !st) { g_last_error = "invalid argument"; return STOKES_EINVAL; }
     fill_stats(h);
