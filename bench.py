@@ -41,6 +41,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched V-cycle measurement (profiling driver)")
+    ap.add_argument("--adjoint-workload", default="th_p3_128x128_nu",
+                    help="workload of the adjoint (gradient) measurement")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the adjoint measurement (profiling driver)")
     return ap.parse_args()
 
 
@@ -266,6 +271,69 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
     }
 
 
+def adjoint_section(a, P, W, dev, stream, flush):
+    """Forward (setup with per-cell viscosity + solve) and backward (adjoint
+    FGMRES-phMG solve, dL/df and dL/dnu kernels) for one seeded forcing and
+    one seeded loss gradient L = gu . u + gp . p, CUDA events on the stream,
+    L2 flushed before each phase."""
+    import numpy as np
+    import torch
+
+    w = W.workload(a.adjoint_workload)
+    kw = dict(barycentric=w.barycentric, hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=P.MIXED,
+              stream=stream.cuda_stream)
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                       hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
+    nc = probe.n_cells()
+    i0 = probe.info()
+    probe.close()
+    nV, nQ, d = i0["n_vel_nodes"], i0["n_pres_nodes"], w.verts.shape[1]
+    nu = W.cell_viscosity(nc, w.seed)
+    rng = np.random.default_rng(w.seed + 7)
+    f = torch.tensor(W.nodal_forcing(nV, d, w.seed).reshape(-1), device=dev)
+    gu = torch.tensor(rng.standard_normal((d, nV)), device=dev)
+    gp = torch.tensor(rng.standard_normal(nQ), device=dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def run():
+        flush.fill_(1.0)
+        e0 = ev()
+        h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, nu_cell=nu, **kw)
+        u, p, its, rel = h.solve(f, tol=TOL)
+        e1 = ev()
+        e1.synchronize()
+        flush.fill_(1.0)
+        e2 = ev()
+        lam_u, _, gf, aits, arel = h.adjoint(gu, gp, tol=TOL)
+        e3 = ev()
+        gnu = h.grad_viscosity(u, lam_u)
+        e4 = ev()
+        e4.synchronize()
+        out = dict(forward=e0.elapsed_time(e1), adjoint_solve=e2.elapsed_time(e3), grad_nu=e3.elapsed_time(e4),
+                   its=its, adjoint_its=aits, adjoint_relres=arel, gnu_norm=float(gnu.norm()),
+                   launches=h.info()["kernel_launches"])
+        h.close()
+        return out
+
+    run()                                   # warm-up
+    reps = [run() for _ in range(max(3, min(a.steps, 5)))]
+    med = {k: sorted(r[k] for r in reps)[len(reps) // 2] for k in ("forward", "adjoint_solve", "grad_nu")}
+    return {
+        "workload": a.adjoint_workload, "n_cells": nc, "n_free": i0["n_free"][0],
+        "forward_ms": med["forward"], "backward_ms": med["adjoint_solve"] + med["grad_nu"],
+        "adjoint_solve_ms": med["adjoint_solve"], "grad_nu_kernel_ms": med["grad_nu"],
+        "backward_over_forward": (med["adjoint_solve"] + med["grad_nu"]) / med["forward"],
+        "fgmres_its": reps[-1]["its"], "adjoint_fgmres_its": reps[-1]["adjoint_its"],
+        "adjoint_relres": reps[-1]["adjoint_relres"], "tol": TOL,
+        "loss": "L = gu . u + gp . p, gu and gp seeded N(0, 1); f seeded U[-1, 1] nodal; nu_e = exp(N(0, 1/4))",
+        "l2": "flushed (256 MB write) before the forward and before the backward",
+    }
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -338,6 +406,9 @@ def main():
         h.close()
         return e0.elapsed_time(e1), its, rel, st, pr
 
+    if a.adjoint_only:
+        print(json.dumps(adjoint_section(a, P, W, dev, stream, flush)))
+        return
     if a.batched_only:
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         hbm_only = json.load(open(peaks_path)).get("hbm_gbs", 6800.0) if os.path.exists(peaks_path) else 6800.0
@@ -399,6 +470,12 @@ def main():
                                       if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0)
         except Exception as e:  # noqa: BLE001
             batched = {"error": str(e)[:300]}
+    adj = None
+    if not a.no_adjoint:
+        try:
+            adj = adjoint_section(a, P, W, dev, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            adj = {"error": str(e)[:300]}
     barrier()
     if rank != 0:
         if pg is not None:
@@ -491,6 +568,8 @@ def main():
     line["speedup_mixed_vs_fp64"] = line["fp64"]["value"] / ms_max
     if batched is not None:
         line["batched"] = batched
+    if adj is not None:
+        line["adjoint"] = adj
     line["clocks"] = clk.summary()
     if not a.no_cpu_baseline and world == 1:
         try:
