@@ -158,6 +158,37 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
  * sides are processed one after another.  r_dev and z_dev may not alias. */
 int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, void* stream);
 
+/* FBF(phMG) for Scott-Vogelius (Eq. fbf, Fig. afbf_solver): FGMRES on the SV
+ * system of the finest (Alfeld-refined) mesh, right-preconditioned by
+ *   P^-1 = [I -A~^-1 B^T; 0 I] diag(A~^-1, S~^-1) [I 0; -B A~^-1 I],
+ * with A~^-1 one phMG V-cycle on the velocity block and S~^-1 the inverse of
+ * the block-diagonal discontinuous pressure mass matrix.  The velocity block
+ * is the vector Laplacian, block diagonal over the components with the same
+ * scalar stiffness in each, so A~^-1 is a scalar phMG V-cycle applied to
+ * every component; its relaxation is Chebyshev(nu) around one additive
+ * Schwarz sweep over ASMStarPC patches (the velocity nodes on the open star of
+ * each mesh vertex, Sec. 3.3), with the hierarchy, Chebyshev interval and
+ * lambda_max estimate of the monolithic solver.  S~^-1 is
+ * -diag_e(nu_e M_p,e^-1): the Schur complement -B A^-1 B^T is negative.
+ *   Arguments as stokes_mg_setup (family SV and the barycentric finest mesh
+ *   are implied; opts.patch_solver is ignored: Gauss-Jordan).
+ * On the returned handle:
+ *   stokes_solve / stokes_adjoint_solve   run FGMRES-FBF(phMG) on the Stokes system;
+ *   stokes_mg_vcycle                      is A~^-1 on one velocity component
+ *                                         ([n_free(level 0)], the scalar level);
+ *   stokes_mg_info, stokes_mg_level_dofs, stokes_mg_get_patches, stokes_mg_asm ...
+ *                                         describe the scalar velocity levels;
+ *   stokes_mg_nodes and the stats' node counts describe the SV Stokes fields.
+ *   stokes_grad_viscosity returns EUNSUPPORTED.
+ * Errors: as stokes_mg_setup. */
+int stokes_fbf_setup(const stokes_mesh* coarse, int n_refine, int k, const stokes_mg_opts* opts,
+                     const double* nu_cell, void* stream, stokes_mg_t* out);
+
+/* z = P^-1 r (Eq. fbf) on an FBF handle.  r_dev, z_dev: device
+ * [d * n_free_vel + n_pres] in the Stokes free order (velocity components
+ * blocked, then pressure); may not alias.  Errors: EINVAL (not an FBF handle). */
+int stokes_fbf_apply(stokes_mg_t h, const double* r_dev, double* z_dev, void* stream);
+
 /* Discrete adjoint of stokes_solve (differentiation of the solution with
  * respect to the forcing and the cell viscosities).  The paper does not
  * differentiate its solver; this is the standard adjoint of the linear solve

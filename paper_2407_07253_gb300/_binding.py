@@ -76,6 +76,8 @@ def lib():
     sig = {
         "stokes_mg_default_opts": (None, [POINTER(Opts)]),
         "stokes_mg_setup": (c_int, [POINTER(Mesh), c_int, c_int, c_int, c_int, POINTER(Opts), P, P, POINTER(P)]),
+        "stokes_fbf_setup": (c_int, [POINTER(Mesh), c_int, c_int, POINTER(Opts), P, P, POINTER(P)]),
+        "stokes_fbf_apply": (c_int, [P, P, P, P]),
         "stokes_mg_vcycle": (c_int, [P, P, P, c_int, P]),
         "stokes_mg_vcycle_batched": (c_int, [P, P, P, c_int, c_int, P]),
         "stokes_adjoint_solve": (c_int, [P, P, P, c_double, c_double, P, P, P, P, P, P]),
@@ -156,7 +158,9 @@ class StokesMG:
     """Handle on a phMG hierarchy built by stokes_mg_setup."""
 
     def __init__(self, verts, cells, n_refine, family, k, barycentric=False, nu_cell=None,
-                 stream=None, **opts):
+                 stream=None, fbf=False, **opts):
+        """fbf=True builds the FBF(phMG) solver of Eq. fbf instead
+        (stokes_fbf_setup; Scott-Vogelius on the Alfeld-refined finest mesh)."""
         verts = np.ascontiguousarray(verts, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         self._mesh = Mesh(verts.shape[1], verts.shape[0], cells.shape[0],
@@ -169,9 +173,16 @@ class StokesMG:
             self._keep = self._keep + (nu,)
         self.h = c_void_p()
         self.stream = stream
-        check(lib().stokes_mg_setup(byref(self._mesh), int(n_refine), int(bool(barycentric)), int(family), int(k),
-                                    byref(self.opts), None if nu is None else nu.ctypes.data_as(c_void_p),
-                                    _stream(stream), byref(self.h)))
+        nu_p = None if nu is None else nu.ctypes.data_as(c_void_p)
+        if fbf:
+            if family != SV:
+                raise ValueError("FBF is the Scott-Vogelius solver (family SV)")
+            check(lib().stokes_fbf_setup(byref(self._mesh), int(n_refine), int(k), byref(self.opts), nu_p,
+                                         _stream(stream), byref(self.h)))
+        else:
+            check(lib().stokes_mg_setup(byref(self._mesh), int(n_refine), int(bool(barycentric)), int(family), int(k),
+                                        byref(self.opts), nu_p, _stream(stream), byref(self.h)))
+        self.is_fbf = bool(fbf)
         self.dim = verts.shape[1]
 
     # ---- queries
@@ -229,6 +240,13 @@ class StokesMG:
         nrhs = 1 if r.dim() == 1 else r.shape[0]
         z = torch.empty_like(r) if out is None else out
         check(lib().stokes_mg_vcycle(self.h, _ptr(r.contiguous()), _ptr(z), nrhs, _stream(self.stream)))
+        return z
+
+    def fbf_apply(self, r, out=None):
+        """z = P^-1 r of Eq. fbf on the Stokes free DoFs (stokes_fbf_apply)."""
+        import torch
+        z = torch.empty_like(r) if out is None else out
+        check(lib().stokes_fbf_apply(self.h, _ptr(r.contiguous()), _ptr(z), _stream(self.stream)))
         return z
 
     def vcycle_batched(self, R, mode=BATCH_3XTF32, out=None):

@@ -1370,7 +1370,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
             H.t_callbacks_ms += tcb - tc;
             tc = tcb;
         }
-        if (l + 1 < ls.size()) build_patches(m, topo[L.mesh_index], L);
+        if (l + 1 < ls.size() && !spec.skip_patches) build_patches(m, topo[L.mesh_index], L);
         H.t_spaces_ms += tb - ta;
         H.t_matrices_ms += tc - tb;
         H.t_patches_ms += now_ms() - tc;
@@ -1391,6 +1391,81 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     }
     H.t_transfers_ms = now_ms() - tt;
     H.t_assembly_ms = now_ms() - t1 - H.t_callbacks_ms;
+}
+
+// rows [0, nr) and columns [0, nc) of a CSR (the column order of each row kept)
+static CSR csr_leading_block(const CSR& a, int nr, int nc) {
+    CSR b;
+    b.nr = nr;
+    b.ncol = nc;
+    b.rp.assign(nr + 1, 0);
+    for (int r = 0; r < nr; ++r) {
+        int cnt = 0;
+        for (int p = a.rp[r]; p < a.rp[r + 1]; ++p) cnt += a.ci[p] < nc;
+        b.rp[r + 1] = b.rp[r] + cnt;
+    }
+    b.ci.resize(b.rp[nr]);
+    b.v.resize(b.rp[nr]);
+    for (int r = 0; r < nr; ++r) {
+        int o = b.rp[r];
+        for (int p = a.rp[r]; p < a.rp[r + 1]; ++p)
+            if (a.ci[p] < nc) { b.ci[o] = a.ci[p]; b.v[o] = a.v[p]; ++o; }
+    }
+    return b;
+}
+
+void velocity_hierarchy(const Hierarchy& S, Hierarchy& A) {
+    A.meshes = S.meshes;
+    A.parents = S.parents;
+    A.levels.assign(S.levels.size(), Level());
+    for (size_t l = 0; l < S.levels.size(); ++l) {
+        const Level& F = S.levels[l];
+        Level& L = A.levels[l];
+        if (F.K.rp.empty()) throw std::runtime_error("velocity_hierarchy needs host-assembled operators");
+        L.d = F.d;
+        L.family = 0;
+        L.k = F.k;
+        L.mesh_index = F.mesh_index;
+        L.p_level = F.p_level;
+        L.V = F.V;
+        L.vfree = F.vfree;
+        L.nVf = F.nVf;
+        L.nQ = 0;
+        L.n_free = F.nVf;
+        L.K = csr_leading_block(F.K, F.nVf, F.nVf);
+        L.RT = F.RT;
+        L.nu_cells = F.nu_cells;
+        L.host_matrices = true;
+        if (l + 1 < S.levels.size()) {
+            L.P = csr_leading_block(F.P, F.nVf, S.levels[l + 1].nVf);
+            L.R = transpose(L.P);
+            // ASMStarPC: the free nodes whose owning entity contains vertex v
+            const int nv = S.meshes[F.mesh_index].nv;
+            std::vector<std::vector<int>> star(nv);
+            for (int i = 0; i < F.V.n; ++i) {
+                const int f = F.vfree[i];
+                if (f < 0) continue;
+                for (int v : F.V.support[i])
+                    if (v >= 0) star[v].push_back(f);
+            }
+            L.patch_off.assign(1, 0);
+            for (int v = 0; v < nv; ++v) {
+                if (star[v].empty()) continue;
+                std::sort(star[v].begin(), star[v].end());
+                L.patch_dofs.insert(L.patch_dofs.end(), star[v].begin(), star[v].end());
+                L.patch_off.push_back((int)L.patch_dofs.size());
+                L.patch_nv.push_back(0);      // no velocity/pressure structure: Gauss-Jordan inverses
+            }
+        }
+    }
+}
+
+std::vector<double> reference_mass(int d, int k) {
+    RefElement e;
+    e.init(d, k);
+    RefTensors t;
+    t.init(e, e);
+    return t.M;
 }
 
 }  // namespace sfem

@@ -121,6 +121,7 @@ struct HierarchySpec {
     // is a long chain of small steps that then runs while the host builds the
     // other levels), then finest to coarsest
     bool coarsest_first = false;
+    bool skip_patches = false;                // no Vanka patches (a hierarchy wanted for its operators)
 };
 
 struct Hierarchy {
@@ -130,6 +131,19 @@ struct Hierarchy {
     double t_mesh_ms = 0, t_assembly_ms = 0;
     double t_spaces_ms = 0, t_matrices_ms = 0, t_patches_ms = 0, t_transfers_ms = 0, t_callbacks_ms = 0;
 };
+
+// The scalar hierarchy of one velocity component of a host-assembled Stokes
+// hierarchy S (the velocity block of Eq. 2.3 is the vector Laplacian, block
+// diagonal over the components with one scalar stiffness A_s): per level the
+// velocity space and free nodes, K = A_s (the component-0 block of S's K),
+// P and R = the component-0 blocks of S's transfers, and ASMStarPC patches,
+// the free nodes on the open star of every mesh vertex (the nodes whose
+// owning entity contains the vertex).  No pressure.
+void velocity_hierarchy(const Hierarchy& S, Hierarchy& A);
+
+// Mass matrix [nb][nb] of the degree-k Lagrange element on the reference
+// d-simplex (exact).
+std::vector<double> reference_mass(int d, int k);
 
 // Build the whole host hierarchy; throws std::runtime_error on invalid input.
 // on_level(l, stage), if given, runs twice per level: stage 0 once its

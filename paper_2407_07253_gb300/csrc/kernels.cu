@@ -23,6 +23,18 @@ __global__ void sub_weighted(int n, double* __restrict__ x, const double* __rest
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] -= w[i] * m;
 }
 
+__global__ void block_mass_inverse(int nc, int nb, const int* __restrict__ qcell, const double* __restrict__ minv,
+                                   const double* __restrict__ scale, const double* __restrict__ y, double* __restrict__ z) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nc * nb;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / nb), a = (int)(t - (long long)e * nb);
+        const int* q = qcell + (long long)e * nb;
+        double acc = 0;
+        for (int b = 0; b < nb; ++b) acc += minv[a * nb + b] * y[q[b]];
+        z[q[a]] = scale[e] * acc;
+    }
+}
+
 // ------------------------------------------------------------ reductions ---
 constexpr int MDOT_MAX = 32;
 

@@ -245,6 +245,11 @@ __global__ void scatter_idx(int n, const int* __restrict__ idx, const T* __restr
 }
 // x[i] -= mean; mean = (sum_i w[i] x[i]) / wsum from a device scalar
 __global__ void sub_scalar(int n, double* __restrict__ x, const double* __restrict__ num, double den);
+// z[qcell[e][a]] = scale[e] * sum_b minv[a][b] y[qcell[e][b]]: a block-diagonal
+// operator whose blocks are one reference matrix times a per-cell scale (the
+// cells own disjoint index sets)
+__global__ void block_mass_inverse(int nc, int nb, const int* __restrict__ qcell, const double* __restrict__ minv,
+                                   const double* __restrict__ scale, const double* __restrict__ y, double* __restrict__ z);
 // x[i] -= w[i] * num[0] / den
 __global__ void sub_weighted(int n, double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ num,
                              double den);

@@ -214,6 +214,20 @@ struct Prof {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
 };
 
+// FBF(phMG) mode (Eq. fbf): the handle's levels are the scalar velocity
+// hierarchy of A~^-1; the outer FGMRES works on the SV Stokes system of the
+// finest level, kept here with the pressure mass blocks of S~^-1.
+struct FbfData {
+    sfem::Level S0;                    // the finest SV level (host-assembled K, Mv, KfD, spaces)
+    int nS = 0, nu = 0, nvf = 0;       // Stokes free DoFs, free velocity DoFs, per component
+    int ncell = 0, nbq = 0;            // finest cells, pressure nodes per cell
+    DevCSR K;                          // the Stokes operator (FP64)
+    double *a = nullptr, *t = nullptr, *w = nullptr, *r = nullptr;
+    double* minv = nullptr;            // [nbq][nbq] inverse reference pressure mass matrix
+    double* scale = nullptr;           // [ncell] -nu_e / |det J_e|
+    int* qcell = nullptr;              // [ncell][nbq] pressure nodes of each cell
+};
+
 }  // namespace
 
 struct stokes_mg {
@@ -249,6 +263,7 @@ struct stokes_mg {
     std::vector<BatchLevel> bl;
     int *bstat_h = nullptr, *bstat_d = nullptr;   // host-mapped timeout flag of the tensor-core patch GEMM
     std::vector<void*> tmaps;                      // per relaxed level: tensor maps over the FP32 inverses
+    std::unique_ptr<FbfData> fbf;                  // FBF(phMG) mode (stokes_fbf_setup)
     cudaGraphExec_t bgraph[2] = {nullptr, nullptr};
     long long bgraph_launches[2] = {0, 0};
     // solve plumbing (finest level)
@@ -287,6 +302,10 @@ struct stokes_mg {
 namespace {
 
 enum ProfKind { PK_PATCH = 0, PK_SPMV = 1, PK_GJ = 2, PK_PULL = 3, PK_TRANSFER = 4 };
+
+// the Stokes level the solve works on: the finest level of the hierarchy, or
+// in FBF mode the SV level kept beside the scalar velocity hierarchy
+const sfem::Level& finest_stokes(const stokes_mg* h) { return h->fbf ? h->fbf->S0 : h->H.levels[0]; }
 
 template <typename F>
 void launch(stokes_mg* h, int kind, cudaStream_t s, F&& f) {
@@ -930,11 +949,13 @@ __global__ void splitmix_uniform(int n, unsigned long long seed, unsigned long l
     }
 }
 
-// FGMRES(restart) right-preconditioned by the V-cycle (Sec. 4), x0 = 0.
-int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, double* rel_out, cudaStream_t s) {
-    DevLevel& l0 = h->L[0];
-    const int n = l0.n, m = h->restart;
-    const int prec = h->opts.precision;
+using Precond = std::function<void(const double*, double*, cudaStream_t)>;
+
+// FGMRES(restart) for K x = b right-preconditioned by M (Sec. 4), x0 = 0;
+// rscr is an n-vector of scratch.
+int fgmres_op(stokes_mg* h, const DevCSR& K, int n, double* rscr, const Precond& M, const double* b, double* x,
+              double tol, int* its_out, double* rel_out, cudaStream_t s) {
+    const int m = h->restart;
     launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(n), 256, 0, s>>>(n, 0.0, x); });
     mdot(h, n, 1, b, n, b, h->hn, nullptr, true, s);
     const double beta0 = d2h_scalar(h, h->hn, s);
@@ -946,7 +967,7 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
         if (rel_out) *rel_out = 0.0;
         return STOKES_OK;
     }
-    double* r = l0.t64;
+    double* r = rscr;
     const double* rcur = b;
     double beta = beta0;
     bool converged = false;
@@ -964,10 +985,8 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
             double* vj = h->V + (long long)j * n;
             double* zj = h->Z + (long long)j * n;
             double* w = h->V + (long long)(j + 1) * n;
-            CK(cudaMemcpyAsync(h->vin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            vcycle_run(h, prec, s);
-            CK(cudaMemcpyAsync(zj, h->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            spmv<double>(h, PK_SPMV, l0.K, skern::SPMV_SET, zj, w, nullptr, s);
+            M(vj, zj, s);
+            spmv<double>(h, PK_SPMV, K, skern::SPMV_SET, zj, w, nullptr, s);
             cgs2(h, n, j + 1, h->V, w, h->h, h->y, h->hn, s);
             launch(h, -1, s, [&] {
                 skern::fgmres_givens<<<1, 1, 0, s>>>(j, m, h->Hh, h->h, h->hn, h->cs, h->sn, h->g, h->resid);
@@ -983,7 +1002,7 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
         launch(h, -1, s, [&] { skern::fgmres_backsolve<<<1, 1, 0, s>>>(jend, m, h->Hh, h->g, h->y); });
         maxpy_l(h, n, jend, h->Z, n, h->y, 1.0, x, s);
         if (converged) break;
-        spmv<double>(h, PK_SPMV, l0.K, skern::SPMV_RESID, x, r, b, s);
+        spmv<double>(h, PK_SPMV, K, skern::SPMV_RESID, x, r, b, s);
         mdot(h, n, 1, r, n, r, h->hn, nullptr, true, s);
         beta = d2h_scalar(h, h->hn, s);
         rel = beta / beta0;
@@ -993,6 +1012,114 @@ int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, d
     if (its_out) *its_out = its;
     if (rel_out) *rel_out = rel;
     return converged ? STOKES_OK : STOKES_ENOTCONVERGED;
+}
+
+void fbf_apply(stokes_mg* h, const double* r, double* z, cudaStream_t s);
+
+// FGMRES-phMG on the finest level (Sec. 4), or FGMRES-FBF(phMG) in FBF mode
+int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, double* rel_out, cudaStream_t s) {
+    if (h->fbf) {
+        FbfData& F = *h->fbf;
+        return fgmres_op(h, F.K, F.nS, F.r, [h](const double* v, double* z, cudaStream_t st) { fbf_apply(h, v, z, st); },
+                         b, x, tol, its_out, rel_out, s);
+    }
+    DevLevel& l0 = h->L[0];
+    const int n = l0.n, prec = h->opts.precision;
+    return fgmres_op(h, l0.K, n, l0.t64,
+                     [h, n, prec](const double* v, double* z, cudaStream_t st) {
+                         CK(cudaMemcpyAsync(h->vin, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+                         vcycle_run(h, prec, st);
+                         CK(cudaMemcpyAsync(z, h->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+                     },
+                     b, x, tol, its_out, rel_out, s);
+}
+
+// P^-1 r of Eq. fbf on the Stokes free DoFs (velocity components blocked,
+// then pressure): a = A~^-1 r_u, z_p = S~^-1 (r_p - B a),
+// z_u = A~^-1 (r_u - B^T z_p).  A~^-1 is the scalar phMG V-cycle on every
+// velocity component; B a and B^T z_p come from the Stokes K applied to
+// (a, 0) and (0, z_p); S~^-1 is the block-diagonal -nu_e M_p,e^-1.
+void fbf_apply(stokes_mg* h, const double* r, double* z, cudaStream_t s) {
+    FbfData& F = *h->fbf;
+    const int nu = F.nu, nS = F.nS, nvf = F.nvf, d = F.S0.d, np = nS - nu, prec = h->opts.precision;
+    auto vcycles = [&](const double* in, double* out) {
+        for (int c = 0; c < d; ++c) {
+            CK(cudaMemcpyAsync(h->vin, in + (size_t)c * nvf, sizeof(double) * nvf, cudaMemcpyDeviceToDevice, s));
+            vcycle_run(h, prec, s);
+            CK(cudaMemcpyAsync(out + (size_t)c * nvf, h->vout, sizeof(double) * nvf, cudaMemcpyDeviceToDevice, s));
+        }
+    };
+    vcycles(r, F.a);
+    CK(cudaMemcpyAsync(F.t, F.a, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(F.t + nu, 0, sizeof(double) * np, s));
+    spmv<double>(h, PK_SPMV, F.K, skern::SPMV_SET, F.t, F.w, nullptr, s);          // w_p = B a
+    axpby_l<double>(h, np, 1.0, r + nu, -1.0, F.w + nu, s);                         // w_p = r_p - B a
+    launch(h, -1, s, [&] {
+        skern::block_mass_inverse<<<grid_for((long long)F.ncell * F.nbq), 256, 0, s>>>(F.ncell, F.nbq, F.qcell, F.minv,
+                                                                                      F.scale, F.w + nu, z + nu);
+    });
+    CK(cudaMemsetAsync(F.t, 0, sizeof(double) * nu, s));
+    CK(cudaMemcpyAsync(F.t + nu, z + nu, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
+    spmv<double>(h, PK_SPMV, F.K, skern::SPMV_SET, F.t, F.w, nullptr, s);          // w_u = B^T z_p
+    axpby_l<double>(h, nu, 1.0, r, -1.0, F.w, s);                                   // w_u = r_u - B^T z_p
+    vcycles(F.w, z);
+}
+
+// FBF data on the device: the Stokes operator, work vectors, and S~^-1 as
+// a reference inverse mass matrix with one scale per cell
+void setup_fbf(stokes_mg* h, cudaStream_t s) {
+    FbfData& F = *h->fbf;
+    const sfem::Level& S0 = F.S0;
+    const sfem::Mesh& m = h->H.meshes[S0.mesh_index];
+    F.K = upload_csr(h, S0.K, false, s);
+    F.a = halloc<double>(h, F.nu);
+    F.t = halloc<double>(h, F.nS);
+    F.w = halloc<double>(h, F.nS);
+    F.r = halloc<double>(h, F.nS);
+    const int d = m.d;
+    F.ncell = m.nc;
+    F.nbq = S0.Q.nb;
+    // inverse of the reference mass matrix of the pressure degree (Gauss-Jordan, partial pivoting)
+    const int nb = F.nbq;
+    std::vector<double> Mr = sfem::reference_mass(d, S0.k - 1), inv((size_t)nb * nb, 0.0);
+    for (int i = 0; i < nb; ++i) inv[(size_t)i * nb + i] = 1.0;
+    for (int c = 0; c < nb; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < nb; ++r)
+            if (std::fabs(Mr[(size_t)r * nb + c]) > std::fabs(Mr[(size_t)piv * nb + c])) piv = r;
+        for (int j = 0; j < nb; ++j) {
+            std::swap(Mr[(size_t)c * nb + j], Mr[(size_t)piv * nb + j]);
+            std::swap(inv[(size_t)c * nb + j], inv[(size_t)piv * nb + j]);
+        }
+        const double p = Mr[(size_t)c * nb + c];
+        if (p == 0.0) throw StokesError(STOKES_ESINGULAR, "singular reference pressure mass matrix");
+        for (int j = 0; j < nb; ++j) { Mr[(size_t)c * nb + j] /= p; inv[(size_t)c * nb + j] /= p; }
+        for (int r = 0; r < nb; ++r) {
+            if (r == c) continue;
+            const double f = Mr[(size_t)r * nb + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < nb; ++j) {
+                Mr[(size_t)r * nb + j] -= f * Mr[(size_t)c * nb + j];
+                inv[(size_t)r * nb + j] -= f * inv[(size_t)c * nb + j];
+            }
+        }
+    }
+    F.minv = hupload(h, inv, s);
+    // scale_e = -nu_e / |det J_e|: M_p,e = |det J_e| M_ref on an affine cell
+    std::vector<double> scale(m.nc);
+    for (int e = 0; e < m.nc; ++e) {
+        const int* C = &m.C[(size_t)e * (d + 1)];
+        double J[9];
+        for (int a = 0; a < d; ++a)
+            for (int c = 0; c < d; ++c) J[c * d + a] = m.X[(size_t)C[a + 1] * d + c] - m.X[(size_t)C[0] * d + c];
+        const double det = d == 2 ? J[0] * J[3] - J[1] * J[2]
+                                  : J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                                        J[2] * (J[3] * J[7] - J[4] * J[6]);
+        const double nue = S0.nu_cells.empty() ? 1.0 : S0.nu_cells[e];
+        scale[e] = -nue / std::fabs(det);
+    }
+    F.scale = hupload(h, scale, s);
+    F.qcell = hupload(h, S0.Q.cell_nodes, s);
 }
 
 // ---------------------------------------------------------------- setup --
@@ -1312,6 +1439,9 @@ void upload_coarse(stokes_mg* h, cudaStream_t su) {
         A[(size_t)r * nb + n] = C.pint[q];
         A[(size_t)n * nb + r] = C.pint[q];
     }
+    // no pressure (the scalar velocity hierarchy of FBF): [A 0; 0 1], whose
+    // inverse applied to (b, 0) is (A^-1 b, 0)
+    if (C.nQ == 0) A[(size_t)n * nb + n] = 1.0;
     h->Cinv = hupload(h, A, su);
     h->c_ipiv = dalloc<int>(nb);
     h->c_colk = dalloc<double>(nb);
@@ -1407,7 +1537,7 @@ void finish_coarse(stokes_mg* h, cudaStream_t s) {
 }
 
 void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
-    const sfem::Level& F = h->H.levels[0];
+    const sfem::Level& F = finest_stokes(h);
     const int d = F.d;
     if (F.host_matrices) {
         h->Mv = upload_csr(h, F.Mv, false, s);
@@ -1450,10 +1580,11 @@ void alloc_level_krylov(stokes_mg* h, int li, cudaStream_t s) {
 // FGMRES / Arnoldi buffers sized by the finest level
 void alloc_krylov(stokes_mg* h, cudaStream_t s) {
     const int n0 = h->L[0].n;
+    const int nK = h->fbf ? std::max(n0, h->fbf->nS) : n0;     // FBF: FGMRES runs on the Stokes system
     const int m = h->restart;
     const int basis = std::max(m + 1, skern::HESS_MAX + 1);
-    h->V = halloc<double>(h, (size_t)basis * n0);
-    h->Z = halloc<double>(h, (size_t)m * n0);
+    h->V = halloc<double>(h, (size_t)basis * nK);
+    h->Z = halloc<double>(h, (size_t)m * nK);
     h->Hh = halloc<double>(h, (size_t)(basis + 1) * basis);
     h->cs = halloc<double>(h, basis);
     h->sn = halloc<double>(h, basis);
@@ -1507,8 +1638,8 @@ void fill_stats(stokes_mg* h) {
         st.patch_entries[i] = sq;
         st.lmax[i] = i < (int)h->L.size() ? h->L[i].lmax : 0.0;
     }
-    st.n_vel_nodes = h->H.levels[0].V.n;
-    st.n_pres_nodes = h->H.levels[0].nQ;
+    st.n_vel_nodes = finest_stokes(h).V.n;
+    st.n_pres_nodes = finest_stokes(h).nQ;
 }
 
 int fail(const StokesError& e) {
@@ -1582,8 +1713,9 @@ void stokes_mg_default_opts(stokes_mg_opts* o) {
     o->use_graph = 1;
 }
 
-int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_finest, int family, int k,
-                    const stokes_mg_opts* opts, const double* nu_cell, void* stream, stokes_mg_t* out) {
+namespace {
+int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, int family, int k,
+               const stokes_mg_opts* opts, const double* nu_cell, void* stream, stokes_mg_t* out, bool fbf_mode) {
     g_last_error.clear();
     if (!out) { g_last_error = "out is NULL"; return STOKES_EINVAL; }
     *out = nullptr;
@@ -1643,7 +1775,8 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         } else {
             require(false, "unknown hierarchy");
         }
-        require(!(family == STOKES_SV && spec.schedule.size() < 2), "Scott-Vogelius needs at least one p-coarsening");
+        require(fbf_mode || !(family == STOKES_SV && spec.schedule.size() < 2),
+                "Scott-Vogelius needs at least one p-coarsening");
         const bool want32 = o.precision == STOKES_MIXED;
         double t_cb_upload = 0;
         std::unique_ptr<Launcher> launcher;
@@ -1764,7 +1897,41 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
                 });
             };
         }
-        sfem::build_hierarchy(cm, spec, nu_cell, h->H, on_level);
+        if (fbf_mode) {
+            // FBF(phMG): the SV Stokes hierarchy is built on the host for its
+            // operators only; the handle's levels become its scalar velocity
+            // hierarchy (ASMStarPC patches), set up level by level as below
+            sfem::HierarchySpec sp = spec;
+            sp.device_assembly = false;
+            sp.coarsest_first = false;
+            sp.skip_patches = true;
+            sfem::Hierarchy S;
+            sfem::build_hierarchy(cm, sp, nu_cell, S, nullptr);
+            h->fbf.reset(new FbfData());
+            FbfData& F = *h->fbf;
+            F.S0 = S.levels[0];
+            F.nS = F.S0.n_free;
+            F.nvf = F.S0.nVf;
+            F.nu = F.S0.d * F.S0.nVf;
+            sfem::velocity_hierarchy(S, h->H);
+            h->H.t_mesh_ms = S.t_mesh_ms;
+            h->H.t_assembly_ms = S.t_assembly_ms;
+            h->H.t_spaces_ms = S.t_spaces_ms;
+            h->H.t_matrices_ms = S.t_matrices_ms;
+            h->H.t_transfers_ms = S.t_transfers_ms;
+            h->opts.patch_solver = 1;          // dense SPD star blocks: Gauss-Jordan
+            const int nlv = (int)h->H.levels.size();
+            if (on_level) {
+                on_level(nlv - 1, 0);
+                on_level(nlv - 1, 1);
+                for (int li = 0; li + 1 < nlv; ++li) {
+                    on_level(li, 0);
+                    on_level(li, 1);
+                }
+            }
+        } else {
+            sfem::build_hierarchy(cm, spec, nu_cell, h->H, on_level);
+        }
         if (!o.host_only) mark(h.get(), "host hierarchy built", h->s_up);
         h->st.t_mesh_ms = h->H.t_mesh_ms;
         h->st.t_assembly_ms = h->H.t_assembly_ms;
@@ -1787,6 +1954,7 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
         for (int li = 0; li + 1 < nl; ++li) upload_transfers(h.get(), li, want32, h->s_up);
         const int n0 = h->L[0].n;
         setup_solve_buffers(h.get(), h->s_up);
+        if (h->fbf) setup_fbf(h.get(), h->s_up);
         mark(h.get(), "transfers uploaded", h->s_up);
         CK(cudaStreamSynchronize(h->s_up));
         h->st.t_upload_ms = t_cb_upload;
@@ -1829,6 +1997,28 @@ int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_fin
     }
     *out = h.release();
     return STOKES_OK;
+}
+}  // namespace
+
+int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_finest, int family, int k,
+                    const stokes_mg_opts* opts, const double* nu_cell, void* stream, stokes_mg_t* out) {
+    return setup_impl(coarse, n_refine, barycentric_finest, family, k, opts, nu_cell, stream, out, false);
+}
+
+int stokes_fbf_setup(const stokes_mesh* coarse, int n_refine, int k, const stokes_mg_opts* opts, const double* nu_cell,
+                     void* stream, stokes_mg_t* out) {
+    return setup_impl(coarse, n_refine, 1, STOKES_SV, k, opts, nu_cell, stream, out, true);
+}
+
+int stokes_fbf_apply(stokes_mg_t h, const double* r_dev, double* z_dev, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && r_dev && z_dev, "invalid argument");
+        require(h->fbf != nullptr, "not an FBF handle (stokes_fbf_setup)");
+        DeviceGuard dg(h);
+        fbf_apply(h, r_dev, z_dev, (cudaStream_t)stream);
+        return STOKES_OK;
+    });
 }
 
 int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, void* stream) {
@@ -1902,10 +2092,10 @@ int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, do
         require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
         DeviceGuard dg(h);
         cudaStream_t s = (cudaStream_t)stream;
-        const sfem::Level& F = h->H.levels[0];
+        const sfem::Level& F = finest_stokes(h);
         const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ, n = F.n_free;
         const double* gfull = g_nodal ? g_nodal : h->gzero;
-        if (h->L[0].dev_asm) {
+        if (!h->fbf && h->L[0].dev_asm) {
             // matrix-free: b = (M f)/nu - K[free, D] g, assembled per row from
             // the incident cells (same element integrals as the operator)
             launch(h, -1, s, [&] { sasm::load_vector(h->L[0].am, f_nodal, g_nodal, 1.0 / nu, h->bvec, s); });
@@ -1944,7 +2134,7 @@ int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, doub
         require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
         DeviceGuard dg(h);
         cudaStream_t s = (cudaStream_t)stream;
-        const sfem::Level& F = h->H.levels[0];
+        const sfem::Level& F = finest_stokes(h);
         const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ;
         double* rp = h->bvec + (size_t)d * nVf;
         // r = (gu on the free velocity DoFs, nu Pi^T gp), Pi^T gp = gp - w (1^T gp) / (w^T 1):
@@ -1965,7 +2155,7 @@ int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, doub
         }
         if (grad_f) {
             // dL/df_c = M lambda_u,c / nu on every velocity node
-            if (h->L[0].dev_asm) {
+            if (!h->fbf && h->L[0].dev_asm) {
                 launch(h, -1, s, [&] { sasm::mass_apply_all(h->L[0].am, lam_u, 1.0 / nu, grad_f, s); });
             } else {
                 for (int c = 0; c < d; ++c)
@@ -1983,9 +2173,9 @@ int stokes_grad_viscosity(stokes_mg_t h, const double* u, const double* lam_u, d
     return guarded([&] {
         require(h && u && lam_u && grad, "invalid argument");
         DeviceGuard dg(h);
-        if (!h->L[0].dev_asm)
-            throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs a device-assembled finest level "
-                                                   "(a hierarchy of more than one level)");
+        if (h->fbf || !h->L[0].dev_asm)
+            throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs the monolithic handle's "
+                                                   "device-assembled finest level");
         cudaStream_t s = (cudaStream_t)stream;
         launch(h, -1, s, [&] { sasm::grad_viscosity(h->L[0].am, u, lam_u, grad, s); });
         return STOKES_OK;
@@ -2052,7 +2242,7 @@ int stokes_mg_nodes(stokes_mg_t h, double* vel_xyz, double* pres_xyz, double* pr
     g_last_error.clear();
     return guarded([&] {
         require(h, "invalid argument");
-        const sfem::Level& L = h->H.levels[0];
+        const sfem::Level& L = finest_stokes(h);
         const int d = L.d;
         if (vel_xyz) std::memcpy(vel_xyz, L.V.X.data(), sizeof(double) * L.V.X.size());
         if (pres_xyz) std::memcpy(pres_xyz, L.Q.X.data(), sizeof(double) * L.Q.X.size());
