@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--adjoint-workload", default="th_p3_128x128_nu",
                     help="workload of the adjoint (gradient) measurement")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--fbf-workload", default="sv_p4_disk",
+                    help="Scott-Vogelius workload of the FBF(phMG) versus monolithic phMG measurement")
+    ap.add_argument("--no-fbf", action="store_true")
+    ap.add_argument("--fbf-only", action="store_true", help="only the FBF measurement (profiling driver)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint measurement (profiling driver)")
     return ap.parse_args()
@@ -334,6 +338,57 @@ def adjoint_section(a, P, W, dev, stream, flush):
     }
 
 
+def fbf_section(a, P, W, dev, stream, flush):
+    """Scott-Vogelius: one step (setup + solve to TOL, mixed precision, L2
+    flushed, CUDA events) with FBF(phMG) (Eq. fbf) and with the monolithic
+    phMG, on the same workload and forcing; median of the timed steps after
+    one warm-up each."""
+    import numpy as np
+    import torch
+
+    w = W.workload(a.fbf_workload)
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                       hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
+    i0 = probe.info()
+    probe.close()
+    d = w.verts.shape[1]
+    f = torch.tensor(W.nodal_forcing(i0["n_vel_nodes"], d, w.seed).reshape(-1), device=dev)
+
+    def step(fbf):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                       hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=P.MIXED, stream=stream.cuda_stream,
+                       fbf=fbf)
+        st = h.info()
+        u, p, its, rel = h.solve(f, tol=TOL)
+        e1.record(stream)
+        e1.synchronize()
+        out = dict(ms=e0.elapsed_time(e1), setup_ms=st["t_total_ms"], its=its, rel=rel,
+                   launches=h.info()["kernel_launches"], u=u.norm().item(), levels=st["n_levels"],
+                   n_free0=st["n_free"][0])
+        h.close()
+        return out
+
+    res = {}
+    for name, fb in (("fbf_phmg", True), ("monolithic_phmg", False)):
+        step(fb)
+        runs = [step(fb) for _ in range(max(3, min(a.steps, 5)))]
+        ms = sorted(r["ms"] for r in runs)[len(runs) // 2]
+        res[name] = {"step_ms": ms, "setup_ms": sorted(r["setup_ms"] for r in runs)[len(runs) // 2],
+                     "iterations": runs[-1]["its"], "relres": runs[-1]["rel"],
+                     "levels": runs[-1]["levels"], "n_free_level0": runs[-1]["n_free0"],
+                     "gpu_launches": runs[-1]["launches"]}
+    res["workload"] = a.fbf_workload
+    res["n_free_stokes"] = int(i0["n_free"][0])
+    res["monolithic_over_fbf"] = res["monolithic_phmg"]["step_ms"] / res["fbf_phmg"]["step_ms"]
+    res["note"] = ("FBF's level-0 n_free is the scalar velocity level; both solve the same SV system to "
+                   f"{TOL} (mixed precision V-cycles, FP64 FGMRES)")
+    return res
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -406,6 +461,9 @@ def main():
         h.close()
         return e0.elapsed_time(e1), its, rel, st, pr
 
+    if a.fbf_only:
+        print(json.dumps(fbf_section(a, P, W, dev, stream, flush)))
+        return
     if a.adjoint_only:
         print(json.dumps(adjoint_section(a, P, W, dev, stream, flush)))
         return
@@ -470,6 +528,12 @@ def main():
                                       if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0)
         except Exception as e:  # noqa: BLE001
             batched = {"error": str(e)[:300]}
+    fbf_res = None
+    if not a.no_fbf:
+        try:
+            fbf_res = fbf_section(a, P, W, dev, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            fbf_res = {"error": str(e)[:300]}
     adj = None
     if not a.no_adjoint:
         try:
@@ -570,6 +634,8 @@ def main():
         line["batched"] = batched
     if adj is not None:
         line["adjoint"] = adj
+    if fbf_res is not None:
+        line["fbf"] = fbf_res
     line["clocks"] = clk.summary()
     if not a.no_cpu_baseline and world == 1:
         try:
