@@ -12,6 +12,11 @@ bench.py times (HIER_EXPLICIT schedule, defaults otherwise).
   operator and load (the solver stops at 1e-8 on its own operator; the two
   operators differ by rounding), and sampled patch inverses match
   numpy.linalg.inv of the oracle's blocks.
+* FBF(phMG) on the SV disk: the same true-residual check.
+* The batched V-cycle on the 16^3 cube with 64 right-hand sides: every column
+  against the single-vector mixed V-cycle.
+* The viscosity gradient on 128^2 with per-cell viscosity: a directional
+  central difference of the library's own solves.
 """
 import numpy as np
 import pytest
@@ -124,3 +129,85 @@ def test_scott_vogelius_disk_true_residual():
 
 def test_taylor_hood_3d_cube_true_residual():
     _true_residual_case("th_p3_cube16", n_sample=12)
+
+
+def test_fbf_disk_true_residual():
+    """FBF(phMG) (Eq. fbf) on the SV P4 disk at full size: the solution's true
+    residual under the oracle's independently assembled operator <= 2e-8, and
+    the solve stays within the monolithic solver's iteration range (the paper
+    reports FBF(phMG) as robust for SV)."""
+    w = W.workload("sv_p4_disk")
+    meshes, _ = geometry.hierarchy(w.verts, w.cells, w.n_refine, w.barycentric)
+    D = stokes.discretize(*meshes[0], w.family, w.k)
+    h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, fbf=True, hierarchy=P.HIER_EXPLICIT,
+                   schedule=w.schedule, precision=P.MIXED)
+    pv, pq = full_field_perms(h, D)
+    f_o = W.nodal_forcing(D.V.n, D.d, w.seed)
+    f_l = np.empty_like(f_o)
+    f_l[:, pv] = f_o
+    u, p, its, rel = h.solve(torch.tensor(f_l.reshape(-1), device="cuda"), tol=1e-8)
+    assert rel <= 1e-8 and its <= 40, (rel, its)
+    b, _ = stokes.load_vector(D, f_o)
+    U = u.cpu().numpy().reshape(D.d, -1)[:, pv].reshape(-1)
+    x = np.concatenate([U, p.cpu().numpy()[pq]])[D.free]
+    res = np.linalg.norm(b - D.K @ x) / np.linalg.norm(b)
+    assert res <= 2e-8, res
+    h.close()
+
+
+def test_batched_columns_match_single_vcycle_on_cube16():
+    """The batched V-cycle in bench's configuration (TH P3/P2 on the 16^3
+    cube, 64 right-hand sides): every column of the 3xTF32 batch equals the
+    single-vector mixed V-cycle to 1e-4 and every TF32 column to 2e-2 (the
+    accuracy argument of tests/test_gpu_batched.py holds at any size)."""
+    w = W.workload("th_p3_cube16")
+    h = _lib(w, P.MIXED)
+    n = h.info()["n_free"][0]
+    R = torch.tensor(np.random.default_rng(4).standard_normal((64, n)), device="cuda")
+    Z1 = h.vcycle(R)
+    scale = Z1.abs().amax(dim=1)
+    e3 = ((h.vcycle_batched(R, P.BATCH_3XTF32) - Z1).abs().amax(dim=1) / scale).max().item()
+    et = ((h.vcycle_batched(R, P.BATCH_TF32) - Z1).abs().amax(dim=1) / scale).max().item()
+    assert e3 < 1e-4 and et < 2e-2, (e3, et)
+    h.close()
+
+
+def test_adjoint_directional_derivative_on_128x128_with_viscosity():
+    """The viscosity gradient in bench's adjoint configuration (TH P3/P2 on
+    128^2 with nu_e = exp(N(0, 1/4))): grad . delta equals the central
+    difference of the library's own forward solves in a random direction
+    (eps = 1e-5, solves to 1e-10; agreement 1e-5)."""
+    w = W.workload("th_p3_128x128_nu")
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, hierarchy=P.HIER_EXPLICIT, schedule=w.schedule,
+                       host_only=1)
+    nc = probe.n_cells()
+    i0 = probe.info()
+    probe.close()
+    nu = W.cell_viscosity(nc, w.seed)
+    r = np.random.default_rng(6)
+    f = torch.tensor(W.nodal_forcing(i0["n_vel_nodes"], 2, w.seed).reshape(-1), device="cuda")
+    gu = torch.tensor(r.standard_normal((2, i0["n_vel_nodes"])), device="cuda")
+    gp = torch.tensor(r.standard_normal(i0["n_pres_nodes"]), device="cuda")
+
+    def forward(nu_):
+        hh = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, nu_cell=nu_, hierarchy=P.HIER_EXPLICIT,
+                        schedule=w.schedule, precision=P.MIXED)
+        u, p, _, rel = hh.solve(f, tol=1e-10)
+        assert rel <= 1e-10
+        return hh, u, p
+
+    h, u, p = forward(nu)
+    lam_u, _, _, _, arel = h.adjoint(gu, gp, tol=1e-10)
+    assert arel <= 1e-10
+    g = h.grad_viscosity(u, lam_u).cpu().numpy()
+    h.close()
+    dn = r.standard_normal(nc) * nu
+    eps = 1e-5
+    L = []
+    for sgn in (1, -1):
+        hh, uu, pp = forward(nu + sgn * eps * dn)
+        L.append(float((gu.reshape(-1) * uu).sum() + (gp * pp).sum()))
+        hh.close()
+    fd = (L[0] - L[1]) / (2 * eps)
+    an = float(g @ dn)
+    assert abs(fd - an) <= 1e-5 * max(abs(an), 1.0), (fd, an)
