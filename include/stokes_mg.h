@@ -189,6 +189,26 @@ int stokes_fbf_setup(const stokes_mesh* coarse, int n_refine, int k, const stoke
  * blocked, then pressure); may not alias.  Errors: EINVAL (not an FBF handle). */
 int stokes_fbf_apply(stokes_mg_t h, const double* r_dev, double* z_dev, void* stream);
 
+/* nrhs independent solves K x_c = b_c (c < nrhs <= STOKES_BATCH_MAX) by
+ * FGMRES(restart) in lockstep (Sec. 4), every column right-preconditioned
+ * by the batched V-cycle of stokes_mg_vcycle_batched (mode STOKES_BATCH_TF32
+ * or _3XTF32).  The Krylov arithmetic is FP64 (K applied with its FP64
+ * values to all columns at once, classical Gram-Schmidt twice, Givens per
+ * column), on the batch interleaved DoF-major; x0 = 0.  Column c counts as
+ * converged once its residual estimate is <= tol ||b_c||; the iteration stops
+ * when every column has converged (the others keep improving meanwhile).
+ *   b_dev, x_dev   device [nrhs][n_free(level 0)] FP64, free-DoF order as
+ *                  stokes_mg_fgmres; the pressure part of every b_c must be
+ *                  orthogonal to the constants (as stokes_solve's is).
+ *   iterations     host out: iterations of the batch; final_relres host
+ *                  [nrhs] out or NULL: each column's residual estimate / ||b_c||.
+ * Needs a monolithic MIXED handle.  Workspace for (restart + 1) + restart
+ * basis vectors of the batch is allocated on first use and kept.
+ * Errors: EINVAL, EUNSUPPORTED (patch too large at this width),
+ * ENOTCONVERGED, ENONFINITE. */
+int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int nrhs, int mode, double tol,
+                          int* iterations, double* final_relres, void* stream);
+
 /* Discrete adjoint of stokes_solve (differentiation of the solution with
  * respect to the forcing and the cell viscosities).  The paper does not
  * differentiate its solver; this is the standard adjoint of the linear solve

@@ -81,6 +81,7 @@ def lib():
         "stokes_mg_vcycle": (c_int, [P, P, P, c_int, P]),
         "stokes_mg_vcycle_batched": (c_int, [P, P, P, c_int, c_int, P]),
         "stokes_adjoint_solve": (c_int, [P, P, P, c_double, c_double, P, P, P, P, P, P]),
+        "stokes_fgmres_batched": (c_int, [P, P, P, c_int, c_int, c_double, P, P, P]),
         "stokes_grad_viscosity": (c_int, [P, P, P, P, P]),
         "stokes_mg_cell_centroids": (c_int, [P, P, P]),
         "stokes_solve": (c_int, [P, P, P, c_double, c_double, P, P, POINTER(c_int), POINTER(c_double), P]),
@@ -241,6 +242,22 @@ class StokesMG:
         z = torch.empty_like(r) if out is None else out
         check(lib().stokes_mg_vcycle(self.h, _ptr(r.contiguous()), _ptr(z), nrhs, _stream(self.stream)))
         return z
+
+    def fgmres_batched(self, B, mode=BATCH_TF32, tol=1e-8, out=None, raise_on_nonconv=True):
+        """X with K X[c] = B[c] for the rows of B [nrhs, n_free] (device
+        float64), by FGMRES-phMG in lockstep with the batched V-cycle
+        (stokes_fgmres_batched).  Returns (X, iterations, relres [nrhs])."""
+        import torch
+        B = B.contiguous()
+        nrhs = 1 if B.dim() == 1 else B.shape[0]
+        X = torch.empty_like(B) if out is None else out
+        its = c_int()
+        rel = np.zeros(nrhs, dtype=np.float64)
+        rc = lib().stokes_fgmres_batched(self.h, _ptr(B), _ptr(X), nrhs, int(mode), float(tol), byref(its),
+                                         rel.ctypes.data_as(c_void_p), _stream(self.stream))
+        if rc != -4 or raise_on_nonconv:
+            check(rc)
+        return X, its.value, rel
 
     def fbf_apply(self, r, out=None):
         """z = P^-1 r of Eq. fbf on the Stokes free DoFs (stokes_fbf_apply)."""

@@ -29,6 +29,8 @@ def _sources():
                         "-c", os.path.join(CSRC, "stokes_mg.cu")],
         "assembly.o": [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                        "-c", os.path.join(CSRC, "assembly.cu")],
+        "bkrylov.o": [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                      "-c", os.path.join(CSRC, "bkrylov.cu")],
         "batched.o": [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                       "-c", os.path.join(CSRC, "batched.cu")],
         "noalloc.o": [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -58,4 +58,35 @@ void pull_scatter(int n, int m, const int* soff, const int* sidx, const float* Y
 // FP64 coarse inverse applied to a batch (FP64 accumulation).
 void coarse_gemm(int nc, int ldc, int m, const double* C, const float* B, float* E, cudaStream_t s);
 
+// ---- FP64 pieces of the batched FGMRES (bkrylov.cu), interleaved [n][m] --
+// Y = A X (mode 0) or Y = B - A X (mode 2) with FP64 values
+void spmm64(int mode, int nr, int m, const int* rp, const int* ci, const double* av, const double* X, double* Y,
+            const double* B, cudaStream_t s);
+// doubles of the partial-sum workspace of col_dots at width m
+size_t col_partial_doubles(int m);
+// out[i][c] (+)= sum_r V_i[r][c] W[r][c] for i < nb (<= 32), basis vectors
+// ldv doubles apart; sqrt_out takes the square root (column norms with
+// V = W); deterministic (fixed-order two-stage reduction)
+void col_dots(int n, int m, int nb, const double* V, long long ldv, const double* W, double* partial, double* out,
+              int sqrt_out, int add, cudaStream_t s);
+// W[r][c] -= sum_{i < nb} H[i][c] V_i[r][c]
+void col_update(int n, int m, int nb, const double* V, long long ldv, const double* H, double* W, cudaStream_t s);
+// Vout = W / h[c] per column (0 where h[c] == 0)
+void col_scale(int n, int m, const double* W, const double* h, double* Vout, cudaStream_t s);
+// per column: Hessenberg column j, Givens rotations, g, |residual estimate|;
+// H [m][ldh][ldh], cs / sn [m][ldh], g [m][ldh + 1], hcol [nb][m], hn / resid [m]
+void col_givens(int j, int m, int ldh, double* H, const double* hcol, const double* hn, double* cs, double* sn,
+                double* g, double* resid, cudaStream_t s);
+void col_backsolve(int jend, int m, int ldh, const double* H, const double* g, double* y, cudaStream_t s);
+// X[r][c] += sum_{j < jend} y[c][j] Z_j[r][c]; y [m][ldy]
+void col_xupdate(int n, int m, int jend, int ldy, const double* Z, long long ldz, const double* y, double* X,
+                 cudaStream_t s);
+// g[c] = (beta[c], 0, ..., 0), g [m][ldg]
+void col_start(int m, int ldg, const double* beta, double* g, cudaStream_t s);
+// FP64 [nrhs][n] <-> interleaved [n][m]; FP64 <-> FP32 of an interleaved batch
+void pack64(int n, int nrhs, int m, const double* r, double* X, cudaStream_t s);
+void unpack64(int n, int nrhs, int m, const double* X, double* z, cudaStream_t s);
+void to32(long long nm, const double* x, float* y, cudaStream_t s);
+void to64(long long nm, const float* x, double* y, cudaStream_t s);
+
 }  // namespace sbat

@@ -264,6 +264,14 @@ struct stokes_mg {
     int *bstat_h = nullptr, *bstat_d = nullptr;   // host-mapped timeout flag of the tensor-core patch GEMM
     std::vector<void*> tmaps;                      // per relaxed level: tensor maps over the FP32 inverses
     std::unique_ptr<FbfData> fbf;                  // FBF(phMG) mode (stokes_fbf_setup)
+    // batched FGMRES workspace (interleaved FP64, width bk_m)
+    struct BatchKrylov {
+        int m = 0;
+        double *V = nullptr, *Z = nullptr, *W = nullptr, *R = nullptr, *B = nullptr, *X = nullptr, *partial = nullptr;
+        double *hcol = nullptr, *hcol2 = nullptr, *hn = nullptr, *Hc = nullptr, *cs = nullptr, *sn = nullptr;
+        double *g = nullptr, *y = nullptr, *resid = nullptr, *beta = nullptr, *beta0 = nullptr;
+        double* host = nullptr;        // pinned [2 m]
+    } bk;
     cudaGraphExec_t bgraph[2] = {nullptr, nullptr};
     long long bgraph_launches[2] = {0, 0};
     // solve plumbing (finest level)
@@ -2037,6 +2045,149 @@ int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs
     });
 }
 
+namespace {
+// batched V-cycle of an interleaved FP64 batch (width h->bm): Z = B_MG V
+void batched_precond(stokes_mg* h, int mode, const double* V, double* Z, cudaStream_t s) {
+    const int m = h->bm;
+    const long long nm = (long long)h->L[0].n * m;
+    launch(h, -1, s, [&] { sbat::to32(nm, V, h->bl[0].b, s); });
+    const bool any_prof = h->prof[PK_PATCH].on || h->prof[PK_SPMV].on || h->prof[PK_PULL].on || h->prof[PK_TRANSFER].on;
+    if (h->opts.use_graph && !any_prof) {
+        if (!h->bgraph[mode]) capture_batched(h, mode, m);
+        CK(cudaGraphLaunch(h->bgraph[mode], s));
+        h->launches += h->bgraph_launches[mode];
+    } else {
+        b_pcycle(h, 0, mode, m, h->bl[0].b, h->bl[0].e, s);
+    }
+    launch(h, -1, s, [&] { sbat::to64(nm, h->bl[0].e, Z, s); });
+}
+
+void ensure_bkrylov(stokes_mg* h, int m) {
+    auto& K = h->bk;
+    if (K.m == m) return;
+    const size_t nm = (size_t)h->L[0].n * m;
+    const int R = h->restart, ldh = R + 1;
+    K.V = halloc<double>(h, (size_t)(R + 1) * nm);
+    K.Z = halloc<double>(h, (size_t)R * nm);
+    K.W = halloc<double>(h, nm);
+    K.R = halloc<double>(h, nm);
+    K.B = halloc<double>(h, nm);
+    K.X = halloc<double>(h, nm);
+    K.partial = halloc<double>(h, sbat::col_partial_doubles(m));
+    K.hcol = halloc<double>(h, (size_t)32 * m);
+    K.hcol2 = halloc<double>(h, (size_t)32 * m);
+    K.hn = halloc<double>(h, m);
+    K.Hc = halloc<double>(h, (size_t)m * ldh * ldh);
+    K.cs = halloc<double>(h, (size_t)m * ldh);
+    K.sn = halloc<double>(h, (size_t)m * ldh);
+    K.g = halloc<double>(h, (size_t)m * (ldh + 1));
+    K.y = halloc<double>(h, (size_t)m * (ldh + 1));
+    K.resid = halloc<double>(h, m);
+    K.beta = halloc<double>(h, m);
+    K.beta0 = halloc<double>(h, m);
+    if (!K.host) CK(cudaMallocHost((void**)&K.host, sizeof(double) * 2 * 64));
+    CK(cudaStreamSynchronize(h->s_up));
+    K.m = m;
+}
+
+// nrhs independent FGMRES(restart) solves (Sec. 4) in lockstep, every
+// column right-preconditioned by the batched V-cycle; x0 = 0, column c
+// stops counting once ||b_c - K x_c|| <= tol ||b_c|| (estimate), the batch
+// once every column has.  Krylov arithmetic in FP64, CGS2 as the
+// single-vector solver, deterministic.
+int fgmres_batched(stokes_mg* h, int nrhs, int mode, const double* B_dev, double* X_dev, double tol, int* its_out,
+                   double* rel_out, cudaStream_t s) {
+    const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
+    ensure_batch(h, m);
+    ensure_bkrylov(h, m);
+    auto& K = h->bk;
+    DevLevel& l0 = h->L[0];
+    const int n = l0.n, R = h->restart, ldh = R + 1;
+    const long long nm = (long long)n * m;
+    launch(h, -1, s, [&] { sbat::pack64(n, nrhs, m, B_dev, K.B, s); });
+    CK(cudaMemsetAsync(K.X, 0, sizeof(double) * nm, s));
+    launch(h, -1, s, [&] { sbat::col_dots(n, m, 1, K.B, 0, K.B, K.partial, K.beta0, 1, 0, s); });
+    CK(cudaMemcpyAsync(K.host, K.beta0, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> beta0(K.host, K.host + m), res(m, 0.0);
+    for (int c = 0; c < nrhs; ++c)
+        if (!std::isfinite(beta0[c])) throw StokesError(STOKES_ENONFINITE, "non-finite right-hand side");
+    auto all_done = [&](const std::vector<double>& r) {
+        for (int c = 0; c < nrhs; ++c)
+            if (beta0[c] > 0.0 && !(r[c] <= tol * beta0[c])) return false;
+        return true;
+    };
+    CK(cudaMemcpyAsync(K.R, K.B, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(K.beta, K.beta0, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    int its = 0;
+    bool converged = all_done(beta0);      // only zero right-hand sides
+    while (!converged && its < h->opts.maxit) {
+        launch(h, -1, s, [&] { sbat::col_start(m, ldh + 1, K.beta, K.g, s); });
+        launch(h, -1, s, [&] { sbat::col_scale(n, m, K.R, K.beta, K.V, s); });
+        int jend = 0;
+        for (int j = 0; j < R; ++j) {
+            const double* Vj = K.V + (long long)j * nm;
+            double* Zj = K.Z + (long long)j * nm;
+            batched_precond(h, mode, Vj, Zj, s);
+            launch(h, PK_SPMV, s, [&] { sbat::spmm64(0, n, m, l0.K.rp, l0.K.ci, l0.K.v64, Zj, K.W, nullptr, s); });
+            // CGS2
+            launch(h, -1, s, [&] { sbat::col_dots(n, m, j + 1, K.V, nm, K.W, K.partial, K.hcol, 0, 0, s); });
+            launch(h, -1, s, [&] { sbat::col_update(n, m, j + 1, K.V, nm, K.hcol, K.W, s); });
+            launch(h, -1, s, [&] { sbat::col_dots(n, m, j + 1, K.V, nm, K.W, K.partial, K.hcol2, 0, 0, s); });
+            launch(h, -1, s, [&] { sbat::col_update(n, m, j + 1, K.V, nm, K.hcol2, K.W, s); });
+            axpby_l<double>(h, (j + 1) * m, 1.0, K.hcol2, 1.0, K.hcol, s);
+            launch(h, -1, s, [&] { sbat::col_dots(n, m, 1, K.W, 0, K.W, K.partial, K.hn, 1, 0, s); });
+            launch(h, -1, s, [&] { sbat::col_scale(n, m, K.W, K.hn, K.V + (long long)(j + 1) * nm, s); });
+            launch(h, -1, s, [&] { sbat::col_givens(j, m, ldh, K.Hc, K.hcol, K.hn, K.cs, K.sn, K.g, K.resid, s); });
+            CK(cudaMemcpyAsync(K.host, K.resid, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            res.assign(K.host, K.host + m);
+            for (int c = 0; c < nrhs; ++c)
+                if (!std::isfinite(res[c])) throw StokesError(STOKES_ENONFINITE, "non-finite FGMRES residual");
+            ++its;
+            jend = j + 1;
+            if (all_done(res)) { converged = true; break; }
+            if (its >= h->opts.maxit) break;
+        }
+        launch(h, -1, s, [&] { sbat::col_backsolve(jend, m, ldh, K.Hc, K.g, K.y, s); });
+        launch(h, -1, s, [&] { sbat::col_xupdate(n, m, jend, ldh + 1, K.Z, nm, K.y, K.X, s); });
+        if (converged) break;
+        // restart: the true residual of every column
+        launch(h, PK_SPMV, s, [&] { sbat::spmm64(2, n, m, l0.K.rp, l0.K.ci, l0.K.v64, K.X, K.R, K.B, s); });
+        launch(h, -1, s, [&] { sbat::col_dots(n, m, 1, K.R, 0, K.R, K.partial, K.beta, 1, 0, s); });
+        CK(cudaMemcpyAsync(K.host, K.beta, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        res.assign(K.host, K.host + m);
+        if (all_done(res)) converged = true;
+    }
+    launch(h, -1, s, [&] { sbat::unpack64(n, nrhs, m, K.X, X_dev, s); });
+    if (its_out) *its_out = its;
+    if (rel_out)
+        for (int c = 0; c < nrhs; ++c) rel_out[c] = beta0[c] > 0.0 ? res[c] / beta0[c] : 0.0;
+    return converged ? STOKES_OK : STOKES_ENOTCONVERGED;
+}
+}  // namespace
+
+int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int nrhs, int mode, double tol,
+                          int* iterations, double* final_relres, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && b_dev && x_dev && nrhs >= 1 && nrhs <= STOKES_BATCH_MAX && tol > 0, "invalid argument");
+        require(mode == STOKES_BATCH_TF32 || mode == STOKES_BATCH_3XTF32, "unknown batch mode");
+        require(!h->host_only && h->opts.precision == STOKES_MIXED && !h->fbf,
+                "the batched FGMRES needs a monolithic MIXED handle");
+        require(h->L[0].K.v64 != nullptr, "level 0 has no FP64 operator");
+        DeviceGuard dg(h);
+        const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
+        for (size_t li = 0; li + 1 < h->L.size(); ++li)
+            if (const char* why = sbat::patch_gemm_check(mode, h->L[li].maxn, m))
+                throw StokesError(STOKES_EUNSUPPORTED, why);
+        int rc = fgmres_batched(h, nrhs, mode, b_dev, x_dev, tol, iterations, final_relres, (cudaStream_t)stream);
+        if (rc != STOKES_OK) g_last_error = "batched FGMRES: a column did not reach the tolerance within maxit";
+        return rc;
+    });
+}
+
 int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, int mode, void* stream) {
     g_last_error.clear();
     return guarded([&] {
@@ -2512,6 +2663,7 @@ void stokes_mg_destroy(stokes_mg_t h) {
     if (h->pinned) cudaFreeHost(h->pinned);
     if (h->pinned_H) cudaFreeHost(h->pinned_H);
     if (h->bstat_h) cudaFreeHost(h->bstat_h);
+    if (h->bk.host) cudaFreeHost(h->bk.host);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     delete h;
 }

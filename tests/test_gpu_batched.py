@@ -92,3 +92,54 @@ def test_batched_bad_arguments():
     with pytest.raises(P.StokesError) as e:
         h64.vcycle_batched(R[:2])
     assert e.value.code == -1
+
+
+def _consistent_rhs(ora, nrhs, seed):
+    """Random free-DoF right-hand sides with mean-free pressure parts (the
+    consistency condition of the singular all-Dirichlet system, Sec. 2)."""
+    D = ora.levels[0].disc
+    B = np.random.default_rng(seed).standard_normal((nrhs, D.n_free))
+    pm = D.pressure_mask_free()
+    B[:, pm] -= B[:, pm].mean(axis=1, keepdims=True)
+    return B
+
+
+@pytest.mark.parametrize("name", ["th_p4_8x8", "sv_p3_alfeld", "th3d_p3"])
+def test_batched_fgmres_matches_single_solves(name):
+    """stokes_fgmres_batched with the 3xTF32 preconditioner: every column's
+    true residual under the oracle's operator is <= 2e-10 (the solve stops at
+    1e-10 on the library's operator), and the batch needs the single-RHS
+    mixed solver's iteration count within one (the preconditioners agree to
+    ~1e-5); repeated runs are bitwise equal."""
+    h, ora, perms = pair(name, P.MIXED)
+    D = ora.levels[0].disc
+    B_o = _consistent_rhs(ora, 5, 8)
+    B = torch.stack([to_lib(B_o[q], perms[0]) for q in range(5)])
+    X, its, rel = h.fgmres_batched(B, P.BATCH_3XTF32, tol=1e-10)
+    assert np.all(rel <= 1e-10), rel
+    X2, _, _ = h.fgmres_batched(B, P.BATCH_3XTF32, tol=1e-10)
+    assert torch.equal(X, X2)
+    its_single = []
+    for q in range(5):
+        x_o = from_lib(X[q], perms[0])
+        res = np.linalg.norm(B_o[q] - D.K @ x_o) / np.linalg.norm(B_o[q])
+        assert res <= 2e-10, (q, res)
+        its_single.append(h.fgmres(B[q].clone(), tol=1e-10)[1])
+    assert abs(its - max(its_single)) <= 1, (its, its_single)
+
+
+def test_batched_fgmres_tf32_and_widths():
+    """TF32 preconditioning still reaches the tolerance (a preconditioner
+    need not be accurate; FP64 Krylov arithmetic sets the accuracy), at
+    widths 8 and 64."""
+    h, ora, perms = pair("th_p4_gradual", P.MIXED)
+    D = ora.levels[0].disc
+    for nrhs in (3, 64):
+        B_o = _consistent_rhs(ora, nrhs, 9)
+        B = torch.tensor(np.stack([np.asarray(to_lib(B_o[q], perms[0]).cpu()) for q in range(nrhs)]), device="cuda")
+        X, its, rel = h.fgmres_batched(B, P.BATCH_TF32, tol=1e-9)
+        assert np.all(rel <= 1e-9), rel
+        for q in (0, nrhs - 1):
+            x_o = from_lib(X[q], perms[0])
+            res = np.linalg.norm(B_o[q] - D.K @ x_o) / np.linalg.norm(B_o[q])
+            assert res <= 2e-9, (nrhs, q, res)
