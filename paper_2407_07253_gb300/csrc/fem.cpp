@@ -1399,22 +1399,27 @@ static CSR csr_leading_block(const CSR& a, int nr, int nc) {
     b.nr = nr;
     b.ncol = nc;
     b.rp.assign(nr + 1, 0);
-    for (int r = 0; r < nr; ++r) {
-        int cnt = 0;
-        for (int p = a.rp[r]; p < a.rp[r + 1]; ++p) cnt += a.ci[p] < nc;
-        b.rp[r + 1] = b.rp[r] + cnt;
-    }
+    parallel_for(nr, [&](int lo, int hi, int) {
+        for (int r = lo; r < hi; ++r) {
+            int cnt = 0;
+            for (int p = a.rp[r]; p < a.rp[r + 1]; ++p) cnt += a.ci[p] < nc;
+            b.rp[r + 1] = cnt;
+        }
+    });
+    for (int r = 0; r < nr; ++r) b.rp[r + 1] += b.rp[r];
     b.ci.resize(b.rp[nr]);
     b.v.resize(b.rp[nr]);
-    for (int r = 0; r < nr; ++r) {
-        int o = b.rp[r];
-        for (int p = a.rp[r]; p < a.rp[r + 1]; ++p)
-            if (a.ci[p] < nc) { b.ci[o] = a.ci[p]; b.v[o] = a.v[p]; ++o; }
-    }
+    parallel_for(nr, [&](int lo, int hi, int) {
+        for (int r = lo; r < hi; ++r) {
+            int o = b.rp[r];
+            for (int p = a.rp[r]; p < a.rp[r + 1]; ++p)
+                if (a.ci[p] < nc) { b.ci[o] = a.ci[p]; b.v[o] = a.v[p]; ++o; }
+        }
+    });
     return b;
 }
 
-void velocity_hierarchy(const Hierarchy& S, Hierarchy& A) {
+void velocity_hierarchy(Hierarchy& S, Hierarchy& A) {
     A.meshes = S.meshes;
     A.parents = S.parents;
     A.levels.assign(S.levels.size(), Level());

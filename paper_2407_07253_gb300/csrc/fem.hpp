@@ -139,7 +139,7 @@ struct Hierarchy {
 // P and R = the component-0 blocks of S's transfers, and ASMStarPC patches,
 // the free nodes on the open star of every mesh vertex (the nodes whose
 // owning entity contains the vertex).  No pressure.
-void velocity_hierarchy(const Hierarchy& S, Hierarchy& A);
+void velocity_hierarchy(Hierarchy& S, Hierarchy& A);
 
 // Mass matrix [nb][nb] of the degree-k Lagrange element on the reference
 // d-simplex (exact).

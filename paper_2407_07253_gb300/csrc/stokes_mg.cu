@@ -1917,11 +1917,11 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
             sfem::build_hierarchy(cm, sp, nu_cell, S, nullptr);
             h->fbf.reset(new FbfData());
             FbfData& F = *h->fbf;
-            F.S0 = S.levels[0];
+            sfem::velocity_hierarchy(S, h->H);
+            F.S0 = std::move(S.levels[0]);
             F.nS = F.S0.n_free;
             F.nvf = F.S0.nVf;
             F.nu = F.S0.d * F.S0.nVf;
-            sfem::velocity_hierarchy(S, h->H);
             h->H.t_mesh_ms = S.t_mesh_ms;
             h->H.t_assembly_ms = S.t_assembly_ms;
             h->H.t_spaces_ms = S.t_spaces_ms;
