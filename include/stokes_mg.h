@@ -209,6 +209,13 @@ int stokes_fbf_apply(stokes_mg_t h, const double* r_dev, double* z_dev, void* st
 int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int nrhs, int mode, double tol,
                           int* iterations, double* final_relres, void* stream);
 
+/* Self-test of the bounded mbarrier wait used by the tensor-core kernels
+ * (no counterpart in the paper): one CTA waits on a barrier that nothing
+ * arrives on, gives up after `polls` polls and returns; *result = 2 then
+ * (1 would mean the barrier phase completed, 0 that the kernel never ran).
+ * Errors: EINVAL, ECUDA. */
+int stokes_selftest_bounded_wait(long long polls, int* result);
+
 /* Discrete adjoint of stokes_solve (differentiation of the solution with
  * respect to the forcing and the cell viscosities).  The paper does not
  * differentiate its solver; this is the standard adjoint of the linear solve

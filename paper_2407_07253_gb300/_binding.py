@@ -82,6 +82,7 @@ def lib():
         "stokes_mg_vcycle_batched": (c_int, [P, P, P, c_int, c_int, P]),
         "stokes_adjoint_solve": (c_int, [P, P, P, c_double, c_double, P, P, P, P, P, P]),
         "stokes_fgmres_batched": (c_int, [P, P, P, c_int, c_int, c_double, P, P, P]),
+        "stokes_selftest_bounded_wait": (c_int, [c_longlong, P]),
         "stokes_grad_viscosity": (c_int, [P, P, P, P, P]),
         "stokes_mg_cell_centroids": (c_int, [P, P, P]),
         "stokes_solve": (c_int, [P, P, P, c_double, c_double, P, P, POINTER(c_int), POINTER(c_double), P]),
@@ -153,6 +154,14 @@ def _stream(stream):
     except ImportError:
         pass
     return None
+
+
+def selftest_bounded_wait(polls=1000):
+    """stokes_selftest_bounded_wait: 2 when the bounded mbarrier wait gives up
+    and its kernel returns."""
+    r = c_int()
+    check(lib().stokes_selftest_bounded_wait(int(polls), byref(r)))
+    return r.value
 
 
 class StokesMG:

@@ -368,15 +368,34 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false (and the CTA's abort flag set) after WAIT_LIMIT polls,
+// bounded wait; false (and the CTA's abort flag set) after `limit` polls,
 // or at once if another role has already given up
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
+                                          long long limit = WAIT_LIMIT) {
+    for (long long i = 0; i < limit; ++i) {
         if (mbar_try(a, parity)) return true;
         if (*abort_flag) return false;
     }
     *abort_flag = 1;
     return false;
+}
+
+// self-test of the bounded wait: one CTA waits on an mbarrier that nothing
+// arrives on; *result = 2 when the wait gives up after `limit` polls and the
+// kernel returns (1 would mean the phase completed)
+__global__ void k_wait_probe(long long limit, int* result) {
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int abort_flag;
+    const uint32_t a = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(a, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(a, 0, &abort_flag, limit);
+    __syncthreads();
+    if (threadIdx.x == 0) *result = ok ? 1 : 2;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint32_t mbar, int x, int y) {
     asm volatile(
@@ -753,6 +772,11 @@ const char* patch_gemm_check(int mode, int maxn, int m) {
     if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, tc::np_of(m)) > 512)
         return "patch too large for the tensor memory at this width";
     return tc_plan(maxn, m, 1).stages ? nullptr : "patch too large for the shared memory of the TF32 patch GEMM";
+}
+
+int wait_probe(long long polls, int* result_dev, cudaStream_t s) {
+    tc::k_wait_probe<<<1, 32, 0, s>>>(polls, result_dev);
+    return (int)cudaGetLastError();
 }
 
 size_t tmap_bytes(int npatch) { return sizeof(CUtensorMap) * (size_t)std::max(npatch, 1); }

@@ -32,6 +32,11 @@ void spmm(int mode, int nr, int m, const int* rp, const int* ci, const float* av
 // DoFs on the current device, else the reason (shared or tensor memory)
 const char* patch_gemm_check(int mode, int maxn, int m);
 
+// self-test of the tensor-core kernel's bounded mbarrier wait (writes 2 to
+// *result_dev when a wait on a barrier nobody arrives on gives up and the
+// kernel returns); returns the launch's cudaError_t
+int wait_probe(long long polls, int* result_dev, cudaStream_t s);
+
 // bytes of the per-patch tensor maps of a level, and their construction
 // (host encoding from the device offsets; synchronous)
 size_t tmap_bytes(int npatch);

@@ -2168,6 +2168,22 @@ int fgmres_batched(stokes_mg* h, int nrhs, int mode, const double* B_dev, double
 }
 }  // namespace
 
+int stokes_selftest_bounded_wait(long long polls, int* result) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(result && polls >= 0, "invalid argument");
+        int* d = nullptr;
+        CK(cudaMalloc((void**)&d, sizeof(int)));
+        CK(cudaMemset(d, 0, sizeof(int)));
+        const int e = sbat::wait_probe(polls, d, nullptr);
+        if (e != cudaSuccess) { cudaFree(d); CK((cudaError_t)e); }
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(result, d, sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaFree(d));
+        return STOKES_OK;
+    });
+}
+
 int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int nrhs, int mode, double tol,
                           int* iterations, double* final_relres, void* stream) {
     g_last_error.clear();

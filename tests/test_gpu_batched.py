@@ -143,3 +143,13 @@ def test_batched_fgmres_tf32_and_widths():
             x_o = from_lib(X[q], perms[0])
             res = np.linalg.norm(B_o[q] - D.K @ x_o) / np.linalg.norm(B_o[q])
             assert res <= 2e-9, (nrhs, q, res)
+
+
+def test_bounded_mbarrier_wait_gives_up_and_returns():
+    """The tensor-core kernel's mbarrier waits are bounded: a wait on a barrier
+    that nothing arrives on runs out after the given number of polls, sets
+    its status and the kernel returns, leaving the context usable."""
+    assert P._binding.selftest_bounded_wait(1000) == 2
+    assert P._binding.selftest_bounded_wait(100000) == 2
+    x = torch.ones(4, device="cuda")
+    assert float((x * 2).sum()) == 8.0
