@@ -178,8 +178,9 @@ int stokes_mg_vcycle(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs
  *                                         ([n_free(level 0)], the scalar level);
  *   stokes_mg_info, stokes_mg_level_dofs, stokes_mg_get_patches, stokes_mg_asm ...
  *                                         describe the scalar velocity levels;
- *   stokes_mg_nodes and the stats' node counts describe the SV Stokes fields.
- *   stokes_grad_viscosity returns EUNSUPPORTED.
+ *   stokes_mg_nodes and the stats' node counts describe the SV Stokes fields;
+ *   stokes_grad_viscosity works on the SV level (the finest level is
+ *   assembled on the device).
  * Errors: as stokes_mg_setup. */
 int stokes_fbf_setup(const stokes_mesh* coarse, int n_refine, int k, const stokes_mg_opts* opts,
                      const double* nu_cell, void* stream, stokes_mg_t* out);

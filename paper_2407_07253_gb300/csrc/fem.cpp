@@ -1360,7 +1360,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         double tb = now_ms();
         L.RT = RT;
         L.nu_cells = nus[L.mesh_index];
-        L.host_matrices = !spec.device_assembly || l + 1 == ls.size();
+        L.host_matrices = spec.device_assembly_finest_only ? l != 0 : (!spec.device_assembly || l + 1 == ls.size());
         if (L.host_matrices) assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
         else prepare_level(m, L, RT);
         double tc = now_ms();
@@ -1426,7 +1426,7 @@ void velocity_hierarchy(Hierarchy& S, Hierarchy& A) {
     for (size_t l = 0; l < S.levels.size(); ++l) {
         const Level& F = S.levels[l];
         Level& L = A.levels[l];
-        if (F.K.rp.empty()) throw std::runtime_error("velocity_hierarchy needs host-assembled operators");
+        if (F.host_matrices && F.K.rp.empty()) throw std::runtime_error("velocity_hierarchy: level without operator");
         L.d = F.d;
         L.family = 0;
         L.k = F.k;
@@ -1437,10 +1437,10 @@ void velocity_hierarchy(Hierarchy& S, Hierarchy& A) {
         L.nVf = F.nVf;
         L.nQ = 0;
         L.n_free = F.nVf;
-        L.K = csr_leading_block(F.K, F.nVf, F.nVf);
+        if (F.host_matrices) L.K = csr_leading_block(F.K, F.nVf, F.nVf);
         L.RT = F.RT;
         L.nu_cells = F.nu_cells;
-        L.host_matrices = true;
+        L.host_matrices = F.host_matrices;
         if (l + 1 < S.levels.size()) {
             L.P = csr_leading_block(F.P, F.nVf, S.levels[l + 1].nVf);
             L.R = transpose(L.P);

@@ -122,6 +122,7 @@ struct HierarchySpec {
     // other levels), then finest to coarsest
     bool coarsest_first = false;
     bool skip_patches = false;                // no Vanka patches (a hierarchy wanted for its operators)
+    bool device_assembly_finest_only = false; // with device_assembly: only level 0 on the device
 };
 
 struct Hierarchy {
@@ -138,7 +139,9 @@ struct Hierarchy {
 // velocity space and free nodes, K = A_s (the component-0 block of S's K),
 // P and R = the component-0 blocks of S's transfers, and ASMStarPC patches,
 // the free nodes on the open star of every mesh vertex (the nodes whose
-// owning entity contains the vertex).  No pressure.
+// owning entity contains the vertex).  No pressure.  A level of S without a
+// host K (device assembly) gets an empty K and host_matrices = false: its
+// velocity block is then extracted on the device.
 void velocity_hierarchy(Hierarchy& S, Hierarchy& A);
 
 // Mass matrix [nb][nb] of the degree-k Lagrange element on the reference

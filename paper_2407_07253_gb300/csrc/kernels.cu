@@ -35,6 +35,29 @@ __global__ void block_mass_inverse(int nc, int nb, const int* __restrict__ qcell
     }
 }
 
+__global__ void csr_block_count(int nr, int nc, const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ len) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int p = rp[r]; p < rp[r + 1]; ++p) c += ci[p] < nc;
+        len[r] = c;
+    }
+}
+
+__global__ void csr_block_fill(int nr, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const double* __restrict__ v, const int* __restrict__ brp, int* __restrict__ bci,
+                               double* __restrict__ bv, float* __restrict__ bv32) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        int o = brp[r];
+        for (int p = rp[r]; p < rp[r + 1]; ++p)
+            if (ci[p] < nc) {
+                bci[o] = ci[p];
+                bv[o] = v[p];
+                if (bv32) bv32[o] = (float)v[p];
+                ++o;
+            }
+    }
+}
+
 // ------------------------------------------------------------ reductions ---
 constexpr int MDOT_MAX = 32;
 

@@ -250,6 +250,12 @@ __global__ void sub_scalar(int n, double* __restrict__ x, const double* __restri
 // cells own disjoint index sets)
 __global__ void block_mass_inverse(int nc, int nb, const int* __restrict__ qcell, const double* __restrict__ minv,
                                    const double* __restrict__ scale, const double* __restrict__ y, double* __restrict__ z);
+// rows [0, nr), columns [0, nc) of a CSR: per-row counts, then (after a scan
+// into brp) the entries in their row order, FP64 and optionally FP32
+__global__ void csr_block_count(int nr, int nc, const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ len);
+__global__ void csr_block_fill(int nr, int nc, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const double* __restrict__ v, const int* __restrict__ brp, int* __restrict__ bci,
+                               double* __restrict__ bv, float* __restrict__ bv32);
 // x[i] -= w[i] * num[0] / den
 __global__ void sub_weighted(int n, double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ num,
                              double den);

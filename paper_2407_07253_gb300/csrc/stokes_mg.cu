@@ -221,7 +221,7 @@ struct FbfData {
     sfem::Level S0;                    // the finest SV level (host-assembled K, Mv, KfD, spaces)
     int nS = 0, nu = 0, nvf = 0;       // Stokes free DoFs, free velocity DoFs, per component
     int ncell = 0, nbq = 0;            // finest cells, pressure nodes per cell
-    DevCSR K;                          // the Stokes operator (FP64)
+    DevLevel S0d;                      // its device assembly: K (FP64) and the inputs of the matrix-free load
     double *a = nullptr, *t = nullptr, *w = nullptr, *r = nullptr;
     double* minv = nullptr;            // [nbq][nbq] inverse reference pressure mass matrix
     double* scale = nullptr;           // [ncell] -nu_e / |det J_e|
@@ -1028,7 +1028,7 @@ void fbf_apply(stokes_mg* h, const double* r, double* z, cudaStream_t s);
 int fgmres(stokes_mg* h, const double* b, double* x, double tol, int* its_out, double* rel_out, cudaStream_t s) {
     if (h->fbf) {
         FbfData& F = *h->fbf;
-        return fgmres_op(h, F.K, F.nS, F.r, [h](const double* v, double* z, cudaStream_t st) { fbf_apply(h, v, z, st); },
+        return fgmres_op(h, F.S0d.K, F.nS, F.r, [h](const double* v, double* z, cudaStream_t st) { fbf_apply(h, v, z, st); },
                          b, x, tol, its_out, rel_out, s);
     }
     DevLevel& l0 = h->L[0];
@@ -1060,7 +1060,7 @@ void fbf_apply(stokes_mg* h, const double* r, double* z, cudaStream_t s) {
     vcycles(r, F.a);
     CK(cudaMemcpyAsync(F.t, F.a, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(F.t + nu, 0, sizeof(double) * np, s));
-    spmv<double>(h, PK_SPMV, F.K, skern::SPMV_SET, F.t, F.w, nullptr, s);          // w_p = B a
+    spmv<double>(h, PK_SPMV, F.S0d.K, skern::SPMV_SET, F.t, F.w, nullptr, s);      // w_p = B a
     axpby_l<double>(h, np, 1.0, r + nu, -1.0, F.w + nu, s);                         // w_p = r_p - B a
     launch(h, -1, s, [&] {
         skern::block_mass_inverse<<<grid_for((long long)F.ncell * F.nbq), 256, 0, s>>>(F.ncell, F.nbq, F.qcell, F.minv,
@@ -1068,7 +1068,7 @@ void fbf_apply(stokes_mg* h, const double* r, double* z, cudaStream_t s) {
     });
     CK(cudaMemsetAsync(F.t, 0, sizeof(double) * nu, s));
     CK(cudaMemcpyAsync(F.t + nu, z + nu, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
-    spmv<double>(h, PK_SPMV, F.K, skern::SPMV_SET, F.t, F.w, nullptr, s);          // w_u = B^T z_p
+    spmv<double>(h, PK_SPMV, F.S0d.K, skern::SPMV_SET, F.t, F.w, nullptr, s);      // w_u = B^T z_p
     axpby_l<double>(h, nu, 1.0, r, -1.0, F.w, s);                                   // w_u = r_u - B^T z_p
     vcycles(F.w, z);
 }
@@ -1079,7 +1079,6 @@ void setup_fbf(stokes_mg* h, cudaStream_t s) {
     FbfData& F = *h->fbf;
     const sfem::Level& S0 = F.S0;
     const sfem::Mesh& m = h->H.meshes[S0.mesh_index];
-    F.K = upload_csr(h, S0.K, false, s);
     F.a = halloc<double>(h, F.nu);
     F.t = halloc<double>(h, F.nS);
     F.w = halloc<double>(h, F.nS);
@@ -1229,9 +1228,11 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
 // Mesh, DoF maps, adjacency and reference tensors of a level whose K is
 // assembled on the device; K's arrays are sized by an upper bound on the
 // row lengths (incident cells times nodes per cell).
+void upload_assembly_inputs_lv(stokes_mg* h, const sfem::Level& HL, DevLevel& l, bool want32, cudaStream_t s);
 void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s) {
-    const sfem::Level& HL = h->H.levels[li];
-    DevLevel& l = h->L[li];
+    upload_assembly_inputs_lv(h, h->H.levels[li], h->L[li], want32, s);
+}
+void upload_assembly_inputs_lv(stokes_mg* h, const sfem::Level& HL, DevLevel& l, bool want32, cudaStream_t s) {
     const sfem::Mesh& mesh = h->H.meshes[HL.mesh_index];
     const int nm = (int)h->H.meshes.size();
     if ((int)h->mesh_X.size() != nm) { h->mesh_X.assign(nm, nullptr); h->mesh_C.assign(nm, nullptr); }
@@ -1289,8 +1290,13 @@ void upload_assembly_inputs(stokes_mg* h, int li, bool want32, cudaStream_t s) {
 }
 
 // K of a device-assembled level: row lengths, scan, values (stream s)
+void assemble_dev(stokes_mg* h, DevLevel& l, cudaStream_t s);
 void assemble_on_device(stokes_mg* h, int li, cudaStream_t s) {
     DevLevel& l = h->L[li];
+    if (!l.am.vcell) return;        // the FBF velocity level 0 is filtered, not assembled
+    assemble_dev(h, l, s);
+}
+void assemble_dev(stokes_mg* h, DevLevel& l, cudaStream_t s) {
     if (!l.dev_asm) return;
     const int n = l.K.nr;
     launch(h, -1, s, [&] { sasm::cell_geometry(l.am, l.cellgeo, s); });
@@ -1305,16 +1311,70 @@ void assemble_on_device(stokes_mg* h, int li, cudaStream_t s) {
 
 // exact nnz of the device-assembled operators (after the setup stream synchronised)
 void finish_assembly(stokes_mg* h) {
-    for (size_t li = 0; li < h->L.size(); ++li) {
-        DevLevel& l = h->L[li];
-        if (!l.dev_asm) continue;
+    auto fin = [&](DevLevel& l, int li) {
+        if (!l.dev_asm) return;
         int st = 0, nnz = 0;
         CK(cudaMemcpy(&st, l.asm_status, sizeof(int), cudaMemcpyDeviceToHost));
         if (st != 0) throw StokesError(STOKES_EUNSUPPORTED, "a node has more than 1024 neighbours (level " + std::to_string(li) + ")");
         CK(cudaMemcpy(&nnz, l.K.rp + l.K.nr, sizeof(int), cudaMemcpyDeviceToHost));
         l.K.nnz = nnz;
         l.K.lanes = choose_lanes(l.K);
+    };
+    if (h->fbf) fin(h->fbf->S0d, 0);
+    for (size_t li = 0; li < h->L.size(); ++li) fin(h->L[li], (int)li);
+}
+
+// FBF: level 0's operator.  The SV Stokes K of the finest mesh is assembled
+// on the device (FbfData::S0d, also the outer FGMRES operator and the input
+// of the matrix-free load); the scalar velocity level's K is its leading
+// (component-0 velocity) block, filtered on the device.  Uploads on s_up,
+// kernels on `target` (after the uploads).
+void fbf_level0_operator(stokes_mg* h, bool want32, cudaStream_t target) {
+    FbfData& F = *h->fbf;
+    const sfem::Level& HL = h->H.levels[0];
+    DevLevel& l = h->L[0];
+    l.n = HL.n_free;
+    l.p_level = HL.p_level;
+    l.b64 = halloc<double>(h, l.n); l.e64 = halloc<double>(h, l.n); l.r64 = halloc<double>(h, l.n);
+    l.d64 = halloc<double>(h, l.n); l.t64 = halloc<double>(h, l.n); l.u64 = halloc<double>(h, l.n);
+    if (want32) {
+        l.b32 = halloc<float>(h, l.n); l.e32 = halloc<float>(h, l.n); l.r32 = halloc<float>(h, l.n);
+        l.d32 = halloc<float>(h, l.n); l.t32 = halloc<float>(h, l.n); l.u32 = halloc<float>(h, l.n);
     }
+    upload_assembly_inputs_lv(h, F.S0, F.S0d, false, h->s_up);
+    const int n = l.n;
+    const long long bound = F.S0d.K.nnz;
+    DevCSR& K = l.K;
+    K.nr = K.nc = n;
+    K.nnz = bound;
+    K.rp = halloc<int>(h, n + 1);
+    K.ci = halloc<int>(h, bound);
+    K.v64 = halloc<double>(h, bound);
+    K.v32 = want32 ? halloc<float>(h, bound) : nullptr;
+    K.lanes = 4;
+    l.asm_len = halloc<int>(h, n);
+    l.asm_tmp = halloc<int>(h, (n + 1023) / 1024 + 2);
+    l.asm_status = halloc<int>(h, 1);
+    CK(cudaMemsetAsync(l.asm_status, 0, sizeof(int), h->s_up));
+    l.dev_asm = true;                   // nnz and lanes are fixed up with the assembled levels
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, h->s_up));
+    CK(cudaStreamWaitEvent(target, ev, 0));
+    CK(cudaEventDestroy(ev));
+}
+
+void fbf_level0_kernels(stokes_mg* h, cudaStream_t s) {
+    FbfData& F = *h->fbf;
+    DevLevel& l = h->L[0];
+    const DevCSR& A = F.S0d.K;
+    const int n = l.n;
+    assemble_dev(h, F.S0d, s);
+    launch(h, -1, s, [&] { skern::csr_block_count<<<grid_for(n), 256, 0, s>>>(n, n, A.rp, A.ci, l.asm_len); });
+    launch(h, -1, s, [&] { sasm::scan_rows(l.asm_len, n, l.K.rp, l.asm_tmp, s); });
+    launch(h, -1, s, [&] {
+        skern::csr_block_fill<<<grid_for(n), 256, 0, s>>>(n, n, A.rp, A.ci, A.v64, l.K.rp, l.K.ci, l.K.v64, l.K.v32);
+    });
 }
 
 void upload_transfers(stokes_mg* h, int li, bool want32, cudaStream_t s) {
@@ -1910,7 +1970,8 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
             // operators only; the handle's levels become its scalar velocity
             // hierarchy (ASMStarPC patches), set up level by level as below
             sfem::HierarchySpec sp = spec;
-            sp.device_assembly = false;
+            sp.device_assembly = !o.host_only;
+            sp.device_assembly_finest_only = true;
             sp.coarsest_first = false;
             sp.skip_patches = true;
             sfem::Hierarchy S;
@@ -1932,7 +1993,16 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
             if (on_level) {
                 on_level(nlv - 1, 0);
                 on_level(nlv - 1, 1);
-                for (int li = 0; li + 1 < nlv; ++li) {
+                // level 0: the device-assembled Stokes K and its velocity block
+                stokes_mg* hp = h.get();
+                const cudaStream_t s0 = hp->s_lvl[0];
+                fbf_level0_operator(hp, want32, s0);
+                launcher->submit([hp, s0] {
+                    CK(cudaSetDevice(hp->device));
+                    fbf_level0_kernels(hp, s0);
+                });
+                on_level(0, 1);
+                for (int li = 1; li + 1 < nlv; ++li) {
                     on_level(li, 0);
                     on_level(li, 1);
                 }
@@ -2262,10 +2332,11 @@ int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, do
         const sfem::Level& F = finest_stokes(h);
         const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ, n = F.n_free;
         const double* gfull = g_nodal ? g_nodal : h->gzero;
-        if (!h->fbf && h->L[0].dev_asm) {
+        const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
+        if (fl.dev_asm) {
             // matrix-free: b = (M f)/nu - K[free, D] g, assembled per row from
             // the incident cells (same element integrals as the operator)
-            launch(h, -1, s, [&] { sasm::load_vector(h->L[0].am, f_nodal, g_nodal, 1.0 / nu, h->bvec, s); });
+            launch(h, -1, s, [&] { sasm::load_vector(fl.am, f_nodal, g_nodal, 1.0 / nu, h->bvec, s); });
         } else {
             // F_c = M f_c
             for (int c = 0; c < d; ++c)
@@ -2322,8 +2393,9 @@ int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, doub
         }
         if (grad_f) {
             // dL/df_c = M lambda_u,c / nu on every velocity node
-            if (!h->fbf && h->L[0].dev_asm) {
-                launch(h, -1, s, [&] { sasm::mass_apply_all(h->L[0].am, lam_u, 1.0 / nu, grad_f, s); });
+            const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
+            if (fl.dev_asm) {
+                launch(h, -1, s, [&] { sasm::mass_apply_all(fl.am, lam_u, 1.0 / nu, grad_f, s); });
             } else {
                 for (int c = 0; c < d; ++c)
                     spmv<double>(h, -1, h->Mv, skern::SPMV_SET, lam_u + (size_t)c * nV, grad_f + (size_t)c * nV, nullptr, s);
@@ -2340,11 +2412,11 @@ int stokes_grad_viscosity(stokes_mg_t h, const double* u, const double* lam_u, d
     return guarded([&] {
         require(h && u && lam_u && grad, "invalid argument");
         DeviceGuard dg(h);
-        if (h->fbf || !h->L[0].dev_asm)
-            throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs the monolithic handle's "
-                                                   "device-assembled finest level");
+        const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
+        if (!fl.dev_asm)
+            throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs a device-assembled finest level");
         cudaStream_t s = (cudaStream_t)stream;
-        launch(h, -1, s, [&] { sasm::grad_viscosity(h->L[0].am, u, lam_u, grad, s); });
+        launch(h, -1, s, [&] { sasm::grad_viscosity(fl.am, u, lam_u, grad, s); });
         return STOKES_OK;
     });
 }
