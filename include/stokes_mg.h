@@ -247,8 +247,8 @@ int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, doub
  * dependence on nu is folded in by using the full u.  Valid for a handle
  * whose viscosity is nu_cell (stokes_solve's nu = 1).
  *   u, lam_u  device [dim][n_vel_nodes];  grad  device [n_cells] out.
- * Errors: EINVAL; EUNSUPPORTED for a single-level hierarchy (the finest
- * level is then assembled on the host). */
+ * Errors: EINVAL; EUNSUPPORTED when the finest level was assembled on the
+ * host (host_only handles). */
 int stokes_grad_viscosity(stokes_mg_t h, const double* u, const double* lam_u, double* grad, void* stream);
 
 /* Cells of the finest mesh: *n_cells, and if xyz != NULL their centroids
