@@ -14,6 +14,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -129,7 +130,7 @@ class Clocks:
     def __init__(self, gpu):
         self.gpu = gpu
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"stokes_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -21,8 +21,8 @@ with
   * S~^-1: the inverse of the block-diagonal discontinuous pressure mass
     matrix, spectrally equivalent to the inverse Schur complement.
 
-Readings (also in the design doc): the Schur complement of K is S = -B A^-1 B^T,
-which is negative definite, so S~^-1 = -diag_e(nu_e M_p,e^-1), with nu_e
+Readings of points the paper leaves open: the Schur complement of K is
+S = -B A^-1 B^T, which is negative definite, so S~^-1 = -diag_e(nu_e M_p,e^-1), with nu_e
 the cell viscosity (the standard scaling for a variable viscosity; 1 for
 constant unit viscosity).  The partition-of-unity weights, the Chebyshev
 interval and the Arnoldi estimate follow oracle.multigrid.

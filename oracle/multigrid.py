@@ -16,7 +16,7 @@ Follows, step by step and without blocking or fusion:
              of the largest eigenvalue of M^-1 K; exact coarsest solve;
              FGMRES(30) stopped on the relative 2-norm residual.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * W_i = diag(1/m_j), m_j = number of patches containing DoF j.
   * Chebyshev interval [0.1, 1.1] * lambda_hat, lambda_hat = largest real
     part of the Ritz values of 15 Arnoldi steps on M^-1 K from a SplitMix64
