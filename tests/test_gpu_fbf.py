@@ -178,3 +178,36 @@ def test_fbf_mixed_precision(name):
     U = u.cpu().numpy().reshape(d, -1)[:, S["pv"]]
     assert rel <= 1e-10 and _rel(U, x[:d * nV].reshape(d, nV)) < 5e-7
     assert abs(its - its64) <= 2, (its, its64)
+
+
+def test_fbf_with_hmg_velocity_cycle():
+    """FBF(hMG), the paper's other FBF variant: the same entry with the
+    hierarchy STOKES_HIER_HMG (no p-coarsening: P_k on every mesh).  One
+    application matches the oracle's FBF over the hMG velocity hierarchy, and
+    the solve reaches the direct solution."""
+    v, c = W.unit_square_mesh(2)
+    k, nref = 3, 1
+    meshes, _ = geometry.hierarchy(v, c, nref, True)
+    D = stokes.discretize(*meshes[0], stokes.SV, k)
+    vh = fbf.VelocityHierarchy(v, c, nref, [k], barycentric=True)
+    lm = [L.lmax for L in vh.levels[:-1]]
+    h = P.StokesMG(v, c, nref, P.SV, k, fbf=True, hierarchy=P.HIER_HMG, lmax_override=lm, precision=P.FP64)
+    assert h.info()["n_levels"] == len(vh.levels)
+    xyz, comp, _ = h.level_dofs(0)
+    ox = vh.levels[0].disc.V.coords[vh.levels[0].disc.free]
+    sp0 = permutation(keys(xyz, comp), keys(ox, np.zeros(len(ox))))
+    pv, pq = full_field_perms(h, D)
+    nvf = vh.levels[0].disc.n_free
+    st = np.concatenate([c_ * nvf + sp0 for c_ in range(D.d)] + [D.d * nvf + pq])
+    r = np.random.default_rng(4).standard_normal(D.n_free)
+    z = h.fbf_apply(_lib(r, st)).cpu().numpy()[st]
+    assert _rel(z, fbf.FBF(D, vh).apply(r)) < 1e-10
+    f_o = np.random.default_rng(5).uniform(-1, 1, (D.d, D.V.n))
+    fl = np.empty_like(f_o)
+    fl[:, pv] = f_o
+    u, p, its, rel = h.solve(torch.tensor(fl.reshape(-1), device="cuda"), tol=1e-10)
+    b, xD = stokes.load_vector(D, f_o)
+    x = stokes.zero_mean_pressure(D, stokes.expand(D, stokes.direct_solve(D, b), xD))
+    U = u.cpu().numpy().reshape(D.d, -1)[:, pv]
+    assert rel <= 1e-10 and _rel(U, x[:D.d * D.V.n].reshape(D.d, D.V.n)) < 1e-7
+    h.close()
