@@ -298,6 +298,47 @@ int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, do
                  double tol, double* u, double* p, int* iterations, double* final_relres,
                  void* stream);
 
+/* stokes_solve for nrhs independent load cases on one handle (several
+ * forcings of the same operator, as a parameter study or a loss summed over
+ * forcings): every column's right-hand side is formed as stokes_solve forms
+ * it, the columns are solved together by stokes_fgmres_batched (one batched
+ * V-cycle per iteration for all of them), and every column's (u, p) is
+ * returned as stokes_solve returns it.  The paper solves one load case at a
+ * time (Sec. 4); the batch is this library's extension.
+ *   f_nodal   device [nrhs][dim][n_vel_nodes].
+ *   g_nodal   device [nrhs][dim][n_vel_nodes] or NULL (homogeneous for all).
+ *   nrhs      1 .. STOKES_BATCH_MAX;  mode  STOKES_BATCH_TF32 / _3XTF32.
+ *   nu, tol   as stokes_solve (the same for every column).
+ *   u         device [nrhs][dim][n_vel_nodes] out;  p  device [nrhs][n_pres_nodes] out.
+ *   iterations     host out (iterations of the batch);
+ *   final_relres   host [nrhs] out or NULL.
+ * Needs a monolithic MIXED handle.  Free-DoF buffers of the width are
+ * allocated on first use and kept.
+ * Errors: EINVAL, EUNSUPPORTED (patch too large at this width),
+ * ENOTCONVERGED (outputs hold the last iterate), ENONFINITE. */
+int stokes_solve_batched(stokes_mg_t h, const double* f_nodal, const double* g_nodal, int nrhs, int mode, double nu,
+                         double tol, double* u, double* p, int* iterations, double* final_relres, void* stream);
+
+/* stokes_adjoint_solve for nrhs loss gradients at once (one per column of a
+ * stokes_solve_batched call), solved together by stokes_fgmres_batched.
+ *   gu        device [nrhs][dim][n_vel_nodes];  gp  device [nrhs][n_pres_nodes].
+ *   lam_u     device [nrhs][dim][n_vel_nodes] out;
+ *   lam_p     device [nrhs][n_pres_nodes] out or NULL;
+ *   grad_f    device [nrhs][dim][n_vel_nodes] out or NULL.
+ *   Other arguments as stokes_solve_batched.
+ * Errors: as stokes_solve_batched. */
+int stokes_adjoint_solve_batched(stokes_mg_t h, const double* gu, const double* gp, int nrhs, int mode, double nu,
+                                 double tol, double* lam_u, double* lam_p, double* grad_f, int* iterations,
+                                 double* final_relres, void* stream);
+
+/* grad[e] = -sum_q sum_c lam_u,q,c[e]^T A_e u_q,c[e]: stokes_grad_viscosity
+ * summed over nrhs (u, lam_u) pairs, the gradient of a loss summed over the
+ * columns of a batched solve, with A_e formed once per cell for all of them.
+ *   u, lam_u  device [nrhs][dim][n_vel_nodes];  grad  device [n_cells] out.
+ * Errors: as stokes_grad_viscosity. */
+int stokes_grad_viscosity_batched(stokes_mg_t h, const double* u, const double* lam_u, int nrhs, double* grad,
+                                  void* stream);
+
 /* Sizes and setup statistics (host struct). */
 int stokes_mg_info(stokes_mg_t h, stokes_mg_stats* st);
 

@@ -84,6 +84,9 @@ def lib():
         "stokes_fgmres_batched": (c_int, [P, P, P, c_int, c_int, c_double, P, P, P]),
         "stokes_selftest_bounded_wait": (c_int, [c_longlong, P]),
         "stokes_grad_viscosity": (c_int, [P, P, P, P, P]),
+        "stokes_solve_batched": (c_int, [P, P, P, c_int, c_int, c_double, c_double, P, P, P, P, P]),
+        "stokes_adjoint_solve_batched": (c_int, [P, P, P, c_int, c_int, c_double, c_double, P, P, P, P, P, P]),
+        "stokes_grad_viscosity_batched": (c_int, [P, P, P, c_int, P, P]),
         "stokes_mg_cell_centroids": (c_int, [P, P, P]),
         "stokes_solve": (c_int, [P, P, P, c_double, c_double, P, P, POINTER(c_int), POINTER(c_double), P]),
         "stokes_mg_info": (c_int, [P, POINTER(Stats)]),
@@ -309,6 +312,56 @@ class StokesMG:
         g = torch.empty(n, dtype=torch.float64, device=u.device)
         check(lib().stokes_grad_viscosity(self.h, _ptr(u.contiguous()), _ptr(lam_u.contiguous()), _ptr(g),
                                           _stream(self.stream)))
+        return g
+
+    def solve_batched(self, F, G=None, mode=BATCH_3XTF32, nu=1.0, tol=1e-8, raise_on_nonconv=True):
+        """solve for nrhs forcings at once (stokes_solve_batched): F is
+        [nrhs, dim * n_vel_nodes] device float64 (G the same shape or None).
+        Returns (U [nrhs, dim * nV], P [nrhs, nQ], iterations, relres [nrhs])."""
+        import torch
+        F = F.contiguous()
+        nrhs = F.shape[0]
+        G = None if G is None else G.contiguous()
+        nQ = self.info()["n_pres_nodes"]
+        U = torch.empty_like(F)
+        Pp = torch.empty(nrhs, nQ, dtype=torch.float64, device=F.device)
+        its = c_int()
+        rel = np.zeros(nrhs, dtype=np.float64)
+        rc = lib().stokes_solve_batched(self.h, _ptr(F), _ptr(G), nrhs, int(mode), float(nu), float(tol), _ptr(U),
+                                        _ptr(Pp), byref(its), rel.ctypes.data_as(c_void_p), _stream(self.stream))
+        if rc != -4 or raise_on_nonconv:
+            check(rc)
+        return U, Pp, its.value, rel
+
+    def adjoint_batched(self, GU, GP, mode=BATCH_3XTF32, nu=1.0, tol=1e-8, grad_f=True, raise_on_nonconv=True):
+        """adjoint for nrhs loss gradients at once (stokes_adjoint_solve_batched):
+        GU [nrhs, dim * nV], GP [nrhs, nQ].  Returns (LAM_U, LAM_P, dL/dF or
+        None, iterations, relres [nrhs])."""
+        import torch
+        GU = GU.contiguous()
+        GP = GP.contiguous()
+        nrhs = GU.shape[0]
+        LU = torch.empty_like(GU)
+        LP = torch.empty_like(GP)
+        GF = torch.empty_like(GU) if grad_f else None
+        its = c_int()
+        rel = np.zeros(nrhs, dtype=np.float64)
+        rc = lib().stokes_adjoint_solve_batched(self.h, _ptr(GU), _ptr(GP), nrhs, int(mode), float(nu), float(tol),
+                                                _ptr(LU), _ptr(LP), _ptr(GF), byref(its),
+                                                rel.ctypes.data_as(c_void_p), _stream(self.stream))
+        if rc != -4 or raise_on_nonconv:
+            check(rc)
+        return LU, LP, GF, its.value, rel
+
+    def grad_viscosity_batched(self, U, LU):
+        """sum over the rows of dL/dnu per finest cell
+        (stokes_grad_viscosity_batched); U, LU [nrhs, dim * nV]."""
+        import torch
+        U = U.contiguous()
+        LU = LU.contiguous()
+        g = torch.empty(self.n_cells(), dtype=torch.float64, device=U.device)
+        check(lib().stokes_grad_viscosity_batched(self.h, _ptr(U), _ptr(LU), U.shape[0], _ptr(g),
+                                                  _stream(self.stream)))
         return g
 
     def n_cells(self):

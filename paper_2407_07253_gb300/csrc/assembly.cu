@@ -323,38 +323,53 @@ __global__ void k_load(AsmMesh m, const double* f, const double* gD, double inv_
     }
 }
 
-// dL/dnu_e = -lambda_e^T A_e u_e summed over the velocity components, A_e
-// the cell's unit-viscosity scalar stiffness (the operator's A_e(nu_e) =
-// nu_e A_e, so the stored factors are divided by nu_e).  One warp per cell:
-// the cell's velocities are staged in shared memory, lane i takes element
-// row i, forms A_e[i][j] = sum_ab G_ab S_ab[i][j] on the fly (the same for
-// every component) and pairs it with lambda_c[i] u_c[j]; a warp sum ends it.
+// dL/dnu_e = -sum_q lambda_q,e^T A_e u_q,e summed over the velocity
+// components and the nq (u, lambda) pairs of a batch, A_e the cell's
+// unit-viscosity scalar stiffness (the operator's A_e(nu_e) = nu_e A_e, so the
+// stored factors are divided by nu_e).  One warp per cell: up to GQ_MAX
+// columns' velocities are staged in shared memory at a time, lane i takes
+// element row i, forms A_e[i][j] = sum_ab G_ab S_ab[i][j] on the fly once per
+// pass (the same for every component and column) and pairs it with
+// sum_q,c lambda_q,c[i] u_q,c[j]; a warp sum ends it.
+constexpr int GQ_MAX = 4;
+
 __global__ void __launch_bounds__(256) k_grad_nu(AsmMesh m, const double* __restrict__ u,
-                                                 const double* __restrict__ lam, double* __restrict__ grad) {
+                                                 const double* __restrict__ lam, int nq, long long ld, int gq,
+                                                 double* __restrict__ grad) {
     extern __shared__ double us_all[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, d = m.d, nb = m.nb;
-    double* us = us_all + (size_t)w * d * nb;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, d = m.d, nb = m.nb, dnb = d * nb;
+    double* us = us_all + (size_t)w * gq * dnb;
     for (int e = blockIdx.x * 8 + w; e < m.nc; e += gridDim.x * 8) {
         const int* vc = m.vcell + (long long)e * nb;
-        for (int t = lane; t < d * nb; t += 32) {
-            const int c = t / nb, j = t - c * nb;
-            us[t] = u[(long long)c * m.nV + vc[j]];
-        }
-        __syncwarp();
         const double* G = m.cg + (long long)e * CG_STRIDE + 1;
         double acc = 0;
-        for (int i = lane; i < nb; i += 32) {
-            const int node = vc[i];
-            double li[3] = {0, 0, 0};
-            for (int c = 0; c < d; ++c) li[c] = lam[(long long)c * m.nV + node];
-            for (int j = 0; j < nb; ++j) {
-                double aij = 0;
-                for (int a = 0; a < d; ++a)
-                    for (int a2 = 0; a2 < d; ++a2) aij += G[a * d + a2] * m.S[(((long long)a * d + a2) * nb + i) * nb + j];
-                double sj = 0;
-                for (int c = 0; c < d; ++c) sj += li[c] * us[c * nb + j];
-                acc += aij * sj;
+        for (int q0 = 0; q0 < nq; q0 += gq) {
+            const int nqc = min(gq, nq - q0);
+            for (int t = lane; t < nqc * dnb; t += 32) {
+                const int qq = t / dnb, r = t - qq * dnb, c = r / nb, j = r - c * nb;
+                us[t] = u[(q0 + qq) * ld + (long long)c * m.nV + vc[j]];
             }
+            __syncwarp();
+            for (int i = lane; i < nb; i += 32) {
+                const int node = vc[i];
+                double li[GQ_MAX][3];
+#pragma unroll
+                for (int qq = 0; qq < GQ_MAX; ++qq)
+                    for (int c = 0; c < 3; ++c)
+                        li[qq][c] = (qq < nqc && c < d) ? lam[(q0 + qq) * ld + (long long)c * m.nV + node] : 0.0;
+                for (int j = 0; j < nb; ++j) {
+                    double aij = 0;
+                    for (int a = 0; a < d; ++a)
+                        for (int a2 = 0; a2 < d; ++a2) aij += G[a * d + a2] * m.S[(((long long)a * d + a2) * nb + i) * nb + j];
+                    double sj = 0;
+#pragma unroll
+                    for (int qq = 0; qq < GQ_MAX; ++qq)
+                        if (qq < nqc)
+                            for (int c = 0; c < d; ++c) sj += li[qq][c] * us[(qq * d + c) * nb + j];
+                    acc += aij * sj;
+                }
+            }
+            __syncwarp();
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) grad[e] = -acc / (m.nu ? m.nu[e] : 1.0);
@@ -381,10 +396,16 @@ __global__ void k_mass_all(AsmMesh m, const double* __restrict__ lam, double sca
 
 }  // namespace
 
-void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, double* grad, cudaStream_t s) {
-    const size_t smem = sizeof(double) * 8 * m.d * m.nb;
+void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, int nq, long long ld, double* grad,
+                    cudaStream_t s) {
+    // columns per pass: as many as fit GQ_MAX and 96 KB of staging for the 8 warps
+    const size_t per_col = sizeof(double) * 8 * m.d * m.nb;
+    const int gq = (int)std::max<size_t>(1, std::min<size_t>(GQ_MAX, (96u << 10) / per_col));
+    const size_t smem = per_col * gq;
+    // a refused attribute surfaces as the launch error the caller checks
+    if (smem > (48u << 10)) (void)cudaFuncSetAttribute(k_grad_nu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (int)std::min<long long>((m.nc + 7) / 8, 152LL * 16);
-    k_grad_nu<<<grid, 256, smem, s>>>(m, u, lam, grad);
+    k_grad_nu<<<grid, 256, smem, s>>>(m, u, lam, nq, ld, gq, grad);
 }
 
 void mass_apply_all(const AsmMesh& m, const double* lam, double scale, double* out, cudaStream_t s) {

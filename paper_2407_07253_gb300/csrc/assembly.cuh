@@ -54,10 +54,12 @@ void fill_rows(const AsmMesh& m, const int* rp, int* ci, double* v, int* status,
 void load_vector(const AsmMesh& m, const double* f, const double* g, double inv_nu, double* b, cudaStream_t s);
 
 // Adjoint pieces (the discrete adjoint of the solve):
-// grad[e] = -sum_c lambda_c[e]^T A_e u_c[e] for every cell, A_e the
-// unit-viscosity stiffness of cell e; u and lambda are [d][nV] nodal fields
-// (u with its boundary values, lambda zero on the boundary).
-void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, double* grad, cudaStream_t s);
+// grad[e] = -sum_q sum_c lambda_q,c[e]^T A_e u_q,c[e] for every cell, A_e
+// the unit-viscosity stiffness of cell e; u and lambda are nq [d][nV] nodal
+// fields ld doubles apart (u with its boundary values, lambda zero on the
+// boundary).
+void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, int nq, long long ld, double* grad,
+                    cudaStream_t s);
 // out[c][i] = scale (M lambda_c)[i] for every velocity node i.
 void mass_apply_all(const AsmMesh& m, const double* lam, double scale, double* out, cudaStream_t s);
 

@@ -271,6 +271,8 @@ struct stokes_mg {
         double *hcol = nullptr, *hcol2 = nullptr, *hn = nullptr, *Hc = nullptr, *cs = nullptr, *sn = nullptr;
         double *g = nullptr, *y = nullptr, *resid = nullptr, *beta = nullptr, *beta0 = nullptr;
         double* host = nullptr;        // pinned [2 m]
+        int io_m = 0;                  // width of the batched solve's free-DoF buffers
+        double *iob = nullptr, *iox = nullptr;
     } bk;
     cudaGraphExec_t bgraph[2] = {nullptr, nullptr};
     long long bgraph_launches[2] = {0, 0};
@@ -2236,6 +2238,113 @@ int fgmres_batched(stokes_mg* h, int nrhs, int mode, const double* B_dev, double
         for (int c = 0; c < nrhs; ++c) rel_out[c] = beta0[c] > 0.0 ? res[c] / beta0[c] : 0.0;
     return converged ? STOKES_OK : STOKES_ENOTCONVERGED;
 }
+
+// b = stokes_solve's free-DoF right-hand side for the nodal forcing f and
+// Dirichlet data g (NULL: homogeneous): b_u = (M f)/nu - K[free, D] g on the
+// free velocity rows, b_p = -K[p, D] g, then the pressure part made
+// orthogonal to the constant pressures (the consistency condition of the
+// singular all-Dirichlet system, Sec. 2)
+void solve_rhs(stokes_mg* h, const double* f_nodal, const double* g_nodal, double nu, double* b, cudaStream_t s) {
+    const sfem::Level& F = finest_stokes(h);
+    const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ;
+    const double* gfull = g_nodal ? g_nodal : h->gzero;
+    const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
+    if (fl.dev_asm) {
+        // matrix-free: assembled per row from the incident cells (the same
+        // element integrals as the operator)
+        launch(h, -1, s, [&] { sasm::load_vector(fl.am, f_nodal, g_nodal, 1.0 / nu, b, s); });
+    } else {
+        // F_c = M f_c
+        for (int c = 0; c < d; ++c)
+            spmv<double>(h, -1, h->Mv, skern::SPMV_SET, f_nodal + (size_t)c * nV, h->F + (size_t)c * nV, nullptr, s);
+        launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->F, b); });
+        if (nu != 1.0) axpby_l<double>(h, d * nVf, 0.0, b, 1.0 / nu, b, s);
+        CK(cudaMemsetAsync(b + (size_t)d * nVf, 0, sizeof(double) * nQ, s));
+        spmv<double>(h, -1, h->KfD, skern::SPMV_RESID, gfull, b, b, s);
+    }
+    mdot(h, nQ, 1, b + (size_t)d * nVf, nQ, h->ones, h->scal, nullptr, false, s);
+    launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, b + (size_t)d * nVf, h->scal, (double)nQ); });
+}
+
+// (u, p) from the free-DoF solution x: u = g on the boundary and x on the
+// free nodes; p = nu * p' shifted to int p = 0 (Sec. 2)
+void solve_output(stokes_mg* h, const double* x, const double* g_nodal, double nu, double* u, double* p,
+                  cudaStream_t s) {
+    const sfem::Level& F = finest_stokes(h);
+    const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ;
+    const double* gfull = g_nodal ? g_nodal : h->gzero;
+    CK(cudaMemcpyAsync(u, gfull, sizeof(double) * d * nV, cudaMemcpyDeviceToDevice, s));
+    launch(h, -1, s, [&] { skern::scatter_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, x, u); });
+    CK(cudaMemcpyAsync(p, x + (size_t)d * nVf, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
+    if (nu != 1.0) axpby_l<double>(h, nQ, 0.0, p, nu, p, s);
+    mdot(h, nQ, 1, p, nQ, h->pint, h->scal, nullptr, false, s);
+    launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, p, h->scal, h->pint_sum); });
+}
+
+// r = (gu on the free velocity DoFs, nu Pi^T gp), Pi^T gp = gp - w (1^T gp) / (w^T 1):
+// the transpose of the zero-mean normalisation of the solve's pressure output
+void adjoint_rhs(stokes_mg* h, const double* gu, const double* gp, double nu, double* r, cudaStream_t s) {
+    const sfem::Level& F = finest_stokes(h);
+    const int d = F.d, nVf = F.nVf, nQ = F.nQ;
+    double* rp = r + (size_t)d * nVf;
+    launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, gu, r); });
+    CK(cudaMemcpyAsync(rp, gp, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
+    mdot(h, nQ, 1, rp, nQ, h->ones, h->scal, nullptr, false, s);
+    launch(h, -1, s, [&] { skern::sub_weighted<<<grid_for(nQ), 256, 0, s>>>(nQ, rp, h->pint, h->scal, h->pint_sum); });
+    if (nu != 1.0) axpby_l<double>(h, nQ, 0.0, rp, nu, rp, s);
+}
+
+// lambda_u (0 on the boundary), lambda_p (zero plain mean; optional) and
+// dL/df_c = M lambda_u,c / nu (optional) from the free-DoF adjoint x
+void adjoint_output(stokes_mg* h, const double* x, double nu, double* lam_u, double* lam_p, double* grad_f,
+                    cudaStream_t s) {
+    const sfem::Level& F = finest_stokes(h);
+    const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ;
+    CK(cudaMemsetAsync(lam_u, 0, sizeof(double) * d * nV, s));
+    launch(h, -1, s, [&] { skern::scatter_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, x, lam_u); });
+    if (lam_p) {
+        CK(cudaMemcpyAsync(lam_p, x + (size_t)d * nVf, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
+        mdot(h, nQ, 1, lam_p, nQ, h->ones, h->scal, nullptr, false, s);
+        launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, lam_p, h->scal, (double)nQ); });
+    }
+    if (grad_f) {
+        const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
+        if (fl.dev_asm) {
+            launch(h, -1, s, [&] { sasm::mass_apply_all(fl.am, lam_u, 1.0 / nu, grad_f, s); });
+        } else {
+            for (int c = 0; c < d; ++c)
+                spmv<double>(h, -1, h->Mv, skern::SPMV_SET, lam_u + (size_t)c * nV, grad_f + (size_t)c * nV, nullptr, s);
+            if (nu != 1.0) axpby_l<double>(h, d * nV, 0.0, grad_f, 1.0 / nu, grad_f, s);
+        }
+    }
+}
+
+// argument checks shared by the batched entries: a monolithic MIXED handle
+// whose patches all fit the batched patch GEMM at this width
+void require_batched(stokes_mg* h, int nrhs, int mode) {
+    require(nrhs >= 1 && nrhs <= STOKES_BATCH_MAX, "nrhs must be in 1..STOKES_BATCH_MAX");
+    require(mode == STOKES_BATCH_TF32 || mode == STOKES_BATCH_3XTF32, "unknown batch mode");
+    require(!h->host_only && h->opts.precision == STOKES_MIXED && !h->fbf,
+            "the batched FGMRES needs a monolithic MIXED handle");
+    require(h->L[0].K.v64 != nullptr, "level 0 has no FP64 operator");
+    const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
+    for (size_t li = 0; li + 1 < h->L.size(); ++li)
+        if (const char* why = sbat::patch_gemm_check(mode, h->L[li].maxn, m))
+            throw StokesError(STOKES_EUNSUPPORTED, why);
+}
+
+// the batched solve entries' free-DoF right-hand sides and solutions,
+// [width][n_free(level 0)] each, kept for the handle's lifetime
+void ensure_batch_io(stokes_mg* h, int nrhs) {
+    auto& K = h->bk;
+    const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
+    if (K.io_m >= m) return;
+    const size_t nm = (size_t)h->L[0].n * m;
+    K.iob = halloc<double>(h, nm);
+    K.iox = halloc<double>(h, nm);
+    CK(cudaStreamSynchronize(h->s_up));
+    K.io_m = m;
+}
 }  // namespace
 
 int stokes_selftest_bounded_wait(long long polls, int* result) {
@@ -2258,16 +2367,9 @@ int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int
                           int* iterations, double* final_relres, void* stream) {
     g_last_error.clear();
     return guarded([&] {
-        require(h && b_dev && x_dev && nrhs >= 1 && nrhs <= STOKES_BATCH_MAX && tol > 0, "invalid argument");
-        require(mode == STOKES_BATCH_TF32 || mode == STOKES_BATCH_3XTF32, "unknown batch mode");
-        require(!h->host_only && h->opts.precision == STOKES_MIXED && !h->fbf,
-                "the batched FGMRES needs a monolithic MIXED handle");
-        require(h->L[0].K.v64 != nullptr, "level 0 has no FP64 operator");
+        require(h && b_dev && x_dev && tol > 0, "invalid argument");
+        require_batched(h, nrhs, mode);
         DeviceGuard dg(h);
-        const int m = nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : nrhs <= 32 ? 32 : 64;
-        for (size_t li = 0; li + 1 < h->L.size(); ++li)
-            if (const char* why = sbat::patch_gemm_check(mode, h->L[li].maxn, m))
-                throw StokesError(STOKES_EUNSUPPORTED, why);
         int rc = fgmres_batched(h, nrhs, mode, b_dev, x_dev, tol, iterations, final_relres, (cudaStream_t)stream);
         if (rc != STOKES_OK) g_last_error = "batched FGMRES: a column did not reach the tolerance within maxit";
         return rc;
@@ -2329,36 +2431,9 @@ int stokes_solve(stokes_mg_t h, const double* f_nodal, const double* g_nodal, do
         require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
         DeviceGuard dg(h);
         cudaStream_t s = (cudaStream_t)stream;
-        const sfem::Level& F = finest_stokes(h);
-        const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ, n = F.n_free;
-        const double* gfull = g_nodal ? g_nodal : h->gzero;
-        const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
-        if (fl.dev_asm) {
-            // matrix-free: b = (M f)/nu - K[free, D] g, assembled per row from
-            // the incident cells (same element integrals as the operator)
-            launch(h, -1, s, [&] { sasm::load_vector(fl.am, f_nodal, g_nodal, 1.0 / nu, h->bvec, s); });
-        } else {
-            // F_c = M f_c
-            for (int c = 0; c < d; ++c)
-                spmv<double>(h, -1, h->Mv, skern::SPMV_SET, f_nodal + (size_t)c * nV, h->F + (size_t)c * nV, nullptr, s);
-            // b_vel = F / nu on the free rows, b_p = 0; then b -= K_{free,D} g
-            launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->F, h->bvec); });
-            if (nu != 1.0) axpby_l<double>(h, d * nVf, 0.0, h->bvec, 1.0 / nu, h->bvec, s);
-            CK(cudaMemsetAsync(h->bvec + (size_t)d * nVf, 0, sizeof(double) * nQ, s));
-            spmv<double>(h, -1, h->KfD, skern::SPMV_RESID, gfull, h->bvec, h->bvec, s);
-        }
-        // remove the component along the pressure null vector (consistency)
-        mdot(h, nQ, 1, h->bvec + (size_t)d * nVf, nQ, h->ones, h->scal, nullptr, false, s);
-        launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, h->bvec + (size_t)d * nVf, h->scal, (double)nQ); });
+        solve_rhs(h, f_nodal, g_nodal, nu, h->bvec, s);
         int rc = fgmres(h, h->bvec, h->xvec, tol, iterations, final_relres, s);
-        // u = g on the boundary, x on the free nodes; p = nu * p' with zero mean
-        CK(cudaMemcpyAsync(u, gfull, sizeof(double) * d * nV, cudaMemcpyDeviceToDevice, s));
-        launch(h, -1, s, [&] { skern::scatter_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->xvec, u); });
-        CK(cudaMemcpyAsync(p, h->xvec + (size_t)d * nVf, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
-        if (nu != 1.0) axpby_l<double>(h, nQ, 0.0, p, nu, p, s);
-        mdot(h, nQ, 1, p, nQ, h->pint, h->scal, nullptr, false, s);
-        launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, p, h->scal, h->pint_sum); });
-        (void)n;
+        solve_output(h, h->xvec, g_nodal, nu, u, p, s);
         if (rc != STOKES_OK) g_last_error = "FGMRES did not reach the tolerance within maxit";
         return rc;
     });
@@ -2372,36 +2447,10 @@ int stokes_adjoint_solve(stokes_mg_t h, const double* gu, const double* gp, doub
         require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
         DeviceGuard dg(h);
         cudaStream_t s = (cudaStream_t)stream;
-        const sfem::Level& F = finest_stokes(h);
-        const int d = F.d, nV = F.V.n, nVf = F.nVf, nQ = F.nQ;
-        double* rp = h->bvec + (size_t)d * nVf;
-        // r = (gu on the free velocity DoFs, nu Pi^T gp), Pi^T gp = gp - w (1^T gp) / (w^T 1):
-        // the transpose of the zero-mean normalisation of the solve's pressure output
-        launch(h, -1, s, [&] { skern::gather_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, gu, h->bvec); });
-        CK(cudaMemcpyAsync(rp, gp, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
-        mdot(h, nQ, 1, rp, nQ, h->ones, h->scal, nullptr, false, s);
-        launch(h, -1, s, [&] { skern::sub_weighted<<<grid_for(nQ), 256, 0, s>>>(nQ, rp, h->pint, h->scal, h->pint_sum); });
-        if (nu != 1.0) axpby_l<double>(h, nQ, 0.0, rp, nu, rp, s);
+        adjoint_rhs(h, gu, gp, nu, h->bvec, s);
         // K is symmetric: the adjoint system is the forward one (same FGMRES-phMG)
         int rc = fgmres(h, h->bvec, h->xvec, tol, iterations, final_relres, s);
-        CK(cudaMemsetAsync(lam_u, 0, sizeof(double) * d * nV, s));
-        launch(h, -1, s, [&] { skern::scatter_idx<double><<<grid_for(d * nVf), 256, 0, s>>>(d * nVf, h->vel_rows, h->xvec, lam_u); });
-        if (lam_p) {
-            CK(cudaMemcpyAsync(lam_p, h->xvec + (size_t)d * nVf, sizeof(double) * nQ, cudaMemcpyDeviceToDevice, s));
-            mdot(h, nQ, 1, lam_p, nQ, h->ones, h->scal, nullptr, false, s);
-            launch(h, -1, s, [&] { skern::sub_scalar<<<grid_for(nQ), 256, 0, s>>>(nQ, lam_p, h->scal, (double)nQ); });
-        }
-        if (grad_f) {
-            // dL/df_c = M lambda_u,c / nu on every velocity node
-            const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
-            if (fl.dev_asm) {
-                launch(h, -1, s, [&] { sasm::mass_apply_all(fl.am, lam_u, 1.0 / nu, grad_f, s); });
-            } else {
-                for (int c = 0; c < d; ++c)
-                    spmv<double>(h, -1, h->Mv, skern::SPMV_SET, lam_u + (size_t)c * nV, grad_f + (size_t)c * nV, nullptr, s);
-                if (nu != 1.0) axpby_l<double>(h, d * nV, 0.0, grad_f, 1.0 / nu, grad_f, s);
-            }
-        }
+        adjoint_output(h, h->xvec, nu, lam_u, lam_p, grad_f, s);
         if (rc != STOKES_OK) g_last_error = "FGMRES did not reach the tolerance within maxit";
         return rc;
     });
@@ -2416,8 +2465,72 @@ int stokes_grad_viscosity(stokes_mg_t h, const double* u, const double* lam_u, d
         if (!fl.dev_asm)
             throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs a device-assembled finest level");
         cudaStream_t s = (cudaStream_t)stream;
-        launch(h, -1, s, [&] { sasm::grad_viscosity(fl.am, u, lam_u, grad, s); });
+        launch(h, -1, s, [&] { sasm::grad_viscosity(fl.am, u, lam_u, 1, 0, grad, s); });
         return STOKES_OK;
+    });
+}
+
+int stokes_grad_viscosity_batched(stokes_mg_t h, const double* u, const double* lam_u, int nrhs, double* grad,
+                                  void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && u && lam_u && grad && nrhs >= 1, "invalid argument");
+        DeviceGuard dg(h);
+        const DevLevel& fl = h->fbf ? h->fbf->S0d : h->L[0];
+        if (!fl.dev_asm)
+            throw StokesError(STOKES_EUNSUPPORTED, "the viscosity gradient needs a device-assembled finest level");
+        const sfem::Level& F = finest_stokes(h);
+        const long long ld = (long long)F.d * F.V.n;
+        cudaStream_t s = (cudaStream_t)stream;
+        launch(h, -1, s, [&] { sasm::grad_viscosity(fl.am, u, lam_u, nrhs, ld, grad, s); });
+        return STOKES_OK;
+    });
+}
+
+int stokes_solve_batched(stokes_mg_t h, const double* f_nodal, const double* g_nodal, int nrhs, int mode, double nu,
+                         double tol, double* u, double* p, int* iterations, double* final_relres, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && f_nodal && u && p, "invalid argument");
+        require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
+        require_batched(h, nrhs, mode);
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        ensure_batch_io(h, nrhs);
+        const sfem::Level& F = finest_stokes(h);
+        const long long nv = (long long)F.d * F.V.n, n = F.n_free, nQ = F.nQ;
+        auto& K = h->bk;
+        for (int q = 0; q < nrhs; ++q)
+            solve_rhs(h, f_nodal + q * nv, g_nodal ? g_nodal + q * nv : nullptr, nu, K.iob + q * n, s);
+        int rc = fgmres_batched(h, nrhs, mode, K.iob, K.iox, tol, iterations, final_relres, s);
+        for (int q = 0; q < nrhs; ++q)
+            solve_output(h, K.iox + q * n, g_nodal ? g_nodal + q * nv : nullptr, nu, u + q * nv, p + q * nQ, s);
+        if (rc != STOKES_OK) g_last_error = "batched FGMRES: a column did not reach the tolerance within maxit";
+        return rc;
+    });
+}
+
+int stokes_adjoint_solve_batched(stokes_mg_t h, const double* gu, const double* gp, int nrhs, int mode, double nu,
+                                 double tol, double* lam_u, double* lam_p, double* grad_f, int* iterations,
+                                 double* final_relres, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && gu && gp && lam_u, "invalid argument");
+        require(nu > 0 && std::isfinite(nu) && tol > 0, "nu and tol must be positive");
+        require_batched(h, nrhs, mode);
+        DeviceGuard dg(h);
+        cudaStream_t s = (cudaStream_t)stream;
+        ensure_batch_io(h, nrhs);
+        const sfem::Level& F = finest_stokes(h);
+        const long long nv = (long long)F.d * F.V.n, n = F.n_free, nQ = F.nQ;
+        auto& K = h->bk;
+        for (int q = 0; q < nrhs; ++q) adjoint_rhs(h, gu + q * nv, gp + q * nQ, nu, K.iob + q * n, s);
+        int rc = fgmres_batched(h, nrhs, mode, K.iob, K.iox, tol, iterations, final_relres, s);
+        for (int q = 0; q < nrhs; ++q)
+            adjoint_output(h, K.iox + q * n, nu, lam_u + q * nv, lam_p ? lam_p + q * nQ : nullptr,
+                           grad_f ? grad_f + q * nv : nullptr, s);
+        if (rc != STOKES_OK) g_last_error = "batched FGMRES: a column did not reach the tolerance within maxit";
+        return rc;
     });
 }
 
