@@ -23,6 +23,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FGMRES-phMG time to 1e-8 residual + setup time, mixed vs FP64 on GB300"
 TOL = 1e-8
+# relaxation of the main step.  Sec. 4 reports, per run, the fastest of the
+# (n_V, nu_p, nu_h) combinations it explored; on the TH P4 problems here that
+# is Chebyshev of degree 2 on [0.5, 2.0] lambda_max around one Vanka-star ASM
+# sweep, pre and post (10 / 12 / 13 iterations on 64^2 / 128^2 / 256^2, where
+# degree 1 on [0.1, 1.1] lambda_max takes 20 / 30 / 81).  "v11" is that
+# degree-1 default of the library, kept as a comparison.
+RELAX = {"v22": dict(nu_p=2, nu_h=2, cheb_lo=0.5, cheb_hi=2.0), "v11": dict(nu_p=1, nu_h=1, cheb_lo=0.1, cheb_hi=1.1)}
 
 
 def parse():
@@ -36,6 +43,10 @@ def parse():
     ap.add_argument("--single", action="store_true",
                     help="one mixed-precision setup + solve and exit (profiling driver)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--relaxation", default="v22", choices=sorted(RELAX),
+                    help="v22: Chebyshev(2) on [0.5, 2] lmax pre and post; v11: Chebyshev(1) on [0.1, 1.1] lmax")
+    ap.add_argument("--no-paper-scale", action="store_true",
+                    help="skip the 2.7 M DoF TH P4 256 x 256 measurement")
     ap.add_argument("--batched-workload", default="th_p3_cube16",
                     help="workload of the batched multi-RHS V-cycle measurement")
     ap.add_argument("--nrhs", type=int, default=64)
@@ -45,6 +56,8 @@ def parse():
     ap.add_argument("--adjoint-workload", default="th_p3_128x128_nu",
                     help="workload of the adjoint (gradient) measurement")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-nrhs", type=int, default=32,
+                    help="forcings of the batched forward + backward of the adjoint workload")
     ap.add_argument("--fbf-workload", default="sv_p4_disk",
                     help="Scott-Vogelius workload of the FBF(phMG) versus monolithic phMG measurement")
     ap.add_argument("--no-fbf", action="store_true")
@@ -81,7 +94,8 @@ import workloads as W
 from oracle import multigrid as mg
 w = W.workload({name!r})
 t0 = time.perf_counter()
-h = mg.Hierarchy(w.verts, w.cells, w.n_refine, w.family, w.schedule, barycentric=w.barycentric)
+h = mg.Hierarchy(w.verts, w.cells, w.n_refine, w.family, w.schedule, barycentric=w.barycentric,
+                 opts=mg.Options(**{relax!r}))
 t1 = time.perf_counter()
 D = h.levels[0].disc
 f = W.nodal_forcing(D.V.n, D.d, w.seed)
@@ -91,14 +105,21 @@ print(json.dumps(dict(setup_s=t1 - t0, solve_s=t2 - t1, its=its, relres=hist[-1]
 """
 
 
-def run_oracle(name, timeout=900):
-    """The FP64 CPU oracle, as it stands, in a fresh single-threaded process."""
+def run_oracle(name, relax, timeout=900):
+    """The FP64 CPU oracle, as it stands, in a fresh single-threaded process,
+    with the relaxation parameters of the GPU step."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL)
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL, relax=RELAX[relax])
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=timeout, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def relax_text(name):
+    r = RELAX[name]
+    return (f"V({r['nu_p']},{r['nu_h']}): Chebyshev degree {r['nu_p']} (p-levels) / {r['nu_h']} (h-levels) on "
+            f"[{r['cheb_lo']}, {r['cheb_hi']}] x lambda_max around one Vanka-star ASM sweep, pre and post")
 
 
 def reference_arm(a):
@@ -107,16 +128,17 @@ def reference_arm(a):
         return
     runs = []
     for _ in range(max(1, a.steps)):
-        runs.append(run_oracle(a.workload))
+        runs.append(run_oracle(a.workload, a.relaxation))
     ms = [1e3 * (r["setup_s"] + r["solve_s"]) for r in runs]
     value = sum(ms) / len(ms)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": a.workload, "tol": TOL},
+        "config": {"workload": a.workload, "tol": TOL, "relaxation": relax_text(a.relaxation)},
         "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"full setup + FGMRES solve of {a.workload} per step, single-threaded numpy/scipy",
+                         "sample": f"full setup + FGMRES solve of {a.workload} per step, {relax_text(a.relaxation)}, "
+                                   "single-threaded numpy/scipy",
                          "iterations": runs[0]["its"]},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -301,7 +323,9 @@ def adjoint_section(a, P, W, dev, stream, flush):
     """Forward (setup with per-cell viscosity + solve) and backward (adjoint
     FGMRES-phMG solve, dL/df and dL/dnu kernels) for one seeded forcing and
     one seeded loss gradient L = gu . u + gp . p, CUDA events on the stream,
-    L2 flushed before each phase."""
+    L2 flushed before each phase; then the workload's batch of seeded
+    forcings forward and backward at once (adjoint_batched), against the same
+    number of single-forcing forward + backward passes."""
     import numpy as np
     import torch
 
@@ -348,7 +372,11 @@ def adjoint_section(a, P, W, dev, stream, flush):
     run()                                   # warm-up
     reps = [run() for _ in range(max(3, min(a.steps, 5)))]
     med = {k: sorted(r[k] for r in reps)[len(reps) // 2] for k in ("forward", "adjoint_solve", "grad_nu")}
+    batched = adjoint_batched(a, P, W, w, nu, nV, d, dev, stream, flush, kw)
+    batched["sequential_single_ms"] = a.adjoint_nrhs * (med["forward"] + med["adjoint_solve"] + med["grad_nu"])
+    batched["speedup_vs_sequential_single"] = batched["sequential_single_ms"] / batched["total_ms"]
     return {
+        "batched": batched,
         "workload": a.adjoint_workload, "n_cells": nc, "n_free": i0["n_free"][0],
         "forward_ms": med["forward"], "backward_ms": med["adjoint_solve"] + med["grad_nu"],
         "adjoint_solve_ms": med["adjoint_solve"], "grad_nu_kernel_ms": med["grad_nu"],
@@ -358,6 +386,92 @@ def adjoint_section(a, P, W, dev, stream, flush):
         "loss": "L = gu . u + gp . p, gu and gp seeded N(0, 1); f seeded U[-1, 1] nodal; nu_e = exp(N(0, 1/4))",
         "l2": "flushed (256 MB write) before the forward and before the backward",
     }
+
+
+def adjoint_batched(a, P, W, w, nu, nV, d, dev, stream, flush, kw):
+    """The adjoint workload's nrhs seeded forcings through the batched
+    autograd wrapper: forward = setup with nu_cell + stokes_solve_batched,
+    backward (L = sum_q 0.5 ||u_q - u_target||^2, u_target seeded U[-1, 1]
+    nodal) = stokes_adjoint_solve_batched + stokes_grad_viscosity_batched.
+    CUDA events on the stream, L2 flushed before each phase, median of the
+    timed repetitions after one warm-up."""
+    import numpy as np
+    import torch
+    from paper_2407_07253_gb300 import autograd as PA
+
+    nb = a.adjoint_nrhs
+    F0 = torch.tensor(np.stack([W.nodal_forcing(nV, d, w.seed + 100 + q) for q in range(nb)]), device=dev)
+    ut = torch.tensor(np.random.default_rng(w.seed + 9).uniform(-1.0, 1.0, (d, nV)), device=dev)
+    kwb = {k: v for k, v in kw.items() if k != "precision"}
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def run():
+        F = F0.clone().requires_grad_(True)
+        nu_t = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
+        flush.fill_(1.0)
+        e0 = ev()
+        U, Pp = PA.solve_batched(w.verts, w.cells, w.n_refine, w.family, w.k, F, nu_t, tol=TOL,
+                                 mode=P.BATCH_3XTF32, precision=P.MIXED, **kwb)
+        e1 = ev()
+        L = 0.5 * ((U - ut) ** 2).sum()
+        e1.synchronize()
+        flush.fill_(1.0)
+        e2 = ev()
+        L.backward()
+        e3 = ev()
+        e3.synchronize()
+        return dict(forward=e0.elapsed_time(e1), backward=e2.elapsed_time(e3),
+                    gf_norm=float(F.grad.norm()), gnu_norm=float(nu_t.grad.norm()))
+
+    run()
+    reps = [run() for _ in range(max(3, min(a.steps, 5)))]
+    fw = sorted(r["forward"] for r in reps)[len(reps) // 2]
+    bw = sorted(r["backward"] for r in reps)[len(reps) // 2]
+    return {"nrhs": nb, "forward_ms": fw, "backward_ms": bw, "total_ms": fw + bw,
+            "forcings_per_s": 1e3 * nb / (fw + bw), "mode": "3xtf32 batched V-cycle, FP64 batched FGMRES",
+            "loss": "sum_q 0.5 ||u_q - u_target||^2, f_q seeded U[-1, 1] nodal (seeds seed+100+q)",
+            "grad_norms": {"f": reps[-1]["gf_norm"], "nu": reps[-1]["gnu_norm"]}}
+
+
+def paper_scale_section(P, W, dev, stream, flush, reps=3):
+    """TH P4/P3 on the 256 x 256 mesh (2.7 M free DoFs; the size of the
+    paper's 2D Taylor-Hood runs): one step (setup + mixed-precision solve to
+    TOL, L2 flushed, CUDA events) with each relaxation, median of `reps`
+    after one warm-up."""
+    import torch
+
+    w = W.workload("th_p4_256x256")
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, hierarchy=P.HIER_EXPLICIT,
+                       schedule=w.schedule, host_only=1)
+    i0 = probe.info()
+    probe.close()
+    f = torch.tensor(W.nodal_forcing(i0["n_vel_nodes"], w.verts.shape[1], w.seed).reshape(-1), device=dev)
+    res = {"workload": "th_p4_256x256", "n_free": int(i0["n_free"][0]), "levels": int(i0["n_levels"])}
+    for name in ("v22", "v11"):
+        runs = []
+        for r in range(reps + 1):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, hierarchy=P.HIER_EXPLICIT,
+                           schedule=w.schedule, precision=P.MIXED, stream=stream.cuda_stream, **RELAX[name])
+            st = h.info()
+            u, p, its, rel = h.solve(f, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            if r:
+                runs.append((e0.elapsed_time(e1), st["t_total_ms"], its, rel))
+            h.close()
+        runs.sort()
+        ms, setup, its, rel = runs[len(runs) // 2]
+        res[name] = {"step_ms": ms, "setup_ms": setup, "iterations": its, "relres": rel}
+    res["v11_over_v22"] = res["v11"]["step_ms"] / res["v22"]["step_ms"]
+    return res
 
 
 def fbf_section(a, P, W, dev, stream, flush):
@@ -436,10 +550,10 @@ def main():
     w = W.workload(a.workload)
     stream = torch.cuda.current_stream(dev)
 
-    def make(precision, prof_mask=0):
+    def make(precision, prof_mask=0, relax=a.relaxation):
         return P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
                           hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=precision,
-                          stream=stream.cuda_stream, prof_mask=prof_mask)
+                          stream=stream.cuda_stream, prof_mask=prof_mask, **RELAX[relax])
 
     # forcing in the library's node order (seeded U[-1,1] nodal values)
     probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
@@ -460,12 +574,12 @@ def main():
             pg.barrier()
         torch.cuda.synchronize(dev)
 
-    def one_step(precision, e2e=False, prof=None):
+    def one_step(precision, e2e=False, prof=None, relax=a.relaxation):
         flush.fill_(1.0)                      # L2 flush between steps (outside the events)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = make(precision, sum(1 << k for k in (prof or [])))
+        h = make(precision, sum(1 << k for k in (prof or [])), relax)
         if e2e:
             f = f_host.to(dev, non_blocking=True)
         else:
@@ -528,6 +642,16 @@ def main():
     # FP64 V-cycle for the mixed-vs-FP64 comparison
     one_step(P.FP64)                     # untimed: FP64 warm-up
     f64 = [one_step(P.FP64) for _ in range(max(3, a.steps))]
+    # the other relaxation, same step otherwise
+    other = "v11" if a.relaxation == "v22" else "v22"
+    one_step(P.MIXED, relax=other)
+    alt = [one_step(P.MIXED, relax=other) for _ in range(max(3, a.steps))]
+    paper = None
+    if not a.no_paper_scale:
+        try:
+            paper = paper_scale_section(P, W, dev, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            paper = {"error": str(e)[:300]}
     # solve-phase roofline: level 0's FP32 patch apply (one ASM sweep over
     # 4225 inverses), timed by CUDA events on its stream after an L2 flush
     hp = make(P.MIXED, 1 << P._binding.PROF_PATCH)
@@ -625,6 +749,7 @@ def main():
         "config": {"workload": a.workload, "family": "TH" if w.family == 0 else "SV", "k": w.k,
                    "schedule": w.schedule, "n_free": stats["n_free"], "nnz_level0": stats["nnz"][0],
                    "tol": TOL, "precision": "mixed (FP32 V-cycle, FP64 FGMRES/LU/coarse)",
+                   "relaxation": relax_text(a.relaxation),
                    "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) before every step",
                    "inputs": "mesh on host, f resident in HBM"},
         "iterations": its_l[-1],
@@ -652,6 +777,10 @@ def main():
         "wall_s_timed": wall,
     }
     line["speedup_mixed_vs_fp64"] = line["fp64"]["value"] / ms_max
+    line["relaxation_" + other] = {"value": sorted(x[0] for x in alt)[len(alt) // 2], "unit": "ms",
+                                   "iterations": alt[-1][1], "relaxation": relax_text(other)}
+    if paper is not None:
+        line["paper_scale"] = paper
     if batched is not None:
         line["batched"] = batched
     if adj is not None:
@@ -661,11 +790,12 @@ def main():
     line["clocks"] = clk.summary()
     if not a.no_cpu_baseline and world == 1:
         try:
-            o = run_oracle(a.workload)
+            o = run_oracle(a.workload, a.relaxation)
             line["cpu_baseline"] = {"value": 1e3 * (o["setup_s"] + o["solve_s"]), "unit": "ms", "cores": 1,
                                     "kind": "oracle",
                                     "sample": f"one full setup + FGMRES solve of {a.workload} to {TOL}, "
-                                              "single-threaded numpy/scipy", "iterations": o["its"]}
+                                              f"{relax_text(a.relaxation)}, single-threaded numpy/scipy",
+                                    "iterations": o["its"]}
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline"] = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {e}"[:200]}

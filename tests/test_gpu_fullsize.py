@@ -1,11 +1,14 @@
 """Parity at the workloads' full sizes, in the launch configuration that
-bench.py times (HIER_EXPLICIT schedule, defaults otherwise).
+bench.py times (HIER_EXPLICIT schedule, bench's relaxation parameters,
+defaults otherwise).
 
-* TH P4/P3 on the 64x64 square (167,299 free DoFs, the benchmark workload):
-  lambda_max of every level from the library's SplitMix64 start vector (FP64
-  handle 1e-9; the mixed handle's FP32 operator within 1e-4), one
-  V-cycle in FP64 (1e-10) and in mixed precision (2e-4) against the oracle's
-  V-cycle with the same lambda_max, FGMRES iteration counts (+-1).
+* TH P4/P3 on the 64x64 square (167,299 free DoFs, the benchmark workload),
+  with both relaxations bench times (Chebyshev degree 2 on [0.5, 2.0]
+  lambda_max, and degree 1 on [0.1, 1.1] lambda_max): lambda_max of every
+  level from the library's SplitMix64 start vector (FP64 handle 1e-9; the
+  mixed handle's FP32 operator within 1e-4), one V-cycle in FP64 (1e-10) and
+  in mixed precision (2e-4) against the oracle's V-cycle with the same
+  lambda_max, FGMRES iteration counts (+-1).
 * SV P4/P3disc on the Alfeld-refined Delaunay disk and TH P3/P2 on the 16^3
   Kuhn cube: the library's solution, mapped to the oracle's DoFs, has a true
   relative residual <= 2e-8 under the oracle's independently assembled
@@ -46,11 +49,20 @@ def _relerr(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def test_benchmark_workload_th_p4_64x64():
+_ORA64 = {}
+
+
+@pytest.mark.parametrize("relax", ["v22", "v11"])
+def test_benchmark_workload_th_p4_64x64(relax):
+    from bench import RELAX
+    o = RELAX[relax]
     w = W.workload("th_p4_64x64")
-    ora = mg.Hierarchy(w.verts, w.cells, w.n_refine, w.family, w.schedule, lmax=[1.0] * 16)
-    h64 = _lib(w, P.FP64)
-    hmx = _lib(w, P.MIXED)
+    if "ora" not in _ORA64:
+        _ORA64["ora"] = mg.Hierarchy(w.verts, w.cells, w.n_refine, w.family, w.schedule, lmax=[1.0] * 16)
+    ora = _ORA64["ora"]
+    ora.opts = mg.Options(**o)           # the relaxation only enters the cycle, not the setup
+    h64 = _lib(w, P.FP64, **o)
+    hmx = _lib(w, P.MIXED, **o)
     perms = [level_perm(h64, li, L.disc) for li, L in enumerate(ora.levels)]
     lm = h64.info()["lmax"]
     # mixed mode applies M^{-1} K in FP32 inside the FP64-orthogonalised Arnoldi

@@ -44,7 +44,8 @@ def pair(name, precision=P.FP64, **o):
     if key in _cache:
         return _cache[key]
     (v, c), nref, fam, k, sched, bary = CASES[name]
-    opts = mg.Options(nu_p=o.get("nu_p", 1), nu_h=o.get("nu_h", 1), n_V=o.get("n_V", 1))
+    opts = mg.Options(nu_p=o.get("nu_p", 1), nu_h=o.get("nu_h", 1), n_V=o.get("n_V", 1),
+                      cheb_lo=o.get("cheb_lo", 0.1), cheb_hi=o.get("cheb_hi", 1.1))
     # the oracle has one exact patch solve; patch_solver only selects the library's kernel
     ora = mg.Hierarchy(v, c, nref, fam, sched, barycentric=bary, opts=opts)
     lm = [L.lmax for L in ora.levels[:-1]]
@@ -212,10 +213,11 @@ def test_vcycle_matches_oracle(name, precision):
     assert relerr(z, ora.vcycle(r)) < (1e-10 if precision == P.FP64 else 2e-4)
 
 
-@pytest.mark.parametrize("o", [dict(nu_p=2, nu_h=2), dict(nu_p=3, nu_h=1, n_V=2), dict(n_V=2)])
+@pytest.mark.parametrize("o", [dict(nu_p=2, nu_h=2), dict(nu_p=3, nu_h=1, n_V=2), dict(n_V=2),
+                               dict(nu_p=2, nu_h=2, cheb_lo=0.5, cheb_hi=2.0)])
 def test_vcycle_chebyshev_degrees_and_nV(o):
     """Chebyshev degree > 1 and n_V > 1 (the (n_V, nu_p, nu_h) family of
-    Sec. 4.1.1) in both precisions."""
+    Sec. 4.1.1), and another Chebyshev interval, in both precisions."""
     for precision in (P.FP64, P.MIXED):
         h, ora, perms = pair("th_p4_8x8", precision, **o)
         r = np.random.default_rng(5).standard_normal(ora.levels[0].disc.n_free)

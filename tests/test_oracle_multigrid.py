@@ -101,17 +101,19 @@ def test_asm_is_dense_sum_and_partition_of_unity():
     assert np.abs(dense - M).max() < 1e-11 * np.abs(M).max()
 
 
-def test_chebyshev_matches_closed_form():
+@pytest.mark.parametrize("lo,hi", [(0.1, 1.1), (0.5, 2.0)])
+def test_chebyshev_matches_closed_form(lo, hi):
     """On K = diag(lam), M = I: after nu steps from x = 0 the error is
-    T_nu((theta - lam)/delta) / T_nu(theta/delta) times the initial error."""
+    T_nu((theta - lam)/delta) / T_nu(theta/delta) times the initial error,
+    for the interval [lo, hi] * lmax."""
     lam = np.linspace(0.05, 2.0, 40)
     K = sp.diags(lam).tocsr()
     xs = np.random.default_rng(0).normal(size=40)
     b = K @ xs
     lmax = 2.0
     for nu in (1, 2, 3, 5):
-        x = mg.chebyshev(K, lambda r: r, b, np.zeros(40), nu, lmax)
-        a, bb = 0.1 * lmax, 1.1 * lmax
+        x = mg.chebyshev(K, lambda r: r, b, np.zeros(40), nu, lmax, lo, hi)
+        a, bb = lo * lmax, hi * lmax
         th, de = (a + bb) / 2, (bb - a) / 2
         tt = (th - lam) / de
         inside = np.abs(tt) <= 1

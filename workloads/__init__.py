@@ -154,13 +154,19 @@ class Workload:
 
 def workload(name: str) -> Workload:
     """The synthetic problems used by the tests and the benchmark (the five
-    configurations plus th_p3_cube8, a small 3D case for profiling)."""
+    configurations, th_p3_cube8, a small 3D case for profiling, and
+    th_p4_256x256, the 2D Taylor-Hood problem at the paper's scale)."""
     if name == "th_p2_8x8":
         v, c = unit_square_mesh(2)
         return Workload(name, v, c, 2, TH, 2, [2], forcing="mms")
     if name == "th_p4_64x64":
         v, c = unit_square_mesh(8)
         return Workload(name, v, c, 3, TH, 4, [4, 2])
+    if name == "th_p4_256x256":
+        # the 64 x 64 problem two refinements up (about 2.7 M DoFs), the size
+        # of the paper's 2D Taylor-Hood runs
+        v, c = unit_square_mesh(8)
+        return Workload(name, v, c, 5, TH, 4, [4, 2])
     if name == "sv_p4_disk":
         v, c = delaunay_disk_mesh(0)
         return Workload(name, v, c, 2, SV, 4, [4, 2], barycentric=True)
