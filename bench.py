@@ -273,6 +273,16 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
     for _ in range(3):
         hp.vcycle_batched(R, P.BATCH_TF32, out=Z)
     torch.cuda.synchronize(dev)
+    plan0, single0 = hp.batch_plan(0, P.BATCH_TF32)
+    plans = {}
+    for mode_name, mode in (("tf32", P.BATCH_TF32), ("3xtf32", P.BATCH_3XTF32)):
+        hp.vcycle_batched(R, mode, out=Z)
+        plans[mode_name] = []
+        for li in range(npatch_levels):
+            parts, single = hp.batch_plan(li, mode)
+            plans[mode_name].append({"launches": [[pt["lo"], pt["hi"], pt["count"], "tc" if pt["kind"] == 2 else "warp",
+                                                   pt["warps"]] for pt in parts],
+                                     "tuned_us": sum(pt["us"] for pt in parts), "one_per_kind_us": single})
     per = []
     for _ in range(reps):
         k0 = hp.prof_read(P._binding.PROF_PATCH)[0]
@@ -281,7 +291,7 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
         torch.cuda.synchronize(dev)
         k1_ = hp.prof_read(P._binding.PROF_PATCH)[0]
         ms = [hp.prof_read_one(P._binding.PROF_PATCH, i) for i in range(k0, k1_)]
-        per.append(ms[0])                 # the cycle's first patch launch: level 0, pre-smoothing
+        per.append(sum(ms[:len(plan0)]))  # the cycle's first patch launches: level 0, pre-smoothing
     hp.close()
     gemm_ms = sorted(per)[len(per) // 2]
     # algorithmic bytes: FP32 inverses once + Yb written (n_i x m) + X read once
@@ -292,10 +302,7 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
     # th_p3_cube8 at 64 right-hand sides (dram__bytes_read.sum +
     # dram__bytes_write.sum = 439.09 + 47.52 MB against 472.14 MB of
     # algorithmic bytes), scaled to this launch by the algorithmic bytes
-    traffic, traffic_src = None, None
-    if m == 64 and w.name in ("th_p3_cube16", "th_p3_cube8"):
-        traffic = gemm_bytes * (439.092480 + 47.523840) / 472.143392
-        traffic_src = "ncu on th_p3_cube8 (486.6 MB for 472.1 MB algorithmic), scaled by algorithmic bytes"
+    traffic, traffic_src = None, "not captured since the patch list and the bucketed launches were added"
     return {
         "workload": a.batched_workload, "nrhs": m, "n_free": n, "relaxed_levels": npatch_levels,
         "vcycle_ms": {"tf32": tf32_ms, "3xtf32": x3_ms, "single_rhs_mixed_per_rhs": single_ms},
@@ -309,7 +316,9 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
                   "rhs_per_s": 1e3 * m / bsolve_ms, "speedup_vs_single_rhs": ssolve_ms * m / bsolve_ms,
                   "note": f"{m} seeded right-hand sides (pressure parts mean-free), tol {TOL}, TF32 batched "
                           "V-cycle preconditioner, FP64 Krylov; single-RHS = stokes_mg_fgmres on the first"},
-        "roofline": {"kernel": "k_patch_gemm_tc (tcgen05 TF32), level 0, one launch", "bound": "hbm",
+        "patch_gemm_plans": plans,
+        "roofline": {"kernel": f"k_patch_gemm (tcgen05 TF32 and warp MMA), level 0, its {len(plan0)} tuned launches "
+                               f"(one launch per kind: {single0:.1f} us)", "bound": "hbm",
                      "achieved": gemm_gbs, "peak": hbm, "unit": "GB/s", "frac": gemm_gbs / hbm,
                      "bytes_per_launch": gemm_bytes, "us_per_launch": 1e3 * gemm_ms,
                      "tf32_tflops": gemm_flop / (gemm_ms * 1e-3) / 1e12,
@@ -317,6 +326,53 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
         "l2": "flushed (256 MB write) before every timed V-cycle",
     }
+
+
+def buckets_section(a, P, W, dev, stream, flush, m=64):
+    """The batched V-cycle on the Scott-Vogelius disk, whose level-0 patches
+    come in several sizes (92 DoFs at the Alfeld centres, 130-482 at the
+    macro vertices): m right-hand sides, each mode, with the autotuned
+    patch-size buckets and with one launch per level and kind
+    (batch_tune = 0); CUDA events, L2 flushed, median of the timed runs."""
+    import numpy as np
+    import torch
+
+    w = W.workload(a.fbf_workload)
+    out = {"workload": a.fbf_workload, "nrhs": m}
+    hs = {}
+    for tag, tune in (("tuned", 1), ("one_per_kind", 0)):
+        hs[tag] = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                             hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=P.MIXED,
+                             stream=stream.cuda_stream, batch_tune=tune)
+    n = hs["tuned"].info()["n_free"][0]
+    R = torch.tensor(np.random.default_rng(w.seed + 3).standard_normal((m, n)), device=dev)
+    Z = torch.empty_like(R)
+    for mode_name, mode in (("tf32", P.BATCH_TF32), ("3xtf32", P.BATCH_3XTF32)):
+        res = {}
+        for tag, h in hs.items():
+            for _ in range(3):
+                h.vcycle_batched(R, mode, out=Z)
+            ts = []
+            for _ in range(max(5, a.steps)):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.vcycle_batched(R, mode, out=Z)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res[tag + "_ms"] = sorted(ts)[len(ts) // 2]
+        parts, single = hs["tuned"].batch_plan(0, mode)
+        res["level0_launches"] = [[pt["lo"], pt["hi"], pt["count"], "tc" if pt["kind"] == 2 else "warp", pt["warps"]]
+                                  for pt in parts]
+        res["level0_tuned_us"] = sum(pt["us"] for pt in parts)
+        res["level0_one_per_kind_us"] = single
+        res["speedup"] = res["one_per_kind_ms"] / res["tuned_ms"]
+        out[mode_name] = res
+    for h in hs.values():
+        h.close()
+    return out
 
 
 def adjoint_section(a, P, W, dev, stream, flush):
@@ -606,7 +662,9 @@ def main():
     if a.batched_only:
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         hbm_only = json.load(open(peaks_path)).get("hbm_gbs", 6800.0) if os.path.exists(peaks_path) else 6800.0
-        print(json.dumps(batched_section(a, P, W, dev, stream, flush, hbm_only)))
+        res = batched_section(a, P, W, dev, stream, flush, hbm_only)
+        res["buckets"] = buckets_section(a, P, W, dev, stream, flush)
+        print(json.dumps(res))
         return
     if a.single:
         ms, its, rel, st, _ = one_step(P.MIXED if a.precision == "mixed" else P.FP64)
@@ -674,6 +732,10 @@ def main():
                                       if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0)
         except Exception as e:  # noqa: BLE001
             batched = {"error": str(e)[:300]}
+        try:
+            batched["buckets"] = buckets_section(a, P, W, dev, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            batched["buckets"] = {"error": str(e)[:300]}
     fbf_res = None
     if not a.no_fbf:
         try:

@@ -95,6 +95,11 @@ typedef struct {
                                  complement S = sum B_c L^-1 B_c^T inverted by
                                  Gauss-Jordan without pivoting;
                                1 partial-pivot Gauss-Jordan on the whole patch */
+    int batch_tune;         /* batched patch GEMM (stokes_mg_vcycle_batched):
+                               1 (default) on first use at a width and mode, time
+                               patch-size buckets of every level and keep the
+                               fastest split (stokes_batch_plan); 0 one launch
+                               per level and kind */
 } stokes_mg_opts;
 
 #define STOKES_MAX_LEVELS 16
@@ -280,6 +285,22 @@ int stokes_mg_cell_centroids(stokes_mg_t h, int* n_cells, double* xyz);
 #define STOKES_BATCH_TF32   0
 #define STOKES_BATCH_3XTF32 1
 int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, int mode, void* stream);
+
+/* The plan of the batched patch GEMM (the W_i K_i^-1 R_i products of
+ * stokes_mg_vcycle_batched) for one relaxed level and mode at the width of
+ * the last batched call, set on its first use in that mode.  The level's
+ * patches, sorted by size, run as *n_parts launches; launch i covers count[i]
+ * patches of sizes lo[i] .. hi[i] and one kind: 1 warp-level MMA, 2 tcgen05
+ * tensor cores (TF32 patches of more than 64 DoFs).  warps[i] is the warp
+ * kernel's warps per CTA (0: the default for its largest patch).  With
+ * opts.batch_tune the buckets and shapes were chosen by timing (part_us[i],
+ * microseconds per launch, best of 3), and *single_us is the level as one
+ * launch per kind, timed alongside; without it the times are 0.
+ *   kind, warps, count, lo, hi, part_us   host [max_parts] out or NULL.
+ * Errors: EINVAL (no batched call in this mode at the current width yet,
+ * level out of range). */
+int stokes_batch_plan(stokes_mg_t h, int mode, int level, int max_parts, int* n_parts, int* kind, int* warps,
+                      int* count, int* lo, int* hi, double* part_us, double* single_us);
 
 /* Solve -nu Laplace(u) + grad p = f, div u = 0, u = g on the boundary with
  * FGMRES(restart) right-preconditioned by the V-cycle (Sec. 4), stopped when

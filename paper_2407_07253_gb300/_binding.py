@@ -30,7 +30,7 @@ class Opts(ctypes.Structure):
                 ("eig_seed", c_ulonglong), ("cheb_lo", c_double), ("cheb_hi", c_double),
                 ("lmax_override", c_double * 16), ("precision", c_int), ("restart", c_int),
                 ("maxit", c_int), ("use_graph", c_int), ("host_only", c_int), ("prof_mask", c_int),
-                ("patch_solver", c_int)]
+                ("patch_solver", c_int), ("batch_tune", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -80,6 +80,7 @@ def lib():
         "stokes_fbf_apply": (c_int, [P, P, P, P]),
         "stokes_mg_vcycle": (c_int, [P, P, P, c_int, P]),
         "stokes_mg_vcycle_batched": (c_int, [P, P, P, c_int, c_int, P]),
+        "stokes_batch_plan": (c_int, [P, c_int, c_int, c_int, POINTER(c_int), P, P, P, P, P, P, POINTER(c_double)]),
         "stokes_adjoint_solve": (c_int, [P, P, P, c_double, c_double, P, P, P, P, P, P]),
         "stokes_fgmres_batched": (c_int, [P, P, P, c_int, c_int, c_double, P, P, P]),
         "stokes_selftest_bounded_wait": (c_int, [c_longlong, P]),
@@ -270,6 +271,21 @@ class StokesMG:
         if rc != -4 or raise_on_nonconv:
             check(rc)
         return X, its.value, rel
+
+    def batch_plan(self, level, mode=BATCH_TF32):
+        """The batched patch GEMM's launches on a relaxed level
+        (stokes_batch_plan): a list of dicts (kind, warps, count, lo, hi,
+        us), and the one-launch-per-kind time in microseconds."""
+        n = c_int()
+        mx = 64
+        arr = {k: np.zeros(mx, dtype=np.int32) for k in ("kind", "warps", "count", "lo", "hi")}
+        us = np.zeros(mx, dtype=np.float64)
+        single = c_double()
+        check(lib().stokes_batch_plan(self.h, int(mode), int(level), mx, byref(n),
+                                      *[arr[k].ctypes.data_as(c_void_p) for k in ("kind", "warps", "count", "lo", "hi")],
+                                      us.ctypes.data_as(c_void_p), byref(single)))
+        parts = [dict({k: int(arr[k][i]) for k in arr}, us=float(us[i])) for i in range(min(n.value, mx))]
+        return parts, single.value
 
     def fbf_apply(self, r, out=None):
         """z = P^-1 r of Eq. fbf on the Stokes free DoFs (stokes_fbf_apply)."""

@@ -132,13 +132,14 @@ __host__ __device__ inline int rt_ld(int n) {
 // columns 4t and 4t + 1, those of the second for 4t + 2 and 4t + 3.  A and B
 // use the same map, so the products pair up exactly.
 template <int M, int MODE, int ST>
-__global__ void __launch_bounds__(512, 1) k_patch_gemm(int npatch, const int* __restrict__ poff,
+__global__ void __launch_bounds__(512, 1) k_patch_gemm(int npatch, const int* __restrict__ plist,
+                                                    const int* __restrict__ poff,
                                                     const int* __restrict__ pdofs, const long long* __restrict__ ioff,
                                                     const float* __restrict__ inv, const float* __restrict__ X,
                                                     const float* __restrict__ wt, float* __restrict__ Yb) {
     extern __shared__ __align__(128) float smem_pg[];
     constexpr int NT = M / 8, Q = M / 4;
-    const int p = blockIdx.x;
+    const int p = plist ? __ldg(plist + blockIdx.x) : (int)blockIdx.x;     // one CTA per listed patch
     const int s = poff[p], n = poff[p + 1] - s;
     const int n16 = (n + 15) & ~15, ld = (n + 3) & ~3, ldk = rt_ld(n);
     const int nw = blockDim.x >> 5;
@@ -413,7 +414,8 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 template <int M, int ST>
-__global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int maxn, const int* __restrict__ poff,
+__global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int maxn, const int* __restrict__ plist,
+                                                              const int* __restrict__ poff,
                                                               const int* __restrict__ pdofs,
                                                               const CUtensorMap* __restrict__ tmaps,
                                                               const float* __restrict__ X,
@@ -458,7 +460,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
         // ---------------------------------------------------------- TMA ---
         if (lane == 0) {
             int it = 0;
-            for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+            for (int i = blockIdx.x; i < npatch; i += gridDim.x) {
+                const int p = plist ? __ldg(plist + i) : i;
                 const int n = poff[p + 1] - poff[p], tiles = tiles_of(n), nst = (n + KS - 1) / KS;
                 const CUtensorMap* tm = tmaps + p;
                 for (int j = 0; j < nst; ++j, ++it) {
@@ -475,7 +478,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
         if (lane == 0) {
             constexpr uint32_t ID = idesc(NP);
             int it = 0, pc = 0;
-            for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++pc) {
+            for (int i = blockIdx.x; i < npatch; i += gridDim.x, ++pc) {
+                const int p = plist ? __ldg(plist + i) : i;
                 const int n = poff[p + 1] - poff[p], tiles = tiles_of(n), nst = (n + KS - 1) / KS;
                 const int b = pc % nbuf;
                 if (pc >= nbuf && !mbar_wait(acce0 + 8 * b, ((pc / nbuf) - 1) & 1, abort_flag)) goto done;
@@ -512,7 +516,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
         constexpr int NE = (NP / 4 + 7) / 8;
         if (g >= G) goto done;
         int it = 0;
-        for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+        for (int i = blockIdx.x; i < npatch; i += gridDim.x) {
+            const int p = plist ? __ldg(plist + i) : i;
             const int s0 = poff[p], n = poff[p + 1] - s0, nst = (n + KS - 1) / KS;
             for (int j = 0; j < nst; ++j, ++it) {
                 if (it % G != g) continue;
@@ -559,7 +564,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
         // ----------------------------------------------------- epilogue ---
         const int q = warp & 3;            // tensor-memory lanes 32 q .. 32 q + 31
         int pc = 0;
-        for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++pc) {
+        for (int i = blockIdx.x; i < npatch; i += gridDim.x, ++pc) {
+            const int p = plist ? __ldg(plist + i) : i;
             const int s0 = poff[p], n = poff[p + 1] - s0, tiles = tiles_of(n);
             const int b = pc % nbuf;
             float w[8];
@@ -662,43 +668,23 @@ void spmm(int mode, int nr, int m, const int* rp, const int* ci, const float* av
 
 // warps per CTA: enough 16-row blocks per warp for the largest patch, at
 // most 16 warps, spread evenly
-static int patch_gemm_warps(int maxn) {
+int gemm_default_warps(int maxn) {
     const int nrb = (maxn + 15) / 16;
     const int per = (nrb + 15) / 16;
     return nrb <= 0 ? 1 : (nrb + per - 1) / per;
 }
 
-static size_t gemm_smem(int maxn, int m, int stages) {
-    return sizeof(float) * ((size_t)m * rt_ld(maxn) + (size_t)patch_gemm_warps(maxn) * stages * SLOT);
+static size_t gemm_smem(int maxn, int m, int stages, int nw) {
+    return sizeof(float) * ((size_t)m * rt_ld(maxn) + (size_t)nw * stages * SLOT);
 }
 
-
 template <int M, int MODE, int ST>
-static void launch_gemm(int threads, size_t smem, int npatch, const int* poff, const int* pdofs,
+static void launch_gemm(int threads, size_t smem, int nlist, const int* plist, const int* poff, const int* pdofs,
                         const long long* ioff, const float* inv, const float* X, const float* wt, float* Yb,
                         cudaStream_t s) {
     cudaFuncSetAttribute(k_patch_gemm<M, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_patch_gemm<M, MODE, ST>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    k_patch_gemm<M, MODE, ST><<<npatch, threads, smem, s>>>(npatch, poff, pdofs, ioff, inv, X, wt, Yb);
-}
-
-template <int M, int MODE>
-static void launch_gemm_st(int maxn, int npatch, const int* poff, const int* pdofs, const long long* ioff,
-                           const float* inv, const float* X, const float* wt, float* Yb, cudaStream_t s) {
-    static int dev_max = 0;
-    if (dev_max == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    }
-    const int threads = 32 * patch_gemm_warps(maxn);
-    if (gemm_smem(maxn, M, 8) <= (size_t)dev_max)
-        launch_gemm<M, MODE, 8>(threads, gemm_smem(maxn, M, 8), npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
-    else if (gemm_smem(maxn, M, 6) <= (size_t)dev_max)
-        launch_gemm<M, MODE, 6>(threads, gemm_smem(maxn, M, 6), npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
-    else
-        launch_gemm<M, MODE, MIN_STAGES>(threads, gemm_smem(maxn, M, MIN_STAGES), npatch, poff, pdofs, ioff, inv, X,
-                                         wt, Yb, s);
+    k_patch_gemm<M, MODE, ST><<<nlist, threads, smem, s>>>(nlist, plist, poff, pdofs, ioff, inv, X, wt, Yb);
 }
 
 static int device_attr(cudaDeviceAttr attr) {
@@ -708,9 +694,29 @@ static int device_attr(cudaDeviceAttr attr) {
     return v;
 }
 
-// Levels whose patches all have <= TC_MIN_N DoFs fill under half of a
-// 128-row MMA tile; the warp-level kernel is faster there.
+// nw warps per CTA (0: gemm_default_warps(maxn)); as many cp.async stages
+// of 8, 6 or MIN_STAGES as fit the shared memory
+template <int M, int MODE>
+static void launch_gemm_st(int maxn, int nw, int nlist, const int* plist, const int* poff, const int* pdofs,
+                           const long long* ioff, const float* inv, const float* X, const float* wt, float* Yb,
+                           cudaStream_t s) {
+    const size_t dev_max = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin);
+    if (nw <= 0) nw = gemm_default_warps(maxn);
+    const int threads = 32 * nw;
+    if (gemm_smem(maxn, M, 8, nw) <= dev_max)
+        launch_gemm<M, MODE, 8>(threads, gemm_smem(maxn, M, 8, nw), nlist, plist, poff, pdofs, ioff, inv, X, wt, Yb, s);
+    else if (gemm_smem(maxn, M, 6, nw) <= dev_max)
+        launch_gemm<M, MODE, 6>(threads, gemm_smem(maxn, M, 6, nw), nlist, plist, poff, pdofs, ioff, inv, X, wt, Yb, s);
+    else
+        launch_gemm<M, MODE, MIN_STAGES>(threads, gemm_smem(maxn, M, MIN_STAGES, nw), nlist, plist, poff, pdofs, ioff,
+                                         inv, X, wt, Yb, s);
+}
+
+// Patches of <= TC_MIN_N DoFs fill under half of a 128-row MMA tile; the
+// warp-level kernel is faster there.
 constexpr int TC_MIN_N = 64;
+
+int gemm_kind(int mode, int n) { return (mode == GEMM_TF32 && n > TC_MIN_N) ? GEMM_KIND_TC : GEMM_KIND_WARP; }
 
 // tensor-core TF32 path: a persistent grid of one CTA per SM (the dynamic
 // shared memory is at least half an SM's, so no two CTAs share an SM and its
@@ -734,20 +740,20 @@ static TcPlan tc_plan(int maxn, int m, int npatch) {
 }
 
 template <int M, int ST>
-static void launch_tc(const TcPlan& pl, int npatch, int maxn, const int* poff, const int* pdofs, const void* tmaps,
-                      const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
+static void launch_tc(const TcPlan& pl, int nlist, const int* plist, int maxn, const int* poff, const int* pdofs,
+                      const void* tmaps, const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
     cudaFuncSetAttribute(tc::k_patch_gemm_tc<M, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     tc::k_patch_gemm_tc<M, ST><<<pl.grid, tc::THREADS, pl.smem, s>>>(
-        npatch, maxn, poff, pdofs, reinterpret_cast<const CUtensorMap*>(tmaps), X, wt, Yb, status);
+        nlist, maxn, plist, poff, pdofs, reinterpret_cast<const CUtensorMap*>(tmaps), X, wt, Yb, status);
 }
 
 template <int M>
-static void launch_tc_st(int npatch, int maxn, const int* poff, const int* pdofs, const void* tmaps, const float* X,
-                         const float* wt, float* Yb, int* status, cudaStream_t s) {
-    const TcPlan pl = tc_plan(maxn, M, npatch);
+static void launch_tc_st(int nlist, const int* plist, int maxn, const int* poff, const int* pdofs, const void* tmaps,
+                         const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
+    const TcPlan pl = tc_plan(maxn, M, nlist);
     switch (pl.stages) {
 #define SBAT_TC_CASE(S) \
-    case S: launch_tc<M, S>(pl, npatch, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s); break;
+    case S: launch_tc<M, S>(pl, nlist, plist, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s); break;
         SBAT_TC_CASE(2) SBAT_TC_CASE(3) SBAT_TC_CASE(4) SBAT_TC_CASE(5) SBAT_TC_CASE(6) SBAT_TC_CASE(7)
         SBAT_TC_CASE(8) SBAT_TC_CASE(9) SBAT_TC_CASE(10) SBAT_TC_CASE(11) SBAT_TC_CASE(12)
 #undef SBAT_TC_CASE
@@ -756,17 +762,24 @@ static void launch_tc_st(int npatch, int maxn, const int* poff, const int* pdofs
 }
 
 template <int M>
-static void patch_gemm_m(int mode, int npatch, int maxn, const int* poff, const int* pdofs, const long long* ioff,
-                         const float* inv, const void* tmaps, const float* X, const float* wt, float* Yb, int* status,
-                         cudaStream_t s) {
-    if (mode == GEMM_3XTF32) launch_gemm_st<M, GEMM_3XTF32>(maxn, npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
-    else if (maxn <= TC_MIN_N) launch_gemm_st<M, GEMM_TF32>(maxn, npatch, poff, pdofs, ioff, inv, X, wt, Yb, s);
-    else launch_tc_st<M>(npatch, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s);
+static void patch_gemm_m(int mode, int kind, int nw, int nlist, const int* plist, int maxn, const int* poff,
+                         const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const float* X,
+                         const float* wt, float* Yb, int* status, cudaStream_t s) {
+    if (kind == GEMM_KIND_AUTO) kind = gemm_kind(mode, maxn);
+    if (kind == GEMM_KIND_TC)
+        launch_tc_st<M>(nlist, plist, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s);
+    else if (mode == GEMM_3XTF32)
+        launch_gemm_st<M, GEMM_3XTF32>(maxn, nw, nlist, plist, poff, pdofs, ioff, inv, X, wt, Yb, s);
+    else
+        launch_gemm_st<M, GEMM_TF32>(maxn, nw, nlist, plist, poff, pdofs, ioff, inv, X, wt, Yb, s);
 }
 
+// the largest patch decides: a smaller patch of either kind needs no more
+// shared or tensor memory than the largest one of that kind
 const char* patch_gemm_check(int mode, int maxn, int m) {
-    if (mode == GEMM_3XTF32 || maxn <= TC_MIN_N)
-        return gemm_smem(maxn, m, MIN_STAGES) <= (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin)
+    if (gemm_kind(mode, maxn) == GEMM_KIND_WARP)
+        return gemm_smem(maxn, m, MIN_STAGES, gemm_default_warps(maxn)) <=
+                       (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin)
                    ? nullptr
                    : "patch too large for the shared memory of the warp-MMA patch GEMM at this width";
     if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, tc::np_of(m)) > 512)
@@ -816,14 +829,16 @@ void build_tmaps(int npatch, const int* poff_d, const long long* ioff_d, const f
         throw std::runtime_error("tensor maps could not be uploaded");
 }
 
-void patch_gemm(int mode, int npatch, int maxn, int m, const int* poff, const int* pdofs, const long long* ioff,
-                const float* inv, const void* tmaps, const float* X, const float* wt, float* Yb, int* status,
-                cudaStream_t s) {
+void patch_gemm(int mode, int kind, int nw, int nlist, const int* plist, int maxn, int m, const int* poff,
+                const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const float* X,
+                const float* wt, float* Yb, int* status, cudaStream_t s) {
+    if (nlist <= 0) return;
     switch (m) {
-        case 8: patch_gemm_m<8>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
-        case 16: patch_gemm_m<16>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
-        case 32: patch_gemm_m<32>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
-        default: patch_gemm_m<64>(mode, npatch, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
+#define SBAT_M(MM) \
+    case MM: patch_gemm_m<MM>(mode, kind, nw, nlist, plist, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
+        SBAT_M(8) SBAT_M(16) SBAT_M(32)
+#undef SBAT_M
+        default: patch_gemm_m<64>(mode, kind, nw, nlist, plist, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s);
     }
 }
 

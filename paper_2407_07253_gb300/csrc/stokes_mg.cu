@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -257,8 +258,15 @@ struct stokes_mg {
     long long graph_launches[2] = {0, 0};
     // batched V-cycle: interleaved work vectors of width bm per level, and
     // one captured graph per patch-GEMM mode for that width
-    struct BatchLevel { float *b = nullptr, *e = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *u = nullptr,
-                              *Yb = nullptr; };
+    // one launch of the batched patch GEMM: `count` patches of one kind from
+    // the level's size-sorted patch list, starting at `off` (sizes lo .. hi)
+    struct GemmPart { int kind = 0, nw = 0, off = 0, count = 0, lo = 0, hi = 0; double us = 0; };
+    struct BatchLevel {
+        float *b = nullptr, *e = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *u = nullptr, *Yb = nullptr;
+        std::vector<GemmPart> plan[2];   // per mode, empty until the first batched use at this width
+        double single_us[2] = {0, 0};    // the level as one launch per kind (the untuned plan), timed alongside
+    };
+    std::vector<int*> bpsort;            // per relaxed level: patch indices sorted by size (device)
     int bm = 0;
     std::vector<BatchLevel> bl;
     int *bstat_h = nullptr, *bstat_d = nullptr;   // host-mapped timeout flag of the tensor-core patch GEMM
@@ -699,10 +707,12 @@ void b_spmm(stokes_mg* h, int kind, const DevCSR& A, int mode, int m, const floa
 void b_asm(stokes_mg* h, int li, int gm, int m, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
     DevLevel& l = h->L[li];
     BatchLevel& B = h->bl[li];
-    launch(h, PK_PATCH, s, [&] {
-        sbat::patch_gemm(gm, l.npatch, l.maxn, m, l.poff, l.pdofs, l.ioff32, l.inv32, h->tmaps[li], r, l.wt32, B.Yb,
-                         h->bstat_d, s);
-    });
+    if (B.plan[gm].empty()) throw StokesError(STOKES_ECUDA, "internal: no batched patch GEMM plan for this level");
+    for (const auto& pt : B.plan[gm])
+        launch(h, PK_PATCH, s, [&] {
+            sbat::patch_gemm(gm, pt.kind, pt.nw, pt.count, h->bpsort[li] + pt.off, pt.hi, m, l.poff, l.pdofs, l.ioff32,
+                             l.inv32, h->tmaps[li], r, l.wt32, B.Yb, h->bstat_d, s);
+        });
     launch(h, PK_PULL, s, [&] { sbat::pull_scatter(l.n, m, l.soff, l.sidx, B.Yb, (float)alpha, (float)beta, out, s); });
 }
 
@@ -816,6 +826,166 @@ void ensure_batch(stokes_mg* h, int m) {
         h->bgraph[i] = nullptr;
     }
     h->bm = m;
+}
+
+// Autotuner of the batched patch GEMM (one level, mode gm, width m).  The
+// patches, sorted by size, are split into buckets of one kind (gemm_kind:
+// the tensor cores for TF32 patches of more than 64 DoFs, the warp-level MMA
+// otherwise) and one size class (128-row tiles for the tensor cores, 32-row
+// groups for the warp kernel).  Each bucket's launch shape follows from its
+// largest patch (pipeline stages and shared memory; for the warp kernel also
+// the warps per CTA, of which the default and half are timed).  Adjacent
+// buckets of one kind are then merged, left to right, while the merged launch
+// is no slower than the two it replaces.  Every choice is timed on the
+// level's own inverses (CUDA events, best of 3 after a warm-up).  A patch's
+// arithmetic depends only on its kind, so the plan changes the time, never
+// the result.
+double time_gemm(stokes_mg* h, int li, int gm, int m, const stokes_mg::GemmPart& pt, const int* plist,
+                 const float* X, cudaStream_t s) {
+    DevLevel& l = h->L[li];
+    BatchLevel& B = h->bl[li];
+    auto run = [&] {
+        sbat::patch_gemm(gm, pt.kind, pt.nw, pt.count, plist ? plist + pt.off : nullptr, pt.hi, m, l.poff, l.pdofs,
+                         l.ioff32, l.inv32, h->tmaps[li], X, l.wt32, B.Yb, h->bstat_d, s);
+        CK(cudaGetLastError());
+    };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    run();
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        CK(cudaEventRecord(e0, s));
+        run();
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+    }
+    CK(cudaEventDestroy(e0));
+    CK(cudaEventDestroy(e1));
+    return 1e3 * best;
+}
+
+void tune_level(stokes_mg* h, int li, int gm, int m, cudaStream_t s) {
+    using GemmPart = stokes_mg::GemmPart;
+    DevLevel& l = h->L[li];
+    BatchLevel& B = h->bl[li];
+    const std::vector<int>& off = h->H.levels[li].patch_off;
+    const int np = l.npatch;
+    std::vector<int> idx(np), ns(np);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return off[a + 1] - off[a] < off[b + 1] - off[b]; });
+    for (int i = 0; i < np; ++i) ns[i] = off[idx[i] + 1] - off[idx[i]];
+    if ((int)h->bpsort.size() <= li) h->bpsort.resize(li + 1, nullptr);
+    if (!h->bpsort[li]) {
+        h->bpsort[li] = halloc<int>(h, np);
+        CK(cudaStreamSynchronize(h->s_up));
+        CK(cudaMemcpyAsync(h->bpsort[li], idx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    }
+    const int* plist = h->bpsort[li];
+    float* X = B.u;                                       // zero input of the timing runs
+    CK(cudaMemsetAsync(X, 0, sizeof(float) * (size_t)l.n * m, s));
+    auto klass = [&](int n) {
+        return sbat::gemm_kind(gm, n) == sbat::GEMM_KIND_TC ? 1000 + (n + 127) / 128 : (n + 31) / 32;
+    };
+    std::vector<GemmPart> parts;
+    for (int i = 0; i < np;) {
+        int j = i;
+        while (j < np && klass(ns[j]) == klass(ns[i])) ++j;
+        GemmPart pt;
+        pt.kind = sbat::gemm_kind(gm, ns[i]);
+        pt.off = i;
+        pt.count = j - i;
+        pt.lo = ns[i];
+        pt.hi = ns[j - 1];
+        parts.push_back(pt);
+        i = j;
+    }
+    auto best_shape = [&](GemmPart& pt) {
+        pt.nw = 0;
+        pt.us = time_gemm(h, li, gm, m, pt, plist, X, s);
+        if (pt.kind == sbat::GEMM_KIND_WARP) {
+            const int nw0 = sbat::gemm_default_warps(pt.hi);
+            if (nw0 > 1) {
+                GemmPart half = pt;
+                half.nw = (nw0 + 1) / 2;
+                half.us = time_gemm(h, li, gm, m, half, plist, X, s);
+                if (half.us < pt.us) pt = half;
+            }
+        }
+    };
+    for (auto& pt : parts) best_shape(pt);
+    for (size_t i = 0; i + 1 < parts.size();) {
+        if (parts[i].kind != parts[i + 1].kind) { ++i; continue; }
+        GemmPart mg = parts[i];
+        mg.count += parts[i + 1].count;
+        mg.hi = parts[i + 1].hi;
+        best_shape(mg);
+        if (mg.us <= parts[i].us + parts[i + 1].us) {
+            parts[i] = mg;
+            parts.erase(parts.begin() + (long)i + 1);
+        } else {
+            ++i;
+        }
+    }
+    // reference: one launch per kind over the whole level, default shape
+    double single = 0;
+    for (int kind : {sbat::GEMM_KIND_WARP, sbat::GEMM_KIND_TC}) {
+        GemmPart all;
+        all.kind = kind;
+        for (const auto& pt : parts)
+            if (pt.kind == kind) {
+                if (all.count == 0) { all.off = pt.off; all.lo = pt.lo; }
+                all.count += pt.count;
+                all.hi = pt.hi;
+            }
+        if (all.count) single += time_gemm(h, li, gm, m, all, plist, X, s);
+    }
+    B.single_us[gm] = single;
+    B.plan[gm] = parts;
+}
+
+// the plan of every relaxed level for mode gm at the current width: tuned,
+// or (opts.batch_tune = 0) one launch per kind in size order
+void ensure_plan(stokes_mg* h, int gm, int m, cudaStream_t s) {
+    using GemmPart = stokes_mg::GemmPart;
+    for (size_t li = 0; li + 1 < h->L.size(); ++li) {
+        BatchLevel& B = h->bl[li];
+        if (!B.plan[gm].empty()) continue;
+        if (h->opts.batch_tune) {
+            tune_level(h, (int)li, gm, m, s);
+            continue;
+        }
+        const std::vector<int>& off = h->H.levels[li].patch_off;
+        const int np = h->L[li].npatch;
+        std::vector<int> idx(np);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return off[a + 1] - off[a] < off[b + 1] - off[b]; });
+        if ((int)h->bpsort.size() <= (int)li) h->bpsort.resize(li + 1, nullptr);
+        if (!h->bpsort[li]) {
+            h->bpsort[li] = halloc<int>(h, np);
+            CK(cudaStreamSynchronize(h->s_up));
+            CK(cudaMemcpyAsync(h->bpsort[li], idx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+        }
+        std::vector<GemmPart> parts;
+        for (int i = 0; i < np;) {
+            const int n0 = off[idx[i] + 1] - off[idx[i]], kind = sbat::gemm_kind(gm, n0);
+            int j = i;
+            while (j < np && sbat::gemm_kind(gm, off[idx[j] + 1] - off[idx[j]]) == kind) ++j;
+            GemmPart pt;
+            pt.kind = kind;
+            pt.off = i;
+            pt.count = j - i;
+            pt.lo = n0;
+            pt.hi = off[idx[j - 1] + 1] - off[idx[j - 1]];
+            parts.push_back(pt);
+            i = j;
+        }
+        B.plan[gm] = parts;
+    }
+    CK(cudaStreamSynchronize(s));
 }
 
 void capture_batched(stokes_mg* h, int gm, int m) {
@@ -1781,6 +1951,7 @@ void stokes_mg_default_opts(stokes_mg_opts* o) {
     o->restart = 30;
     o->maxit = 1000;
     o->use_graph = 1;
+    o->batch_tune = 1;
 }
 
 namespace {
@@ -2121,6 +2292,7 @@ namespace {
 // batched V-cycle of an interleaved FP64 batch (width h->bm): Z = B_MG V
 void batched_precond(stokes_mg* h, int mode, const double* V, double* Z, cudaStream_t s) {
     const int m = h->bm;
+    ensure_plan(h, mode, m, s);
     const long long nm = (long long)h->L[0].n * m;
     launch(h, -1, s, [&] { sbat::to32(nm, V, h->bl[0].b, s); });
     const bool any_prof = h->prof[PK_PATCH].on || h->prof[PK_SPMV].on || h->prof[PK_PULL].on || h->prof[PK_TRANSFER].on;
@@ -2376,6 +2548,28 @@ int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int
     });
 }
 
+int stokes_batch_plan(stokes_mg_t h, int mode, int level, int max_parts, int* n_parts, int* kind, int* warps,
+                      int* count, int* lo, int* hi, double* part_us, double* single_us) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(h && n_parts && (mode == STOKES_BATCH_TF32 || mode == STOKES_BATCH_3XTF32), "invalid argument");
+        require(level >= 0 && level + 1 < (int)h->L.size() && level < (int)h->bl.size(), "no such relaxed level");
+        const auto& plan = h->bl[level].plan[mode];
+        require(!plan.empty(), "no batched call in this mode at the current width yet");
+        *n_parts = (int)plan.size();
+        for (int i = 0; i < (int)plan.size() && i < max_parts; ++i) {
+            if (kind) kind[i] = plan[i].kind;
+            if (warps) warps[i] = plan[i].nw;
+            if (count) count[i] = plan[i].count;
+            if (lo) lo[i] = plan[i].lo;
+            if (hi) hi[i] = plan[i].hi;
+            if (part_us) part_us[i] = plan[i].us;
+        }
+        if (single_us) *single_us = h->bl[level].single_us[mode];
+        return STOKES_OK;
+    });
+}
+
 int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, int nrhs, int mode, void* stream) {
     g_last_error.clear();
     return guarded([&] {
@@ -2395,6 +2589,7 @@ int stokes_mg_vcycle_batched(stokes_mg_t h, const double* r_dev, double* z_dev, 
                                             "its mbarrier; its output was not written");
         }
         ensure_batch(h, m);
+        ensure_plan(h, mode, m, s);
         const int n = h->L[0].n;
         launch(h, -1, s, [&] { sbat::to_interleaved(n, nrhs, m, r_dev, h->bl[0].b, s); });
         const bool any_prof = h->prof[PK_PATCH].on || h->prof[PK_SPMV].on || h->prof[PK_PULL].on ||

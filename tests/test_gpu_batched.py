@@ -145,6 +145,43 @@ def test_batched_fgmres_tf32_and_widths():
             assert res <= 2e-9, (nrhs, q, res)
 
 
+@pytest.mark.parametrize("name", ["sv_p3_alfeld", "th3d_p3", "sv_p4_disk"])
+def test_batched_plan_buckets_cover_every_patch_once(name):
+    """The autotuned plan of every relaxed level: its launches cover the
+    level's patches once, in size order, each launch of one kind (tensor
+    cores exactly for the TF32 patches of more than 64 DoFs)."""
+    h, ora, perms = pair(name, P.MIXED)
+    _, R = _batch(ora, perms[0], 8, 2)
+    for mode in (P.BATCH_TF32, P.BATCH_3XTF32):
+        h.vcycle_batched(R, mode)
+        for li in range(h.info()["n_levels"] - 1):
+            off, _ = h.patches(li)
+            sizes = np.sort(np.diff(off))
+            parts, single = h.batch_plan(li, mode)
+            assert sum(pt["count"] for pt in parts) == len(sizes) and single > 0
+            i = 0
+            for pt in parts:
+                seg = sizes[i:i + pt["count"]]
+                assert seg[0] == pt["lo"] and seg[-1] == pt["hi"], (li, pt)
+                tc = mode == P.BATCH_TF32 and pt["lo"] > 64
+                assert pt["kind"] == (2 if tc else 1) and (tc or pt["hi"] <= 64 or mode == P.BATCH_3XTF32), (li, pt)
+                assert pt["us"] > 0
+                i += pt["count"]
+
+
+@pytest.mark.parametrize("name", ["sv_p4_disk", "th3d_p3"])
+def test_batched_tuned_plan_gives_the_untuned_result(name):
+    """A patch's arithmetic depends only on its kind, so the tuned buckets and
+    launch shapes give the result of one launch per kind bit for bit."""
+    h, ora, perms = pair(name, P.MIXED)
+    hu, _, _ = pair(name, P.MIXED, batch_tune=0)
+    _, R = _batch(ora, perms[0], 16, 7)
+    for mode in (P.BATCH_TF32, P.BATCH_3XTF32):
+        assert torch.equal(h.vcycle_batched(R, mode), hu.vcycle_batched(R, mode))
+        parts, single = hu.batch_plan(0, mode)
+        assert single == 0.0 and len(parts) <= 2
+
+
 def test_bounded_mbarrier_wait_gives_up_and_returns():
     """The tensor-core kernel's mbarrier waits are bounded: a wait on a barrier
     that nothing arrives on runs out after the given number of polls, sets
