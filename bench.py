@@ -26,10 +26,12 @@ TOL = 1e-8
 # relaxation of the main step.  Sec. 4 reports, per run, the fastest of the
 # (n_V, nu_p, nu_h) combinations it explored; on the TH P4 problems here that
 # is Chebyshev of degree 2 on [0.5, 2.0] lambda_max around one Vanka-star ASM
-# sweep, pre and post (10 / 12 / 13 iterations on 64^2 / 128^2 / 256^2, where
-# degree 1 on [0.1, 1.1] lambda_max takes 20 / 30 / 81).  "v11" is that
-# degree-1 default of the library, kept as a comparison.
-RELAX = {"v22": dict(nu_p=2, nu_h=2, cheb_lo=0.5, cheb_hi=2.0), "v11": dict(nu_p=1, nu_h=1, cheb_lo=0.1, cheb_hi=1.1)}
+# sweep, pre and post, with lambda_max from 8 Arnoldi steps (9 / 11 / 12
+# iterations on 64^2 / 128^2 / 256^2, where degree 1 on [0.1, 1.1] lambda_max
+# from 15 steps takes 20 / 30 / 81).  "v11" is that degree-1 default of the
+# library, kept as a comparison.
+RELAX = {"v22": dict(nu_p=2, nu_h=2, cheb_lo=0.5, cheb_hi=2.0, eig_steps=8),
+         "v11": dict(nu_p=1, nu_h=1, cheb_lo=0.1, cheb_hi=1.1, eig_steps=15)}
 
 
 def parse():
@@ -50,6 +52,8 @@ def parse():
     ap.add_argument("--batched-workload", default="th_p3_cube16",
                     help="workload of the batched multi-RHS V-cycle measurement")
     ap.add_argument("--nrhs", type=int, default=64)
+    ap.add_argument("--batch-tune", type=int, default=1, choices=[0, 1],
+                    help="batched section: 1 autotuned patch-size buckets, 0 one launch per level and kind")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched V-cycle measurement (profiling driver)")
@@ -119,7 +123,8 @@ def run_oracle(name, relax, timeout=900):
 def relax_text(name):
     r = RELAX[name]
     return (f"V({r['nu_p']},{r['nu_h']}): Chebyshev degree {r['nu_p']} (p-levels) / {r['nu_h']} (h-levels) on "
-            f"[{r['cheb_lo']}, {r['cheb_hi']}] x lambda_max around one Vanka-star ASM sweep, pre and post")
+            f"[{r['cheb_lo']}, {r['cheb_hi']}] x lambda_max ({r['eig_steps']} Arnoldi steps) around one "
+            "Vanka-star ASM sweep, pre and post")
 
 
 def reference_arm(a):
@@ -206,7 +211,7 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
     def make(prof_mask=0):
         return P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
                           hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, precision=P.MIXED,
-                          stream=stream.cuda_stream, prof_mask=prof_mask)
+                          stream=stream.cuda_stream, prof_mask=prof_mask, batch_tune=a.batch_tune)
 
     h = make()
     n = h.info()["n_free"][0]
@@ -302,7 +307,15 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
     # th_p3_cube8 at 64 right-hand sides (dram__bytes_read.sum +
     # dram__bytes_write.sum = 439.09 + 47.52 MB against 472.14 MB of
     # algorithmic bytes), scaled to this launch by the algorithmic bytes
-    traffic, traffic_src = None, "not captured since the patch list and the bucketed launches were added"
+    # DRAM traffic per launch: one ncu capture of the tensor-core launch of
+    # level 0 on th_p3_cube8 at 64 right-hand sides (batch_tune 0: the 681
+    # patches of more than 64 DoFs in one launch; dram__bytes_read.sum +
+    # dram__bytes_write.sum = 440.98 + 43.14 MB against 471.24 MB of
+    # algorithmic bytes), scaled to this level by the algorithmic bytes
+    traffic, traffic_src = None, None
+    if m == 64 and w.name in ("th_p3_cube16", "th_p3_cube8"):
+        traffic = gemm_bytes * (440.978176 + 43.141888) / 471.237536
+        traffic_src = "ncu on th_p3_cube8 (484.1 MB for 471.2 MB algorithmic), scaled by algorithmic bytes"
     return {
         "workload": a.batched_workload, "nrhs": m, "n_free": n, "relaxed_levels": npatch_levels,
         "vcycle_ms": {"tf32": tf32_ms, "3xtf32": x3_ms, "single_rhs_mixed_per_rhs": single_ms},
