@@ -105,19 +105,54 @@ D = h.levels[0].disc
 f = W.nodal_forcing(D.V.n, D.d, w.seed)
 full, its, hist, b, x = mg.solve(h, f, None, tol={tol!r})
 t2 = time.perf_counter()
+if {save!r}:
+    np.savez({save!r}, full=full, vx=D.V.coords, px=D.Q.coords)
 print(json.dumps(dict(setup_s=t1 - t0, solve_s=t2 - t1, its=its, relres=hist[-1])))
 """
 
 
-def run_oracle(name, relax, timeout=900):
+def run_oracle(name, relax, timeout=900, save=None):
     """The FP64 CPU oracle, as it stands, in a fresh single-threaded process,
-    with the relaxation parameters of the GPU step."""
+    with the relaxation parameters of the GPU step (its solution and node
+    coordinates written to `save`, an .npz path, when given; outside the
+    timed part)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL, relax=RELAX[relax])
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL, relax=RELAX[relax], save=save)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=timeout, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_error(P, w, npz, sol_mixed, sol_fp64):
+    """Relative max-norm differences between the GPU solutions (mixed and
+    FP64, solved to TOL) and the oracle's (solved to TOL in FP64), the nodes
+    matched by their coordinates; pressures are both zero-mean."""
+    import numpy as np
+
+    z = np.load(npz)
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
+                       hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
+    vx, px, _ = probe.nodes()
+    probe.close()
+
+    def perm(lib_xyz, ora_xyz):
+        key = lambda x: [tuple(r) for r in np.round(np.asarray(x) * 1e9).astype(np.int64).tolist()]  # noqa: E731
+        where = {k: i for i, k in enumerate(key(lib_xyz))}
+        return np.array([where[k] for k in key(ora_xyz)])
+
+    pv, pq = perm(vx, z["vx"]), perm(px, z["px"])
+    d, nV = w.verts.shape[1], len(z["vx"])
+    u_o = z["full"][:d * nV].reshape(d, nV)
+    p_o = z["full"][d * nV:]
+    out = {}
+    for tag, (u, p) in (("mixed", sol_mixed), ("fp64", sol_fp64)):
+        U = u.reshape(d, -1)[:, pv]
+        out[tag] = {"u_rel": float(np.abs(U - u_o).max() / np.abs(u_o).max()),
+                    "p_rel": float(np.abs(p[pq] - p_o).max() / np.abs(p_o).max())}
+    out["note"] = (f"max-norm differences, relative to the oracle's max; every solve stops at {TOL} relative "
+                   "residual, so they differ by about that tolerance times the condition number")
+    return out
 
 
 def relax_text(name):
@@ -707,12 +742,14 @@ def main():
         wall = time.perf_counter() - t0
     ms_local = sum(times) / len(times)
     ms_max = max_over_ranks(ms_local, pg, dev)
+    sol_mixed = (u_dev.cpu().numpy().copy(), p_dev.cpu().numpy().copy())
     # e2e through host buffers (pinned H2D of f, D2H of u and p inside the step)
     one_step(P.MIXED, e2e=True)          # untimed: first pinned-copy path
     e2e_times = [one_step(P.MIXED, e2e=True)[0] for _ in range(max(3, a.steps))]
     # FP64 V-cycle for the mixed-vs-FP64 comparison
     one_step(P.FP64)                     # untimed: FP64 warm-up
     f64 = [one_step(P.FP64) for _ in range(max(3, a.steps))]
+    sol_fp64 = (u_dev.cpu().numpy().copy(), p_dev.cpu().numpy().copy())
     # the other relaxation, same step otherwise
     other = "v11" if a.relaxation == "v22" else "v22"
     one_step(P.MIXED, relax=other)
@@ -865,7 +902,15 @@ def main():
     line["clocks"] = clk.summary()
     if not a.no_cpu_baseline and world == 1:
         try:
-            o = run_oracle(a.workload, a.relaxation)
+            npz = os.path.join(tempfile.gettempdir(), f"stokes_bench_oracle_{os.getpid()}.npz")
+            o = run_oracle(a.workload, a.relaxation, save=npz)
+            try:
+                line["oracle_error"] = oracle_error(P, w, npz, sol_mixed, sol_fp64)
+            except Exception as e:  # noqa: BLE001
+                line["oracle_error"] = {"error": str(e)[:200]}
+            finally:
+                if os.path.exists(npz):
+                    os.remove(npz)
             line["cpu_baseline"] = {"value": 1e3 * (o["setup_s"] + o["solve_s"]), "unit": "ms", "cores": 1,
                                     "kind": "oracle",
                                     "sample": f"one full setup + FGMRES solve of {a.workload} to {TOL}, "
