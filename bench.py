@@ -124,10 +124,14 @@ def run_oracle(name, relax, timeout=900, save=None):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_error(P, w, npz, sol_mixed, sol_fp64):
+def oracle_error(P, W, w, npz, solve):
     """Relative max-norm differences between the GPU solutions (mixed and
-    FP64, solved to TOL) and the oracle's (solved to TOL in FP64), the nodes
-    matched by their coordinates; pressures are both zero-mean."""
+    FP64, solved to TOL) and the oracle's (solved to TOL in FP64) for the
+    oracle's forcing: the seeded nodal values in the oracle's node order,
+    moved to the library's nodes by their coordinates (an input permutation;
+    the timed steps draw the same generator in the library's order).
+    solve(precision, f) returns (u, p) of the library as numpy arrays;
+    pressures are both zero-mean."""
     import numpy as np
 
     z = np.load(npz)
@@ -145,8 +149,11 @@ def oracle_error(P, w, npz, sol_mixed, sol_fp64):
     d, nV = w.verts.shape[1], len(z["vx"])
     u_o = z["full"][:d * nV].reshape(d, nV)
     p_o = z["full"][d * nV:]
+    f_lib = np.empty((d, nV))
+    f_lib[:, pv] = W.nodal_forcing(nV, d, w.seed)
     out = {}
-    for tag, (u, p) in (("mixed", sol_mixed), ("fp64", sol_fp64)):
+    for tag, prec in (("mixed", P.MIXED), ("fp64", P.FP64)):
+        u, p = solve(prec, f_lib)
         U = u.reshape(d, -1)[:, pv]
         out[tag] = {"u_rel": float(np.abs(U - u_o).max() / np.abs(u_o).max()),
                     "p_rel": float(np.abs(p[pq] - p_o).max() / np.abs(p_o).max())}
@@ -742,14 +749,12 @@ def main():
         wall = time.perf_counter() - t0
     ms_local = sum(times) / len(times)
     ms_max = max_over_ranks(ms_local, pg, dev)
-    sol_mixed = (u_dev.cpu().numpy().copy(), p_dev.cpu().numpy().copy())
     # e2e through host buffers (pinned H2D of f, D2H of u and p inside the step)
     one_step(P.MIXED, e2e=True)          # untimed: first pinned-copy path
     e2e_times = [one_step(P.MIXED, e2e=True)[0] for _ in range(max(3, a.steps))]
     # FP64 V-cycle for the mixed-vs-FP64 comparison
     one_step(P.FP64)                     # untimed: FP64 warm-up
     f64 = [one_step(P.FP64) for _ in range(max(3, a.steps))]
-    sol_fp64 = (u_dev.cpu().numpy().copy(), p_dev.cpu().numpy().copy())
     # the other relaxation, same step otherwise
     other = "v11" if a.relaxation == "v22" else "v22"
     one_step(P.MIXED, relax=other)
@@ -905,7 +910,13 @@ def main():
             npz = os.path.join(tempfile.gettempdir(), f"stokes_bench_oracle_{os.getpid()}.npz")
             o = run_oracle(a.workload, a.relaxation, save=npz)
             try:
-                line["oracle_error"] = oracle_error(P, w, npz, sol_mixed, sol_fp64)
+                def solve_lib(prec, f_np):
+                    hh = make(prec)
+                    uu, pp, _, _ = hh.solve(torch.tensor(f_np.reshape(-1), device=dev), tol=TOL)
+                    res = (uu.cpu().numpy(), pp.cpu().numpy())
+                    hh.close()
+                    return res
+                line["oracle_error"] = oracle_error(P, W, w, npz, solve_lib)
             except Exception as e:  # noqa: BLE001
                 line["oracle_error"] = {"error": str(e)[:200]}
             finally:
