@@ -518,18 +518,61 @@ static inline uint64_t face_key(int a, int b, int c, int nv) {
 static void build_topology(const Mesh& m, Topology& T) {
     const int d = m.d, nvpc = d + 1, nle = d == 2 ? 3 : 6;
     T.d = d;
-    T.cell_edge.resize((size_t)m.nc * nle);
-    std::unordered_map<uint64_t, int> eid;
-    eid.reserve((size_t)m.nc * (d == 2 ? 2 : 2));
-    for (int e = 0; e < m.nc; ++e) {
-        const int* v = &m.C[(size_t)e * nvpc];
-        for (int t = 0; t < nle; ++t) {
-            const int i = d == 2 ? kEdges2[t][0] : kEdges3[t][0], j = d == 2 ? kEdges2[t][1] : kEdges3[t][1];
-            auto ins = eid.emplace(edge_key(v[i], v[j]), (int)eid.size());
-            T.cell_edge[(size_t)e * nle + t] = ins.first->second;
-        }
+    // vertex -> cells (cells in increasing index)
+    T.v2c_off.assign(m.nv + 1, 0);
+    for (int x : m.C) T.v2c_off[x + 1]++;
+    for (int i = 0; i < m.nv; ++i) T.v2c_off[i + 1] += T.v2c_off[i];
+    T.v2c.resize(m.C.size());
+    {
+        std::vector<int> fill(T.v2c_off.begin(), T.v2c_off.end() - 1);
+        for (int e = 0; e < m.nc; ++e)
+            for (int i = 0; i < nvpc; ++i) T.v2c[fill[m.C[(size_t)e * nvpc + i]]++] = e;
     }
-    T.ne = (int)eid.size();
+    // edges numbered vertex by vertex: edge (a, b), a < b, is the rank of b
+    // among the sorted distinct neighbours w > a of a (over a's cells),
+    // offset by the counts of the vertices before a.  Built in parallel
+    // without hashing; only the identity of the ids matters downstream.
+    std::vector<int> nbr_off(m.nv + 1, 0);
+    auto upper_neighbours = [&](int a, std::vector<int>& w) {
+        w.clear();
+        for (int x = T.v2c_off[a]; x < T.v2c_off[a + 1]; ++x) {
+            const int* v = &m.C[(size_t)T.v2c[x] * nvpc];
+            for (int i = 0; i < nvpc; ++i)
+                if (v[i] > a) w.push_back(v[i]);
+        }
+        std::sort(w.begin(), w.end());
+        w.erase(std::unique(w.begin(), w.end()), w.end());
+    };
+    parallel_for(m.nv, [&](int lo, int hi, int) {
+        std::vector<int> w;
+        for (int a = lo; a < hi; ++a) {
+            upper_neighbours(a, w);
+            nbr_off[a + 1] = (int)w.size();
+        }
+    }, 1024);
+    for (int a = 0; a < m.nv; ++a) nbr_off[a + 1] += nbr_off[a];
+    std::vector<int> nbr(nbr_off[m.nv]);
+    parallel_for(m.nv, [&](int lo, int hi, int) {
+        std::vector<int> w;
+        for (int a = lo; a < hi; ++a) {
+            upper_neighbours(a, w);
+            std::copy(w.begin(), w.end(), nbr.begin() + nbr_off[a]);
+        }
+    }, 1024);
+    T.cell_edge.resize((size_t)m.nc * nle);
+    parallel_for(m.nc, [&](int lo, int hi, int) {
+        for (int e = lo; e < hi; ++e) {
+            const int* v = &m.C[(size_t)e * nvpc];
+            for (int t = 0; t < nle; ++t) {
+                const int i = d == 2 ? kEdges2[t][0] : kEdges3[t][0], j = d == 2 ? kEdges2[t][1] : kEdges3[t][1];
+                const int a = std::min(v[i], v[j]), b = std::max(v[i], v[j]);
+                const int* first = nbr.data() + nbr_off[a];
+                const int* last = nbr.data() + nbr_off[a + 1];
+                T.cell_edge[(size_t)e * nle + t] = nbr_off[a] + (int)(std::lower_bound(first, last, b) - first);
+            }
+        }
+    }, 1024);
+    T.ne = nbr_off[m.nv];
     std::vector<int> facet_count;
     if (d == 3) {
         T.cell_face.resize((size_t)m.nc * 4);
@@ -574,13 +617,6 @@ static void build_topology(const Mesh& m, Topology& T) {
             }
         }
     }
-    T.v2c_off.assign(m.nv + 1, 0);
-    for (int x : m.C) T.v2c_off[x + 1]++;
-    for (int i = 0; i < m.nv; ++i) T.v2c_off[i + 1] += T.v2c_off[i];
-    T.v2c.resize(m.C.size());
-    std::vector<int> fill(T.v2c_off.begin(), T.v2c_off.end() - 1);
-    for (int e = 0; e < m.nc; ++e)
-        for (int i = 0; i < nvpc; ++i) T.v2c[fill[m.C[(size_t)e * nvpc + i]]++] = e;
 }
 
 static int binom(int n, int r) {
@@ -1325,9 +1361,13 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     for (int mi = 0; mi < nm; ++mi) ls.push_back({mi, (np == 0 && mi == 0) ? spec.family : 0, q, false});
     if ((int)ls.size() > 16) throw std::invalid_argument("too many levels");
     H.levels.assign(ls.size(), Level());
-    std::map<std::pair<int, int>, RefElement> refs;
-    std::map<std::pair<int, int>, RefTensors> tensors;
-    auto ref = [&](int dd, int kk) -> RefElement& {
+    // reference elements and tensors depend on (d, k) only: computed once per
+    // process and kept (std::map entries do not move on insertion)
+    static std::mutex ref_mu;
+    static std::map<std::pair<int, int>, RefElement> refs;
+    static std::map<std::pair<int, int>, RefTensors> tensors;
+    auto ref = [&](int dd, int kk) -> const RefElement& {
+        std::lock_guard<std::mutex> g(ref_mu);
         auto key = std::make_pair(dd, kk);
         auto it = refs.find(key);
         if (it == refs.end()) { refs[key].init(dd, kk); it = refs.find(key); }
@@ -1353,10 +1393,15 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         const RefElement& rq = ref(d, L.k - 1);
         build_space(m, topo[L.mesh_index], rv, true, L.V);
         build_space(m, topo[L.mesh_index], rq, L.family == 0, L.Q);
-        auto rkey = std::make_pair(d * 100 + L.k, 0);
-        auto rit = tensors.find(rkey);
-        if (rit == tensors.end()) { tensors[rkey].init(rv, rq); rit = tensors.find(rkey); }
-        const RefTensors& RT = rit->second;
+        const RefTensors* rtp;
+        {
+            std::lock_guard<std::mutex> g(ref_mu);
+            auto rkey = std::make_pair(d * 100 + L.k, 0);
+            auto rit = tensors.find(rkey);
+            if (rit == tensors.end()) { tensors[rkey].init(rv, rq); rit = tensors.find(rkey); }
+            rtp = &rit->second;
+        }
+        const RefTensors& RT = *rtp;
         double tb = now_ms();
         L.RT = RT;
         L.nu_cells = nus[L.mesh_index];
