@@ -23,6 +23,9 @@ defaults otherwise).
   central difference of the library's own solves.
 * The bench's relaxation keeps the FGMRES iteration count flat from 64^2 to
   128^2 (a property of the method under these parameters, not a parity check).
+* The bench's 32-forcing batched forward and adjoint on 128^2 with per-cell
+  viscosity: sampled columns' true residuals under the oracle's operator, and
+  the batched viscosity gradient against the per-column sum.
 """
 import numpy as np
 import pytest
@@ -246,3 +249,48 @@ def test_bench_relaxation_iterations_stay_flat_under_refinement():
         its.append(it)
         h.close()
     assert its[0] <= 11 and its[1] <= its[0] + 3, its
+
+
+def test_batched_forward_and_adjoint_on_128x128_as_bench_runs_them():
+    """The bench's 32-forcing batch on TH P3/P2 128^2 with nu_e = exp(N(0, 1/4))
+    (stokes_solve_batched, stokes_adjoint_solve_batched and
+    stokes_grad_viscosity_batched, 3xTF32 batched V-cycle, tolerance 1e-8):
+    sampled columns have a true relative residual <= 2e-8 under the oracle's
+    independently assembled operator and load (the library stops at 1e-8 on
+    its own operator), every column converged, and the batched viscosity
+    gradient equals the sum of the columns' single gradients (1e-12)."""
+    w = W.workload("th_p3_128x128_nu")
+    probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, hierarchy=P.HIER_EXPLICIT, schedule=w.schedule,
+                       host_only=1)
+    nc = probe.n_cells()
+    cent = probe.cell_centroids()
+    probe.close()
+    nu_l = W.cell_viscosity(nc, w.seed)
+    meshes, _ = geometry.hierarchy(w.verts, w.cells, w.n_refine, False)
+    vf, cf = meshes[0]
+    pc = permutation(keys(cent, np.zeros(nc)), keys(vf[cf].mean(axis=1), np.zeros(len(cf))))
+    nu_o = nu_l[pc]                                   # oracle cell i is library cell pc[i]
+    D = stokes.discretize(vf, cf, stokes.TH, w.k, nu_cells=nu_o)
+    h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, nu_cell=nu_l, hierarchy=P.HIER_EXPLICIT,
+                   schedule=w.schedule, precision=P.MIXED)
+    pv, pq = full_field_perms(h, D)
+    nV, d, nb = D.V.n, D.d, 32
+    F_l = np.stack([W.nodal_forcing(nV, d, w.seed + 100 + q) for q in range(nb)])     # library node order
+    U, Pp, its, rel = h.solve_batched(torch.tensor(F_l.reshape(nb, -1), device="cuda"), tol=1e-8)
+    assert np.all(rel <= 1e-8), rel
+    for q in (0, 13, 31):
+        f_o = F_l[q][:, pv]                          # the same forcing in the oracle's node order
+        b, _ = stokes.load_vector(D, f_o)
+        u_o = U[q].cpu().numpy().reshape(d, -1)[:, pv].reshape(-1)
+        x = np.concatenate([u_o, Pp[q].cpu().numpy()[pq]])[D.free]
+        res = np.linalg.norm(b - D.K @ x) / np.linalg.norm(b)
+        assert res <= 2e-8, (q, res)
+    ut = torch.tensor(np.random.default_rng(w.seed + 9).uniform(-1.0, 1.0, (d, nV)).reshape(-1), device="cuda")
+    GU = (U - ut).contiguous()
+    GP = torch.zeros_like(Pp)
+    LU, _, _, _, arel = h.adjoint_batched(GU, GP, tol=1e-8)
+    assert np.all(arel <= 1e-8), arel
+    g = h.grad_viscosity_batched(U, LU)
+    ref = sum(h.grad_viscosity(U[q].contiguous(), LU[q].contiguous()) for q in range(nb))
+    assert float((g - ref).abs().max() / ref.abs().max()) < 1e-12
+    h.close()
