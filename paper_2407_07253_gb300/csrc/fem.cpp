@@ -644,6 +644,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         S.boundary.assign(S.n, 0);
         S.support.resize(S.n);
         S.owner_cell.resize(S.n);
+        S.owner_local.resize(S.n);
         parallel_for(m.nc, [&](int lo, int hi, int) {
             for (int e = lo; e < hi; ++e) {
                 const int* v = &m.C[(size_t)e * nvpc];
@@ -660,6 +661,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
                     }
                     S.support[id] = sup;
                     S.owner_cell[id] = e;
+                    S.owner_local[id] = l;
                 }
             }
         });
@@ -754,6 +756,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
     S.boundary.assign(n, 0);
     S.support.assign(n, {-1, -1, -1, -1});
     S.owner_cell.assign(n, -1);
+    S.owner_local.assign(n, -1);
     // node data from its first (cell, local node)
     parallel_for((int)ntot, [&](int lo, int hi, int) {
         for (int t = lo; t < hi; ++t) {
@@ -761,6 +764,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
             const int e = t / nb, l = t % nb, id = rankpos[t];
             const int* v = &m.C[(size_t)e * nvpc];
             S.owner_cell[id] = e;
+            S.owner_local[id] = l;
             for (int c = 0; c < d; ++c) {
                 double x = 0;
                 for (int i = 0; i < nvpc; ++i) x += re.alpha[l][i] * m.X[(size_t)v[i] * d + c];
@@ -1200,30 +1204,47 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
 // fine cell owning it.  Entries with |v| <= 1e-14 (exact lattice zeros) are
 // dropped.
 static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const Space& Vc,
-                         const RefElement& rec, const std::vector<int>* parent) {
+                         const RefElement& rec, const std::vector<int>* parent, const RefElement* ref_f) {
     const int d = mf.d, nbc = Vc.nb;
     CSR P;
     P.nr = Vf.n;
     P.ncol = Vc.n;
+    // On one mesh (a p-transfer) a fine node with local index l sits at the
+    // reference point alpha_l / k_f of its owner cell, the coarse cell too:
+    // the coarse basis values there are one table row per l.
+    std::vector<double> tab;
+    if (!parent && ref_f && ref_f->k > 0 && ref_f->nb == Vf.nb) {
+        tab.resize((size_t)ref_f->nb * nbc);
+        for (int l = 0; l < ref_f->nb; ++l) {
+            double xi[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) xi[a] = (double)ref_f->alpha[l][a + 1] / ref_f->k;
+            rec.eval(xi, tab.data() + (size_t)l * nbc);
+        }
+    }
     // a row has at most nbc entries: fill fixed slots in parallel, then compact
     std::vector<int> cnt(Vf.n);
     fvec<int> scol((size_t)Vf.n * nbc);
     fvec<double> sval((size_t)Vf.n * nbc);
     parallel_for(Vf.n, [&](int lo, int hi, int) {
-        double val[320];
+        double vbuf[320];
         std::pair<int, double> row[320];
         for (int i = lo; i < hi; ++i) {
             int fc = Vf.owner_cell[i];
             int cc = parent ? (*parent)[fc] : fc;
-            CellGeom g = cell_geom(mc, cc);
-            const int* cv = &mc.C[(size_t)cc * (d + 1)];
-            double xi[3] = {0, 0, 0};
-            for (int a = 0; a < d; ++a) {
-                double s = 0;
-                for (int c = 0; c < d; ++c) s += g.Jinv[a * d + c] * (Vf.X[(size_t)i * d + c] - mc.X[(size_t)cv[0] * d + c]);
-                xi[a] = s;
+            const double* val = vbuf;
+            if (!tab.empty()) {
+                val = tab.data() + (size_t)Vf.owner_local[i] * nbc;
+            } else {
+                CellGeom g = cell_geom(mc, cc);
+                const int* cv = &mc.C[(size_t)cc * (d + 1)];
+                double xi[3] = {0, 0, 0};
+                for (int a = 0; a < d; ++a) {
+                    double s = 0;
+                    for (int c = 0; c < d; ++c) s += g.Jinv[a * d + c] * (Vf.X[(size_t)i * d + c] - mc.X[(size_t)cv[0] * d + c]);
+                    xi[a] = s;
+                }
+                rec.eval(xi, vbuf);
             }
-            rec.eval(xi, val);
             int m = 0;
             for (int l = 0; l < nbc; ++l)
                 if (std::fabs(val[l]) > 1e-14) row[m++] = {Vc.cell_nodes[(size_t)cc * nbc + l], val[l]};
@@ -1250,9 +1271,10 @@ static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const 
 }
 
 static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Level& C,
-                              const RefElement& recV, const RefElement& recQ, const std::vector<int>* parent) {
-    CSR PV = scalar_interp(mf, F.V, mc, C.V, recV, parent);
-    CSR PQ = scalar_interp(mf, F.Q, mc, C.Q, recQ, parent);
+                              const RefElement& recV, const RefElement& recQ, const std::vector<int>* parent,
+                              const RefElement* refV_f, const RefElement* refQ_f) {
+    CSR PV = scalar_interp(mf, F.V, mc, C.V, recV, parent, refV_f);
+    CSR PQ = scalar_interp(mf, F.Q, mc, C.Q, recQ, parent, refQ_f);
     const int d = mf.d;
     CSR& P = F.P;
     P.nr = F.n_free;
@@ -1432,7 +1454,8 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     for (size_t l = 0; l + 1 < ls.size(); ++l) {
         Level &F = H.levels[l], &C = H.levels[l + 1];
         const std::vector<int>* par_map = (F.mesh_index == C.mesh_index) ? nullptr : &H.parents[F.mesh_index];
-        monolithic_interp(H.meshes[F.mesh_index], F, H.meshes[C.mesh_index], C, ref(d, C.k), ref(d, C.k - 1), par_map);
+        monolithic_interp(H.meshes[F.mesh_index], F, H.meshes[C.mesh_index], C, ref(d, C.k), ref(d, C.k - 1), par_map,
+                          &ref(d, F.k), &ref(d, F.k - 1));
     }
     H.t_transfers_ms = now_ms() - tt;
     H.t_assembly_ms = now_ms() - t1 - H.t_callbacks_ms;

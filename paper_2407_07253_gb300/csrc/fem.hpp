@@ -84,6 +84,7 @@ struct Space {
     std::vector<unsigned char> boundary;       // [n]
     std::vector<std::array<int, 4>> support;   // [n] vertices of the owning entity (-1 padded)
     std::vector<int> owner_cell;               // [n] a cell containing the node
+    std::vector<int> owner_local;              // [n] the node's local index in owner_cell
 };
 
 struct Level {
