@@ -32,7 +32,8 @@ def _worker(rank, world, port, out):
 def test_max_over_ranks_two_gloo_replicas():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    # spawn, not fork: the test process may already run the library's host threads
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
