@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--fbf-workload", default="sv_p4_disk",
                     help="Scott-Vogelius workload of the FBF(phMG) versus monolithic phMG measurement")
     ap.add_argument("--no-fbf", action="store_true")
+    ap.add_argument("--no-highk", action="store_true", help="skip the direct-versus-gradual P6 / P8 measurement")
+    ap.add_argument("--highk-only", action="store_true", help="only the high-order measurement")
     ap.add_argument("--fbf-only", action="store_true", help="only the FBF measurement (profiling driver)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the adjoint measurement (profiling driver)")
@@ -106,59 +108,96 @@ f = W.nodal_forcing(D.V.n, D.d, w.seed)
 full, its, hist, b, x = mg.solve(h, f, None, tol={tol!r})
 t2 = time.perf_counter()
 if {save!r}:
-    np.savez({save!r}, full=full, vx=D.V.coords, px=D.Q.coords)
+    # untimed: the same forcing solved to a relative residual of {tight!r}
+    # (the discrete solution to rounding), and the owner-cell centroid of
+    # every pressure node (discontinuous pressures share coordinates)
+    full_tight = mg.solve(h, f, None, tol={tight!r})[0]
+    cells = np.asarray(D.cells)
+    cent = D.verts[cells].mean(axis=1)
+    owner = np.zeros(D.Q.n, dtype=np.int64)
+    for ci in range(len(cells)):
+        owner[D.Q.cell_nodes[ci]] = ci
+    pc = cent[owner] if not D.Q.continuous else np.zeros_like(D.Q.coords)
+    np.savez({save!r}, full=full, full_tight=full_tight, vx=D.V.coords, px=D.Q.coords, pc=pc)
 print(json.dumps(dict(setup_s=t1 - t0, solve_s=t2 - t1, its=its, relres=hist[-1])))
 """
+TIGHT = 1e-14         # the oracle's tight solve (its pinned route to the discrete solution)
+TIGHT_LIB = 1e-13     # the library's FP64 solve compared with it
 
 
-def run_oracle(name, relax, timeout=900, save=None):
-    """The FP64 CPU oracle, as it stands, in a fresh single-threaded process,
-    with the relaxation parameters of the GPU step (its solution and node
-    coordinates written to `save`, an .npz path, when given; outside the
-    timed part)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL, relax=RELAX[relax], save=save)
+def run_oracle(name, relax, timeout=900, save=None, threads=1):
+    """The FP64 CPU oracle, as it stands, in a fresh process whose BLAS uses
+    `threads` threads, with the relaxation parameters of the GPU step (its
+    solutions and node coordinates written to `save`, an .npz path, when
+    given; outside the timed part)."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, tol=TOL, relax=RELAX[relax], save=save, tight=TIGHT)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=timeout, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def node_perm(lib_xyz, ora_xyz, lib_center=None, ora_center=None):
+    """perm such that library node perm[i] is oracle node i, matched by
+    coordinates rounded to 1e-9 and, for discontinuous spaces (several nodes
+    at one position), the owning cell's centroid.  Raises if a key is not
+    unique or has no partner."""
+    import numpy as np
+
+    def key(x, c):
+        a = np.round(np.asarray(x) * 1e9).astype(np.int64)
+        if c is not None:
+            a = np.concatenate([a, np.round(np.asarray(c) * 1e9).astype(np.int64)], axis=1)
+        return [tuple(r) for r in a.tolist()]
+
+    kl, ko = key(lib_xyz, lib_center), key(ora_xyz, ora_center)
+    where = {k: i for i, k in enumerate(kl)}
+    if len(where) != len(kl) or len(set(ko)) != len(ko) or len(kl) != len(ko):
+        raise ValueError("node keys are not unique: pass the owner-cell centroids of discontinuous nodes")
+    return np.array([where[k] for k in ko])
+
+
 def oracle_error(P, W, w, npz, solve):
-    """Relative max-norm differences between the GPU solutions (mixed and
-    FP64, solved to TOL) and the oracle's (solved to TOL in FP64) for the
-    oracle's forcing: the seeded nodal values in the oracle's node order,
-    moved to the library's nodes by their coordinates (an input permutation;
-    the timed steps draw the same generator in the library's order).
-    solve(precision, f) returns (u, p) of the library as numpy arrays;
+    """Relative max-norm differences between the GPU solutions and the
+    oracle's for the oracle's forcing: the seeded nodal values in the
+    oracle's node order, moved to the library's nodes by their coordinates
+    (an input permutation; the timed steps draw the same generator in the
+    library's order).
+      mixed, fp64   library solved to TOL against the oracle solved to TOL
+                    (they differ by about TOL times the condition number);
+      fp64_tight    library FP64 solved to TIGHT_LIB against the oracle solved
+                    to TIGHT, i.e. both at the discrete solution: the accuracy
+                    target of 1e-10 relative for u and the zero-mean p.
+    solve(precision, f, tol) returns (u, p) of the library as numpy arrays;
     pressures are both zero-mean."""
     import numpy as np
 
     z = np.load(npz)
     probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
                        hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
-    vx, px, _ = probe.nodes()
+    vx, px, pc = probe.nodes()
     probe.close()
-
-    def perm(lib_xyz, ora_xyz):
-        key = lambda x: [tuple(r) for r in np.round(np.asarray(x) * 1e9).astype(np.int64).tolist()]  # noqa: E731
-        where = {k: i for i, k in enumerate(key(lib_xyz))}
-        return np.array([where[k] for k in key(ora_xyz)])
-
-    pv, pq = perm(vx, z["vx"]), perm(px, z["px"])
+    disc = bool(np.abs(z["pc"]).max() > 0)
+    pv = node_perm(vx, z["vx"])
+    pq = node_perm(px, z["px"], pc if disc else None, z["pc"] if disc else None)
     d, nV = w.verts.shape[1], len(z["vx"])
-    u_o = z["full"][:d * nV].reshape(d, nV)
-    p_o = z["full"][d * nV:]
     f_lib = np.empty((d, nV))
     f_lib[:, pv] = W.nodal_forcing(nV, d, w.seed)
     out = {}
-    for tag, prec in (("mixed", P.MIXED), ("fp64", P.FP64)):
-        u, p = solve(prec, f_lib)
+    for tag, prec, tol, ref in (("mixed", P.MIXED, TOL, "full"), ("fp64", P.FP64, TOL, "full"),
+                                ("fp64_tight", P.FP64, TIGHT_LIB, "full_tight")):
+        u_o = z[ref][:d * nV].reshape(d, nV)
+        p_o = z[ref][d * nV:]
+        u, p = solve(prec, f_lib, tol)
         U = u.reshape(d, -1)[:, pv]
         out[tag] = {"u_rel": float(np.abs(U - u_o).max() / np.abs(u_o).max()),
-                    "p_rel": float(np.abs(p[pq] - p_o).max() / np.abs(p_o).max())}
-    out["note"] = (f"max-norm differences, relative to the oracle's max; every solve stops at {TOL} relative "
-                   "residual, so they differ by about that tolerance times the condition number")
+                    "p_rel": float(np.abs(p[pq] - p_o).max() / np.abs(p_o).max()), "tol": tol}
+    out["fp64_tight"]["oracle_tol"] = TIGHT
+    out["note"] = (f"max-norm differences, relative to the oracle's max. mixed and fp64: both sides stop at {TOL} "
+                   "relative residual, so they differ by about that tolerance times the condition number. "
+                   f"fp64_tight: the library's FP64 path at {TIGHT_LIB} against the oracle at {TIGHT} (target 1e-10)")
     return out
 
 
@@ -169,10 +208,20 @@ def relax_text(name):
             "Vanka-star ASM sweep, pre and post")
 
 
+def step_config(a, w, world):
+    """The workload of one step, identical in both arms."""
+    return {"workload": a.workload, "family": "TH" if w.family == 0 else "SV", "k": w.k,
+            "schedule": list(w.schedule), "tol": TOL, "relaxation": relax_text(a.relaxation),
+            "parallelism": f"replicas{world}"}
+
+
 def reference_arm(a):
+    import workloads as W
+
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    w = W.workload(a.workload)
     runs = []
     for _ in range(max(1, a.steps)):
         runs.append(run_oracle(a.workload, a.relaxation))
@@ -182,8 +231,10 @@ def reference_arm(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": a.workload, "tol": TOL, "relaxation": relax_text(a.relaxation)},
-        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+        "config": step_config(a, w, world),
+        "precision": "FP64 throughout (numpy/scipy)",
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "host_cores": os.cpu_count() or 1,
+                         "kind": "oracle",
                          "sample": f"full setup + FGMRES solve of {a.workload} per step, {relax_text(a.relaxation)}, "
                                    "single-threaded numpy/scipy",
                          "iterations": runs[0]["its"]},
@@ -585,6 +636,49 @@ def paper_scale_section(P, W, dev, stream, flush, reps=3):
     return res
 
 
+def highk_section(a, P, W, dev, stream, flush, reps=3):
+    """High order (Fig. 7, Sec. 4.1.1): TH P6/P5 and P8/P7 on the 32 x 32
+    square, one step (setup + mixed-precision solve to TOL, L2 flushed, CUDA
+    events) with direct p-coarsening k -> 2 and with the gradual schedule of
+    Fig. 7, median of `reps` after one warm-up, with the bench relaxation."""
+    import torch
+
+    res = {"relaxation": relax_text(a.relaxation)}
+    for name in ("th_p6_32x32", "th_p8_32x32"):
+        w = W.workload(name)
+        probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, hierarchy=P.HIER_EXPLICIT,
+                           schedule=w.schedule, host_only=1)
+        i0 = probe.info()
+        probe.close()
+        f = torch.tensor(W.nodal_forcing(i0["n_vel_nodes"], w.verts.shape[1], w.seed).reshape(-1), device=dev)
+        row = {"n_free": int(i0["n_free"][0]), "max_patch": int(i0["max_patch"][0])}
+        for hier, sched in (("direct", [w.k, 2]), ("gradual", list(w.schedule))):
+            runs = []
+            try:
+                for r in range(reps + 1):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, hierarchy=P.HIER_EXPLICIT,
+                                   schedule=sched, precision=P.MIXED, stream=stream.cuda_stream,
+                                   **RELAX[a.relaxation])
+                    st = h.info()
+                    u, p, its, rel = h.solve(f, tol=TOL)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r:
+                        runs.append((e0.elapsed_time(e1), st["t_total_ms"], its, rel))
+                    h.close()
+                runs.sort()
+                ms, setup, its, rel = runs[len(runs) // 2]
+                row[hier] = {"schedule": sched, "step_ms": ms, "setup_ms": setup, "iterations": its, "relres": rel}
+            except Exception as e:  # noqa: BLE001
+                row[hier] = {"schedule": sched, "error": str(e)[:200]}
+        res[name] = row
+    return res
+
+
 def fbf_section(a, P, W, dev, stream, flush):
     """Scott-Vogelius: one step (setup + solve to TOL, mixed precision, L2
     flushed, CUDA events) with FBF(phMG) (Eq. fbf) and with the monolithic
@@ -714,6 +808,9 @@ def main():
     if a.adjoint_only:
         print(json.dumps(adjoint_section(a, P, W, dev, stream, flush)))
         return
+    if a.highk_only:
+        print(json.dumps(highk_section(a, P, W, dev, stream, flush)))
+        return
     if a.batched_only:
         peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         hbm_only = json.load(open(peaks_path)).get("hbm_gbs", 6800.0) if os.path.exists(peaks_path) else 6800.0
@@ -765,6 +862,18 @@ def main():
             paper = paper_scale_section(P, W, dev, stream, flush)
         except Exception as e:  # noqa: BLE001
             paper = {"error": str(e)[:300]}
+    # FP64 pipe peak, measured live: a DFMA loop on every SM
+    fp64_probe = {}
+    try:
+        P._binding.probe_fp64_peak(1 << 12, 2, stream=stream.cuda_stream)
+        with Clocks(local) as pclk:
+            runs = [P._binding.probe_fp64_peak(1 << 17, 2, stream=stream.cuda_stream) for _ in range(5)]
+        tf = sorted(r[0] for r in runs)
+        fp64_probe = {"median_tflops": tf[len(tf) // 2], "max_tflops": tf[-1], "min_tflops": tf[0],
+                      "ms_per_launch": sorted(r[1] for r in runs)[len(runs) // 2], "launches": len(runs),
+                      "clocks": pclk.summary()}
+    except Exception as e:  # noqa: BLE001
+        fp64_probe = {"error": str(e)[:200]}
     # solve-phase roofline: level 0's FP32 patch apply (one ASM sweep over
     # 4225 inverses), timed by CUDA events on its stream after an L2 flush
     hp = make(P.MIXED, 1 << P._binding.PROF_PATCH)
@@ -797,6 +906,12 @@ def main():
             fbf_res = fbf_section(a, P, W, dev, stream, flush)
         except Exception as e:  # noqa: BLE001
             fbf_res = {"error": str(e)[:300]}
+    highk = None
+    if not a.no_highk:
+        try:
+            highk = highk_section(a, P, W, dev, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            highk = {"error": str(e)[:300]}
     adj = None
     if not a.no_adjoint:
         try:
@@ -845,8 +960,10 @@ def main():
     gj_launches_per_step = gj_prof[0] / a.steps
     gj_ms_per_step = gj_prof[1] / a.steps
     # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
-    # clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s)
-    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+    # clock x 2 flop x 2.07 GHz = 1.259 TFLOP/s (the nominal 1.25 TFLOP/s);
+    # the roofline uses the live DFMA-loop measurement (median of 5)
+    fp64_derived_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+    fp64_peak_tflops = fp64_probe["median_tflops"] if fp64_probe.get("median_tflops") else fp64_derived_tflops
     # dominant kernel: level 0's saddle block inversion launch (4225 patches)
     gj0_ms = sorted(gj0)[len(gj0) // 2] if gj0 else 0.0
     achieved_gj0 = flops_levels[0] / (gj0_ms * 1e-3) / 1e12 if gj0_ms > 0 else None
@@ -863,12 +980,10 @@ def main():
         "metric": METRIC, "value": ms_max, "unit": "ms", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": a.workload, "family": "TH" if w.family == 0 else "SV", "k": w.k,
-                   "schedule": w.schedule, "n_free": stats["n_free"], "nnz_level0": stats["nnz"][0],
-                   "tol": TOL, "precision": "mixed (FP32 V-cycle, FP64 FGMRES/LU/coarse)",
-                   "relaxation": relax_text(a.relaxation),
-                   "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) before every step",
-                   "inputs": "mesh on host, f resident in HBM"},
+        "config": step_config(a, w, world),
+        "precision": "mixed (FP32 V-cycle, FP64 FGMRES/LU/coarse)",
+        "problem": {"n_free": stats["n_free"], "nnz_level0": stats["nnz"][0],
+                    "l2": "flushed (256 MB write) before every step", "inputs": "mesh on host, f resident in HBM"},
         "iterations": its_l[-1],
         "setup_ms": {k: round(stats[k], 3) for k in ("t_mesh_ms", "t_assembly_ms", "t_spaces_ms", "t_matrices_ms",
                                                      "t_patches_ms", "t_transfers_ms", "t_upload_ms", "t_launch_thread_ms", "t_launch_wait_ms", "t_upload_post_ms", "t_gather_lu_ms",
@@ -883,7 +998,11 @@ def main():
                      "bound": "alu", "achieved": achieved_gj0, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                      "frac": (achieved_gj0 / fp64_peak_tflops) if achieved_gj0 else None,
                      "traffic": traffic_gj0,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                     "peak_source": ("measured: DFMA loop (stokes_probe_fp64_peak, 8 FMA chains x 256 threads x 2 "
+                                     "CTAs per SM), median of 5 launches in this run"
+                                     if fp64_probe.get("median_tflops") else
+                                     "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"),
+                     "peak_derived": fp64_derived_tflops, "fp64_probe": fp64_probe,
                      "flop_per_launch": flops_levels[0], "ms_per_launch": gj0_ms,
                      "all_levels": {"launches_per_step": gj_launches_per_step, "ms_per_step": gj_ms_per_step,
                                     "flop_per_step": flops_gj, "achieved": achieved_gj}},
@@ -904,15 +1023,17 @@ def main():
         line["adjoint"] = adj
     if fbf_res is not None:
         line["fbf"] = fbf_res
+    if highk is not None:
+        line["high_k"] = highk
     line["clocks"] = clk.summary()
     if not a.no_cpu_baseline and world == 1:
         try:
             npz = os.path.join(tempfile.gettempdir(), f"stokes_bench_oracle_{os.getpid()}.npz")
             o = run_oracle(a.workload, a.relaxation, save=npz)
             try:
-                def solve_lib(prec, f_np):
+                def solve_lib(prec, f_np, tol):
                     hh = make(prec)
-                    uu, pp, _, _ = hh.solve(torch.tensor(f_np.reshape(-1), device=dev), tol=TOL)
+                    uu, pp, _, _ = hh.solve(torch.tensor(f_np.reshape(-1), device=dev), tol=tol)
                     res = (uu.cpu().numpy(), pp.cpu().numpy())
                     hh.close()
                     return res
@@ -922,11 +1043,20 @@ def main():
             finally:
                 if os.path.exists(npz):
                     os.remove(npz)
+            host_cores = os.cpu_count() or 1
             line["cpu_baseline"] = {"value": 1e3 * (o["setup_s"] + o["solve_s"]), "unit": "ms", "cores": 1,
-                                    "kind": "oracle",
+                                    "host_cores": host_cores, "kind": "oracle",
                                     "sample": f"one full setup + FGMRES solve of {a.workload} to {TOL}, "
                                               f"{relax_text(a.relaxation)}, single-threaded numpy/scipy",
-                                    "iterations": o["its"]}
+                                    "iterations": o["its"],
+                                    "setup_ms": 1e3 * o["setup_s"], "solve_ms": 1e3 * o["solve_s"]}
+            try:
+                oa = run_oracle(a.workload, a.relaxation, threads=host_cores)
+                line["cpu_baseline"]["all_cores"] = {"value": 1e3 * (oa["setup_s"] + oa["solve_s"]), "unit": "ms",
+                                                     "threads": host_cores, "iterations": oa["its"],
+                                                     "note": "same oracle run with BLAS threads = host cores"}
+            except Exception as e:  # noqa: BLE001
+                line["cpu_baseline"]["all_cores"] = {"error": str(e)[:200]}
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline"] = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {e}"[:200]}

@@ -222,6 +222,17 @@ int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int
  * Errors: EINVAL, ECUDA. */
 int stokes_selftest_bounded_wait(long long polls, int* result);
 
+/* Measurement utility (no counterpart in the paper): the FP64 pipe's peak on
+ * this GPU, the denominator of the roofline of the FP64-bound kernels (the
+ * patch inversion).  Launches blocks_per_sm (1..8) CTAs of 256 threads per SM,
+ * each thread running 8 independent FP64 FMA chains of `iters` steps, once
+ * untimed and once timed with CUDA events on `stream`.
+ *   tflops  host out: 2 * 8 * iters * threads / duration, in TFLOP/s;
+ *   ms      host out: the timed launch's duration.
+ * Allocates one small device buffer (stream-ordered) and synchronises
+ * `stream`.  Errors: EINVAL, ECUDA. */
+int stokes_probe_fp64_peak(long long iters, int blocks_per_sm, double* tflops, float* ms, void* stream);
+
 /* Discrete adjoint of stokes_solve (differentiation of the solution with
  * respect to the forcing and the cell viscosities).  The paper does not
  * differentiate its solver; this is the standard adjoint of the linear solve
@@ -464,11 +475,15 @@ int stokes_prof_read_one(stokes_mg_t h, int kind, long long index, double* ms);
  * (offsets, pivot status, pivot workspace of matrices larger than 160) is a
  * fixed array of about 7 MB in this library's device memory, held by every
  * GPU that loads the library until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  Every call
- * shares the one array and it keeps the last call's contents (the pivot
- * status is cleared by each call): calls whose GPU work overlaps, on any
- * stream or thread, race on it.  The call synchronises `stream`.
+ * device does a one-time set-up: it looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture begins.  Every call shares the one array and it
+ * keeps the last call's contents (the pivot status is cleared by each call):
+ * GPU work of two calls that overlapped would race on it.  Within one process
+ * the entry point prevents that itself: a process-wide lock is held from the
+ * staging of the offsets (in static host arrays) until `stream` has drained,
+ * so concurrent calls from several host threads, on one device or on
+ * several, run one after another.  The call synchronises `stream`.
  * Errors: EINVAL (sizes), ESINGULAR, ECUDA; message from
  * stokes_noalloc_last_error(). */
 #define STOKES_NOALLOC_MAX_PATCHES 65536

@@ -84,6 +84,7 @@ def lib():
         "stokes_adjoint_solve": (c_int, [P, P, P, c_double, c_double, P, P, P, P, P, P]),
         "stokes_fgmres_batched": (c_int, [P, P, P, c_int, c_int, c_double, P, P, P]),
         "stokes_selftest_bounded_wait": (c_int, [c_longlong, P]),
+        "stokes_probe_fp64_peak": (c_int, [c_longlong, c_int, POINTER(c_double), POINTER(ctypes.c_float), P]),
         "stokes_grad_viscosity": (c_int, [P, P, P, P, P]),
         "stokes_solve_batched": (c_int, [P, P, P, c_int, c_int, c_double, c_double, P, P, P, P, P]),
         "stokes_adjoint_solve_batched": (c_int, [P, P, P, c_int, c_int, c_double, c_double, P, P, P, P, P, P]),
@@ -166,6 +167,13 @@ def selftest_bounded_wait(polls=1000):
     r = c_int()
     check(lib().stokes_selftest_bounded_wait(int(polls), byref(r)))
     return r.value
+
+
+def probe_fp64_peak(iters=1 << 16, blocks_per_sm=2, stream=None):
+    """stokes_probe_fp64_peak: (TFLOP/s, ms) of a timed DFMA-loop launch."""
+    t, ms = c_double(), ctypes.c_float()
+    check(lib().stokes_probe_fp64_peak(int(iters), int(blocks_per_sm), byref(t), byref(ms), _stream(stream)))
+    return t.value, ms.value
 
 
 class StokesMG:

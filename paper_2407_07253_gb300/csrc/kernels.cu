@@ -1120,4 +1120,19 @@ __host__ __device__ void hessenberg_eig_core(int m, int ld, const double* Hs, do
     out[1] = failed;
 }
 
+__global__ void __launch_bounds__(256) fp64_fma_probe(long long iters, double a, double b, double never,
+                                                      double* __restrict__ out) {
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = 1e-3 * (threadIdx.x + 1) + u;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = fma(x[u], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += x[u];
+    if (s == never) out[blockIdx.x] = s;
+}
+
 }  // namespace skern

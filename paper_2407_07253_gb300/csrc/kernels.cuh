@@ -257,6 +257,11 @@ __global__ void csr_block_fill(int nr, int nc, const int* __restrict__ rp, const
                                const double* __restrict__ v, const int* __restrict__ brp, int* __restrict__ bci,
                                double* __restrict__ bv, float* __restrict__ bv32);
 // x[i] -= w[i] * num[0] / den
+// FP64 pipe peak probe: every thread runs 8 independent FMA chains of
+// `iters` steps (x = x * a + b); out is written only if the sum equals the
+// impossible value `never`, which keeps the chains live.
+__global__ void fp64_fma_probe(long long iters, double a, double b, double never, double* __restrict__ out);
+
 __global__ void sub_weighted(int n, double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ num,
                              double den);
 

@@ -15,6 +15,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/stokes_mg.h"
 #include "kernels.cuh"
@@ -41,10 +42,16 @@ constexpr size_t kScratchBytes = align256(kOffCol + sizeof(double) * kMaxEntries
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Host copies of the offsets and of the status array (static, not allocated).
+// Host copies of the offsets and of the status array (static, not allocated),
+// shared by every thread of the process.  g_call_mu serialises whole calls:
+// a call holds it from filling these arrays until its stream has drained and
+// the status has been read back, so concurrent host calls (on one device or
+// on several) never overwrite each other's offsets or status.  std::mutex
+// has a constexpr constructor and locks through the kernel's futex: no heap.
 static int h_poff[kMaxPatches + 1];
 static long long h_moff[kMaxPatches + 1];
 static int h_status[kMaxPatches];
+static std::mutex g_call_mu;
 
 // Device address of g_noalloc_scratch, looked up once per device: in host
 // code the symbol's name is only a host-side stand-in and must never be
@@ -71,6 +78,7 @@ extern "C" int stokes_batched_inverse_noalloc(int npatch, const int* sizes, doub
     if (first_singular) *first_singular = -1;
     if (npatch < 1 || npatch > kMaxPatches || !sizes || !mats)
         return fail(STOKES_EINVAL, "npatch must be in [1, STOKES_NOALLOC_MAX_PATCHES] and pointers non-NULL");
+    std::lock_guard<std::mutex> call_lock(g_call_mu);
     long long total = 0;
     int nmax = 0;
     h_poff[0] = 0;
@@ -111,8 +119,17 @@ extern "C" int stokes_batched_inverse_noalloc(int npatch, const int* sizes, doub
         return fail(STOKES_ECUDA, cudaGetErrorString(e));
     const int nsm = nmax < skern::GJ_SMEM_MAX_N ? nmax : skern::GJ_SMEM_MAX_N;
     const size_t smem = (size_t)nsm * nsm * sizeof(double) + nsm * sizeof(double) + nsm * sizeof(int) + 64;
-    if ((e = cudaFuncSetAttribute(skern::gj_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return fail(STOKES_ECUDA, cudaGetErrorString(e));
+    // The attribute is process-wide and the setup path launches the same
+    // kernel from other threads and streams: always set the one upper bound
+    // (the largest shared-memory patch) that the setup path sets, never a
+    // smaller value, and launch with this call's own smaller size.
+    {
+        const size_t gmax = skern::GJ_SMEM_MAX_N;
+        const size_t smem_max = gmax * gmax * sizeof(double) + gmax * sizeof(double) + gmax * sizeof(int) + 64;
+        if ((e = cudaFuncSetAttribute(skern::gj_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_max)) != cudaSuccess)
+            return fail(STOKES_ECUDA, cudaGetErrorString(e));
+    }
     skern::gj_inverse_smem<<<npatch, 256, smem, s>>>(npatch, poff, moff, mats, nullptr, nullptr, nullptr, nullptr, status, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(STOKES_ECUDA, cudaGetErrorString(e));
     if (nmax > skern::GJ_SMEM_MAX_N) {

@@ -2535,6 +2535,37 @@ int stokes_selftest_bounded_wait(long long polls, int* result) {
     });
 }
 
+int stokes_probe_fp64_peak(long long iters, int blocks_per_sm, double* tflops, float* ms, void* stream) {
+    g_last_error.clear();
+    return guarded([&] {
+        require(tflops && ms && iters >= 1 && blocks_per_sm >= 1 && blocks_per_sm <= 8, "invalid argument");
+        int dev = 0, nsm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const cudaStream_t s = (cudaStream_t)stream;
+        const int grid = nsm * blocks_per_sm;
+        double* out = nullptr;
+        CK(cudaMallocAsync((void**)&out, sizeof(double) * grid, s));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        // warm-up launch, then the timed one
+        skern::fp64_fma_probe<<<grid, 256, 0, s>>>(iters / 8 + 1, 0.999999, 1e-7, -1.0, out);
+        CK(cudaEventRecord(e0, s));
+        skern::fp64_fma_probe<<<grid, 256, 0, s>>>(iters, 0.999999, 1e-7, -1.0, out);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaGetLastError());
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        CK(cudaEventDestroy(e0));
+        CK(cudaEventDestroy(e1));
+        CK(cudaFreeAsync(out, s));
+        CK(cudaStreamSynchronize(s));
+        *tflops = 2.0 * 8.0 * (double)iters * 256.0 * grid / (*ms * 1e-3) / 1e12;
+        return STOKES_OK;
+    });
+}
+
 int stokes_fgmres_batched(stokes_mg_t h, const double* b_dev, double* x_dev, int nrhs, int mode, double tol,
                           int* iterations, double* final_relres, void* stream) {
     g_last_error.clear();

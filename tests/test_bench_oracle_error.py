@@ -43,11 +43,26 @@ def test_oracle_error_of_the_oracle_itself_is_zero():
     f_o = W.nodal_forcing(nV, d, w.seed)
     seen = []
 
-    def solve(prec, f_lib):
+    def solve(prec, f_lib, tol):
         assert np.array_equal(f_lib, f_o[:, lv])
-        seen.append(prec)
-        return u_o[:, lv].reshape(-1), p_o[lq]
+        seen.append((prec, tol))
+        ref = z["full"] if tol == bench.TOL else z["full_tight"]
+        return ref[:d * nV].reshape(d, nV)[:, lv].reshape(-1), ref[d * nV:][lq]
     err = bench.oracle_error(P, W, w, npz, solve)
-    assert sorted(seen) == sorted([P.MIXED, P.FP64])
-    for tag in ("mixed", "fp64"):
+    assert sorted(seen) == sorted([(P.MIXED, bench.TOL), (P.FP64, bench.TOL), (P.FP64, bench.TIGHT_LIB)])
+    for tag in ("mixed", "fp64", "fp64_tight"):
         assert err[tag]["u_rel"] == 0.0 and err[tag]["p_rel"] == 0.0
+    # the tight solve is the discrete solution; the TOL solve is within TOL * cond of it
+    assert np.abs(z["full_tight"] - z["full"]).max() < 1e-5 * np.abs(z["full"]).max()
+
+
+def test_node_perm_needs_centroids_for_discontinuous_pressure():
+    """Scott-Vogelius pressures are discontinuous: nodes of different cells
+    share coordinates, so matching by position alone must fail loudly, and
+    matching by (position, owner-cell centroid) must be a bijection."""
+    xyz = np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 0.0]])
+    cen = np.array([[0.2, 0.1], [0.1, 0.2], [0.5, 0.3]])
+    with pytest.raises(ValueError):
+        bench.node_perm(xyz, xyz[::-1])
+    perm = bench.node_perm(xyz, xyz[[2, 0, 1]], cen, cen[[2, 0, 1]])
+    assert perm.tolist() == [2, 0, 1]

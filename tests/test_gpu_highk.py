@@ -4,7 +4,8 @@ The library builds the hierarchy itself from STOKES_HIER_GRADUAL: k = 6 and 7
 go 6/7 -> 4 -> 2, k >= 8 goes k -> 5 -> 2 (the schedule in
 tests/golden/pmg_schedule.txt), and Scott-Vogelius levels below the top go
 through Taylor-Hood (Sec. 3.2).  The patches are large: up to 561 DoFs at
-k = 8 and 758 for SV P6, which takes the saddle inverse's global-memory path.
+k = 8 and 758 for SV P6 in 2D, 2,922 for TH P6 and 2,067 for SV P3 in 3D,
+which take the saddle inverse's global-memory path.
 
 The patch blocks' condition numbers grow quickly with k on the equispaced
 lattice (max over the relaxed levels: 3.0e7 at k = 6, 1.5e8 at k = 7, 8.1e8
@@ -44,6 +45,12 @@ CASES = {
     "th_p8_4x4": (W.unit_square_mesh(2), 1, 0, 8, [8, 5, 2], False),
     "th_p6_8x8": (W.unit_square_mesh(2), 2, 0, 6, [6, 4, 2], False),
     "sv_p6_alfeld": (W.unit_square_mesh(2), 1, 1, 6, [6, 4, 2], True),
+    # 3D (Sec. 4.1.2, Sec. 4.2): Taylor-Hood P6/P5 on the 2^3 Kuhn cube
+    # (5,324 free DoFs, patches up to 2,922 DoFs), and monolithic
+    # Scott-Vogelius P3/P2disc on its Alfeld split (4,455 free DoFs, patches
+    # up to 2,067 DoFs; the coarser levels are Taylor-Hood P2)
+    "th3d_p6_2x2x2": (W.kuhn_cube_mesh(2), 0, 0, 6, [6, 4, 2], False),
+    "sv3d_p3_alfeld": (W.kuhn_cube_mesh(2), 0, 1, 3, [3, 2], True),
 }
 
 _cache = {}

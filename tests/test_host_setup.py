@@ -19,6 +19,7 @@ CASES = [
     ("sv_p3_alfeld", W.unit_square_mesh(2), 1, 1, 3, [3, 2], True),
     ("sv_p4_disk", W.delaunay_disk_mesh(0, h=0.5), 1, 1, 4, [4, 2], True),
     ("th3d_p3", W.kuhn_cube_mesh(1), 1, 0, 3, [3, 2], False),
+    ("sv3d_p3_alfeld", W.kuhn_cube_mesh(1), 0, 1, 3, [3, 2], True),
 ]
 
 

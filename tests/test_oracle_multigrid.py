@@ -223,3 +223,57 @@ def test_phmg_solver_converges_and_matches_direct():
     assert its < 40
     xd = stokes.zero_mean_pressure(D, stokes.expand(D, stokes.direct_solve(D, b), stokes.load_vector(D, f, g)[1]))
     assert np.abs(full - xd).max() < 1e-9
+
+
+@pytest.mark.parametrize("mesh", [("square", 2), ("square", 4), ("cube", 2)])
+def test_bordered_coarse_solve_is_the_zero_mean_solution(mesh):
+    """The coarsest solve (Sec. 4: exact; Sec. 2: p in L^2_0) returns, for a
+    consistent right-hand side r (pressure part orthogonal to the constant
+    null vector n of K), the unique x with K x = r and int p_h = 0.  Pinned
+    without the oracle's LU: the minimum-norm least-squares solution of the
+    dense K (SVD) moved along n until int p_h = 0, with the pressure
+    integrals summing to the domain's measure."""
+    kind, n = mesh
+    v, c = W.unit_square_mesh(n) if kind == "square" else W.kuhn_cube_mesh(n)
+    h = mg.Hierarchy(v, c, 1, stokes.TH, [2])
+    D = h.levels[-1].disc
+    assert len(D.cells) == len(c)                       # the coarsest level is the input mesh
+    nf = D.n_free
+    pm = D.pressure_mask_free()
+    w = D.p_integrals[D.free[pm] - D.d * D.V.n]         # int psi_j of the free pressures
+    assert abs(w.sum() - 1.0) < 1e-12                   # |unit square| = |unit cube| = 1
+    nullv = np.zeros(nf)
+    nullv[pm] = 1.0
+    K = D.K.toarray()
+    assert np.abs(K @ nullv).max() < 1e-12 * np.abs(K).max()
+    r = np.random.default_rng(n).standard_normal(nf)
+    r[pm] -= r[pm].mean()                               # consistent: n . r = 0
+    x = h.coarse_solve(r)
+    assert np.abs(K @ x - r).max() < 1e-11 * np.abs(r).max()
+    assert abs(w @ x[pm]) < 1e-13 * np.abs(x).max()
+    y = np.linalg.lstsq(K, r, rcond=1e-12)[0]           # orthogonal to n
+    ref = y - (w @ y[pm]) / w.sum() * nullv
+    assert np.abs(x - ref).max() < 1e-10 * np.abs(ref).max()
+    # the constant null space is the only one (the border makes K uniquely solvable)
+    s = np.linalg.svd(K, compute_uv=False)
+    assert s[-1] < 1e-12 * s[0] < s[-2]
+
+
+def test_tight_fgmres_reaches_the_discrete_solution():
+    """FGMRES-phMG run to a relative residual of 1e-14 (with the V(2,2)
+    relaxation on [0.5, 2.0] lambda_hat) gives the discrete solution of
+    Eq. 2.3 on the 16x16 P4/P3 problem: u and the zero-mean p agree with the
+    bordered sparse LU solve (with one refinement step) to 1e-11, relative to
+    their max norms.  The GPU parity test of the full-size P4/P3 problem
+    compares with this tight oracle solve."""
+    v, c = W.unit_square_mesh(8)
+    h = mg.Hierarchy(v, c, 1, stokes.TH, [4, 2],
+                     opts=mg.Options(nu_p=2, nu_h=2, cheb_lo=0.5, cheb_hi=2.0, eig_steps=8))
+    D = h.levels[0].disc
+    f = W.nodal_forcing(D.V.n, D.d, 0)
+    full, its, hist, b, x = mg.solve(h, f, None, tol=1e-14)
+    assert hist[-1] <= 1e-14 and its < 30
+    xd = stokes.zero_mean_pressure(D, stokes.expand(D, stokes.direct_solve(D, b), np.zeros(D.n_full)))
+    nu = D.d * D.V.n
+    assert np.abs(full[:nu] - xd[:nu]).max() < 1e-11 * np.abs(xd[:nu]).max()
+    assert np.abs(full[nu:] - xd[nu:]).max() < 1e-11 * np.abs(xd[nu:]).max()

@@ -8,6 +8,7 @@ DoFs, so both the shared-memory kernel and the global-memory kernel (whose
 pivot workspace lives in the library's fixed scratch array) run.  This file
 is collected last on purpose."""
 import ctypes
+import threading
 from ctypes import byref, c_int, c_void_p
 
 import numpy as np
@@ -23,9 +24,9 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10   # the tolerance of the patch-inverse parity test (cond * eps)
 
 
-def _call(sizes, mats):
+def _call(sizes, mats, stream=None):
     first = c_int(-2)
-    stream = c_void_p(torch.cuda.current_stream().cuda_stream)
+    stream = c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
     rc = P.lib().stokes_batched_inverse_noalloc(len(sizes), sizes.ctypes.data_as(c_void_p),
                                                 c_void_p(mats.data_ptr()), byref(first), stream)
     return rc, first.value
@@ -71,3 +72,50 @@ def test_noalloc_rejects_oversized_and_reports_singular():
     rc, fs = _call(sizes, m)
     assert rc == -3 and fs == 1
     assert torch.equal(m[:9].cpu(), torch.eye(3, dtype=torch.float64).reshape(-1))
+
+
+def test_noalloc_concurrent_host_threads():
+    """Two host threads call the entry point at the same time, each on its
+    own stream with its own patch sizes and matrices (ctypes releases the
+    interpreter lock during the call).  The calls share the static host
+    staging arrays and the device scratch; the entry point serialises them,
+    so every result is still the inverse of that thread's own matrices."""
+    v, c = W.kuhn_cube_mesh(2)
+    h = P.StokesMG(v, c, 1, 0, 3, hierarchy=P.HIER_EXPLICIT, schedule=[3, 2])
+    off, _ = h.patches(0)
+    sizes = np.ascontiguousarray(np.diff(off), dtype=np.int32)
+    K = h.patch_matrices(0)
+    ref = h.patch_inverses(0)
+    h.close()
+    # thread 0: every patch of the level; thread 1: the first half of the
+    # patches, scaled by 2 (its inverses are the references halved)
+    half = len(sizes) // 2
+    n_half = int((sizes[:half].astype(np.int64) ** 2).sum())
+    jobs = [(sizes, K, ref), (np.ascontiguousarray(sizes[:half]), 2.0 * K[:n_half], 0.5 * ref[:n_half])]
+    errors = [None, None]
+
+    def work(t):
+        sz, mat, want = jobs[t]
+        st = torch.cuda.Stream()
+        try:
+            for _ in range(3):
+                with torch.cuda.stream(st):
+                    m = torch.tensor(mat, device="cuda")
+                st.synchronize()
+                rc, fs = _call(sz, m, st)
+                assert rc == 0 and fs == -1, (rc, fs)
+                got = m.cpu().numpy()
+                pos = 0
+                for n in sz:
+                    a, b = got[pos:pos + n * n], want[pos:pos + n * n]
+                    assert np.abs(a - b).max() <= TOL * np.abs(b).max()
+                    pos += n * n
+        except Exception as e:  # noqa: BLE001
+            errors[t] = e
+
+    th = [threading.Thread(target=work, args=(t,)) for t in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert errors == [None, None], errors

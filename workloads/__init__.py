@@ -178,6 +178,12 @@ def workload(name: str) -> Workload:
         # the patches (a small case for profiling the batched kernels)
         v, c = kuhn_cube_mesh(4)
         return Workload(name, v, c, 1, TH, 3, [3, 2])
+    if name in ("th_p6_32x32", "th_p8_32x32"):
+        # high order on the 32 x 32 square; the schedule is Fig. 7's gradual
+        # one (6 -> 4 -> 2, 8 -> 5 -> 2), the direct k -> 2 is the comparison
+        k = int(name[4])
+        v, c = unit_square_mesh(8)
+        return Workload(name, v, c, 2, TH, k, [k, 4, 2] if k <= 7 else [k, 5, 2])
     if name == "th_p3_128x128_nu":
         v, c = unit_square_mesh(8)
         return Workload(name, v, c, 4, TH, 3, [3, 2], nu_cells=True)
