@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single", action="store_true",
                     help="one mixed-precision setup + solve and exit (profiling driver)")
+    ap.add_argument("--warmup-single", action="store_true",
+                    help="with --single: run --warmup untimed steps before the single step")
+    ap.add_argument("--fp64-probe-only", action="store_true",
+                    help="only the FP64 pipe peak probe, over launch shapes")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--relaxation", default="v22", choices=sorted(RELAX),
                     help="v22: Chebyshev(2) on [0.5, 2] lmax pre and post; v11: Chebyshev(1) on [0.1, 1.1] lmax")
@@ -808,6 +812,14 @@ def main():
     if a.adjoint_only:
         print(json.dumps(adjoint_section(a, P, W, dev, stream, flush)))
         return
+    if a.fp64_probe_only:
+        out = {}
+        P._binding.probe_fp64_peak(1 << 12, 2, stream=stream.cuda_stream)
+        for bps in (1, 2, 4, 8):
+            r = sorted(P._binding.probe_fp64_peak(1 << 17, bps, stream=stream.cuda_stream)[0] for _ in range(3))
+            out[f"ctas_per_sm_{bps}"] = r[1]
+        print(json.dumps({"fp64_probe_tflops": out}))
+        return
     if a.highk_only:
         print(json.dumps(highk_section(a, P, W, dev, stream, flush)))
         return
@@ -819,6 +831,9 @@ def main():
         print(json.dumps(res))
         return
     if a.single:
+        # a.warmup untimed steps first (STOKES_TRACE=1 then also traces warm setups)
+        for _ in range(a.warmup if a.warmup_single else 0):
+            one_step(P.MIXED if a.precision == "mixed" else P.FP64)
         ms, its, rel, st, _ = one_step(P.MIXED if a.precision == "mixed" else P.FP64)
         torch.cuda.synchronize(dev)
         print(json.dumps({"single_step_ms": ms, "iterations": its, "relres": rel,
@@ -934,26 +949,35 @@ def main():
     # (2 n_i^3 flop per patch; FP64 ALU bound on GB300)
     sizes = []
     flops_gj = 0.0
-    # algorithmic flops of the saddle block inverse per patch (n_v velocity
-    # nodes per component, n_p pressures, d components), symmetric version:
+    # algorithmic flops of the factored saddle block inverse per patch (n_v
+    # velocity nodes per component, n_p pressures, d components):
     #   n_v^3 (sweep of L, upper triangle) + 2 d n_v^2 n_p (W = L^-1 B^T)
-    #   + d n_v n_p^2 (S = B W, upper) + n_p^3 (sweep of S) + 2 d n_v n_p^2
-    #   (X = W S^-1) + d^2 n_v^2 n_p (velocity block, upper triangle)
+    #   + d n_v n_p^2 (S = B W, upper) + n_p^3 (sweep of S);
+    # the stored form is (L^-1, W, S^-1), so X = W S^-1 and the explicit
+    # velocity block are not formed
+    # algorithmic bytes of one FP32 saddle apply per patch: L^-1, W and S^-1
+    # read once (leading dimensions rounded up to 4), the gathered residual,
+    # the weights and the result (3 n_i floats)
     probe = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric,
                        hierarchy=P.HIER_EXPLICIT, schedule=w.schedule, host_only=1)
     flops_levels = []
+    apply_bytes = []
+    up4 = lambda x: (x + 3) // 4 * 4  # noqa: E731
     for li in range(stats["n_levels"] - 1):
         off, dofs = probe.patches(li)
         _, comp, _ = probe.level_dofs(li)
         cd = comp[dofs]
         f = 0.0
+        by = 0.0
         for pi in range(len(off) - 1):
             c = cd[off[pi]:off[pi + 1]]
             nv = float((c == 0).sum())
             npr = float((c == d).sum())
-            f += (nv ** 3 + 2 * d * nv * nv * npr + d * nv * npr * npr + npr ** 3 + 2 * d * nv * npr * npr
-                  + d * d * nv * nv * npr)
+            f += nv ** 3 + 2 * d * nv * nv * npr + d * nv * npr * npr + npr ** 3
+            nvi, npi = int(nv), int(npr)
+            by += 4.0 * (up4(nvi) * nvi + up4(d * nvi) * npi + up4(npi) * npi) + 12.0 * (d * nvi + npi)
         flops_levels.append(f)
+        apply_bytes.append(by)
         sizes.append(np.diff(off))
     flops_gj = sum(flops_levels)
     probe.close()
@@ -970,11 +994,10 @@ def main():
     achieved_gj = flops_gj / (gj_ms_per_step * 1e-3) / 1e12 if gj_ms_per_step > 0 else None
     # DRAM bytes of that launch from one ncu capture of the same kernel and
     # workload (dram__bytes_read.sum + dram__bytes_write.sum)
-    traffic_gj0 = (288.104448 + 968.318976) * 1e6 if a.workload == "th_p4_64x64" else None
-    # level-0 FP32 patch apply: algorithmic bytes = sum n_i^2 * 4 (inverses)
-    # + 3 * sum n_i * 4 (gathered residual, weights, result)
-    n_i = sizes[0].astype(np.float64)
-    patch_bytes = 4.0 * float((n_i ** 2).sum()) + 12.0 * float(n_i.sum())
+    # (None until the current kernel has been captured)
+    traffic_gj0 = None
+    # level-0 FP32 saddle apply: algorithmic bytes (above)
+    patch_bytes = apply_bytes[0]
     patch_gbs = patch_bytes / (patch_ms * 1e-3) / 1e9 if patch_ms > 0 else None
     line = {
         "metric": METRIC, "value": ms_max, "unit": "ms", "n_gpus": world, "steps": a.steps,
@@ -994,7 +1017,8 @@ def main():
         "fp64": {"value": sum(x[0] for x in f64) / len(f64), "unit": "ms", "iterations": f64[-1][1],
                  "setup_ms": f64[-1][3]["t_total_ms"]},
         "gpu_launches": int(launches / a.steps),
-        "roofline": {"kernel": "saddle_inverse_smem, level-0 launch (4225 Vanka patches, FP64 saddle block inverse)",
+        "roofline": {"kernel": "saddle_inverse_smem, level-0 launch (4225 Vanka patches, FP64 factored saddle block "
+                               "inverse)",
                      "bound": "alu", "achieved": achieved_gj0, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                      "frac": (achieved_gj0 / fp64_peak_tflops) if achieved_gj0 else None,
                      "traffic": traffic_gj0,
@@ -1006,7 +1030,8 @@ def main():
                      "flop_per_launch": flops_levels[0], "ms_per_launch": gj0_ms,
                      "all_levels": {"launches_per_step": gj_launches_per_step, "ms_per_step": gj_ms_per_step,
                                     "flop_per_step": flops_gj, "achieved": achieved_gj}},
-        "roofline_solve": {"kernel": "patch_apply_f32, level 0 (one ASM sweep)", "bound": "hbm",
+        "roofline_solve": {"kernel": "saddle_apply_f32, level 0 (one ASM sweep over the factored FP32 inverses)",
+                           "bound": "hbm",
                            "achieved": patch_gbs, "peak": hbm, "unit": "GB/s",
                            "frac": (patch_gbs / hbm) if patch_gbs else None, "bytes_per_launch": patch_bytes,
                            "us_per_launch": 1e3 * patch_ms, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},

@@ -582,8 +582,15 @@ __device__ void sweep_spd(double* A, int n, int lda, double* ck, double* cs, dou
 // (symmetric) inverse is formed on its upper triangle and every value written
 // to both of its positions: column-major padded FP64 / FP32 and, if back,
 // row-major into K.
+// Factored form (fac64 / fac32, VEC = 2 / 4): per patch, column-major with
+// leading dimensions rounded up to VEC, padding zero:
+//   Li [ldl][nv]  (ldl = nv up to VEC), W [ldw][np] (ldw = d nv up to VEC),
+//   Si [lds][np]  (lds = np up to VEC),
+// from which K_i^{-1} r = (blockdiag(Li) r_u + W s, -s), s = Si (r_p - W^T r_u)
+// (saddle_apply).  With no explicit output (inv64, inv32 NULL, back 0) the
+// products X = W Si and blockdiag(Li) - X W^T are skipped.
 __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, double* inv64, float* inv32,
-                            int back, int* status) {
+                            double* fac64, float* fac32, int back, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int np = n - d * nv, npp = np | 1, dnv = d * nv;
@@ -601,6 +608,20 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
         for (int q = lane; q < np; q += 32) Bt[(long long)r * npp + q] = K[(long long)r * n + dnv + q];
     __syncthreads();
     sweep_spd(Ls, nv, nv, ck, cs, rinv, status);
+    const bool fac = fac64 || fac32;
+    const int ldl = fac64 ? (nv + 1) & ~1 : (nv + 3) & ~3;
+    const int ldw = fac64 ? (dnv + 1) & ~1 : (dnv + 3) & ~3;
+    const int lds = fac64 ? (np + 1) & ~1 : (np + 3) & ~3;
+    if (fac) {
+        // Li (symmetric, full after the sweep)
+        const int tot = nv * ldl;
+        for (int t = tid; t < tot; t += nt) {
+            const int b = t / ldl, a = t - b * ldl;
+            const double v = a < nv ? Ls[a * nv + b] : 0.0;
+            if (fac64) fac64[t] = v;
+            if (fac32) fac32[t] = (float)v;
+        }
+    }
     // W_c = Li B_c^T: entry t = (r, q), r = c nv + a
     const int nw_out = dnv * np;
     for (int t = tid; t < nw_out; t += nt) {
@@ -613,6 +634,16 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
         Wm[(long long)r * npp + q] = s;
     }
     __syncthreads();
+    if (fac) {
+        const long long o = (long long)ldl * nv;
+        const int tot = np * ldw;
+        for (int t = tid; t < tot; t += nt) {
+            const int q = t / ldw, r = t - q * ldw;
+            const double v = r < dnv ? Wm[(long long)r * npp + q] : 0.0;
+            if (fac64) fac64[o + t] = v;
+            if (fac32) fac32[o + t] = (float)v;
+        }
+    }
     // S = sum_c B_c W_c, upper triangle q <= r
     const int ns = np * (np + 1) / 2;
     for (int t = tid; t < ns; t += nt) {
@@ -625,6 +656,17 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
     }
     __syncthreads();
     sweep_spd(Ss, np, np, ck, cs, rinv, status);
+    if (fac) {
+        const long long o = (long long)ldl * nv + (long long)ldw * np;
+        const int tot = np * lds;
+        for (int t = tid; t < tot; t += nt) {
+            const int r = t / lds, q = t - r * lds;
+            const double v = q < np ? Ss[q * np + r] : 0.0;
+            if (fac64) fac64[o + t] = v;
+            if (fac32) fac32[o + t] = (float)v;
+        }
+    }
+    if (!inv64 && !inv32 && !back) return;      // factored form only
     // X_c = W_c Si (overwrites Bt)
     for (int t = tid; t < nw_out; t += nt) {
         const int r = t / np, q = t - r * np;
@@ -678,7 +720,9 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
                                                            const int* __restrict__ pnv, const long long* __restrict__ moff,
                                                            double* __restrict__ work, const long long* __restrict__ off64,
                                                            double* __restrict__ inv64, const long long* __restrict__ off32,
-                                                           float* __restrict__ inv32, int back, long long max_scratch,
+                                                           float* __restrict__ inv32, const long long* __restrict__ foff64,
+                                                           double* __restrict__ fac64, const long long* __restrict__ foff32,
+                                                           float* __restrict__ fac32, int back, long long max_scratch,
                                                            int* __restrict__ status) {
     extern __shared__ double sscr[];
     const int p = blockIdx.x;
@@ -688,7 +732,7 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
     if (threadIdx.x == 0) st = 0;
     __syncthreads();
     saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr, inv32 ? inv32 + off32[p] : nullptr,
-                back, &st);
+                fac64 ? fac64 + foff64[p] : nullptr, fac32 ? fac32 + foff32[p] : nullptr, back, &st);
     __syncthreads();
     if (threadIdx.x == 0) status[p] = st;
 }
@@ -697,7 +741,9 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
                                                              const int* __restrict__ pnv, const long long* __restrict__ moff,
                                                              double* __restrict__ work, const long long* __restrict__ off64,
                                                              double* __restrict__ inv64, const long long* __restrict__ off32,
-                                                             float* __restrict__ inv32, int back, long long max_scratch,
+                                                             float* __restrict__ inv32, const long long* __restrict__ foff64,
+                                                             double* __restrict__ fac64, const long long* __restrict__ foff32,
+                                                             float* __restrict__ fac32, int back, long long max_scratch,
                                                              const long long* __restrict__ soff, double* __restrict__ scratch,
                                                              int* __restrict__ status) {
     const int p = blockIdx.x;
@@ -707,7 +753,8 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
     if (threadIdx.x == 0) st = 0;
     __syncthreads();
     saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,
-                inv32 ? inv32 + off32[p] : nullptr, back, &st);
+                inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
+                fac32 ? fac32 + foff32[p] : nullptr, back, &st);
     __syncthreads();
     if (threadIdx.x == 0) status[p] = st;
 }
@@ -803,6 +850,162 @@ __global__ void __launch_bounds__(128) patch_apply_f64(int npatch, const int* __
     double2* red = reinterpret_cast<double2*>(smem_pa);
     double* xs = reinterpret_cast<double*>(smem_pa + sizeof(double2) * (blockDim.x + 4));
     patch_apply_body<double, double2, 2>(blockIdx.x, poff, pdofs, ioff, inv, r, wt, Y, xs, red);
+}
+
+// One ASM sweep with factored saddle inverses (saddle_core's factored form):
+//   t = r_p - W^T r_u,  s = Si t,  z_u = blockdiag(Li) r_u + W s,  z_p = -s,
+//   Y[poff[i] + a] = w[dof_a] z_a.
+// One CTA of SADDLE_APPLY_THREADS threads per patch.  The gathered residual
+// and W are staged in shared memory (W is used twice); Li is streamed from
+// HBM once, as in patch_apply_body: a thread owns VEC consecutive rows and
+// accumulates them for the d components at once, G groups of row owners
+// split the columns, eight 16-byte loads in flight per thread, the groups'
+// partial sums added in a fixed order.
+__device__ __forceinline__ float vcomp(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vcomp(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ float4 mkvec(const float* a, float4*) { return make_float4(a[0], a[1], a[2], a[3]); }
+__device__ __forceinline__ double2 mkvec(const double* a, double2*) { return make_double2(a[0], a[1]); }
+
+template <typename T, typename V, int VEC>
+__device__ __forceinline__ void saddle_apply_body(int p, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                                  const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                                  const T* __restrict__ fac, const T* __restrict__ r,
+                                                  const T* __restrict__ wt, T* __restrict__ Y, int xs_len, int ws_len,
+                                                  unsigned char* smem) {
+    constexpr int NT = SADDLE_APPLY_THREADS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s0 = poff[p], n = poff[p + 1] - s0, nv = pnv[p], dnv = d * nv, np = n - dnv;
+    if (n == 0) return;
+    const int ldl = (nv + VEC - 1) / VEC * VEC, ldw = (dnv + VEC - 1) / VEC * VEC;
+    const T* Li = fac + foff[p];
+    const T* Wg = Li + (long long)ldl * nv;
+    const T* Sg = Wg + (long long)ldw * np;
+    V* red = reinterpret_cast<V*>(smem);                         // [NT][3]
+    T* ws = reinterpret_cast<T*>(smem + sizeof(V) * NT * 3);     // [ws_len]   W, column-major
+    T* xs = ws + ws_len;                                         // [xs_len]   gathered r
+    T* ys = xs + xs_len;                                         // [xs_len]   blockdiag(Li) r_u
+    T* tq = ys + xs_len;                                         // [xs_len]   t
+    T* sq = tq + xs_len;                                         // [xs_len]   s
+    for (int a = tid; a < n; a += NT) xs[a] = r[pdofs[s0 + a]];
+    {
+        const V* wv = reinterpret_cast<const V*>(Wg);
+        V* wsv = reinterpret_cast<V*>(ws);
+        const int nvec = ldw * np / VEC;
+        for (int t = tid; t < nvec; t += NT) wsv[t] = __ldcs(wv + t);
+    }
+    __syncthreads();
+    // t = r_p - W^T r_u: one warp per pressure row, lanes over the velocity DoFs
+    for (int q = warp; q < np; q += NT / 32) {
+        const T* wc = ws + (long long)q * ldw;
+        T acc = 0;
+        for (int a = lane; a < dnv; a += 32) acc += wc[a] * xs[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) tq[q] = xs[dnv + q] - acc;
+    }
+    __syncthreads();
+    // s = Si t (Si symmetric: entry (q, x) at Sg[x * lds + q]) and
+    // y_c = Li r_c for every component c
+    const int lds = (np + VEC - 1) / VEC * VEC;
+    for (int q = tid; q < np; q += NT) {
+        T acc = 0;
+        for (int x = 0; x < np; ++x) acc += __ldcs(Sg + (long long)x * lds + q) * tq[x];
+        sq[q] = acc;
+    }
+    const int ldv = ldl / VEC;
+    const int G = ldv >= NT ? 1 : NT / ldv;
+    const V* base = reinterpret_cast<const V*>(Li);
+    for (int t0 = 0; t0 < ldv; t0 += NT) {
+        const int rg = t0 + (G == 1 ? tid : tid % ldv), g = G == 1 ? 0 : tid / ldv;
+        T acc[3][VEC];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[c][u] = 0;
+        const bool own = g < G && rg < ldv;
+        if (own) {
+            const V* col = base + rg;
+            int b = g;
+            for (; b + 7 * G < nv; b += 8 * G) {
+                V v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcs(col + (long long)(b + u * G) * ldv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (c < d) {
+                            const T x = xs[c * nv + b + u * G];
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) acc[c][e] += vcomp(v[u], e) * x;
+                        }
+                    }
+            }
+            for (; b < nv; b += G) {
+                const V v = __ldcs(col + (long long)b * ldv);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (c < d) {
+                        const T x = xs[c * nv + b];
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) acc[c][e] += vcomp(v, e) * x;
+                    }
+            }
+        }
+        if (G > 1) {
+            if (own)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (c < d) red[(g * ldv + (rg - t0)) * 3 + c] = mkvec(acc[c], (V*)nullptr);
+            __syncthreads();
+            if (tid < ldv) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (c < d) {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) acc[c][e] = vcomp(red[tid * 3 + c], e);
+                        for (int gg = 1; gg < G; ++gg) {
+                            const V q = red[(gg * ldv + tid) * 3 + c];
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) acc[c][e] += vcomp(q, e);
+                        }
+                    }
+            }
+        }
+        if (g == 0 && rg < ldv) {
+            const int row0 = VEC * rg;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (c < d)
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e)
+                        if (row0 + e < nv) ys[c * nv + row0 + e] = acc[c][e];
+        }
+        __syncthreads();
+    }
+    // z_u = y + W s, z_p = -s, weighted
+    for (int a = tid; a < dnv; a += NT) {
+        T z = ys[a];
+        for (int q = 0; q < np; ++q) z += ws[(long long)q * ldw + a] * sq[q];
+        Y[s0 + a] = wt[pdofs[s0 + a]] * z;
+    }
+    for (int q = tid; q < np; q += NT) Y[s0 + dnv + q] = -wt[pdofs[s0 + dnv + q]] * sq[q];
+}
+
+__global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f32(
+    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+    const long long* __restrict__ foff, const float* __restrict__ fac, const float* __restrict__ r,
+    const float* __restrict__ wt, float* __restrict__ Y, int xs_len, int ws_len) {
+    extern __shared__ __align__(16) unsigned char smem_sa[];
+    saddle_apply_body<float, float4, 4>(blockIdx.x, d, poff, pdofs, pnv, foff, fac, r, wt, Y, xs_len, ws_len, smem_sa);
+}
+
+__global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f64(
+    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+    const long long* __restrict__ foff, const double* __restrict__ fac, const double* __restrict__ r,
+    const double* __restrict__ wt, double* __restrict__ Y, int xs_len, int ws_len) {
+    extern __shared__ __align__(16) unsigned char smem_sa[];
+    saddle_apply_body<double, double2, 2>(blockIdx.x, d, poff, pdofs, pnv, foff, fac, r, wt, Y, xs_len, ws_len, smem_sa);
 }
 
 // ---------------------------------------------------------- coarse GJ ---

@@ -154,17 +154,47 @@ __host__ __device__ inline long long saddle_scratch(int d, int n, int nv) {
     return (long long)nv * nv + 2LL * d * nv * npp + (long long)np * np + 3LL * mx + 2;
 }
 constexpr long long SADDLE_SMEM_MAX_DOUBLES = 25600;   // 200 KB of shared memory
+// Outputs (each may be NULL): explicit inverses inv64 / inv32 (column-major,
+// leading dimension n rounded up to 2 / 4), the factored form fac64 / fac32
+// at foff64[p] / foff32[p] (saddle_factor_len), and, if back, the explicit
+// inverse row-major in place of K_i.
 __global__ void saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
                                     const long long* __restrict__ moff, double* __restrict__ work,
                                     const long long* __restrict__ off64, double* __restrict__ inv64,
-                                    const long long* __restrict__ off32, float* __restrict__ inv32, int back,
+                                    const long long* __restrict__ off32, float* __restrict__ inv32,
+                                    const long long* __restrict__ foff64, double* __restrict__ fac64,
+                                    const long long* __restrict__ foff32, float* __restrict__ fac32, int back,
                                     long long max_scratch, int* __restrict__ status);
 __global__ void saddle_inverse_global(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
                                       const long long* __restrict__ moff, double* __restrict__ work,
                                       const long long* __restrict__ off64, double* __restrict__ inv64,
-                                      const long long* __restrict__ off32, float* __restrict__ inv32, int back,
+                                      const long long* __restrict__ off32, float* __restrict__ inv32,
+                                      const long long* __restrict__ foff64, double* __restrict__ fac64,
+                                      const long long* __restrict__ foff32, float* __restrict__ fac32, int back,
                                       long long max_scratch, const long long* __restrict__ soff,
                                       double* __restrict__ scratch, int* __restrict__ status);
+// Elements of one patch's factored inverse (Li, W, Si with leading
+// dimensions rounded up to vec = 2 (FP64) or 4 (FP32)).
+__host__ __device__ inline long long saddle_factor_len(int d, int n, int nv, int vec) {
+    const int np = n - d * nv;
+    const long long ldl = (nv + vec - 1) / vec * vec, ldw = (d * nv + vec - 1) / vec * vec,
+                    lds = (np + vec - 1) / vec * vec;
+    return ldl * nv + ldw * np + lds * np;
+}
+// Shared memory (bytes) of saddle_apply_*: partial sums, W, and five
+// vectors of xs_len (>= the largest patch) elements.
+constexpr int SADDLE_APPLY_THREADS = 128;
+__host__ __device__ inline size_t saddle_apply_smem(int elem_bytes, int vec, long long ws_len, long long xs_len) {
+    return (size_t)elem_bytes * vec * SADDLE_APPLY_THREADS * 3 + (size_t)elem_bytes * (ws_len + 5 * xs_len);
+}
+__global__ void saddle_apply_f32(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                 const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                 const float* __restrict__ fac, const float* __restrict__ r, const float* __restrict__ wt,
+                                 float* __restrict__ Y, int xs_len, int ws_len);
+__global__ void saddle_apply_f64(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                 const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                 const double* __restrict__ fac, const double* __restrict__ r,
+                                 const double* __restrict__ wt, double* __restrict__ Y, int xs_len, int ws_len);
 
 // One ASM sweep (Eq. 3.4): Y[poff[i] + a] = w[dof_a] * sum_b Kinv_i[a][b] r[dof_b].
 // FP32: float4 loads of 4 consecutive rows per thread; FP64: double2 loads

@@ -173,8 +173,17 @@ struct DevLevel {
     long long saddle_global = 0;    // total scratch (doubles) of the others
     long long* scoff = nullptr;     // their offsets into the global scratch
     long long ninv64 = 0, ninv32 = 0;
-    double* inv64 = nullptr;
+    double* inv64 = nullptr;            // explicit inverses (Gauss-Jordan patches; FP32 also for the batched path)
     float* inv32 = nullptr;
+    // factored saddle inverses (Li, W, Si per patch; saddle_core), the stored
+    // form of the saddle-block solver: FP64 on FP64 handles, FP32 on MIXED
+    bool factored = false;
+    long long *foff64 = nullptr, *foff32 = nullptr;
+    long long nfac64 = 0, nfac32 = 0;
+    double* fac64 = nullptr;
+    float* fac32 = nullptr;
+    int sa_xs = 0;                      // saddle apply: largest patch
+    long long sa_ws64 = 0, sa_ws32 = 0; // saddle apply: largest W (elements)
     double* wt64 = nullptr;
     float* wt32 = nullptr;
     int *soff = nullptr, *sidx = nullptr;
@@ -521,10 +530,19 @@ void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, doub
 
 template <>
 void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
-    const size_t smem = sizeof(float4) * (128 + 4) + sizeof(float) * l.maxn;
-    launch(h, PK_PATCH, s, [&] {
-        skern::patch_apply_f32<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff32, l.inv32, r, l.wt32, l.Y32);
-    });
+    if (l.fac32) {
+        const size_t smem = skern::saddle_apply_smem(4, 4, l.sa_ws32, l.sa_xs);
+        launch(h, PK_PATCH, s, [&] {
+            skern::saddle_apply_f32<<<l.npatch, skern::SADDLE_APPLY_THREADS, smem, s>>>(
+                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_xs, (int)l.sa_ws32);
+        });
+    } else {
+        if (!l.inv32) throw StokesError(STOKES_EINVAL, "no FP32 patch inverses on this handle (FP64 handle)");
+        const size_t smem = sizeof(float4) * (128 + 4) + sizeof(float) * l.maxn;
+        launch(h, PK_PATCH, s, [&] {
+            skern::patch_apply_f32<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff32, l.inv32, r, l.wt32, l.Y32);
+        });
+    }
     launch(h, PK_PULL, s, [&] {
         skern::pull_scatter<float><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y32, (float)alpha, (float)beta, out);
     });
@@ -532,10 +550,19 @@ void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, dou
 
 template <>
 void asm_apply<double>(stokes_mg* h, DevLevel& l, const double* r, double* out, double alpha, double beta, cudaStream_t s) {
-    const size_t smem = sizeof(double2) * (128 + 4) + sizeof(double) * l.maxn;
-    launch(h, PK_PATCH, s, [&] {
-        skern::patch_apply_f64<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff64, l.inv64, r, l.wt64, l.Y64);
-    });
+    if (l.fac64) {
+        const size_t smem = skern::saddle_apply_smem(8, 2, l.sa_ws64, l.sa_xs);
+        launch(h, PK_PATCH, s, [&] {
+            skern::saddle_apply_f64<<<l.npatch, skern::SADDLE_APPLY_THREADS, smem, s>>>(
+                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_xs, (int)l.sa_ws64);
+        });
+    } else {
+        if (!l.inv64) throw StokesError(STOKES_EINVAL, "no FP64 patch inverses on this handle (MIXED handle)");
+        const size_t smem = sizeof(double2) * (128 + 4) + sizeof(double) * l.maxn;
+        launch(h, PK_PATCH, s, [&] {
+            skern::patch_apply_f64<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff64, l.inv64, r, l.wt64, l.Y64);
+        });
+    }
     launch(h, PK_PULL, s, [&] {
         skern::pull_scatter<double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y64, alpha, beta, out);
     });
@@ -792,6 +819,32 @@ void b_pcycle(stokes_mg* h, int li, int gm, int m, const float* b, float* e, cud
     b_smooth(h, li, gm, m, b, e, false, nu, s);
 }
 
+// What gather_and_invert writes: the handle's stored form (factored saddle
+// inverses or explicit inverses, in the handle's precision), the explicit
+// inverse row-major in place of the gathered block (work), or explicit FP32
+// inverses into l.inv32 (the batched path's operand).
+enum InvOut { INV_STORE = 0, INV_BACK = 1, INV_EXPLICIT32 = 2 };
+void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status, cudaStream_t s);
+
+// The batched patch GEMM multiplies by explicit FP32 inverses.  A handle
+// that stores factored saddle inverses builds them on first use (one gather
+// and explicit saddle inversion per relaxed level, kept afterwards).
+void ensure_explicit32(stokes_mg* h, cudaStream_t s) {
+    const int nl = (int)h->L.size();
+    for (int li = 0; li + 1 < nl; ++li) {
+        DevLevel& l = h->L[li];
+        if (l.inv32 || l.npatch == 0) continue;
+        l.inv32 = halloc<float>(h, l.ninv32);
+        double* work = palloc<double>(h->device, l.nsq, s);
+        int* status = palloc<int>(h->device, l.npatch, s);
+        CK(cudaMemsetAsync(status, 0, sizeof(int) * l.npatch, s));
+        gather_and_invert(h, li, work, INV_EXPLICIT32, status, s);
+        CK(cudaFreeAsync(work, s));
+        CK(cudaFreeAsync(status, s));
+    }
+    CK(cudaStreamSynchronize(s));
+}
+
 // interleaved work vectors of width m on every level (kept for later calls)
 void ensure_batch(stokes_mg* h, int m) {
     if (!h->bstat_h) {
@@ -812,6 +865,8 @@ void ensure_batch(stokes_mg* h, int m) {
     // per-patch tensor maps over the FP32 inverses (the tensor-core TF32
     // path), built once per handle
     if (h->tmaps.empty()) {
+        CK(cudaStreamSynchronize(h->s_up));
+        ensure_explicit32(h, h->s_up);
         h->tmaps.assign(nl, nullptr);
         for (int li = 0; li + 1 < nl; ++li) h->tmaps[li] = halloc<unsigned char>(h, sbat::tmap_bytes(h->L[li].npatch));
         CK(cudaStreamSynchronize(h->s_up));
@@ -1074,7 +1129,7 @@ int arnoldi_launch(stokes_mg* h, int li, const double* v0, int steps, double* Hs
     // the operator M^{-1} K is applied in the precision of the smoother that
     // the estimate serves (FP32 K and inverses in mixed mode); the basis and
     // its orthogonalisation stay FP64
-    const bool f32 = h->opts.precision == STOKES_MIXED && l.inv32 && l.K.v32 && l.t32 && l.u32;
+    const bool f32 = h->opts.precision == STOKES_MIXED && (l.inv32 || l.fac32) && l.K.v32 && l.t32 && l.u32;
     for (int j = 0; j < m; ++j) {
         double* w = V + (long long)(j + 1) * n;
         if (f32) {
@@ -1385,13 +1440,34 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         trace("patch maps", li, tt);
         tt = host_ms();
         l.Y64 = halloc<double>(h, l.nent);
-        l.inv64 = halloc<double>(h, l.ninv64);
+        // the stored inverses: the factored saddle form for the saddle-block
+        // solver, explicit otherwise; FP32 on MIXED handles (the V-cycle and
+        // the lambda_max estimate run in FP32 there), FP64 on FP64 handles
+        l.factored = h->opts.patch_solver == 0;
+        if (l.factored) {
+            std::vector<long long> f64(l.npatch + 1, 0), f32(l.npatch + 1, 0);
+            l.sa_xs = l.maxn;
+            for (int p = 0; p < l.npatch; ++p) {
+                const int n = HL.patch_off[p + 1] - HL.patch_off[p], nv = HL.patch_nv[p];
+                const int np = n - HL.d * nv;
+                f64[p + 1] = f64[p] + skern::saddle_factor_len(HL.d, n, nv, 2);
+                f32[p + 1] = f32[p] + skern::saddle_factor_len(HL.d, n, nv, 4);
+                l.sa_ws64 = std::max<long long>(l.sa_ws64, (long long)((HL.d * nv + 1) & ~1) * np);
+                l.sa_ws32 = std::max<long long>(l.sa_ws32, (long long)((HL.d * nv + 3) & ~3) * np);
+            }
+            l.nfac64 = f64[l.npatch];
+            l.nfac32 = f32[l.npatch];
+            if (want32) { l.foff32 = hupload(h, f32, s); l.fac32 = halloc<float>(h, l.nfac32); }
+            else { l.foff64 = hupload(h, f64, s); l.fac64 = halloc<double>(h, l.nfac64); }
+        } else if (!want32) {
+            l.inv64 = halloc<double>(h, l.ninv64);
+        }
         if (want32) {
             l.wt32 = halloc<float>(h, l.n);
             skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.wt64, l.wt32);
             CK(cudaGetLastError());
             l.Y32 = halloc<float>(h, l.nent);
-            l.inv32 = halloc<float>(h, l.ninv32);
+            if (!l.factored) l.inv32 = halloc<float>(h, l.ninv32);
         }
     }
     trace("patch uploads + allocs", li, tt);
@@ -1558,7 +1634,7 @@ void upload_transfers(stokes_mg* h, int li, bool want32, cudaStream_t s) {
 
 // gather K_i and invert every patch of level li; work receives the
 // row-major inverses (sum n_i^2 doubles) when keep != nullptr.
-void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* status, cudaStream_t s) {
+void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status, cudaStream_t s) {
     DevLevel& l = h->L[li];
     if (l.npatch == 0) return;
     launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(l.nsq), 256, 0, s>>>(l.nsq, 0.0, work); });
@@ -1566,11 +1642,15 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
         skern::patch_gather<<<l.npatch, 256, l.maxn * sizeof(int), s>>>(l.npatch, l.poff, l.pdofs, l.moff, l.K.rp, l.K.ci,
                                                                        l.K.v64, work);
     });
+    const bool store = out == INV_STORE;
+    double* i64 = store ? l.inv64 : nullptr;
+    float* i32 = store || out == INV_EXPLICIT32 ? l.inv32 : nullptr;
+    const int back = out == INV_BACK ? 1 : 0;
     if (h->opts.patch_solver == 0) {
         // saddle block inverse (default)
         const int d = h->dim;
-        double* i64 = store ? l.inv64 : nullptr;
-        float* i32 = store ? l.inv32 : nullptr;
+        double* f64 = store ? l.fac64 : nullptr;
+        float* f32 = store ? l.fac32 : nullptr;
         if (l.saddle_smem > 0) {
             const size_t smem = (size_t)l.saddle_smem * sizeof(double);
             // one upper bound for every level (levels launch from one thread
@@ -1579,19 +1659,20 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
                                     (int)(skern::SADDLE_SMEM_MAX_DOUBLES * sizeof(double))));
             launch(h, PK_GJ, s, [&] {
                 skern::saddle_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
-                                                                       l.ioff32, i32, store ? 0 : 1,
+                                                                       l.ioff32, i32, l.foff64, f64, l.foff32, f32, back,
                                                                        skern::SADDLE_SMEM_MAX_DOUBLES, status);
             });
         }
         if (l.saddle_global > 0) {
-            double* scr = dalloc<double>(l.saddle_global);
+            // scratch of the patches too large for shared memory, from the
+            // stream-ordered pool (freed on the same stream, no host wait)
+            double* scr = palloc<double>(h->device, l.saddle_global, s);
             launch(h, PK_GJ, s, [&] {
                 skern::saddle_inverse_global<<<l.npatch, 256, 0, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
-                                                                      l.ioff32, i32, store ? 0 : 1,
+                                                                      l.ioff32, i32, l.foff64, f64, l.foff32, f32, back,
                                                                       skern::SADDLE_SMEM_MAX_DOUBLES, l.scoff, scr, status);
             });
-            CK(cudaStreamSynchronize(s));
-            cudaFree(scr);
+            CK(cudaFreeAsync(scr, s));
         }
         return;
     }
@@ -1603,21 +1684,18 @@ void gather_and_invert(stokes_mg* h, int li, double* work, bool store, int* stat
                                 (int)((size_t)gmax * gmax * sizeof(double) + gmax * sizeof(double) + gmax * sizeof(int) + 64)));
     }
     launch(h, PK_GJ, s, [&] {
-        skern::gj_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, l.poff, l.moff, work, store ? l.ioff64 : nullptr,
-                                                           store ? l.inv64 : nullptr, store ? l.ioff32 : nullptr,
-                                                           store ? l.inv32 : nullptr, status, 0);
+        skern::gj_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, l.poff, l.moff, work, i64 ? l.ioff64 : nullptr, i64,
+                                                           i32 ? l.ioff32 : nullptr, i32, status, 0);
     });
     if (l.maxn > skern::GJ_SMEM_MAX_N) {
-        int* ipiv = dalloc<int>(l.nent);
-        double* col = dalloc<double>(l.nent);
+        int* ipiv = palloc<int>(h->device, l.nent, s);
+        double* col = palloc<double>(h->device, l.nent, s);
         launch(h, PK_GJ, s, [&] {
-            skern::gj_inverse_global<<<l.npatch, 512, 0, s>>>(l.npatch, l.poff, l.moff, work, store ? l.ioff64 : nullptr,
-                                                              store ? l.inv64 : nullptr, store ? l.ioff32 : nullptr,
-                                                              store ? l.inv32 : nullptr, status, ipiv, col);
+            skern::gj_inverse_global<<<l.npatch, 512, 0, s>>>(l.npatch, l.poff, l.moff, work, i64 ? l.ioff64 : nullptr, i64,
+                                                              i32 ? l.ioff32 : nullptr, i32, status, ipiv, col);
         });
-        CK(cudaStreamSynchronize(s));
-        cudaFree(ipiv);
-        cudaFree(col);
+        CK(cudaFreeAsync(ipiv, s));
+        CK(cudaFreeAsync(col, s));
     }
 }
 
@@ -1633,7 +1711,7 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
     pp.stream = s;   // freed on the same stream after finish_patches synchronised it
     h->pending.push_back(pp);
     CK(cudaMemsetAsync(pp.status, 0, sizeof(int) * l.npatch, s));
-    gather_and_invert(h, li, pp.work, true, pp.status, s);
+    gather_and_invert(h, li, pp.work, INV_STORE, pp.status, s);
 }
 
 void free_pending(stokes_mg* h) {
@@ -2911,7 +2989,7 @@ int stokes_mg_patch_inverses(stokes_mg_t h, int level, double* out, void* stream
         int* status = dalloc<int>(l.npatch);
         cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int) * l.npatch, s);
         try {
-            gather_and_invert(h, level, work, false, status, s);
+            gather_and_invert(h, level, work, INV_BACK, status, s);
         } catch (...) {
             cudaFree(work);
             cudaFree(status);
@@ -2971,7 +3049,7 @@ int stokes_mg_asm(stokes_mg_t h, int level, const double* r, double* z, int prec
         if (precision == STOKES_FP64) {
             asm_apply<double>(h, l, r, z, 1.0, 0.0, s);
         } else {
-            require(l.inv32, "mixed precision needs a MIXED handle");
+            require(l.inv32 || l.fac32, "mixed precision needs a MIXED handle");
             Tmp32 tr(l.n), tz(l.n);
             skern::convert_vec<float, double><<<grid_for(l.n), 256, 0, s>>>(l.n, r, tr.p);
             asm_apply<float>(h, l, tr.p, tz.p, 1.0, 0.0, s);
