@@ -887,7 +887,10 @@ __device__ __forceinline__ void saddle_apply_body(int p, int d, const int* __res
     T* tq = ys + xs_len;                                         // [xs_len]   t
     T* sq = tq + xs_len;                                         // [xs_len]   s
     for (int a = tid; a < n; a += NT) xs[a] = r[pdofs[s0 + a]];
-    {
+    // W is staged in shared memory when the level's largest fits (ws_len > 0),
+    // else both of its uses read it from global memory (the second from cache)
+    const T* wsrc = ws_len > 0 ? ws : Wg;
+    if (ws_len > 0) {
         const V* wv = reinterpret_cast<const V*>(Wg);
         V* wsv = reinterpret_cast<V*>(ws);
         const int nvec = ldw * np / VEC;
@@ -896,7 +899,7 @@ __device__ __forceinline__ void saddle_apply_body(int p, int d, const int* __res
     __syncthreads();
     // t = r_p - W^T r_u: one warp per pressure row, lanes over the velocity DoFs
     for (int q = warp; q < np; q += NT / 32) {
-        const T* wc = ws + (long long)q * ldw;
+        const T* wc = wsrc + (long long)q * ldw;
         T acc = 0;
         for (int a = lane; a < dnv; a += 32) acc += wc[a] * xs[a];
 #pragma unroll
@@ -986,7 +989,7 @@ __device__ __forceinline__ void saddle_apply_body(int p, int d, const int* __res
     // z_u = y + W s, z_p = -s, weighted
     for (int a = tid; a < dnv; a += NT) {
         T z = ys[a];
-        for (int q = 0; q < np; ++q) z += ws[(long long)q * ldw + a] * sq[q];
+        for (int q = 0; q < np; ++q) z += wsrc[(long long)q * ldw + a] * sq[q];
         Y[s0 + a] = wt[pdofs[s0 + a]] * z;
     }
     for (int q = tid; q < np; q += NT) Y[s0 + dnv + q] = -wt[pdofs[s0 + dnv + q]] * sq[q];
@@ -1006,6 +1009,166 @@ __global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f64(
     const double* __restrict__ wt, double* __restrict__ Y, int xs_len, int ws_len) {
     extern __shared__ __align__(16) unsigned char smem_sa[];
     saddle_apply_body<double, double2, 2>(blockIdx.x, d, poff, pdofs, pnv, foff, fac, r, wt, Y, xs_len, ws_len, smem_sa);
+}
+
+// ---- the same sweep with the factored blocks streamed by bulk copies ----
+// Persistent CTAs (SA_TMA_THREADS threads) take patches blockIdx.x,
+// blockIdx.x + gridDim.x, ...; each patch's factored block (Li, W, Si:
+// contiguous, a multiple of 16 bytes) is brought into shared memory by one
+// cp.async.bulk issued one patch ahead into the other of two buffers, so the
+// HBM stream of the next patch overlaps the arithmetic of this one.  All
+// products then read shared memory:
+//   t = r_p - W^T r_u   (one warp per pressure row, lanes over the velocity rows)
+//   s = Si t            (one thread per pressure row)
+//   y_c = Li r_c        (one thread per velocity row and component)
+//   z_u = y + W s, z_p = -s, weighted.
+// Waits on the buffers' mbarriers are bounded: after SA_WAIT_LIMIT polls the
+// CTA sets *status = 1 and returns (no hang, no trap).
+__device__ __forceinline__ uint32_t sa_smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void sa_mbar_init(uint32_t a) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool sa_mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void sa_bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void saddle_apply_tma_body(
+    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+    const long long* __restrict__ foff, const T* __restrict__ fac, const T* __restrict__ r,
+    const T* __restrict__ wt, T* __restrict__ Y, int buf_bytes, int xs_len, int* __restrict__ status,
+    unsigned char* smem_st, unsigned long long* bars, int& abort_flag) {
+    constexpr int NT = SA_TMA_THREADS;
+    constexpr int VEC = 16 / sizeof(T);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* xs = reinterpret_cast<T*>(smem_st + 2 * (size_t)buf_bytes);   // [xs_len] gathered r
+    T* ys = xs + xs_len;                                              // [xs_len] z_u
+    T* tq = ys + xs_len;                                              // [xs_len] t
+    T* sq = tq + xs_len;                                              // [xs_len] s
+    const uint32_t bar0 = sa_smem_u32(&bars[0]), bar1 = sa_smem_u32(&bars[1]);
+    if (tid == 0) {
+        sa_mbar_init(bar0);
+        sa_mbar_init(bar1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // every issue completes one phase of its buffer's barrier (an empty
+    // block arrives without a copy)
+    auto issue = [&](int p, int b) {
+        const long long o = foff[p];
+        const uint32_t bytes = (uint32_t)((foff[p + 1] - o) * (long long)sizeof(T));
+        const uint32_t bar = b ? bar1 : bar0;
+        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem_st + (size_t)b * buf_bytes), fac + o, bytes, bar);
+        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    };
+    auto wait = [&](uint32_t bar, uint32_t parity) {
+        for (long long it = 0; it < SA_WAIT_LIMIT; ++it) {
+            if (sa_mbar_try(bar, parity)) return true;
+            if (abort_flag) return false;
+        }
+        return false;
+    };
+    if (tid == 0 && (int)blockIdx.x < npatch) issue(blockIdx.x, 0);
+    int k = 0;
+    for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int pn = p + gridDim.x;
+        if (tid == 0 && pn < npatch) issue(pn, b ^ 1);
+        const int s0 = poff[p], n = poff[p + 1] - s0, nv = pnv[p], dnv = d * nv, np = n - dnv;
+        for (int a = tid; a < n; a += NT) xs[a] = r[pdofs[s0 + a]];
+        // bounded wait for this patch's block (phase k >> 1 of its buffer)
+        if (!wait(b ? bar1 : bar0, (uint32_t)((k >> 1) & 1))) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) {
+            // give up: let the prefetch in flight (if any) land, bounded, and
+            // report through *status
+            if (tid == 0) {
+                if (pn < npatch) {
+                    const uint32_t bo = b ? bar0 : bar1, po = (uint32_t)(((k + 1) >> 1) & 1);
+                    for (long long it = 0; it < SA_WAIT_LIMIT && !sa_mbar_try(bo, po); ++it) {}
+                }
+                atomicExch(status, 1);
+            }
+            return;
+        }
+        const int ldl = (nv + VEC - 1) / VEC * VEC, ldw = (dnv + VEC - 1) / VEC * VEC;
+        const int lds = (np + VEC - 1) / VEC * VEC;
+        const T* Li = reinterpret_cast<const T*>(smem_st + (size_t)b * buf_bytes);
+        const T* Wm = Li + ldl * nv;
+        const T* Si = Wm + ldw * np;
+        // t = r_p - W^T r_u
+        for (int q = warp; q < np; q += NT / 32) {
+            const T* wc = Wm + q * ldw;
+            T acc = 0;
+            for (int a = lane; a < dnv; a += 32) acc += wc[a] * xs[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) tq[q] = xs[dnv + q] - acc;
+        }
+        // y_c = Li r_c (Li symmetric: row a read as column a, consecutive a
+        // in consecutive threads)
+        for (int t = tid; t < dnv; t += NT) {
+            const int c = t / nv, a = t - c * nv;
+            const T* xc = xs + c * nv;
+            T acc = 0;
+            for (int bb = 0; bb < nv; ++bb) acc += Li[bb * ldl + a] * xc[bb];
+            ys[t] = acc;
+        }
+        __syncthreads();
+        // s = Si t
+        for (int q = tid; q < np; q += NT) {
+            T acc = 0;
+            for (int x = 0; x < np; ++x) acc += Si[x * lds + q] * tq[x];
+            sq[q] = acc;
+        }
+        __syncthreads();
+        // z_u = y + W s, z_p = -s, weighted
+        for (int a = tid; a < dnv; a += NT) {
+            T z = ys[a];
+            for (int q = 0; q < np; ++q) z += Wm[q * ldw + a] * sq[q];
+            Y[s0 + a] = wt[pdofs[s0 + a]] * z;
+        }
+        for (int q = tid; q < np; q += NT) Y[s0 + dnv + q] = -wt[pdofs[s0 + dnv + q]] * sq[q];
+        __syncthreads();   // the buffer and the vectors are reused
+    }
+}
+
+__global__ void __launch_bounds__(SA_TMA_THREADS) saddle_apply_tma_f32(
+    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+    const long long* __restrict__ foff, const float* __restrict__ fac, const float* __restrict__ r,
+    const float* __restrict__ wt, float* __restrict__ Y, int buf_bytes, int xs_len, int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_st[];
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ int abort_flag;
+    saddle_apply_tma_body<float>(npatch, d, poff, pdofs, pnv, foff, fac, r, wt, Y, buf_bytes, xs_len, status, smem_st,
+                                 bars, abort_flag);
+}
+__global__ void __launch_bounds__(SA_TMA_THREADS) saddle_apply_tma_f64(
+    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+    const long long* __restrict__ foff, const double* __restrict__ fac, const double* __restrict__ r,
+    const double* __restrict__ wt, double* __restrict__ Y, int buf_bytes, int xs_len, int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_st[];
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ int abort_flag;
+    saddle_apply_tma_body<double>(npatch, d, poff, pdofs, pnv, foff, fac, r, wt, Y, buf_bytes, xs_len, status, smem_st,
+                                  bars, abort_flag);
 }
 
 // ---------------------------------------------------------- coarse GJ ---

@@ -181,12 +181,34 @@ __host__ __device__ inline long long saddle_factor_len(int d, int n, int nv, int
                     lds = (np + vec - 1) / vec * vec;
     return ldl * nv + ldw * np + lds * np;
 }
-// Shared memory (bytes) of saddle_apply_*: partial sums, W, and five
-// vectors of xs_len (>= the largest patch) elements.
+// Shared memory (bytes) of saddle_apply_*: partial sums, W (ws_len
+// elements; 0 = W read from global memory), and five vectors of xs_len
+// (>= the largest patch) elements.  W is staged when the total stays within
+// SADDLE_APPLY_SMEM_MAX bytes (the kernels' shared-memory attribute).
 constexpr int SADDLE_APPLY_THREADS = 128;
+constexpr size_t SADDLE_APPLY_SMEM_MAX = 200 * 1024;
 __host__ __device__ inline size_t saddle_apply_smem(int elem_bytes, int vec, long long ws_len, long long xs_len) {
     return (size_t)elem_bytes * vec * SADDLE_APPLY_THREADS * 3 + (size_t)elem_bytes * (ws_len + 5 * xs_len);
 }
+// The same sweep with persistent CTAs streaming each patch's factored block
+// into one of two shared-memory buffers by a bulk copy, one patch ahead
+// (buf_bytes >= the largest block, a multiple of 128; xs_len >= the largest
+// patch).  *status = 1 if a CTA gave up waiting for a copy (bounded wait).
+constexpr int SA_TMA_THREADS = 256;
+constexpr long long SA_WAIT_LIMIT = 1ll << 22;
+__host__ __device__ inline size_t saddle_apply_tma_smem(int buf_bytes, int elem_bytes, int xs_len) {
+    return 2 * (size_t)buf_bytes + (size_t)elem_bytes * 4 * xs_len;
+}
+__global__ void saddle_apply_tma_f32(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                     const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                     const float* __restrict__ fac, const float* __restrict__ r,
+                                     const float* __restrict__ wt, float* __restrict__ Y, int buf_bytes, int xs_len,
+                                     int* __restrict__ status);
+__global__ void saddle_apply_tma_f64(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                     const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                     const double* __restrict__ fac, const double* __restrict__ r,
+                                     const double* __restrict__ wt, double* __restrict__ Y, int buf_bytes, int xs_len,
+                                     int* __restrict__ status);
 __global__ void saddle_apply_f32(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
                                  const int* __restrict__ pnv, const long long* __restrict__ foff,
                                  const float* __restrict__ fac, const float* __restrict__ r, const float* __restrict__ wt,

@@ -184,6 +184,8 @@ struct DevLevel {
     float* fac32 = nullptr;
     int sa_xs = 0;                      // saddle apply: largest patch
     long long sa_ws64 = 0, sa_ws32 = 0; // saddle apply: largest W (elements)
+    int sa_buf = 0;                     // bulk-copy apply: buffer bytes (0: not used on this level)
+    int sa_grid = 0;                    // its persistent grid
     double* wt64 = nullptr;
     float* wt32 = nullptr;
     int *soff = nullptr, *sidx = nullptr;
@@ -304,6 +306,7 @@ struct stokes_mg {
     Prof prof[5];
     bool capturing = false;
     bool host_only = false;
+    int* sa_status = nullptr;           // device: 1 once a bulk-copy apply CTA gave up waiting
     // bump allocator for the handle's long-lived device buffers: a few large
     // cudaMalloc chunks instead of one call per array
     char* slab_cur = nullptr;
@@ -523,6 +526,17 @@ template <> struct LV<float> {
     static float* u(DevLevel& l) { return l.u32; }
 };
 
+// The bulk-copy apply's bounded waits report through h->sa_status: read it
+// (one int, after the stream's work) and fail with ECUDA if a CTA gave up.
+void check_sa_status(stokes_mg* h, cudaStream_t s) {
+    if (!h->sa_status) return;
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, h->sa_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (v != 0)
+        throw StokesError(STOKES_ECUDA, "a patch-apply CTA gave up waiting for its bulk copy (bounded wait)");
+}
+
 // one ASM sweep: Y = W_i K_i^{-1} I_i r for every patch, then
 // out = alpha * sum_i I_i^T Y_i + beta * out
 template <typename T>
@@ -530,11 +544,20 @@ void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, doub
 
 template <>
 void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
-    if (l.fac32) {
-        const size_t smem = skern::saddle_apply_smem(4, 4, l.sa_ws32, l.sa_xs);
+    if (l.fac32 && l.sa_buf > 0) {
+        const size_t smem = skern::saddle_apply_tma_smem(l.sa_buf, 4, l.sa_xs);
+        launch(h, PK_PATCH, s, [&] {
+            skern::saddle_apply_tma_f32<<<l.sa_grid, skern::SA_TMA_THREADS, smem, s>>>(
+                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_buf, l.sa_xs,
+                h->sa_status);
+        });
+    } else if (l.fac32) {
+        long long ws = l.sa_ws32;
+        if (skern::saddle_apply_smem(4, 4, ws, l.sa_xs) > skern::SADDLE_APPLY_SMEM_MAX) ws = 0;
+        const size_t smem = skern::saddle_apply_smem(4, 4, ws, l.sa_xs);
         launch(h, PK_PATCH, s, [&] {
             skern::saddle_apply_f32<<<l.npatch, skern::SADDLE_APPLY_THREADS, smem, s>>>(
-                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_xs, (int)l.sa_ws32);
+                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_xs, (int)ws);
         });
     } else {
         if (!l.inv32) throw StokesError(STOKES_EINVAL, "no FP32 patch inverses on this handle (FP64 handle)");
@@ -550,11 +573,20 @@ void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, dou
 
 template <>
 void asm_apply<double>(stokes_mg* h, DevLevel& l, const double* r, double* out, double alpha, double beta, cudaStream_t s) {
-    if (l.fac64) {
-        const size_t smem = skern::saddle_apply_smem(8, 2, l.sa_ws64, l.sa_xs);
+    if (l.fac64 && l.sa_buf > 0) {
+        const size_t smem = skern::saddle_apply_tma_smem(l.sa_buf, 8, l.sa_xs);
+        launch(h, PK_PATCH, s, [&] {
+            skern::saddle_apply_tma_f64<<<l.sa_grid, skern::SA_TMA_THREADS, smem, s>>>(
+                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_buf, l.sa_xs,
+                h->sa_status);
+        });
+    } else if (l.fac64) {
+        long long ws = l.sa_ws64;
+        if (skern::saddle_apply_smem(8, 2, ws, l.sa_xs) > skern::SADDLE_APPLY_SMEM_MAX) ws = 0;
+        const size_t smem = skern::saddle_apply_smem(8, 2, ws, l.sa_xs);
         launch(h, PK_PATCH, s, [&] {
             skern::saddle_apply_f64<<<l.npatch, skern::SADDLE_APPLY_THREADS, smem, s>>>(
-                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_xs, (int)l.sa_ws64);
+                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_xs, (int)ws);
         });
     } else {
         if (!l.inv64) throw StokesError(STOKES_EINVAL, "no FP64 patch inverses on this handle (MIXED handle)");
@@ -1244,6 +1276,7 @@ int fgmres_op(stokes_mg* h, const DevCSR& K, int n, double* rscr, const Precond&
         if (beta <= tol * beta0) { converged = true; break; }
         rcur = r;
     }
+    check_sa_status(h, s);
     if (its_out) *its_out = its;
     if (rel_out) *rel_out = rel;
     return converged ? STOKES_OK : STOKES_ENOTCONVERGED;
@@ -1457,6 +1490,45 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
             }
             l.nfac64 = f64[l.npatch];
             l.nfac32 = f32[l.npatch];
+            if (skern::saddle_apply_smem(8, 2, 0, l.sa_xs) > skern::SADDLE_APPLY_SMEM_MAX)
+                throw StokesError(STOKES_EUNSUPPORTED, "patch too large for the saddle apply's shared memory");
+            // one process-wide upper bound (never lowered)
+            CK(cudaFuncSetAttribute(skern::saddle_apply_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)skern::SADDLE_APPLY_SMEM_MAX));
+            CK(cudaFuncSetAttribute(skern::saddle_apply_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)skern::SADDLE_APPLY_SMEM_MAX));
+            CK(cudaFuncSetAttribute(skern::saddle_apply_tma_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)skern::SADDLE_APPLY_SMEM_MAX));
+            CK(cudaFuncSetAttribute(skern::saddle_apply_tma_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)skern::SADDLE_APPLY_SMEM_MAX));
+            // the bulk-copy apply when two of the level's largest blocks fit
+            // in shared memory (persistent grid: as many CTAs as fit per SM)
+            {
+                const int eb = want32 ? 4 : 8;
+                const std::vector<long long>& fo = want32 ? f32 : f64;
+                long long mb = 0;
+                for (int p = 0; p < l.npatch; ++p) mb = std::max(mb, fo[p + 1] - fo[p]);
+                const long long buf = (mb * eb + 127) & ~127LL;
+                const size_t smem = skern::saddle_apply_tma_smem((int)std::min<long long>(buf, 1 << 30), eb, l.sa_xs);
+                if (buf > 0 && smem <= skern::SADDLE_APPLY_SMEM_MAX && !std::getenv("STOKES_NO_BULK_APPLY")) {
+                    int per_sm = 0, nsm = 0;
+                    if (want32)
+                        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, skern::saddle_apply_tma_f32,
+                                                                         skern::SA_TMA_THREADS, smem));
+                    else
+                        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, skern::saddle_apply_tma_f64,
+                                                                         skern::SA_TMA_THREADS, smem));
+                    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+                    if (per_sm > 0) {
+                        l.sa_buf = (int)buf;
+                        l.sa_grid = std::min<long long>(l.npatch, (long long)per_sm * nsm);
+                    }
+                }
+                if (!h->sa_status) {
+                    h->sa_status = halloc<int>(h, 1);
+                    CK(cudaMemsetAsync(h->sa_status, 0, sizeof(int), s));
+                }
+            }
             if (want32) { l.foff32 = hupload(h, f32, s); l.fac32 = halloc<float>(h, l.nfac32); }
             else { l.foff64 = hupload(h, f64, s); l.fac64 = halloc<double>(h, l.nfac64); }
         } else if (!want32) {
@@ -2313,6 +2385,8 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         t1 = host_ms();
         if (o.use_graph) capture_graph(h.get(), o.precision, s);
         CK(cudaStreamSynchronize(s));
+        for (cudaStream_t x : h->s_lvl)
+            if (x) check_sa_status(h.get(), x);
         h->st.t_graph_ms = host_ms() - t1;
         h->st.t_total_ms = host_ms() - t0;
         mark(h.get(), "setup end", s);
