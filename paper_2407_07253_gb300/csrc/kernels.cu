@@ -716,6 +716,92 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
     }
 }
 
+// The factored form alone (no explicit output), in less shared memory: the
+// components' B_c^T and W_c = Li B_c^T go through one pair of buffers, W_c
+// is written out as soon as it exists and S = sum_c B_c W_c accumulates over
+// the components.  Scratch: saddle_scratch_factored(d, n, nv) doubles.
+__device__ void saddle_core_factored(int d, int n, int nv, const double* K, double* scratch, double* fac64,
+                                     float* fac32, int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int np = n - d * nv, npp = np | 1, dnv = d * nv;
+    const int mx = nv > np ? nv : np;
+    double* Ls = scratch;                          // [nv][nv]
+    double* Bt = Ls + (long long)nv * nv;          // [a][q] of the current component
+    double* Wm = Bt + (long long)nv * npp;         // [a][q] of the current component
+    double* Ss = Wm + (long long)nv * npp;         // [q][r]
+    double* ck = Ss + (long long)np * np;          // [2][mx]
+    double* cs = ck + 2 * mx;                      // [mx]
+    double* rinv = cs + mx;                        // [2]
+    const int ldl = fac64 ? (nv + 1) & ~1 : (nv + 3) & ~3;
+    const int ldw = fac64 ? (dnv + 1) & ~1 : (dnv + 3) & ~3;
+    const int lds = fac64 ? (np + 1) & ~1 : (np + 3) & ~3;
+    const long long oW = (long long)ldl * nv, oS = oW + (long long)ldw * np;
+    const int ns = np * (np + 1) / 2;
+    for (int i = warp; i < nv; i += nw)
+        for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
+    for (int t = tid; t < np * np; t += nt) Ss[t] = 0.0;
+    __syncthreads();
+    sweep_spd(Ls, nv, nv, ck, cs, rinv, status);
+    {
+        const int tot = nv * ldl;
+        for (int t = tid; t < tot; t += nt) {
+            const int b = t / ldl, a = t - b * ldl;
+            const double v = a < nv ? Ls[a * nv + b] : 0.0;
+            if (fac64) fac64[t] = v;
+            if (fac32) fac32[t] = (float)v;
+        }
+        // W's padding rows
+        for (int t = tid; t < np * (ldw - dnv); t += nt) {
+            const int q = t / (ldw - dnv), r = dnv + t - q * (ldw - dnv);
+            if (fac64) fac64[oW + (long long)q * ldw + r] = 0.0;
+            if (fac32) fac32[oW + (long long)q * ldw + r] = 0.0f;
+        }
+    }
+    for (int c = 0; c < d; ++c) {
+        for (int a = warp; a < nv; a += nw)
+            for (int q = lane; q < np; q += 32) Bt[(long long)a * npp + q] = K[(long long)(c * nv + a) * n + dnv + q];
+        __syncthreads();
+        // W_c = Li B_c^T: entry t = (a, q)
+        const int nw_out = nv * np;
+        for (int t = tid; t < nw_out; t += nt) {
+            const int a = t / np, q = t - a * np;
+            const double* li = Ls + a * nv;
+            const double* bt = Bt + q;
+            double sacc = 0.0;
+            for (int b = 0; b < nv; ++b) sacc = fma(li[b], bt[(long long)b * npp], sacc);
+            Wm[(long long)a * npp + q] = sacc;
+        }
+        __syncthreads();
+        for (int t = tid; t < nv * np; t += nt) {
+            const int q = t / nv, a = t - q * nv;
+            const double v = Wm[(long long)a * npp + q];
+            if (fac64) fac64[oW + (long long)q * ldw + c * nv + a] = v;
+            if (fac32) fac32[oW + (long long)q * ldw + c * nv + a] = (float)v;
+        }
+        // S += B_c W_c on the upper triangle q <= r (each entry one thread)
+        for (int t = tid; t < ns; t += nt) {
+            int q = 0, rem = t;
+            while (rem >= np - q) { rem -= np - q; ++q; }
+            const int r = q + rem;
+            double sacc = 0.0;
+            for (int a = 0; a < nv; ++a) sacc = fma(Bt[(long long)a * npp + q], Wm[(long long)a * npp + r], sacc);
+            Ss[q * np + r] += sacc;
+        }
+        __syncthreads();
+    }
+    sweep_spd(Ss, np, np, ck, cs, rinv, status);
+    {
+        const int tot = np * lds;
+        for (int t = tid; t < tot; t += nt) {
+            const int r = t / lds, q = t - r * lds;
+            const double v = q < np ? Ss[q * np + r] : 0.0;
+            if (fac64) fac64[oS + t] = v;
+            if (fac32) fac32[oS + t] = (float)v;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff,
                                                            const int* __restrict__ pnv, const long long* __restrict__ moff,
                                                            double* __restrict__ work, const long long* __restrict__ off64,
@@ -731,8 +817,13 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
     __shared__ int st;
     if (threadIdx.x == 0) st = 0;
     __syncthreads();
-    saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr, inv32 ? inv32 + off32[p] : nullptr,
-                fac64 ? fac64 + foff64[p] : nullptr, fac32 ? fac32 + foff32[p] : nullptr, back, &st);
+    if (!inv64 && !inv32 && !back)
+        saddle_core_factored(d, n, nv, work + moff[p], sscr, fac64 ? fac64 + foff64[p] : nullptr,
+                             fac32 ? fac32 + foff32[p] : nullptr, &st);
+    else
+        saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr,
+                    inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
+                    fac32 ? fac32 + foff32[p] : nullptr, back, &st);
     __syncthreads();
     if (threadIdx.x == 0) status[p] = st;
 }
@@ -752,9 +843,13 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
     __shared__ int st;
     if (threadIdx.x == 0) st = 0;
     __syncthreads();
-    saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,
-                inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
-                fac32 ? fac32 + foff32[p] : nullptr, back, &st);
+    if (!inv64 && !inv32 && !back)
+        saddle_core_factored(d, n, nv, work + moff[p], scratch + soff[p], fac64 ? fac64 + foff64[p] : nullptr,
+                             fac32 ? fac32 + foff32[p] : nullptr, &st);
+    else
+        saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,
+                    inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
+                    fac32 ? fac32 + foff32[p] : nullptr, back, &st);
     __syncthreads();
     if (threadIdx.x == 0) status[p] = st;
 }
@@ -1011,19 +1106,19 @@ __global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f64(
     saddle_apply_body<double, double2, 2>(blockIdx.x, d, poff, pdofs, pnv, foff, fac, r, wt, Y, xs_len, ws_len, smem_sa);
 }
 
-// ---- the same sweep with the factored blocks streamed by bulk copies ----
-// Persistent CTAs (SA_TMA_THREADS threads) take patches blockIdx.x,
-// blockIdx.x + gridDim.x, ...; each patch's factored block (Li, W, Si:
-// contiguous, a multiple of 16 bytes) is brought into shared memory by one
-// cp.async.bulk issued one patch ahead into the other of two buffers, so the
-// HBM stream of the next patch overlaps the arithmetic of this one.  All
-// products then read shared memory:
+// ---- the same sweep with each patch's factored block brought into shared
+// memory by one bulk copy (cp.async.bulk, completion on an mbarrier) -------
+// One CTA of SA_BULK_THREADS threads per patch: thread 0 issues the copy of
+// the patch's (Li, W, Si) block (contiguous, a multiple of 16 bytes) while
+// the others gather the residual and the partition-of-unity weights of the
+// patch's DoFs; every product then reads shared memory:
 //   t = r_p - W^T r_u   (one warp per pressure row, lanes over the velocity rows)
-//   s = Si t            (one thread per pressure row)
 //   y_c = Li r_c        (one thread per velocity row and component)
+//   s = Si t            (one thread per pressure row)
 //   z_u = y + W s, z_p = -s, weighted.
-// Waits on the buffers' mbarriers are bounded: after SA_WAIT_LIMIT polls the
-// CTA sets *status = 1 and returns (no hang, no trap).
+// A CTA holds only its own block, so several CTAs per SM stream their blocks
+// at once.  The wait on the copy is bounded: after SA_WAIT_LIMIT polls the
+// CTA sets *status = 1, waits (bounded) for the copy once more and returns.
 __device__ __forceinline__ uint32_t sa_smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -1049,126 +1144,98 @@ __device__ __forceinline__ void sa_bulk_load(uint32_t dst, const void* src, uint
 }
 
 template <typename T>
-__device__ __forceinline__ void saddle_apply_tma_body(
-    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+__device__ __forceinline__ void saddle_apply_bulk_body(
+    int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
     const long long* __restrict__ foff, const T* __restrict__ fac, const T* __restrict__ r,
     const T* __restrict__ wt, T* __restrict__ Y, int buf_bytes, int xs_len, int* __restrict__ status,
-    unsigned char* smem_st, unsigned long long* bars, int& abort_flag) {
-    constexpr int NT = SA_TMA_THREADS;
+    unsigned char* smem, unsigned long long* bar) {
+    constexpr int NT = SA_BULK_THREADS;
     constexpr int VEC = 16 / sizeof(T);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    T* xs = reinterpret_cast<T*>(smem_st + 2 * (size_t)buf_bytes);   // [xs_len] gathered r
-    T* ys = xs + xs_len;                                              // [xs_len] z_u
-    T* tq = ys + xs_len;                                              // [xs_len] t
-    T* sq = tq + xs_len;                                              // [xs_len] s
-    const uint32_t bar0 = sa_smem_u32(&bars[0]), bar1 = sa_smem_u32(&bars[1]);
+    const int p = blockIdx.x;
+    T* xs = reinterpret_cast<T*>(smem + (size_t)buf_bytes);   // [xs_len] gathered r
+    T* wq = xs + xs_len;                                       // [xs_len] weights
+    T* ys = wq + xs_len;                                       // [xs_len] y
+    T* tq = ys + xs_len;                                       // [xs_len] t
+    T* sq = tq + xs_len;                                       // [xs_len] s
+    const uint32_t b = sa_smem_u32(bar);
+    const int s0 = poff[p], n = poff[p + 1] - s0, nv = pnv[p], dnv = d * nv, np = n - dnv;
     if (tid == 0) {
-        sa_mbar_init(bar0);
-        sa_mbar_init(bar1);
-        abort_flag = 0;
+        sa_mbar_init(b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // every issue completes one phase of its buffer's barrier (an empty
-    // block arrives without a copy)
-    auto issue = [&](int p, int b) {
         const long long o = foff[p];
         const uint32_t bytes = (uint32_t)((foff[p + 1] - o) * (long long)sizeof(T));
-        const uint32_t bar = b ? bar1 : bar0;
-        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem_st + (size_t)b * buf_bytes), fac + o, bytes, bar);
-        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-    };
-    auto wait = [&](uint32_t bar, uint32_t parity) {
-        for (long long it = 0; it < SA_WAIT_LIMIT; ++it) {
-            if (sa_mbar_try(bar, parity)) return true;
-            if (abort_flag) return false;
-        }
-        return false;
-    };
-    if (tid == 0 && (int)blockIdx.x < npatch) issue(blockIdx.x, 0);
-    int k = 0;
-    for (int p = blockIdx.x; p < npatch; p += gridDim.x, ++k) {
-        const int b = k & 1;
-        const int pn = p + gridDim.x;
-        if (tid == 0 && pn < npatch) issue(pn, b ^ 1);
-        const int s0 = poff[p], n = poff[p + 1] - s0, nv = pnv[p], dnv = d * nv, np = n - dnv;
-        for (int a = tid; a < n; a += NT) xs[a] = r[pdofs[s0 + a]];
-        // bounded wait for this patch's block (phase k >> 1 of its buffer)
-        if (!wait(b ? bar1 : bar0, (uint32_t)((k >> 1) & 1))) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) {
-            // give up: let the prefetch in flight (if any) land, bounded, and
-            // report through *status
-            if (tid == 0) {
-                if (pn < npatch) {
-                    const uint32_t bo = b ? bar0 : bar1, po = (uint32_t)(((k + 1) >> 1) & 1);
-                    for (long long it = 0; it < SA_WAIT_LIMIT && !sa_mbar_try(bo, po); ++it) {}
-                }
-                atomicExch(status, 1);
-            }
-            return;
-        }
-        const int ldl = (nv + VEC - 1) / VEC * VEC, ldw = (dnv + VEC - 1) / VEC * VEC;
-        const int lds = (np + VEC - 1) / VEC * VEC;
-        const T* Li = reinterpret_cast<const T*>(smem_st + (size_t)b * buf_bytes);
-        const T* Wm = Li + ldl * nv;
-        const T* Si = Wm + ldw * np;
-        // t = r_p - W^T r_u
-        for (int q = warp; q < np; q += NT / 32) {
-            const T* wc = Wm + q * ldw;
-            T acc = 0;
-            for (int a = lane; a < dnv; a += 32) acc += wc[a] * xs[a];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) tq[q] = xs[dnv + q] - acc;
-        }
-        // y_c = Li r_c (Li symmetric: row a read as column a, consecutive a
-        // in consecutive threads)
-        for (int t = tid; t < dnv; t += NT) {
-            const int c = t / nv, a = t - c * nv;
-            const T* xc = xs + c * nv;
-            T acc = 0;
-            for (int bb = 0; bb < nv; ++bb) acc += Li[bb * ldl + a] * xc[bb];
-            ys[t] = acc;
-        }
-        __syncthreads();
-        // s = Si t
-        for (int q = tid; q < np; q += NT) {
-            T acc = 0;
-            for (int x = 0; x < np; ++x) acc += Si[x * lds + q] * tq[x];
-            sq[q] = acc;
-        }
-        __syncthreads();
-        // z_u = y + W s, z_p = -s, weighted
-        for (int a = tid; a < dnv; a += NT) {
-            T z = ys[a];
-            for (int q = 0; q < np; ++q) z += Wm[q * ldw + a] * sq[q];
-            Y[s0 + a] = wt[pdofs[s0 + a]] * z;
-        }
-        for (int q = tid; q < np; q += NT) Y[s0 + dnv + q] = -wt[pdofs[s0 + dnv + q]] * sq[q];
-        __syncthreads();   // the buffer and the vectors are reused
+        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem), fac + o, bytes, b);
+        else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
     }
+    for (int a = tid; a < n; a += NT) {
+        const int j = pdofs[s0 + a];
+        xs[a] = r[j];
+        wq[a] = wt[j];
+    }
+    // the barrier's initialisation (thread 0) is ordered before anyone polls
+    // it by this __syncthreads; then every thread waits on it, bounded
+    __syncthreads();
+    bool ok = false;
+    for (long long it = 0; it < SA_WAIT_LIMIT; ++it)
+        if (sa_mbar_try(b, 0)) { ok = true; break; }
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            for (long long it = 0; it < SA_WAIT_LIMIT && !sa_mbar_try(b, 0); ++it) {}
+            atomicExch(status, 1);
+        }
+        return;
+    }
+    const int ldl = (nv + VEC - 1) / VEC * VEC, ldw = (dnv + VEC - 1) / VEC * VEC;
+    const int lds = (np + VEC - 1) / VEC * VEC;
+    const T* Li = reinterpret_cast<const T*>(smem);
+    const T* Wm = Li + ldl * nv;
+    const T* Si = Wm + ldw * np;
+    for (int q = warp; q < np; q += NT / 32) {
+        const T* wc = Wm + q * ldw;
+        T acc = 0;
+        for (int a = lane; a < dnv; a += 32) acc += wc[a] * xs[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) tq[q] = xs[dnv + q] - acc;
+    }
+    for (int t = tid; t < dnv; t += NT) {
+        const int c = t / nv, a = t - c * nv;
+        const T* xc = xs + c * nv;
+        T acc = 0;
+        for (int bb = 0; bb < nv; ++bb) acc += Li[bb * ldl + a] * xc[bb];
+        ys[t] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < np; q += NT) {
+        T acc = 0;
+        for (int x = 0; x < np; ++x) acc += Si[x * lds + q] * tq[x];
+        sq[q] = acc;
+    }
+    __syncthreads();
+    for (int a = tid; a < dnv; a += NT) {
+        T z = ys[a];
+        for (int q = 0; q < np; ++q) z += Wm[q * ldw + a] * sq[q];
+        Y[s0 + a] = wq[a] * z;
+    }
+    for (int q = tid; q < np; q += NT) Y[s0 + dnv + q] = -wq[dnv + q] * sq[q];
 }
 
-__global__ void __launch_bounds__(SA_TMA_THREADS) saddle_apply_tma_f32(
-    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+__global__ void __launch_bounds__(SA_BULK_THREADS) saddle_apply_bulk_f32(
+    int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
     const long long* __restrict__ foff, const float* __restrict__ fac, const float* __restrict__ r,
     const float* __restrict__ wt, float* __restrict__ Y, int buf_bytes, int xs_len, int* __restrict__ status) {
-    extern __shared__ __align__(128) unsigned char smem_st[];
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ int abort_flag;
-    saddle_apply_tma_body<float>(npatch, d, poff, pdofs, pnv, foff, fac, r, wt, Y, buf_bytes, xs_len, status, smem_st,
-                                 bars, abort_flag);
+    extern __shared__ __align__(128) unsigned char smem_sb[];
+    __shared__ __align__(8) unsigned long long bar;
+    saddle_apply_bulk_body<float>(d, poff, pdofs, pnv, foff, fac, r, wt, Y, buf_bytes, xs_len, status, smem_sb, &bar);
 }
-__global__ void __launch_bounds__(SA_TMA_THREADS) saddle_apply_tma_f64(
-    int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
+__global__ void __launch_bounds__(SA_BULK_THREADS) saddle_apply_bulk_f64(
+    int d, const int* __restrict__ poff, const int* __restrict__ pdofs, const int* __restrict__ pnv,
     const long long* __restrict__ foff, const double* __restrict__ fac, const double* __restrict__ r,
     const double* __restrict__ wt, double* __restrict__ Y, int buf_bytes, int xs_len, int* __restrict__ status) {
-    extern __shared__ __align__(128) unsigned char smem_st[];
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ int abort_flag;
-    saddle_apply_tma_body<double>(npatch, d, poff, pdofs, pnv, foff, fac, r, wt, Y, buf_bytes, xs_len, status, smem_st,
-                                  bars, abort_flag);
+    extern __shared__ __align__(128) unsigned char smem_sb[];
+    __shared__ __align__(8) unsigned long long bar;
+    saddle_apply_bulk_body<double>(d, poff, pdofs, pnv, foff, fac, r, wt, Y, buf_bytes, xs_len, status, smem_sb, &bar);
 }
 
 // ---------------------------------------------------------- coarse GJ ---
@@ -1347,6 +1414,121 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_inverse(int n, double*
         __syncthreads();
     }
     for (long long t = tid; t < (long long)nr * n; t += nt) A[(long long)r0 * n + t] = rows[t];
+}
+
+// ---- blocked Gauss-Jordan inverse (partial pivoting) on every SM -------
+// Panel [k0, k0 + B) of the row-major n x n matrix A: the columns of all rows
+// in shared memory (pan[j n + i]), B Gauss-Jordan steps on them (pivot row
+// p >= k with the largest |a_pk|, ties to the smaller row; swap; scale row k
+// by r = 1 / a_kk and put r in place of a_kk; eliminate column k from every
+// other row, putting -a_ik r in its place).  The panel columns go back to A
+// and to Pk (row-major n x B) for the trailing update; ipiv[k] = p;
+// status <- 1 + the step of the first zero pivot.
+__global__ void __launch_bounds__(GJB_THREADS) gj_block_panel(int n, int k0, int B, double* __restrict__ A,
+                                                              int* __restrict__ ipiv, double* __restrict__ Pk,
+                                                              int* __restrict__ status) {
+    extern __shared__ double pan[];
+    __shared__ double rv[GJB_THREADS / 32];
+    __shared__ int ri[GJB_THREADS / 32];
+    __shared__ int s_p;
+    __shared__ double s_r;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    for (long long t = tid; t < (long long)n * B; t += nt) {
+        const int i = (int)(t / B), j = (int)(t - (long long)i * B);
+        pan[(long long)j * n + i] = A[(long long)i * n + k0 + j];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < B; ++jj) {
+        const int k = k0 + jj;
+        double* col = pan + (long long)jj * n;
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += nt) {
+            const double v = fabs(col[i]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nt / 32; ++w)
+                if (rv[w] > best || (rv[w] == best && ri[w] < bi)) { best = rv[w]; bi = ri[w]; }
+            if (!(best > 0.0) || bi >= n) {
+                bi = k;
+                if (*status == 0) *status = k + 1;
+            }
+            s_p = bi;
+            ipiv[k] = bi;
+            const double a = col[bi];
+            s_r = a != 0.0 ? 1.0 / a : 0.0;
+        }
+        __syncthreads();
+        const int p = s_p;
+        const double r = s_r;
+        for (int j = tid; j < B; j += nt) {
+            double* cj = pan + (long long)j * n;
+            if (p != k) { const double t = cj[k]; cj[k] = cj[p]; cj[p] = t; }
+            cj[k] = j == jj ? r : cj[k] * r;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) {
+            if (i == k) continue;
+            const double f = col[i];
+            for (int j = 0; j < B; ++j) {
+                if (j == jj) continue;
+                double* cj = pan + (long long)j * n;
+                cj[i] = fma(-f, cj[k], cj[i]);
+            }
+            col[i] = -f * r;
+        }
+        __syncthreads();
+    }
+    for (long long t = tid; t < (long long)n * B; t += nt) {
+        const int i = (int)(t / B), j = (int)(t - (long long)i * B);
+        const double v = pan[(long long)j * n + i];
+        A[(long long)i * n + k0 + j] = v;
+        Pk[t] = v;
+    }
+}
+
+// The panel's row swaps on every column outside it, and the swapped rows
+// k0 .. k0 + B - 1 copied to Yb[j n + c] (before the update overwrites them).
+__global__ void __launch_bounds__(256) gj_block_swap(int n, int k0, int B, double* __restrict__ A,
+                                                     const int* __restrict__ ipiv, double* __restrict__ Yb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || (c >= k0 && c < k0 + B)) return;
+    for (int jj = 0; jj < B; ++jj) {
+        const int k = k0 + jj, p = ipiv[k];
+        if (p != k) {
+            const double t = A[(long long)k * n + c];
+            A[(long long)k * n + c] = A[(long long)p * n + c];
+            A[(long long)p * n + c] = t;
+        }
+    }
+    for (int jj = 0; jj < B; ++jj) Yb[(long long)jj * n + c] = A[(long long)(k0 + jj) * n + c];
+}
+
+// Trailing update of the columns outside the panel, on 32 x 32 tiles:
+//   A[i][c] = (i in panel rows ? 0 : A[i][c]) + sum_j Pk[i][j] Yb[j][c].
+__global__ void __launch_bounds__(256) gj_block_update(int n, int k0, int B, double* __restrict__ A,
+                                                       const double* __restrict__ Pk, const double* __restrict__ Yb) {
+    __shared__ double ys[GJB_MAX_B][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane, i0 = blockIdx.y * 32;
+    const bool colok = c < n && !(c >= k0 && c < k0 + B);
+    for (int jj = warp; jj < B; jj += 8) ys[jj][lane] = colok ? Yb[(long long)jj * n + c] : 0.0;
+    __syncthreads();
+    if (!colok) return;
+    for (int i = i0 + warp; i < min(n, i0 + 32); i += 8) {
+        const double* pk = Pk + (long long)i * B;
+        double acc = (i >= k0 && i < k0 + B) ? 0.0 : A[(long long)i * n + c];
+        for (int jj = 0; jj < B; ++jj) acc = fma(pk[jj], ys[jj][lane], acc);
+        A[(long long)i * n + c] = acc;
+    }
 }
 
 __global__ void gj_unpivot_rows(int n, double* __restrict__ A, const int* __restrict__ ipiv) {

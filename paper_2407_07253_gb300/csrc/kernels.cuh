@@ -154,6 +154,12 @@ __host__ __device__ inline long long saddle_scratch(int d, int n, int nv) {
     return (long long)nv * nv + 2LL * d * nv * npp + (long long)np * np + 3LL * mx + 2;
 }
 constexpr long long SADDLE_SMEM_MAX_DOUBLES = 25600;   // 200 KB of shared memory
+// scratch of the factored-only inversion (one component's B^T and W at a time)
+__host__ __device__ inline long long saddle_scratch_factored(int d, int n, int nv) {
+    const int np = n - d * nv, npp = np | 1;
+    const int mx = nv > np ? nv : np;
+    return (long long)nv * nv + 2LL * nv * npp + (long long)np * np + 3LL * mx + 2;
+}
 // Outputs (each may be NULL): explicit inverses inv64 / inv32 (column-major,
 // leading dimension n rounded up to 2 / 4), the factored form fac64 / fac32
 // at foff64[p] / foff32[p] (saddle_factor_len), and, if back, the explicit
@@ -190,25 +196,25 @@ constexpr size_t SADDLE_APPLY_SMEM_MAX = 200 * 1024;
 __host__ __device__ inline size_t saddle_apply_smem(int elem_bytes, int vec, long long ws_len, long long xs_len) {
     return (size_t)elem_bytes * vec * SADDLE_APPLY_THREADS * 3 + (size_t)elem_bytes * (ws_len + 5 * xs_len);
 }
-// The same sweep with persistent CTAs streaming each patch's factored block
-// into one of two shared-memory buffers by a bulk copy, one patch ahead
-// (buf_bytes >= the largest block, a multiple of 128; xs_len >= the largest
-// patch).  *status = 1 if a CTA gave up waiting for a copy (bounded wait).
-constexpr int SA_TMA_THREADS = 256;
+// The same sweep with one CTA per patch whose factored block is brought into
+// shared memory by one bulk copy (buf_bytes >= the largest block, a
+// multiple of 128; xs_len >= the largest patch).  *status = 1 if a CTA gave
+// up waiting for its copy (bounded wait).
+constexpr int SA_BULK_THREADS = 128;
 constexpr long long SA_WAIT_LIMIT = 1ll << 22;
-__host__ __device__ inline size_t saddle_apply_tma_smem(int buf_bytes, int elem_bytes, int xs_len) {
-    return 2 * (size_t)buf_bytes + (size_t)elem_bytes * 4 * xs_len;
+__host__ __device__ inline size_t saddle_apply_bulk_smem(int buf_bytes, int elem_bytes, int xs_len) {
+    return (size_t)buf_bytes + (size_t)elem_bytes * 5 * xs_len;
 }
-__global__ void saddle_apply_tma_f32(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
-                                     const int* __restrict__ pnv, const long long* __restrict__ foff,
-                                     const float* __restrict__ fac, const float* __restrict__ r,
-                                     const float* __restrict__ wt, float* __restrict__ Y, int buf_bytes, int xs_len,
-                                     int* __restrict__ status);
-__global__ void saddle_apply_tma_f64(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
-                                     const int* __restrict__ pnv, const long long* __restrict__ foff,
-                                     const double* __restrict__ fac, const double* __restrict__ r,
-                                     const double* __restrict__ wt, double* __restrict__ Y, int buf_bytes, int xs_len,
-                                     int* __restrict__ status);
+__global__ void saddle_apply_bulk_f32(int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                      const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                      const float* __restrict__ fac, const float* __restrict__ r,
+                                      const float* __restrict__ wt, float* __restrict__ Y, int buf_bytes,
+                                      int xs_len, int* __restrict__ status);
+__global__ void saddle_apply_bulk_f64(int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
+                                      const int* __restrict__ pnv, const long long* __restrict__ foff,
+                                      const double* __restrict__ fac, const double* __restrict__ r,
+                                      const double* __restrict__ wt, double* __restrict__ Y, int buf_bytes,
+                                      int xs_len, int* __restrict__ status);
 __global__ void saddle_apply_f32(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pdofs,
                                  const int* __restrict__ pnv, const long long* __restrict__ foff,
                                  const float* __restrict__ fac, const float* __restrict__ r, const float* __restrict__ wt,
@@ -249,6 +255,18 @@ __global__ void gj_step_pivot(int n, int k, double* __restrict__ A, int* __restr
                               double* __restrict__ colk, int* __restrict__ status);
 __global__ void gj_step_eliminate(int n, int k, double* __restrict__ A, const double* __restrict__ colk);
 __global__ void gj_unpivot_rows(int n, double* __restrict__ A, const int* __restrict__ ipiv);
+// Blocked Gauss-Jordan inverse of one n x n row-major matrix on every SM,
+// B <= GJB_MAX_B pivots per panel: for each panel gj_block_panel (one CTA,
+// gj_block_panel_smem bytes), gj_block_swap (one thread per column),
+// gj_block_update (grid ceil(n/32) x ceil(n/32)); then gj_unpivot_rows.
+constexpr int GJB_THREADS = 512, GJB_MAX_B = 32;
+__host__ __device__ inline size_t gj_block_panel_smem(int n, int B) { return (size_t)n * B * sizeof(double); }
+__global__ void gj_block_panel(int n, int k0, int B, double* __restrict__ A, int* __restrict__ ipiv,
+                               double* __restrict__ Pk, int* __restrict__ status);
+__global__ void gj_block_swap(int n, int k0, int B, double* __restrict__ A, const int* __restrict__ ipiv,
+                              double* __restrict__ Yb);
+__global__ void gj_block_update(int n, int k0, int B, double* __restrict__ A, const double* __restrict__ Pk,
+                                const double* __restrict__ Yb);
 // Whole in-place Gauss-Jordan inverse (partial pivoting, row swaps in ipiv)
 // of one n x n matrix by one cluster of GJC_CTAS CTAs holding its rows in
 // shared memory: (ceil(n / GJC_CTAS) + 2) n + 2 ceil(n / GJC_CTAS) doubles

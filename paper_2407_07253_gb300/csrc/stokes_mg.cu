@@ -170,6 +170,7 @@ struct DevLevel {
     int *poff = nullptr, *pdofs = nullptr, *pnv = nullptr;
     long long *moff = nullptr, *ioff64 = nullptr, *ioff32 = nullptr;
     long long saddle_smem = 0;      // max scratch (doubles) of the patches inverted in shared memory
+    long long saddle_smem_fac = 0;  // the same for the factored-only inversion
     long long saddle_global = 0;    // total scratch (doubles) of the others
     long long* scoff = nullptr;     // their offsets into the global scratch
     long long ninv64 = 0, ninv32 = 0;
@@ -185,7 +186,6 @@ struct DevLevel {
     int sa_xs = 0;                      // saddle apply: largest patch
     long long sa_ws64 = 0, sa_ws32 = 0; // saddle apply: largest W (elements)
     int sa_buf = 0;                     // bulk-copy apply: buffer bytes (0: not used on this level)
-    int sa_grid = 0;                    // its persistent grid
     double* wt64 = nullptr;
     float* wt32 = nullptr;
     int *soff = nullptr, *sidx = nullptr;
@@ -545,11 +545,10 @@ void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, doub
 template <>
 void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
     if (l.fac32 && l.sa_buf > 0) {
-        const size_t smem = skern::saddle_apply_tma_smem(l.sa_buf, 4, l.sa_xs);
+        const size_t smem = skern::saddle_apply_bulk_smem(l.sa_buf, 4, l.sa_xs);
         launch(h, PK_PATCH, s, [&] {
-            skern::saddle_apply_tma_f32<<<l.sa_grid, skern::SA_TMA_THREADS, smem, s>>>(
-                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_buf, l.sa_xs,
-                h->sa_status);
+            skern::saddle_apply_bulk_f32<<<l.npatch, skern::SA_BULK_THREADS, smem, s>>>(
+                h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_buf, l.sa_xs, h->sa_status);
         });
     } else if (l.fac32) {
         long long ws = l.sa_ws32;
@@ -574,11 +573,10 @@ void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, dou
 template <>
 void asm_apply<double>(stokes_mg* h, DevLevel& l, const double* r, double* out, double alpha, double beta, cudaStream_t s) {
     if (l.fac64 && l.sa_buf > 0) {
-        const size_t smem = skern::saddle_apply_tma_smem(l.sa_buf, 8, l.sa_xs);
+        const size_t smem = skern::saddle_apply_bulk_smem(l.sa_buf, 8, l.sa_xs);
         launch(h, PK_PATCH, s, [&] {
-            skern::saddle_apply_tma_f64<<<l.sa_grid, skern::SA_TMA_THREADS, smem, s>>>(
-                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_buf, l.sa_xs,
-                h->sa_status);
+            skern::saddle_apply_bulk_f64<<<l.npatch, skern::SA_BULK_THREADS, smem, s>>>(
+                h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_buf, l.sa_xs, h->sa_status);
         });
     } else if (l.fac64) {
         long long ws = l.sa_ws64;
@@ -1444,7 +1442,13 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
         std::vector<long long> scoff(l.npatch + 1, 0);
         for (int p = 0; p < l.npatch; ++p) {
             const long long sc = skern::saddle_scratch(HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p]);
-            if (sc <= skern::SADDLE_SMEM_MAX_DOUBLES) { l.saddle_smem = std::max(l.saddle_smem, sc); scoff[p + 1] = scoff[p]; }
+            if (sc <= skern::SADDLE_SMEM_MAX_DOUBLES) {
+                l.saddle_smem = std::max(l.saddle_smem, sc);
+                l.saddle_smem_fac = std::max(l.saddle_smem_fac, skern::saddle_scratch_factored(
+                                                                    HL.d, HL.patch_off[p + 1] - HL.patch_off[p],
+                                                                    HL.patch_nv[p]));
+                scoff[p + 1] = scoff[p];
+            }
             else scoff[p + 1] = scoff[p] + sc;
         }
         l.saddle_global = scoff[l.npatch];
@@ -1497,33 +1501,21 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
                                     (int)skern::SADDLE_APPLY_SMEM_MAX));
             CK(cudaFuncSetAttribute(skern::saddle_apply_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)skern::SADDLE_APPLY_SMEM_MAX));
-            CK(cudaFuncSetAttribute(skern::saddle_apply_tma_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            CK(cudaFuncSetAttribute(skern::saddle_apply_bulk_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)skern::SADDLE_APPLY_SMEM_MAX));
-            CK(cudaFuncSetAttribute(skern::saddle_apply_tma_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            CK(cudaFuncSetAttribute(skern::saddle_apply_bulk_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)skern::SADDLE_APPLY_SMEM_MAX));
-            // the bulk-copy apply when two of the level's largest blocks fit
-            // in shared memory (persistent grid: as many CTAs as fit per SM)
+            // the bulk-copy apply when the level's largest block fits in
+            // shared memory with room for at least two CTAs per SM
             {
                 const int eb = want32 ? 4 : 8;
                 const std::vector<long long>& fo = want32 ? f32 : f64;
                 long long mb = 0;
                 for (int p = 0; p < l.npatch; ++p) mb = std::max(mb, fo[p + 1] - fo[p]);
                 const long long buf = (mb * eb + 127) & ~127LL;
-                const size_t smem = skern::saddle_apply_tma_smem((int)std::min<long long>(buf, 1 << 30), eb, l.sa_xs);
-                if (buf > 0 && smem <= skern::SADDLE_APPLY_SMEM_MAX && !std::getenv("STOKES_NO_BULK_APPLY")) {
-                    int per_sm = 0, nsm = 0;
-                    if (want32)
-                        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, skern::saddle_apply_tma_f32,
-                                                                         skern::SA_TMA_THREADS, smem));
-                    else
-                        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, skern::saddle_apply_tma_f64,
-                                                                         skern::SA_TMA_THREADS, smem));
-                    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-                    if (per_sm > 0) {
-                        l.sa_buf = (int)buf;
-                        l.sa_grid = std::min<long long>(l.npatch, (long long)per_sm * nsm);
-                    }
-                }
+                const size_t smem = skern::saddle_apply_bulk_smem((int)std::min<long long>(buf, 1 << 30), eb, l.sa_xs);
+                if (buf > 0 && smem <= skern::SADDLE_APPLY_SMEM_MAX / 2 && !std::getenv("STOKES_NO_BULK_APPLY"))
+                    l.sa_buf = (int)buf;
                 if (!h->sa_status) {
                     h->sa_status = halloc<int>(h, 1);
                     CK(cudaMemsetAsync(h->sa_status, 0, sizeof(int), s));
@@ -1724,7 +1716,8 @@ void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status,
         double* f64 = store ? l.fac64 : nullptr;
         float* f32 = store ? l.fac32 : nullptr;
         if (l.saddle_smem > 0) {
-            const size_t smem = (size_t)l.saddle_smem * sizeof(double);
+            const bool fac_only = !i64 && !i32 && !back;
+            const size_t smem = (size_t)(fac_only ? l.saddle_smem_fac : l.saddle_smem) * sizeof(double);
             // one upper bound for every level (levels launch from one thread
             // onto different streams)
             CK(cudaFuncSetAttribute(skern::saddle_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1877,6 +1870,29 @@ bool coarse_cluster_ok(stokes_mg* h, int nb, size_t* smem_out) {
 void launch_coarse(stokes_mg* h, cudaStream_t s) {
     const int nb = h->nc + 1;
     size_t smem = 0;
+    // blocked Gauss-Jordan on every SM: panels of B pivots (one CTA holds the
+    // panel's columns of all rows), trailing updates on 32 x 32 tiles
+    int B = skern::GJB_MAX_B;
+    while (B > 1 && skern::gj_block_panel_smem(nb, B) > 200 * 1024) B >>= 1;
+    if (skern::gj_block_panel_smem(nb, B) <= 200 * 1024 && !std::getenv("STOKES_COARSE_CLUSTER")) {
+        CK(cudaFuncSetAttribute(skern::gj_block_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        double* Pk = palloc<double>(h->device, (size_t)nb * B, s);
+        double* Yb = palloc<double>(h->device, (size_t)nb * B, s);
+        const dim3 ug((nb + 31) / 32, (nb + 31) / 32);
+        for (int k0 = 0; k0 < nb; k0 += B) {
+            const int b = std::min(B, nb - k0);
+            launch(h, -1, s, [&] {
+                skern::gj_block_panel<<<1, skern::GJB_THREADS, skern::gj_block_panel_smem(nb, b), s>>>(
+                    nb, k0, b, h->Cinv, h->c_ipiv, Pk, h->c_status);
+            });
+            launch(h, -1, s, [&] { skern::gj_block_swap<<<(nb + 255) / 256, 256, 0, s>>>(nb, k0, b, h->Cinv, h->c_ipiv, Yb); });
+            launch(h, -1, s, [&] { skern::gj_block_update<<<ug, 256, 0, s>>>(nb, k0, b, h->Cinv, Pk, Yb); });
+        }
+        launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
+        CK(cudaFreeAsync(Pk, s));
+        CK(cudaFreeAsync(Yb, s));
+        return;
+    }
     if (coarse_cluster_ok(h, nb, &smem)) {
         // the whole factorisation in one cluster launch
         launch(h, -1, s, [&] {
