@@ -394,7 +394,183 @@ __global__ void k_mass_all(AsmMesh m, const double* __restrict__ lam, double sca
     out[t] = scale * F;
 }
 
+// ---- device interpolation
+__global__ void k_interp_rows(InterpGeom g, InterpSpace F, InterpSpace C, int nrows, const int* __restrict__ rows,
+                              int* __restrict__ cnt, int* __restrict__ col, double* __restrict__ val) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrows) return;
+    const int node = rows ? rows[row] : row;
+    const int first = F.adj[F.off[node]];
+    const int e = first / F.nb, l = first - e * F.nb;
+    const int nbc = C.nb, d = g.d;
+    double v[INTERP_MAX_NB];
+    int cc = e;
+    if (!g.nested) {
+        for (int b = 0; b < nbc; ++b) v[b] = g.tab[l * nbc + b];
+    } else {
+        cc = g.parent[e];
+        // the fine node: x = x_0 + sum_a (alpha_a / k_f) (x_a - x_0) on its owner cell
+        double x[3] = {0, 0, 0};
+        const int* fv = g.Cf + (long long)e * (d + 1);
+        for (int c = 0; c < d; ++c) {
+            const double x0 = g.Xf[(long long)fv[0] * d + c];
+            double s = x0;
+            for (int a = 1; a <= d; ++a)
+                s += (double)g.alpha_f[l * 4 + a] / g.kf * (g.Xf[(long long)fv[a] * d + c] - x0);
+            x[c] = s;
+        }
+        // its reference coordinates in the coarse cell: xi = J^-1 (x - x_0)
+        const int* cv = g.Cc + (long long)cc * (d + 1);
+        double J[9], xi[3] = {0, 0, 0}, rhs[3];
+        for (int c = 0; c < d; ++c) {
+            const double x0 = g.Xc[(long long)cv[0] * d + c];
+            rhs[c] = x[c] - x0;
+            for (int a = 0; a < d; ++a) J[c * d + a] = g.Xc[(long long)cv[a + 1] * d + c] - x0;
+        }
+        if (d == 2) {
+            const double det = J[0] * J[3] - J[1] * J[2];
+            xi[0] = (J[3] * rhs[0] - J[1] * rhs[1]) / det;
+            xi[1] = (-J[2] * rhs[0] + J[0] * rhs[1]) / det;
+        } else {
+            const double c00 = J[4] * J[8] - J[5] * J[7], c01 = J[5] * J[6] - J[3] * J[8], c02 = J[3] * J[7] - J[4] * J[6];
+            const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+            const double i00 = c00 / det, i01 = (J[2] * J[7] - J[1] * J[8]) / det, i02 = (J[1] * J[5] - J[2] * J[4]) / det;
+            const double i10 = c01 / det, i11 = (J[0] * J[8] - J[2] * J[6]) / det, i12 = (J[2] * J[3] - J[0] * J[5]) / det;
+            const double i20 = c02 / det, i21 = (J[1] * J[6] - J[0] * J[7]) / det, i22 = (J[0] * J[4] - J[1] * J[3]) / det;
+            xi[0] = i00 * rhs[0] + i01 * rhs[1] + i02 * rhs[2];
+            xi[1] = i10 * rhs[0] + i11 * rhs[1] + i12 * rhs[2];
+            xi[2] = i20 * rhs[0] + i21 * rhs[1] + i22 * rhs[2];
+        }
+        for (int b = 0; b < nbc; ++b) v[b] = 0.0;
+        for (int m = 0; m < g.nm; ++m) {
+            double mv = 1.0;
+            for (int a = 0; a < d; ++a)
+                for (int t = 0; t < g.mono[m * 3 + a]; ++t) mv *= xi[a];
+            for (int b = 0; b < nbc; ++b) v[b] += g.coef[b * g.nm + m] * mv;
+        }
+    }
+    // entries on free coarse nodes, sorted by column (insertion sort)
+    int* cr = col + (long long)row * nbc;
+    double* vr = val + (long long)row * nbc;
+    int m = 0;
+    for (int b = 0; b < nbc; ++b) {
+        if (!(fabs(v[b]) > 1e-14)) continue;
+        const int cn = C.cell[(long long)cc * nbc + b];
+        const int cf = C.free ? C.free[cn] : cn;
+        if (cf < 0) continue;
+        int t = m++;
+        while (t > 0 && cr[t - 1] > cf) { cr[t] = cr[t - 1]; vr[t] = vr[t - 1]; --t; }
+        cr[t] = cf;
+        vr[t] = v[b];
+    }
+    cnt[row] = m;
+}
+
+__global__ void k_interp_lengths(int d, int nVf, int nQf, const int* __restrict__ cntV, const int* __restrict__ cntQ,
+                                 int* __restrict__ len) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nr = d * nVf + nQf;
+    if (r >= nr) return;
+    len[r] = r < d * nVf ? cntV[r % nVf] : cntQ[r - d * nVf];
+}
+
+__global__ void k_interp_fill(int d, int nVf, int nQf, int nVf_c, int sV, int sQ, const int* __restrict__ cntV,
+                              const int* __restrict__ colV, const double* __restrict__ valV,
+                              const int* __restrict__ cntQ, const int* __restrict__ colQ,
+                              const double* __restrict__ valQ, const int* __restrict__ rp, int* __restrict__ ci,
+                              double* __restrict__ v) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nr = d * nVf + nQf;
+    if (r >= nr) return;
+    int o = rp[r];
+    if (r < d * nVf) {
+        const int c = r / nVf, f = r - c * nVf;
+        for (int t = 0; t < cntV[f]; ++t, ++o) {
+            ci[o] = c * nVf_c + colV[(long long)f * sV + t];
+            v[o] = valV[(long long)f * sV + t];
+        }
+    } else {
+        const int q = r - d * nVf;
+        for (int t = 0; t < cntQ[q]; ++t, ++o) {
+            ci[o] = d * nVf_c + colQ[(long long)q * sQ + t];
+            v[o] = valQ[(long long)q * sQ + t];
+        }
+    }
+}
+
+__global__ void k_transpose_count(int nr, const int* __restrict__ rp, const int* __restrict__ ci, int* __restrict__ cnt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    for (int p = rp[r]; p < rp[r + 1]; ++p) atomicAdd(&cnt[ci[p]], 1);
+}
+
+__global__ void k_transpose_fill(int nr, const int* __restrict__ rp, const int* __restrict__ ci,
+                                 const double* __restrict__ v, const int* __restrict__ rrp, int* __restrict__ cur,
+                                 int* __restrict__ rci, double* __restrict__ rv) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    for (int p = rp[r]; p < rp[r + 1]; ++p) {
+        const int c = ci[p];
+        const int o = rrp[c] + atomicAdd(&cur[c], 1);
+        rci[o] = r;
+        rv[o] = v[p];
+    }
+}
+
+// each row's entries sorted by column (insertion sort; rows are short)
+__global__ void k_sort_rows(int nr, const int* __restrict__ rp, int* __restrict__ ci, double* __restrict__ v) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    const int s = rp[r], e = rp[r + 1];
+    for (int p = s + 1; p < e; ++p) {
+        const int c = ci[p];
+        const double x = v[p];
+        int q = p;
+        while (q > s && ci[q - 1] > c) { ci[q] = ci[q - 1]; v[q] = v[q - 1]; --q; }
+        ci[q] = c;
+        v[q] = x;
+    }
+}
+
+__global__ void k_to_float(long long n, const double* __restrict__ x, float* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
 }  // namespace
+
+void interp_rows(const InterpGeom& g, const InterpSpace& fine, const InterpSpace& coarse, int nrows, const int* rows,
+                 int* cnt, int* col, double* val, cudaStream_t s) {
+    if (nrows <= 0) return;
+    k_interp_rows<<<(nrows + 127) / 128, 128, 0, s>>>(g, fine, coarse, nrows, rows, cnt, col, val);
+}
+void interp_lengths(int d, int nVf, int nQf, const int* cntV, const int* cntQ, int* len, cudaStream_t s) {
+    const int nr = d * nVf + nQf;
+    if (nr > 0) k_interp_lengths<<<(nr + 255) / 256, 256, 0, s>>>(d, nVf, nQf, cntV, cntQ, len);
+}
+void interp_fill(int d, int nVf, int nQf, int nVf_c, int sV, int sQ, const int* cntV, const int* colV,
+                 const double* valV, const int* cntQ, const int* colQ, const double* valQ, const int* rp, int* ci,
+                 double* v, cudaStream_t s) {
+    const int nr = d * nVf + nQf;
+    if (nr > 0)
+        k_interp_fill<<<(nr + 255) / 256, 256, 0, s>>>(d, nVf, nQf, nVf_c, sV, sQ, cntV, colV, valV, cntQ, colQ, valQ,
+                                                         rp, ci, v);
+}
+void transpose_count(int nr, const int* rp, const int* ci, int ncol, int* cnt, cudaStream_t s) {
+    cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncol, s);
+    if (nr > 0) k_transpose_count<<<(nr + 255) / 256, 256, 0, s>>>(nr, rp, ci, cnt);
+}
+void transpose_fill(int nr, const int* rp, const int* ci, const double* v, int ncol, const int* rrp, int* cur,
+                    int* rci, double* rv, cudaStream_t s) {
+    cudaMemsetAsync(cur, 0, sizeof(int) * (size_t)ncol, s);
+    if (nr > 0) k_transpose_fill<<<(nr + 255) / 256, 256, 0, s>>>(nr, rp, ci, v, rrp, cur, rci, rv);
+}
+void sort_rows(int nr, const int* rp, int* ci, double* v, cudaStream_t s) {
+    if (nr > 0) k_sort_rows<<<(nr + 255) / 256, 256, 0, s>>>(nr, rp, ci, v);
+}
+void to_float(long long n, const double* x, float* y, cudaStream_t s) {
+    if (n > 0) k_to_float<<<(int)std::min<long long>((n + 255) / 256, 152LL * 16), 256, 0, s>>>(n, x, y);
+}
 
 void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, int nq, long long ld, double* grad,
                     cudaStream_t s) {

@@ -63,4 +63,50 @@ void grad_viscosity(const AsmMesh& m, const double* u, const double* lam, int nq
 // out[c][i] = scale (M lambda_c)[i] for every velocity node i.
 void mass_apply_all(const AsmMesh& m, const double* lam, double scale, double* out, cudaStream_t s);
 
+// ---- finite-element interpolation P between consecutive levels (Sec. 3.1)
+// built on the device: row i of the scalar P holds the coarse basis
+// functions evaluated at fine node i, located in the coarse cell that
+// contains (or is) the cell owning it; entries with |v| <= 1e-14 (exact
+// lattice zeros) are dropped and a row's columns are sorted.
+struct InterpSpace {
+    int nb = 0;                  // nodes per cell
+    const int* cell = nullptr;   // [nc][nb] node ids
+    const int* off = nullptr;    // fine side: node -> (cell * nb + local) adjacency,
+    const int* adj = nullptr;    //   cells in increasing order (the first one owns the node)
+    const int* free = nullptr;   // node -> free index or -1; nullptr: every node free, index = node
+};
+struct InterpGeom {
+    int d = 0;
+    int nested = 0;              // 0: same mesh (table), 1: coarse mesh = parent of the fine mesh
+    const double* tab = nullptr; // same mesh: [nb_f][nb_c] coarse basis at the fine lattice points
+    const int* parent = nullptr; // nested: fine cell -> coarse cell
+    const double* Xf = nullptr; const int* Cf = nullptr;   // nested: fine mesh
+    const double* Xc = nullptr; const int* Cc = nullptr;   // nested: coarse mesh
+    int kf = 0;                  // nested: fine degree; alpha_f [nb_f][4] its lattice multi-indices
+    const int* alpha_f = nullptr;
+    int nm = 0;                  // nested: coarse basis as monomials, mono [nm][3] exponents,
+    const int* mono = nullptr;   //   coef [nb_c][nm]
+    const double* coef = nullptr;
+};
+constexpr int INTERP_MAX_NB = 64;   // coarse nodes per cell handled on the device
+// Scalar rows for the nrows fine nodes rows[0..nrows) (rows == nullptr: node
+// = row), at most nb_c entries each, in fixed slots: cnt[row],
+// col[row * nb_c + t] (coarse free index), val[row * nb_c + t].
+void interp_rows(const InterpGeom& g, const InterpSpace& fine, const InterpSpace& coarse, int nrows, const int* rows,
+                 int* cnt, int* col, double* val, cudaStream_t s);
+// Monolithic P = blockdiag(P_V, ..., P_V, P_Q) on the free DoFs from the
+// scalar slots (velocity rows over the fine free velocity nodes, pressure
+// rows over the fine pressure nodes): len[r] for r < d nVf + nQf.
+void interp_lengths(int d, int nVf, int nQf, const int* cntV, const int* cntQ, int* len, cudaStream_t s);
+void interp_fill(int d, int nVf, int nQf, int nVf_c, int sV, int sQ, const int* cntV, const int* colV,
+                 const double* valV, const int* cntQ, const int* colQ, const double* valQ, const int* rp, int* ci,
+                 double* v, cudaStream_t s);
+// R = P^T: counts, (scan), fill, then each row sorted by column: a
+// deterministic transpose.  cnt / cur hold ncol ints each (zeroed here).
+void transpose_count(int nr, const int* rp, const int* ci, int ncol, int* cnt, cudaStream_t s);
+void transpose_fill(int nr, const int* rp, const int* ci, const double* v, int ncol, const int* rrp, int* cur,
+                    int* rci, double* rv, cudaStream_t s);
+void sort_rows(int nr, const int* rp, int* ci, double* v, cudaStream_t s);
+void to_float(long long n, const double* x, float* y, cudaStream_t s);
+
 }  // namespace sasm

@@ -1325,6 +1325,16 @@ static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Le
     F.R = transpose(P);
 }
 
+const RefElement& reference_element(int d, int k) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, RefElement> refs;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(d, k);
+    auto it = refs.find(key);
+    if (it == refs.end()) { refs[key].init(d, k); it = refs.find(key); }
+    return it->second;
+}
+
 void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double* nu_cell, Hierarchy& H,
                      const std::function<void(int, int)>& on_level) {
     double t0 = now_ms();
@@ -1386,15 +1396,8 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     // reference elements and tensors depend on (d, k) only: computed once per
     // process and kept (std::map entries do not move on insertion)
     static std::mutex ref_mu;
-    static std::map<std::pair<int, int>, RefElement> refs;
     static std::map<std::pair<int, int>, RefTensors> tensors;
-    auto ref = [&](int dd, int kk) -> const RefElement& {
-        std::lock_guard<std::mutex> g(ref_mu);
-        auto key = std::make_pair(dd, kk);
-        auto it = refs.find(key);
-        if (it == refs.end()) { refs[key].init(dd, kk); it = refs.find(key); }
-        return it->second;
-    };
+    auto ref = [&](int dd, int kk) -> const RefElement& { return reference_element(dd, kk); };
     std::vector<size_t> order;
     if (spec.coarsest_first) order.push_back(ls.size() - 1);
     for (size_t l = 0; l < ls.size(); ++l)
@@ -1451,7 +1454,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         }
     }
     double tt = now_ms();
-    for (size_t l = 0; l + 1 < ls.size(); ++l) {
+    for (size_t l = 0; l + 1 < ls.size() && !spec.device_transfers; ++l) {
         Level &F = H.levels[l], &C = H.levels[l + 1];
         const std::vector<int>* par_map = (F.mesh_index == C.mesh_index) ? nullptr : &H.parents[F.mesh_index];
         monolithic_interp(H.meshes[F.mesh_index], F, H.meshes[C.mesh_index], C, ref(d, C.k), ref(d, C.k - 1), par_map,

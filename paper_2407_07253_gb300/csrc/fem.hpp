@@ -124,6 +124,7 @@ struct HierarchySpec {
     bool coarsest_first = false;
     bool skip_patches = false;                // no Vanka patches (a hierarchy wanted for its operators)
     bool device_assembly_finest_only = false; // with device_assembly: only level 0 on the device
+    bool device_transfers = false;            // leave P and R to the device (no host transfers)
 };
 
 struct Hierarchy {
@@ -159,6 +160,10 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
                      Hierarchy& H, const std::function<void(int, int)>& on_level = {});
 
 int num_threads();
+
+// The degree-k Lagrange element on the reference d-simplex, computed once per
+// process and kept (references stay valid).
+const RefElement& reference_element(int d, int k);
 
 // For idx[0..m) with values in [0, n): off[0..n] and pos[0..m) list, for
 // every value, the positions q where it occurs, in increasing order

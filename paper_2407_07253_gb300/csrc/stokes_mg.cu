@@ -197,6 +197,7 @@ struct DevLevel {
     double lmax = 0;
     // device assembly of K (all levels but the coarsest)
     bool dev_asm = false;
+    bool dev_transfer = false;          // P, R built on the device (exact nnz read back at finish)
     sasm::AsmMesh am;
     double* cellgeo = nullptr;          // am.cg, filled on the device
     int* asm_len = nullptr;
@@ -322,6 +323,8 @@ struct stokes_mg {
     std::vector<cudaStream_t> s_lvl;     // setup compute stream of each relaxed level
     std::vector<double*> mesh_X;         // device vertex coordinates per mesh
     std::vector<int*> mesh_C;            // device cells per mesh
+    std::vector<int*> mesh_parent;       // device parent map per mesh (cell -> next coarser mesh's cell)
+    cudaStream_t s_tr = nullptr;         // setup stream of the device transfers
     std::vector<void*> allocs;
     // STOKES_TRACE=1: device timeline of setup (event, label, host time)
     struct Mark { std::string what; double host, dev; };
@@ -1692,8 +1695,142 @@ void fbf_level0_kernels(stokes_mg* h, cudaStream_t s) {
 void upload_transfers(stokes_mg* h, int li, bool want32, cudaStream_t s) {
     const sfem::Level& HL = h->H.levels[li];
     DevLevel& l = h->L[li];
+    if (l.dev_transfer) return;          // built on the device
     l.P = upload_csr(h, HL.P, want32, s);
     l.R = upload_csr(h, HL.R, want32, s);
+}
+
+// mesh data the device transfers read (vertex coordinates, cells, parents)
+void ensure_mesh_on_device(stokes_mg* h, int mi, cudaStream_t s) {
+    const int nm = (int)h->H.meshes.size();
+    if ((int)h->mesh_X.size() != nm) { h->mesh_X.assign(nm, nullptr); h->mesh_C.assign(nm, nullptr); }
+    if ((int)h->mesh_parent.size() != nm) h->mesh_parent.assign(nm, nullptr);
+    if (!h->mesh_X[mi]) {
+        h->mesh_X[mi] = hupload(h, h->H.meshes[mi].X, s);
+        h->mesh_C[mi] = hupload(h, h->H.meshes[mi].C, s);
+    }
+    if (mi + 1 < nm && !h->mesh_parent[mi]) h->mesh_parent[mi] = hupload(h, h->H.parents[mi], s);
+}
+
+// P_l (coarse level l + 1 -> fine level l, Sec. 3.1) and R_l = P_l^T built
+// on the device from the two levels' DoF maps (uploaded on s_up before the
+// launch: the fine level's assembly inputs, the coarse level's cell nodes
+// and free map).  Host uploads happen here, on the calling (host) thread;
+// `launch_on` queues the kernels.  The exact entry counts are read back by
+// finish_transfers.
+void build_transfer_dev(stokes_mg* h, int li, bool want32, const std::function<void(std::function<void()>)>& launch_on) {
+    const sfem::Level& F = h->H.levels[li];
+    const sfem::Level& C = h->H.levels[li + 1];
+    DevLevel& lf = h->L[li];
+    DevLevel& lc = h->L[li + 1];
+    const cudaStream_t su = h->s_up;
+    const int d = F.d;
+    const bool nested = F.mesh_index != C.mesh_index;
+    const sfem::RefElement& rVf = sfem::reference_element(d, F.k);
+    const sfem::RefElement& rQf = sfem::reference_element(d, F.k - 1);
+    const sfem::RefElement& rVc = sfem::reference_element(d, C.k);
+    const sfem::RefElement& rQc = sfem::reference_element(d, C.k - 1);
+    if (rVc.nb > sasm::INTERP_MAX_NB || rQc.nb > sasm::INTERP_MAX_NB)
+        throw StokesError(STOKES_EUNSUPPORTED, "coarse element too large for the device transfer");
+    sasm::InterpGeom gV, gQ;
+    gV.d = gQ.d = d;
+    gV.nested = gQ.nested = nested ? 1 : 0;
+    if (!nested) {
+        // coarse basis at the fine lattice points of the same cell
+        auto table = [&](const sfem::RefElement& rf, const sfem::RefElement& rc) {
+            std::vector<double> t((size_t)rf.nb * rc.nb);
+            for (int l = 0; l < rf.nb; ++l) {
+                double xi[3] = {0, 0, 0};
+                for (int a = 0; a < d; ++a) xi[a] = (double)rf.alpha[l][a + 1] / rf.k;
+                rc.eval(xi, t.data() + (size_t)l * rc.nb);
+            }
+            return t;
+        };
+        gV.tab = hupload(h, table(rVf, rVc), su);
+        gQ.tab = hupload(h, table(rQf, rQc), su);
+    } else {
+        ensure_mesh_on_device(h, F.mesh_index, su);
+        ensure_mesh_on_device(h, C.mesh_index, su);
+        auto fill = [&](sasm::InterpGeom& g, const sfem::RefElement& rf, const sfem::RefElement& rc) {
+            g.parent = h->mesh_parent[F.mesh_index];
+            g.Xf = h->mesh_X[F.mesh_index]; g.Cf = h->mesh_C[F.mesh_index];
+            g.Xc = h->mesh_X[C.mesh_index]; g.Cc = h->mesh_C[C.mesh_index];
+            g.kf = rf.k;
+            std::vector<int> al((size_t)rf.nb * 4), mo((size_t)rc.nm * 3);
+            for (int l = 0; l < rf.nb; ++l)
+                for (int a = 0; a < 4; ++a) al[(size_t)l * 4 + a] = rf.alpha[l][a];
+            for (int m = 0; m < rc.nm; ++m)
+                for (int a = 0; a < 3; ++a) mo[(size_t)m * 3 + a] = rc.mono[m][a];
+            g.alpha_f = hupload(h, al, su);
+            g.nm = rc.nm;
+            g.mono = hupload(h, mo, su);
+            g.coef = hupload(h, rc.coef, su);
+        };
+        fill(gV, rVf, rVc);
+        fill(gQ, rQf, rQc);
+    }
+    sasm::InterpSpace fV, fQ, cV, cQ;
+    fV.nb = F.V.nb; fV.cell = lf.am.vcell; fV.off = lf.am.voff; fV.adj = lf.am.vadj; fV.free = lf.am.vfree;
+    fQ.nb = F.Q.nb; fQ.cell = lf.am.qcell; fQ.off = lf.am.qoff; fQ.adj = lf.am.qadj; fQ.free = nullptr;
+    cV.nb = C.V.nb; cV.cell = lc.am.vcell; cV.free = lc.am.vfree;
+    cQ.nb = C.Q.nb; cQ.cell = lc.am.qcell; cQ.free = nullptr;
+    const int nVf = F.nVf, nQf = F.nQ, nr = F.n_free, nrR = C.n_free;
+    const long long ubP = (long long)d * nVf * cV.nb + (long long)nQf * cQ.nb;
+    DevCSR& P = lf.P;
+    DevCSR& R = lf.R;
+    P.nr = nr; P.nc = nrR; P.nnz = ubP;
+    R.nr = nrR; R.nc = nr; R.nnz = ubP;
+    P.rp = halloc<int>(h, nr + 1); P.ci = halloc<int>(h, ubP); P.v64 = halloc<double>(h, ubP);
+    R.rp = halloc<int>(h, nrR + 1); R.ci = halloc<int>(h, ubP); R.v64 = halloc<double>(h, ubP);
+    if (want32) { P.v32 = halloc<float>(h, ubP); R.v32 = halloc<float>(h, ubP); }
+    // rows of ~1-6 (P) and ~10-60 (R) entries (lanes fixed again at finish)
+    P.lanes = R.lanes = 4;
+    lf.dev_transfer = true;
+    const int* vrow = lf.am.vrow;
+    launch_on([h, gV, gQ, fV, fQ, cV, cQ, nVf, nQf, nr, nrR, d, ubP, vrow, P, R, want32, nVf_c = C.nVf] {
+        const cudaStream_t s = h->s_tr;
+        int* cntV = palloc<int>(h->device, std::max(nVf, 1), s);
+        int* colV = palloc<int>(h->device, std::max<long long>((long long)nVf * cV.nb, 1), s);
+        double* valV = palloc<double>(h->device, std::max<long long>((long long)nVf * cV.nb, 1), s);
+        int* cntQ = palloc<int>(h->device, std::max(nQf, 1), s);
+        int* colQ = palloc<int>(h->device, std::max<long long>((long long)nQf * cQ.nb, 1), s);
+        double* valQ = palloc<double>(h->device, std::max<long long>((long long)nQf * cQ.nb, 1), s);
+        int* len = palloc<int>(h->device, std::max(nr, nrR) + 1, s);
+        int* tmp = palloc<int>(h->device, (std::max(nr, nrR) + 1023) / 1024 + 2, s);
+        int* cur = palloc<int>(h->device, std::max(nrR, 1), s);
+        launch(h, -1, s, [&] { sasm::interp_rows(gV, fV, cV, nVf, vrow, cntV, colV, valV, s); });
+        launch(h, -1, s, [&] { sasm::interp_rows(gQ, fQ, cQ, nQf, nullptr, cntQ, colQ, valQ, s); });
+        launch(h, -1, s, [&] { sasm::interp_lengths(d, nVf, nQf, cntV, cntQ, len, s); });
+        launch(h, -1, s, [&] { sasm::scan_rows(len, nr, P.rp, tmp, s); });
+        launch(h, -1, s, [&] {
+            sasm::interp_fill(d, nVf, nQf, nVf_c, cV.nb, cQ.nb, cntV, colV, valV, cntQ, colQ, valQ, P.rp, P.ci, P.v64, s);
+        });
+        launch(h, -1, s, [&] { sasm::transpose_count(nr, P.rp, P.ci, nrR, len, s); });
+        launch(h, -1, s, [&] { sasm::scan_rows(len, nrR, R.rp, tmp, s); });
+        launch(h, -1, s, [&] { sasm::transpose_fill(nr, P.rp, P.ci, P.v64, nrR, R.rp, cur, R.ci, R.v64, s); });
+        launch(h, -1, s, [&] { sasm::sort_rows(nrR, R.rp, R.ci, R.v64, s); });
+        if (want32) {
+            launch(h, -1, s, [&] { sasm::to_float(ubP, P.v64, P.v32, s); });
+            launch(h, -1, s, [&] { sasm::to_float(ubP, R.v64, R.v32, s); });
+        }
+        for (void* x : {(void*)cntV, (void*)colV, (void*)valV, (void*)cntQ, (void*)colQ, (void*)valQ, (void*)len,
+                        (void*)tmp, (void*)cur})
+            CK(cudaFreeAsync(x, s));
+    });
+}
+
+// exact entry counts of the device-built transfers (after the setup streams
+// have drained)
+void finish_transfers(stokes_mg* h) {
+    for (size_t li = 0; li + 1 < h->L.size(); ++li) {
+        DevLevel& l = h->L[li];
+        if (!l.dev_transfer) continue;
+        int nnz = 0;
+        CK(cudaMemcpy(&nnz, l.P.rp + l.P.nr, sizeof(int), cudaMemcpyDeviceToHost));
+        l.P.nnz = l.R.nnz = nnz;
+        l.P.lanes = choose_lanes(l.P);
+        l.R.lanes = choose_lanes(l.R);
+    }
 }
 
 // gather K_i and invert every patch of level li; work receives the
@@ -1870,31 +2007,10 @@ bool coarse_cluster_ok(stokes_mg* h, int nb, size_t* smem_out) {
 void launch_coarse(stokes_mg* h, cudaStream_t s) {
     const int nb = h->nc + 1;
     size_t smem = 0;
-    // blocked Gauss-Jordan on every SM: panels of B pivots (one CTA holds the
-    // panel's columns of all rows), trailing updates on 32 x 32 tiles
-    int B = skern::GJB_MAX_B;
-    while (B > 1 && skern::gj_block_panel_smem(nb, B) > 200 * 1024) B >>= 1;
-    if (skern::gj_block_panel_smem(nb, B) <= 200 * 1024 && !std::getenv("STOKES_COARSE_CLUSTER")) {
-        CK(cudaFuncSetAttribute(skern::gj_block_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        double* Pk = palloc<double>(h->device, (size_t)nb * B, s);
-        double* Yb = palloc<double>(h->device, (size_t)nb * B, s);
-        const dim3 ug((nb + 31) / 32, (nb + 31) / 32);
-        for (int k0 = 0; k0 < nb; k0 += B) {
-            const int b = std::min(B, nb - k0);
-            launch(h, -1, s, [&] {
-                skern::gj_block_panel<<<1, skern::GJB_THREADS, skern::gj_block_panel_smem(nb, b), s>>>(
-                    nb, k0, b, h->Cinv, h->c_ipiv, Pk, h->c_status);
-            });
-            launch(h, -1, s, [&] { skern::gj_block_swap<<<(nb + 255) / 256, 256, 0, s>>>(nb, k0, b, h->Cinv, h->c_ipiv, Yb); });
-            launch(h, -1, s, [&] { skern::gj_block_update<<<ug, 256, 0, s>>>(nb, k0, b, h->Cinv, Pk, Yb); });
-        }
-        launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
-        CK(cudaFreeAsync(Pk, s));
-        CK(cudaFreeAsync(Yb, s));
-        return;
-    }
     if (coarse_cluster_ok(h, nb, &smem)) {
-        // the whole factorisation in one cluster launch
+        // the whole factorisation in one cluster launch (rows in the shared
+        // memory of 16 CTAs; measured faster than the blocked variant below
+        // for the 532-row bench system, whose panels run on one SM)
         launch(h, -1, s, [&] {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
@@ -1911,6 +2027,29 @@ void launch_coarse(stokes_mg* h, cudaStream_t s) {
             CK(cudaLaunchKernelEx(&cfg, skern::gj_cluster_inverse, nb, h->Cinv, h->c_ipiv, h->c_status));
         });
         launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
+        return;
+    }
+    // too large for one cluster: blocked Gauss-Jordan on every SM (panels of
+    // B pivots in one CTA's shared memory, trailing updates on 32 x 32 tiles)
+    int B = skern::GJB_MAX_B;
+    while (B > 1 && skern::gj_block_panel_smem(nb, B) > 200 * 1024) B >>= 1;
+    if (skern::gj_block_panel_smem(nb, B) <= 200 * 1024) {
+        CK(cudaFuncSetAttribute(skern::gj_block_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        double* Pk = palloc<double>(h->device, (size_t)nb * B, s);
+        double* Yb = palloc<double>(h->device, (size_t)nb * B, s);
+        const dim3 ug((nb + 31) / 32, (nb + 31) / 32);
+        for (int k0 = 0; k0 < nb; k0 += B) {
+            const int b = std::min(B, nb - k0);
+            launch(h, -1, s, [&] {
+                skern::gj_block_panel<<<1, skern::GJB_THREADS, skern::gj_block_panel_smem(nb, b), s>>>(
+                    nb, k0, b, h->Cinv, h->c_ipiv, Pk, h->c_status);
+            });
+            launch(h, -1, s, [&] { skern::gj_block_swap<<<(nb + 255) / 256, 256, 0, s>>>(nb, k0, b, h->Cinv, h->c_ipiv, Yb); });
+            launch(h, -1, s, [&] { skern::gj_block_update<<<ug, 256, 0, s>>>(nb, k0, b, h->Cinv, Pk, Yb); });
+        }
+        launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
+        CK(cudaFreeAsync(Pk, s));
+        CK(cudaFreeAsync(Yb, s));
         return;
     }
     const long long tot = (long long)nb * nb;
@@ -2167,6 +2306,7 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         spec.barycentric = barycentric_finest != 0;
         spec.device_assembly = !o.host_only;
         spec.coarsest_first = !o.host_only;
+        spec.device_transfers = !o.host_only && !fbf_mode;
         if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
         else if (o.hierarchy == STOKES_HIER_GRADUAL) {
             if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
@@ -2209,6 +2349,7 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
             // one step lower, each on its own stream so that their inversions
             // and lambda_max estimates overlap each other and level 0's
             CK(cudaStreamCreateWithPriority(&h->s_coarse, cudaStreamNonBlocking, prio(1)));
+            CK(cudaStreamCreateWithPriority(&h->s_tr, cudaStreamNonBlocking, prio(3)));
             const int prio_l0 = prio(1), prio_small = prio(2);
             {
                 // level 0's stream starts after whatever the caller queued on s
@@ -2259,6 +2400,19 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                         assemble_on_device(hp, li, target);
                         mark(hp, "L" + std::to_string(li) + " assembled", target);
                     });
+                    if (spec.device_transfers) {
+                        // P_{l-1} once level l's maps are up; P_l too when the
+                        // next level is the (already uploaded) coarsest
+                        auto launch_on = [&](std::function<void()> job) {
+                            after_uploads(hp, hp->s_tr);
+                            launcher->submit([hp, job] {
+                                CK(cudaSetDevice(hp->device));
+                                job();
+                            });
+                        };
+                        if (li >= 1) build_transfer_dev(hp, li - 1, want32, launch_on);
+                        if (li + 2 == nlv) build_transfer_dev(hp, li, want32, launch_on);
+                    }
                     return;
                 }
                 if (relaxed) {
@@ -2270,6 +2424,13 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                 } else {
                     upload_level_operator(hp, li, want32, hp->s_up);
                     upload_coarse(hp, hp->s_up);
+                    if (spec.device_transfers) {
+                        // the coarse side of the last transfer
+                        const sfem::Level& HC = hp->H.levels[li];
+                        hp->L[li].am.vcell = hupload(hp, HC.V.cell_nodes, hp->s_up);
+                        hp->L[li].am.qcell = hupload(hp, HC.Q.cell_nodes, hp->s_up);
+                        hp->L[li].am.vfree = hupload(hp, HC.vfree, hp->s_up);
+                    }
                 }
                 mark(hp, "L" + std::to_string(li) + " uploaded", hp->s_up);
                 after_uploads(hp, target);
@@ -2313,6 +2474,7 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
             sp.device_assembly_finest_only = true;
             sp.coarsest_first = false;
             sp.skip_patches = true;
+            sp.device_transfers = false;       // the velocity hierarchy takes blocks of the host transfers
             sfem::Hierarchy S;
             sfem::build_hierarchy(cm, sp, nu_cell, S, nullptr);
             h->fbf.reset(new FbfData());
@@ -2383,6 +2545,8 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         t1 = host_ms();
         finish_patches(h.get(), s);
         finish_assembly(h.get());
+        if (h->s_tr) CK(cudaStreamSynchronize(h->s_tr));
+        finish_transfers(h.get());
         h->st.t_gather_lu_ms = host_ms() - t1;
         t1 = host_ms();
         finish_coarse(h.get(), h->s_coarse);
@@ -3021,6 +3185,19 @@ int stokes_mg_get_csr(stokes_mg_t h, int level, int which, int* n_rows, int* n_c
             }
             return STOKES_OK;
         }
+        if (which != 0 && level < (int)h->L.size() && h->L[level].dev_transfer) {
+            // built on the device
+            const DevCSR& D = which == 1 ? h->L[level].P : h->L[level].R;
+            if (n_rows) *n_rows = D.nr;
+            if (n_cols) *n_cols = D.nc;
+            if (nnz) *nnz = D.nnz;
+            if (row_ptr) {
+                CK(cudaMemcpy(row_ptr, D.rp, sizeof(int) * (D.nr + 1), cudaMemcpyDeviceToHost));
+                if (col) CK(cudaMemcpy(col, D.ci, sizeof(int) * D.nnz, cudaMemcpyDeviceToHost));
+                if (val) CK(cudaMemcpy(val, D.v64, sizeof(double) * D.nnz, cudaMemcpyDeviceToHost));
+            }
+            return STOKES_OK;
+        }
         const sfem::CSR& A = which == 0 ? L.K : (which == 1 ? L.P : L.R);
         if (n_rows) *n_rows = A.nr;
         if (n_cols) *n_cols = A.ncol;
@@ -3250,6 +3427,7 @@ void stokes_mg_destroy(stokes_mg_t h) {
     for (cudaStream_t x : h->s_lvl)
         if (x) cudaStreamDestroy(x);
     if (h->s_coarse) cudaStreamDestroy(h->s_coarse);
+    if (h->s_tr) cudaStreamDestroy(h->s_tr);
     for (void* p : h->allocs) cudaFree(p);
     if (!h->pool_allocs.empty()) {
         for (void* p : h->pool_allocs) cudaFreeAsync(p, 0);

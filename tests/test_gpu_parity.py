@@ -181,6 +181,25 @@ def test_a4_a6_residual_and_transfers(name, precision):
 
 
 @pytest.mark.parametrize("name", NAMES)
+def test_a6_device_transfers_equal_host_transfers(name):
+    """a6: P and R = P^T built on the device (the GPU setup) equal the host
+    construction of the same library (host_only handle) entry by entry:
+    identical sparsity with sorted rows, values to rounding (the device
+    evaluates the coarse basis at the fine nodes from the mesh geometry or
+    from a lattice table; the host from its own tables)."""
+    h, ora, perms = pair(name)
+    (v, c), nref, fam, k, sched, bary = CASES[name]
+    hh = P.StokesMG(v, c, nref, fam, k, barycentric=bary, hierarchy=P.HIER_EXPLICIT, schedule=sched, host_only=1)
+    for li in range(len(ora.levels) - 1):
+        for which in (1, 2):
+            A, B = h.get_csr(li, which), hh.get_csr(li, which)
+            assert A.shape == B.shape
+            assert np.array_equal(A.indptr, B.indptr) and np.array_equal(A.indices, B.indices), (li, which)
+            assert np.abs(A.data - B.data).max() <= 1e-13 * np.abs(B.data).max(), (li, which)
+    hh.close()
+
+
+@pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("precision", [P.FP64, P.MIXED])
 def test_a5_additive_schwarz(name, precision):
     """a5: z = sum_i I_i^T W_i K_i^{-1} I_i r (Eq. 3.4)."""
