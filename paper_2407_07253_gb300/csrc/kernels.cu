@@ -1495,6 +1495,121 @@ __global__ void __launch_bounds__(GJB_THREADS) gj_block_panel(int n, int k0, int
     }
 }
 
+// The same panel held by one thread-block cluster of GJC_CTAS CTAs: CTA r
+// keeps rows [r R, (r + 1) R) of the panel's B columns in shared memory and
+// a pivot step is the one of gj_cluster_inverse restricted to those columns
+// (candidates -> cluster barrier -> pivot row and old row k read from their
+// owners -> cluster barrier -> own rows eliminated), so the per-pivot work
+// is R B instead of R n and the trailing columns are left to
+// gj_block_swap / gj_block_update on every SM.
+__global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, int B, double* __restrict__ A,
+                                                                int* __restrict__ ipiv, double* __restrict__ Pk,
+                                                                int* __restrict__ status) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ double gsm[];
+    const int R = (n + GJC_CTAS - 1) / GJC_CTAS;
+    const int rank = (int)cluster.block_rank();
+    const int r0 = rank * R, nr = max(0, min(R, n - r0));
+    double* rows = gsm;                         // [R][B] this CTA's rows of the panel
+    double* prow = rows + (size_t)R * B;        // [B] scaled pivot row
+    double* rowk = prow + B;                    // [B] old row k (CTA that owns p)
+    double* fcol = rowk + B;                    // [R] multiplier of my rows
+    __shared__ double cand_v[GJC_THREADS / 32], s_inv, s_cv, s_sv;
+    __shared__ int cand_i[GJC_THREADS / 32], s_p, s_ci;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    for (int t = tid; t < nr * B; t += nt) {
+        const int ii = t / B, j = t - ii * B;
+        rows[t] = A[(long long)(r0 + ii) * n + k0 + j];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < B; ++jj) {
+        const int k = k0 + jj;
+        double bv = -1.0;
+        int bi = n;
+        for (int ii = tid; ii < nr; ii += nt) {
+            const int i = r0 + ii;
+            if (i < k) continue;
+            const double av = fabs(rows[(size_t)ii * B + jj]);
+            if (av > bv) { bv = av; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { cand_v[warp] = bv; cand_i[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = -1.0;
+            int i0 = n;
+            for (int w = 0; w < nt / 32; ++w)
+                if (cand_v[w] > b || (cand_v[w] == b && cand_i[w] < i0)) { b = cand_v[w]; i0 = cand_i[w]; }
+            s_cv = b;
+            s_ci = i0;
+            s_sv = i0 < n ? rows[(size_t)(i0 - r0) * B + jj] : 0.0;
+        }
+        cluster.sync();                                            // (1) candidates visible
+        if (warp == 0) {
+            double b = -1.0, sgn = 0.0;
+            int p = n;
+            if (lane < GJC_CTAS) {
+                b = *cluster.map_shared_rank(&s_cv, lane);
+                p = *cluster.map_shared_rank(&s_ci, lane);
+                sgn = *cluster.map_shared_rank(&s_sv, lane);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, b, o), os = __shfl_down_sync(0xffffffffu, sgn, o);
+                const int op = __shfl_down_sync(0xffffffffu, p, o);
+                if (ob > b || (ob == b && op < p)) { b = ob; p = op; sgn = os; }
+            }
+            if (lane == 0) {
+                if (!(b > 0.0) || p >= n) {
+                    p = k;
+                    sgn = 0.0;
+                    if (rank == 0 && *status == 0) *status = k + 1;
+                }
+                s_p = p;
+                s_inv = sgn != 0.0 ? 1.0 / sgn : 0.0;
+                if (rank == 0) ipiv[k] = p;
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        const double inv = s_inv;
+        {
+            const double* src = cluster.map_shared_rank(rows, p / R) + (size_t)(p % R) * B;
+            for (int j = tid; j < B; j += nt) prow[j] = j == jj ? inv : src[j] * inv;
+            if (p != k && p >= r0 && p < r0 + nr) {
+                const double* srk = cluster.map_shared_rank(rows, k / R) + (size_t)(k % R) * B;
+                for (int j = tid; j < B; j += nt) rowk[j] = srk[j];
+            }
+        }
+        cluster.sync();                                            // (2) remote reads done
+        // per own row the multiplier f (old a_ik; for row p the old a_kk)
+        for (int ii = tid; ii < nr; ii += nt) fcol[ii] = (r0 + ii == p) ? rowk[jj] : rows[(size_t)ii * B + jj];
+        __syncthreads();
+        for (int t = tid; t < nr * B; t += nt) {
+            const int ii = t / B, j = t - ii * B;
+            const int i = r0 + ii;
+            double* row = rows + (size_t)ii * B;
+            if (i == k) {
+                row[j] = prow[j];
+            } else {
+                const double f = fcol[ii];
+                const double src = i == p ? rowk[j] : row[j];
+                row[j] = j == jj ? -f * inv : fma(-f, prow[j], src);
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < nr * B; t += nt) {
+        const int ii = t / B, j = t - ii * B;
+        A[(long long)(r0 + ii) * n + k0 + j] = rows[t];
+        Pk[(long long)(r0 + ii) * B + j] = rows[t];
+    }
+}
+
 // The panel's row swaps on every column outside it, and the swapped rows
 // k0 .. k0 + B - 1 copied to Yb[j n + c] (before the update overwrites them).
 __global__ void __launch_bounds__(256) gj_block_swap(int n, int k0, int B, double* __restrict__ A,

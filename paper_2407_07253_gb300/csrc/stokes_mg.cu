@@ -2004,46 +2004,79 @@ bool coarse_cluster_ok(stokes_mg* h, int nb, size_t* smem_out) {
     return nclusters > 0;
 }
 
+// can one cluster of GJC_CTAS CTAs run gj_cluster_panel with this much
+// dynamic shared memory on this device?
+bool cluster_panel_ok(stokes_mg* h, size_t smem) {
+    if (cudaFuncSetAttribute(skern::gj_cluster_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(skern::gj_cluster_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = skern::GJC_CTAS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(skern::GJC_CTAS);
+    cfg.blockDim = dim3(skern::GJC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, skern::gj_cluster_panel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters > 0;
+}
+
 void launch_coarse(stokes_mg* h, cudaStream_t s) {
     const int nb = h->nc + 1;
-    size_t smem = 0;
-    if (coarse_cluster_ok(h, nb, &smem)) {
-        // the whole factorisation in one cluster launch (rows in the shared
-        // memory of 16 CTAs; measured faster than the blocked variant below
-        // for the 532-row bench system, whose panels run on one SM)
-        launch(h, -1, s, [&] {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = skern::GJC_CTAS;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(skern::GJC_CTAS);
-            cfg.blockDim = dim3(skern::GJC_THREADS);
-            cfg.dynamicSmemBytes = smem;
-            cfg.stream = s;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            CK(cudaLaunchKernelEx(&cfg, skern::gj_cluster_inverse, nb, h->Cinv, h->c_ipiv, h->c_status));
-        });
-        launch(h, -1, s, [&] { skern::gj_unpivot_rows<<<grid_for(nb), 256, 0, s>>>(nb, h->Cinv, h->c_ipiv); });
-        return;
-    }
-    // too large for one cluster: blocked Gauss-Jordan on every SM (panels of
-    // B pivots in one CTA's shared memory, trailing updates on 32 x 32 tiles)
-    int B = skern::GJB_MAX_B;
-    while (B > 1 && skern::gj_block_panel_smem(nb, B) > 200 * 1024) B >>= 1;
-    if (skern::gj_block_panel_smem(nb, B) <= 200 * 1024) {
-        CK(cudaFuncSetAttribute(skern::gj_block_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        double* Pk = palloc<double>(h->device, (size_t)nb * B, s);
-        double* Yb = palloc<double>(h->device, (size_t)nb * B, s);
+    // blocked Gauss-Jordan: the pivots of a panel of B columns on one cluster
+    // of 16 CTAs (each holding its share of the rows of the panel), then the
+    // panel's row swaps and the rank-B update of every other column on all
+    // SMs (32 x 32 tiles).  The per-pivot cluster work is rows/16 x B, so the
+    // pivot chain costs little more than its two cluster barriers per pivot.
+    const int B = skern::GJB_MAX_B;
+    const size_t psmem = (size_t)skern::gj_cluster_panel_smem_doubles(nb, B) * sizeof(double);
+    const bool clus = cluster_panel_ok(h, psmem);
+    if (!clus) CK(cudaFuncSetAttribute(skern::gj_block_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    const int Bb = [&] {
+        int b = B;
+        while (!clus && b > 1 && skern::gj_block_panel_smem(nb, b) > 200 * 1024) b >>= 1;
+        return b;
+    }();
+    if (clus || skern::gj_block_panel_smem(nb, Bb) <= 200 * 1024) {
+        double* Pk = palloc<double>(h->device, (size_t)nb * Bb, s);
+        double* Yb = palloc<double>(h->device, (size_t)nb * Bb, s);
         const dim3 ug((nb + 31) / 32, (nb + 31) / 32);
-        for (int k0 = 0; k0 < nb; k0 += B) {
-            const int b = std::min(B, nb - k0);
-            launch(h, -1, s, [&] {
-                skern::gj_block_panel<<<1, skern::GJB_THREADS, skern::gj_block_panel_smem(nb, b), s>>>(
-                    nb, k0, b, h->Cinv, h->c_ipiv, Pk, h->c_status);
-            });
+        for (int k0 = 0; k0 < nb; k0 += Bb) {
+            const int b = std::min(Bb, nb - k0);
+            if (clus) {
+                launch(h, -1, s, [&] {
+                    cudaLaunchConfig_t cfg = {};
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeClusterDimension;
+                    attr[0].val.clusterDim.x = skern::GJC_CTAS;
+                    attr[0].val.clusterDim.y = 1;
+                    attr[0].val.clusterDim.z = 1;
+                    cfg.gridDim = dim3(skern::GJC_CTAS);
+                    cfg.blockDim = dim3(skern::GJC_THREADS);
+                    cfg.dynamicSmemBytes = psmem;
+                    cfg.stream = s;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    CK(cudaLaunchKernelEx(&cfg, skern::gj_cluster_panel, nb, k0, b, h->Cinv, h->c_ipiv, Pk,
+                                          h->c_status));
+                });
+            } else {
+                launch(h, -1, s, [&] {
+                    skern::gj_block_panel<<<1, skern::GJB_THREADS, skern::gj_block_panel_smem(nb, b), s>>>(
+                        nb, k0, b, h->Cinv, h->c_ipiv, Pk, h->c_status);
+                });
+            }
             launch(h, -1, s, [&] { skern::gj_block_swap<<<(nb + 255) / 256, 256, 0, s>>>(nb, k0, b, h->Cinv, h->c_ipiv, Yb); });
             launch(h, -1, s, [&] { skern::gj_block_update<<<ug, 256, 0, s>>>(nb, k0, b, h->Cinv, Pk, Yb); });
         }
