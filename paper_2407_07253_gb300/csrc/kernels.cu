@@ -721,7 +721,7 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
 // is written out as soon as it exists and S = sum_c B_c W_c accumulates over
 // the components.  Scratch: saddle_scratch_factored(d, n, nv) doubles.
 __device__ void saddle_core_factored(int d, int n, int nv, const double* K, double* scratch, double* fac64,
-                                     float* fac32, int* status) {
+                                     float* fac32, int packed, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int np = n - d * nv, npp = np | 1, dnv = d * nv;
@@ -733,17 +733,33 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, doub
     double* ck = Ss + (long long)np * np;          // [2][mx]
     double* cs = ck + 2 * mx;                      // [mx]
     double* rinv = cs + mx;                        // [2]
-    const int ldl = fac64 ? (nv + 1) & ~1 : (nv + 3) & ~3;
-    const int ldw = fac64 ? (dnv + 1) & ~1 : (dnv + 3) & ~3;
-    const int lds = fac64 ? (np + 1) & ~1 : (np + 3) & ~3;
-    const long long oW = (long long)ldl * nv, oS = oW + (long long)ldw * np;
+    const int vec = fac64 ? 2 : 4;
+    const int ldl = (nv + vec - 1) / vec * vec;
+    const int ldw = (dnv + vec - 1) / vec * vec;
+    const int lds = (np + vec - 1) / vec * vec;
+    const long long lenL = packed ? ((long long)nv * (nv + 1) / 2 + vec - 1) / vec * vec : (long long)ldl * nv;
+    const long long oW = lenL, oS = oW + (long long)ldw * np;
     const int ns = np * (np + 1) / 2;
     for (int i = warp; i < nv; i += nw)
         for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
     for (int t = tid; t < np * np; t += nt) Ss[t] = 0.0;
     __syncthreads();
     sweep_spd(Ls, nv, nv, ck, cs, rinv, status);
-    {
+    if (packed) {
+        // upper triangle row by row: (a, b >= a) at a nv - a (a - 1) / 2 + b - a
+        for (int a = warp; a < nv; a += nw) {
+            const long long o = (long long)a * nv - (long long)a * (a - 1) / 2 - a;
+            for (int b = a + lane; b < nv; b += 32) {
+                const double v = Ls[a * nv + b];
+                if (fac64) fac64[o + b] = v;
+                if (fac32) fac32[o + b] = (float)v;
+            }
+        }
+        for (long long t = (long long)nv * (nv + 1) / 2 + tid; t < lenL; t += nt) {
+            if (fac64) fac64[t] = 0.0;
+            if (fac32) fac32[t] = 0.0f;
+        }
+    } else {
         const int tot = nv * ldl;
         for (int t = tid; t < tot; t += nt) {
             const int b = t / ldl, a = t - b * ldl;
@@ -751,6 +767,8 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, doub
             if (fac64) fac64[t] = v;
             if (fac32) fac32[t] = (float)v;
         }
+    }
+    {
         // W's padding rows
         for (int t = tid; t < np * (ldw - dnv); t += nt) {
             const int q = t / (ldw - dnv), r = dnv + t - q * (ldw - dnv);
@@ -808,8 +826,8 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
                                                            double* __restrict__ inv64, const long long* __restrict__ off32,
                                                            float* __restrict__ inv32, const long long* __restrict__ foff64,
                                                            double* __restrict__ fac64, const long long* __restrict__ foff32,
-                                                           float* __restrict__ fac32, int back, long long max_scratch,
-                                                           int* __restrict__ status) {
+                                                           float* __restrict__ fac32, int back, int packed,
+                                                           long long max_scratch, int* __restrict__ status) {
     extern __shared__ double sscr[];
     const int p = blockIdx.x;
     const int n = poff[p + 1] - poff[p], nv = pnv[p];
@@ -819,7 +837,7 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
     __syncthreads();
     if (!inv64 && !inv32 && !back)
         saddle_core_factored(d, n, nv, work + moff[p], sscr, fac64 ? fac64 + foff64[p] : nullptr,
-                             fac32 ? fac32 + foff32[p] : nullptr, &st);
+                             fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
     else
         saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr,
                     inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
@@ -834,9 +852,9 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
                                                              double* __restrict__ inv64, const long long* __restrict__ off32,
                                                              float* __restrict__ inv32, const long long* __restrict__ foff64,
                                                              double* __restrict__ fac64, const long long* __restrict__ foff32,
-                                                             float* __restrict__ fac32, int back, long long max_scratch,
-                                                             const long long* __restrict__ soff, double* __restrict__ scratch,
-                                                             int* __restrict__ status) {
+                                                             float* __restrict__ fac32, int back, int packed,
+                                                             long long max_scratch, const long long* __restrict__ soff,
+                                                             double* __restrict__ scratch, int* __restrict__ status) {
     const int p = blockIdx.x;
     const int n = poff[p + 1] - poff[p], nv = pnv[p];
     if (n == 0 || saddle_scratch(d, n, nv) <= max_scratch) return;
@@ -845,7 +863,7 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
     __syncthreads();
     if (!inv64 && !inv32 && !back)
         saddle_core_factored(d, n, nv, work + moff[p], scratch + soff[p], fac64 ? fac64 + foff64[p] : nullptr,
-                             fac32 ? fac32 + foff32[p] : nullptr, &st);
+                             fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
     else
         saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,
                     inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
@@ -1186,10 +1204,11 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
         }
         return;
     }
-    const int ldl = (nv + VEC - 1) / VEC * VEC, ldw = (dnv + VEC - 1) / VEC * VEC;
+    const int ldw = (dnv + VEC - 1) / VEC * VEC;
     const int lds = (np + VEC - 1) / VEC * VEC;
-    const T* Li = reinterpret_cast<const T*>(smem);
-    const T* Wm = Li + ldl * nv;
+    const int lenL = (nv * (nv + 1) / 2 + VEC - 1) / VEC * VEC;
+    const T* Lp = reinterpret_cast<const T*>(smem);            // Li, packed upper triangle
+    const T* Wm = Lp + lenL;
     const T* Si = Wm + ldw * np;
     for (int q = warp; q < np; q += NT / 32) {
         const T* wc = Wm + q * ldw;
@@ -1199,11 +1218,19 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) tq[q] = xs[dnv + q] - acc;
     }
+    // y_c = Li r_c: Li[a][bb] is packed entry (min, max); walking bb, the
+    // column-a part (bb < a) advances by nv - 1 - bb, the row-a part by 1
     for (int t = tid; t < dnv; t += NT) {
         const int c = t / nv, a = t - c * nv;
         const T* xc = xs + c * nv;
+        const int offa = a * nv - a * (a - 1) / 2 - a;
         T acc = 0;
-        for (int bb = 0; bb < nv; ++bb) acc += Li[bb * ldl + a] * xc[bb];
+        int up = a;                                            // (bb, a), bb < a
+        for (int bb = 0; bb < nv; ++bb) {
+            const int idx = bb < a ? up : offa + bb;
+            acc += Lp[idx] * xc[bb];
+            up += nv - 1 - bb;
+        }
         ys[t] = acc;
     }
     __syncthreads();
@@ -1496,12 +1523,17 @@ __global__ void __launch_bounds__(GJB_THREADS) gj_block_panel(int n, int k0, int
 }
 
 // The same panel held by one thread-block cluster of GJC_CTAS CTAs: CTA r
-// keeps rows [r R, (r + 1) R) of the panel's B columns in shared memory and
-// a pivot step is the one of gj_cluster_inverse restricted to those columns
-// (candidates -> cluster barrier -> pivot row and old row k read from their
-// owners -> cluster barrier -> own rows eliminated), so the per-pivot work
-// is R B instead of R n and the trailing columns are left to
-// gj_block_swap / gj_block_update on every SM.
+// keeps rows [r R, (r + 1) R) of the panel's B columns in shared memory, in
+// two buffers that alternate by pivot step, so one cluster barrier per pivot
+// suffices: a step reads the current buffer (its own and, through distributed
+// shared memory, the pivot row and the old row k of their owners) and writes
+// the other, which nobody reads before the next barrier.  A step:
+//   own candidate (largest |a_ik| over own rows i >= k; ties to the smaller
+//   row) -> cluster barrier -> the 16 candidates read, pivot p chosen alike
+//   everywhere -> pivot row (scaled by 1 / a_pk) and, in the CTA owning p,
+//   the old row k read -> own rows eliminated into the other buffer.
+// The per-pivot work is R B; the trailing columns are left to gj_block_swap
+// / gj_block_update on every SM.
 __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, int B, double* __restrict__ A,
                                                                 int* __restrict__ ipiv, double* __restrict__ Pk,
                                                                 int* __restrict__ status) {
@@ -1511,26 +1543,29 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, i
     const int R = (n + GJC_CTAS - 1) / GJC_CTAS;
     const int rank = (int)cluster.block_rank();
     const int r0 = rank * R, nr = max(0, min(R, n - r0));
-    double* rows = gsm;                         // [R][B] this CTA's rows of the panel
-    double* prow = rows + (size_t)R * B;        // [B] scaled pivot row
-    double* rowk = prow + B;                    // [B] old row k (CTA that owns p)
-    double* fcol = rowk + B;                    // [R] multiplier of my rows
-    __shared__ double cand_v[GJC_THREADS / 32], s_inv, s_cv, s_sv;
-    __shared__ int cand_i[GJC_THREADS / 32], s_p, s_ci;
+    double* buf0 = gsm;                          // [R][B] rows, even steps read this one
+    double* buf1 = buf0 + (size_t)R * B;         // [R][B] odd steps read this one
+    double* prow = buf1 + (size_t)R * B;         // [B] scaled pivot row
+    double* rowk = prow + B;                     // [B] old row k (CTA that owns p)
+    double* fcol = rowk + B;                     // [R] multiplier of my rows
+    __shared__ double cand_v[GJC_THREADS / 32], s_inv, s_cv[2], s_sv[2];
+    __shared__ int cand_i[GJC_THREADS / 32], s_p, s_ci[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     for (int t = tid; t < nr * B; t += nt) {
         const int ii = t / B, j = t - ii * B;
-        rows[t] = A[(long long)(r0 + ii) * n + k0 + j];
+        buf0[t] = A[(long long)(r0 + ii) * n + k0 + j];
     }
     __syncthreads();
     for (int jj = 0; jj < B; ++jj) {
-        const int k = k0 + jj;
+        const int k = k0 + jj, par = jj & 1;
+        double* cur = par ? buf1 : buf0;
+        double* nxt = par ? buf0 : buf1;
         double bv = -1.0;
         int bi = n;
         for (int ii = tid; ii < nr; ii += nt) {
             const int i = r0 + ii;
             if (i < k) continue;
-            const double av = fabs(rows[(size_t)ii * B + jj]);
+            const double av = fabs(cur[(size_t)ii * B + jj]);
             if (av > bv) { bv = av; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -1545,18 +1580,18 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, i
             int i0 = n;
             for (int w = 0; w < nt / 32; ++w)
                 if (cand_v[w] > b || (cand_v[w] == b && cand_i[w] < i0)) { b = cand_v[w]; i0 = cand_i[w]; }
-            s_cv = b;
-            s_ci = i0;
-            s_sv = i0 < n ? rows[(size_t)(i0 - r0) * B + jj] : 0.0;
+            s_cv[par] = b;
+            s_ci[par] = i0;
+            s_sv[par] = i0 < n ? cur[(size_t)(i0 - r0) * B + jj] : 0.0;
         }
-        cluster.sync();                                            // (1) candidates visible
+        cluster.sync();                                            // candidates and rows of this step visible
         if (warp == 0) {
             double b = -1.0, sgn = 0.0;
             int p = n;
             if (lane < GJC_CTAS) {
-                b = *cluster.map_shared_rank(&s_cv, lane);
-                p = *cluster.map_shared_rank(&s_ci, lane);
-                sgn = *cluster.map_shared_rank(&s_sv, lane);
+                b = *cluster.map_shared_rank(&s_cv[par], lane);
+                p = *cluster.map_shared_rank(&s_ci[par], lane);
+                sgn = *cluster.map_shared_rank(&s_sv[par], lane);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const double ob = __shfl_down_sync(0xffffffffu, b, o), os = __shfl_down_sync(0xffffffffu, sgn, o);
@@ -1578,35 +1613,36 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, i
         const int p = s_p;
         const double inv = s_inv;
         {
-            const double* src = cluster.map_shared_rank(rows, p / R) + (size_t)(p % R) * B;
+            const double* src = cluster.map_shared_rank(cur, p / R) + (size_t)(p % R) * B;
             for (int j = tid; j < B; j += nt) prow[j] = j == jj ? inv : src[j] * inv;
             if (p != k && p >= r0 && p < r0 + nr) {
-                const double* srk = cluster.map_shared_rank(rows, k / R) + (size_t)(k % R) * B;
+                const double* srk = cluster.map_shared_rank(cur, k / R) + (size_t)(k % R) * B;
                 for (int j = tid; j < B; j += nt) rowk[j] = srk[j];
             }
         }
-        cluster.sync();                                            // (2) remote reads done
-        // per own row the multiplier f (old a_ik; for row p the old a_kk)
-        for (int ii = tid; ii < nr; ii += nt) fcol[ii] = (r0 + ii == p) ? rowk[jj] : rows[(size_t)ii * B + jj];
+        __syncthreads();
+        for (int ii = tid; ii < nr; ii += nt) fcol[ii] = (r0 + ii == p) ? rowk[jj] : cur[(size_t)ii * B + jj];
         __syncthreads();
         for (int t = tid; t < nr * B; t += nt) {
             const int ii = t / B, j = t - ii * B;
             const int i = r0 + ii;
-            double* row = rows + (size_t)ii * B;
             if (i == k) {
-                row[j] = prow[j];
+                nxt[t] = prow[j];
             } else {
                 const double f = fcol[ii];
-                const double src = i == p ? rowk[j] : row[j];
-                row[j] = j == jj ? -f * inv : fma(-f, prow[j], src);
+                const double src = i == p ? rowk[j] : cur[t];
+                nxt[t] = j == jj ? -f * inv : fma(-f, prow[j], src);
             }
         }
         __syncthreads();
     }
+    // every CTA must be done reading the others' buffers before any exits
+    cluster.sync();
+    const double* fin = (B & 1) ? buf1 : buf0;
     for (int t = tid; t < nr * B; t += nt) {
         const int ii = t / B, j = t - ii * B;
-        A[(long long)(r0 + ii) * n + k0 + j] = rows[t];
-        Pk[(long long)(r0 + ii) * B + j] = rows[t];
+        A[(long long)(r0 + ii) * n + k0 + j] = fin[t];
+        Pk[(long long)(r0 + ii) * B + j] = fin[t];
     }
 }
 

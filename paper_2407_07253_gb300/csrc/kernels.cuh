@@ -170,22 +170,25 @@ __global__ void saddle_inverse_smem(int npatch, int d, const int* __restrict__ p
                                     const long long* __restrict__ off32, float* __restrict__ inv32,
                                     const long long* __restrict__ foff64, double* __restrict__ fac64,
                                     const long long* __restrict__ foff32, float* __restrict__ fac32, int back,
-                                    long long max_scratch, int* __restrict__ status);
+                                    int packed, long long max_scratch, int* __restrict__ status);
 __global__ void saddle_inverse_global(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
                                       const long long* __restrict__ moff, double* __restrict__ work,
                                       const long long* __restrict__ off64, double* __restrict__ inv64,
                                       const long long* __restrict__ off32, float* __restrict__ inv32,
                                       const long long* __restrict__ foff64, double* __restrict__ fac64,
                                       const long long* __restrict__ foff32, float* __restrict__ fac32, int back,
-                                      long long max_scratch, const long long* __restrict__ soff,
+                                      int packed, long long max_scratch, const long long* __restrict__ soff,
                                       double* __restrict__ scratch, int* __restrict__ status);
 // Elements of one patch's factored inverse (Li, W, Si with leading
-// dimensions rounded up to vec = 2 (FP64) or 4 (FP32)).
-__host__ __device__ inline long long saddle_factor_len(int d, int n, int nv, int vec) {
+// dimensions rounded up to vec = 2 (FP64) or 4 (FP32)); packed: Li as its
+// upper triangle row by row (nv (nv + 1) / 2 entries, rounded up to vec),
+// the layout of the bulk-copy apply.
+__host__ __device__ inline long long saddle_factor_len(int d, int n, int nv, int vec, int packed = 0) {
     const int np = n - d * nv;
     const long long ldl = (nv + vec - 1) / vec * vec, ldw = (d * nv + vec - 1) / vec * vec,
                     lds = (np + vec - 1) / vec * vec;
-    return ldl * nv + ldw * np + lds * np;
+    const long long lenL = packed ? ((long long)nv * (nv + 1) / 2 + vec - 1) / vec * vec : ldl * nv;
+    return lenL + ldw * np + lds * np;
 }
 // Shared memory (bytes) of saddle_apply_*: partial sums, W (ws_len
 // elements; 0 = W read from global memory), and five vectors of xs_len
@@ -280,7 +283,7 @@ __host__ __device__ inline long long gj_cluster_smem_doubles(int n) {
 // gj_cluster_panel_smem_doubles(n, B) doubles of dynamic shared memory.
 __host__ __device__ inline long long gj_cluster_panel_smem_doubles(int n, int B) {
     const long long R = (n + GJC_CTAS - 1) / GJC_CTAS;
-    return R * B + 2LL * B + R;
+    return 2 * R * B + 2LL * B + R;
 }
 __global__ void gj_cluster_panel(int n, int k0, int B, double* __restrict__ A, int* __restrict__ ipiv,
                                  double* __restrict__ Pk, int* __restrict__ status);

@@ -186,6 +186,7 @@ struct DevLevel {
     int sa_xs = 0;                      // saddle apply: largest patch
     long long sa_ws64 = 0, sa_ws32 = 0; // saddle apply: largest W (elements)
     int sa_buf = 0;                     // bulk-copy apply: buffer bytes (0: not used on this level)
+    bool fac_packed = false;            // L^-1 stored as its packed upper triangle (bulk-copy apply only)
     double* wt64 = nullptr;
     float* wt32 = nullptr;
     int *soff = nullptr, *sidx = nullptr;
@@ -1508,17 +1509,27 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
                                     (int)skern::SADDLE_APPLY_SMEM_MAX));
             CK(cudaFuncSetAttribute(skern::saddle_apply_bulk_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)skern::SADDLE_APPLY_SMEM_MAX));
-            // the bulk-copy apply when the level's largest block fits in
-            // shared memory with room for at least two CTAs per SM
+            // the bulk-copy apply, with L^-1 stored as its packed upper
+            // triangle, when the level's largest packed block fits in shared
+            // memory with room for at least two CTAs per SM
             {
-                const int eb = want32 ? 4 : 8;
-                const std::vector<long long>& fo = want32 ? f32 : f64;
+                const int eb = want32 ? 4 : 8, vec = 16 / eb;
                 long long mb = 0;
-                for (int p = 0; p < l.npatch; ++p) mb = std::max(mb, fo[p + 1] - fo[p]);
+                std::vector<long long> fp(l.npatch + 1, 0);
+                for (int p = 0; p < l.npatch; ++p) {
+                    const long long len = skern::saddle_factor_len(HL.d, HL.patch_off[p + 1] - HL.patch_off[p],
+                                                                   HL.patch_nv[p], vec, 1);
+                    fp[p + 1] = fp[p] + len;
+                    mb = std::max(mb, len);
+                }
                 const long long buf = (mb * eb + 127) & ~127LL;
                 const size_t smem = skern::saddle_apply_bulk_smem((int)std::min<long long>(buf, 1 << 30), eb, l.sa_xs);
-                if (buf > 0 && smem <= skern::SADDLE_APPLY_SMEM_MAX / 2 && !std::getenv("STOKES_NO_BULK_APPLY"))
+                if (buf > 0 && smem <= skern::SADDLE_APPLY_SMEM_MAX / 2 && !std::getenv("STOKES_NO_BULK_APPLY")) {
                     l.sa_buf = (int)buf;
+                    l.fac_packed = true;
+                    (want32 ? f32 : f64) = fp;
+                    (want32 ? l.nfac32 : l.nfac64) = fp[l.npatch];
+                }
                 if (!h->sa_status) {
                     h->sa_status = halloc<int>(h, 1);
                     CK(cudaMemsetAsync(h->sa_status, 0, sizeof(int), s));
@@ -1862,7 +1873,8 @@ void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status,
             launch(h, PK_GJ, s, [&] {
                 skern::saddle_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
                                                                        l.ioff32, i32, l.foff64, f64, l.foff32, f32, back,
-                                                                       skern::SADDLE_SMEM_MAX_DOUBLES, status);
+                                                                       l.fac_packed ? 1 : 0, skern::SADDLE_SMEM_MAX_DOUBLES,
+                                                                       status);
             });
         }
         if (l.saddle_global > 0) {
@@ -1872,7 +1884,8 @@ void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status,
             launch(h, PK_GJ, s, [&] {
                 skern::saddle_inverse_global<<<l.npatch, 256, 0, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
                                                                       l.ioff32, i32, l.foff64, f64, l.foff32, f32, back,
-                                                                      skern::SADDLE_SMEM_MAX_DOUBLES, l.scoff, scr, status);
+                                                                      l.fac_packed ? 1 : 0, skern::SADDLE_SMEM_MAX_DOUBLES,
+                                                                      l.scoff, scr, status);
             });
             CK(cudaFreeAsync(scr, s));
         }
@@ -2376,12 +2389,13 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
             CK(cudaStreamCreateWithPriority(&h->s_up, cudaStreamNonBlocking, prio(0)));
             // level 0 (the critical path: largest inversion, then its
             // lambda_max estimate) runs on its own stream one step below the
-            // uploads; the coarse Gauss-Jordan, a chain of small latency-bound
-            // launches, at the same priority so that its blocks are placed
-            // between the patch-inversion blocks; the other relaxed levels
-            // one step lower, each on its own stream so that their inversions
-            // and lambda_max estimates overlap each other and level 0's
-            CK(cudaStreamCreateWithPriority(&h->s_coarse, cudaStreamNonBlocking, prio(1)));
+            // uploads; the other relaxed levels one step lower, each on its
+            // own stream so that their inversions and lambda_max estimates
+            // overlap each other and level 0's.  The coarse factorisation is
+            // a chain of dependent launches whose own SM time is small: top
+            // priority, so that its CTAs (a 16-CTA cluster per panel) are
+            // placed ahead of the patch inversions' waiting CTAs
+            CK(cudaStreamCreateWithPriority(&h->s_coarse, cudaStreamNonBlocking, prio(0)));
             CK(cudaStreamCreateWithPriority(&h->s_tr, cudaStreamNonBlocking, prio(3)));
             const int prio_l0 = prio(1), prio_small = prio(2);
             {
