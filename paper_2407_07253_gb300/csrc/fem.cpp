@@ -1399,9 +1399,13 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     static std::map<std::pair<int, int>, RefTensors> tensors;
     auto ref = [&](int dd, int kk) -> const RefElement& { return reference_element(dd, kk); };
     std::vector<size_t> order;
+    if (spec.coarsest_first && spec.finest_before_coarsest && ls.size() > 1) order.push_back(0);
     if (spec.coarsest_first) order.push_back(ls.size() - 1);
-    for (size_t l = 0; l < ls.size(); ++l)
-        if (!(spec.coarsest_first && l + 1 == ls.size())) order.push_back(l);
+    for (size_t l = 0; l < ls.size(); ++l) {
+        if (spec.coarsest_first && l + 1 == ls.size()) continue;
+        if (spec.coarsest_first && spec.finest_before_coarsest && l == 0) continue;
+        order.push_back(l);
+    }
     for (size_t l : order) {
         Level& L = H.levels[l];
         L.d = d;

@@ -1320,129 +1320,6 @@ __global__ void __launch_bounds__(256) gj_step_eliminate(int n, int k, double* _
     }
 }
 
-// In-place Gauss-Jordan inverse with partial pivoting of one dense n x n
-// matrix (row-major) by one thread-block cluster of GJC_CTAS CTAs.  CTA r
-// keeps rows [r R, (r + 1) R) (R = ceil(n / GJC_CTAS)) in shared memory for
-// the whole elimination; a pivot step is
-//   every CTA: candidate max |a_ik| over its rows i >= k   -> cluster barrier
-//   every CTA: pivot row p = best candidate (ties: smaller row), the pivot
-//     row (scaled by 1 / a_pk) and, in the CTA that owns p, the old row k,
-//     read from their owners' shared memory                -> cluster barrier
-//   every CTA: rows k and p swapped, column k eliminated from its rows
-// so rows never travel through global memory.  The barriers are the
-// hardware cluster barrier.  Row swaps are recorded in ipiv; the columns are
-// unscrambled afterwards by gj_unpivot_rows.  status <- 1 + step of the
-// first zero pivot.
-__global__ void __launch_bounds__(GJC_THREADS) gj_cluster_inverse(int n, double* __restrict__ A, int* __restrict__ ipiv,
-                                                                   int* __restrict__ status) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ double gsm[];
-    const int R = (n + GJC_CTAS - 1) / GJC_CTAS;
-    const int rank = (int)cluster.block_rank();
-    const int r0 = rank * R, nr = max(0, min(R, n - r0));
-    double* rows = gsm;                         // [R][n]
-    double* prow = rows + (size_t)R * n;        // [n] pivot row / a_pk
-    double* rowk = prow + n;                    // [n] old row k (CTA that owns p)
-    double* fcol = rowk + n;                    // [R] multiplier of my rows
-    double* fcolk = fcol + R;                   // [R] their new column-k entries
-    __shared__ double cand_v[GJC_THREADS / 32], s_inv, s_cv, s_sv;   // s_cv, s_ci, s_sv: this CTA's candidate
-    __shared__ int cand_i[GJC_THREADS / 32], s_p, s_ci;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    for (long long t = tid; t < (long long)nr * n; t += nt) rows[t] = A[(long long)r0 * n + t];
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        // candidate of this CTA: largest |a_ik| over its rows i >= k
-        double bv = -1.0;
-        int bi = n;
-        for (int ii = tid; ii < nr; ii += nt) {
-            const int i = r0 + ii;
-            if (i < k) continue;
-            const double av = fabs(rows[(size_t)ii * n + k]);
-            if (av > bv) { bv = av; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-        }
-        if (lane == 0) { cand_v[warp] = bv; cand_i[warp] = bi; }
-        __syncthreads();
-        if (tid == 0) {
-            double b = -1.0;
-            int i0 = n;
-            for (int w = 0; w < nt / 32; ++w)
-                if (cand_v[w] > b || (cand_v[w] == b && cand_i[w] < i0)) { b = cand_v[w]; i0 = cand_i[w]; }
-            s_cv = b;
-            s_ci = i0;
-            s_sv = i0 < n ? rows[(size_t)(i0 - r0) * n + k] : 0.0;   // signed pivot candidate
-        }
-        cluster.sync();                                            // (1) candidates visible
-        if (warp == 0) {
-            // lane r reads CTA r's candidate; a shuffle tree picks the pivot
-            double b = -1.0, sgn = 0.0;
-            int p = n;
-            if (lane < GJC_CTAS) {
-                b = *cluster.map_shared_rank(&s_cv, lane);
-                p = *cluster.map_shared_rank(&s_ci, lane);
-                sgn = *cluster.map_shared_rank(&s_sv, lane);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_down_sync(0xffffffffu, b, o), os = __shfl_down_sync(0xffffffffu, sgn, o);
-                const int op = __shfl_down_sync(0xffffffffu, p, o);
-                if (ob > b || (ob == b && op < p)) { b = ob; p = op; sgn = os; }
-            }
-            if (lane == 0) {
-                if (!(b > 0.0) || p >= n) {
-                    p = k;
-                    sgn = 0.0;
-                    if (rank == 0 && *status == 0) *status = k + 1;
-                }
-                s_p = p;
-                s_inv = sgn != 0.0 ? 1.0 / sgn : 0.0;
-                if (rank == 0) ipiv[k] = p;
-            }
-        }
-        __syncthreads();
-        const int p = s_p;
-        const double inv = s_inv;
-        {
-            const double* src = cluster.map_shared_rank(rows, p / R) + (size_t)(p % R) * n;
-            for (int j = tid; j < n; j += nt) prow[j] = src[j] * inv;
-            if (p != k && p >= r0 && p < r0 + nr) {
-                const double* srk = cluster.map_shared_rank(rows, k / R) + (size_t)(k % R) * n;
-                for (int j = tid; j < n; j += nt) rowk[j] = srk[j];
-            }
-        }
-        cluster.sync();                                            // (2) remote reads done
-        // per own row: the multiplier f (old a_ik; for row p the old a_kk)
-        // and the new column-k entry -f / a_pk, one multiply per row
-        for (int ii = tid; ii < nr; ii += nt) {
-            const int i = r0 + ii;
-            const double f = i == p ? rowk[k] : rows[(size_t)ii * n + k];
-            fcol[ii] = f;
-            fcolk[ii] = -f * inv;
-        }
-        __syncthreads();
-        for (int ii = 0; ii < nr; ++ii) {
-            const int i = r0 + ii;
-            double* row = rows + (size_t)ii * n;
-            const double* src = i == p ? rowk : row;
-            const double f = fcol[ii], fk = fcolk[ii];
-            if (i == k) {
-                for (int j = tid; j < n; j += nt) row[j] = j == k ? inv : prow[j];
-            } else {
-                for (int j = tid; j < n; j += nt) {
-                    const double v = fma(-f, prow[j], src[j]);   // one FMA per entry
-                    row[j] = j == k ? fk : v;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    for (long long t = tid; t < (long long)nr * n; t += nt) A[(long long)r0 * n + t] = rows[t];
-}
-
 // ---- blocked Gauss-Jordan inverse (partial pivoting) on every SM -------
 // Panel [k0, k0 + B) of the row-major n x n matrix A: the columns of all rows
 // in shared memory (pan[j n + i]), B Gauss-Jordan steps on them (pivot row
@@ -1547,7 +1424,6 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, i
     double* buf1 = buf0 + (size_t)R * B;         // [R][B] odd steps read this one
     double* prow = buf1 + (size_t)R * B;         // [B] scaled pivot row
     double* rowk = prow + B;                     // [B] old row k (CTA that owns p)
-    double* fcol = rowk + B;                     // [R] multiplier of my rows
     __shared__ double cand_v[GJC_THREADS / 32], s_inv, s_cv[2], s_sv[2];
     __shared__ int cand_i[GJC_THREADS / 32], s_p, s_ci[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
@@ -1575,14 +1451,19 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, i
         }
         if (lane == 0) { cand_v[warp] = bv; cand_i[warp] = bi; }
         __syncthreads();
-        if (tid == 0) {
-            double b = -1.0;
-            int i0 = n;
-            for (int w = 0; w < nt / 32; ++w)
-                if (cand_v[w] > b || (cand_v[w] == b && cand_i[w] < i0)) { b = cand_v[w]; i0 = cand_i[w]; }
-            s_cv[par] = b;
-            s_ci[par] = i0;
-            s_sv[par] = i0 < n ? cur[(size_t)(i0 - r0) * B + jj] : 0.0;
+        if (warp == 0) {
+            double b = lane < nt / 32 ? cand_v[lane] : -1.0;
+            int i0 = lane < nt / 32 ? cand_i[lane] : n;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, b, o);
+                const int oi = __shfl_down_sync(0xffffffffu, i0, o);
+                if (ob > b || (ob == b && oi < i0)) { b = ob; i0 = oi; }
+            }
+            if (lane == 0) {
+                s_cv[par] = b;
+                s_ci[par] = i0;
+                s_sv[par] = i0 < n ? cur[(size_t)(i0 - r0) * B + jj] : 0.0;
+            }
         }
         cluster.sync();                                            // candidates and rows of this step visible
         if (warp == 0) {
@@ -1621,15 +1502,15 @@ __global__ void __launch_bounds__(GJC_THREADS) gj_cluster_panel(int n, int k0, i
             }
         }
         __syncthreads();
-        for (int ii = tid; ii < nr; ii += nt) fcol[ii] = (r0 + ii == p) ? rowk[jj] : cur[(size_t)ii * B + jj];
-        __syncthreads();
+        // (cur is only read in this step, so each thread takes its row's
+        // multiplier from it directly)
         for (int t = tid; t < nr * B; t += nt) {
             const int ii = t / B, j = t - ii * B;
             const int i = r0 + ii;
             if (i == k) {
                 nxt[t] = prow[j];
             } else {
-                const double f = fcol[ii];
+                const double f = i == p ? rowk[jj] : cur[(size_t)ii * B + jj];
                 const double src = i == p ? rowk[j] : cur[t];
                 nxt[t] = j == jj ? -f * inv : fma(-f, prow[j], src);
             }

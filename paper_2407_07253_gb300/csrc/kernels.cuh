@@ -270,15 +270,7 @@ __global__ void gj_block_swap(int n, int k0, int B, double* __restrict__ A, cons
                               double* __restrict__ Yb);
 __global__ void gj_block_update(int n, int k0, int B, double* __restrict__ A, const double* __restrict__ Pk,
                                 const double* __restrict__ Yb);
-// Whole in-place Gauss-Jordan inverse (partial pivoting, row swaps in ipiv)
-// of one n x n matrix by one cluster of GJC_CTAS CTAs holding its rows in
-// shared memory: (ceil(n / GJC_CTAS) + 2) n + 2 ceil(n / GJC_CTAS) doubles
-// of dynamic shared memory per CTA; follow with gj_unpivot_rows.
 constexpr int GJC_CTAS = 16, GJC_THREADS = 512;
-__host__ __device__ inline long long gj_cluster_smem_doubles(int n) {
-    const long long R = (n + GJC_CTAS - 1) / GJC_CTAS;
-    return (R + 2) * n + 2 * R;
-}
 // The panel on one cluster of GJC_CTAS CTAs (rows split among them):
 // gj_cluster_panel_smem_doubles(n, B) doubles of dynamic shared memory.
 __host__ __device__ inline long long gj_cluster_panel_smem_doubles(int n, int B) {
@@ -288,7 +280,7 @@ __host__ __device__ inline long long gj_cluster_panel_smem_doubles(int n, int B)
 __global__ void gj_cluster_panel(int n, int k0, int B, double* __restrict__ A, int* __restrict__ ipiv,
                                  double* __restrict__ Pk, int* __restrict__ status);
 
-__global__ void gj_cluster_inverse(int n, double* __restrict__ A, int* __restrict__ ipiv, int* __restrict__ status);
+
 // y[i] = sum_j A[i][j] x[j] for i < nout (row-major, leading dimension lda)
 __global__ void dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A, const double* __restrict__ x,
                            double* __restrict__ y);

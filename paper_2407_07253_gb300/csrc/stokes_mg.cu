@@ -199,6 +199,7 @@ struct DevLevel {
     // device assembly of K (all levels but the coarsest)
     bool dev_asm = false;
     bool dev_transfer = false;          // P, R built on the device (exact nnz read back at finish)
+    bool maps_up = false;               // the DoF maps the device transfers read are uploaded
     sasm::AsmMesh am;
     double* cellgeo = nullptr;          // am.cg, filled on the device
     int* asm_len = nullptr;
@@ -1984,39 +1985,6 @@ void upload_coarse(stokes_mg* h, cudaStream_t su) {
     h->ce64 = halloc<double>(h, n);
 }
 
-// coarse factorisation steps on stream s (the upload must be ordered before)
-// One cluster of skern::GJC_CTAS CTAs can hold the bordered coarse matrix in
-// shared memory (and the device runs clusters of that size)?
-bool coarse_cluster_ok(stokes_mg* h, int nb, size_t* smem_out) {
-    const size_t smem = (size_t)skern::gj_cluster_smem_doubles(nb) * sizeof(double);
-    int dev_max = 0;
-    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (smem + 1024 > (size_t)dev_max) return false;
-    if (cudaFuncSetAttribute(skern::gj_cluster_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(skern::gj_cluster_inverse, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = skern::GJC_CTAS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(skern::GJC_CTAS);
-    cfg.blockDim = dim3(skern::GJC_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, skern::gj_cluster_inverse, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    *smem_out = smem;
-    return nclusters > 0;
-}
-
 // can one cluster of GJC_CTAS CTAs run gj_cluster_panel with this much
 // dynamic shared memory on this device?
 bool cluster_panel_ok(stokes_mg* h, size_t smem) {
@@ -2353,6 +2321,10 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         spec.device_assembly = !o.host_only;
         spec.coarsest_first = !o.host_only;
         spec.device_transfers = !o.host_only && !fbf_mode;
+        // the finest level first: its patch inversion and lambda_max estimate
+        // are the longest device chain; the coarse factorisation (top stream
+        // priority) runs beside them
+        spec.finest_before_coarsest = !o.host_only && !fbf_mode;
         if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
         else if (o.hierarchy == STOKES_HIER_GRADUAL) {
             if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
@@ -2417,6 +2389,15 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                 CK(cudaStreamWaitEvent(target, ev, 0));
                 CK(cudaEventDestroy(ev));
             };
+            // device transfers: after the uploads on s_up, on their own stream
+            auto launch_transfer = [&](std::function<void()> job) {
+                after_uploads(h.get(), h->s_tr);
+                stokes_mg* hp0 = h.get();
+                launcher->submit([hp0, job] {
+                    CK(cudaSetDevice(hp0->device));
+                    job();
+                });
+            };
             on_level = [&](int li, int stage) {
                 const double tu = host_ms();
                 stokes_mg* hp = h.get();
@@ -2448,17 +2429,12 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                         mark(hp, "L" + std::to_string(li) + " assembled", target);
                     });
                     if (spec.device_transfers) {
-                        // P_{l-1} once level l's maps are up; P_l too when the
-                        // next level is the (already uploaded) coarsest
-                        auto launch_on = [&](std::function<void()> job) {
-                            after_uploads(hp, hp->s_tr);
-                            launcher->submit([hp, job] {
-                                CK(cudaSetDevice(hp->device));
-                                job();
-                            });
-                        };
-                        if (li >= 1) build_transfer_dev(hp, li - 1, want32, launch_on);
-                        if (li + 2 == nlv) build_transfer_dev(hp, li, want32, launch_on);
+                        // P_{l-1} once level l's maps are up (levels are
+                        // built finest to coarsest); P_l too when the next
+                        // level is the coarsest and its maps are up already
+                        hp->L[li].maps_up = true;
+                        if (li >= 1) build_transfer_dev(hp, li - 1, want32, launch_transfer);
+                        if (li + 2 == nlv && hp->L[li + 1].maps_up) build_transfer_dev(hp, li, want32, launch_transfer);
                     }
                     return;
                 }
@@ -2477,6 +2453,10 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                         hp->L[li].am.vcell = hupload(hp, HC.V.cell_nodes, hp->s_up);
                         hp->L[li].am.qcell = hupload(hp, HC.Q.cell_nodes, hp->s_up);
                         hp->L[li].am.vfree = hupload(hp, HC.vfree, hp->s_up);
+                        hp->L[li].maps_up = true;
+                        // the last transfer now if its fine level came first
+                        if (nlv >= 2 && hp->L[nlv - 2].maps_up && !hp->L[nlv - 2].dev_transfer)
+                            build_transfer_dev(hp, nlv - 2, want32, launch_transfer);
                     }
                 }
                 mark(hp, "L" + std::to_string(li) + " uploaded", hp->s_up);
