@@ -309,8 +309,11 @@ constexpr long long WAIT_LIMIT = 1ll << 22;
 
 __host__ __device__ constexpr int np_of(int m) { return m < 16 ? 16 : m; }
 __host__ __device__ inline int tiles_of(int n) { return (n + 127) >> 7; }
-__host__ __device__ inline int stage_bytes(int maxn, int np) {
-    return (tiles_of(maxn) * A_TILE + np * KS * 4 + 1023) & ~1023;
+// a stage: the inverse's 128-row tiles (split: the hi tiles, then the lo
+// tiles), then the B operand (split: its hi part, then its lo part)
+__host__ __device__ inline int stage_bytes(int maxn, int np, bool split = false) {
+    const int f = split ? 2 : 1;
+    return (f * tiles_of(maxn) * A_TILE + f * np * KS * 4 + 1023) & ~1023;
 }
 __host__ __device__ inline int acc_cols(int maxn, int np) { return tiles_of(maxn) * np; }
 __host__ __device__ inline int acc_bufs(int maxn, int np) { return 2 * acc_cols(maxn, np) <= 512 ? 2 : 1; }
@@ -413,24 +416,33 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&v)[16]) {
         : "r"(taddr));
 }
 
-template <int M, int ST>
+// SPLIT (3xTF32): the inverse comes as two arrays, hi = TF32(a) and
+// lo = a - hi (tmaps over hi, tmaps_lo over lo), R as hi = TF32(r) and
+// lo = TF32(r - hi), and every k-step issues three MMAs into the same
+// accumulator: lo x hi, hi x lo, hi x hi (lo x lo, of relative size 2^-22,
+// is dropped).  This keeps FP32 accuracy on the tensor cores.
+template <int M, int ST, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int maxn, const int* __restrict__ plist,
                                                               const int* __restrict__ poff,
                                                               const int* __restrict__ pdofs,
                                                               const CUtensorMap* __restrict__ tmaps,
+                                                              const CUtensorMap* __restrict__ tmaps_lo,
                                                               const float* __restrict__ X,
                                                               const float* __restrict__ wt, float* __restrict__ Yb,
                                                               int* status) {
     constexpr int NP = np_of(M);
+    constexpr int F = SPLIT ? 2 : 1;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t base = smem_u32(smem_tc);
     const uint32_t full0 = base, empty0 = base + 8 * ST, accf0 = base + 16 * ST, acce0 = accf0 + 16;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_tc + 16 * ST + 32);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem_tc + 16 * ST + 36);
-    const int sbytes = stage_bytes(maxn, NP);
+    const int sbytes = stage_bytes(maxn, NP, SPLIT);
     const uint32_t stage0 = (base + HDR + 1023) & ~1023u;     // swizzle atoms need 1024-byte alignment
-    const uint32_t b_off = (uint32_t)(tiles_of(maxn) * A_TILE);      // B operand inside a stage
+    const uint32_t lo_off = (uint32_t)(tiles_of(maxn) * A_TILE);     // lo tiles inside a stage (SPLIT)
+    const uint32_t b_off = (uint32_t)(F * tiles_of(maxn) * A_TILE);  // B operand inside a stage
+    constexpr uint32_t BLO = (uint32_t)(NP * KS * 4);                 // its lo part after the hi part (SPLIT)
     const int nbuf = acc_bufs(maxn, NP), ccols = acc_cols(maxn, NP), ncols = tmem_cols(maxn, NP);
 
     if (warp == 0) {
@@ -464,12 +476,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
                 const int p = plist ? __ldg(plist + i) : i;
                 const int n = poff[p + 1] - poff[p], tiles = tiles_of(n), nst = (n + KS - 1) / KS;
                 const CUtensorMap* tm = tmaps + p;
+                const CUtensorMap* tml = SPLIT ? tmaps_lo + p : nullptr;
                 for (int j = 0; j < nst; ++j, ++it) {
                     const int s = it % ST;
                     if (it >= ST && !mbar_wait(empty0 + 8 * s, ((it / ST) - 1) & 1, abort_flag)) goto done;
                     const uint32_t st = stage0 + (uint32_t)(s * sbytes);
-                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(tiles * A_TILE));
-                    for (int mt = 0; mt < tiles; ++mt) tma_load_2d(st + mt * A_TILE, tm, full0 + 8 * s, j * KS, mt * 128);
+                    mbar_expect_tx(full0 + 8 * s, (uint32_t)(F * tiles * A_TILE));
+                    for (int mt = 0; mt < tiles; ++mt) {
+                        tma_load_2d(st + mt * A_TILE, tm, full0 + 8 * s, j * KS, mt * 128);
+                        if (SPLIT) tma_load_2d(st + lo_off + mt * A_TILE, tml, full0 + 8 * s, j * KS, mt * 128);
+                    }
                 }
             }
         }
@@ -493,9 +509,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
 #pragma unroll
                     for (int u = 0; u < KS / 8; ++u) {
                         const uint64_t bd = desc_plain(st + b_off + (uint32_t)(u * 2 * 128), 128, B_GROUP);
-                        for (int mt = 0; mt < tiles; ++mt)
-                            mma(acc + (uint32_t)(mt * NP), desc_sw64(st + (uint32_t)(mt * A_TILE + u * 32)), bd, ID,
-                                (j | u) != 0);
+                        for (int mt = 0; mt < tiles; ++mt) {
+                            const uint64_t ad = desc_sw64(st + (uint32_t)(mt * A_TILE + u * 32));
+                            if (SPLIT) {
+                                const uint64_t adl = desc_sw64(st + lo_off + (uint32_t)(mt * A_TILE + u * 32));
+                                const uint64_t bdl = desc_plain(st + b_off + BLO + (uint32_t)(u * 2 * 128), 128, B_GROUP);
+                                mma(acc + (uint32_t)(mt * NP), adl, bd, ID, (j | u) != 0);
+                                mma(acc + (uint32_t)(mt * NP), ad, bdl, ID, 1);
+                                mma(acc + (uint32_t)(mt * NP), ad, bd, ID, 1);
+                            } else {
+                                mma(acc + (uint32_t)(mt * NP), ad, bd, ID, (j | u) != 0);
+                            }
+                        }
                     }
                     commit(empty0 + 8 * s);
                 }
@@ -550,8 +575,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_patch_gemm_tc(int npatch, int ma
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
                                 const int cc = c + u;
-                                *reinterpret_cast<uint32_t*>(bp + (cc >> 3) * B_GROUP + k4 * 128 + (cc & 7) * 16 + kk * 4) =
-                                    to_tf32(f[u]);
+                                const int o = (cc >> 3) * B_GROUP + k4 * 128 + (cc & 7) * 16 + kk * 4;
+                                const uint32_t hi = to_tf32(f[u]);
+                                *reinterpret_cast<uint32_t*>(bp + o) = hi;
+                                if (SPLIT) *reinterpret_cast<uint32_t*>(bp + BLO + o) = to_tf32(f[u] - __uint_as_float(hi));
                             }
                         }
                     }
@@ -713,23 +740,29 @@ static void launch_gemm_st(int maxn, int nw, int nlist, const int* plist, const 
 }
 
 // Patches of <= TC_MIN_N DoFs fill under half of a 128-row MMA tile; the
-// warp-level kernel is faster there.
-constexpr int TC_MIN_N = 64;
+// warp-level kernel is faster there.  The 3xTF32 tensor-core kernel holds
+// twice the operands per stage; up to TC_SPLIT_MAX_N DoFs (6 row tiles) two
+// stages still fit.
+constexpr int TC_MIN_N = 64, TC_SPLIT_MAX_N = 768;
 
-int gemm_kind(int mode, int n) { return (mode == GEMM_TF32 && n > TC_MIN_N) ? GEMM_KIND_TC : GEMM_KIND_WARP; }
+int gemm_kind(int mode, int n) {
+    if (n <= TC_MIN_N) return GEMM_KIND_WARP;
+    if (mode == GEMM_TF32) return GEMM_KIND_TC;
+    return n <= TC_SPLIT_MAX_N ? GEMM_KIND_TC : GEMM_KIND_WARP;
+}
 
 // tensor-core TF32 path: a persistent grid of one CTA per SM (the dynamic
 // shared memory is at least half an SM's, so no two CTAs share an SM and its
 // 512 tensor-memory columns), with as many pipeline stages as fit, at most 12
 struct TcPlan { int stages = 0; size_t smem = 0; int grid = 0; };
 
-static TcPlan tc_plan(int maxn, int m, int npatch) {
+static TcPlan tc_plan(int maxn, int m, int npatch, bool split = false) {
     TcPlan pl;
     const int np = tc::np_of(m);
     if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, np) > 512) return pl;
     const long long optin = device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin);
     const long long per_sm = device_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor);
-    const long long fixed = tc::HDR + 1024, sb = tc::stage_bytes(maxn, np);
+    const long long fixed = tc::HDR + 1024, sb = tc::stage_bytes(maxn, np, split);
     const long long st = std::min<long long>(12, (optin - fixed) / sb);
     if (st < 2) return pl;
     pl.stages = (int)st;
@@ -739,21 +772,23 @@ static TcPlan tc_plan(int maxn, int m, int npatch) {
     return pl;
 }
 
-template <int M, int ST>
+template <int M, int ST, bool SPLIT>
 static void launch_tc(const TcPlan& pl, int nlist, const int* plist, int maxn, const int* poff, const int* pdofs,
-                      const void* tmaps, const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
-    cudaFuncSetAttribute(tc::k_patch_gemm_tc<M, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-    tc::k_patch_gemm_tc<M, ST><<<pl.grid, tc::THREADS, pl.smem, s>>>(
-        nlist, maxn, plist, poff, pdofs, reinterpret_cast<const CUtensorMap*>(tmaps), X, wt, Yb, status);
+                      const void* tmaps, const void* tmaps_lo, const float* X, const float* wt, float* Yb, int* status,
+                      cudaStream_t s) {
+    cudaFuncSetAttribute(tc::k_patch_gemm_tc<M, ST, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    tc::k_patch_gemm_tc<M, ST, SPLIT><<<pl.grid, tc::THREADS, pl.smem, s>>>(
+        nlist, maxn, plist, poff, pdofs, reinterpret_cast<const CUtensorMap*>(tmaps),
+        reinterpret_cast<const CUtensorMap*>(tmaps_lo), X, wt, Yb, status);
 }
 
-template <int M>
+template <int M, bool SPLIT>
 static void launch_tc_st(int nlist, const int* plist, int maxn, const int* poff, const int* pdofs, const void* tmaps,
-                         const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
-    const TcPlan pl = tc_plan(maxn, M, nlist);
+                         const void* tmaps_lo, const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
+    const TcPlan pl = tc_plan(maxn, M, nlist, SPLIT);
     switch (pl.stages) {
 #define SBAT_TC_CASE(S) \
-    case S: launch_tc<M, S>(pl, nlist, plist, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s); break;
+    case S: launch_tc<M, S, SPLIT>(pl, nlist, plist, maxn, poff, pdofs, tmaps, tmaps_lo, X, wt, Yb, status, s); break;
         SBAT_TC_CASE(2) SBAT_TC_CASE(3) SBAT_TC_CASE(4) SBAT_TC_CASE(5) SBAT_TC_CASE(6) SBAT_TC_CASE(7)
         SBAT_TC_CASE(8) SBAT_TC_CASE(9) SBAT_TC_CASE(10) SBAT_TC_CASE(11) SBAT_TC_CASE(12)
 #undef SBAT_TC_CASE
@@ -763,11 +798,14 @@ static void launch_tc_st(int nlist, const int* plist, int maxn, const int* poff,
 
 template <int M>
 static void patch_gemm_m(int mode, int kind, int nw, int nlist, const int* plist, int maxn, const int* poff,
-                         const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const float* X,
-                         const float* wt, float* Yb, int* status, cudaStream_t s) {
+                         const int* pdofs, const long long* ioff, const float* inv, const void* tmaps,
+                         const void* tmaps_hi, const void* tmaps_lo, const float* X, const float* wt, float* Yb,
+                         int* status, cudaStream_t s) {
     if (kind == GEMM_KIND_AUTO) kind = gemm_kind(mode, maxn);
-    if (kind == GEMM_KIND_TC)
-        launch_tc_st<M>(nlist, plist, maxn, poff, pdofs, tmaps, X, wt, Yb, status, s);
+    if (kind == GEMM_KIND_TC && mode == GEMM_3XTF32)
+        launch_tc_st<M, true>(nlist, plist, maxn, poff, pdofs, tmaps_hi, tmaps_lo, X, wt, Yb, status, s);
+    else if (kind == GEMM_KIND_TC)
+        launch_tc_st<M, false>(nlist, plist, maxn, poff, pdofs, tmaps, nullptr, X, wt, Yb, status, s);
     else if (mode == GEMM_3XTF32)
         launch_gemm_st<M, GEMM_3XTF32>(maxn, nw, nlist, plist, poff, pdofs, ioff, inv, X, wt, Yb, s);
     else
@@ -784,7 +822,23 @@ const char* patch_gemm_check(int mode, int maxn, int m) {
                    : "patch too large for the shared memory of the warp-MMA patch GEMM at this width";
     if (tc::tiles_of(maxn) > 8 || tc::tmem_cols(maxn, tc::np_of(m)) > 512)
         return "patch too large for the tensor memory at this width";
-    return tc_plan(maxn, m, 1).stages ? nullptr : "patch too large for the shared memory of the TF32 patch GEMM";
+    return tc_plan(maxn, m, 1, mode == GEMM_3XTF32).stages ? nullptr
+                                                           : "patch too large for the shared memory of the tensor-core patch GEMM";
+}
+
+namespace {
+__global__ void k_split_tf32(long long n, const float* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float x = a[i];
+        const float h = __uint_as_float(to_tf32(x));
+        hi[i] = h;
+        lo[i] = x - h;
+    }
+}
+}  // namespace
+
+void split_tf32(long long n, const float* a, float* hi, float* lo, cudaStream_t s) {
+    if (n > 0) k_split_tf32<<<grid_of(n, 256), 256, 0, s>>>(n, a, hi, lo);
 }
 
 int wait_probe(long long polls, int* result_dev, cudaStream_t s) {
@@ -830,15 +884,20 @@ void build_tmaps(int npatch, const int* poff_d, const long long* ioff_d, const f
 }
 
 void patch_gemm(int mode, int kind, int nw, int nlist, const int* plist, int maxn, int m, const int* poff,
-                const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const float* X,
-                const float* wt, float* Yb, int* status, cudaStream_t s) {
+                const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const void* tmaps_hi,
+                const void* tmaps_lo, const float* X, const float* wt, float* Yb, int* status, cudaStream_t s) {
     if (nlist <= 0) return;
     switch (m) {
 #define SBAT_M(MM) \
-    case MM: patch_gemm_m<MM>(mode, kind, nw, nlist, plist, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s); break;
+    case MM: \
+        patch_gemm_m<MM>(mode, kind, nw, nlist, plist, maxn, poff, pdofs, ioff, inv, tmaps, tmaps_hi, tmaps_lo, X, wt, \
+                         Yb, status, s); \
+        break;
         SBAT_M(8) SBAT_M(16) SBAT_M(32)
 #undef SBAT_M
-        default: patch_gemm_m<64>(mode, kind, nw, nlist, plist, maxn, poff, pdofs, ioff, inv, tmaps, X, wt, Yb, status, s);
+        default:
+            patch_gemm_m<64>(mode, kind, nw, nlist, plist, maxn, poff, pdofs, ioff, inv, tmaps, tmaps_hi, tmaps_lo, X, wt,
+                             Yb, status, s);
     }
 }
 

@@ -46,21 +46,28 @@ void build_tmaps(int npatch, const int* poff, const long long* ioff, const float
 // X[pdofs[poff[p] + a] * m + c], for the nlist patches p = plist[i] (plist
 // NULL: p = i < nlist); inverses column-major with leading dimension
 // (n + 3) & ~3 at ioff[p] (the FP32 ASM layout), symmetric.
-//   kind GEMM_KIND_TC     tcgen05 tensor cores (GEMM_TF32 only), inverses
-//                         read through tmaps (build_tmaps);
+//   kind GEMM_KIND_TC     tcgen05 tensor cores; GEMM_TF32 reads the inverses
+//                         through tmaps (build_tmaps over inv), GEMM_3XTF32
+//                         through tmaps_hi / tmaps_lo (build_tmaps over the
+//                         split_tf32 parts, same layout) with three MMAs per
+//                         k-step;
 //   kind GEMM_KIND_WARP   warp-level MMA, nw warps per CTA (0: from maxn);
 //   kind GEMM_KIND_AUTO   gemm_kind(mode, maxn).
 // gemm_kind gives each patch's kind by its size: the tensor cores for
-// GEMM_TF32 patches of more than 64 DoFs, the warp-level MMA otherwise.  A
-// patch's arithmetic depends only on its kind, not on nw, maxn or the list it
-// is in.  maxn bounds the listed patches' sizes; *status (host-mapped) is set
-// to 1 if a tensor-core CTA gave up waiting on one of its mbarriers.
+// patches of more than 64 DoFs (3xTF32: up to 768), the warp-level MMA
+// otherwise.  A patch's arithmetic depends only on its kind, not on nw, maxn
+// or the list it is in.  maxn bounds the listed patches' sizes; *status
+// (host-mapped) is set to 1 if a tensor-core CTA gave up waiting on one of
+// its mbarriers.
 enum GemmKind { GEMM_KIND_AUTO = 0, GEMM_KIND_WARP = 1, GEMM_KIND_TC = 2 };
 int gemm_kind(int mode, int n);
 int gemm_default_warps(int maxn);
 void patch_gemm(int mode, int kind, int nw, int nlist, const int* plist, int maxn, int m, const int* poff,
-                const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const float* X,
-                const float* wt, float* Yb, int* status, cudaStream_t s);
+                const int* pdofs, const long long* ioff, const float* inv, const void* tmaps, const void* tmaps_hi,
+                const void* tmaps_lo, const float* X, const float* wt, float* Yb, int* status, cudaStream_t s);
+// hi[i] = TF32(a[i]) (round to nearest), lo[i] = a[i] - hi[i] (exact): the
+// operands of the 3xTF32 tensor-core GEMM
+void split_tf32(long long n, const float* a, float* hi, float* lo, cudaStream_t s);
 
 // out[j * m + c] = alpha * sum_{q in slots(j)} Yb[sidx[q] * m + c] + beta * out[j * m + c]
 // (slots in increasing order: a fixed summation order)

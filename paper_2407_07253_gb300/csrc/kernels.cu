@@ -1127,15 +1127,16 @@ __global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f64(
 // ---- the same sweep with each patch's factored block brought into shared
 // memory by one bulk copy (cp.async.bulk, completion on an mbarrier) -------
 // One CTA of SA_BULK_THREADS threads per patch: thread 0 issues the copy of
-// the patch's (Li, W, Si) block (contiguous, a multiple of 16 bytes) while
-// the others gather the residual and the partition-of-unity weights of the
-// patch's DoFs; every product then reads shared memory:
+// the patch's packed Li (the start of its block, a multiple of 16 bytes)
+// while the others gather the residual and the partition-of-unity weights
+// of the patch's DoFs; W and Si are read from global memory in coalesced
+// rows (W twice, the second time from L2), which keeps a CTA's shared
+// memory small and many CTAs per SM:
 //   t = r_p - W^T r_u   (one warp per pressure row, lanes over the velocity rows)
 //   y_c = Li r_c        (one thread per velocity row and component)
 //   s = Si t            (one thread per pressure row)
 //   z_u = y + W s, z_p = -s, weighted.
-// A CTA holds only its own block, so several CTAs per SM stream their blocks
-// at once.  The wait on the copy is bounded: after SA_WAIT_LIMIT polls the
+// The wait on the copy is bounded: after SA_WAIT_LIMIT polls the
 // CTA sets *status = 1, waits (bounded) for the copy once more and returns.
 __device__ __forceinline__ uint32_t sa_smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -1178,12 +1179,12 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
     T* sq = tq + xs_len;                                       // [xs_len] s
     const uint32_t b = sa_smem_u32(bar);
     const int s0 = poff[p], n = poff[p + 1] - s0, nv = pnv[p], dnv = d * nv, np = n - dnv;
+    const int lenL = (nv * (nv + 1) / 2 + VEC - 1) / VEC * VEC;
     if (tid == 0) {
         sa_mbar_init(b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const long long o = foff[p];
-        const uint32_t bytes = (uint32_t)((foff[p + 1] - o) * (long long)sizeof(T));
-        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem), fac + o, bytes, b);
+        const uint32_t bytes = (uint32_t)(lenL * (int)sizeof(T));
+        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem), fac + foff[p], bytes, b);
         else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
     }
     for (int a = tid; a < n; a += NT) {
@@ -1206,10 +1207,9 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
     }
     const int ldw = (dnv + VEC - 1) / VEC * VEC;
     const int lds = (np + VEC - 1) / VEC * VEC;
-    const int lenL = (nv * (nv + 1) / 2 + VEC - 1) / VEC * VEC;
-    const T* Lp = reinterpret_cast<const T*>(smem);            // Li, packed upper triangle
-    const T* Wm = Lp + lenL;
-    const T* Si = Wm + ldw * np;
+    const T* Lp = reinterpret_cast<const T*>(smem);            // Li, packed upper triangle (shared memory)
+    const T* Wm = fac + foff[p] + lenL;                         // W and Si: global memory, coalesced reads
+    const T* Si = Wm + ldw * np;                                //   (W's second read comes from L2)
     for (int q = warp; q < np; q += NT / 32) {
         const T* wc = Wm + q * ldw;
         T acc = 0;

@@ -285,6 +285,8 @@ struct stokes_mg {
     std::vector<BatchLevel> bl;
     int *bstat_h = nullptr, *bstat_d = nullptr;   // host-mapped timeout flag of the tensor-core patch GEMM
     std::vector<void*> tmaps;                      // per relaxed level: tensor maps over the FP32 inverses
+    std::vector<void*> tmaps_hi, tmaps_lo;         // per relaxed level: over their TF32 hi / lo parts (3xTF32)
+    std::vector<float*> inv_hi, inv_lo;            // per relaxed level: the hi / lo parts
     std::unique_ptr<FbfData> fbf;                  // FBF(phMG) mode (stokes_fbf_setup)
     // batched FGMRES workspace (interleaved FP64, width bk_m)
     struct BatchKrylov {
@@ -766,6 +768,8 @@ void b_spmm(stokes_mg* h, int kind, const DevCSR& A, int mode, int m, const floa
     launch(h, kind, s, [&] { sbat::spmm(mode, A.nr, m, A.rp, A.ci, A.v32, X, Y, B, s); });
 }
 
+const void* split_map(const std::vector<void*>& v, size_t li) { return li < v.size() ? v[li] : nullptr; }
+
 void b_asm(stokes_mg* h, int li, int gm, int m, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
     DevLevel& l = h->L[li];
     BatchLevel& B = h->bl[li];
@@ -773,7 +777,8 @@ void b_asm(stokes_mg* h, int li, int gm, int m, const float* r, float* out, doub
     for (const auto& pt : B.plan[gm])
         launch(h, PK_PATCH, s, [&] {
             sbat::patch_gemm(gm, pt.kind, pt.nw, pt.count, h->bpsort[li] + pt.off, pt.hi, m, l.poff, l.pdofs, l.ioff32,
-                             l.inv32, h->tmaps[li], r, l.wt32, B.Yb, h->bstat_d, s);
+                             l.inv32, h->tmaps[li], split_map(h->tmaps_hi, li), split_map(h->tmaps_lo, li), r, l.wt32,
+                             B.Yb, h->bstat_d, s);
         });
     launch(h, PK_PULL, s, [&] { sbat::pull_scatter(l.n, m, l.soff, l.sidx, B.Yb, (float)alpha, (float)beta, out, s); });
 }
@@ -880,6 +885,35 @@ void ensure_explicit32(stokes_mg* h, cudaStream_t s) {
     CK(cudaStreamSynchronize(s));
 }
 
+// The 3xTF32 tensor-core GEMM reads each FP32 inverse as two arrays, its TF32
+// part hi and the rest lo = a - hi, through their own tensor maps: built on
+// the first 3xTF32 use and kept.
+void ensure_split(stokes_mg* h, cudaStream_t s) {
+    const int nl = (int)h->L.size();
+    if ((int)h->tmaps_hi.size() == nl) return;
+    h->inv_hi.assign(nl, nullptr);
+    h->inv_lo.assign(nl, nullptr);
+    std::vector<void*> mh(nl, nullptr), ml(nl, nullptr);
+    for (int li = 0; li + 1 < nl; ++li) {
+        DevLevel& l = h->L[li];
+        h->inv_hi[li] = halloc<float>(h, l.ninv32);
+        h->inv_lo[li] = halloc<float>(h, l.ninv32);
+        mh[li] = halloc<unsigned char>(h, sbat::tmap_bytes(l.npatch));
+        ml[li] = halloc<unsigned char>(h, sbat::tmap_bytes(l.npatch));
+    }
+    CK(cudaStreamSynchronize(h->s_up));      // new chunks are pool-ordered on s_up
+    for (int li = 0; li + 1 < nl; ++li) {
+        DevLevel& l = h->L[li];
+        sbat::split_tf32(l.ninv32, l.inv32, h->inv_hi[li], h->inv_lo[li], s);
+        CK(cudaGetLastError());
+        sbat::build_tmaps(l.npatch, l.poff, l.ioff32, h->inv_hi[li], mh[li]);
+        sbat::build_tmaps(l.npatch, l.poff, l.ioff32, h->inv_lo[li], ml[li]);
+    }
+    CK(cudaStreamSynchronize(s));
+    h->tmaps_hi = mh;
+    h->tmaps_lo = ml;
+}
+
 // interleaved work vectors of width m on every level (kept for later calls)
 void ensure_batch(stokes_mg* h, int m) {
     if (!h->bstat_h) {
@@ -936,7 +970,8 @@ double time_gemm(stokes_mg* h, int li, int gm, int m, const stokes_mg::GemmPart&
     BatchLevel& B = h->bl[li];
     auto run = [&] {
         sbat::patch_gemm(gm, pt.kind, pt.nw, pt.count, plist ? plist + pt.off : nullptr, pt.hi, m, l.poff, l.pdofs,
-                         l.ioff32, l.inv32, h->tmaps[li], X, l.wt32, B.Yb, h->bstat_d, s);
+                         l.ioff32, l.inv32, h->tmaps[li], split_map(h->tmaps_hi, li), split_map(h->tmaps_lo, li), X,
+                         l.wt32, B.Yb, h->bstat_d, s);
         CK(cudaGetLastError());
     };
     cudaEvent_t e0, e1;
@@ -1041,6 +1076,7 @@ void tune_level(stokes_mg* h, int li, int gm, int m, cudaStream_t s) {
 // or (opts.batch_tune = 0) one launch per kind in size order
 void ensure_plan(stokes_mg* h, int gm, int m, cudaStream_t s) {
     using GemmPart = stokes_mg::GemmPart;
+    if (gm == sbat::GEMM_3XTF32) ensure_split(h, s);
     for (size_t li = 0; li + 1 < h->L.size(); ++li) {
         BatchLevel& B = h->bl[li];
         if (!B.plan[gm].empty()) continue;
@@ -1520,8 +1556,9 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
                 for (int p = 0; p < l.npatch; ++p) {
                     const long long len = skern::saddle_factor_len(HL.d, HL.patch_off[p + 1] - HL.patch_off[p],
                                                                    HL.patch_nv[p], vec, 1);
+                    const long long nvp = HL.patch_nv[p];
                     fp[p + 1] = fp[p] + len;
-                    mb = std::max(mb, len);
+                    mb = std::max(mb, (nvp * (nvp + 1) / 2 + vec - 1) / vec * vec);   // the copied packed L^-1
                 }
                 const long long buf = (mb * eb + 127) & ~127LL;
                 const size_t smem = skern::saddle_apply_bulk_smem((int)std::min<long long>(buf, 1 << 30), eb, l.sa_xs);
@@ -2321,10 +2358,10 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         spec.device_assembly = !o.host_only;
         spec.coarsest_first = !o.host_only;
         spec.device_transfers = !o.host_only && !fbf_mode;
-        // the finest level first: its patch inversion and lambda_max estimate
-        // are the longest device chain; the coarse factorisation (top stream
-        // priority) runs beside them
-        spec.finest_before_coarsest = !o.host_only && !fbf_mode;
+        // (finest_before_coarsest stays off: with the level-0 inversion
+        // already filling the GPU, the coarse factorisation's chain of
+        // launches took 5.7 ms and ended after level 0's lambda_max; started
+        // first it ends well before)
         if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
         else if (o.hierarchy == STOKES_HIER_GRADUAL) {
             if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
