@@ -1127,11 +1127,11 @@ __global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f64(
 // ---- the same sweep with each patch's factored block brought into shared
 // memory by one bulk copy (cp.async.bulk, completion on an mbarrier) -------
 // One CTA of SA_BULK_THREADS threads per patch: thread 0 issues the copy of
-// the patch's packed Li (the start of its block, a multiple of 16 bytes)
+// the patch's (packed Li, W, Si) block (contiguous, a multiple of 16 bytes)
 // while the others gather the residual and the partition-of-unity weights
-// of the patch's DoFs; W and Si are read from global memory in coalesced
-// rows (W twice, the second time from L2), which keeps a CTA's shared
-// memory small and many CTAs per SM:
+// of the patch's DoFs; every product then reads shared memory (reading W and
+// Si from global memory instead, to fit more CTAs per SM, measured slower:
+// 42 us against 38 us per level-0 sweep of the bench problem):
 //   t = r_p - W^T r_u   (one warp per pressure row, lanes over the velocity rows)
 //   y_c = Li r_c        (one thread per velocity row and component)
 //   s = Si t            (one thread per pressure row)
@@ -1183,8 +1183,9 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
     if (tid == 0) {
         sa_mbar_init(b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const uint32_t bytes = (uint32_t)(lenL * (int)sizeof(T));
-        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem), fac + foff[p], bytes, b);
+        const long long o = foff[p];
+        const uint32_t bytes = (uint32_t)((foff[p + 1] - o) * (long long)sizeof(T));
+        if (bytes > 0) sa_bulk_load(sa_smem_u32(smem), fac + o, bytes, b);
         else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
     }
     for (int a = tid; a < n; a += NT) {
@@ -1207,9 +1208,9 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
     }
     const int ldw = (dnv + VEC - 1) / VEC * VEC;
     const int lds = (np + VEC - 1) / VEC * VEC;
-    const T* Lp = reinterpret_cast<const T*>(smem);            // Li, packed upper triangle (shared memory)
-    const T* Wm = fac + foff[p] + lenL;                         // W and Si: global memory, coalesced reads
-    const T* Si = Wm + ldw * np;                                //   (W's second read comes from L2)
+    const T* Lp = reinterpret_cast<const T*>(smem);            // Li, packed upper triangle
+    const T* Wm = Lp + lenL;
+    const T* Si = Wm + ldw * np;
     for (int q = warp; q < np; q += NT / 32) {
         const T* wc = Wm + q * ldw;
         T acc = 0;

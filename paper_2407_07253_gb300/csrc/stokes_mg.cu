@@ -1556,9 +1556,8 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
                 for (int p = 0; p < l.npatch; ++p) {
                     const long long len = skern::saddle_factor_len(HL.d, HL.patch_off[p + 1] - HL.patch_off[p],
                                                                    HL.patch_nv[p], vec, 1);
-                    const long long nvp = HL.patch_nv[p];
                     fp[p + 1] = fp[p] + len;
-                    mb = std::max(mb, (nvp * (nvp + 1) / 2 + vec - 1) / vec * vec);   // the copied packed L^-1
+                    mb = std::max(mb, len);
                 }
                 const long long buf = (mb * eb + 127) & ~127LL;
                 const size_t smem = skern::saddle_apply_bulk_smem((int)std::min<long long>(buf, 1 << 30), eb, l.sa_xs);
