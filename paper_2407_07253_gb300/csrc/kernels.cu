@@ -1194,11 +1194,15 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
         wq[a] = wt[j];
     }
     // the barrier's initialisation (thread 0) is ordered before anyone polls
-    // it by this __syncthreads; then every thread waits on it, bounded
+    // it by this __syncthreads; then warp 0 alone polls it (bounded: polling
+    // by every warp took issue slots from the other CTAs on the SM), the
+    // others wait at the block barrier and test the completed phase once
     __syncthreads();
-    bool ok = false;
-    for (long long it = 0; it < SA_WAIT_LIMIT; ++it)
-        if (sa_mbar_try(b, 0)) { ok = true; break; }
+    bool ok = warp != 0;
+    if (warp == 0)
+        for (long long it = 0; it < SA_WAIT_LIMIT; ++it)
+            if (sa_mbar_try(b, 0)) { ok = true; break; }
+    if (__syncthreads_and(ok) && warp != 0) ok = sa_mbar_try(b, 0);
     if (!__syncthreads_and(ok)) {
         if (tid == 0) {
             for (long long it = 0; it < SA_WAIT_LIMIT && !sa_mbar_try(b, 0); ++it) {}
@@ -1221,6 +1225,8 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
     }
     // y_c = Li r_c: Li[a][bb] is packed entry (min, max); walking bb, the
     // column-a part (bb < a) advances by nv - 1 - bb, the row-a part by 1
+    // (two threads per row, each over half of bb and every component, were
+    // measured no faster)
     for (int t = tid; t < dnv; t += NT) {
         const int c = t / nv, a = t - c * nv;
         const T* xc = xs + c * nv;
