@@ -952,6 +952,8 @@ __global__ void __launch_bounds__(128) patch_apply_f32(int npatch, const int* __
     extern __shared__ __align__(16) unsigned char smem_pa[];
     float4* red = reinterpret_cast<float4*>(smem_pa);
     float* xs = reinterpret_cast<float*>(smem_pa + sizeof(float4) * (blockDim.x + 4));
+    pdl_wait();
+    pdl_release();
     patch_apply_body<float, float4, 4>(blockIdx.x, poff, pdofs, ioff, inv, r, wt, Y, xs, red);
 }
 
@@ -962,6 +964,8 @@ __global__ void __launch_bounds__(128) patch_apply_f64(int npatch, const int* __
     extern __shared__ __align__(16) unsigned char smem_pa[];
     double2* red = reinterpret_cast<double2*>(smem_pa);
     double* xs = reinterpret_cast<double*>(smem_pa + sizeof(double2) * (blockDim.x + 4));
+    pdl_wait();
+    pdl_release();
     patch_apply_body<double, double2, 2>(blockIdx.x, poff, pdofs, ioff, inv, r, wt, Y, xs, red);
 }
 
@@ -1113,6 +1117,8 @@ __global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f32(
     const long long* __restrict__ foff, const float* __restrict__ fac, const float* __restrict__ r,
     const float* __restrict__ wt, float* __restrict__ Y, int xs_len, int ws_len) {
     extern __shared__ __align__(16) unsigned char smem_sa[];
+    pdl_wait();
+    pdl_release();
     saddle_apply_body<float, float4, 4>(blockIdx.x, d, poff, pdofs, pnv, foff, fac, r, wt, Y, xs_len, ws_len, smem_sa);
 }
 
@@ -1121,6 +1127,8 @@ __global__ void __launch_bounds__(SADDLE_APPLY_THREADS) saddle_apply_f64(
     const long long* __restrict__ foff, const double* __restrict__ fac, const double* __restrict__ r,
     const double* __restrict__ wt, double* __restrict__ Y, int xs_len, int ws_len) {
     extern __shared__ __align__(16) unsigned char smem_sa[];
+    pdl_wait();
+    pdl_release();
     saddle_apply_body<double, double2, 2>(blockIdx.x, d, poff, pdofs, pnv, foff, fac, r, wt, Y, xs_len, ws_len, smem_sa);
 }
 
@@ -1180,6 +1188,8 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
     const uint32_t b = sa_smem_u32(bar);
     const int s0 = poff[p], n = poff[p + 1] - s0, nv = pnv[p], dnv = d * nv, np = n - dnv;
     const int lenL = (nv * (nv + 1) / 2 + VEC - 1) / VEC * VEC;
+    // the factors are constant: their copy starts before the wait for the
+    // kernel that wrote r (programmatic dependent launch)
     if (tid == 0) {
         sa_mbar_init(b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1188,6 +1198,8 @@ __device__ __forceinline__ void saddle_apply_bulk_body(
         if (bytes > 0) sa_bulk_load(sa_smem_u32(smem), fac + o, bytes, b);
         else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
     }
+    pdl_wait();
+    pdl_release();
     for (int a = tid; a < n; a += NT) {
         const int j = pdofs[s0 + a];
         xs[a] = r[j];
@@ -1580,17 +1592,6 @@ __global__ void gj_unpivot_rows(int n, double* __restrict__ A, const int* __rest
                 A[(long long)i * n + p] = t;
             }
         }
-}
-
-__global__ void __launch_bounds__(256) dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A,
-                                                  const double* __restrict__ x, double* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= nout) return;
-    double s = 0;
-    for (int j = lane; j < ncol; j += 32) s += A[(long long)row * lda + j] * x[j];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] = s;
 }
 
 // ------------------------------------------------------ small Hessenberg ---

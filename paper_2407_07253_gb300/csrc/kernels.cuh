@@ -24,6 +24,18 @@ namespace skern {
 
 constexpr int GJ_SMEM_MAX_N = 160;   // FP64 patch held in shared memory up to this size
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialisation attribute may start while the kernel before it on the
+// stream is still running.  pdl_wait() blocks until that kernel has finished
+// and its writes are visible; every kernel of the V-cycle calls it before it
+// reads an input another kernel writes, or writes anything, and may read
+// constant data (operators, patch factors, maps) before it.  pdl_release()
+// lets the next kernel's blocks be scheduled once every block of this one has
+// called it or exited.  Both are no-ops in a kernel launched without the
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ----------------------------------------------------------------- SpMV ---
 enum SpmvMode { SPMV_SET = 0, SPMV_ADD = 1, SPMV_RESID = 2 };
 
@@ -36,15 +48,32 @@ __global__ void __launch_bounds__(256) spmv_csr(int nrows, const int* __restrict
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = gtid / LANES;
     const int lane = threadIdx.x % LANES;
-    if (row >= nrows) return;   // whole LANES-group exits together (LANES divides 32)
-    const int s = __ldg(rp + row), e = __ldg(rp + row + 1);
+    // the operator is constant: its first round of column and value loads
+    // is issued before waiting for the kernel that wrote x (and b)
+    const bool live = row < nrows;
+    const int s = live ? __ldg(rp + row) : 0, e = live ? __ldg(rp + row + 1) : 0;
+    int c[4];
+    T a[4];
+    int base = s + lane;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int p = base + u * LANES;
+        const bool ok = p < e;
+        c[u] = ok ? __ldg(ci + p) : 0;
+        a[u] = ok ? __ldg(av + p) : T(0);
+    }
+    pdl_wait();
+    pdl_release();
+    if (!live) return;   // whole LANES-group exits together (LANES divides 32)
     T acc = 0;
     // four entries per lane per round: their column and value loads, then
     // their x loads, are issued together (a row of ~40 entries takes one
     // round at 16 lanes instead of a chain of three dependent load pairs)
-    for (int base = s + lane; base < e; base += 4 * LANES) {
-        int c[4];
-        T a[4];
+    for (;;) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += a[u] * x[c[u]];
+        base += 4 * LANES;
+        if (base >= e) break;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int p = base + u * LANES;
@@ -52,8 +81,6 @@ __global__ void __launch_bounds__(256) spmv_csr(int nrows, const int* __restrict
             c[u] = ok ? __ldg(ci + p) : 0;
             a[u] = ok ? __ldg(av + p) : T(0);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc += a[u] * __ldg(x + c[u]);
     }
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LANES);
@@ -67,6 +94,8 @@ __global__ void __launch_bounds__(256) spmv_csr(int nrows, const int* __restrict
 // ------------------------------------------------------- vector kernels ---
 template <typename TO, typename TI>
 __global__ void convert_vec(int n, const TI* __restrict__ x, TO* __restrict__ y) {
+    pdl_wait();
+    pdl_release();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = (TO)x[i];
 }
 
@@ -78,6 +107,8 @@ __global__ void fill_vec(long long n, T v, T* __restrict__ y) {
 // y = a x + b y
 template <typename T>
 __global__ void axpby(int n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+    pdl_wait();
+    pdl_release();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = a * x[i] + b * y[i];
 }
 
@@ -238,15 +269,26 @@ __global__ void patch_apply_f64(int npatch, const int* __restrict__ poff, const 
                                 const double* __restrict__ r, const double* __restrict__ wt, double* __restrict__ Y);
 
 // out[j] = alpha * sum_{s in slots(j)} Y[s] + beta * out[j]  (slots in a
-// fixed order, so the sum is bitwise reproducible)
+// fixed order, so the sum is bitwise reproducible).  Fused Chebyshev
+// bookkeeping: xmode PULL_X_SET also sets x[j] = out[j], PULL_X_ADD adds
+// x[j] += out[j]; with rdst != NULL, rdst[j] = bsrc[j].
+enum PullX { PULL_X_NONE = 0, PULL_X_SET = 1, PULL_X_ADD = 2 };
 template <typename T>
 __global__ void __launch_bounds__(256) pull_scatter(int n, const int* __restrict__ soff, const int* __restrict__ sidx,
-                                                    const T* __restrict__ Y, T alpha, T beta, T* __restrict__ out) {
+                                                    const T* __restrict__ Y, T alpha, T beta, T* __restrict__ out,
+                                                    T* __restrict__ x, int xmode, const T* __restrict__ bsrc,
+                                                    T* __restrict__ rdst) {
+    pdl_wait();
+    pdl_release();
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         T s = 0;
         const int e = soff[j + 1];
         for (int q = soff[j]; q < e; ++q) s += Y[sidx[q]];
-        out[j] = beta == T(0) ? alpha * s : alpha * s + beta * out[j];
+        const T o = beta == T(0) ? alpha * s : alpha * s + beta * out[j];
+        out[j] = o;
+        if (xmode == PULL_X_SET) x[j] = o;
+        else if (xmode == PULL_X_ADD) x[j] += o;
+        if (rdst) rdst[j] = bsrc[j];
     }
 }
 
@@ -281,9 +323,22 @@ __global__ void gj_cluster_panel(int n, int k0, int B, double* __restrict__ A, i
                                  double* __restrict__ Pk, int* __restrict__ status);
 
 
-// y[i] = sum_j A[i][j] x[j] for i < nout (row-major, leading dimension lda)
-__global__ void dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A, const double* __restrict__ x,
-                           double* __restrict__ y);
+// y[i] = sum_j A[i][j] x[j] for i < nout (row-major, leading dimension lda),
+// one warp per row, accumulated in FP64 whatever the vectors' type (an FP32
+// x is widened exactly, y rounded once)
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256) dense_gemv(int nout, int ncol, int lda, const double* __restrict__ A,
+                                                  const TI* __restrict__ x, TO* __restrict__ y) {
+    pdl_wait();
+    pdl_release();
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= nout) return;
+    double s = 0;
+    for (int j = lane; j < ncol; j += 32) s += A[(long long)row * lda + j] * (double)x[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = (TO)s;
+}
 
 // --------------------------------------------------- small Hessenberg ---
 // FGMRES: apply the previous Givens rotations to column j of H (stored

@@ -254,7 +254,6 @@ struct stokes_mg {
     // coarse bordered inverse
     int nc = 0;
     double* Cinv = nullptr;
-    double *cb64 = nullptr, *ce64 = nullptr;
     // FGMRES
     int restart = 30;
     double *V = nullptr, *Z = nullptr, *Hh = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
@@ -312,6 +311,11 @@ struct stokes_mg {
     bool capturing = false;
     bool host_only = false;
     int* sa_status = nullptr;           // device: 1 once a bulk-copy apply CTA gave up waiting
+    // programmatic dependent launch inside a V-cycle's chain of kernels:
+    // pdl_chain while the chain is issued, pdl_armed once a kernel of the
+    // chain precedes the next launch on the stream (a copy disarms it)
+    bool pdl_chain = false;
+    bool pdl_armed = false;
     // bump allocator for the handle's long-lived device buffers: a few large
     // cudaMalloc chunks instead of one call per array
     char* slab_cur = nullptr;
@@ -362,6 +366,31 @@ void launch(stokes_mg* h, int kind, cudaStream_t s, F&& f) {
         p->pending.push_back({a, b});
         p->launches++;
     }
+}
+
+// One kernel launch.  While a V-cycle chain is issued (pdl_chain) every
+// kernel after the chain's first is launched with programmatic stream
+// serialisation: its blocks may be scheduled while the kernel before it
+// finishes, and wait (skern::pdl_wait) before they touch what that kernel
+// writes.  Only kernels that call pdl_wait go through here.
+template <typename... KArgs, typename... Args>
+void kl(stokes_mg* h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    if (h->pdl_armed) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = block;
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    } else {
+        kern<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+    }
+    h->pdl_armed = h->pdl_chain;
 }
 
 // Device timeline of setup under STOKES_TRACE=1: a host function enqueued
@@ -493,24 +522,25 @@ template <>
 const float* vals<float>(const DevCSR& A) { return A.v32; }
 
 template <typename T, int MODE>
-void spmv_lanes(const DevCSR& A, const T* x, T* y, const T* b, cudaStream_t s) {
+void spmv_lanes(stokes_mg* h, const DevCSR& A, const T* x, T* y, const T* b, cudaStream_t s) {
     const long long threads = (long long)A.nr * A.lanes;
     const int grid = (int)((threads + 255) / 256);
     if (A.nr == 0) return;
+    const T* av = vals<T>(A);
     switch (A.lanes) {
-        case 4: skern::spmv_csr<T, 4, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
-        case 8: skern::spmv_csr<T, 8, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
-        case 16: skern::spmv_csr<T, 16, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
-        default: skern::spmv_csr<T, 32, MODE><<<grid, 256, 0, s>>>(A.nr, A.rp, A.ci, vals<T>(A), x, y, b); break;
+        case 4: kl(h, skern::spmv_csr<T, 4, MODE>, grid, 256, 0, s, A.nr, A.rp, A.ci, av, x, y, b); break;
+        case 8: kl(h, skern::spmv_csr<T, 8, MODE>, grid, 256, 0, s, A.nr, A.rp, A.ci, av, x, y, b); break;
+        case 16: kl(h, skern::spmv_csr<T, 16, MODE>, grid, 256, 0, s, A.nr, A.rp, A.ci, av, x, y, b); break;
+        default: kl(h, skern::spmv_csr<T, 32, MODE>, grid, 256, 0, s, A.nr, A.rp, A.ci, av, x, y, b); break;
     }
 }
 
 template <typename T>
 void spmv(stokes_mg* h, int kind, const DevCSR& A, int mode, const T* x, T* y, const T* b, cudaStream_t s) {
     launch(h, kind, s, [&] {
-        if (mode == skern::SPMV_SET) spmv_lanes<T, skern::SPMV_SET>(A, x, y, b, s);
-        else if (mode == skern::SPMV_ADD) spmv_lanes<T, skern::SPMV_ADD>(A, x, y, b, s);
-        else spmv_lanes<T, skern::SPMV_RESID>(A, x, y, b, s);
+        if (mode == skern::SPMV_SET) spmv_lanes<T, skern::SPMV_SET>(h, A, x, y, b, s);
+        else if (mode == skern::SPMV_ADD) spmv_lanes<T, skern::SPMV_ADD>(h, A, x, y, b, s);
+        else spmv_lanes<T, skern::SPMV_RESID>(h, A, x, y, b, s);
     });
 }
 
@@ -544,70 +574,83 @@ void check_sa_status(stokes_mg* h, cudaStream_t s) {
         throw StokesError(STOKES_ECUDA, "a patch-apply CTA gave up waiting for its bulk copy (bounded wait)");
 }
 
+// per-precision patch data and apply kernels of a level
+template <typename T> struct PatchOf;
+template <> struct PatchOf<float> {
+    static const float* fac(const DevLevel& l) { return l.fac32; }
+    static const long long* foff(const DevLevel& l) { return l.foff32; }
+    static const float* inv(const DevLevel& l) { return l.inv32; }
+    static const long long* ioff(const DevLevel& l) { return l.ioff32; }
+    static const float* wt(const DevLevel& l) { return l.wt32; }
+    static float* Y(const DevLevel& l) { return l.Y32; }
+    static long long ws(const DevLevel& l) { return l.sa_ws32; }
+    static constexpr auto bulk = skern::saddle_apply_bulk_f32;
+    static constexpr auto fact = skern::saddle_apply_f32;
+    static constexpr auto expl = skern::patch_apply_f32;
+    static constexpr int vec = 4;
+    static constexpr size_t red = sizeof(float4);
+    static constexpr const char* none = "no FP32 patch inverses on this handle (FP64 handle)";
+};
+template <> struct PatchOf<double> {
+    static const double* fac(const DevLevel& l) { return l.fac64; }
+    static const long long* foff(const DevLevel& l) { return l.foff64; }
+    static const double* inv(const DevLevel& l) { return l.inv64; }
+    static const long long* ioff(const DevLevel& l) { return l.ioff64; }
+    static const double* wt(const DevLevel& l) { return l.wt64; }
+    static double* Y(const DevLevel& l) { return l.Y64; }
+    static long long ws(const DevLevel& l) { return l.sa_ws64; }
+    static constexpr auto bulk = skern::saddle_apply_bulk_f64;
+    static constexpr auto fact = skern::saddle_apply_f64;
+    static constexpr auto expl = skern::patch_apply_f64;
+    static constexpr int vec = 2;
+    static constexpr size_t red = sizeof(double2);
+    static constexpr const char* none = "no FP64 patch inverses on this handle (MIXED handle)";
+};
+
 // one ASM sweep: Y = W_i K_i^{-1} I_i r for every patch, then
-// out = alpha * sum_i I_i^T Y_i + beta * out
+// out = alpha * sum_i I_i^T Y_i + beta * out in the same pass as the
+// Chebyshev bookkeeping: x = out or x += out (xmode), rdst = bsrc (if rdst)
 template <typename T>
-void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, double beta, cudaStream_t s);
-
-template <>
-void asm_apply<float>(stokes_mg* h, DevLevel& l, const float* r, float* out, double alpha, double beta, cudaStream_t s) {
-    if (l.fac32 && l.sa_buf > 0) {
-        const size_t smem = skern::saddle_apply_bulk_smem(l.sa_buf, 4, l.sa_xs);
+void asm_apply(stokes_mg* h, DevLevel& l, const T* r, T* out, double alpha, double beta, cudaStream_t s,
+               T* x = nullptr, int xmode = skern::PULL_X_NONE, const T* bsrc = nullptr, T* rdst = nullptr) {
+    using PO = PatchOf<T>;
+    const T* fac = PO::fac(l);
+    const long long* foff = PO::foff(l);
+    const T* wt = PO::wt(l);
+    T* Y = PO::Y(l);
+    const int *poff = l.poff, *pdofs = l.pdofs, *pnv = l.pnv;
+    if (fac && l.sa_buf > 0) {
+        const size_t smem = skern::saddle_apply_bulk_smem(l.sa_buf, sizeof(T), l.sa_xs);
         launch(h, PK_PATCH, s, [&] {
-            skern::saddle_apply_bulk_f32<<<l.npatch, skern::SA_BULK_THREADS, smem, s>>>(
-                h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_buf, l.sa_xs, h->sa_status);
+            kl(h, PO::bulk, l.npatch, skern::SA_BULK_THREADS, smem, s, h->dim, poff, pdofs, pnv, foff, fac, r, wt, Y,
+               (int)l.sa_buf, (int)l.sa_xs, h->sa_status);
         });
-    } else if (l.fac32) {
-        long long ws = l.sa_ws32;
-        if (skern::saddle_apply_smem(4, 4, ws, l.sa_xs) > skern::SADDLE_APPLY_SMEM_MAX) ws = 0;
-        const size_t smem = skern::saddle_apply_smem(4, 4, ws, l.sa_xs);
+    } else if (fac) {
+        long long ws = PO::ws(l);
+        if (skern::saddle_apply_smem(sizeof(T), PO::vec, ws, l.sa_xs) > skern::SADDLE_APPLY_SMEM_MAX) ws = 0;
+        const size_t smem = skern::saddle_apply_smem(sizeof(T), PO::vec, ws, l.sa_xs);
         launch(h, PK_PATCH, s, [&] {
-            skern::saddle_apply_f32<<<l.npatch, skern::SADDLE_APPLY_THREADS, smem, s>>>(
-                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff32, l.fac32, r, l.wt32, l.Y32, l.sa_xs, (int)ws);
-        });
-    } else {
-        if (!l.inv32) throw StokesError(STOKES_EINVAL, "no FP32 patch inverses on this handle (FP64 handle)");
-        const size_t smem = sizeof(float4) * (128 + 4) + sizeof(float) * l.maxn;
-        launch(h, PK_PATCH, s, [&] {
-            skern::patch_apply_f32<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff32, l.inv32, r, l.wt32, l.Y32);
-        });
-    }
-    launch(h, PK_PULL, s, [&] {
-        skern::pull_scatter<float><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y32, (float)alpha, (float)beta, out);
-    });
-}
-
-template <>
-void asm_apply<double>(stokes_mg* h, DevLevel& l, const double* r, double* out, double alpha, double beta, cudaStream_t s) {
-    if (l.fac64 && l.sa_buf > 0) {
-        const size_t smem = skern::saddle_apply_bulk_smem(l.sa_buf, 8, l.sa_xs);
-        launch(h, PK_PATCH, s, [&] {
-            skern::saddle_apply_bulk_f64<<<l.npatch, skern::SA_BULK_THREADS, smem, s>>>(
-                h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_buf, l.sa_xs, h->sa_status);
-        });
-    } else if (l.fac64) {
-        long long ws = l.sa_ws64;
-        if (skern::saddle_apply_smem(8, 2, ws, l.sa_xs) > skern::SADDLE_APPLY_SMEM_MAX) ws = 0;
-        const size_t smem = skern::saddle_apply_smem(8, 2, ws, l.sa_xs);
-        launch(h, PK_PATCH, s, [&] {
-            skern::saddle_apply_f64<<<l.npatch, skern::SADDLE_APPLY_THREADS, smem, s>>>(
-                l.npatch, h->dim, l.poff, l.pdofs, l.pnv, l.foff64, l.fac64, r, l.wt64, l.Y64, l.sa_xs, (int)ws);
+            kl(h, PO::fact, l.npatch, skern::SADDLE_APPLY_THREADS, smem, s, l.npatch, h->dim, poff, pdofs, pnv, foff,
+               fac, r, wt, Y, (int)l.sa_xs, (int)ws);
         });
     } else {
-        if (!l.inv64) throw StokesError(STOKES_EINVAL, "no FP64 patch inverses on this handle (MIXED handle)");
-        const size_t smem = sizeof(double2) * (128 + 4) + sizeof(double) * l.maxn;
+        const T* inv = PO::inv(l);
+        if (!inv) throw StokesError(STOKES_EINVAL, PO::none);
+        const size_t smem = PO::red * (128 + 4) + sizeof(T) * l.maxn;
         launch(h, PK_PATCH, s, [&] {
-            skern::patch_apply_f64<<<l.npatch, 128, smem, s>>>(l.npatch, l.poff, l.pdofs, l.ioff64, l.inv64, r, l.wt64, l.Y64);
+            kl(h, PO::expl, l.npatch, 128, smem, s, l.npatch, poff, pdofs, PO::ioff(l), inv, r, wt, Y);
         });
     }
+    const int *soff = l.soff, *sidx = l.sidx;
     launch(h, PK_PULL, s, [&] {
-        skern::pull_scatter<double><<<grid_for(l.n), 256, 0, s>>>(l.n, l.soff, l.sidx, l.Y64, alpha, beta, out);
+        kl(h, skern::pull_scatter<T>, grid_for(l.n), 256, 0, s, l.n, soff, sidx, (const T*)Y, (T)alpha, (T)beta, out, x,
+           xmode, bsrc, rdst);
     });
 }
 
 template <typename T>
 void axpby_l(stokes_mg* h, int n, double a, const T* x, double b, T* y, cudaStream_t s) {
-    launch(h, -1, s, [&] { skern::axpby<T><<<grid_for(n), 256, 0, s>>>(n, (T)a, x, (T)b, y); });
+    launch(h, -1, s, [&] { kl(h, skern::axpby<T>, grid_for(n), 256, 0, s, n, (T)a, x, (T)b, y); });
 }
 
 // Chebyshev(nu) preconditioned by one ASM sweep per step, on [lo, hi]*lmax
@@ -630,37 +673,28 @@ void smooth(stokes_mg* h, int li, const T* b, T* x, bool x_zero, int nu, cudaStr
         asm_apply<T>(h, l, rin, x, 1.0 / theta, x_zero ? 0.0 : 1.0, s);
         return;
     }
+    // d = M r (step 1), then x = d and r = b from x = 0, else x += d; every
+    // later step: r -= K d, d = (2 rho_i / delta) M r + rho_i rho_{i-1} d,
+    // x += d (the updates of x and the copy of b ride in the scatter pass)
     T* d = LV<T>::d(l);
-    asm_apply<T>(h, l, rin, d, 1.0 / theta, 0.0, s);
-    if (x_zero) {
-        CK(cudaMemcpyAsync(x, d, sizeof(T) * l.n, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(r, b, sizeof(T) * l.n, cudaMemcpyDeviceToDevice, s));
-    } else {
-        axpby_l<T>(h, l.n, 1.0, d, 1.0, x, s);
-    }
+    if (x_zero) asm_apply<T>(h, l, rin, d, 1.0 / theta, 0.0, s, x, skern::PULL_X_SET, b, r);
+    else asm_apply<T>(h, l, rin, d, 1.0 / theta, 0.0, s, x, skern::PULL_X_ADD);
     for (int i = 1; i < nu; ++i) {
         spmv<T>(h, PK_SPMV, l.K, skern::SPMV_RESID, d, r, r, s);    // r -= K d
         const double rho_new = 1.0 / (2.0 * sigma - rho);
-        asm_apply<T>(h, l, r, d, 2.0 * rho_new / delta, rho_new * rho, s);
-        axpby_l<T>(h, l.n, 1.0, d, 1.0, x, s);
+        asm_apply<T>(h, l, r, d, 2.0 * rho_new / delta, rho_new * rho, s, x, skern::PULL_X_ADD);
         rho = rho_new;
     }
 }
 
+// e = C^-1 (b, 0) on the bordered coarse inverse, in FP64 (an FP32 b is
+// widened exactly and e rounded once, in the same kernel)
 template <typename T>
-void coarse_apply(stokes_mg* h, const T* b, T* e, cudaStream_t s);
-
-template <>
-void coarse_apply<double>(stokes_mg* h, const double* b, double* e, cudaStream_t s) {
+void coarse_apply(stokes_mg* h, const T* b, T* e, cudaStream_t s) {
     const int n = h->nc;
-    launch(h, -1, s, [&] { skern::dense_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, n, n + 1, h->Cinv, b, e); });
-}
-template <>
-void coarse_apply<float>(stokes_mg* h, const float* b, float* e, cudaStream_t s) {
-    const int n = h->nc;
-    launch(h, -1, s, [&] { skern::convert_vec<double, float><<<grid_for(n), 256, 0, s>>>(n, b, h->cb64); });
-    launch(h, -1, s, [&] { skern::dense_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, n, n + 1, h->Cinv, h->cb64, h->ce64); });
-    launch(h, -1, s, [&] { skern::convert_vec<float, double><<<grid_for(n), 256, 0, s>>>(n, h->ce64, e); });
+    launch(h, -1, s, [&] {
+        kl(h, skern::dense_gemv<T, T>, (n * 32 + 255) / 256, 256, 0, s, n, n, n + 1, (const double*)h->Cinv, b, e);
+    });
 }
 
 // hMG V-cycle (Eq. 3.1, Fig. 2) on level li from e = 0
@@ -705,17 +739,27 @@ void pcycle(stokes_mg* h, int li, const T* b, T* e, cudaStream_t s) {
     smooth<T>(h, li, b, e, false, nu, s);
 }
 
-// vout = B_MG vin in the requested precision (vin/vout are the FP64 graph I/O buffers)
-void vcycle_body(stokes_mg* h, int prec, cudaStream_t s) {
+// vout = B_MG vin in the requested precision (vin/vout are the FP64 graph
+// I/O buffers).  With pdl, every kernel after the first is launched with
+// programmatic dependent launch (the body issues kernels only).
+void vcycle_body(stokes_mg* h, int prec, cudaStream_t s, bool pdl = true) {
     DevLevel& l0 = h->L[0];
     const int n = l0.n;
-    if (prec == STOKES_FP64) {
-        pcycle<double>(h, 0, h->vin, h->vout, s);
-    } else {
-        launch(h, -1, s, [&] { skern::convert_vec<float, double><<<grid_for(n), 256, 0, s>>>(n, h->vin, l0.b32); });
-        pcycle<float>(h, 0, l0.b32, l0.e32, s);
-        launch(h, -1, s, [&] { skern::convert_vec<double, float><<<grid_for(n), 256, 0, s>>>(n, l0.e32, h->vout); });
+    h->pdl_chain = pdl;
+    h->pdl_armed = false;
+    try {
+        if (prec == STOKES_FP64) {
+            pcycle<double>(h, 0, h->vin, h->vout, s);
+        } else {
+            launch(h, -1, s, [&] { kl(h, skern::convert_vec<float, double>, grid_for(n), 256, 0, s, n, (const double*)h->vin, l0.b32); });
+            pcycle<float>(h, 0, l0.b32, l0.e32, s);
+            launch(h, -1, s, [&] { kl(h, skern::convert_vec<double, float>, grid_for(n), 256, 0, s, n, (const float*)l0.e32, h->vout); });
+        }
+    } catch (...) {
+        h->pdl_chain = h->pdl_armed = false;
+        throw;
     }
+    h->pdl_chain = h->pdl_armed = false;
 }
 
 void vcycle_run(stokes_mg* h, int prec, cudaStream_t s) {
@@ -726,7 +770,7 @@ void vcycle_run(stokes_mg* h, int prec, cudaStream_t s) {
         CK(cudaGraphLaunch(h->graph[prec], s));
         h->launches += h->graph_launches[prec];
     } else {
-        vcycle_body(h, prec, s);
+        vcycle_body(h, prec, s, !any_prof);
     }
 }
 
@@ -2017,8 +2061,6 @@ void upload_coarse(stokes_mg* h, cudaStream_t su) {
     h->c_colk = dalloc<double>(nb);
     h->c_status = dalloc<int>(1);
     CK(cudaMemsetAsync(h->c_status, 0, sizeof(int), su));
-    h->cb64 = halloc<double>(h, n);
-    h->ce64 = halloc<double>(h, n);
 }
 
 // can one cluster of GJC_CTAS CTAs run gj_cluster_panel with this much
