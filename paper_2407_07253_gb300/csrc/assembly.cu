@@ -605,6 +605,45 @@ void scan_rows(const int* len, int n, int* rp, int* tmp, cudaStream_t s) {
     k_scan_add<<<(n + 255) / 256, 256, 0, s>>>(rp, n, tmp, nblk);
 }
 
+namespace {
+__global__ void k_nc_count(long long m, const int* __restrict__ idx, int* __restrict__ cnt) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m; t += (long long)gridDim.x * blockDim.x)
+        atomicAdd(cnt + idx[t], 1);
+}
+__global__ void k_nc_fill(long long m, const int* __restrict__ idx, const int* __restrict__ off, int* __restrict__ cur,
+                          int* __restrict__ adj) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m; t += (long long)gridDim.x * blockDim.x) {
+        const int i = idx[t];
+        adj[off[i] + atomicAdd(cur + i, 1)] = (int)t;
+    }
+}
+// the fill's order within a list depends on the atomics: sort every list
+__global__ void k_nc_sort(int n, const int* __restrict__ off, int* __restrict__ adj) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int* a = adj + off[i];
+        const int len = off[i + 1] - off[i];
+        for (int x = 1; x < len; ++x) {
+            const int v = a[x];
+            int y = x;
+            for (; y > 0 && a[y - 1] > v; --y) a[y] = a[y - 1];
+            a[y] = v;
+        }
+    }
+}
+}  // namespace
+
+void node_cells(const int* cell_nodes, long long m, int n, int* off, int* adj, int* cnt, int* cur, int* tmp,
+                cudaStream_t s) {
+    if (n <= 0) return;
+    cudaMemsetAsync(cnt, 0, sizeof(int) * n, s);
+    cudaMemsetAsync(cur, 0, sizeof(int) * n, s);
+    const int g = (int)std::min<long long>((m + 255) / 256, 152LL * 16);
+    if (m > 0) k_nc_count<<<g, 256, 0, s>>>(m, cell_nodes, cnt);
+    scan_rows(cnt, n, off, tmp, s);
+    if (m > 0) k_nc_fill<<<g, 256, 0, s>>>(m, cell_nodes, off, cur, adj);
+    k_nc_sort<<<(n + 255) / 256, 256, 0, s>>>(n, off, adj);
+}
+
 void fill_rows(const AsmMesh& m, const int* rp, int* ci, double* v, int* status, cudaStream_t s) {
     const int items = m.nVf + m.nQ;
     k_fill<<<(items + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(m, rp, ci, v, status);

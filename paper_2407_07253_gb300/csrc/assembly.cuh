@@ -46,6 +46,12 @@ void row_lengths(const AsmMesh& m, int* len, int* status, cudaStream_t s);
 // Exclusive scan of len into rp[0..n] (rp[n] = total); tmp holds
 // ceil(n / 1024) + 1 ints.
 void scan_rows(const int* len, int n, int* rp, int* tmp, cudaStream_t s);
+// Incidence lists of a space's nodes: adj[off[i] .. off[i+1]) holds the
+// positions t = e * per_cell + l of node i in cell_nodes[0 .. m), in
+// increasing order (so the incident cells in increasing index).  cnt and cur
+// hold n ints, tmp ceil(n / 1024) + 1; off n + 1, adj m.
+void node_cells(const int* cell_nodes, long long m, int n, int* off, int* adj, int* cnt, int* cur, int* tmp,
+                cudaStream_t s);
 // Pass 2: columns and values.
 void fill_rows(const AsmMesh& m, const int* rp, int* ci, double* v, int* status, cudaStream_t s);
 // b[r] = (M f)(row r) / nu_const on velocity rows, 0 on pressure rows, minus

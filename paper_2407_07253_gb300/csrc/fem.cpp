@@ -215,6 +215,26 @@ static double now_ms() {
                std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// STOKES_TRACE=1: times of the host build's phases on stderr
+static bool host_trace() {
+    static const bool on = [] {
+        const char* e = std::getenv("STOKES_TRACE");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+struct PhaseClock {
+    const char* scope;
+    double t;
+    explicit PhaseClock(const char* s) : scope(s), t(host_trace() ? now_ms() : 0.0) {}
+    void lap(const char* what) {
+        if (!host_trace()) return;
+        const double n = now_ms();
+        std::fprintf(stderr, "[sfem]   %-10s %-22s %7.3f ms\n", scope, what, n - t);
+        t = n;
+    }
+};
+
 // ---------------------------------------------------------------- meshes --
 static inline uint64_t edge_key(int a, int b) {
     if (a > b) std::swap(a, b);
@@ -517,6 +537,7 @@ static inline uint64_t face_key(int a, int b, int c, int nv) {
 
 static void build_topology(const Mesh& m, Topology& T) {
     const int d = m.d, nvpc = d + 1, nle = d == 2 ? 3 : 6;
+    PhaseClock pc("topology");
     T.d = d;
     // vertex -> cells (cells in increasing index)
     T.v2c_off.assign(m.nv + 1, 0);
@@ -532,6 +553,7 @@ static void build_topology(const Mesh& m, Topology& T) {
     // among the sorted distinct neighbours w > a of a (over a's cells),
     // offset by the counts of the vertices before a.  Built in parallel
     // without hashing; only the identity of the ids matters downstream.
+    pc.lap("vertex->cells");
     std::vector<int> nbr_off(m.nv + 1, 0);
     auto upper_neighbours = [&](int a, std::vector<int>& w) {
         w.clear();
@@ -559,6 +581,7 @@ static void build_topology(const Mesh& m, Topology& T) {
             std::copy(w.begin(), w.end(), nbr.begin() + nbr_off[a]);
         }
     }, 1024);
+    pc.lap("edge lists");
     T.cell_edge.resize((size_t)m.nc * nle);
     parallel_for(m.nc, [&](int lo, int hi, int) {
         for (int e = lo; e < hi; ++e) {
@@ -573,6 +596,7 @@ static void build_topology(const Mesh& m, Topology& T) {
         }
     }, 1024);
     T.ne = nbr_off[m.nv];
+    pc.lap("cell edges");
     std::vector<int> facet_count;
     if (d == 3) {
         T.cell_face.resize((size_t)m.nc * 4);
@@ -595,6 +619,7 @@ static void build_topology(const Mesh& m, Topology& T) {
         facet_count.assign(T.ne, 0);
         for (int x : T.cell_edge) facet_count[x]++;
     }
+    pc.lap("faces/facet counts");
     // boundary facets: owned by one cell; mark their vertices, edges, faces
     T.bvert.assign(m.nv, 0);
     T.bedge.assign(T.ne, 0);
@@ -617,6 +642,7 @@ static void build_topology(const Mesh& m, Topology& T) {
             }
         }
     }
+    pc.lap("boundary");
 }
 
 static int binom(int n, int r) {
@@ -667,6 +693,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         });
         return;
     }
+    PhaseClock pc(continuous ? "space" : "space-dg");
     // rank tables for compositions of k into m positive parts
     std::vector<std::vector<int>> rank(5);
     std::vector<int> nint(5, 0);
@@ -706,6 +733,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         base[4] = base[3] + nf * nint[3];
     }
     long long ntmp = d == 2 ? base[3] + (long long)m.nc * nint[3] : base[4] + (long long)m.nc * nint[4];
+    pc.lap("rank tables");
     // entity-based id of every (cell, local node)
     std::vector<int> tmp((size_t)m.nc * nb);
     parallel_for(m.nc, [&](int lo, int hi, int) {
@@ -733,6 +761,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
     }, 512);
     // renumber by first appearance: first[x] = least position of id x, the
     // first positions in increasing order get 0, 1, 2, ...
+    pc.lap("entity ids");
     const long long ntot = (long long)tmp.size();
     std::vector<int> first(ntmp, INT32_MAX);
     parallel_for((int)ntot, [&](int lo, int hi, int) {
@@ -747,10 +776,12 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
         for (int t = lo; t < hi; ++t) isfirst[t] = first[tmp[t]] == t;
     }, 16384);
     parallel_scan(isfirst.data(), (int)ntot, rankpos.data());
+    pc.lap("first appearance");
     const int n = rankpos[ntot];
     parallel_for((int)ntot, [&](int lo, int hi, int) {
         for (int t = lo; t < hi; ++t) S.cell_nodes[t] = rankpos[first[tmp[t]]];
     }, 16384);
+    pc.lap("cell nodes");
     S.n = n;
     S.X.assign((size_t)n * d, 0.0);
     S.boundary.assign(n, 0);
@@ -787,6 +818,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
             S.boundary[id] = b;
         }
     }, 4096);
+    pc.lap("node data");
 }
 
 // --------------------------------------------------------------- assembly --
@@ -831,6 +863,7 @@ static void node_cells(const Space& S, int nc, std::vector<int>& off, std::vecto
 static void prepare_level(const Mesh& m, Level& L, const RefTensors& RT) {
     const int d = m.d, nq = L.Q.nb, nc = m.nc;
     const Space &V = L.V, &Q = L.Q;
+    PhaseClock pc("prepare");
     L.vfree.assign(V.n, -1);
     int nVf = 0;
     for (int i = 0; i < V.n; ++i)
@@ -838,8 +871,9 @@ static void prepare_level(const Mesh& m, Level& L, const RefTensors& RT) {
     L.nVf = nVf;
     L.nQ = Q.n;
     L.n_free = d * nVf + Q.n;
-    node_cells(V, nc, L.voff, L.vadj);
-    node_cells(Q, nc, L.qoff, L.qadj);
+    pc.lap("free numbering");
+    // (the node -> cell incidence lists a device assembly reads are built on
+    // the device from the cell-node maps)
     std::vector<double> det(nc);
     L.cell_center.resize((size_t)nc * d);
     parallel_for(nc, [&](int lo, int hi, int) {
@@ -852,15 +886,12 @@ static void prepare_level(const Mesh& m, Level& L, const RefTensors& RT) {
             }
         }
     }, 1024);
-    // int psi_q: contributions of the incident cells in increasing order
+    // int psi_q: the contributions of the incident cells in increasing cell
+    // order (a node occurs once per cell)
     L.pint.assign(Q.n, 0.0);
-    parallel_for(Q.n, [&](int lo, int hi, int) {
-        for (int q = lo; q < hi; ++q) {
-            double s = 0.0;
-            for (int x = L.qoff[q]; x < L.qoff[q + 1]; ++x) s += det[L.qadj[x] / nq] * RT.qint[L.qadj[x] % nq];
-            L.pint[q] = s;
-        }
-    }, 4096);
+    for (int e = 0; e < nc; ++e)
+        for (int l = 0; l < nq; ++l) L.pint[Q.cell_nodes[(size_t)e * nq + l]] += det[e] * RT.qint[l];
+    pc.lap("geometry, int psi");
 }
 
 static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const std::vector<double>& nu,
@@ -1138,6 +1169,7 @@ centers:
 // cells around it).
 static void build_patches(const Mesh& m, const Topology& T, Level& L) {
     const int d = m.d, nb = L.V.nb, nq = L.Q.nb;
+    PhaseClock pc("patches");
     // per vertex: the free velocity nodes of the cells around it, then the
     // pressure nodes of its star (TH: nodes whose entity has the vertex in
     // its closure) or of those cells (SV), each group sorted and unique
@@ -1172,6 +1204,7 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
         NV[v] = (int)(s1 - s0);
         NP[v] = (int)(out.size() - s1);
     });
+    pc.lap("star lists");
     // vertices with a non-empty patch, in order; patch p lists d blocks of its
     // velocity nodes (one per component), then its pressures
     std::vector<int> vid;
@@ -1197,6 +1230,7 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
             L.patch_nv[p] = nvv;
         }
     }, 512);
+    pc.lap("patch dofs");
 }
 
 // Finite-element interpolation (Sec. 3.1): the coarse basis evaluated at the
