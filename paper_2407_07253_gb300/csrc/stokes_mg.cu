@@ -259,6 +259,8 @@ struct stokes_mg {
     double *V = nullptr, *Z = nullptr, *Hh = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *h = nullptr, *hn = nullptr, *resid = nullptr, *partial = nullptr, *scal = nullptr;
     double* pinned = nullptr;
+    int* pinned_rb = nullptr;            // setup readback: statuses and sizes (finish_setup)
+    size_t n_rb = 0;
     double* pinned_H = nullptr;          // [STOKES_MAX_LEVELS + 1][HESS_MAX * HESS_MAX]
     double* Hlev = nullptr;              // device Hessenberg matrices, one per level
     double* v0buf = nullptr;             // Arnoldi start vector
@@ -1738,19 +1740,6 @@ void assemble_dev(stokes_mg* h, DevLevel& l, cudaStream_t s) {
 }
 
 // exact nnz of the device-assembled operators (after the setup stream synchronised)
-void finish_assembly(stokes_mg* h) {
-    auto fin = [&](DevLevel& l, int li) {
-        if (!l.dev_asm) return;
-        int st = 0, nnz = 0;
-        CK(cudaMemcpy(&st, l.asm_status, sizeof(int), cudaMemcpyDeviceToHost));
-        if (st != 0) throw StokesError(STOKES_EUNSUPPORTED, "a node has more than 1024 neighbours (level " + std::to_string(li) + ")");
-        CK(cudaMemcpy(&nnz, l.K.rp + l.K.nr, sizeof(int), cudaMemcpyDeviceToHost));
-        l.K.nnz = nnz;
-        l.K.lanes = choose_lanes(l.K);
-    };
-    if (h->fbf) fin(h->fbf->S0d, 0);
-    for (size_t li = 0; li < h->L.size(); ++li) fin(h->L[li], (int)li);
-}
 
 // FBF: level 0's operator.  The SV Stokes K of the finest mesh is assembled
 // on the device (FbfData::S0d, also the outer FGMRES operator and the input
@@ -1830,7 +1819,7 @@ void ensure_mesh_on_device(stokes_mg* h, int mi, cudaStream_t s) {
 // launch: the fine level's assembly inputs, the coarse level's cell nodes
 // and free map).  Host uploads happen here, on the calling (host) thread;
 // `launch_on` queues the kernels.  The exact entry counts are read back by
-// finish_transfers.
+// finish_setup.
 void build_transfer_dev(stokes_mg* h, int li, bool want32, const std::function<void(std::function<void()>)>& launch_on) {
     const sfem::Level& F = h->H.levels[li];
     const sfem::Level& C = h->H.levels[li + 1];
@@ -1934,17 +1923,6 @@ void build_transfer_dev(stokes_mg* h, int li, bool want32, const std::function<v
 
 // exact entry counts of the device-built transfers (after the setup streams
 // have drained)
-void finish_transfers(stokes_mg* h) {
-    for (size_t li = 0; li + 1 < h->L.size(); ++li) {
-        DevLevel& l = h->L[li];
-        if (!l.dev_transfer) continue;
-        int nnz = 0;
-        CK(cudaMemcpy(&nnz, l.P.rp + l.P.nr, sizeof(int), cudaMemcpyDeviceToHost));
-        l.P.nnz = l.R.nnz = nnz;
-        l.P.lanes = choose_lanes(l.P);
-        l.R.lanes = choose_lanes(l.R);
-    }
-}
 
 // gather K_i and invert every patch of level li; work receives the
 // row-major inverses (sum n_i^2 doubles) when keep != nullptr.
@@ -2017,7 +1995,7 @@ void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status,
 }
 
 // Launch the gather + inversion of level li on stream s without waiting;
-// the workspace and status array stay in h->pending until finish_patches.
+// the workspace and status array stay in h->pending until finish_setup.
 void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
     DevLevel& l = h->L[li];
     if (l.npatch == 0) return;
@@ -2025,7 +2003,7 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
     pp.level = li;
     pp.work = palloc<double>(h->device, l.nsq, s);
     pp.status = palloc<int>(h->device, l.npatch, s);
-    pp.stream = s;   // freed on the same stream after finish_patches synchronised it
+    pp.stream = s;   // freed on the same stream after finish_setup synchronised it
     h->pending.push_back(pp);
     CK(cudaMemsetAsync(pp.status, 0, sizeof(int) * l.npatch, s));
     gather_and_invert(h, li, pp.work, INV_STORE, pp.status, s);
@@ -2040,23 +2018,6 @@ void free_pending(stokes_mg* h) {
 }
 
 // Wait for every launched patch inversion and report the first zero pivot.
-void finish_patches(stokes_mg* h, cudaStream_t s) {
-    CK(cudaStreamSynchronize(s));
-    for (cudaStream_t x : h->s_lvl)
-        if (x) CK(cudaStreamSynchronize(x));
-    for (auto& pp : h->pending) {
-        DevLevel& l = h->L[pp.level];
-        std::vector<int> hs(l.npatch);
-        CK(cudaMemcpy(hs.data(), pp.status, sizeof(int) * l.npatch, cudaMemcpyDeviceToHost));
-        for (int p = 0; p < l.npatch; ++p)
-            if (hs[p] != 0) {
-                h->st.singular_patch = pp.level * (1 << 24) + p;
-                throw StokesError(STOKES_ESINGULAR, "zero pivot in patch " + std::to_string(p) + " of level " +
-                                                        std::to_string(pp.level));
-            }
-    }
-    free_pending(h);
-}
 
 // Bordered coarse matrix (zero-mean pressure constraint, Sec. 2) inverted in
 // place on stream s (no wait): by one thread-block cluster when its rows fit
@@ -2183,15 +2144,95 @@ void free_coarse_ws(stokes_mg* h) {
     h->c_status = nullptr;
 }
 
-void finish_coarse(stokes_mg* h, cudaStream_t s) {
-    int hs = 0;
-    CK(cudaMemcpyAsync(&hs, h->c_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+
+// pinned room for finish_setup's readback (allocated while the device still
+// works on level 0, off the critical path)
+void alloc_readback(stokes_mg* h) {
+    size_t n = 8 + 4 * (h->L.size() + 1);
+    for (const auto& l : h->L) n += (size_t)std::max(l.npatch, 0);
+    if (n <= h->n_rb) return;
+    if (h->pinned_rb) CK(cudaFreeHost(h->pinned_rb));
+    CK(cudaMallocHost((void**)&h->pinned_rb, sizeof(int) * n));
+    h->n_rb = n;
+}
+
+// What the host still needs from the setup kernels, with one wait: every
+// setup stream is joined into s, the patch statuses, the assembly statuses
+// and sizes, the transfer sizes and the coarse and apply statuses are copied
+// into pinned memory on s, and s is synchronised once.  The checks then run
+// in that order: patches, assembly, transfers, coarse factorisation, apply.
+void finish_setup(stokes_mg* h, cudaStream_t s) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    std::vector<cudaStream_t> ss(h->s_lvl.begin(), h->s_lvl.end());
+    ss.push_back(h->s_tr);
+    ss.push_back(h->s_coarse);
+    ss.push_back(h->s_up);
+    for (cudaStream_t x : ss)
+        if (x && x != s) {
+            CK(cudaEventRecord(ev, x));
+            CK(cudaStreamWaitEvent(s, ev, 0));
+        }
+    CK(cudaEventDestroy(ev));
+    alloc_readback(h);
+    int* rb = h->pinned_rb;
+    size_t o = 0;
+    auto get = [&](const int* d, size_t n) {
+        if (o + n > h->n_rb) throw StokesError(STOKES_ECUDA, "internal: setup readback overflow");
+        CK(cudaMemcpyAsync(rb + o, d, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        const size_t at = o;
+        o += n;
+        return at;
+    };
+    std::vector<size_t> at_pp;
+    for (auto& pp : h->pending) at_pp.push_back(get(pp.status, (size_t)h->L[pp.level].npatch));
+    std::vector<DevLevel*> asm_lv;
+    if (h->fbf && h->fbf->S0d.dev_asm) asm_lv.push_back(&h->fbf->S0d);
+    for (auto& l : h->L)
+        if (l.dev_asm) asm_lv.push_back(&l);
+    std::vector<size_t> at_asm;
+    for (DevLevel* l : asm_lv) {
+        at_asm.push_back(get(l->asm_status, 1));
+        get(l->K.rp + l->K.nr, 1);
+    }
+    std::vector<size_t> at_tr(h->L.size(), 0);
+    for (size_t li = 0; li + 1 < h->L.size(); ++li)
+        if (h->L[li].dev_transfer) at_tr[li] = get(h->L[li].P.rp + h->L[li].P.nr, 1);
+    const size_t at_c = h->c_status ? get(h->c_status, 1) : 0;
+    const size_t at_sa = h->sa_status ? get(h->sa_status, 1) : 0;
     CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < h->pending.size(); ++i) {
+        const auto& pp = h->pending[i];
+        const int np = h->L[pp.level].npatch;
+        for (int p = 0; p < np; ++p)
+            if (rb[at_pp[i] + p] != 0) {
+                h->st.singular_patch = pp.level * (1 << 24) + p;
+                throw StokesError(STOKES_ESINGULAR, "zero pivot in patch " + std::to_string(p) + " of level " +
+                                                        std::to_string(pp.level));
+            }
+    }
+    free_pending(h);
+    for (size_t i = 0; i < asm_lv.size(); ++i) {
+        DevLevel& l = *asm_lv[i];
+        if (rb[at_asm[i]] != 0) throw StokesError(STOKES_EUNSUPPORTED, "a node has more than 1024 neighbours");
+        l.K.nnz = rb[at_asm[i] + 1];
+        l.K.lanes = choose_lanes(l.K);
+    }
+    for (size_t li = 0; li + 1 < h->L.size(); ++li) {
+        DevLevel& l = h->L[li];
+        if (!l.dev_transfer) continue;
+        l.P.nnz = l.R.nnz = rb[at_tr[li]];
+        l.P.lanes = choose_lanes(l.P);
+        l.R.lanes = choose_lanes(l.R);
+    }
+    const int cst = h->c_status ? rb[at_c] : 0;
     free_coarse_ws(h);
-    if (hs != 0) {
+    if (cst != 0) {
         h->st.singular_patch = -2;
         throw StokesError(STOKES_ESINGULAR, "zero pivot in the coarse bordered LU");
     }
+    if (h->sa_status && rb[at_sa] != 0)
+        throw StokesError(STOKES_ECUDA, "a patch-apply CTA gave up waiting for its bulk copy (bounded wait)");
 }
 
 void setup_solve_buffers(stokes_mg* h, cudaStream_t s) {
@@ -2637,7 +2678,10 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         } else {
             sfem::build_hierarchy(cm, spec, nu_cell, h->H, on_level);
         }
-        if (!o.host_only) mark(h.get(), "host hierarchy built", h->s_up);
+        if (!o.host_only) {
+            mark(h.get(), "host hierarchy built", h->s_up);
+            alloc_readback(h.get());
+        }
         h->st.t_mesh_ms = h->H.t_mesh_ms;
         h->st.t_assembly_ms = h->H.t_assembly_ms;
         h->st.t_spaces_ms = h->H.t_spaces_ms;
@@ -2666,17 +2710,12 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         h->st.t_upload_post_ms = host_ms() - t1;
         h->st.t_launch_wait_ms = t_wait_launch;
         h->st.t_launch_thread_ms = t_launch;
-        // what remains of the patch inversions and of the coarse
-        // factorisation once the host is done
+        // what remains of the patch inversions, the lambda_max estimates and
+        // the coarse factorisation once the host is done (one wait)
         t1 = host_ms();
-        finish_patches(h.get(), s);
-        finish_assembly(h.get());
-        if (h->s_tr) CK(cudaStreamSynchronize(h->s_tr));
-        finish_transfers(h.get());
+        finish_setup(h.get(), s);
         h->st.t_gather_lu_ms = host_ms() - t1;
-        t1 = host_ms();
-        finish_coarse(h.get(), h->s_coarse);
-        h->st.t_coarse_ms = host_ms() - t1;
+        h->st.t_coarse_ms = 0;
         t1 = host_ms();
         {
             const size_t hsz = (size_t)skern::HESS_MAX * skern::HESS_MAX;
@@ -2690,9 +2729,6 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         h->st.t_eig_ms = host_ms() - t1;
         t1 = host_ms();
         if (o.use_graph) capture_graph(h.get(), o.precision, s);
-        CK(cudaStreamSynchronize(s));
-        for (cudaStream_t x : h->s_lvl)
-            if (x) check_sa_status(h.get(), x);
         h->st.t_graph_ms = host_ms() - t1;
         h->st.t_total_ms = host_ms() - t0;
         mark(h.get(), "setup end", s);
@@ -3560,6 +3596,7 @@ void stokes_mg_destroy(stokes_mg_t h) {
         cudaStreamSynchronize(0);
     }
     if (h->pinned) cudaFreeHost(h->pinned);
+    if (h->pinned_rb) cudaFreeHost(h->pinned_rb);
     if (h->pinned_H) cudaFreeHost(h->pinned_H);
     if (h->bstat_h) cudaFreeHost(h->bstat_h);
     if (h->bk.host) cudaFreeHost(h->bk.host);
