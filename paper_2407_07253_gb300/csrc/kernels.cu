@@ -720,8 +720,24 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
 // components' B_c^T and W_c = Li B_c^T go through one pair of buffers, W_c
 // is written out as soon as it exists and S = sum_c B_c W_c accumulates over
 // the components.  Scratch: saddle_scratch_factored(d, n, nv) doubles.
-__device__ void saddle_core_factored(int d, int n, int nv, const double* K, double* scratch, double* fac64,
-                                     float* fac32, int packed, int* status) {
+// position of global DoF c in a patch's sorted DoF list sd[0 .. n), or -1
+__device__ __forceinline__ int patch_pos(const int* sd, int n, int c) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sd[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return sd[lo] == c ? lo : -1;
+}
+
+// K == nullptr: the blocks are read from the CSR operator (rp, ci, av) rows
+// of the patch's DoFs sd (sorted, shared memory) instead of a dense copy:
+// the velocity block of component 0 (its upper triangle) and, per component,
+// B_c^T, each entry placed by a binary search of its column in sd
+__device__ void saddle_core_factored(int d, int n, int nv, const double* K, const int* sd, const int* __restrict__ rp,
+                                     const int* __restrict__ ci, const double* __restrict__ av, double* scratch,
+                                     double* fac64, float* fac32, int packed, int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int np = n - d * nv, npp = np | 1, dnv = d * nv;
@@ -740,8 +756,23 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, doub
     const long long lenL = packed ? ((long long)nv * (nv + 1) / 2 + vec - 1) / vec * vec : (long long)ldl * nv;
     const long long oW = lenL, oS = oW + (long long)ldw * np;
     const int ns = np * (np + 1) / 2;
-    for (int i = warp; i < nv; i += nw)
-        for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
+    if (K) {
+        for (int i = warp; i < nv; i += nw)
+            for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
+    } else {
+        // the rows of component 0 give the velocity block and B_0^T
+        for (int t = tid; t < nv * nv; t += nt) Ls[t] = 0.0;
+        for (int t = tid; t < nv * npp; t += nt) Bt[t] = 0.0;
+        __syncthreads();
+        for (int i = warp; i < nv; i += nw) {
+            const int g = sd[i], e = rp[g + 1];
+            for (int q = rp[g] + lane; q < e; q += 32) {
+                const int pos = patch_pos(sd, n, ci[q]);
+                if (pos >= i && pos < nv) Ls[i * nv + pos] = av[q];
+                else if (pos >= dnv) Bt[(long long)i * npp + pos - dnv] = av[q];
+            }
+        }
+    }
     for (int t = tid; t < np * np; t += nt) Ss[t] = 0.0;
     __syncthreads();
     sweep_spd(Ls, nv, nv, ck, cs, rinv, status);
@@ -777,8 +808,20 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, doub
         }
     }
     for (int c = 0; c < d; ++c) {
-        for (int a = warp; a < nv; a += nw)
-            for (int q = lane; q < np; q += 32) Bt[(long long)a * npp + q] = K[(long long)(c * nv + a) * n + dnv + q];
+        if (K) {
+            for (int a = warp; a < nv; a += nw)
+                for (int q = lane; q < np; q += 32) Bt[(long long)a * npp + q] = K[(long long)(c * nv + a) * n + dnv + q];
+        } else if (c > 0) {
+            for (int t = tid; t < nv * npp; t += nt) Bt[t] = 0.0;
+            __syncthreads();
+            for (int a = warp; a < nv; a += nw) {
+                const int g = sd[c * nv + a], e = rp[g + 1];
+                for (int q = rp[g] + lane; q < e; q += 32) {
+                    const int pos = patch_pos(sd, n, ci[q]);
+                    if (pos >= dnv) Bt[(long long)a * npp + pos - dnv] = av[q];
+                }
+            }
+        }
         __syncthreads();
         // W_c = Li B_c^T: entry t = (a, q)
         const int nw_out = nv * np;
@@ -827,17 +870,27 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
                                                            float* __restrict__ inv32, const long long* __restrict__ foff64,
                                                            double* __restrict__ fac64, const long long* __restrict__ foff32,
                                                            float* __restrict__ fac32, int back, int packed,
-                                                           long long max_scratch, int* __restrict__ status) {
+                                                           long long max_scratch, const int* __restrict__ pdofs,
+                                                           const int* __restrict__ rp, const int* __restrict__ ci,
+                                                           const double* __restrict__ av, int sd_off,
+                                                           int* __restrict__ status) {
     extern __shared__ double sscr[];
     const int p = blockIdx.x;
     const int n = poff[p + 1] - poff[p], nv = pnv[p];
     if (n == 0 || saddle_scratch(d, n, nv) > max_scratch) return;
     __shared__ int st;
+    int* sd = reinterpret_cast<int*>(sscr + sd_off);
+    if (!work && (inv64 || inv32 || back)) {      // the explicit forms need the dense block
+        if (threadIdx.x == 0) status[p] = 1;
+        return;
+    }
     if (threadIdx.x == 0) st = 0;
+    if (!work)
+        for (int a = threadIdx.x; a < n; a += blockDim.x) sd[a] = pdofs[poff[p] + a];
     __syncthreads();
     if (!inv64 && !inv32 && !back)
-        saddle_core_factored(d, n, nv, work + moff[p], sscr, fac64 ? fac64 + foff64[p] : nullptr,
-                             fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
+        saddle_core_factored(d, n, nv, work ? work + moff[p] : nullptr, sd, rp, ci, av, sscr,
+                             fac64 ? fac64 + foff64[p] : nullptr, fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
     else
         saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr,
                     inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,
@@ -862,8 +915,8 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
     if (threadIdx.x == 0) st = 0;
     __syncthreads();
     if (!inv64 && !inv32 && !back)
-        saddle_core_factored(d, n, nv, work + moff[p], scratch + soff[p], fac64 ? fac64 + foff64[p] : nullptr,
-                             fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
+        saddle_core_factored(d, n, nv, work + moff[p], nullptr, nullptr, nullptr, nullptr, scratch + soff[p],
+                             fac64 ? fac64 + foff64[p] : nullptr, fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
     else
         saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,
                     inv32 ? inv32 + off32[p] : nullptr, fac64 ? fac64 + foff64[p] : nullptr,

@@ -194,14 +194,19 @@ __host__ __device__ inline long long saddle_scratch_factored(int d, int n, int n
 // Outputs (each may be NULL): explicit inverses inv64 / inv32 (column-major,
 // leading dimension n rounded up to 2 / 4), the factored form fac64 / fac32
 // at foff64[p] / foff32[p] (saddle_factor_len), and, if back, the explicit
-// inverse row-major in place of K_i.
+// inverse row-major in place of K_i.  saddle_inverse_smem with work == NULL
+// (factored form only) reads each patch's rows of the CSR operator (rp, ci,
+// av) directly, its sorted DoF list pdofs[poff[p] ..) held in shared memory
+// at double offset sd_off (after the scratch).
 __global__ void saddle_inverse_smem(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
                                     const long long* __restrict__ moff, double* __restrict__ work,
                                     const long long* __restrict__ off64, double* __restrict__ inv64,
                                     const long long* __restrict__ off32, float* __restrict__ inv32,
                                     const long long* __restrict__ foff64, double* __restrict__ fac64,
                                     const long long* __restrict__ foff32, float* __restrict__ fac32, int back,
-                                    int packed, long long max_scratch, int* __restrict__ status);
+                                    int packed, long long max_scratch, const int* __restrict__ pdofs,
+                                    const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ av,
+                                    int sd_off, int* __restrict__ status);
 __global__ void saddle_inverse_global(int npatch, int d, const int* __restrict__ poff, const int* __restrict__ pnv,
                                       const long long* __restrict__ moff, double* __restrict__ work,
                                       const long long* __restrict__ off64, double* __restrict__ inv64,

@@ -1926,14 +1926,24 @@ void build_transfer_dev(stokes_mg* h, int li, bool want32, const std::function<v
 
 // gather K_i and invert every patch of level li; work receives the
 // row-major inverses (sum n_i^2 doubles) when keep != nullptr.
+// whether level li's factored inverses are computed straight from its CSR
+// operator (every patch inverted in shared memory, with room for its DoF list)
+bool fused_factor(const stokes_mg* h, const DevLevel& l) {
+    return h->opts.patch_solver == 0 && !l.inv64 && !l.inv32 && l.saddle_global == 0 && l.saddle_smem > 0 &&
+           l.saddle_smem_fac + (l.maxn + 1) / 2 <= skern::SADDLE_SMEM_MAX_DOUBLES;
+}
+
 void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status, cudaStream_t s) {
     DevLevel& l = h->L[li];
     if (l.npatch == 0) return;
-    launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(l.nsq), 256, 0, s>>>(l.nsq, 0.0, work); });
-    launch(h, -1, s, [&] {
-        skern::patch_gather<<<l.npatch, 256, l.maxn * sizeof(int), s>>>(l.npatch, l.poff, l.pdofs, l.moff, l.K.rp, l.K.ci,
-                                                                       l.K.v64, work);
-    });
+    const bool fused = out == INV_STORE && fused_factor(h, l);
+    if (!fused) {
+        launch(h, -1, s, [&] { skern::fill_vec<double><<<grid_for(l.nsq), 256, 0, s>>>(l.nsq, 0.0, work); });
+        launch(h, -1, s, [&] {
+            skern::patch_gather<<<l.npatch, 256, l.maxn * sizeof(int), s>>>(l.npatch, l.poff, l.pdofs, l.moff, l.K.rp,
+                                                                           l.K.ci, l.K.v64, work);
+        });
+    }
     const bool store = out == INV_STORE;
     double* i64 = store ? l.inv64 : nullptr;
     float* i32 = store || out == INV_EXPLICIT32 ? l.inv32 : nullptr;
@@ -1945,16 +1955,17 @@ void gather_and_invert(stokes_mg* h, int li, double* work, int out, int* status,
         float* f32 = store ? l.fac32 : nullptr;
         if (l.saddle_smem > 0) {
             const bool fac_only = !i64 && !i32 && !back;
-            const size_t smem = (size_t)(fac_only ? l.saddle_smem_fac : l.saddle_smem) * sizeof(double);
+            const long long sd_off = fac_only ? l.saddle_smem_fac : l.saddle_smem;
+            const size_t smem = (size_t)(sd_off + (fused ? (l.maxn + 1) / 2 : 0)) * sizeof(double);
             // one upper bound for every level (levels launch from one thread
             // onto different streams)
             CK(cudaFuncSetAttribute(skern::saddle_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(skern::SADDLE_SMEM_MAX_DOUBLES * sizeof(double))));
             launch(h, PK_GJ, s, [&] {
-                skern::saddle_inverse_smem<<<l.npatch, 256, smem, s>>>(l.npatch, d, l.poff, l.pnv, l.moff, work, l.ioff64, i64,
-                                                                       l.ioff32, i32, l.foff64, f64, l.foff32, f32, back,
-                                                                       l.fac_packed ? 1 : 0, skern::SADDLE_SMEM_MAX_DOUBLES,
-                                                                       status);
+                skern::saddle_inverse_smem<<<l.npatch, 256, smem, s>>>(
+                    l.npatch, d, l.poff, l.pnv, l.moff, fused ? nullptr : work, l.ioff64, i64, l.ioff32, i32, l.foff64, f64,
+                    l.foff32, f32, back, l.fac_packed ? 1 : 0, skern::SADDLE_SMEM_MAX_DOUBLES, l.pdofs, l.K.rp, l.K.ci,
+                    l.K.v64, (int)sd_off, status);
             });
         }
         if (l.saddle_global > 0) {
@@ -2001,7 +2012,7 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
     if (l.npatch == 0) return;
     PendingPatches pp;
     pp.level = li;
-    pp.work = palloc<double>(h->device, l.nsq, s);
+    pp.work = fused_factor(h, l) ? nullptr : palloc<double>(h->device, l.nsq, s);
     pp.status = palloc<int>(h->device, l.npatch, s);
     pp.stream = s;   // freed on the same stream after finish_setup synchronised it
     h->pending.push_back(pp);
@@ -2011,7 +2022,7 @@ void launch_patches(stokes_mg* h, int li, cudaStream_t s) {
 
 void free_pending(stokes_mg* h) {
     for (auto& pp : h->pending) {
-        cudaFreeAsync(pp.work, pp.stream);
+        if (pp.work) cudaFreeAsync(pp.work, pp.stream);
         cudaFreeAsync(pp.status, pp.stream);
     }
     h->pending.clear();
