@@ -950,11 +950,14 @@ def main():
     sizes = []
     flops_gj = 0.0
     # algorithmic flops of the factored saddle block inverse per patch (n_v
-    # velocity nodes per component, n_p pressures, d components):
-    #   n_v^3 (sweep of L, upper triangle) + 2 d n_v^2 n_p (W = L^-1 B^T)
-    #   + d n_v n_p^2 (S = B W, upper) + n_p^3 (sweep of S);
-    # the stored form is (L^-1, W, S^-1), so X = W S^-1 and the explicit
-    # velocity block are not formed
+    # velocity nodes per component, n_p pressures, d components, z_c(q) the
+    # nonzero rows of column q of B_c^T, z_c = sum_q z_c(q)):
+    #   n_v^3 (sweep of L, upper triangle) + 2 n_v z_c per component
+    #   (W_c = L^-1 B_c^T over B's nonzeros) + 2 sum_{q <= r} z_c(q) per
+    #   component (S = B W, upper) + n_p^3 (sweep of S); the kernel skips the
+    #   structural zeros of B (a pressure node couples only with the velocity
+    #   nodes of its support cells); the stored form is (L^-1, W, S^-1), so
+    #   X = W S^-1 and the explicit velocity block are not formed
     # algorithmic bytes of one FP32 saddle apply per patch: L^-1, W and S^-1
     # read once (leading dimensions rounded up to 4), the gathered residual,
     # the weights and the result (3 n_i floats)
@@ -966,14 +969,20 @@ def main():
     for li in range(stats["n_levels"] - 1):
         off, dofs = probe.patches(li)
         _, comp, _ = probe.level_dofs(li)
+        K = probe.get_csr(li).tocsr()
         cd = comp[dofs]
         f = 0.0
         by = 0.0
         for pi in range(len(off) - 1):
+            pd = dofs[off[pi]:off[pi + 1]]
             c = cd[off[pi]:off[pi + 1]]
             nv = float((c == 0).sum())
             npr = float((c == d).sum())
-            f += nv ** 3 + 2 * d * nv * nv * npr + d * nv * npr * npr + npr ** 3
+            f += nv ** 3 + npr ** 3
+            pres = pd[c == d]
+            for cc in range(d):
+                zq = np.asarray((K[pd[c == cc]][:, pres] != 0).sum(axis=0)).ravel().astype(float)
+                f += 2 * nv * zq.sum() + 2 * float((zq * (npr - np.arange(len(zq)))).sum())
             nvi, npi = int(nv), int(npr)
             # L^-1 as its packed upper triangle (the bulk-copy apply's layout)
             by += 4.0 * (up4(nvi * (nvi + 1) // 2) + up4(d * nvi) * npi + up4(npi) * npi) + 12.0 * (d * nvi + npi)

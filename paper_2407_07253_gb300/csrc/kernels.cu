@@ -749,6 +749,13 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
     double* ck = Ss + (long long)np * np;          // [2][mx]
     double* cs = ck + 2 * mx;                      // [mx]
     double* rinv = cs + mx;                        // [2]
+    // [np][mw]: bit a of column q set where B_c^T[a][q] != 0; the products
+    // with B_c^T visit those rows only, in increasing order (the skipped
+    // terms are exact zeros, so the sums equal the dense ones), which saves
+    // most of the DFMAs of W and S: B couples a pressure node only with the
+    // velocity nodes of the cells in its support
+    const int mw = (nv + 63) >> 6;
+    unsigned long long* mk = reinterpret_cast<unsigned long long*>(rinv + 2);
     const int vec = fac64 ? 2 : 4;
     const int ldl = (nv + vec - 1) / vec * vec;
     const int ldw = (dnv + vec - 1) / vec * vec;
@@ -823,15 +830,29 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
             }
         }
         __syncthreads();
-        // W_c = Li B_c^T: entry t = (a, q)
-        const int nw_out = nv * np;
-        for (int t = tid; t < nw_out; t += nt) {
-            const int a = t / np, q = t - a * np;
-            const double* li = Ls + a * nv;
+        // nonzero rows of every column of B_c^T (a warp per column)
+        for (int q = warp; q < np; q += nw)
+            for (int w = 0; w < mw; ++w) {
+                const int a0 = w * 64 + lane, a1 = a0 + 32;
+                const unsigned lo = __ballot_sync(0xffffffffu, a0 < nv && Bt[(long long)a0 * npp + q] != 0.0);
+                const unsigned hi = __ballot_sync(0xffffffffu, a1 < nv && Bt[(long long)a1 * npp + q] != 0.0);
+                if (lane == 0) mk[q * mw + w] = ((unsigned long long)hi << 32) | lo;
+            }
+        __syncthreads();
+        // W_c = Li B_c^T: a warp takes column q for 32 rows a, so that its
+        // lanes share q's mask (one trip count: FP64 instructions are issued
+        // for the whole warp); Li is symmetric, read along row b
+        const int nh = (nv + 31) >> 5;
+        for (int it = warp; it < np * nh; it += nw) {
+            const int q = it / nh, a = (it - q * nh) * 32 + lane;
             const double* bt = Bt + q;
             double sacc = 0.0;
-            for (int b = 0; b < nv; ++b) sacc = fma(li[b], bt[(long long)b * npp], sacc);
-            Wm[(long long)a * npp + q] = sacc;
+            for (int w = 0; w < mw; ++w)
+                for (unsigned long long m = mk[q * mw + w]; m; m &= m - 1) {
+                    const int b = w * 64 + __ffsll((long long)m) - 1;
+                    if (a < nv) sacc = fma(Ls[b * nv + a], bt[(long long)b * npp], sacc);
+                }
+            if (a < nv) Wm[(long long)a * npp + q] = sacc;
         }
         __syncthreads();
         for (int t = tid; t < nv * np; t += nt) {
@@ -846,7 +867,11 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
             while (rem >= np - q) { rem -= np - q; ++q; }
             const int r = q + rem;
             double sacc = 0.0;
-            for (int a = 0; a < nv; ++a) sacc = fma(Bt[(long long)a * npp + q], Wm[(long long)a * npp + r], sacc);
+            for (int w = 0; w < mw; ++w)
+                for (unsigned long long m = mk[q * mw + w]; m; m &= m - 1) {
+                    const int a = w * 64 + __ffsll((long long)m) - 1;
+                    sacc = fma(Bt[(long long)a * npp + q], Wm[(long long)a * npp + r], sacc);
+                }
             Ss[q * np + r] += sacc;
         }
         __syncthreads();
