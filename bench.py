@@ -1003,9 +1003,9 @@ def main():
     achieved_gj0 = flops_levels[0] / (gj0_ms * 1e-3) / 1e12 if gj0_ms > 0 else None
     achieved_gj = flops_gj / (gj_ms_per_step * 1e-3) / 1e12 if gj_ms_per_step > 0 else None
     # DRAM bytes of that launch from one ncu capture of the same kernel and
-    # workload (dram__bytes_read.sum + dram__bytes_write.sum; the summary is
-    # profiles/saddle_inverse_smem_th_p4_64x64.md)
-    traffic_gj0 = (220.420352 + 50.486016) * 1e6 if a.workload == "th_p4_64x64" else None
+    # workload (dram__bytes_read.sum + dram__bytes_write.sum of the level-0
+    # launch of the CSR-reading, sparse-B inversion)
+    traffic_gj0 = (74.866432 + 32.339968) * 1e6 if a.workload == "th_p4_64x64" else None
     # level-0 FP32 saddle apply: algorithmic bytes (above)
     patch_bytes = apply_bytes[0]
     patch_gbs = patch_bytes / (patch_ms * 1e-3) / 1e9 if patch_ms > 0 else None
