@@ -571,6 +571,108 @@ __device__ void sweep_spd(double* A, int n, int lda, double* ck, double* cs, dou
     __syncthreads();
 }
 
+// sweep_spd two pivots per step: the same two FMAs per entry and pivot pair,
+// in the same order, with the same special cases, so the result is bit for
+// bit that of sweep_spd, with half the block barriers.  Warp 0 prepares a
+// step from the published columns k and k+1 (both before pivot k): the
+// scaled column cs = col_k / a_kk, column k+1 after pivot k (each entry by
+// the operation its owner would apply, so c1p equals the column sweep_spd
+// would publish), its scaled copy cs1 and the two reciprocals; then every
+// entry is swept by pivot k and pivot k+1, and the owners of columns k+2 and
+// k+3 publish them for the next step.  Scratch: ck[4n] (two column pairs,
+// double-buffered), cs[n], c1p[n], cs1[n], rinv[2].  status <- 1 + step of
+// the first non-positive pivot.
+__device__ void sweep_spd2(double* A, int n, int lda, double* ck, double* cs, double* c1p, double* cs1, double* rinv,
+                           int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int npair = (n + 1) >> 1;
+    for (int i = tid; i < n; i += nt) {
+        ck[i] = A[i];                                              // column 0 = row 0
+        if (n > 1) ck[n + i] = i == 0 ? A[1] : A[(long long)lda + i];   // column 1
+    }
+    __syncthreads();
+    for (int k = 0, b = 0; k < n; k += 2, ++b) {
+        const double* col0 = ck + (b & 1) * 2 * n;                 // column k before pivot k
+        const double* col1 = col0 + n;                             // column k+1 before pivot k
+        double* nx0 = ck + ((b + 1) & 1) * 2 * n;                  // columns k+2, k+3 for the next step
+        double* nx1 = nx0 + n;
+        const bool two = k + 1 < n;
+        if (warp == 0) {
+            const double akk = col0[k];
+            double inv0 = 0.0;
+            if (lane == 0) {
+                if (!(akk > 0.0) && *status == 0) *status = k + 1;
+                inv0 = akk > 0.0 ? 1.0 / akk : 0.0;
+            }
+            inv0 = __shfl_sync(0xffffffffu, inv0, 0);
+            double csk1 = 0.0, p1 = 0.0, inv1 = 0.0;
+            if (two) {
+                csk1 = col0[k + 1] * inv0;
+                p1 = fma(-csk1, col0[k + 1], col1[k + 1]);         // (k+1, k+1) after pivot k
+                if (lane == 0) {
+                    if (!(p1 > 0.0) && *status == 0) *status = k + 2;
+                    inv1 = p1 > 0.0 ? 1.0 / p1 : 0.0;
+                }
+                inv1 = __shfl_sync(0xffffffffu, inv1, 0);
+            }
+            for (int i = lane; i < n; i += 32) {
+                const double csi = col0[i] * inv0;
+                cs[i] = csi;
+                if (two) {
+                    double v;
+                    if (i == k) v = csk1;                                         // (k, k+1)
+                    else if (i < k + 1) v = fma(-csi, col0[k + 1], col1[i]);      // (i, k+1)
+                    else if (i == k + 1) v = p1;                                  // (k+1, k+1)
+                    else v = fma(-csk1, col0[i], col1[i]);                        // (k+1, i)
+                    c1p[i] = v;
+                    cs1[i] = v * inv1;
+                }
+            }
+            if (lane == 0) {
+                rinv[0] = inv0;
+                rinv[1] = inv1;
+            }
+        }
+        __syncthreads();
+        const double inv0 = rinv[0], inv1 = rinv[1];
+        for (int pr = warp; pr < npair; pr += nw) {
+            const int tot = pair_len(n, pr);
+            for (int l = lane; l < tot; l += 32) {
+                int i, j;
+                pair_entry(n, pr, l, i, j);
+                double* a = A + (long long)i * lda + j;
+                double v = fma(-cs[i], col0[j], *a);
+                if (i == k || j == k) v = (i == j) ? flip(inv0) : cs[i == k ? j : i];
+                if (two) {
+                    const int k1 = k + 1;
+                    double w = fma(-cs1[i], c1p[j], v);
+                    if (i == k1 || j == k1) w = (i == j) ? flip(inv1) : cs1[i == k1 ? j : i];
+                    v = w;
+                }
+                *a = v;
+                if (j == k + 2) nx0[i] = v;
+                else if (i == k + 2) nx0[j] = v;
+                if (j == k + 3) nx1[i] = v;
+                else if (i == k + 3) nx1[j] = v;
+            }
+        }
+        __syncthreads();
+    }
+    // -A^{-1} (upper) -> +A^{-1} (full)
+    for (int pr = warp; pr < npair; pr += nw) {
+        const int tot = pair_len(n, pr);
+        for (int l = lane; l < tot; l += 32) {
+            int i, j;
+            pair_entry(n, pr, l, i, j);
+            const double v = flip(A[(long long)i * lda + j]);
+            A[(long long)i * lda + j] = v;
+            A[(long long)j * lda + i] = v;
+        }
+    }
+    __syncthreads();
+}
+
 // Block inverse of one Vanka patch with the saddle structure
 //   K_i = [L 0 .. B_0^T; 0 L .. B_1^T; ..; B_0 B_1 .. 0]
 // (the d velocity components share the SPD block L on the same nodes):
@@ -746,9 +848,11 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
     double* Bt = Ls + (long long)nv * nv;          // [a][q] of the current component
     double* Wm = Bt + (long long)nv * npp;         // [a][q] of the current component
     double* Ss = Wm + (long long)nv * npp;         // [q][r]
-    double* ck = Ss + (long long)np * np;          // [2][mx]
-    double* cs = ck + 2 * mx;                      // [mx]
-    double* rinv = cs + mx;                        // [2]
+    double* ck = Ss + (long long)np * np;          // [4][mx] (sweep_spd2's column pairs)
+    double* cs = ck + 4 * mx;                      // [mx]
+    double* c1p = cs + mx;                         // [mx]
+    double* cs1 = c1p + mx;                        // [mx]
+    double* rinv = cs1 + mx;                       // [2]
     // [np][mw]: bit a of column q set where B_c^T[a][q] != 0; the products
     // with B_c^T visit those rows only, in increasing order (the skipped
     // terms are exact zeros, so the sums equal the dense ones), which saves
@@ -782,7 +886,7 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
     }
     for (int t = tid; t < np * np; t += nt) Ss[t] = 0.0;
     __syncthreads();
-    sweep_spd(Ls, nv, nv, ck, cs, rinv, status);
+    sweep_spd2(Ls, nv, nv, ck, cs, c1p, cs1, rinv, status);
     if (packed) {
         // upper triangle row by row: (a, b >= a) at a nv - a (a - 1) / 2 + b - a
         for (int a = warp; a < nv; a += nw) {
@@ -876,7 +980,7 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
         }
         __syncthreads();
     }
-    sweep_spd(Ss, np, np, ck, cs, rinv, status);
+    sweep_spd2(Ss, np, np, ck, cs, c1p, cs1, rinv, status);
     {
         const int tot = np * lds;
         for (int t = tid; t < tot; t += nt) {

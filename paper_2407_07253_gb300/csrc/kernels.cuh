@@ -186,11 +186,12 @@ __host__ __device__ inline long long saddle_scratch(int d, int n, int nv) {
 }
 constexpr long long SADDLE_SMEM_MAX_DOUBLES = 25600;   // 200 KB of shared memory
 // scratch of the factored-only inversion (one component's B^T and W at a
-// time, and one bit mask per pressure column of B^T: its nonzero rows)
+// time, the two-pivot sweep's columns, and one bit mask per pressure column
+// of B^T: its nonzero rows)
 __host__ __device__ inline long long saddle_scratch_factored(int d, int n, int nv) {
     const int np = n - d * nv, npp = np | 1;
     const int mx = nv > np ? nv : np;
-    return (long long)nv * nv + 2LL * nv * npp + (long long)np * np + 3LL * mx + 2 + (long long)np * ((nv + 63) / 64);
+    return (long long)nv * nv + 2LL * nv * npp + (long long)np * np + 7LL * mx + 2 + (long long)np * ((nv + 63) / 64);
 }
 // Outputs (each may be NULL): explicit inverses inv64 / inv32 (column-major,
 // leading dimension n rounded up to 2 / 4), the factored form fac64 / fac32

@@ -1545,7 +1545,9 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
                                                                     HL.patch_nv[p]));
                 scoff[p + 1] = scoff[p];
             }
-            else scoff[p + 1] = scoff[p] + sc;
+            else
+                scoff[p + 1] = scoff[p] + std::max(sc, skern::saddle_scratch_factored(
+                                                           HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p]));
         }
         l.saddle_global = scoff[l.npatch];
         l.scoff = hupload(h, scoff, s);
