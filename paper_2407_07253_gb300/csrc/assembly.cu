@@ -52,20 +52,26 @@ __global__ void k_cell_geometry(AsmMesh m, double* cg) {
 }
 
 // Warp-cooperative insertion of this lane's candidate into the list of
-// distinct values (first-appearance order).  Returns false on overflow.
-__device__ bool warp_insert(int* list, int* cnt, int cand, bool valid) {
+// distinct values (first-appearance order).  *where receives the candidate's
+// position in the list (-1 if !valid).  Returns false on overflow.
+__device__ bool warp_insert(int* list, int* cnt, int cand, bool valid, int* where) {
     const int lane = threadIdx.x & 31;
     const int n0 = *cnt;
     bool keep = valid;
+    int found = -1;
     if (keep)
         for (int t = 0; t < n0; ++t)
-            if (list[t] == cand) { keep = false; break; }
+            if (list[t] == cand) { keep = false; found = t; break; }
     const unsigned same = __match_any_sync(FULL, keep ? cand : INT_MIN + lane);
-    keep = keep && (lane == __ffs(same) - 1);
+    const int leader = __ffs(same) - 1;
+    keep = keep && (lane == leader);
     const unsigned km = __ballot_sync(FULL, keep);
     const int pos = n0 + __popc(km & ((1u << lane) - 1u));
     const bool ok = n0 + __popc(km) <= MAX_ROW;
     if (keep && ok) list[pos] = cand;
+    // a new value's position is its group leader's
+    const int lpos = __shfl_sync(FULL, pos, leader);
+    *where = !valid ? -1 : (found >= 0 ? found : lpos);
     __syncwarp();
     if (lane == 0) *cnt = ok ? n0 + __popc(km) : MAX_ROW + 1;
     __syncwarp();
@@ -73,9 +79,13 @@ __device__ bool warp_insert(int* list, int* cnt, int cand, bool valid) {
 }
 
 // neighbours of node `node` whose incident cells are adj[off[node] .. ):
-// free velocity nodes into lv, pressure nodes into lq (if lq != nullptr)
+// free velocity nodes into lv, pressure nodes into lq (if lq != nullptr).
+// With pv (pq) != nullptr, pv[c * nb + b] receives the list position of
+// velocity node b of incident cell c (-1: not free), pq likewise for the
+// pressure nodes; the caller passes them when every incident (cell, node)
+// pair fits in MAX_POS.
 __device__ bool neighbours(const AsmMesh& m, const int* off, const int* adj, int per_cell, int node, int* lv,
-                           int* cv, int* lq, int* cq) {
+                           int* cv, int* lq, int* cq, short* pv = nullptr, short* pq = nullptr) {
     const int lane = threadIdx.x & 31;
     const int c0 = off[node], ncell = off[node + 1] - c0;
     if (lane == 0) { *cv = 0; if (lq) *cq = 0; }
@@ -90,7 +100,9 @@ __device__ bool neighbours(const AsmMesh& m, const int* off, const int* adj, int
             cand = m.vcell[(long long)e * m.nb + t % m.nb];
             valid = m.vfree[cand] >= 0;
         }
-        if (!warp_insert(lv, cv, cand, valid)) return false;
+        int where;
+        if (!warp_insert(lv, cv, cand, valid, &where)) return false;
+        if (pv && t < tv) pv[t] = (short)where;
     }
     if (lq) {
         const int tq = ncell * m.nq;
@@ -103,7 +115,9 @@ __device__ bool neighbours(const AsmMesh& m, const int* off, const int* adj, int
                 cand = m.qcell[(long long)e * m.nq + t % m.nq];
                 valid = true;
             }
-            if (!warp_insert(lq, cq, cand, valid)) return false;
+            int where;
+            if (!warp_insert(lq, cq, cand, valid, &where)) return false;
+            if (pq && t < tq) pq[t] = (short)where;
         }
     }
     return true;
@@ -115,9 +129,14 @@ __device__ int find(const int* list, int n, int x) {
     return -1;
 }
 
+// incident (cell, node) pairs of one node whose list positions are kept
+// (rows with more use a search of the list)
+constexpr int MAX_POS = 256;
 struct WarpLists {
     int lv[MAX_ROW];
     int lq[MAX_ROW];
+    short pv[MAX_POS];
+    short pq[MAX_POS];
     int cv, cq;
 };
 
@@ -155,7 +174,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
     const int d = m.d, nb = m.nb, nq = m.nq;
     if (item < m.nVf) {
         const int node = m.vrow[item];
-        if (!neighbours(m, m.voff, m.vadj, nb, node, L.lv, &L.cv, L.lq, &L.cq)) {
+        const int ncell = m.voff[node + 1] - m.voff[node];
+        const bool map = ncell * nb <= MAX_POS && ncell * nq <= MAX_POS;
+        if (!neighbours(m, m.voff, m.vadj, nb, node, L.lv, &L.cv, L.lq, &L.cq, map ? L.pv : nullptr,
+                        map ? L.pq : nullptr)) {
             if (lane == 0) atomicExch(status, 1);
             return;
         }
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
         __syncwarp();
         const long long r00 = rp[item];
         for (int x = m.voff[node]; x < m.voff[node + 1]; ++x) {
-            const int e = m.vadj[x] / nb, la = m.vadj[x] % nb;
+            const int e = m.vadj[x] / nb, la = m.vadj[x] % nb, xl = x - m.voff[node];
             const double* G = m.cg + (long long)e * CG_STRIDE + 1;      // weighted stiffness factors
             const double* D = G + d * d;                                // divergence factors
             for (int b = lane; b < nb; b += 32) {
@@ -179,11 +201,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
                 double s = 0;
                 for (int a = 0; a < d; ++a)
                     for (int bb = 0; bb < d; ++bb) s += G[a * d + bb] * m.S[(((long long)a * d + bb) * nb + la) * nb + b];
-                val[r00 + find(L.lv, L.cv, j)] += s;
+                val[r00 + (map ? L.pv[xl * nb + b] : find(L.lv, L.cv, j))] += s;
             }
             for (int p = lane; p < nq; p += 32) {
                 const int q = m.qcell[(long long)e * nq + p];
-                const int pos = L.cv + find(L.lq, L.cq, q);
+                const int pos = L.cv + (map ? L.pq[xl * nq + p] : find(L.lq, L.cq, q));
                 for (int c = 0; c < d; ++c) {
                     double s = 0;
                     for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + p) * nb + la];
@@ -199,7 +221,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
         }
     } else if (item < m.nVf + m.nQ) {
         const int q = item - m.nVf;
-        if (!neighbours(m, m.qoff, m.qadj, nq, q, L.lv, &L.cv, nullptr, nullptr)) {
+        const int ncell = m.qoff[q + 1] - m.qoff[q];
+        const bool map = ncell * nb <= MAX_POS;
+        if (!neighbours(m, m.qoff, m.qadj, nq, q, L.lv, &L.cv, nullptr, nullptr, map ? L.pv : nullptr)) {
             if (lane == 0) atomicExch(status, 1);
             return;
         }
@@ -211,12 +235,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
             }
         __syncwarp();
         for (int x = m.qoff[q]; x < m.qoff[q + 1]; ++x) {
-            const int e = m.qadj[x] / nq, lp = m.qadj[x] % nq;
+            const int e = m.qadj[x] / nq, lp = m.qadj[x] % nq, xl = x - m.qoff[q];
             const double* D = m.cg + (long long)e * CG_STRIDE + 1 + d * d;
             for (int b = lane; b < nb; b += 32) {
                 const int j = m.vcell[(long long)e * nb + b];
                 if (m.vfree[j] < 0) continue;
-                const int pos = find(L.lv, L.cv, j);
+                const int pos = map ? L.pv[xl * nb + b] : find(L.lv, L.cv, j);
                 for (int c = 0; c < d; ++c) {
                     double s = 0;
                     for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + b];
