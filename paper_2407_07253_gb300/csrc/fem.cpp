@@ -16,6 +16,7 @@
 #include <map>
 #include <numeric>
 #include <stdexcept>
+#include <exception>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -31,6 +32,10 @@ int num_threads() {
     return n;
 }
 
+// set on a thread that must not use the shared pool (the coarsest level's
+// builder): its parallel loops run inline
+thread_local bool t_pool_inline = false;
+
 // Persistent worker pool: parallel_for splits [0, n) into one contiguous,
 // ordered chunk per worker (the caller runs chunk 0).
 class Pool {
@@ -41,7 +46,7 @@ class Pool {
     }
     int size() const { return (int)workers_.size() + 1; }
     void run(int chunks, const std::function<void(int)>& job) {
-        if (chunks <= 1 || workers_.empty()) {
+        if (chunks <= 1 || workers_.empty() || t_pool_inline) {
             for (int c = 0; c < chunks; ++c) job(c);
             return;
         }
@@ -1432,15 +1437,10 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
     static std::mutex ref_mu;
     static std::map<std::pair<int, int>, RefTensors> tensors;
     auto ref = [&](int dd, int kk) -> const RefElement& { return reference_element(dd, kk); };
-    std::vector<size_t> order;
-    if (spec.coarsest_first && spec.finest_before_coarsest && ls.size() > 1) order.push_back(0);
-    if (spec.coarsest_first) order.push_back(ls.size() - 1);
-    for (size_t l = 0; l < ls.size(); ++l) {
-        if (spec.coarsest_first && l + 1 == ls.size()) continue;
-        if (spec.coarsest_first && spec.finest_before_coarsest && l == 0) continue;
-        order.push_back(l);
-    }
-    for (size_t l : order) {
+    // one level: spaces, operator data (or host matrices), callback stage 0,
+    // patches, callback stage 1; the phase times merge under tmu
+    std::mutex tmu;
+    auto build_one = [&](size_t l) {
         Level& L = H.levels[l];
         L.d = d;
         L.family = ls[l].family;
@@ -1472,24 +1472,56 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         if (L.host_matrices) assemble_level(m, L, RT, nus[L.mesh_index], l == 0);
         else prepare_level(m, L, RT);
         double tc = now_ms();
+        double t_cb = 0;
         if (on_level) {
             on_level((int)l, 0);
             const double tcb = now_ms();
-            H.t_callbacks_ms += tcb - tc;
+            t_cb += tcb - tc;
             tc = tcb;
         }
         if (l + 1 < ls.size() && !spec.skip_patches) build_patches(m, topo[L.mesh_index], L);
+        const double td = now_ms();
+        if (host_trace())
+            std::fprintf(stderr, "[sfem] level %zu: spaces %.3f  operator data %.3f  patches %.3f ms\n", l, tb - ta,
+                         tc - tb, td - tc);
+        if (on_level) {
+            on_level((int)l, 1);
+            t_cb += now_ms() - td;
+        }
+        std::lock_guard<std::mutex> g(tmu);
         H.t_spaces_ms += tb - ta;
         H.t_matrices_ms += tc - tb;
-        H.t_patches_ms += now_ms() - tc;
-        if (const char* tr = std::getenv("STOKES_TRACE"); tr && tr[0] == '1')
-            std::fprintf(stderr, "[sfem] level %zu: spaces %.3f  operator data %.3f  patches %.3f ms\n", l, tb - ta,
-                         tc - tb, now_ms() - tc);
-        if (on_level) {
-            const double tcb = now_ms();
-            on_level((int)l, 1);
-            H.t_callbacks_ms += now_ms() - tcb;
-        }
+        H.t_patches_ms += td - tc;
+        H.t_callbacks_ms += t_cb;
+    };
+    std::vector<size_t> order;
+    const bool side = spec.coarsest_first && spec.coarsest_thread && ls.size() > 1;
+    if (spec.coarsest_first && !side) order.push_back(ls.size() - 1);
+    for (size_t l = 0; l + 1 < ls.size(); ++l) order.push_back(l);
+    if (!spec.coarsest_first) order.push_back(ls.size() - 1);
+    {
+        // the coarsest level beside the others (joined before this scope
+        // ends, also when a level throws)
+        std::exception_ptr side_err;
+        std::thread th;
+        if (side)
+            th = std::thread([&] {
+                t_pool_inline = true;
+                try {
+                    build_one(ls.size() - 1);
+                } catch (...) {
+                    side_err = std::current_exception();
+                }
+            });
+        struct Join {
+            std::thread& t;
+            ~Join() {
+                if (t.joinable()) t.join();
+            }
+        } join{th};
+        for (size_t l : order) build_one(l);
+        if (th.joinable()) th.join();
+        if (side_err) std::rethrow_exception(side_err);
     }
     double tt = now_ms();
     for (size_t l = 0; l + 1 < ls.size() && !spec.device_transfers; ++l) {

@@ -122,9 +122,11 @@ struct HierarchySpec {
     // is a long chain of small steps that then runs while the host builds the
     // other levels), then finest to coarsest
     bool coarsest_first = false;
-    // with coarsest_first: the finest level before the coarsest one (the
-    // finest level's inversion is then the first device work), then the rest
-    bool finest_before_coarsest = false;
+    // with coarsest_first: the coarsest level is built on a host thread of
+    // its own (its loops run inline there, off the shared pool) while this
+    // thread builds the others, finest to coarsest; the per-level callbacks
+    // then come from two threads and must be thread-safe
+    bool coarsest_thread = false;
     bool skip_patches = false;                // no Vanka patches (a hierarchy wanted for its operators)
     bool device_assembly_finest_only = false; // with device_assembly: only level 0 on the device
     bool device_transfers = false;            // leave P and R to the device (no host transfers)

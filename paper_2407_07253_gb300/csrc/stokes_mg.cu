@@ -2473,11 +2473,14 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         spec.barycentric = barycentric_finest != 0;
         spec.device_assembly = !o.host_only;
         spec.coarsest_first = !o.host_only;
+        // the coarsest level's host work beside level 0's, on a thread of its
+        // own (the callbacks below are serialised by cb_mu)
+        spec.coarsest_thread = !o.host_only;
         spec.device_transfers = !o.host_only && !fbf_mode;
-        // (finest_before_coarsest stays off: with the level-0 inversion
-        // already filling the GPU, the coarse factorisation's chain of
-        // launches took 5.7 ms and ended after level 0's lambda_max; started
-        // first it ends well before)
+        // (building level 0 before the coarsest level on one thread was
+        // slower: with the level-0 inversion already filling the GPU, the
+        // coarse factorisation's chain of launches took 5.7 ms and ended
+        // after level 0's lambda_max; started first it ends well before)
         if (o.hierarchy == STOKES_HIER_DIRECT) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
         else if (o.hierarchy == STOKES_HIER_GRADUAL) {
             if (k <= 5) spec.schedule = k > 2 ? std::vector<int>{k, 2} : std::vector<int>{2};
@@ -2500,6 +2503,7 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
         std::unique_ptr<Launcher> launcher;
         double t_launch = 0;
         std::function<void(int, int)> on_level;
+        std::mutex cb_mu;                  // the callbacks come from two host threads
         if (!o.host_only) {
             // level-by-level pipeline: upload on s_up, then the patch
             // inversion (or the coarse factorisation) starts on the device
@@ -2552,6 +2556,7 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                 });
             };
             on_level = [&](int li, int stage) {
+                std::lock_guard<std::mutex> cb_guard(cb_mu);
                 const double tu = host_ms();
                 stokes_mg* hp = h.get();
                 const int nlv = (int)hp->H.levels.size();
