@@ -2559,6 +2559,7 @@ int setup_impl(const stokes_mesh* coarse, int n_refine, int barycentric_finest, 
                 std::lock_guard<std::mutex> cb_guard(cb_mu);
                 const double tu = host_ms();
                 stokes_mg* hp = h.get();
+                CK(cudaSetDevice(hp->device));    // the callback may run on a helper thread
                 const int nlv = (int)hp->H.levels.size();
                 if ((int)hp->L.size() != nlv) {
                     hp->L.assign(nlv, DevLevel());
