@@ -37,7 +37,14 @@ int num_threads() {
 thread_local bool t_pool_inline = false;
 
 // Persistent worker pool: parallel_for splits [0, n) into one contiguous,
-// ordered chunk per worker (the caller runs chunk 0).
+// ordered chunk per worker (the caller runs chunk 0).  A job is published
+// under the mutex with a new generation; workers that spin on the
+// generation (bounded, yielding, then asleep on the condition variable)
+// register for it under the mutex, so they read its fields consistently, and
+// claim chunks with an atomic counter.  The caller retires the job under the
+// mutex once every chunk is done and waits for the registered workers to
+// leave it, so no worker touches a finished job.  (The wake through the
+// condition variable alone cost tens of microseconds per parallel loop.)
 class Pool {
   public:
     static Pool& get() {
@@ -50,32 +57,34 @@ class Pool {
             for (int c = 0; c < chunks; ++c) job(c);
             return;
         }
-        std::unique_lock<std::mutex> lk(m_);
-        job_ = &job;
-        chunks_ = chunks;
-        next_ = 1;
-        pending_ = chunks - 1;
-        ++gen_;
-        cv_.notify_all();
-        lk.unlock();
-        job(0);
-        lk.lock();
-        // help with remaining chunks, then wait for the workers
-        while (next_ < chunks_) {
-            int c = next_++;
-            lk.unlock();
-            job(c);
-            lk.lock();
-            --pending_;
+        std::lock_guard<std::mutex> serial(run_mu_);     // one job at a time
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            job_ = &job;
+            chunks_ = chunks;
+            next_.store(1, std::memory_order_relaxed);
+            done_.store(0, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_release);
         }
-        done_.wait(lk, [&] { return pending_ == 0; });
-        job_ = nullptr;
+        if (sleepers_.load(std::memory_order_acquire) > 0) cv_.notify_all();
+        run_chunk(job, 0);
+        for (int c; (c = next_.fetch_add(1, std::memory_order_acq_rel)) < chunks;) run_chunk(job, c);
+        while (done_.load(std::memory_order_acquire) < chunks) std::this_thread::yield();
+        std::exception_ptr err;
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            job_ = nullptr;
+            err = err_;
+            err_ = nullptr;
+        }
+        while (active_.load(std::memory_order_acquire) > 0) std::this_thread::yield();
+        if (err) std::rethrow_exception(err);
     }
     ~Pool() {
         {
             std::lock_guard<std::mutex> lk(m_);
-            stop_ = true;
-            ++gen_;
+            stop_.store(true, std::memory_order_release);
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         for (auto& t : workers_) t.join();
@@ -85,30 +94,68 @@ class Pool {
     explicit Pool(int n) {
         for (int i = 1; i < n; ++i) workers_.emplace_back([this] { loop(); });
     }
+    // one chunk; its exception (the first) is kept for the caller, and the
+    // chunk still counts as done so that the job completes.  A parallel loop
+    // nested inside a chunk runs inline (the pool runs one job at a time).
+    void run_chunk(const std::function<void(int)>& job, int c) {
+        const bool was_inline = t_pool_inline;
+        t_pool_inline = true;
+        try {
+            job(c);
+        } catch (...) {
+            std::lock_guard<std::mutex> lk(m_);
+            if (!err_) err_ = std::current_exception();
+        }
+        t_pool_inline = was_inline;
+        done_.fetch_add(1, std::memory_order_acq_rel);
+    }
     void loop() {
         unsigned seen = 0;
-        std::unique_lock<std::mutex> lk(m_);
         for (;;) {
-            cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
-            if (stop_) return;
-            seen = gen_;
-            while (job_ && next_ < chunks_) {
-                int c = next_++;
-                const std::function<void(int)>* j = job_;
-                lk.unlock();
-                (*j)(c);
-                lk.lock();
-                if (--pending_ == 0) done_.notify_all();
+            // wait for a new generation: spin (yielding) for about kSpinUs,
+            // then sleep on the condition variable
+            auto t0 = std::chrono::steady_clock::now();
+            for (int spin = 0; gen_.load(std::memory_order_acquire) == seen; ++spin) {
+                if (stop_.load(std::memory_order_acquire)) return;
+                if ((spin & 63) != 63 ||
+                    std::chrono::steady_clock::now() - t0 < std::chrono::microseconds(kSpinUs)) {
+                    std::this_thread::yield();
+                    continue;
+                }
+                std::unique_lock<std::mutex> lk(m_);
+                sleepers_.fetch_add(1, std::memory_order_acq_rel);
+                cv_.wait(lk, [&] {
+                    return gen_.load(std::memory_order_acquire) != seen || stop_.load(std::memory_order_acquire);
+                });
+                sleepers_.fetch_sub(1, std::memory_order_acq_rel);
+                spin = 0;
+                t0 = std::chrono::steady_clock::now();
             }
+            const std::function<void(int)>* j = nullptr;
+            int ch = 0;
+            {
+                std::lock_guard<std::mutex> lk(m_);
+                if (stop_.load(std::memory_order_acquire)) return;
+                seen = gen_.load(std::memory_order_acquire);
+                if (!job_) continue;                         // already retired
+                j = job_;
+                ch = chunks_;
+                active_.fetch_add(1, std::memory_order_acq_rel);
+            }
+            for (int c; (c = next_.fetch_add(1, std::memory_order_acq_rel)) < ch;) run_chunk(*j, c);
+            active_.fetch_sub(1, std::memory_order_acq_rel);
         }
     }
+    static constexpr int kSpinUs = 300;                       // spin before sleeping
     std::vector<std::thread> workers_;
-    std::mutex m_;
-    std::condition_variable cv_, done_;
-    const std::function<void(int)>* job_ = nullptr;
-    int chunks_ = 0, next_ = 0, pending_ = 0;
-    unsigned gen_ = 0;
-    bool stop_ = false;
+    std::mutex m_, run_mu_;
+    std::condition_variable cv_;
+    const std::function<void(int)>* job_ = nullptr;          // guarded by m_
+    std::exception_ptr err_;                                  // guarded by m_
+    int chunks_ = 0;                                          // guarded by m_
+    std::atomic<int> next_{0}, done_{0}, active_{0}, sleepers_{0};
+    std::atomic<unsigned> gen_{0};
+    std::atomic<bool> stop_{false};
 };
 
 // chunks for n items of at least `grain` items each (1 = run inline: waking
