@@ -476,9 +476,9 @@ int stokes_prof_read_one(stokes_mg_t h, int kind, long long index, double* ms);
  * fixed array of about 7 MB in this library's device memory, held by every
  * GPU that loads the library until the process exits.  The first call on a
  * device does a one-time set-up: it looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture begins.  Every call shares the one array and it
- * keeps the last call's contents (the pivot status is cleared by each call):
+ * (cudaGetSymbolAddress) with the device current.  Every call shares the
+ * one array and it keeps the last call's contents (the pivot status is
+ * cleared by each call):
  * GPU work of two calls that overlapped would race on it.  Within one process
  * the entry point prevents that itself: a process-wide lock is held from the
  * staging of the offsets (in static host arrays) until `stream` has drained,
