@@ -54,7 +54,7 @@ __global__ void k_cell_geometry(AsmMesh m, double* cg) {
 // Warp-cooperative insertion of this lane's candidate into the list of
 // distinct values (first-appearance order).  *where receives the candidate's
 // position in the list (-1 if !valid).  Returns false on overflow.
-__device__ bool warp_insert(int* list, int* cnt, int cand, bool valid, int* where) {
+__device__ bool warp_insert(int* list, int* cnt, int cap, int cand, bool valid, int* where) {
     const int lane = threadIdx.x & 31;
     const int n0 = *cnt;
     bool keep = valid;
@@ -67,13 +67,13 @@ __device__ bool warp_insert(int* list, int* cnt, int cand, bool valid, int* wher
     keep = keep && (lane == leader);
     const unsigned km = __ballot_sync(FULL, keep);
     const int pos = n0 + __popc(km & ((1u << lane) - 1u));
-    const bool ok = n0 + __popc(km) <= MAX_ROW;
+    const bool ok = n0 + __popc(km) <= cap;
     if (keep && ok) list[pos] = cand;
     // a new value's position is its group leader's
     const int lpos = __shfl_sync(FULL, pos, leader);
     *where = !valid ? -1 : (found >= 0 ? found : lpos);
     __syncwarp();
-    if (lane == 0) *cnt = ok ? n0 + __popc(km) : MAX_ROW + 1;
+    if (lane == 0) *cnt = ok ? n0 + __popc(km) : cap + 1;
     __syncwarp();
     return ok;
 }
@@ -101,7 +101,7 @@ __device__ bool neighbours(const AsmMesh& m, const int* off, const int* adj, int
             valid = m.vfree[cand] >= 0;
         }
         int where;
-        if (!warp_insert(lv, cv, cand, valid, &where)) return false;
+        if (!warp_insert(lv, cv, m.cap_v, cand, valid, &where)) return false;
         if (pv && t < tv) pv[t] = (short)where;
     }
     if (lq) {
@@ -116,7 +116,7 @@ __device__ bool neighbours(const AsmMesh& m, const int* off, const int* adj, int
                 valid = true;
             }
             int where;
-            if (!warp_insert(lq, cq, cand, valid, &where)) return false;
+            if (!warp_insert(lq, cq, m.cap_q, cand, valid, &where)) return false;
             if (pq && t < tq) pq[t] = (short)where;
         }
     }
@@ -132,34 +132,58 @@ __device__ int find(const int* list, int n, int x) {
 // incident (cell, node) pairs of one node whose list positions are kept
 // (rows with more use a search of the list)
 constexpr int MAX_POS = 256;
+
+// One warp's lists in dynamic shared memory: the two counts, the velocity
+// and pressure neighbour lists (cap_v, cap_q entries) and the position maps
+// (min(cap, MAX_POS) entries each), 16-byte aligned per warp.
 struct WarpLists {
-    int lv[MAX_ROW];
-    int lq[MAX_ROW];
-    short pv[MAX_POS];
-    short pq[MAX_POS];
-    int cv, cq;
+    int* lv;
+    int* lq;
+    short* pv;
+    short* pq;
+    int* cv;
+    int* cq;
+    int npv, npq;                      // entries of pv, pq
 };
+__host__ __device__ inline size_t warp_list_bytes(int cap_v, int cap_q) {
+    const int npv = cap_v < MAX_POS ? cap_v : MAX_POS, npq = cap_q < MAX_POS ? cap_q : MAX_POS;
+    const size_t b = 8 + 4 * (size_t)(cap_v + cap_q) + 2 * (size_t)(npv + npq);
+    return (b + 15) & ~(size_t)15;
+}
+__device__ WarpLists warp_lists(const AsmMesh& m, int w) {
+    extern __shared__ int4 asm_smem[];
+    char* p = reinterpret_cast<char*>(asm_smem) + (size_t)w * warp_list_bytes(m.cap_v, m.cap_q);
+    WarpLists L;
+    L.npv = m.cap_v < MAX_POS ? m.cap_v : MAX_POS;
+    L.npq = m.cap_q < MAX_POS ? m.cap_q : MAX_POS;
+    L.cv = reinterpret_cast<int*>(p);
+    L.cq = L.cv + 1;
+    L.lv = L.cv + 2;
+    L.lq = L.lv + m.cap_v;
+    L.pv = reinterpret_cast<short*>(L.lq + m.cap_q);
+    L.pq = L.pv + L.npv;
+    return L;
+}
 
 __global__ void __launch_bounds__(WARPS * 32) k_row_lengths(AsmMesh m, int* len, int* status) {
-    __shared__ WarpLists W[WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WARPS + w;
-    WarpLists& L = W[w];
+    const WarpLists L = warp_lists(m, w);
     if (item < m.nVf) {
         const int node = m.vrow[item];
-        if (!neighbours(m, m.voff, m.vadj, m.nb, node, L.lv, &L.cv, L.lq, &L.cq)) {
+        if (!neighbours(m, m.voff, m.vadj, m.nb, node, L.lv, L.cv, L.lq, L.cq)) {
             if (lane == 0) atomicExch(status, 1);
             return;
         }
         if (lane == 0)
-            for (int c = 0; c < m.d; ++c) len[c * m.nVf + item] = L.cv + L.cq;
+            for (int c = 0; c < m.d; ++c) len[c * m.nVf + item] = *L.cv + *L.cq;
     } else if (item < m.nVf + m.nQ) {
         const int q = item - m.nVf;
-        if (!neighbours(m, m.qoff, m.qadj, m.nq, q, L.lv, &L.cv, nullptr, nullptr)) {
+        if (!neighbours(m, m.qoff, m.qadj, m.nq, q, L.lv, L.cv, nullptr, nullptr)) {
             if (lane == 0) atomicExch(status, 1);
             return;
         }
-        if (lane == 0) len[m.d * m.nVf + q] = m.d * L.cv;
+        if (lane == 0) len[m.d * m.nVf + q] = m.d * *L.cv;
     }
 }
 
@@ -167,26 +191,26 @@ __global__ void __launch_bounds__(WARPS * 32) k_row_lengths(AsmMesh m, int* len,
 // rows, lanes of one cell touch distinct positions, and __syncwarp orders the
 // cells, so the sums are deterministic without atomics.
 __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, int* ci, double* val, int* status) {
-    __shared__ WarpLists W[WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.x * WARPS + w;
-    WarpLists& L = W[w];
+    const WarpLists L = warp_lists(m, w);
     const int d = m.d, nb = m.nb, nq = m.nq;
     if (item < m.nVf) {
         const int node = m.vrow[item];
         const int ncell = m.voff[node + 1] - m.voff[node];
-        const bool map = ncell * nb <= MAX_POS && ncell * nq <= MAX_POS;
-        if (!neighbours(m, m.voff, m.vadj, nb, node, L.lv, &L.cv, L.lq, &L.cq, map ? L.pv : nullptr,
+        const bool map = ncell * nb <= L.npv && ncell * nq <= L.npq;
+        if (!neighbours(m, m.voff, m.vadj, nb, node, L.lv, L.cv, L.lq, L.cq, map ? L.pv : nullptr,
                         map ? L.pq : nullptr)) {
             if (lane == 0) atomicExch(status, 1);
             return;
         }
-        const int len = L.cv + L.cq;
+        const int cv = *L.cv, cq = *L.cq;
+        const int len = cv + cq;
         for (int c = 0; c < d; ++c) {
             const long long r0 = rp[c * m.nVf + item];
             for (int t = lane; t < len; t += 32) {
                 val[r0 + t] = 0.0;
-                ci[r0 + t] = t < L.cv ? c * m.nVf + m.vfree[L.lv[t]] : d * m.nVf + L.lq[t - L.cv];
+                ci[r0 + t] = t < cv ? c * m.nVf + m.vfree[L.lv[t]] : d * m.nVf + L.lq[t - cv];
             }
         }
         __syncwarp();
@@ -201,11 +225,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
                 double s = 0;
                 for (int a = 0; a < d; ++a)
                     for (int bb = 0; bb < d; ++bb) s += G[a * d + bb] * m.S[(((long long)a * d + bb) * nb + la) * nb + b];
-                val[r00 + (map ? L.pv[xl * nb + b] : find(L.lv, L.cv, j))] += s;
+                val[r00 + (map ? L.pv[xl * nb + b] : find(L.lv, cv, j))] += s;
             }
             for (int p = lane; p < nq; p += 32) {
                 const int q = m.qcell[(long long)e * nq + p];
-                const int pos = L.cv + (map ? L.pq[xl * nq + p] : find(L.lq, L.cq, q));
+                const int pos = cv + (map ? L.pq[xl * nq + p] : find(L.lq, cq, q));
                 for (int c = 0; c < d; ++c) {
                     double s = 0;
                     for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + p) * nb + la];
@@ -217,21 +241,22 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
         // the velocity block is the same for every component
         for (int c = 1; c < d; ++c) {
             const long long r0 = rp[c * m.nVf + item];
-            for (int t = lane; t < L.cv; t += 32) val[r0 + t] = val[r00 + t];
+            for (int t = lane; t < cv; t += 32) val[r0 + t] = val[r00 + t];
         }
     } else if (item < m.nVf + m.nQ) {
         const int q = item - m.nVf;
         const int ncell = m.qoff[q + 1] - m.qoff[q];
-        const bool map = ncell * nb <= MAX_POS;
-        if (!neighbours(m, m.qoff, m.qadj, nq, q, L.lv, &L.cv, nullptr, nullptr, map ? L.pv : nullptr)) {
+        const bool map = ncell * nb <= L.npv;
+        if (!neighbours(m, m.qoff, m.qadj, nq, q, L.lv, L.cv, nullptr, nullptr, map ? L.pv : nullptr)) {
             if (lane == 0) atomicExch(status, 1);
             return;
         }
+        const int cv = *L.cv;
         const long long r0 = rp[d * m.nVf + q];
         for (int c = 0; c < d; ++c)
-            for (int t = lane; t < L.cv; t += 32) {
-                ci[r0 + (long long)c * L.cv + t] = c * m.nVf + m.vfree[L.lv[t]];
-                val[r0 + (long long)c * L.cv + t] = 0.0;
+            for (int t = lane; t < cv; t += 32) {
+                ci[r0 + (long long)c * cv + t] = c * m.nVf + m.vfree[L.lv[t]];
+                val[r0 + (long long)c * cv + t] = 0.0;
             }
         __syncwarp();
         for (int x = m.qoff[q]; x < m.qoff[q + 1]; ++x) {
@@ -240,11 +265,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_fill(AsmMesh m, const int* rp, i
             for (int b = lane; b < nb; b += 32) {
                 const int j = m.vcell[(long long)e * nb + b];
                 if (m.vfree[j] < 0) continue;
-                const int pos = map ? L.pv[xl * nb + b] : find(L.lv, L.cv, j);
+                const int pos = map ? L.pv[xl * nb + b] : find(L.lv, cv, j);
                 for (int c = 0; c < d; ++c) {
                     double s = 0;
                     for (int a = 0; a < d; ++a) s += D[a * d + c] * m.Cq[((long long)a * nq + lp) * nb + b];
-                    val[r0 + (long long)c * L.cv + pos] += s;
+                    val[r0 + (long long)c * cv + pos] += s;
                 }
             }
             __syncwarp();
@@ -617,9 +642,17 @@ void cell_geometry(const AsmMesh& m, double* cg, cudaStream_t s) {
     k_cell_geometry<<<(m.nc + 127) / 128, 128, 0, s>>>(m, cg);
 }
 
+void set_list_caps(AsmMesh& m, int max_cells) {
+    const long long cv = max_cells > 0 ? (long long)max_cells * m.nb : MAX_ROW;
+    const long long cq = max_cells > 0 ? (long long)max_cells * m.nq : MAX_ROW;
+    m.cap_v = (int)std::min<long long>(std::max<long long>(cv, 1), MAX_ROW);
+    m.cap_q = (int)std::min<long long>(std::max<long long>(cq, 1), MAX_ROW);
+}
+
 void row_lengths(const AsmMesh& m, int* len, int* status, cudaStream_t s) {
     const int items = m.nVf + m.nQ;
-    k_row_lengths<<<(items + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(m, len, status);
+    k_row_lengths<<<(items + WARPS - 1) / WARPS, WARPS * 32, WARPS * warp_list_bytes(m.cap_v, m.cap_q), s>>>(
+        m, len, status);
 }
 
 void scan_rows(const int* len, int n, int* rp, int* tmp, cudaStream_t s) {
@@ -670,7 +703,8 @@ void node_cells(const int* cell_nodes, long long m, int n, int* off, int* adj, i
 
 void fill_rows(const AsmMesh& m, const int* rp, int* ci, double* v, int* status, cudaStream_t s) {
     const int items = m.nVf + m.nQ;
-    k_fill<<<(items + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(m, rp, ci, v, status);
+    k_fill<<<(items + WARPS - 1) / WARPS, WARPS * 32, WARPS * warp_list_bytes(m.cap_v, m.cap_q), s>>>(
+        m, rp, ci, v, status);
 }
 
 void load_vector(const AsmMesh& m, const double* f, const double* g, double inv_nu, double* b, cudaStream_t s) {

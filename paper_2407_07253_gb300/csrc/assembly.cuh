@@ -30,6 +30,8 @@ struct AsmMesh {
     const double* Cq;                  // [d][nq][nb] int psi_p d(phi_j)/dxi_a
     const double* M;                   // [nb][nb] reference mass matrix
     const double* cg;                  // [nc][CG_STRIDE] per-cell factors (cell_geometry)
+    int cap_v, cap_q;                  // list capacity per node (velocity / pressure neighbours):
+                                       // set by set_list_caps
 };
 
 // Per-cell factors of the affine map x = x_0 + J xi, computed once per level:
@@ -40,6 +42,12 @@ constexpr int CG_STRIDE = 20;
 void cell_geometry(const AsmMesh& m, double* cg, cudaStream_t s);
 
 constexpr int MAX_ROW = 1024;          // neighbours of one node (per kind)
+
+// List capacities for row_lengths / fill_rows: a node in at most max_cells
+// cells has at most max_cells * nb velocity and max_cells * nq pressure
+// neighbours (capped at MAX_ROW; max_cells <= 0: MAX_ROW).  A row that does
+// not fit sets the status word.
+void set_list_caps(AsmMesh& m, int max_cells);
 
 // Pass 1: row lengths.  len[r] for r < d*nVf + nQ.
 void row_lengths(const AsmMesh& m, int* len, int* status, cudaStream_t s);

@@ -192,7 +192,7 @@ struct FlatLists {
 };
 
 template <class F>
-static FlatLists build_lists(int n, F&& fill) {
+static FlatLists build_lists(int n, F&& fill, int per_item = 32) {
     const int T = chunk_count(n);
     std::vector<std::vector<int>> buf(T);
     FlatLists L;
@@ -201,7 +201,7 @@ static FlatLists build_lists(int n, F&& fill) {
     for (int t = 0; t <= T; ++t) lo[t] = (int)((long long)n * t / T);
     Pool::get().run(T, [&](int t) {
         std::vector<int>& b = buf[t];
-        b.reserve((size_t)(lo[t + 1] - lo[t]) * 32);
+        b.reserve((size_t)(lo[t + 1] - lo[t]) * per_item);
         for (int i = lo[t]; i < lo[t + 1]; ++i) {
             size_t before = b.size();
             fill(i, b, t);
@@ -215,6 +215,43 @@ static FlatLists build_lists(int n, F&& fill) {
             if (!buf[t].empty()) std::memcpy(L.data.data() + L.off[lo[t]], buf[t].data(), buf[t].size() * sizeof(int));
     });
     return L;
+}
+
+// Sort out[s0..) and drop repeated values, in place.  A list whose values
+// span a narrow range (a vertex star: its nodes are numbered close together)
+// is marked in a bit map of that range, which is then read back in order;
+// a list over a wide range is sorted.  The bit map is per thread and all
+// zero between calls.
+static void sort_unique_tail(std::vector<int>& out, size_t s0) {
+    thread_local std::vector<uint64_t> bits;
+    const size_t n = out.size() - s0;
+    if (n <= 1) return;
+    int lo = out[s0], hi = out[s0];
+    for (size_t i = s0 + 1; i < out.size(); ++i) {
+        lo = std::min(lo, out[i]);
+        hi = std::max(hi, out[i]);
+    }
+    const long long words = (((long long)hi - lo) >> 6) + 1;
+    if (words > 8 * (long long)n + 64) {
+        std::sort(out.begin() + s0, out.end());
+        out.erase(std::unique(out.begin() + s0, out.end()), out.end());
+        return;
+    }
+    if ((long long)bits.size() < words) bits.resize((size_t)words, 0);
+    for (size_t i = s0; i < out.size(); ++i) {
+        const unsigned r = (unsigned)(out[i] - lo);
+        bits[r >> 6] |= 1ull << (r & 63);
+    }
+    size_t w = s0;
+    for (long long k = 0; k < words; ++k) {
+        uint64_t b = bits[k];
+        bits[k] = 0;
+        while (b) {
+            out[w++] = lo + (int)(k << 6) + __builtin_ctzll(b);
+            b &= b - 1;
+        }
+    }
+    out.resize(w);
 }
 
 // Parallel exclusive scan of cnt[0..n) into out[0..n] (out[n] = total).
@@ -568,6 +605,7 @@ struct Topology {
     std::vector<int> cell_face;             // [nc][4] (3D): face opposite local vertex i
     std::vector<unsigned char> bvert, bedge, bface;   // on the boundary, by vertex / edge / face id
     std::vector<int> v2c_off, v2c;          // vertex -> cells
+    int max_valence = 0;                    // most cells around one vertex
 };
 
 // local vertex pairs of the edges of a simplex (2D uses the first three
@@ -594,7 +632,11 @@ static void build_topology(const Mesh& m, Topology& T) {
     // vertex -> cells (cells in increasing index)
     T.v2c_off.assign(m.nv + 1, 0);
     for (int x : m.C) T.v2c_off[x + 1]++;
-    for (int i = 0; i < m.nv; ++i) T.v2c_off[i + 1] += T.v2c_off[i];
+    T.max_valence = 0;
+    for (int i = 0; i < m.nv; ++i) {
+        T.max_valence = std::max(T.max_valence, T.v2c_off[i + 1]);
+        T.v2c_off[i + 1] += T.v2c_off[i];
+    }
     T.v2c.resize(m.C.size());
     {
         std::vector<int> fill(T.v2c_off.begin(), T.v2c_off.end() - 1);
@@ -1235,8 +1277,7 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
                 if (L.vfree[j] >= 0) out.push_back(L.vfree[j]);
             }
         }
-        std::sort(out.begin() + s0, out.end());
-        out.erase(std::unique(out.begin() + s0, out.end()), out.end());
+        sort_unique_tail(out, s0);
         const size_t s1 = out.size();
         for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
             const int e = T.v2c[a];
@@ -1251,11 +1292,10 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
                 out.push_back(q);
             }
         }
-        std::sort(out.begin() + s1, out.end());
-        out.erase(std::unique(out.begin() + s1, out.end()), out.end());
+        sort_unique_tail(out, s1);
         NV[v] = (int)(s1 - s0);
         NP[v] = (int)(out.size() - s1);
-    });
+    }, 192);
     pc.lap("star lists");
     // vertices with a non-empty patch, in order; patch p lists d blocks of its
     // velocity nodes (one per component), then its pressures
@@ -1499,6 +1539,7 @@ void build_hierarchy(const Mesh& coarse, const HierarchySpec& spec, const double
         const Mesh& m = H.meshes[L.mesh_index];
         double ta = now_ms();
         need_topo(L.mesh_index);
+        L.max_cells = topo[L.mesh_index].max_valence;
         const RefElement& rv = ref(d, L.k);
         const RefElement& rq = ref(d, L.k - 1);
         build_space(m, topo[L.mesh_index], rv, true, L.V);

@@ -106,6 +106,8 @@ struct Level {
     // what a device assembly needs: node -> (cell * nb + local) adjacency,
     // the reference tensors and the cell viscosities
     std::vector<int> voff, vadj, qoff, qadj;
+    int max_cells = 0;                        // most cells around one vertex of the mesh: no
+                                              // node lies in more cells than that
     RefTensors RT;
     std::vector<double> nu_cells;
     bool host_matrices = true;                // K (and on level 0 Mv, KfD) assembled here

@@ -1702,6 +1702,7 @@ void upload_assembly_inputs_lv(stokes_mg* h, const sfem::Level& HL, DevLevel& l,
     a.M = hupload(h, HL.RT.M, s);
     l.cellgeo = halloc<double>(h, (size_t)mesh.nc * sasm::CG_STRIDE);
     a.cg = l.cellgeo;
+    sasm::set_list_caps(a, HL.max_cells);
     // entries: a velocity row of a node in c cells has at most c (nb + nq),
     // a pressure row at most d c nb; the incidences sum to nc nb and nc nq
     const long long bound = (long long)HL.d * mesh.nc * a.nb * (a.nb + a.nq) + (long long)HL.d * mesh.nc * a.nq * a.nb;
