@@ -1268,29 +1268,35 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
     // pressure nodes of its star (TH: nodes whose entity has the vertex in
     // its closure) or of those cells (SV), each group sorted and unique
     std::vector<int> NV(m.nv, 0), NP(m.nv, 0);
+    // TH: lattice node l of a cell lies on an entity that contains the cell's
+    // local vertex i iff its barycentric index alpha_l[i] is positive; SV:
+    // every pressure node of the cell belongs to the star
+    const int nvpc = d + 1;
+    std::vector<unsigned char> in_star((size_t)nvpc * nq, 1);
+    if (L.family == 0) {
+        const RefElement& rq = reference_element(d, L.Q.k);
+        for (int i = 0; i < nvpc; ++i)
+            for (int l = 0; l < nq; ++l) in_star[(size_t)i * nq + l] = rq.alpha[l][i] > 0;
+    }
     FlatLists lists = build_lists(m.nv, [&](int v, std::vector<int>& out, int) {
         const size_t s0 = out.size();
         for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
-            const int e = T.v2c[a];
+            const int* cn = &L.V.cell_nodes[(size_t)T.v2c[a] * nb];
             for (int l = 0; l < nb; ++l) {
-                const int j = L.V.cell_nodes[(size_t)e * nb + l];
-                if (L.vfree[j] >= 0) out.push_back(L.vfree[j]);
+                const int f = L.vfree[cn[l]];
+                if (f >= 0) out.push_back(f);
             }
         }
         sort_unique_tail(out, s0);
         const size_t s1 = out.size();
         for (int a = T.v2c_off[v]; a < T.v2c_off[v + 1]; ++a) {
             const int e = T.v2c[a];
-            for (int l = 0; l < nq; ++l) {
-                const int q = L.Q.cell_nodes[(size_t)e * nq + l];
-                if (L.family == 0) {
-                    const auto& sp = L.Q.support[q];
-                    bool in = false;
-                    for (int t2 = 0; t2 < 4; ++t2) in |= (sp[t2] == v);
-                    if (!in) continue;
-                }
-                out.push_back(q);
-            }
+            int i = 0;
+            while (i < nvpc && m.C[(size_t)e * nvpc + i] != v) ++i;
+            const unsigned char* ok = &in_star[(size_t)std::min(i, nvpc - 1) * nq];
+            const int* qn = &L.Q.cell_nodes[(size_t)e * nq];
+            for (int l = 0; l < nq; ++l)
+                if (ok[l]) out.push_back(qn[l]);
         }
         sort_unique_tail(out, s1);
         NV[v] = (int)(s1 - s0);
