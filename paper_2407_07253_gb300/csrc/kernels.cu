@@ -581,15 +581,24 @@ __device__ void sweep_spd(double* A, int n, int lda, double* ck, double* cs, dou
 // entry is swept by pivot k and pivot k+1, and the owners of columns k+2 and
 // k+3 publish them for the next step.  Scratch: ck[4n] (two column pairs,
 // double-buffered), cs[n], c1p[n], cs1[n], rinv[2].  status <- 1 + step of
-// the first non-positive pivot.
+// the first non-positive pivot.  PP: A is the pair-packed upper triangle
+// (pp_row; lda unused), which the sweep touches in its own order, and on
+// return holds +A^{-1} there (negated in place, not mirrored).
+template <bool PP>
 __device__ void sweep_spd2(double* A, int n, int lda, double* ck, double* cs, double* c1p, double* cs1, double* rinv,
                            int* status) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int npair = (n + 1) >> 1;
     for (int i = tid; i < n; i += nt) {
-        ck[i] = A[i];                                              // column 0 = row 0
-        if (n > 1) ck[n + i] = i == 0 ? A[1] : A[(long long)lda + i];   // column 1
+        // column 0 = row 0, column 1 = (0, 1) then row 1
+        if (PP) {
+            ck[i] = A[i];
+            if (n > 1) ck[n + i] = i == 0 ? A[1] : A[pp_row(n, 1) + i];
+        } else {
+            ck[i] = A[i];
+            if (n > 1) ck[n + i] = i == 0 ? A[1] : A[(long long)lda + i];
+        }
     }
     __syncthreads();
     for (int k = 0, b = 0; k < n; k += 2, ++b) {
@@ -641,7 +650,7 @@ __device__ void sweep_spd2(double* A, int n, int lda, double* ck, double* cs, do
             for (int l = lane; l < tot; l += 32) {
                 int i, j;
                 pair_entry(n, pr, l, i, j);
-                double* a = A + (long long)i * lda + j;
+                double* a = PP ? A + (long long)pr * (n + 1) + l : A + (long long)i * lda + j;
                 double v = fma(-cs[i], col0[j], *a);
                 if (i == k || j == k) v = (i == j) ? flip(inv0) : cs[i == k ? j : i];
                 if (two) {
@@ -659,15 +668,20 @@ __device__ void sweep_spd2(double* A, int n, int lda, double* ck, double* cs, do
         }
         __syncthreads();
     }
-    // -A^{-1} (upper) -> +A^{-1} (full)
+    // -A^{-1} (upper) -> +A^{-1} (full, or the packed upper triangle)
     for (int pr = warp; pr < npair; pr += nw) {
         const int tot = pair_len(n, pr);
         for (int l = lane; l < tot; l += 32) {
-            int i, j;
-            pair_entry(n, pr, l, i, j);
-            const double v = flip(A[(long long)i * lda + j]);
-            A[(long long)i * lda + j] = v;
-            A[(long long)j * lda + i] = v;
+            if (PP) {
+                double* a = A + (long long)pr * (n + 1) + l;
+                *a = flip(*a);
+            } else {
+                int i, j;
+                pair_entry(n, pr, l, i, j);
+                const double v = flip(A[(long long)i * lda + j]);
+                A[(long long)i * lda + j] = v;
+                A[(long long)j * lda + i] = v;
+            }
         }
     }
     __syncthreads();
@@ -821,7 +835,7 @@ __device__ void saddle_core(int d, int n, int nv, double* K, double* scratch, do
 // The factored form alone (no explicit output), in less shared memory: the
 // components' B_c^T and W_c = Li B_c^T go through one pair of buffers, W_c
 // is written out as soon as it exists and S = sum_c B_c W_c accumulates over
-// the components.  Scratch: saddle_scratch_factored(d, n, nv) doubles.
+// the components.  Scratch: saddle_scratch_factored(d, n, nv, PP) doubles.
 // position of global DoF c in a patch's sorted DoF list sd[0 .. n), or -1
 __device__ __forceinline__ int patch_pos(const int* sd, int n, int c) {
     int lo = 0, hi = n - 1;
@@ -837,6 +851,7 @@ __device__ __forceinline__ int patch_pos(const int* sd, int n, int c) {
 // of the patch's DoFs sd (sorted, shared memory) instead of a dense copy:
 // the velocity block of component 0 (its upper triangle) and, per component,
 // B_c^T, each entry placed by a binary search of its column in sd
+template <bool PP>
 __device__ void saddle_core_factored(int d, int n, int nv, const double* K, const int* sd, const int* __restrict__ rp,
                                      const int* __restrict__ ci, const double* __restrict__ av, double* scratch,
                                      double* fac64, float* fac32, int packed, int* status) {
@@ -844,8 +859,8 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int np = n - d * nv, npp = np | 1, dnv = d * nv;
     const int mx = nv > np ? nv : np;
-    double* Ls = scratch;                          // [nv][nv]
-    double* Bt = Ls + (long long)nv * nv;          // [a][q] of the current component
+    double* Ls = scratch;                          // PP: pair-packed upper triangle (pp_row), else [nv][nv]
+    double* Bt = Ls + (PP ? pp_size(nv) : (long long)nv * nv);   // [a][q] of the current component
     double* Wm = Bt + (long long)nv * npp;         // [a][q] of the current component
     double* Ss = Wm + (long long)nv * npp;         // [q][r]
     double* ck = Ss + (long long)np * np;          // [4][mx] (sweep_spd2's column pairs)
@@ -869,30 +884,31 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
     const int ns = np * (np + 1) / 2;
     if (K) {
         for (int i = warp; i < nv; i += nw)
-            for (int j = i + lane; j < nv; j += 32) Ls[i * nv + j] = K[(long long)i * n + j];
+            for (int j = i + lane; j < nv; j += 32) Ls[(PP ? pp_row(nv, i) : i * nv) + j] = K[(long long)i * n + j];
     } else {
         // the rows of component 0 give the velocity block and B_0^T
-        for (int t = tid; t < nv * nv; t += nt) Ls[t] = 0.0;
+        for (int t = tid; t < (PP ? pp_size(nv) : (long long)nv * nv); t += nt) Ls[t] = 0.0;
         for (int t = tid; t < nv * npp; t += nt) Bt[t] = 0.0;
         __syncthreads();
         for (int i = warp; i < nv; i += nw) {
             const int g = sd[i], e = rp[g + 1];
             for (int q = rp[g] + lane; q < e; q += 32) {
                 const int pos = patch_pos(sd, n, ci[q]);
-                if (pos >= i && pos < nv) Ls[i * nv + pos] = av[q];
+                if (pos >= i && pos < nv) Ls[(PP ? pp_row(nv, i) : i * nv) + pos] = av[q];
                 else if (pos >= dnv) Bt[(long long)i * npp + pos - dnv] = av[q];
             }
         }
     }
     for (int t = tid; t < np * np; t += nt) Ss[t] = 0.0;
     __syncthreads();
-    sweep_spd2(Ls, nv, nv, ck, cs, c1p, cs1, rinv, status);
+    sweep_spd2<PP>(Ls, nv, nv, ck, cs, c1p, cs1, rinv, status);
     if (packed) {
         // upper triangle row by row: (a, b >= a) at a nv - a (a - 1) / 2 + b - a
         for (int a = warp; a < nv; a += nw) {
             const long long o = (long long)a * nv - (long long)a * (a - 1) / 2 - a;
+            const int ra = PP ? pp_row(nv, a) : a * nv;
             for (int b = a + lane; b < nv; b += 32) {
-                const double v = Ls[a * nv + b];
+                const double v = Ls[ra + b];
                 if (fac64) fac64[o + b] = v;
                 if (fac32) fac32[o + b] = (float)v;
             }
@@ -905,7 +921,7 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
         const int tot = nv * ldl;
         for (int t = tid; t < tot; t += nt) {
             const int b = t / ldl, a = t - b * ldl;
-            const double v = a < nv ? Ls[a * nv + b] : 0.0;
+            const double v = a >= nv ? 0.0 : PP ? Ls[a <= b ? pp_row(nv, a) + b : pp_row(nv, b) + a] : Ls[a * nv + b];
             if (fac64) fac64[t] = v;
             if (fac32) fac32[t] = (float)v;
         }
@@ -949,12 +965,14 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
         const int nh = (nv + 31) >> 5;
         for (int it = warp; it < np * nh; it += nw) {
             const int q = it / nh, a = (it - q * nh) * 32 + lane;
+            const int ra = PP ? pp_row(nv, a) : 0;
             const double* bt = Bt + q;
             double sacc = 0.0;
             for (int w = 0; w < mw; ++w)
                 for (unsigned long long m = mk[q * mw + w]; m; m &= m - 1) {
                     const int b = w * 64 + __ffsll((long long)m) - 1;
-                    if (a < nv) sacc = fma(Ls[b * nv + a], bt[(long long)b * npp], sacc);
+                    if (a < nv)
+                        sacc = fma(Ls[PP ? (b <= a ? pp_row(nv, b) + a : ra + b) : b * nv + a], bt[(long long)b * npp], sacc);
                 }
             if (a < nv) Wm[(long long)a * npp + q] = sacc;
         }
@@ -980,7 +998,7 @@ __device__ void saddle_core_factored(int d, int n, int nv, const double* K, cons
         }
         __syncthreads();
     }
-    sweep_spd2(Ss, np, np, ck, cs, c1p, cs1, rinv, status);
+    sweep_spd2<false>(Ss, np, np, ck, cs, c1p, cs1, rinv, status);
     {
         const int tot = np * lds;
         for (int t = tid; t < tot; t += nt) {
@@ -1018,7 +1036,7 @@ __global__ void __launch_bounds__(256) saddle_inverse_smem(int npatch, int d, co
         for (int a = threadIdx.x; a < n; a += blockDim.x) sd[a] = pdofs[poff[p] + a];
     __syncthreads();
     if (!inv64 && !inv32 && !back)
-        saddle_core_factored(d, n, nv, work ? work + moff[p] : nullptr, sd, rp, ci, av, sscr,
+        saddle_core_factored<true>(d, n, nv, work ? work + moff[p] : nullptr, sd, rp, ci, av, sscr,
                              fac64 ? fac64 + foff64[p] : nullptr, fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
     else
         saddle_core(d, n, nv, work + moff[p], sscr, inv64 ? inv64 + off64[p] : nullptr,
@@ -1044,7 +1062,7 @@ __global__ void __launch_bounds__(256) saddle_inverse_global(int npatch, int d, 
     if (threadIdx.x == 0) st = 0;
     __syncthreads();
     if (!inv64 && !inv32 && !back)
-        saddle_core_factored(d, n, nv, work + moff[p], nullptr, nullptr, nullptr, nullptr, scratch + soff[p],
+        saddle_core_factored<false>(d, n, nv, work + moff[p], nullptr, nullptr, nullptr, nullptr, scratch + soff[p],
                              fac64 ? fac64 + foff64[p] : nullptr, fac32 ? fac32 + foff32[p] : nullptr, packed, &st);
     else
         saddle_core(d, n, nv, work + moff[p], scratch + soff[p], inv64 ? inv64 + off64[p] : nullptr,

@@ -188,10 +188,17 @@ constexpr long long SADDLE_SMEM_MAX_DOUBLES = 25600;   // 200 KB of shared memor
 // scratch of the factored-only inversion (one component's B^T and W at a
 // time, the two-pivot sweep's columns, and one bit mask per pressure column
 // of B^T: its nonzero rows)
-__host__ __device__ inline long long saddle_scratch_factored(int d, int n, int nv) {
+// Pair-packed upper triangle of a symmetric n x n matrix: rows pr and
+// n - 1 - pr share the n + 1 slots from pr (n + 1), in the order of the
+// sweeps' row-pair mapping; entry (a, b), a <= b, sits at pp_row(n, a) + b.
+__host__ __device__ inline long long pp_size(int n) { return (long long)((n + 1) / 2) * (n + 1); }
+__host__ __device__ inline int pp_row(int n, int a) { return 2 * a < n ? a * n : (n - 1 - a) * (n + 1) + 1; }
+// pp: the velocity block pair-packed (the shared-memory kernel) or full
+// (the global-scratch kernel, whose lane accesses then stay coalesced)
+__host__ __device__ inline long long saddle_scratch_factored(int d, int n, int nv, bool pp = true) {
     const int np = n - d * nv, npp = np | 1;
     const int mx = nv > np ? nv : np;
-    return (long long)nv * nv + 2LL * nv * npp + (long long)np * np + 7LL * mx + 2 + (long long)np * ((nv + 63) / 64);
+    return (pp ? pp_size(nv) : (long long)nv * nv) + 2LL * nv * npp + (long long)np * np + 7LL * mx + 2 + (long long)np * ((nv + 63) / 64);
 }
 // Outputs (each may be NULL): explicit inverses inv64 / inv32 (column-major,
 // leading dimension n rounded up to 2 / 4), the factored form fac64 / fac32

@@ -1547,7 +1547,8 @@ void upload_level_patches(stokes_mg* h, int li, bool want32, cudaStream_t s) {
             }
             else
                 scoff[p + 1] = scoff[p] + std::max(sc, skern::saddle_scratch_factored(
-                                                           HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p]));
+                                                           HL.d, HL.patch_off[p + 1] - HL.patch_off[p], HL.patch_nv[p],
+                                                           false));
         }
         l.saddle_global = scoff[l.npatch];
         l.scoff = hupload(h, scoff, s);
