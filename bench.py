@@ -1005,7 +1005,7 @@ def main():
     # DRAM bytes of that launch from one ncu capture of the same kernel and
     # workload (dram__bytes_read.sum + dram__bytes_write.sum of the level-0
     # launch of the CSR-reading, sparse-B inversion)
-    traffic_gj0 = (74.866432 + 32.339968) * 1e6 if a.workload == "th_p4_64x64" else None
+    traffic_gj0 = (74.930176 + 31.753216) * 1e6 if a.workload == "th_p4_64x64" else None
     # level-0 FP32 saddle apply: algorithmic bytes (above)
     patch_bytes = apply_bytes[0]
     patch_gbs = patch_bytes / (patch_ms * 1e-3) / 1e9 if patch_ms > 0 else None
