@@ -53,6 +53,11 @@ def test_host_hierarchy_matches_oracle(case):
         Rm = h.get_csr(li, 2)[pc][:, pf]
         assert abs(Rm - L.R).max() <= 1e-13
         off, dofs = h.patches(li)
+        # each patch lists its DoFs strictly increasing (velocity components
+        # blocked, then pressures): the inversion places operator entries by a
+        # binary search of this list
+        for i in range(len(off) - 1):
+            assert np.all(np.diff(dofs[off[i]:off[i + 1]]) > 0), (li, i)
         inv = np.argsort(pf)          # library index -> oracle index
         lib_sets = sorted(tuple(sorted(inv[dofs[off[i]:off[i + 1]]].tolist())) for i in range(len(off) - 1))
         ora_sets = sorted(tuple(p.tolist()) for p in L.asm.patches)
