@@ -162,9 +162,12 @@ class Pool {
 // the workers costs more than a light loop over a few thousand items)
 static int chunk_count(int n, int grain = 64) { return std::max(1, std::min(Pool::get().size(), n / grain)); }
 
-// Static-chunk parallel loop over [0, n): body(lo, hi, chunk).
-static void parallel_for(int n, const std::function<void(int, int, int)>& body, int grain = 64) {
-    const int T = chunk_count(n, grain);
+// Parallel loop over [0, n) in contiguous chunks of at least `grain` items:
+// body(lo, hi, chunk), chunk < Pool::size() unless split > 1 (then up to
+// split chunks per thread, claimed as threads come free, so that a thread
+// that is descheduled holds back less of the loop).
+static void parallel_for(int n, const std::function<void(int, int, int)>& body, int grain = 64, int split = 1) {
+    const int T = std::max(1, std::min(Pool::get().size() * std::max(1, split), n / grain));
     Pool::get().run(T, [&](int t) {
         int lo = (int)((long long)n * t / T), hi = (int)((long long)n * (t + 1) / T);
         body(lo, hi, t);
@@ -191,9 +194,12 @@ struct FlatLists {
     int size(int i) const { return off[i + 1] - off[i]; }
 };
 
+// fill(i, out, t) appends item i's list to out; t is the chunk, below
+// Pool::size() unless split > 1 (then up to split chunks per thread, claimed
+// as threads come free: a thread that is descheduled holds back less work)
 template <class F>
-static FlatLists build_lists(int n, F&& fill, int per_item = 32) {
-    const int T = chunk_count(n);
+static FlatLists build_lists(int n, F&& fill, int per_item = 32, int split = 1) {
+    const int T = std::max(1, std::min(Pool::get().size() * std::max(1, split), n / 64));
     std::vector<std::vector<int>> buf(T);
     FlatLists L;
     L.off.assign(n + 1, 0);
@@ -665,7 +671,7 @@ static void build_topology(const Mesh& m, Topology& T) {
             upper_neighbours(a, w);
             nbr_off[a + 1] = (int)w.size();
         }
-    }, 1024);
+    }, 64, 4);
     for (int a = 0; a < m.nv; ++a) nbr_off[a + 1] += nbr_off[a];
     std::vector<int> nbr(nbr_off[m.nv]);
     parallel_for(m.nv, [&](int lo, int hi, int) {
@@ -674,7 +680,7 @@ static void build_topology(const Mesh& m, Topology& T) {
             upper_neighbours(a, w);
             std::copy(w.begin(), w.end(), nbr.begin() + nbr_off[a]);
         }
-    }, 1024);
+    }, 64, 4);
     pc.lap("edge lists");
     T.cell_edge.resize((size_t)m.nc * nle);
     parallel_for(m.nc, [&](int lo, int hi, int) {
@@ -688,7 +694,7 @@ static void build_topology(const Mesh& m, Topology& T) {
                 T.cell_edge[(size_t)e * nle + t] = nbr_off[a] + (int)(std::lower_bound(first, last, b) - first);
             }
         }
-    }, 1024);
+    }, 256, 4);
     T.ne = nbr_off[m.nv];
     pc.lap("cell edges");
     std::vector<int> facet_count;
@@ -852,36 +858,40 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
                 tmp[(size_t)e * nb + l] = (int)(base[mm] + eid * nint[mm] + r);
             }
         }
-    }, 512);
+    }, 128, 4);
     // renumber by first appearance: first[x] = least position of id x, the
     // first positions in increasing order get 0, 1, 2, ...
     pc.lap("entity ids");
     const long long ntot = (long long)tmp.size();
-    std::vector<int> first(ntmp, INT32_MAX);
+    fvec<int> first(ntmp);
+    parallel_for((int)ntmp, [&](int lo, int hi, int) { std::fill(first.begin() + lo, first.begin() + hi, INT32_MAX); },
+                 8192, 4);
     parallel_for((int)ntot, [&](int lo, int hi, int) {
         for (int t = lo; t < hi; ++t) {
             int* f = &first[tmp[t]];
             int cur = __atomic_load_n(f, __ATOMIC_RELAXED);
             while (t < cur && !__atomic_compare_exchange_n(f, &cur, t, true, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {}
         }
-    }, 16384);
-    std::vector<int> isfirst(ntot), rankpos(ntot + 1);
+    }, 4096, 4);
+    fvec<int> isfirst(ntot), rankpos(ntot + 1);
     parallel_for((int)ntot, [&](int lo, int hi, int) {
         for (int t = lo; t < hi; ++t) isfirst[t] = first[tmp[t]] == t;
-    }, 16384);
+    }, 4096, 4);
     parallel_scan(isfirst.data(), (int)ntot, rankpos.data());
     pc.lap("first appearance");
     const int n = rankpos[ntot];
     parallel_for((int)ntot, [&](int lo, int hi, int) {
         for (int t = lo; t < hi; ++t) S.cell_nodes[t] = rankpos[first[tmp[t]]];
-    }, 16384);
+    }, 4096, 4);
     pc.lap("cell nodes");
     S.n = n;
-    S.X.assign((size_t)n * d, 0.0);
-    S.boundary.assign(n, 0);
-    S.support.assign(n, {-1, -1, -1, -1});
-    S.owner_cell.assign(n, -1);
-    S.owner_local.assign(n, -1);
+    // every field of every node is written below, by its first (cell, local
+    // node): no serial initialisation
+    S.X.resize((size_t)n * d);
+    S.boundary.resize(n);
+    S.support.resize(n);
+    S.owner_cell.resize(n);
+    S.owner_local.resize(n);
     // node data from its first (cell, local node)
     parallel_for((int)ntot, [&](int lo, int hi, int) {
         for (int t = lo; t < hi; ++t) {
@@ -902,7 +912,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
                 int tmpv[4];
                 for (int q = 0; q < mm; ++q) tmpv[q] = sv[q];
                 std::sort(tmpv, tmpv + mm);
-                for (int q = 0; q < mm; ++q) S.support[id][q] = tmpv[q];
+                for (int q = 0; q < 4; ++q) S.support[id][q] = q < mm ? tmpv[q] : -1;
             }
             bool b;
             if (mm == 1) b = T.bvert[sv[0]];
@@ -911,7 +921,7 @@ static void build_space(const Mesh& m, const Topology& T, const RefElement& re, 
             else b = false;
             S.boundary[id] = b;
         }
-    }, 4096);
+    }, 4096, 4);
     pc.lap("node data");
 }
 
@@ -1301,7 +1311,7 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
         sort_unique_tail(out, s1);
         NV[v] = (int)(s1 - s0);
         NP[v] = (int)(out.size() - s1);
-    }, 192);
+    }, 192, 4);
     pc.lap("star lists");
     // vertices with a non-empty patch, in order; patch p lists d blocks of its
     // velocity nodes (one per component), then its pressures
@@ -1327,7 +1337,7 @@ static void build_patches(const Mesh& m, const Topology& T, Level& L) {
             for (int x = 0; x < NP[v]; ++x) *dst++ = d * L.nVf + src[nvv + x];
             L.patch_nv[p] = nvv;
         }
-    }, 512);
+    }, 128, 4);
     pc.lap("patch dofs");
 }
 

@@ -80,11 +80,11 @@ struct Space {
     int d = 0, k = 0, nb = 0, n = 0;
     bool continuous = true;
     std::vector<int> cell_nodes;               // [nc][nb]
-    std::vector<double> X;                     // [n][d]
-    std::vector<unsigned char> boundary;       // [n]
-    std::vector<std::array<int, 4>> support;   // [n] vertices of the owning entity (-1 padded)
-    std::vector<int> owner_cell;               // [n] a cell containing the node
-    std::vector<int> owner_local;              // [n] the node's local index in owner_cell
+    fvec<double> X;                            // [n][d]
+    fvec<unsigned char> boundary;              // [n]
+    fvec<std::array<int, 4>> support;          // [n] vertices of the owning entity (-1 padded)
+    fvec<int> owner_cell;                      // [n] a cell containing the node
+    fvec<int> owner_local;                     // [n] the node's local index in owner_cell
 };
 
 struct Level {
