@@ -90,3 +90,51 @@ def test_library_exports_every_declared_symbol():
     lib = P.lib()
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing and len(names) >= 20, missing
+
+
+_DIGEST_SCRIPT = r"""
+import hashlib, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import workloads as W
+import paper_2407_07253_gb300 as P
+h = hashlib.sha256()
+for v, c, nref, fam, k, sched, bary in [
+        (*W.unit_square_mesh(4), 3, 0, 4, [4, 2], False),
+        (*W.unit_square_mesh(2), 2, 1, 4, [4, 2], True),
+        (*W.kuhn_cube_mesh(1), 2, 0, 3, [3, 2], False)]:
+    m = P.StokesMG(v, c, nref, fam, k, barycentric=bary, host_only=1,
+                   hierarchy=P.HIER_EXPLICIT, schedule=sched)
+    for li in range(m.info()["n_levels"]):
+        A = m.get_csr(li, 0)
+        for a in (A.indptr, A.indices, A.data):
+            h.update(np.ascontiguousarray(a).tobytes())
+        if li + 1 < m.info()["n_levels"]:
+            for part in (1, 2):
+                T = m.get_csr(li, part)
+                for a in (T.indptr, T.indices, T.data):
+                    h.update(np.ascontiguousarray(a).tobytes())
+            for a in m.patches(li):
+                h.update(np.ascontiguousarray(a).tobytes())
+print(h.hexdigest())
+"""
+
+
+def test_host_build_is_identical_for_any_thread_count():
+    """The host build's parallel loops (atomic first-appearance numbering,
+    per-thread list buffers, chunks claimed as threads come free) give the
+    same numbering, operators, transfers and patches bit for bit whatever
+    the number of worker threads.  The pool size is fixed per process, so
+    each count runs in a child process."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    digests = {}
+    for t in (1, 3, 8):
+        env = dict(os.environ, STOKES_HOST_THREADS=str(t))
+        out = subprocess.run([sys.executable, "-c", _DIGEST_SCRIPT, root], env=env, cwd=root,
+                             capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        digests[t] = out.stdout.strip().splitlines()[-1]
+    assert len(set(digests.values())) == 1, digests
