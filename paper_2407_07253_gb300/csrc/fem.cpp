@@ -405,11 +405,6 @@ Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent) {
 }
 
 // ------------------------------------------------------ reference element --
-static double factorial(int n) {
-    double f = 1;
-    for (int i = 2; i <= n; ++i) f *= i;
-    return f;
-}
 
 void RefElement::init(int d_, int k_) {
     d = d_;

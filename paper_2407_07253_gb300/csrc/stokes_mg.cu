@@ -70,19 +70,6 @@ T* dalloc(size_t n) {
     return (T*)p;
 }
 
-// Host-to-device upload.  On Grace-based GB300 nodes pageable copies run over
-// NVLink-C2C through the host page tables (measured ~165 GB/s, vs ~13 GB/s
-// for a single-threaded host copy into a pinned staging buffer), so arrays
-// are copied straight from their pageable host vectors.
-template <typename Vec>
-typename Vec::value_type* dupload(const Vec& h, cudaStream_t s) {
-    using T = typename Vec::value_type;
-    T* p = dalloc<T>(h.size());
-    const size_t bytes = h.size() * sizeof(T);
-    if (bytes) CK(cudaMemcpyAsync(p, h.data(), bytes, cudaMemcpyHostToDevice, s));
-    return p;
-}
-
 // One host thread that issues the device side of setup (uploads, kernel
 // launches) in submission order, so that it overlaps with the assembly of
 // the next level on the calling thread.  The first exception is kept and
@@ -479,6 +466,11 @@ T* halloc(stokes_mg* h, size_t n) {
     return p;
 }
 
+// Host-to-device upload into the handle's memory.  On Grace-based GB300
+// nodes pageable copies run over NVLink-C2C through the host page tables
+// (measured ~165 GB/s, against ~13 GB/s for a single-threaded host copy into
+// a pinned staging buffer), so arrays are copied straight from their
+// pageable host vectors.
 template <typename Vec>
 typename Vec::value_type* hupload(stokes_mg* h, const Vec& v, cudaStream_t s) {
     using T = typename Vec::value_type;
