@@ -152,7 +152,9 @@ void stokes_mg_default_opts(stokes_mg_opts* o);
  *   stream           device work of setup (gather, LU, eigen-estimate) runs here.
  *   out              receives the handle.
  * Errors: EINVAL (bad mesh/family/k), ESINGULAR (zero pivot; the stats
- * name the patch), EOOM, ECUDA. */
+ * name the patch), EOOM, ECUDA, EUNSUPPORTED (among others: a level whose
+ * operator, transfer or patch lists would exceed 2^31 - 1 entries, the
+ * range of the 32-bit CSR and list indices). */
 int stokes_mg_setup(const stokes_mesh* coarse, int n_refine, int barycentric_finest,
                     int family, int k, const stokes_mg_opts* opts,
                     const double* nu_cell, void* stream, stokes_mg_t* out);

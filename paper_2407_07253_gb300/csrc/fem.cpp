@@ -32,6 +32,14 @@ int num_threads() {
     return n;
 }
 
+// CSR row pointers, column indices and list offsets are 32-bit: a total
+// beyond that range is rejected (std::length_error) before any array is sized
+static int index_total(long long n, const char* what) {
+    if (n > INT32_MAX)
+        throw std::length_error(std::string(what) + " beyond 2^31 - 1 entries (32-bit indices)");
+    return (int)n;
+}
+
 // set on a thread that must not use the shared pool (the coarsest level's
 // builder): its parallel loops run inline
 thread_local bool t_pool_inline = false;
@@ -214,7 +222,11 @@ static FlatLists build_lists(int n, F&& fill, int per_item = 32, int split = 1) 
             L.off[i + 1] = (int)(b.size() - before);
         }
     });
-    for (int i = 0; i < n; ++i) L.off[i + 1] += L.off[i];
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        total += L.off[i + 1];
+        L.off[i + 1] = index_total(total, "index lists");
+    }
     L.data.resize(L.off[n]);
     parallel_for(T, [&](int a, int b2, int) {
         for (int t = a; t < b2; ++t)
@@ -583,7 +595,7 @@ CSR transpose(const CSR& a) {
             run += hist[th][col];
         }
     }
-    t.rp[t.nr] = (int)run;
+    t.rp[t.nr] = index_total(run, "transposed matrix");
     t.ci.resize(run);
     t.v.resize(run);
     Pool::get().run(T, [&](int th) {
@@ -1147,7 +1159,15 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
         K.rp[d * nVf + q + 1] = d * qvn.size(q);
         KD.rp[d * nVf + q + 1] = d * qdn.size(q);
     }
-    for (int r = 0; r < n; ++r) { K.rp[r + 1] += K.rp[r]; KD.rp[r + 1] += KD.rp[r]; }
+    {
+        long long sk = 0, sd = 0;
+        for (int r = 0; r < n; ++r) {
+            sk += K.rp[r + 1];
+            sd += KD.rp[r + 1];
+            K.rp[r + 1] = index_total(sk, "level operator");
+            KD.rp[r + 1] = index_total(sd, "Dirichlet columns of the operator");
+        }
+    }
     K.ci.resize(K.rp[n]);
     K.v.resize(K.rp[n]);
     KD.ci.resize(KD.rp[n]);
@@ -1233,7 +1253,10 @@ static void assemble_level(const Mesh& m, Level& L, const RefTensors& RT, const 
     CSR& Mv = L.Mv;
     Mv.nr = Mv.ncol = V.n;
     Mv.rp.assign(V.n + 1, 0);
-    for (int i = 0; i < V.n; ++i) Mv.rp[i + 1] = Mv.rp[i] + vnb.size(i) + vdn.size(i);
+    {
+        long long sm = 0;
+        for (int i = 0; i < V.n; ++i) Mv.rp[i + 1] = index_total(sm += vnb.size(i) + vdn.size(i), "mass matrix");
+    }
     Mv.ci.resize(Mv.rp[V.n]);
     Mv.v.resize(Mv.rp[V.n]);
     parallel_for(V.n, [&](int lo, int hi, int t) {
@@ -1394,7 +1417,10 @@ static CSR scalar_interp(const Mesh& mf, const Space& Vf, const Mesh& mc, const 
         }
     });
     P.rp.assign(P.nr + 1, 0);
-    for (int i = 0; i < P.nr; ++i) P.rp[i + 1] = P.rp[i] + cnt[i];
+    {
+        long long sp = 0;
+        for (int i = 0; i < P.nr; ++i) P.rp[i + 1] = index_total(sp += cnt[i], "transfer");
+    }
     P.ci.resize(P.rp[P.nr]);
     P.v.resize(P.rp[P.nr]);
     parallel_for(P.nr, [&](int lo, int hi, int) {
@@ -1433,7 +1459,10 @@ static void monolithic_interp(const Mesh& mf, Level& F, const Mesh& mc, const Le
     for (int c = 0; c < d; ++c)
         for (int f = 0; f < F.nVf; ++f) P.rp[c * F.nVf + f + 1] = vcount[f];
     for (int q = 0; q < F.Q.n; ++q) P.rp[d * F.nVf + q + 1] = PQ.rp[q + 1] - PQ.rp[q];
-    for (int r = 0; r < P.nr; ++r) P.rp[r + 1] += P.rp[r];
+    {
+        long long sp = 0;
+        for (int r = 0; r < P.nr; ++r) P.rp[r + 1] = index_total(sp += P.rp[r + 1], "transfer");
+    }
     P.ci.resize(P.rp[P.nr]);
     P.v.resize(P.rp[P.nr]);
     parallel_for(F.nVf, [&](int lo, int hi, int) {

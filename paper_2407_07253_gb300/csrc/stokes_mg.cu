@@ -1699,6 +1699,9 @@ void upload_assembly_inputs_lv(stokes_mg* h, const sfem::Level& HL, DevLevel& l,
     // entries: a velocity row of a node in c cells has at most c (nb + nq),
     // a pressure row at most d c nb; the incidences sum to nc nb and nc nq
     const long long bound = (long long)HL.d * mesh.nc * a.nb * (a.nb + a.nq) + (long long)HL.d * mesh.nc * a.nq * a.nb;
+    // the CSR's row pointers and column indices are 32-bit
+    if (bound > INT32_MAX)
+        throw StokesError(STOKES_EUNSUPPORTED, "level operator beyond 2^31 - 1 entries (32-bit CSR indices)");
     const int n = HL.n_free;
     DevCSR& K = l.K;
     K.nr = K.nc = n;
@@ -1874,6 +1877,8 @@ void build_transfer_dev(stokes_mg* h, int li, bool want32, const std::function<v
     cQ.nb = C.Q.nb; cQ.cell = lc.am.qcell; cQ.free = nullptr;
     const int nVf = F.nVf, nQf = F.nQ, nr = F.n_free, nrR = C.n_free;
     const long long ubP = (long long)d * nVf * cV.nb + (long long)nQf * cQ.nb;
+    if (ubP > INT32_MAX)
+        throw StokesError(STOKES_EUNSUPPORTED, "transfer beyond 2^31 - 1 entries (32-bit CSR indices)");
     DevCSR& P = lf.P;
     DevCSR& R = lf.R;
     P.nr = nr; P.nc = nrR; P.nnz = ubP;
@@ -1916,9 +1921,6 @@ void build_transfer_dev(stokes_mg* h, int li, bool want32, const std::function<v
             CK(cudaFreeAsync(x, s));
     });
 }
-
-// exact entry counts of the device-built transfers (after the setup streams
-// have drained)
 
 // gather K_i and invert every patch of level li; work receives the
 // row-major inverses (sum n_i^2 doubles) when keep != nullptr.
@@ -2362,6 +2364,9 @@ int guarded(F&& f) {
     } catch (const std::invalid_argument& e) {
         g_last_error = e.what();
         return STOKES_EINVAL;
+    } catch (const std::length_error& e) {         // a size beyond the 32-bit indices of the host build
+        g_last_error = e.what();
+        return STOKES_EUNSUPPORTED;
     } catch (const std::bad_alloc&) {
         g_last_error = "host allocation failed";
         return STOKES_EOOM;
