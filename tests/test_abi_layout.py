@@ -60,3 +60,57 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert ctypes.sizeof(py) == lay[(cname, "sizeof")], cname
         for field, _ in py._fields_:
             assert getattr(py, field).offset == lay[(cname, field)], (cname, field)
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) for every function the
+    header declares."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "stokes_mg.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(r"((?:const\s+)?\w+\s*\**)\s*\b(stokes_\w+)\s*\(([^)]*)\)\s*;", hdr):
+        ps = [" ".join(p.split()) for p in params.split(",")]
+        if ps == ["void"]:
+            ps = []
+        types = []
+        for p in ps:
+            p = re.sub(r"\[[^\]]*\]", "*", p)              # array parameters decay to pointers
+            stars = p.count("*")
+            words = [w for w in p.replace("*", " ").split() if w not in ("const",)]
+            base = " ".join(words[:-1]) if len(words) > 1 else words[0]
+            types.append("ptr" if stars or base == "stokes_mg_t" else base)   # the handle is a pointer
+        out[name] = (ret.replace(" ", ""), types)
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the binding wraps takes as many arguments as its
+    prototype, of the same kind (pointer, int, long long, double), and
+    returns what the prototype returns."""
+    import ctypes
+    lib = pytest.importorskip("paper_2407_07253_gb300").lib()
+    kind = {ctypes.c_int: "int", ctypes.c_longlong: "long long", ctypes.c_double: "double",
+            ctypes.c_ulonglong: "unsigned long long"}
+    protos = _prototypes()
+    wrapped = 0
+    for name, (ret, types) in protos.items():
+        f = getattr(lib, name)
+        if f.argtypes is None:
+            continue
+        wrapped += 1
+        got = []
+        for t in f.argtypes:
+            if t in kind:
+                got.append(kind[t])
+            else:
+                assert t is ctypes.c_void_p or t is ctypes.c_char_p or issubclass(t, ctypes._Pointer), (name, t)
+                got.append("ptr")
+        assert got == types, (name, got, types)
+        if ret == "void":
+            assert f.restype is None, name
+        elif ret.endswith("*"):
+            assert f.restype in (ctypes.c_char_p, ctypes.c_void_p), name
+        else:
+            assert kind.get(f.restype) == ret, (name, f.restype, ret)
+    assert wrapped >= 30, wrapped
