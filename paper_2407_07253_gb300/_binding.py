@@ -149,6 +149,43 @@ def _ptr(t):
     return c_void_p(t.data_ptr())
 
 
+def _vin(t, n, what):
+    """An input vector for the library: a contiguous float64 CUDA tensor with
+    at least n elements (n None: no length check).  A tensor of another
+    dtype, on the host or with gaps is converted first (on torch's current
+    stream); one with too few elements raises ValueError, since the library
+    would read past its end."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch.Tensor, got {type(t).__name__}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the library reads {n}")
+    if not t.is_cuda:
+        t = t.to(torch.device("cuda", torch.cuda.current_device()))
+    if t.dtype != torch.float64:
+        t = t.to(torch.float64)
+    return t.contiguous()
+
+
+def _vout(t, n, what):
+    """An output (or in-out) vector: the library writes it in place, so it
+    must already be a contiguous float64 CUDA tensor with at least n
+    elements; anything else raises ValueError."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch.Tensor, got {type(t).__name__}")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{what}: must be a contiguous float64 CUDA tensor "
+                         f"(got {t.dtype} on {t.device}, contiguous={t.is_contiguous()})")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the library writes {n}")
+    return t
+
+
+def _rows(t):
+    return 1 if t.dim() <= 1 else t.shape[0]
+
+
 def _stream(stream):
     if stream is not None:
         return c_void_p(stream)
@@ -206,6 +243,11 @@ class StokesMG:
                                         byref(self.opts), nu_p, _stream(stream), byref(self.h)))
         self.is_fbf = bool(fbf)
         self.dim = verts.shape[1]
+        i = self.info()
+        # vector lengths the ABI reads and writes (fixed once the handle exists)
+        self._nfree = list(i["n_free"])
+        self._nV = i["n_vel_nodes"]
+        self._nQ = i["n_pres_nodes"]
 
     # ---- queries
     def info(self):
@@ -256,12 +298,15 @@ class StokesMG:
                                           dofs.ctypes.data_as(c_void_p)))
         return off, dofs
 
-    # ---- device work (torch CUDA tensors, float64)
+    # ---- device work (torch CUDA tensors, float64; inputs of another dtype
+    # or on the host are converted, outputs are checked, see _vin / _vout)
     def vcycle(self, r, out=None):
         import torch
-        nrhs = 1 if r.dim() == 1 else r.shape[0]
-        z = torch.empty_like(r) if out is None else out
-        check(lib().stokes_mg_vcycle(self.h, _ptr(r.contiguous()), _ptr(z), nrhs, _stream(self.stream)))
+        nrhs = _rows(r)
+        n = nrhs * self._nfree[0]
+        r = _vin(r, n, "r")
+        z = torch.empty_like(r) if out is None else _vout(out, n, "out")
+        check(lib().stokes_mg_vcycle(self.h, _ptr(r), _ptr(z), nrhs, _stream(self.stream)))
         return z
 
     def fgmres_batched(self, B, mode=BATCH_TF32, tol=1e-8, out=None, raise_on_nonconv=True):
@@ -269,9 +314,9 @@ class StokesMG:
         float64), by FGMRES-phMG in lockstep with the batched V-cycle
         (stokes_fgmres_batched).  Returns (X, iterations, relres [nrhs])."""
         import torch
-        B = B.contiguous()
-        nrhs = 1 if B.dim() == 1 else B.shape[0]
-        X = torch.empty_like(B) if out is None else out
+        nrhs = _rows(B)
+        B = _vin(B, nrhs * self._nfree[0], "B")
+        X = torch.empty_like(B) if out is None else _vout(out, nrhs * self._nfree[0], "out")
         its = c_int()
         rel = np.zeros(nrhs, dtype=np.float64)
         rc = lib().stokes_fgmres_batched(self.h, _ptr(B), _ptr(X), nrhs, int(mode), float(tol), byref(its),
@@ -298,17 +343,18 @@ class StokesMG:
     def fbf_apply(self, r, out=None):
         """z = P^-1 r of Eq. fbf on the Stokes free DoFs (stokes_fbf_apply)."""
         import torch
-        z = torch.empty_like(r) if out is None else out
-        check(lib().stokes_fbf_apply(self.h, _ptr(r.contiguous()), _ptr(z), _stream(self.stream)))
+        r = _vin(r, None, "r")
+        z = torch.empty_like(r) if out is None else _vout(out, r.numel(), "out")
+        check(lib().stokes_fbf_apply(self.h, _ptr(r), _ptr(z), _stream(self.stream)))
         return z
 
     def vcycle_batched(self, R, mode=BATCH_3XTF32, out=None):
         """Z = B_MG R for R of shape [nrhs, n_free] (float64, device), all
         right-hand sides in one interleaved pass (stokes_mg_vcycle_batched)."""
         import torch
-        R = R.contiguous()
-        nrhs = 1 if R.dim() == 1 else R.shape[0]
-        Z = torch.empty_like(R) if out is None else out
+        nrhs = _rows(R)
+        R = _vin(R, nrhs * self._nfree[0], "R")
+        Z = torch.empty_like(R) if out is None else _vout(out, nrhs * self._nfree[0], "out")
         check(lib().stokes_mg_vcycle_batched(self.h, _ptr(R), _ptr(Z), nrhs, int(mode), _stream(self.stream)))
         return Z
 
@@ -317,8 +363,8 @@ class StokesMG:
         lam_p, dL/df or None, iterations, relres) for gu = dL/du [dim, nV]
         and gp = dL/dp [nQ] (device float64)."""
         import torch
-        gu = gu.contiguous()
-        gp = gp.contiguous()
+        gu = _vin(gu, self.dim * self._nV, "gu")
+        gp = _vin(gp, self._nQ, "gp")
         lam_u = torch.empty_like(gu)
         lam_p = torch.empty_like(gp)
         gf = torch.empty_like(gu) if grad_f else None
@@ -333,9 +379,10 @@ class StokesMG:
         """dL/dnu per finest cell (stokes_grad_viscosity)."""
         import torch
         n = self.n_cells()
+        u = _vin(u, self.dim * self._nV, "u")
+        lam_u = _vin(lam_u, self.dim * self._nV, "lam_u")
         g = torch.empty(n, dtype=torch.float64, device=u.device)
-        check(lib().stokes_grad_viscosity(self.h, _ptr(u.contiguous()), _ptr(lam_u.contiguous()), _ptr(g),
-                                          _stream(self.stream)))
+        check(lib().stokes_grad_viscosity(self.h, _ptr(u), _ptr(lam_u), _ptr(g), _stream(self.stream)))
         return g
 
     def solve_batched(self, F, G=None, mode=BATCH_3XTF32, nu=1.0, tol=1e-8, raise_on_nonconv=True):
@@ -343,10 +390,10 @@ class StokesMG:
         [nrhs, dim * n_vel_nodes] device float64 (G the same shape or None).
         Returns (U [nrhs, dim * nV], P [nrhs, nQ], iterations, relres [nrhs])."""
         import torch
-        F = F.contiguous()
         nrhs = F.shape[0]
-        G = None if G is None else G.contiguous()
-        nQ = self.info()["n_pres_nodes"]
+        F = _vin(F, nrhs * self.dim * self._nV, "F")
+        G = None if G is None else _vin(G, nrhs * self.dim * self._nV, "G")
+        nQ = self._nQ
         U = torch.empty_like(F)
         Pp = torch.empty(nrhs, nQ, dtype=torch.float64, device=F.device)
         its = c_int()
@@ -362,9 +409,9 @@ class StokesMG:
         GU [nrhs, dim * nV], GP [nrhs, nQ].  Returns (LAM_U, LAM_P, dL/dF or
         None, iterations, relres [nrhs])."""
         import torch
-        GU = GU.contiguous()
-        GP = GP.contiguous()
         nrhs = GU.shape[0]
+        GU = _vin(GU, nrhs * self.dim * self._nV, "GU")
+        GP = _vin(GP, nrhs * self._nQ, "GP")
         LU = torch.empty_like(GU)
         LP = torch.empty_like(GP)
         GF = torch.empty_like(GU) if grad_f else None
@@ -381,8 +428,9 @@ class StokesMG:
         """sum over the rows of dL/dnu per finest cell
         (stokes_grad_viscosity_batched); U, LU [nrhs, dim * nV]."""
         import torch
-        U = U.contiguous()
-        LU = LU.contiguous()
+        nrhs = U.shape[0]
+        U = _vin(U, nrhs * self.dim * self._nV, "U")
+        LU = _vin(LU, nrhs * self.dim * self._nV, "LU")
         g = torch.empty(self.n_cells(), dtype=torch.float64, device=U.device)
         check(lib().stokes_grad_viscosity_batched(self.h, _ptr(U), _ptr(LU), U.shape[0], _ptr(g),
                                                   _stream(self.stream)))
@@ -402,11 +450,13 @@ class StokesMG:
 
     def solve(self, f, g=None, nu=1.0, tol=1e-8, u=None, p=None, raise_on_nonconv=True):
         import torch
-        i = self.info()
-        u = torch.empty(self.dim * i["n_vel_nodes"], dtype=torch.float64, device=f.device) if u is None else u
-        p = torch.empty(i["n_pres_nodes"], dtype=torch.float64, device=f.device) if p is None else p
+        nu_ = self.dim * self._nV
+        f = _vin(f, nu_, "f")
+        g = None if g is None else _vin(g, nu_, "g")
+        u = torch.empty(nu_, dtype=torch.float64, device=f.device) if u is None else _vout(u, nu_, "u")
+        p = torch.empty(self._nQ, dtype=torch.float64, device=f.device) if p is None else _vout(p, self._nQ, "p")
         its, rel = c_int(), c_double()
-        rc = lib().stokes_solve(self.h, _ptr(f.contiguous()), _ptr(g), float(nu), float(tol), _ptr(u), _ptr(p),
+        rc = lib().stokes_solve(self.h, _ptr(f), _ptr(g), float(nu), float(tol), _ptr(u), _ptr(p),
                                 byref(its), byref(rel), _stream(self.stream))
         if rc != 0 and (raise_on_nonconv or rc != -4):
             check(rc)
@@ -414,6 +464,7 @@ class StokesMG:
 
     def fgmres(self, b, tol=1e-8):
         import torch
+        b = _vin(b, self._nfree[0], "b")
         x = torch.empty_like(b)
         its, rel = c_int(), c_double()
         check(lib().stokes_mg_fgmres(self.h, _ptr(b), _ptr(x), float(tol), byref(its), byref(rel), _stream(self.stream)))
@@ -433,30 +484,46 @@ class StokesMG:
 
     def arnoldi_lmax(self, level, v0, steps=10):
         out = c_double()
+        v0 = _vin(v0, self._level_n(level), "v0")
         check(lib().stokes_mg_arnoldi_lmax(self.h, level, _ptr(v0), steps, byref(out), _stream(self.stream)))
         return out.value
 
     def residual(self, level, b, x, precision=FP64):
         import torch
+        n = self._level_n(level)
+        b = _vin(b, n, "b")
+        x = _vin(x, n, "x")
         r = torch.empty_like(b)
         check(lib().stokes_mg_residual(self.h, level, _ptr(b), _ptr(x), _ptr(r), precision, _stream(self.stream)))
         return r
 
     def asm(self, level, r, precision=FP64):
         import torch
+        r = _vin(r, self._level_n(level), "r")
         z = torch.empty_like(r)
         check(lib().stokes_mg_asm(self.h, level, _ptr(r), _ptr(z), precision, _stream(self.stream)))
         return z
 
     def transfer(self, level, direction, x, y, precision=FP64):
+        """direction 0: y = R_l x (x on level l, y on l + 1); 1: y += P_l x
+        (x on l + 1, y on l).  y is written in place."""
+        nf, nc = self._level_n(level), self._level_n(level + 1)
+        x = _vin(x, nc if direction else nf, "x")
+        y = _vout(y, nf if direction else nc, "y")
         check(lib().stokes_mg_transfer(self.h, level, direction, _ptr(x), _ptr(y), precision, _stream(self.stream)))
         return y
 
     def coarse_solve(self, r):
         import torch
+        r = _vin(r, self._nfree[-1], "r")
         x = torch.empty_like(r)
         check(lib().stokes_mg_coarse_solve(self.h, _ptr(r), _ptr(x), _stream(self.stream)))
         return x
+
+    def _level_n(self, level):
+        if not 0 <= level < len(self._nfree):
+            raise ValueError(f"level {level} outside [0, {len(self._nfree)})")
+        return self._nfree[level]
 
     def prof_enable(self, kind, on=True):
         check(lib().stokes_prof_enable(self.h, kind, int(on)))
