@@ -114,3 +114,16 @@ def test_binding_signatures_match_the_header():
         else:
             assert kind.get(f.restype) == ret, (name, f.restype, ret)
     assert wrapped >= 30, wrapped
+
+
+def test_default_options_are_the_documented_ones():
+    """stokes_mg_default_opts gives what the header states: GRADUAL,
+    nu_p = nu_h = n_V = 1, 15 Arnoldi steps, seed 0, interval [0.1, 1.1],
+    FP64, restart 30, maxit 1000, use_graph 1, batch_tune 1, and zero for
+    everything else (no lambda_max overrides, host_only 0, the saddle-block
+    patch solver)."""
+    o = P.default_opts()
+    assert (o.hierarchy, o.nu_p, o.nu_h, o.n_V, o.eig_steps, o.eig_seed) == (P.HIER_GRADUAL, 1, 1, 1, 15, 0)
+    assert (o.cheb_lo, o.cheb_hi, o.precision, o.restart, o.maxit) == (0.1, 1.1, P.FP64, 30, 1000)
+    assert (o.use_graph, o.batch_tune, o.host_only, o.prof_mask, o.patch_solver, o.n_schedule) == (1, 1, 0, 0, 0, 0)
+    assert list(o.lmax_override) == [0.0] * 16 and list(o.schedule) == [0] * 8
