@@ -400,19 +400,14 @@ def batched_section(a, P, W, dev, stream, flush, hbm):
     gemm_bytes = 4.0 * float((n_i * ld_i).sum()) + 4.0 * m * float(n_i.sum()) + 4.0 * m * n
     gemm_flop = 2.0 * m * float((n_i * n_i).sum())
     gemm_gbs = gemm_bytes / (gemm_ms * 1e-3) / 1e9
-    # DRAM traffic per launch: one ncu capture of the same kernel on
-    # th_p3_cube8 at 64 right-hand sides (dram__bytes_read.sum +
-    # dram__bytes_write.sum = 439.09 + 47.52 MB against 472.14 MB of
-    # algorithmic bytes), scaled to this launch by the algorithmic bytes
-    # DRAM traffic per launch: one ncu capture of the tensor-core launch of
-    # level 0 on th_p3_cube8 at 64 right-hand sides (batch_tune 0: the 681
-    # patches of more than 64 DoFs in one launch; dram__bytes_read.sum +
-    # dram__bytes_write.sum = 440.98 + 43.14 MB against 471.24 MB of
-    # algorithmic bytes), scaled to this level by the algorithmic bytes
-    traffic, traffic_src = None, None
-    if m == 64 and w.name in ("th_p3_cube16", "th_p3_cube8"):
-        traffic = gemm_bytes * (440.978176 + 43.141888) / 471.237536
-        traffic_src = "ncu on th_p3_cube8 (484.1 MB for 471.2 MB algorithmic), scaled by algorithmic bytes"
+    # DRAM traffic per launch: the last ncu capture of the tensor-core launch
+    # (level 0 of th_p3_cube8 at 64 right-hand sides, batch_tune 0:
+    # dram__bytes_read.sum + dram__bytes_write.sum = 440.98 + 43.14 MB
+    # against 471.24 MB of algorithmic bytes) predates the 3xTF32 split of the
+    # kernel, so no traffic is reported for the current kernel
+    traffic = None
+    traffic_src = ("not re-captured since the kernel gained its 3xTF32 split; the TF32 launch measured "
+                   "484.1 MB for 471.2 MB algorithmic (1.03x) on th_p3_cube8 before that change")
     return {
         "workload": a.batched_workload, "nrhs": m, "n_free": n, "relaxed_levels": npatch_levels,
         "vcycle_ms": {"tf32": tf32_ms, "3xtf32": x3_ms, "single_rhs_mixed_per_rhs": single_ms},
