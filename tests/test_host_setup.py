@@ -138,3 +138,23 @@ def test_host_build_is_identical_for_any_thread_count():
         assert out.returncode == 0, out.stderr[-2000:]
         digests[t] = out.stdout.strip().splitlines()[-1]
     assert len(set(digests.values())) == 1, digests
+
+
+def test_host_gradual_hierarchy_follows_fig7_schedule():
+    """The library's GRADUAL hierarchy (no explicit schedule) takes the p-levels
+    of Fig. 7 (tests/golden/pmg_schedule.txt) on the finest mesh, then the P2
+    h-levels down to the coarse mesh: TH in 2D, host-only handles."""
+    import os
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pmg_schedule.txt")
+    rows = [l.split() for l in open(golden) if l[0] != "#"]
+    v, c = W.unit_square_mesh(1)
+    for k, sched in rows:
+        k, sched = int(k), [int(s) for s in sched.split(",")]
+        h = P.StokesMG(v, c, 2, P.TH, k, host_only=1, hierarchy=P.HIER_GRADUAL)
+        info = h.info()
+        nl = info["n_levels"]
+        deg, mesh = info["degree"][:nl], info["mesh_index"][:nl]
+        assert deg[:len(sched)] == sched and all(x == 0 for x in mesh[:len(sched)]), (k, deg, mesh)
+        assert deg[len(sched) - 1:] == [2] * (nl - len(sched) + 1), (k, deg)
+        assert mesh[len(sched) - 1:] == list(range(nl - len(sched) + 1)), (k, mesh)
+        h.close()
