@@ -158,3 +158,22 @@ def test_host_gradual_hierarchy_follows_fig7_schedule():
         assert deg[len(sched) - 1:] == [2] * (nl - len(sched) + 1), (k, deg)
         assert mesh[len(sched) - 1:] == list(range(nl - len(sched) + 1)), (k, mesh)
         h.close()
+
+
+def test_host_sv_hierarchy_levels():
+    """Scott-Vogelius hierarchy (the reading of Sec. 3.2 / Sec. 4.2): SV P_k on the
+    Alfeld-split finest mesh, the remaining Fig. 7 p-levels and the P2 level
+    as Taylor-Hood on that same split mesh, then P2 h-levels on the unsplit
+    finest mesh and every coarser mesh."""
+    v, c = W.unit_square_mesh(1)
+    for k, sched in ((3, [3, 2]), (4, [4, 2]), (6, [6, 4, 2]), (8, [8, 5, 2])):
+        h = P.StokesMG(v, c, 2, P.SV, k, barycentric=True, host_only=1, hierarchy=P.HIER_GRADUAL)
+        i = h.info()
+        nl = i["n_levels"]
+        p = len(sched)
+        assert i["degree"][:nl] == sched + [2] * (nl - p), (k, i["degree"][:nl])
+        assert i["level_family"][:nl] == [P.SV] + [P.TH] * (nl - 1), (k, i["level_family"][:nl])
+        assert i["mesh_index"][:nl] == [0] * p + list(range(1, nl - p + 1)), (k, i["mesh_index"][:nl])
+        assert i["is_p_level"][:nl] == [1] * (p - 1) + [0] * (nl - p + 1), (k, i["is_p_level"][:nl])
+        assert nl - p == 3                       # meshes: split finest, finest, once refined, coarse
+        h.close()
