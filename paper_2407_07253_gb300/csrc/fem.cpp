@@ -490,86 +490,271 @@ void RefElement::eval(const double* xi, double* out) const {
     }
 }
 
-// polynomial as (exponent, coefficient) list
-struct Poly {
-    std::vector<std::array<int, 3>> e;
-    std::vector<double> c;
+// Reference tensors through the Bernstein basis.  B_beta = n!/beta! lambda^beta
+// (|beta| = n, lambda_0 = 1 - sum xi, lambda_c = xi_c) are nonnegative, and
+// the Lagrange basis on the equispaced lattice has moderate coefficients in
+// them (below 1.5e3 at k = 10), while its monomial coefficients reach 1e9 and
+// their exact integrals cancel to a few digits at high k.  Integrals of
+// Bernstein products have a closed form with positive terms:
+//   int_T B_beta^m B_gamma^n = m! n! / (beta! gamma!) (beta + gamma)! / (m + n + d)!
+// on the reference simplex (volume 1/d!), and dB_beta^n/dxi_a =
+// n (B^{n-1}_{beta - e_a} - B^{n-1}_{beta - e_0}).
+
+// Error-free transformations (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005): a + b = s + e and a * b = p + e exactly.  The rounded
+// product passes through a volatile so that no compiler contraction fuses it
+// into a later addition; std::fma is correctly rounded on every target, so
+// the results are the same on every host.
+static inline void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+static inline void two_prod(double a, double b, double& p, double& e) {
+    volatile double pv = a * b;
+    p = pv;
+    e = std::fma(a, b, -p);
+}
+
+// multi-indices (beta_0, ..., beta_d) of total degree n, in the order of
+// RefElement::alpha
+static std::vector<std::array<int, 4>> lattice_indices(int d, int n) {
+    std::vector<std::array<int, 4>> out;
+    if (d == 2) {
+        for (int j = 0; j <= n; ++j)
+            for (int i = 0; i <= n - j; ++i) out.push_back({n - i - j, i, j, 0});
+    } else {
+        for (int l = 0; l <= n; ++l)
+            for (int j = 0; j <= n - l; ++j)
+                for (int i = 0; i <= n - l - j; ++i) out.push_back({n - i - j - l, i, j, l});
+    }
+    return out;
+}
+
+// multinomial n! / (b_0! ... b_d!) for |b| = n, exact in 64-bit integers
+// (every partial product is itself a multinomial coefficient)
+static long long multinomial(const std::array<int, 4>& b, int d) {
+    long long r = 1;
+    int m = 0;
+    for (int c = 0; c <= d; ++c)
+        for (int t = 1; t <= b[c]; ++t) r = r * (++m) / t;
+    return r;
+}
+
+// Bernstein coefficients of the degree-k Lagrange basis of `e`: row i holds
+// phi_i = sum_b C[i][b] B_b, b in lattice_indices(d, k) order.  C = G^-T for
+// the collocation matrix G[node][b] = B_b(node) = (k!/b!) prod_c alpha_c^b_c
+// / k^k.  k^k G is an integer matrix with entries at most k^k (the
+// multinomial theorem), exact in double up to k = 10, so it is inverted
+// exactly as given: Gauss-Jordan with partial pivoting (cond below 4e3 up to
+// k = 10 in 3D), then iterative refinement.
+static std::vector<double> lagrange_in_bernstein(const RefElement& e) {
+    const int d = e.d, k = e.k, n = e.nb;
+    const auto B = lattice_indices(d, k);
+    long long kk = 1;
+    for (int c = 0; c < k; ++c) kk *= k;
+    if (kk > (1LL << 53)) throw std::runtime_error("reference element degree too high for exact collocation");
+    std::vector<double> A((size_t)n * 2 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        for (int b = 0; b < n; ++b) {
+            const long long mult = multinomial(B[b], d);    // k! / b!
+            long long num = 1;
+            for (int c = 0; c <= d; ++c)
+                for (int t = 0; t < B[b][c]; ++t) num *= e.alpha[i][c];
+            A[(size_t)i * 2 * n + b] = (double)(mult * num);   // at most k^k
+        }
+        A[(size_t)i * 2 * n + n + i] = 1.0;
+    }
+    std::vector<double> G((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int b = 0; b < n; ++b) G[(size_t)i * n + b] = A[(size_t)i * 2 * n + b];
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * 2 * n + c]) > std::fabs(A[(size_t)p * 2 * n + c])) p = r;
+        if (p != c)
+            for (int j = 0; j < 2 * n; ++j) std::swap(A[(size_t)p * 2 * n + j], A[(size_t)c * 2 * n + j]);
+        const double piv = A[(size_t)c * 2 * n + c];
+        if (piv == 0) throw std::runtime_error("singular Bernstein collocation matrix");
+        for (int j = 0; j < 2 * n; ++j) A[(size_t)c * 2 * n + j] /= piv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * 2 * n + c];
+            if (f == 0) continue;
+            for (int j = 0; j < 2 * n; ++j) A[(size_t)r * 2 * n + j] -= f * A[(size_t)c * 2 * n + j];
+        }
+    }
+    // X = G^-1 sits in A[.][n ..); two steps of iterative refinement,
+    // X += X (I - G X), with the residual from compensated dot products
+    // bring X to working accuracy (the elimination alone leaves about
+    // cond(G) eps = 4e-13 at k = 10, which the tensors' sums amplify)
+    std::vector<double> X((size_t)n * n), R((size_t)n * n);
+    for (int b = 0; b < n; ++b)
+        for (int i = 0; i < n; ++i) X[(size_t)b * n + i] = A[(size_t)b * 2 * n + n + i];
+    for (int step = 0; step < 2; ++step) {
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double sum = i == j ? 1.0 : 0.0, err = 0;
+                for (int l = 0; l < n; ++l) {
+                    double p, pe, se;
+                    two_prod(-G[(size_t)i * n + l], X[(size_t)l * n + j], p, pe);
+                    two_sum(sum, p, sum, se);
+                    err += pe + se;
+                }
+                R[(size_t)i * n + j] = sum + err;
+            }
+        std::vector<double> Xn(X);
+        for (int b = 0; b < n; ++b)
+            for (int j = 0; j < n; ++j) {
+                double corr = 0;
+                for (int l = 0; l < n; ++l) corr += X[(size_t)b * n + l] * R[(size_t)l * n + j];
+                Xn[(size_t)b * n + j] += corr;
+            }
+        X.swap(Xn);
+    }
+    std::vector<double> C((size_t)n * n);
+    for (int b = 0; b < n; ++b)
+        for (int i = 0; i < n; ++i) C[(size_t)i * n + b] = X[(size_t)b * n + i] * (double)kk;
+    return C;
+}
+
+// W[b][g] = int B_b^m B_g^n over the reference d-simplex, as an unevaluated
+// pair hi + lo: with s = b + g,
+//   W = mult(m; b) mult(n; g) / (mult(m + n; s) (m+n+1) ... (m+n+d)),
+// numerator and denominator exact in double (below 2^53 up to m = n = 10),
+// so hi is the rounded quotient and lo its exact remainder divided out
+struct PairMatrix {
+    std::vector<double> hi, lo;
 };
-
-static Poly basis_poly(const RefElement& re, int i) {
-    Poly p;
-    for (int m = 0; m < re.nm; ++m) {
-        p.e.push_back(re.mono[m]);
-        p.c.push_back(re.coef[(size_t)i * re.nm + m]);
-    }
-    return p;
+static PairMatrix bernstein_products(int d, int m, int n) {
+    const auto Bm = lattice_indices(d, m), Bn = lattice_indices(d, n);
+    PairMatrix W;
+    W.hi.resize(Bm.size() * Bn.size());
+    W.lo.resize(Bm.size() * Bn.size());
+    long long tail = 1;
+    for (int t = 1; t <= d; ++t) tail *= m + n + t;
+    for (size_t b = 0; b < Bm.size(); ++b)
+        for (size_t g = 0; g < Bn.size(); ++g) {
+            std::array<int, 4> s{};
+            for (int c = 0; c <= d; ++c) s[c] = Bm[b][c] + Bn[g][c];
+            const long long num = multinomial(Bm[b], d) * multinomial(Bn[g], d);
+            const long long den = multinomial(s, d) * tail;
+            if (num > (1LL << 53) || den > (1LL << 53))
+                throw std::runtime_error("reference element degree too high for exact Bernstein integrals");
+            const double hi = (double)num / (double)den;
+            const double rem = std::fma(-hi, (double)den, (double)num);   // exact: num - hi den
+            W.hi[b * Bn.size() + g] = hi;
+            W.lo[b * Bn.size() + g] = rem / (double)den;
+        }
+    return W;
 }
 
-static Poly deriv(const Poly& p, int a) {
-    Poly q;
-    for (size_t t = 0; t < p.e.size(); ++t) {
-        if (p.e[t][a] == 0) continue;
-        auto e = p.e[t];
-        double f = e[a];
-        e[a] -= 1;
-        q.e.push_back(e);
-        q.c.push_back(p.c[t] * f);
-    }
-    return q;
+// PW[r][y] = sum_x P[r][x] W[x][y] (P: rp x nx, W: nx x ny) as pairs hi + lo,
+// compensated: the Lagrange coefficients in P carry signs, and plain double
+// sums lose three to four digits to cancellation at k = 10
+static PairMatrix left_product(const std::vector<double>& P, int rp, int nx, const PairMatrix& W, int ny) {
+    PairMatrix PW;
+    PW.hi.resize((size_t)rp * ny);
+    PW.lo.resize((size_t)rp * ny);
+    for (int r = 0; r < rp; ++r)
+        for (int y = 0; y < ny; ++y) {
+            double sum = 0, err = 0;
+            for (int x = 0; x < nx; ++x) {
+                const double a = P[(size_t)r * nx + x];
+                double p, pe, se;
+                two_prod(a, W.hi[(size_t)x * ny + y], p, pe);
+                two_sum(sum, p, sum, se);
+                err += pe + se + a * W.lo[(size_t)x * ny + y];
+            }
+            two_sum(sum, err, PW.hi[(size_t)r * ny + y], PW.lo[(size_t)r * ny + y]);
+        }
+    return PW;
 }
 
-// exact integral of x^a y^b z^c over the reference d-simplex:
-// a! b! c! / (a + b + c + d)!
-static double mono_integral(int d, int a, int b, int c) {
-    static const std::vector<double> f = [] {
-        std::vector<double> t(80, 1.0);
-        for (int i = 1; i < 80; ++i) t[i] = t[i - 1] * i;
-        return t;
-    }();
-    return f[a] * f[b] * f[c] / f[a + b + c + d];
-}
-
-static double integrate_product(int d, const Poly& p, const Poly& q) {
-    double s = 0;
-    for (size_t i = 0; i < p.e.size(); ++i) {
-        if (p.c[i] == 0) continue;
-        for (size_t j = 0; j < q.e.size(); ++j)
-            s += p.c[i] * q.c[j] *
-                 mono_integral(d, p.e[i][0] + q.e[j][0], p.e[i][1] + q.e[j][1], p.e[i][2] + q.e[j][2]);
-    }
-    return s;
+// out[r][c] = sum_y PW[r][y] Q[c][y]  (Q: cq x ny), compensated
+static std::vector<double> right_product(const PairMatrix& PW, int rp, const std::vector<double>& Q, int cq, int ny) {
+    std::vector<double> out((size_t)rp * cq);
+    for (int r = 0; r < rp; ++r)
+        for (int c = 0; c < cq; ++c) {
+            double sum = 0, err = 0;
+            for (int y = 0; y < ny; ++y) {
+                const double q = Q[(size_t)c * ny + y];
+                double p, pe, se;
+                two_prod(PW.hi[(size_t)r * ny + y], q, p, pe);
+                two_sum(sum, p, sum, se);
+                err += pe + se + PW.lo[(size_t)r * ny + y] * q;
+            }
+            out[(size_t)r * cq + c] = sum + err;
+        }
+    return out;
 }
 
 void RefTensors::init(const RefElement& v, const RefElement& q) {
     d = v.d;
     nb = v.nb;
     nq = q.nb;
-    std::vector<Poly> phi(nb), psi(nq);
-    std::vector<std::vector<Poly>> dphi(d, std::vector<Poly>(nb));
-    for (int i = 0; i < nb; ++i) {
-        phi[i] = basis_poly(v, i);
-        for (int a = 0; a < d; ++a) dphi[a][i] = deriv(phi[i], a);
+    const int k = v.k, kq = q.k;
+    const std::vector<double> Cv = lagrange_in_bernstein(v), Cp = lagrange_in_bernstein(q);
+    // derivative coefficients in the degree k - 1 Bernstein basis:
+    // dphi_i/dxi_a = sum_g D_a[i][g] B_g^{k-1}
+    const auto Bk = lattice_indices(d, k), Bk1 = lattice_indices(d, k - 1);
+    const int n1 = (int)Bk1.size();
+    // position in Bk (RefElement order) of a degree-k multi-index, from (beta_1, .., beta_d)
+    std::vector<int> pos_k((size_t)(k + 1) * (k + 1) * (d == 3 ? k + 1 : 1), -1);
+    auto key = [&](const std::array<int, 4>& b) { return (size_t)b[1] + (size_t)(k + 1) * (b[2] + (size_t)(k + 1) * b[3]); };
+    for (int x = 0; x < (int)Bk.size(); ++x) pos_k[key(Bk[x])] = x;
+    auto index_k = [&](const std::array<int, 4>& b) { return pos_k[key(b)]; };
+    std::vector<int> up0(n1), upa((size_t)d * n1);
+    for (int g = 0; g < n1; ++g) {
+        auto b = Bk1[g];
+        b[0] += 1;
+        up0[g] = index_k(b);
+        for (int a = 0; a < d; ++a) {
+            auto c = Bk1[g];
+            c[a + 1] += 1;
+            upa[(size_t)a * n1 + g] = index_k(c);
+        }
     }
-    for (int p = 0; p < nq; ++p) psi[p] = basis_poly(q, p);
+    std::vector<std::vector<double>> D(d, std::vector<double>((size_t)nb * n1));
+    for (int a = 0; a < d; ++a)
+        for (int i = 0; i < nb; ++i)
+            for (int g = 0; g < n1; ++g)
+                D[a][(size_t)i * n1 + g] = k * (Cv[(size_t)i * nb + upa[(size_t)a * n1 + g]] - Cv[(size_t)i * nb + up0[g]]);
+    const PairMatrix Wkk = bernstein_products(d, k, k), W11 = bernstein_products(d, k - 1, k - 1),
+                     Wq1 = bernstein_products(d, kq, k - 1);
+    // S[a][b] = D_a W D_b^T; S[b][a] is its transpose
     S.assign((size_t)d * d * nb * nb, 0.0);
-    for (int a = 0; a < d; ++a)
-        for (int b = 0; b < d; ++b)
+    for (int a = 0; a < d; ++a) {
+        const PairMatrix DW = left_product(D[a], nb, n1, W11, n1);
+        for (int b = a; b < d; ++b) {
+            const std::vector<double> Sab = right_product(DW, nb, D[b], nb, n1);
             for (int i = 0; i < nb; ++i)
-                for (int j = 0; j < nb; ++j)
-                    S[(((size_t)a * d + b) * nb + i) * nb + j] = integrate_product(d, dphi[a][i], dphi[b][j]);
+                for (int j = 0; j < nb; ++j) {
+                    S[(((size_t)a * d + b) * nb + i) * nb + j] = Sab[(size_t)i * nb + j];
+                    S[(((size_t)b * d + a) * nb + j) * nb + i] = Sab[(size_t)i * nb + j];
+                }
+        }
+    }
     Cq.assign((size_t)d * nq * nb, 0.0);
-    for (int a = 0; a < d; ++a)
-        for (int p = 0; p < nq; ++p)
-            for (int j = 0; j < nb; ++j)
-                Cq[((size_t)a * nq + p) * nb + j] = integrate_product(d, psi[p], dphi[a][j]);
-    M.assign((size_t)nb * nb, 0.0);
-    for (int i = 0; i < nb; ++i)
-        for (int j = 0; j < nb; ++j) M[(size_t)i * nb + j] = integrate_product(d, phi[i], phi[j]);
+    const PairMatrix CW = left_product(Cp, nq, nq, Wq1, n1);
+    for (int a = 0; a < d; ++a) {
+        const std::vector<double> Ca = right_product(CW, nq, D[a], nb, n1);
+        std::copy(Ca.begin(), Ca.end(), Cq.begin() + (size_t)a * nq * nb);
+    }
+    M = right_product(left_product(Cv, nb, nb, Wkk, nb), nb, Cv, nb, nb);
+    // int B_b^kq = kq! / (kq + d)! = 1 / ((kq + 1) ... (kq + d)) for every b
     qint.assign(nq, 0.0);
-    Poly one;
-    one.e.push_back({0, 0, 0});
-    one.c.push_back(1.0);
-    for (int p = 0; p < nq; ++p) qint[p] = integrate_product(d, psi[p], one);
+    double tail = 1.0;
+    for (int t = 1; t <= d; ++t) tail *= kq + t;
+    for (int p = 0; p < nq; ++p) {
+        double sum = 0, err = 0;
+        for (int b = 0; b < nq; ++b) {
+            double se;
+            two_sum(sum, Cp[(size_t)p * nq + b], sum, se);
+            err += se;
+        }
+        qint[p] = (sum + err) / tail;
+    }
 }
 
 CSR transpose(const CSR& a) {

@@ -20,6 +20,9 @@ CASES = [
     ("sv_p4_disk", W.delaunay_disk_mesh(0, h=0.5), 1, 1, 4, [4, 2], True),
     ("th3d_p3", W.kuhn_cube_mesh(1), 1, 0, 3, [3, 2], False),
     ("sv3d_p3_alfeld", W.kuhn_cube_mesh(1), 0, 1, 3, [3, 2], True),
+    ("th_p7_gradual", W.unit_square_mesh(2), 1, 0, 7, [7, 4, 2], False),
+    ("sv_p6_gradual", W.unit_square_mesh(1), 1, 1, 6, [6, 4, 2], True),
+    ("th3d_p4", W.kuhn_cube_mesh(1), 1, 0, 4, [4, 2], False),
 ]
 
 
