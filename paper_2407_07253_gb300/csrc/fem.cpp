@@ -504,7 +504,7 @@ void RefElement::eval(const double* xi, double* out) const {
 // product", 2005): a + b = s + e and a * b = p + e exactly.  The rounded
 // product passes through a volatile so that no compiler contraction fuses it
 // into a later addition; std::fma is correctly rounded on every target, so
-// the results are the same on every host.
+// both transformations are exact on every host.
 static inline void two_sum(double a, double b, double& s, double& e) {
     s = a + b;
     const double z = s - a;
