@@ -37,6 +37,23 @@ def _build(case):
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_host_hierarchy_matches_oracle(case):
     h, ora = _build(case)
+    _check_hierarchy(h, ora)
+
+
+@pytest.mark.slow
+def test_host_hierarchy_matches_oracle_at_bench_size():
+    """The same comparison on the benchmark workload: TH P4/P3 on the 64x64
+    square (167,299 free DoFs, 4225 level-0 patches), every level."""
+    w = W.workload("th_p4_64x64")
+    h = P.StokesMG(w.verts, w.cells, w.n_refine, w.family, w.k, barycentric=w.barycentric, host_only=1,
+                   hierarchy=P.HIER_EXPLICIT, schedule=w.schedule)
+    ora = mg.Hierarchy(w.verts, w.cells, w.n_refine, w.family, w.schedule, barycentric=w.barycentric,
+                       lmax=[1.0] * 16)
+    assert h.info()["n_free"][0] == 167299
+    _check_hierarchy(h, ora)
+
+
+def _check_hierarchy(h, ora):
     info = h.info()
     assert info["n_levels"] == len(ora.levels)
     perms = []
