@@ -418,6 +418,8 @@ Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent) {
 
 // ------------------------------------------------------ reference element --
 
+static std::vector<double> lagrange_in_bernstein(const RefElement& e);
+
 void RefElement::init(int d_, int k_) {
     d = d_;
     k = k_;
@@ -473,21 +475,7 @@ void RefElement::init(int d_, int k_) {
     coef.assign((size_t)n * n, 0.0);
     for (int m = 0; m < n; ++m)
         for (int i = 0; i < n; ++i) coef[(size_t)i * n + m] = (double)A[(size_t)m * 2 * n + n + i];
-}
-
-void RefElement::eval(const double* xi, double* out) const {
-    double mv[320];   // up to P_10 in 3D (286 monomials)
-    for (int m = 0; m < nm; ++m) {
-        double v = 1;
-        for (int c = 0; c < d; ++c)
-            for (int p = 0; p < mono[m][c]; ++p) v *= xi[c];
-        mv[m] = v;
-    }
-    for (int i = 0; i < nb; ++i) {
-        double s = 0;
-        for (int m = 0; m < nm; ++m) s += coef[(size_t)i * nm + m] * mv[m];
-        out[i] = s;
-    }
+    bcoef = lagrange_in_bernstein(*this);
 }
 
 // Reference tensors through the Bernstein basis.  B_beta = n!/beta! lambda^beta
@@ -689,12 +677,46 @@ static std::vector<double> right_product(const PairMatrix& PW, int rp, const std
     return out;
 }
 
+// phi_i(xi) = sum_b bcoef[i][b] B_b(lambda(xi)), compensated: the Bernstein
+// values are nonnegative and sum to one, so the result is accurate to a few
+// units of the last place at any degree (the monomial expansion in coef
+// loses digits with the degree: 1.7e-10 for P9 at lattice points)
+void RefElement::eval(const double* xi, double* out) const {
+    double lam[4] = {1.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c < d; ++c) {
+        lam[c + 1] = xi[c];
+        lam[0] -= xi[c];
+    }
+    double pw[4][11];                 // lambda_c^e, e <= k <= 10
+    for (int c = 0; c <= d; ++c) {
+        pw[c][0] = 1.0;
+        for (int e2 = 1; e2 <= k; ++e2) pw[c][e2] = pw[c][e2 - 1] * lam[c];
+    }
+    double bv[320];                   // up to P_10 in 3D (286 basis functions)
+    for (int b = 0; b < nb; ++b) {
+        double v = (double)multinomial(alpha[b], d);
+        for (int c = 0; c <= d; ++c) v *= pw[c][alpha[b][c]];
+        bv[b] = v;
+    }
+    for (int i = 0; i < nb; ++i) {
+        double sum = 0, err = 0;
+        for (int b = 0; b < nb; ++b) {
+            double p, pe, se;
+            two_prod(bcoef[(size_t)i * nb + b], bv[b], p, pe);
+            two_sum(sum, p, sum, se);
+            err += pe + se;
+        }
+        out[i] = sum + err;
+    }
+}
+
 void RefTensors::init(const RefElement& v, const RefElement& q) {
     d = v.d;
     nb = v.nb;
     nq = q.nb;
     const int k = v.k, kq = q.k;
-    const std::vector<double> Cv = lagrange_in_bernstein(v), Cp = lagrange_in_bernstein(q);
+    const std::vector<double>& Cv = v.bcoef;
+    const std::vector<double>& Cp = q.bcoef;
     // derivative coefficients in the degree k - 1 Bernstein basis:
     // dphi_i/dxi_a = sum_g D_a[i][g] B_g^{k-1}
     const auto Bk = lattice_indices(d, k), Bk1 = lattice_indices(d, k - 1);

@@ -45,15 +45,18 @@ Mesh refine_uniform(const Mesh& m, std::vector<int>& parent);
 Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent);
 
 // Lagrange element of degree k on the reference d-simplex with the
-// equispaced lattice nodes xi = (alpha_1, ..., alpha_d) / k.  For point
-// evaluation (the transfers' coarse basis) the basis functions are expanded
-// in monomials, the coefficients from inverting the Vandermonde matrix of
-// the nodes; the reference tensors below use the Bernstein form instead.
+// equispaced lattice nodes xi = (alpha_1, ..., alpha_d) / k.  The basis is
+// held in Bernstein form (bcoef: phi_i = sum_b bcoef[i][b] B_b, b in the
+// order of alpha), which eval and the reference tensors use, and expanded
+// in monomials (coef, from inverting the Vandermonde matrix of the nodes)
+// for the device kernel that evaluates the P2 coarse basis of the
+// h-transfers.
 struct RefElement {
     int d = 0, k = 0, nb = 0, nm = 0;
     std::vector<std::array<int, 4>> alpha;   // [nb] barycentric multi-index, alpha[0] = k - sum
     std::vector<std::array<int, 3>> mono;    // [nm] exponents
     std::vector<double> coef;                // [nb][nm]
+    std::vector<double> bcoef;               // [nb][nb]
     void init(int d, int k);
     void eval(const double* xi, double* out) const;   // out[nb]
 };

@@ -23,6 +23,7 @@ CASES = [
     ("th_p7_gradual", W.unit_square_mesh(2), 1, 0, 7, [7, 4, 2], False),
     ("sv_p6_gradual", W.unit_square_mesh(1), 1, 1, 6, [6, 4, 2], True),
     ("th3d_p4", W.kuhn_cube_mesh(1), 1, 0, 4, [4, 2], False),
+    ("th_p10_explicit", W.unit_square_mesh(1), 1, 0, 10, [10, 9, 2], False),
 ]
 
 
