@@ -49,8 +49,9 @@ Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent);
 // held in Bernstein form (bcoef: phi_i = sum_b bcoef[i][b] B_b, b in the
 // order of alpha), which eval and the reference tensors use, and expanded
 // in monomials (coef, from inverting the Vandermonde matrix of the nodes)
-// for the device kernel that evaluates the P2 coarse basis of the
-// h-transfers.
+// for the device kernel that evaluates the coarse basis of the h-transfers
+// (P2 in every phMG hierarchy, where the expansion is exact; it loses
+// digits at high degree).
 struct RefElement {
     int d = 0, k = 0, nb = 0, nm = 0;
     std::vector<std::array<int, 4>> alpha;   // [nb] barycentric multi-index, alpha[0] = k - sum
