@@ -419,6 +419,7 @@ Mesh refine_alfeld(const Mesh& m, std::vector<int>& parent) {
 // ------------------------------------------------------ reference element --
 
 static std::vector<double> lagrange_in_bernstein(const RefElement& e);
+static std::vector<double> invert_refined(const std::vector<double>& G, int n, int steps);
 
 void RefElement::init(int d_, int k_) {
     d = d_;
@@ -441,40 +442,27 @@ void RefElement::init(int d_, int k_) {
     nb = (int)alpha.size();
     nm = (int)mono.size();
     if (nb != nm) throw std::runtime_error("reference element: node/monomial count mismatch");
-    // Vandermonde V[node][m] = xi^mono_m, inverted by Gauss-Jordan in long double
+    // Vandermonde V[node][m] = xi^mono_m with xi = alpha / k.  Scaled by
+    // k^|m| per column it is an integer matrix (entries prod alpha^m, at most
+    // k^k, exact in double), inverted as given with iterative refinement;
+    // then coef[i][m] = k^|m| Vhat^-1[m][i].
     const int n = nb;
-    std::vector<long double> A((size_t)n * 2 * n, 0.0L);
-    for (int i = 0; i < n; ++i) {
-        long double xi[3] = {0, 0, 0};
-        for (int c = 0; c < d; ++c) xi[c] = (long double)alpha[i][c + 1] / (k > 0 ? k : 1);
+    std::vector<double> V((size_t)n * n);
+    for (int i = 0; i < n; ++i)
         for (int m = 0; m < n; ++m) {
-            long double v = 1;
+            long long v = 1;
             for (int c = 0; c < d; ++c)
-                for (int p = 0; p < mono[m][c]; ++p) v *= xi[c];
-            A[(size_t)i * 2 * n + m] = v;
+                for (int p = 0; p < mono[m][c]; ++p) v *= alpha[i][c + 1];
+            V[(size_t)i * n + m] = (double)v;
         }
-        A[(size_t)i * 2 * n + n + i] = 1;
-    }
-    for (int c = 0; c < n; ++c) {
-        int p = c;
-        for (int r = c + 1; r < n; ++r)
-            if (fabsl(A[(size_t)r * 2 * n + c]) > fabsl(A[(size_t)p * 2 * n + c])) p = r;
-        if (p != c)
-            for (int j = 0; j < 2 * n; ++j) std::swap(A[(size_t)p * 2 * n + j], A[(size_t)c * 2 * n + j]);
-        long double piv = A[(size_t)c * 2 * n + c];
-        if (piv == 0) throw std::runtime_error("singular Vandermonde");
-        for (int j = 0; j < 2 * n; ++j) A[(size_t)c * 2 * n + j] /= piv;
-        for (int r = 0; r < n; ++r) {
-            if (r == c) continue;
-            long double f = A[(size_t)r * 2 * n + c];
-            if (f == 0) continue;
-            for (int j = 0; j < 2 * n; ++j) A[(size_t)r * 2 * n + j] -= f * A[(size_t)c * 2 * n + j];
-        }
-    }
-    // Vinv[m][i] -> coef[i][m]
+    const std::vector<double> X = invert_refined(V, n, 4);   // cond up to 2e11 at k = 10 in 3D
     coef.assign((size_t)n * n, 0.0);
-    for (int m = 0; m < n; ++m)
-        for (int i = 0; i < n; ++i) coef[(size_t)i * n + m] = (double)A[(size_t)m * 2 * n + n + i];
+    for (int m = 0; m < n; ++m) {
+        double scale = 1.0;
+        for (int c = 0; c < d; ++c)
+            for (int p = 0; p < mono[m][c]; ++p) scale *= k;
+        for (int i = 0; i < n; ++i) coef[(size_t)i * n + m] = X[(size_t)m * n + i] * scale;
+    }
     bcoef = lagrange_in_bernstein(*this);
 }
 
@@ -536,26 +524,16 @@ static long long multinomial(const std::array<int, 4>& b, int d) {
 // multinomial theorem), exact in double up to k = 10, so it is inverted
 // exactly as given: Gauss-Jordan with partial pivoting (cond below 4e3 up to
 // k = 10 in 3D), then iterative refinement.
-static std::vector<double> lagrange_in_bernstein(const RefElement& e) {
-    const int d = e.d, k = e.k, n = e.nb;
-    const auto B = lattice_indices(d, k);
-    long long kk = 1;
-    for (int c = 0; c < k; ++c) kk *= k;
-    if (kk > (1LL << 53)) throw std::runtime_error("reference element degree too high for exact collocation");
+// G^-1 for an n x n matrix G given exactly: Gauss-Jordan with partial
+// pivoting, then `steps` steps of iterative refinement X += X (I - G X) with
+// the residual from compensated dot products, each of which multiplies the
+// error by about cond(G) eps (so cond(G) well below 1/eps is needed).
+static std::vector<double> invert_refined(const std::vector<double>& G, int n, int steps) {
     std::vector<double> A((size_t)n * 2 * n, 0.0);
     for (int i = 0; i < n; ++i) {
-        for (int b = 0; b < n; ++b) {
-            const long long mult = multinomial(B[b], d);    // k! / b!
-            long long num = 1;
-            for (int c = 0; c <= d; ++c)
-                for (int t = 0; t < B[b][c]; ++t) num *= e.alpha[i][c];
-            A[(size_t)i * 2 * n + b] = (double)(mult * num);   // at most k^k
-        }
+        for (int j = 0; j < n; ++j) A[(size_t)i * 2 * n + j] = G[(size_t)i * n + j];
         A[(size_t)i * 2 * n + n + i] = 1.0;
     }
-    std::vector<double> G((size_t)n * n);
-    for (int i = 0; i < n; ++i)
-        for (int b = 0; b < n; ++b) G[(size_t)i * n + b] = A[(size_t)i * 2 * n + b];
     for (int c = 0; c < n; ++c) {
         int p = c;
         for (int r = c + 1; r < n; ++r)
@@ -563,7 +541,7 @@ static std::vector<double> lagrange_in_bernstein(const RefElement& e) {
         if (p != c)
             for (int j = 0; j < 2 * n; ++j) std::swap(A[(size_t)p * 2 * n + j], A[(size_t)c * 2 * n + j]);
         const double piv = A[(size_t)c * 2 * n + c];
-        if (piv == 0) throw std::runtime_error("singular Bernstein collocation matrix");
+        if (piv == 0) throw std::runtime_error("singular collocation matrix of a reference element");
         for (int j = 0; j < 2 * n; ++j) A[(size_t)c * 2 * n + j] /= piv;
         for (int r = 0; r < n; ++r) {
             if (r == c) continue;
@@ -572,14 +550,10 @@ static std::vector<double> lagrange_in_bernstein(const RefElement& e) {
             for (int j = 0; j < 2 * n; ++j) A[(size_t)r * 2 * n + j] -= f * A[(size_t)c * 2 * n + j];
         }
     }
-    // X = G^-1 sits in A[.][n ..); two steps of iterative refinement,
-    // X += X (I - G X), with the residual from compensated dot products
-    // bring X to working accuracy (the elimination alone leaves about
-    // cond(G) eps = 4e-13 at k = 10, which the tensors' sums amplify)
     std::vector<double> X((size_t)n * n), R((size_t)n * n);
     for (int b = 0; b < n; ++b)
         for (int i = 0; i < n; ++i) X[(size_t)b * n + i] = A[(size_t)b * 2 * n + n + i];
-    for (int step = 0; step < 2; ++step) {
+    for (int step = 0; step < steps; ++step) {
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) {
                 double sum = i == j ? 1.0 : 0.0, err = 0;
@@ -600,6 +574,30 @@ static std::vector<double> lagrange_in_bernstein(const RefElement& e) {
             }
         X.swap(Xn);
     }
+    return X;
+}
+
+// Bernstein coefficients of the degree-k Lagrange basis of `e`: row i holds
+// phi_i = sum_b C[i][b] B_b, b in lattice_indices(d, k) order.  C = G^-T for
+// the collocation matrix G[node][b] = B_b(node) = (k!/b!) prod_c alpha_c^b_c
+// / k^k.  k^k G is an integer matrix with entries at most k^k (the
+// multinomial theorem), exact in double up to k = 10, so it is inverted
+// exactly as given (cond below 4e3 up to k = 10 in 3D).
+static std::vector<double> lagrange_in_bernstein(const RefElement& e) {
+    const int d = e.d, k = e.k, n = e.nb;
+    const auto B = lattice_indices(d, k);
+    long long kk = 1;
+    for (int c = 0; c < k; ++c) kk *= k;
+    if (kk > (1LL << 53)) throw std::runtime_error("reference element degree too high for exact collocation");
+    std::vector<double> G((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int b = 0; b < n; ++b) {
+            long long num = 1;
+            for (int c = 0; c <= d; ++c)
+                for (int t = 0; t < B[b][c]; ++t) num *= e.alpha[i][c];
+            G[(size_t)i * n + b] = (double)(multinomial(B[b], d) * num);   // at most k^k
+        }
+    const std::vector<double> X = invert_refined(G, n, 2);
     std::vector<double> C((size_t)n * n);
     for (int b = 0; b < n; ++b)
         for (int i = 0; i < n; ++i) C[(size_t)i * n + b] = X[(size_t)b * n + i] * (double)kk;
