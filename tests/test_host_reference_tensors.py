@@ -36,7 +36,15 @@ def dump(tmp_path_factory):
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
 
-    def run(d, k):
+    def run(d, k, points=None):
+        if points is not None:
+            txt = "\n".join(" ".join(repr(float(x)) for x in p) for p in points) + "\n"
+            out = subprocess.run([exe, str(d), str(k), "eval"], input=txt, capture_output=True, text=True,
+                                 check=True).stdout.split("\n")
+            nb = len(lagrange.multi_indices(k, d))
+            av = [tuple(map(int, x.split()))[:d + 1] for x in out[:nb]]
+            vals = np.array([[float(y) for y in x.split()] for x in out[nb:] if x])
+            return av, vals
         out = subprocess.run([exe, str(d), str(k)], capture_output=True, text=True, check=True).stdout.split("\n")
         nb, nq = map(int, out[0].split())
         av = [tuple(map(int, x.split()))[:d + 1] for x in out[1:1 + nb]]
@@ -85,3 +93,21 @@ def test_reference_tensors_match_oracle(dump, d, k):
             assert np.array_equal(S[a, b], S[b, a].T), (d, k, a, b)   # stored exactly symmetric
     assert rel(qi, qio[pq]) < 1e-13, (d, k)
     assert abs(qi.sum() - 1 / math.factorial(d)) < 1e-14          # the pressure basis sums to one
+
+
+@pytest.mark.parametrize("d,k", [(2, 2), (2, 5), (2, 10), (3, 3), (3, 6)])
+def test_basis_evaluation_matches_oracle(dump, d, k):
+    """RefElement::eval (the transfers evaluate the coarse basis with it) at
+    seeded random points of the reference simplex and at its vertices: the
+    library's Bernstein-form values equal the oracle's Silvester product to
+    1e-13 relative to the largest value (both float64; at k = 10 in 2D the
+    values reach about 6 and the two differ by 7.5e-14 at most)."""
+    rng = np.random.default_rng(10 * d + k)
+    lam = rng.dirichlet(np.ones(d + 1), size=40)
+    lam = np.vstack([lam, np.eye(d + 1)])
+    av, vals = dump(d, k, points=lam[:, 1:])
+    iv = [tuple(x) for x in lagrange.multi_indices(k, d)]
+    pv = [iv.index(a) for a in av]
+    want = lagrange.basis(k, d, lam)[:, pv]
+    assert vals.shape == want.shape
+    assert np.abs(vals - want).max() < 1e-13 * max(1.0, np.abs(want).max()), (d, k)
