@@ -198,3 +198,32 @@ def test_host_sv_hierarchy_levels():
         assert i["is_p_level"][:nl] == [1] * (p - 1) + [0] * (nl - p + 1), (k, i["is_p_level"][:nl])
         assert nl - p == 3                       # meshes: split finest, finest, once refined, coarse
         h.close()
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[3], CASES[5]], ids=[CASES[i][0] for i in (1, 3, 5)])
+def test_host_hierarchy_with_cell_viscosity_matches_oracle(case):
+    """A seeded per-cell viscosity on the finest cells (nu = exp(N(0, 1/4))):
+    the library's K on every level, coarse cells taking their children's
+    mean, equals the oracle's with the same reading.  Cells are matched by
+    their centroids."""
+    from oracle import geometry
+    from tests.dofmap import keys, permutation
+    name, (v, c), nref, fam, k, sched, bary = case
+    meshes, _ = geometry.hierarchy(v, c, nref, bary)
+    vf, cf = meshes[0]
+    nu_o = np.exp(0.5 * np.random.default_rng(5).standard_normal(len(cf)))
+    probe = P.StokesMG(v, c, nref, fam, k, barycentric=bary, host_only=1, hierarchy=P.HIER_EXPLICIT, schedule=sched)
+    cent = probe.cell_centroids()
+    probe.close()
+    pc = permutation(keys(cent, np.zeros(len(cent))), keys(vf[cf].mean(axis=1), np.zeros(len(cf))))
+    nu_l = np.empty_like(nu_o)
+    nu_l[pc] = nu_o
+    h = P.StokesMG(v, c, nref, fam, k, barycentric=bary, nu_cell=nu_l, host_only=1,
+                   hierarchy=P.HIER_EXPLICIT, schedule=sched)
+    ora = mg.Hierarchy(v, c, nref, fam, sched, barycentric=bary, nu_cells=nu_o, lmax=[1.0] * 16)
+    assert h.info()["n_levels"] == len(ora.levels)
+    for li, L in enumerate(ora.levels):
+        perm = level_perm(h, li, L.disc)
+        K = h.get_csr(li, 0)[perm][:, perm]
+        assert abs(K - L.disc.K).max() <= 1e-12 * abs(L.disc.K).max(), (name, li)
+    h.close()
